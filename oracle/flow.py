@@ -1,0 +1,557 @@
+"""FP64 oracle: right-hand side and explicit stage update of the reacting Navier-Stokes equations.
+
+TEST INFRASTRUCTURE (see oracle/gas.py header). Not used by the product path.
+
+Discrete model (2D, staggered grid of Fig. 1; arrays indexed [j, i] with x fastest):
+
+* centres  (Ny, Nx):     rho, rho_s for every species but the first (N2, omitted, Sec. 2.1), rho*E
+* x-faces  (Ny, Nx+1):   rho*u          y-faces (Ny+1, Nx): rho*v
+* corners  (Ny+1, Nx+1): tau_xy and the cross momentum fluxes
+
+The right-hand side follows Eqs. (5)-(6) with the stress of Eq. (9) (Stokes' 2/3 restored), the
+heat flux of Eq. (10), the algebraic diffusion of Eq. (18) driven by mole-fraction gradients
+(Eq. 16), the sponge of Eq. (26), the nondimensionalisation of Eqs. (7)-(8), (11), and an
+artificial shear viscosity, bulk viscosity, conductivity and species diffusivity for shock
+capturing (Sec. 3.3). Time integration is the two-register third-order Runge-Kutta scheme
+(Sec. 3.1). Every step is written in the order it is listed in ``rhs``; the compact operators come
+from oracle/compact.py and the closure from oracle/gas.py.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+from scipy.special import erf
+
+from . import compact as C
+from . import gas as G
+
+KIND_CNEQ, KIND_FROZEN, KIND_CPG = "cneq", "frozen", "cpg"
+
+SUTHERLAND_C1 = 1.458e-6      # kg m^-1 s^-1 K^-1/2 (Eq. 24)
+SUTHERLAND_TS = 110.4         # K (Eq. 24)
+RECOVERY_FACTOR = 0.85
+DUCROS_EPS = 1.0e-32
+GAUSS9 = (3565.0 / 10368.0, 3091.0 / 12960.0, 1997.0 / 25920.0, 149.0 / 12960.0, 107.0 / 103680.0)
+
+# Williamson low-storage RK3 (two registers): dQ <- A_k dQ + dt R(Q);  Q <- Q + B_k dQ
+RK_A = (0.0, -5.0 / 9.0, -153.0 / 128.0)
+RK_B = (1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0)
+
+
+def sutherland(T):
+    """Eq. (24)."""
+    return SUTHERLAND_C1 * T ** 1.5 / (T + SUTHERLAND_TS)
+
+
+@dataclasses.dataclass
+class Scales:
+    """Freestream reference values of Eq. (7) and the numbers of Eq. (11)."""
+    rho: float
+    a: float
+    T: float
+    p: float
+    mu: float
+    k: float
+    cp: float
+    gamma: float
+    R: float
+    T_ref: float
+    L_ref: float
+    Re: float
+    Pr: float
+    mach: float
+
+
+def freestream_scales(tab, kind, cfg) -> Scales:
+    Y = np.array(cfg["Y_inf"], dtype=np.float64)[:, None]
+    T = np.array([cfg["T_inf"]])
+    R = float(G.mixture_gas_constant(tab, Y)[0])
+    cv = float(G.mixture_cv(tab, T, Y)[0])
+    cp = cv + R
+    gamma = cp / cv
+    rho = cfg["p_inf"] / (R * cfg["T_inf"])
+    a = math.sqrt(gamma * R * cfg["T_inf"])
+    if kind == KIND_CPG:
+        mu = float(sutherland(cfg["T_inf"]))
+        k = mu * cp / cfg["prandtl_cpg"]
+    else:
+        X = G.mole_fractions(tab, Y)
+        mu_s = G.species_viscosity(tab, T)
+        k_s = G.species_conductivity(tab, T, mu_s)
+        mu = float(G.wilke_mix(tab, X, mu_s, mu_s)[0])
+        k = float(G.wilke_mix(tab, X, mu_s, k_s)[0])
+    Re = cfg["reynolds"]
+    return Scales(rho=rho, a=a, T=cfg["T_inf"], p=cfg["p_inf"], mu=mu, k=k, cp=cp, gamma=gamma,
+                  R=R, T_ref=(gamma - 1.0) * cfg["T_inf"], L_ref=Re * mu / (rho * a), Re=Re,
+                  Pr=mu * cp / k, mach=cfg["mach"])
+
+
+# ---------------------------------------------------------------------------------------------
+# Grid (tensor product of 1-D maps; Eq. 27 and a tanh wall clustering)
+# ---------------------------------------------------------------------------------------------
+
+def y_map(cfg, eta):
+    """Physical y of the index coordinate eta in [0, Ny] (faces at integers) and dy/deta."""
+    y0, y1, ny = cfg["y0"], cfg["y1"], cfg["ny"]
+    s = np.asarray(eta, dtype=np.float64) / ny
+    kind, q = cfg["y_stretch"], cfg["y_param"]
+    if kind == "uniform":
+        y = y0 + (y1 - y0) * s
+        dy = np.full_like(s, (y1 - y0))
+    elif kind == "tanh":
+        y = y0 + (y1 - y0) * (1.0 - np.tanh(q * (1.0 - s)) / np.tanh(q))
+        dy = (y1 - y0) * q / np.cosh(q * (1.0 - s)) ** 2 / np.tanh(q)
+    elif kind == "cubic":
+        y = y0 + (y1 - y0) * ((1.0 - q) * s ** 3 + q * s)
+        dy = (y1 - y0) * (3.0 * (1.0 - q) * s ** 2 + q)
+    else:
+        raise ValueError(kind)
+    return y, dy / ny
+
+
+@dataclasses.dataclass
+class Grid:
+    nx: int
+    ny: int
+    xc: np.ndarray
+    xf: np.ndarray
+    yc: np.ndarray
+    yf: np.ndarray
+    xi_c: np.ndarray      # d(xi)/dx at x-centres
+    xi_f: np.ndarray      # at x-faces
+    eta_c: np.ndarray     # d(eta)/dy at y-centres
+    eta_f: np.ndarray     # at y-faces
+
+
+def make_grid(cfg) -> Grid:
+    nx, ny = cfg["nx"], cfg["ny"]
+    dx = (cfg["x1"] - cfg["x0"]) / nx
+    xf = cfg["x0"] + dx * np.arange(nx + 1)
+    xc = cfg["x0"] + dx * (np.arange(nx) + 0.5)
+    yf, dyf = y_map(cfg, np.arange(ny + 1, dtype=np.float64))
+    yc, dyc = y_map(cfg, np.arange(ny, dtype=np.float64) + 0.5)
+    return Grid(nx, ny, xc, xf, yc, yf, np.full(nx, 1.0 / dx), np.full(nx + 1, 1.0 / dx),
+                1.0 / dyc, 1.0 / dyf)
+
+
+# ---------------------------------------------------------------------------------------------
+# Case set-up: reference solution, sponge, initial state
+# ---------------------------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Case:
+    cfg: dict
+    tab: G.GasTable
+    kind: str
+    sc: Scales
+    grid: Grid
+    U_ref: dict
+    sigma: dict          # sponge strength at 'c', 'xf', 'yf'
+    U0: dict
+
+
+def oblique_shock(M1, theta, gamma):
+    """Weak oblique-shock solution of the theta-beta-M relation and the Rankine-Hugoniot jumps.
+    Returns beta, p2/p1, rho2/rho1, T2/T1, M2."""
+    def deflection(beta):
+        return math.atan(2.0 / math.tan(beta) * (M1 ** 2 * math.sin(beta) ** 2 - 1.0)
+                         / (M1 ** 2 * (gamma + math.cos(2.0 * beta)) + 2.0))
+    mu = math.asin(1.0 / M1)
+    lo = mu + 1e-12
+    hi = lo
+    step = 1.0e-3
+    while deflection(hi + step) > deflection(hi):
+        hi += step
+    if deflection(hi) < theta:
+        raise ValueError("deflection beyond the attached-shock limit")
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if deflection(mid) < theta:
+            lo = mid
+        else:
+            hi = mid
+    beta = 0.5 * (lo + hi)
+    Mn1 = M1 * math.sin(beta)
+    p21 = 1.0 + 2.0 * gamma / (gamma + 1.0) * (Mn1 ** 2 - 1.0)
+    r21 = (gamma + 1.0) * Mn1 ** 2 / ((gamma - 1.0) * Mn1 ** 2 + 2.0)
+    T21 = p21 / r21
+    Mn2 = math.sqrt((1.0 + 0.5 * (gamma - 1.0) * Mn1 ** 2) / (gamma * Mn1 ** 2 - 0.5 * (gamma - 1.0)))
+    M2 = Mn2 / math.sin(beta - theta)
+    return beta, p21, r21, T21, M2
+
+
+def _primitive_profile(case_cfg, sc, tab, kind, x, y):
+    """Reference primitives (T[K], p[Pa], u, v [nondim], Y) at points (x, y)."""
+    cfg = case_cfg
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    shape = np.broadcast(x, y).shape
+    x = np.broadcast_to(x, shape)
+    y = np.broadcast_to(y, shape)
+
+    def edge_profile(Te, pe, ue, ve, Me):
+        if cfg["wall"]:
+            delta = cfg["delta_coef"] * np.sqrt(x / (sc.Re * sc.mach))
+            f = erf(2.0 * (y - cfg["y0"]) / delta)
+            Tr = Te * (1.0 + RECOVERY_FACTOR * 0.5 * (sc.gamma - 1.0) * Me ** 2)
+            Tw = cfg["T_wall"]
+            T = Tw + (Tr - Tw) * f - (Tr - Te) * f * f
+        else:
+            f = np.ones(shape)
+            T = np.full(shape, Te)
+        return T, np.full(shape, pe), ue * f, ve * f, f
+
+    T, p, u, v, f = edge_profile(sc.T, sc.p, sc.mach, 0.0, sc.mach)
+    if cfg["flow"] == "sbli":
+        theta = math.radians(cfg["shock_deflection_deg"])
+        beta, p21, r21, T21, M2 = oblique_shock(sc.mach, theta, sc.gamma)
+        V2 = M2 * math.sqrt(T21)
+        T2, p2, u2, v2, f2 = edge_profile(sc.T * T21, sc.p * p21, V2 * math.cos(theta),
+                                          -V2 * math.sin(theta), M2)
+        ys = (cfg["shock_x"] - x) * math.tan(beta)
+        H = 0.5 * (1.0 + np.tanh((y - ys) / cfg["shock_width"]))
+        T = (1.0 - H) * T + H * T2
+        p = (1.0 - H) * p + H * p2
+        u = (1.0 - H) * u + H * u2
+        v = (1.0 - H) * v + H * v2
+    Yinf = np.array(cfg["Y_inf"], dtype=np.float64)
+    Y = np.zeros((tab.ns,) + shape)
+    m = cfg["minor_species"] * 4.0 * f * (1.0 - f) if (cfg["wall"] and kind != KIND_CPG) else 0.0 * f
+    names = [s.name for s in tab.species]
+    Y[:] = Yinf.reshape((-1,) + (1,) * len(shape))
+    Y[names.index("N2")] = Yinf[names.index("N2")] * (1.0 - m)
+    Y[names.index("O2")] = Yinf[names.index("O2")] * (1.0 - m)
+    Y[names.index("NO")] = 0.5 * m
+    Y[names.index("N")] = 0.2 * m
+    Y[names.index("O")] = 0.3 * m
+    return T, p, u, v, Y
+
+
+def _conserved_from_primitive(tab, kind, sc, T, p, u, v, Y):
+    """Nondimensional rho, rho_s, rho*E at points given SI T, p and nondim u, v."""
+    flatT = T.ravel()
+    flatY = Y.reshape(tab.ns, -1)
+    if kind == KIND_CPG:
+        rho_si = p.ravel() / (sc.R * flatT)
+        e_nd = (flatT / sc.T_ref) / sc.gamma
+    else:
+        rho_si = p.ravel() / (G.mixture_gas_constant(tab, flatY) * flatT)
+        e_nd = G.mixture_energy(tab, flatT, flatY) / sc.a ** 2
+    rho = (rho_si / sc.rho).reshape(T.shape)
+    e_nd = e_nd.reshape(T.shape)
+    rhoE = rho * (e_nd + 0.5 * (u * u + v * v))
+    return rho, rho * Y, rhoE
+
+
+STATE_FIELDS = None   # documented layout: rho, rho_s[1..ns-1], rhoE at centres; rhou; rhov
+
+
+def state_layout(ns, nx, ny):
+    """Offsets of the canonical state vector: (name, shape) in order."""
+    out = [("rho", (ny, nx))]
+    out += [(f"rs{s}", (ny, nx)) for s in range(1, ns)]
+    out += [("rhoE", (ny, nx)), ("rhou", (ny, nx + 1)), ("rhov", (ny + 1, nx))]
+    return out
+
+
+def pack(ns, nx, ny, fields):
+    return np.concatenate([np.asarray(fields[name], dtype=np.float64).ravel()
+                           for name, _ in state_layout(ns, nx, ny)])
+
+
+def unpack(ns, nx, ny, U):
+    out, off = {}, 0
+    for name, shape in state_layout(ns, nx, ny):
+        size = shape[0] * shape[1]
+        out[name] = np.asarray(U[off:off + size]).reshape(shape)
+        off += size
+    assert off == U.size
+    return out
+
+
+def sponge(cfg, grid, x, y):
+    """sigma(x, y) = sigma_max (r_in^3 + r_out^3 + r_top^3): cubic ramps inside each zone (Eq. 26)."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    s = np.zeros(np.broadcast(x, y).shape)
+    if cfg["sponge_in"] > 0:
+        r = np.clip((cfg["x0"] + cfg["sponge_in"] - x) / cfg["sponge_in"], 0.0, 1.0)
+        s = s + r ** 3
+    if cfg["sponge_out"] > 0:
+        r = np.clip((x - (cfg["x1"] - cfg["sponge_out"])) / cfg["sponge_out"], 0.0, 1.0)
+        s = s + r ** 3
+    ntop = cfg["sponge_top_cells"]
+    if ntop > 0:
+        ytop = grid.yf[cfg["ny"] - ntop]
+        r = np.clip((y - ytop) / (cfg["y1"] - ytop), 0.0, 1.0)
+        s = s + r ** 3
+    return cfg["sponge_sigma"] * s
+
+
+def make_case(cfg, tab, noise=None) -> Case:
+    kind = cfg["kind"]
+    sc = freestream_scales(tab, kind, cfg)
+    g = make_grid(cfg)
+    nx, ny, ns = g.nx, g.ny, tab.ns
+    Xc, Yc = np.meshgrid(g.xc, g.yc)
+    Xu, Yu = np.meshgrid(g.xf, g.yc)
+    Xv, Yv = np.meshgrid(g.xc, g.yf)
+    ref = {}
+    T, p, u, v, Y = _primitive_profile(cfg, sc, tab, kind, Xc, Yc)
+    rho, rhoY, rhoE = _conserved_from_primitive(tab, kind, sc, T, p, u, v, Y)
+    ref["rho"] = rho
+    for s in range(1, ns):
+        ref[f"rs{s}"] = rhoY[s]
+    ref["rhoE"] = rhoE
+    T, p, u, v, Y = _primitive_profile(cfg, sc, tab, kind, Xu, Yu)
+    rho_u, _, _ = _conserved_from_primitive(tab, kind, sc, T, p, u, v, Y)
+    ref["rhou"] = rho_u * u
+    T, p, u, v, Y = _primitive_profile(cfg, sc, tab, kind, Xv, Yv)
+    rho_v, _, _ = _conserved_from_primitive(tab, kind, sc, T, p, u, v, Y)
+    ref["rhov"] = rho_v * v
+    sigma = dict(c=sponge(cfg, g, Xc, Yc), xf=sponge(cfg, g, Xu, Yu), yf=sponge(cfg, g, Xv, Yv))
+    U_ref = pack(ns, nx, ny, ref)
+    U0 = U_ref.copy()
+    if noise is not None and cfg["noise_amp"] > 0:
+        U0 = U_ref * (1.0 + cfg["noise_amp"] * noise)
+        f = unpack(ns, nx, ny, U0)
+        r = unpack(ns, nx, ny, U_ref)
+        f["rhou"][:, 0] = r["rhou"][:, 0]
+        f["rhou"][:, nx] = r["rhou"][:, nx]
+        f["rhov"][0, :] = r["rhov"][0, :]
+        f["rhov"][ny, :] = r["rhov"][ny, :]
+    return Case(cfg=cfg, tab=tab, kind=kind, sc=sc, grid=g, U_ref=U_ref, sigma=sigma, U0=U0)
+
+
+# ---------------------------------------------------------------------------------------------
+# Pointwise closure in nondimensional variables
+# ---------------------------------------------------------------------------------------------
+
+def closure_nd(case: Case, rho, e, Y):
+    """Nondimensional T, p, h_s, w_s, mu, k, D_s, X_s, W_s = rho M_s / M_mix, frozen sound speed."""
+    sc, tab, kind = case.sc, case.tab, case.kind
+    shape = rho.shape
+    r1 = rho.ravel()
+    e1 = e.ravel()
+    Y1 = Y.reshape(tab.ns, -1)
+    ns = tab.ns
+    if kind == KIND_CPG:
+        T = sc.gamma * e1
+        p = r1 * (sc.gamma - 1.0) / sc.gamma * T
+        mu = sutherland(T * sc.T_ref) / sc.mu
+        out = dict(T=T, p=p, h_s=np.zeros_like(Y1), wdot=np.zeros_like(Y1), mu=mu, k=mu,
+                   D=np.zeros_like(Y1), X=np.zeros_like(Y1), W=np.zeros_like(Y1),
+                   a=np.sqrt(sc.gamma * p / r1))
+    else:
+        th = G.thermo_eval(tab, r1 * sc.rho, e1 * sc.a ** 2, Y1, reactions=(kind == KIND_CNEQ))
+        M = tab.M()[:, None]
+        Mmix = 1.0 / np.sum(Y1 / M, axis=0)
+        diffusive = kind == KIND_CNEQ
+        out = dict(T=th["T"] / sc.T_ref, p=th["p"] / (sc.rho * sc.a ** 2),
+                   h_s=th["h_s"] / sc.a ** 2,
+                   wdot=th["wdot"] * sc.L_ref / (sc.rho * sc.a),
+                   mu=th["mu"] / sc.mu, k=th["k"] / sc.k,
+                   D=(th["D"] * sc.rho / sc.mu) if diffusive else np.zeros_like(Y1),
+                   X=th["X"], W=(r1 * M / Mmix) if diffusive else np.zeros_like(Y1),
+                   a=th["a"] / sc.a)
+    res = {}
+    for key, val in out.items():
+        res[key] = val.reshape((ns,) + shape) if val.ndim == 2 else val.reshape(shape)
+    return res
+
+
+# ---------------------------------------------------------------------------------------------
+# Artificial diffusivity helpers (Sec. 3.3)
+# ---------------------------------------------------------------------------------------------
+
+def delta4(f, axis):
+    """Fourth index difference (1, -4, 6, -4, 1); the two rows nearest each end reuse the
+    stencil centred on the nearest row where it fits."""
+    fm = np.moveaxis(f, axis, 0)
+    n = fm.shape[0]
+    out = np.empty_like(fm)
+    for i in range(n):
+        c = min(max(i, 2), n - 3)
+        out[i] = fm[c - 2] - 4.0 * fm[c - 1] + 6.0 * fm[c] - 4.0 * fm[c + 1] + fm[c + 2]
+    return np.moveaxis(out, 0, axis)
+
+
+def gauss9(f, axis):
+    """Nine-point truncated Gaussian filter; indices beyond the ends take the end value."""
+    fm = np.moveaxis(f, axis, 0)
+    n = fm.shape[0]
+    out = np.zeros_like(fm)
+    for i in range(n):
+        acc = GAUSS9[0] * fm[i]
+        for d in range(1, 5):
+            acc = acc + GAUSS9[d] * (fm[max(i - d, 0)] + fm[min(i + d, n - 1)])
+        out[i] = acc
+    return np.moveaxis(out, 0, axis)
+
+
+def filter2(f):
+    return gauss9(gauss9(f, 1), 0)
+
+
+# ---------------------------------------------------------------------------------------------
+# The right-hand side
+# ---------------------------------------------------------------------------------------------
+
+def rhs(case: Case, U, return_parts=False):
+    cfg, sc, g, tab = case.cfg, case.sc, case.grid, case.tab
+    ns, nx, ny = tab.ns, g.nx, g.ny
+    q = unpack(ns, nx, ny, np.asarray(U, dtype=np.float64))
+    Re, Pr = sc.Re, sc.Pr
+    wall = bool(cfg["wall"])
+    xi_c = g.xi_c[None, :]
+    xi_f = g.xi_f[None, :]
+    eta_c = g.eta_c[:, None]
+    eta_f = g.eta_f[:, None]
+    rho = q["rho"]
+    rhou, rhov, rhoE = q["rhou"], q["rhov"], q["rhoE"]
+
+    # (A) primitives at centres (face momenta interpolated to centres; omitted species recovered)
+    ru_c = C.ifc(rhou, 1)
+    rv_c = C.ifc(rhov, 0)
+    rho_s = [rho - sum(q[f"rs{s}"] for s in range(1, ns))] + [q[f"rs{s}"] for s in range(1, ns)]
+    Y = np.stack([r / rho for r in rho_s])
+    u_c = ru_c / rho
+    v_c = rv_c / rho
+    e = rhoE / rho - 0.5 * (u_c * u_c + v_c * v_c)          # Eq. (8) with Ec = 1
+    th = closure_nd(case, rho, e, Y)
+    T, p = th["T"], th["p"]
+    H = (rhoE + p) / rho
+
+    # (B) face velocities
+    rho_xf = C.icf(rho, 1)
+    u_xf = rhou / rho_xf
+    rho_yf = C.icf(rho, 0)
+    v_yf = rhov / rho_yf
+
+    # (C) velocity gradients: normal ones at centres, cross ones at corners
+    dudx = xi_c * C.dfc(u_xf, 1)
+    dvdy = eta_c * C.dfc(v_yf, 0)
+    div = dudx + dvdy
+    uwall = 0.0 if wall else None
+    dudy_cn = eta_f * C.dcf(u_xf, 0, uwall)
+    dvdx_cn = xi_f * C.dcf(v_yf, 1)
+    u_cn = C.icf(u_xf, 0, uwall)
+    v_cn = C.icf(v_yf, 1)
+
+    # (D) artificial diffusivities at centres
+    if cfg["artificial_diffusivity"]:
+        dudy_c = C.ifc(C.ifc(dudy_cn, 0), 1)
+        dvdx_c = C.ifc(C.ifc(dvdx_cn, 0), 1)
+        S = np.sqrt(dudx * dudx + dvdy * dvdy + 0.5 * (dudy_c + dvdx_c) ** 2)
+        omega = dvdx_c - dudy_c
+        fsw = np.where(div < 0.0, div * div / (div * div + omega * omega + DUCROS_EPS), 0.0)
+        dx = 1.0 / xi_c
+        dy = 1.0 / eta_c
+        mu_st = filter2(cfg["C_mu"] * rho * np.abs(delta4(S, 1) * dx * dx + delta4(S, 0) * dy * dy))
+        beta_st = filter2(cfg["C_beta"] * rho * fsw
+                          * np.abs(delta4(div, 1) * dx * dx + delta4(div, 0) * dy * dy))
+        kap_st = filter2(cfg["C_kappa"] * rho * th["a"] / T
+                         * np.abs(delta4(e, 1) * dx + delta4(e, 0) * dy))
+        D_st = np.stack([filter2(cfg["C_D"] * th["a"]
+                                 * np.abs(delta4(Y[s], 1) * dx + delta4(Y[s], 0) * dy))
+                         for s in range(ns)])
+    else:
+        mu_st = beta_st = kap_st = np.zeros_like(rho)
+        D_st = np.zeros_like(Y)
+    if case.kind != KIND_CNEQ:
+        D_st = np.zeros_like(Y)
+
+    # (E) transport coefficients (viscous scale 1/Re, conduction 1/(Re Pr Ec), diffusion 1/Re)
+    mu_e = th["mu"] / Re + mu_st
+    K = th["k"] / (Re * Pr) + kap_st
+    Gd = th["W"] * (th["D"] / Re + D_st)
+
+    # (F) viscous stresses, Eq. (9) with the Stokes 2/3 and the artificial bulk viscosity
+    tau_xx = mu_e * (2.0 * dudx - 2.0 / 3.0 * div) + beta_st * div
+    tau_yy = mu_e * (2.0 * dvdy - 2.0 / 3.0 * div) + beta_st * div
+    mu_cn = C.icf(C.icf(mu_e, 1), 0)
+    tau_xy = mu_cn * (dudy_cn + dvdx_cn)
+
+    # (G) x-fluxes at x-faces
+    Yx = np.stack([C.icf(Y[s], 1) for s in range(ns)])
+    Gx = np.stack([C.icf(Gd[s], 1) for s in range(ns)])
+    hx = np.stack([C.icf(th["h_s"][s], 1) for s in range(ns)])
+    dXdx = np.stack([xi_f * C.dcf(th["X"][s], 1) for s in range(ns)])
+    Hx = C.icf(H, 1)
+    Kx = C.icf(K, 1)
+    dTdx = xi_f * C.dcf(T, 1)
+    txx_x = C.icf(tau_xx, 1)
+    v_x = C.icf(v_c, 1)
+    txy_x = C.ifc(tau_xy, 0)
+    sumx = np.sum(Gx * dXdx, axis=0)
+    Jx = -(Gx * dXdx - Yx * sumx)                            # Eq. (18), gradient of X (Eq. 16)
+    Fsx = [rhou * Yx[s] + Jx[s] for s in range(ns)]
+    qx = -Kx * dTdx + np.sum(hx * Jx, axis=0)                # Eq. (10)
+    FEx = rhou * Hx + qx - (txx_x * u_xf + txy_x * v_x)
+
+    # (H) y-fluxes at y-faces (wall: T = T_w, u = 0, no diffusion through the wall)
+    Tw = cfg["T_wall"] / sc.T_ref if wall else None
+    Yy = np.stack([C.icf(Y[s], 0) for s in range(ns)])
+    Gy = np.stack([C.icf(Gd[s], 0) for s in range(ns)])
+    hy = np.stack([C.icf(th["h_s"][s], 0) for s in range(ns)])
+    dXdy = np.stack([eta_f * C.dcf(th["X"][s], 0) for s in range(ns)])
+    Hy = C.icf(H, 0)
+    Ky = C.icf(K, 0)
+    dTdy = eta_f * C.dcf(T, 0, Tw)
+    tyy_y = C.icf(tau_yy, 0)
+    u_y = C.icf(u_c, 0, uwall)
+    txy_y = C.ifc(tau_xy, 1)
+    sumy = np.sum(Gy * dXdy, axis=0)
+    Jy = -(Gy * dXdy - Yy * sumy)
+    if wall:
+        Jy[:, 0, :] = 0.0
+    Fsy = [rhov * Yy[s] + Jy[s] for s in range(ns)]
+    qy = -Ky * dTdy + np.sum(hy * Jy, axis=0)
+    FEy = rhov * Hy + qy - (txy_y * u_y + tyy_y * v_yf)
+
+    # (I) momentum fluxes
+    Gxx = ru_c * u_c + p - tau_xx
+    Gyy = rv_c * v_c + p - tau_yy
+    rho_cn = C.icf(rho_xf, 0)
+    Gxy = rho_cn * u_cn * v_cn - tau_xy
+
+    # (J) divergences, sources, sponge, boundary rows
+    R = {}
+    R["rho"] = -(xi_c * C.dfc(rhou, 1) + eta_c * C.dfc(rhov, 0))
+    for s in range(1, ns):
+        R[f"rs{s}"] = -(xi_c * C.dfc(Fsx[s], 1) + eta_c * C.dfc(Fsy[s], 0)) + th["wdot"][s]
+    R["rhoE"] = -(xi_c * C.dfc(FEx, 1) + eta_c * C.dfc(FEy, 0))
+    R["rhou"] = -(xi_f * C.dcf(Gxx, 1) + eta_c * C.dfc(Gxy, 0))
+    R["rhov"] = -(xi_c * C.dfc(Gxy, 1) + eta_f * C.dcf(Gyy, 0))
+    ref = unpack(ns, nx, ny, case.U_ref)
+    for name, _ in state_layout(ns, nx, ny):
+        sig = case.sigma["xf" if name == "rhou" else "yf" if name == "rhov" else "c"]
+        R[name] = R[name] - sig * (q[name] - ref[name])
+    R["rhou"][:, 0] = 0.0
+    R["rhou"][:, nx] = 0.0
+    R["rhov"][0, :] = 0.0
+    R["rhov"][ny, :] = 0.0
+    out = pack(ns, nx, ny, R)
+    if return_parts:
+        return out, dict(T=T, p=p, th=th, mu_st=mu_st, beta_st=beta_st, kap_st=kap_st, D_st=D_st,
+                         tau_xy=tau_xy, dTdy=dTdy)
+    return out
+
+
+def rk_stage(case: Case, U, dQ, stage, dt):
+    """One stage of the two-register RK3: returns (U_new, dQ_new, R)."""
+    R = rhs(case, U)
+    dQ = RK_A[stage] * dQ + dt * R
+    return U + RK_B[stage] * dQ, dQ, R
+
+
+def wall_fluxes(case: Case, U):
+    """Wall heat flux q_w = -K dT/dy and shear tau_w = mu du/dy at the wall (nondimensional)."""
+    _, parts = rhs(case, U, return_parts=True)
+    sc = case.sc
+    th = parts["th"]
+    K = th["k"] / (sc.Re * sc.Pr) + parts["kap_st"]
+    Kw = C.icf(K, 0)[0]
+    return -Kw * parts["dTdy"][0], parts["tau_xy"][0]

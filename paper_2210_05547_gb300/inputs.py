@@ -1,0 +1,75 @@
+"""Seeded synthetic inputs shared by the CUDA path, its tests, the bench and the oracle.
+
+This module holds case parameters and random draws only: it performs none of the method's
+arithmetic (no thermodynamics, no grid metrics, no fluxes). Both sides turn these parameters into
+states with their own code.
+
+Workloads (shapes follow the paper's cases; there is no dataset):
+
+* ``bl_case``   -- Mach 10 flat-plate boundary layer (Table 1, Table 2 proportions), 256 x 64 cells,
+  tanh wall clustering, isothermal 1000 K wall, T_inf = 350 K, p_inf = 3 kPa.
+* ``sbli_case`` -- oblique-shock / boundary-layer interaction, 2048 x 256 cells, domain and
+  freestream of the Mach 5.92 case of Table 3 (x 19-254, y 0-36, kappa_y = 0.15, T_inf = 1110.5 K,
+  p_inf = 60967 Pa); Mach number drawn in [6, 9] and flow deflection in [8, 14] degrees from the seed;
+  artificial diffusivity on.
+* ``thermo_states`` -- independent thermochemical states: T log-uniform in [300, 15000] K,
+  rho log-uniform in [1e-4, 1] kg/m^3, mass fractions Dirichlet(1).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+AIR_Y = (0.767, 0.233, 0.0, 0.0, 0.0)      # N2, O2, NO, N, O
+
+
+def bl_case(nx=256, ny=64, seed=0, kind="cneq"):
+    """Hypersonic flat-plate boundary layer (Mach 10, Re_inf = 1e5 on a_inf)."""
+    return dict(
+        name=f"bl_{nx}x{ny}", kind=kind, seed=seed,
+        nx=nx, ny=ny, x0=14.0, x1=86.0, y0=0.0, y1=1.6, y_stretch="tanh", y_param=2.5,
+        T_inf=350.0, p_inf=3000.0, Y_inf=AIR_Y, mach=10.0, reynolds=1.0e5, prandtl_cpg=0.72,
+        flow="bl", wall=1, T_wall=1000.0, delta_coef=70.0, minor_species=0.02,
+        shock_deflection_deg=0.0, shock_x=0.0, shock_width=0.0,
+        sponge_sigma=2.0, sponge_in=5.0, sponge_out=15.0, sponge_top_cells=max(2, (26 * ny) // 211),
+        artificial_diffusivity=0, C_mu=0.002, C_beta=1.75, C_kappa=0.01, C_D=0.0,
+        noise_amp=1.0e-4, dt=2.0e-4,
+    )
+
+
+def sbli_case(nx=2048, ny=256, seed=0, kind="cneq"):
+    """Oblique shock impinging on a hypersonic boundary layer, artificial diffusivity on."""
+    rng = np.random.default_rng(seed)
+    mach = float(rng.uniform(6.0, 9.0))
+    deflection = float(rng.uniform(8.0, 14.0))
+    return dict(
+        name=f"sbli_{nx}x{ny}", kind=kind, seed=seed,
+        nx=nx, ny=ny, x0=19.0, x1=254.0, y0=0.0, y1=36.0, y_stretch="cubic", y_param=0.15,
+        T_inf=1110.5, p_inf=60967.0, Y_inf=AIR_Y, mach=mach, reynolds=2000.0, prandtl_cpg=0.72,
+        flow="sbli", wall=1, T_wall=1500.0, delta_coef=5.0 * 4.0, minor_species=0.02,
+        shock_deflection_deg=deflection, shock_x=120.0, shock_width=1.0,
+        sponge_sigma=2.0, sponge_in=10.0, sponge_out=30.0, sponge_top_cells=max(2, (26 * ny) // 211),
+        artificial_diffusivity=1, C_mu=0.002, C_beta=1.75, C_kappa=0.01, C_D=0.01,
+        noise_amp=1.0e-4, dt=2.0e-3,
+    )
+
+
+def box_case(nx=32, ny=24, seed=0, kind="cneq"):
+    """Uniform freestream in a box with far-field boundaries on all sides (no wall)."""
+    c = bl_case(nx, ny, seed, kind)
+    c.update(name=f"box_{nx}x{ny}", wall=0, y_stretch="tanh", minor_species=0.0, noise_amp=0.0,
+             sponge_in=0.0, sponge_out=0.0)
+    return c
+
+
+def state_noise(n, seed):
+    """Perturbation field in [-1, 1], one value per entry of the conserved state vector."""
+    return np.random.default_rng(np.random.SeedSequence([seed, 0x5eed])).uniform(-1.0, 1.0, n)
+
+
+def thermo_states(n, seed=0, ns=5):
+    """Independent states for the thermochemistry sweep: (T, rho, Y[ns, n])."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0x7e57]))
+    T = np.exp(rng.uniform(np.log(300.0), np.log(15000.0), n))
+    rho = np.exp(rng.uniform(np.log(1.0e-4), np.log(1.0), n))
+    Y = rng.dirichlet(np.ones(ns), n).T.copy()
+    return T, rho, Y

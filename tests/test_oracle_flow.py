@@ -1,0 +1,299 @@
+"""Pins for the oracle's discrete right-hand side and Runge-Kutta stage (Eqs. 1-11, 26; Sec. 3.1).
+
+* Freestream preservation: a uniform state has a zero right-hand side.
+* Sponge (Eq. 26): with a uniform state the right-hand side is exactly -sigma (Q - Q_ref).
+* RK3: the stage sequence applied to y' = lambda y multiplies y by 1 + z + z^2/2 + z^3/6.
+* PDE consistency, perfect gas: on smooth manufactured fields the discrete right-hand side
+  converges to the continuous one, differentiated symbolically here from Eqs. (1)-(6), (9), (10),
+  (22) and (24).
+* PDE consistency, reacting gas: a cold two-species (N2/O2) mixture, where the algebraic
+  diffusion model must reduce to Fick's law J = -rho D_12 grad Y; the continuous reference is
+  built from that textbook form by pointwise closure calls and finite differences.
+"""
+import math
+
+import numpy as np
+import pytest
+import sympy
+
+from oracle import compact as C
+from oracle import flow as F
+from oracle import gas as G
+from paper_2210_05547_gb300 import inputs as I
+
+
+def _nstate(cfg, ns=5):
+    return sum(a * b for _, (a, b) in F.state_layout(ns, cfg["nx"], cfg["ny"]))
+
+
+def test_freestream_preservation(table):
+    cfg = I.box_case(24, 16)
+    case = F.make_case(cfg, table)
+    R = F.rhs(case, case.U0)
+    parts = F.unpack(5, 24, 16, R)
+    ref = F.unpack(5, 24, 16, case.U0)
+    for name in parts:
+        scale = max(np.abs(ref[name]).max(), 1.0)
+        assert np.abs(parts[name]).max() < 1e-13 * scale, name
+
+
+def test_sponge_term_on_uniform_state(table):
+    cfg = I.box_case(24, 16)
+    cfg.update(sponge_in=20.0, sponge_out=20.0, sponge_top_cells=5)
+    case = F.make_case(cfg, table)
+    U = case.U0.copy()
+    case.U_ref = U * 1.01 + 0.001
+    R = F.unpack(5, 24, 16, F.rhs(case, U))
+    d = F.unpack(5, 24, 16, U - case.U_ref)
+    exp = {n: -case.sigma["xf" if n == "rhou" else "yf" if n == "rhov" else "c"] * d[n] for n in d}
+    exp["rhou"][:, [0, 24]] = 0.0
+    exp["rhov"][[0, 16], :] = 0.0
+    assert max(case.sigma["c"].max(), 0) > 0.5
+    for n in R:
+        assert np.abs(R[n] - exp[n]).max() < 1e-13 * max(1.0, np.abs(U).max()), n
+
+
+def test_rk3_amplification_polynomial(monkeypatch):
+    for z in (0.3, -1.1, 0.5j, -0.7 + 1.2j):
+        monkeypatch.setattr(F, "rhs", lambda case, U, z=z: z * U)
+        U = np.array([1.0 + 0.0j])
+        dQ = np.zeros_like(U)
+        for k in range(3):
+            U, dQ, _ = F.rk_stage(None, U, dQ, k, 1.0)
+        assert abs(U[0] - (1 + z + z * z / 2 + z ** 3 / 6)) < 1e-15
+
+
+# ------------------------------------------------------------------------------------------
+# Manufactured fields
+# ------------------------------------------------------------------------------------------
+
+def _mms_fields(cfg):
+    x, y = sympy.symbols("x y", real=True)
+    Lx, Ly = cfg["x1"] - cfg["x0"], cfg["y1"] - cfg["y0"]
+    X = 2 * sympy.pi * (x - cfg["x0"]) / Lx
+    Yv = 2 * sympy.pi * (y - cfg["y0"]) / Ly
+    rho = 1 + sympy.Rational(2, 10) * sympy.sin(X + sympy.Rational(1, 10)) * sympy.cos(Yv + sympy.Rational(2, 10))
+    u = sympy.Rational(3, 2) + sympy.Rational(3, 10) * sympy.cos(X) * sympy.sin(Yv + sympy.Rational(1, 2))
+    v = sympy.Rational(2, 10) * sympy.sin(X + 1) * sympy.cos(Yv)
+    Tf = 1 + sympy.Rational(2, 10) * sympy.cos(X + sympy.Rational(3, 10)) * sympy.cos(Yv + sympy.Rational(1, 10))
+    return x, y, rho, u, v, Tf
+
+
+def _nodes(grid):
+    return dict(c=np.meshgrid(grid.xc, grid.yc), xf=np.meshgrid(grid.xf, grid.yc),
+                yf=np.meshgrid(grid.xc, grid.yf))
+
+
+def _mms_box(nx, ny, kind):
+    cfg = I.box_case(nx, ny, kind=kind)
+    cfg.update(x0=0.0, x1=1.3, y0=0.0, y1=1.0, y_stretch="tanh", y_param=1.2, reynolds=50.0,
+               sponge_in=0.0, sponge_out=0.0, sponge_top_cells=0, mach=1.5)
+    return cfg
+
+
+def _cpg_exact_rhs(cfg, sc):
+    x, y, rho, u, v, Tshape = _mms_fields(cfg)
+    g = sc.gamma
+    T = Tshape / (g - 1)                               # nondimensional, freestream 1/(gamma - 1)
+    p = rho * (g - 1) / g * T                          # Eq. (22)
+    mu = F.SUTHERLAND_C1 * (T * sc.T_ref) ** sympy.Rational(3, 2) / (T * sc.T_ref + F.SUTHERLAND_TS) / sc.mu
+    Re, Pr = sc.Re, sc.Pr
+    ux, uy, vx, vy = sympy.diff(u, x), sympy.diff(u, y), sympy.diff(v, x), sympy.diff(v, y)
+    div = ux + vy
+    txx = mu / Re * (2 * ux - sympy.Rational(2, 3) * div)
+    tyy = mu / Re * (2 * vy - sympy.Rational(2, 3) * div)
+    txy = mu / Re * (uy + vx)
+    qx = -mu / (Re * Pr) * sympy.diff(T, x)            # k = mu (nondimensional)
+    qy = -mu / (Re * Pr) * sympy.diff(T, y)
+    E = T / g + (u * u + v * v) / 2
+    H = E + p / rho
+    R = dict(
+        rho=-(sympy.diff(rho * u, x) + sympy.diff(rho * v, y)),
+        rhou=-(sympy.diff(rho * u * u + p - txx, x) + sympy.diff(rho * u * v - txy, y)),
+        rhov=-(sympy.diff(rho * u * v - txy, x) + sympy.diff(rho * v * v + p - tyy, y)),
+        rhoE=-(sympy.diff(rho * H * u + qx - (txx * u + txy * v), x)
+               + sympy.diff(rho * H * v + qy - (txy * u + tyy * v), y)),
+    )
+    prim = dict(rho=rho, u=u, v=v, T=T, E=E)
+    f = {k: sympy.lambdify((x, y), val, "numpy") for k, val in {**R, **{"p_" + k: w for k, w in prim.items()}}.items()}
+    return f
+
+
+def _set_state_cpg(case, f):
+    g = case.grid
+    nd = _nodes(g)
+    ns, nx, ny = 5, g.nx, g.ny
+    fields = {}
+    Xc, Yc = nd["c"]
+    rho = f["p_rho"](Xc, Yc)
+    fields["rho"] = rho
+    fields["rs1"] = 0.233 * rho
+    for s in range(2, ns):
+        fields[f"rs{s}"] = 0.0 * rho
+    fields["rhoE"] = rho * f["p_E"](Xc, Yc)
+    Xu, Yu = nd["xf"]
+    fields["rhou"] = f["p_rho"](Xu, Yu) * f["p_u"](Xu, Yu)
+    Xv, Yv = nd["yf"]
+    fields["rhov"] = f["p_rho"](Xv, Yv) * f["p_v"](Xv, Yv)
+    return F.pack(ns, nx, ny, fields)
+
+
+def _errors_against(case, U, exact):
+    """Normwise errors per conserved field, Dirichlet boundary faces excluded."""
+    g = case.grid
+    nd = _nodes(g)
+    R = F.unpack(5, g.nx, g.ny, F.rhs(case, U))
+    out = {}
+    for name, node in (("rho", "c"), ("rhou", "xf"), ("rhov", "yf"), ("rhoE", "c")):
+        Xn, Yn = nd[node]
+        ex = np.broadcast_to(exact[name](Xn, Yn), R[name].shape).copy()
+        d = R[name] - ex
+        if name == "rhou":
+            d, ex = d[:, 1:-1], ex[:, 1:-1]
+        if name == "rhov":
+            d, ex = d[1:-1, :], ex[1:-1, :]
+        out[name] = np.abs(d).max() / np.abs(ex).max()
+    return out
+
+
+def test_pde_consistency_perfect_gas(table):
+    errs = []
+    for nx, ny in ((26, 20), (52, 40), (104, 80)):
+        cfg = _mms_box(nx, ny, "cpg")
+        case = F.make_case(cfg, table)
+        f = _cpg_exact_rhs(cfg, case.sc)
+        U = _set_state_cpg(case, f)
+        errs.append(_errors_against(case, U, f))
+    for name in errs[0]:
+        order = math.log2(errs[1][name] / errs[2][name])
+        assert errs[2][name] < 2e-3, (name, errs)
+        assert order > 2.8, (name, [e[name] for e in errs])
+
+
+# ------------------------------------------------------------------------------------------
+# Binary cold mixture: Fick's law reference
+# ------------------------------------------------------------------------------------------
+
+def _binary_reference(cfg, case):
+    """Continuous right-hand side for N2/O2 at 250-350 K (reactions frozen by the temperature),
+    with J_O2 = -rho D_12 dY_O2/dx_j (Fick) and q = -k grad T + sum_s h_s J_s (Eq. 10)."""
+    sc, tab = case.sc, case.tab
+    x, y, rho_e, u_e, v_e, T_e = _mms_fields(cfg)
+    Lx = cfg["x1"] - cfg["x0"]
+    YO2_e = sympy.Rational(233, 1000) + sympy.Rational(5, 100) * sympy.sin(2 * sympy.pi * (x - cfg["x0"]) / Lx + sympy.Rational(7, 10)) * sympy.sin(2 * sympy.pi * y + 1)
+    Tsi_e = 300 * T_e                                 # K
+    prim = {k: sympy.lambdify((x, y), val, "numpy") for k, val in
+            dict(rho=rho_e, u=u_e, v=v_e, Tsi=Tsi_e, Y=YO2_e).items()}
+    grads = {k + d: sympy.lambdify((x, y), sympy.diff(val, sym), "numpy")
+             for k, val in dict(u=u_e, v=v_e, Tsi=Tsi_e, Y=YO2_e).items()
+             for d, sym in (("x", x), ("y", y))}
+    M = tab.M()
+
+    def point_state(X, Yy):
+        X = np.atleast_1d(X).astype(float)
+        Yy = np.broadcast_to(np.atleast_1d(Yy).astype(float), X.shape)
+        n = X.size
+        rho = prim["rho"](X, Yy) * np.ones(n)
+        Tsi = prim["Tsi"](X, Yy) * np.ones(n)
+        yo2 = prim["Y"](X, Yy) * np.ones(n)
+        Ys = np.zeros((5, n))
+        Ys[0], Ys[1] = 1 - yo2, yo2
+        return rho, Tsi, Ys
+
+    def fluxes(X, Yy):
+        rho, Tsi, Ys = point_state(X, Yy)
+        u = prim["u"](X, Yy) * np.ones_like(rho)
+        v = prim["v"](X, Yy) * np.ones_like(rho)
+        Tarr = np.atleast_1d(Tsi)
+        p_si = rho * sc.rho * G.mixture_gas_constant(tab, Ys) * Tarr
+        p = p_si / (sc.rho * sc.a ** 2)
+        e = G.mixture_energy(tab, Tarr, Ys) / sc.a ** 2
+        Xm = G.mole_fractions(tab, Ys)
+        mu_s = G.species_viscosity(tab, Tarr)
+        mu = G.wilke_mix(tab, Xm, mu_s, mu_s) / sc.mu
+        k = G.wilke_mix(tab, Xm, mu_s, G.species_conductivity(tab, Tarr, mu_s)) / sc.k
+        D12 = G.binary_diffusion(tab, Tarr, p_si)[0, 1] * sc.rho / sc.mu
+        h = G.enthalpy_species(tab, Tarr) / sc.a ** 2
+        Re, Pr = sc.Re, sc.Pr
+        ux, uy = grads["ux"](X, Yy), grads["uy"](X, Yy)
+        vx, vy = grads["vx"](X, Yy), grads["vy"](X, Yy)
+        Tx, Ty = grads["Tsix"](X, Yy) / sc.T_ref, grads["Tsiy"](X, Yy) / sc.T_ref
+        Yx, Yyy = grads["Yx"](X, Yy), grads["Yy"](X, Yy)
+        div = ux + vy
+        txx = mu / Re * (2 * ux - 2 / 3 * div)
+        tyy = mu / Re * (2 * vy - 2 / 3 * div)
+        txy = mu / Re * (uy + vx)
+        Jx = -rho * D12 / Re * Yx                        # Fick, O2
+        Jy = -rho * D12 / Re * Yyy
+        qx = -k / (Re * Pr) * Tx + (h[1] - h[0]) * Jx
+        qy = -k / (Re * Pr) * Ty + (h[1] - h[0]) * Jy
+        E = e + 0.5 * (u * u + v * v)
+        H = E + p / rho
+        Fx = dict(rho=rho * u, rs1=rho * Ys[1] * u + Jx, rhou=rho * u * u + p - txx,
+                  rhov=rho * u * v - txy, rhoE=rho * H * u + qx - (txx * u + txy * v))
+        Fy = dict(rho=rho * v, rs1=rho * Ys[1] * v + Jy, rhou=rho * u * v - txy,
+                  rhov=rho * v * v + p - tyy, rhoE=rho * H * v + qy - (txy * u + tyy * v))
+        return Fx, Fy, (rho, Ys, E)
+
+    def exact(name, X, Yy):
+        h = 1e-4
+        acc = np.zeros(np.size(X))
+        for c, sgn in ((8.0, 1), (-8.0, -1), (-1.0, 2), (1.0, -2)):
+            pass
+        # 4th-order central differences of the pointwise fluxes
+        fxp = fluxes(X + h, Yy)[0][name]
+        fxm = fluxes(X - h, Yy)[0][name]
+        fxp2 = fluxes(X + 2 * h, Yy)[0][name]
+        fxm2 = fluxes(X - 2 * h, Yy)[0][name]
+        fyp = fluxes(X, Yy + h)[1][name]
+        fym = fluxes(X, Yy - h)[1][name]
+        fyp2 = fluxes(X, Yy + 2 * h)[1][name]
+        fym2 = fluxes(X, Yy - 2 * h)[1][name]
+        dFx = (8 * (fxp - fxm) - (fxp2 - fxm2)) / (12 * h)
+        dFy = (8 * (fyp - fym) - (fyp2 - fym2)) / (12 * h)
+        return -(dFx + dFy)
+
+    return point_state, fluxes, exact
+
+
+def test_pde_consistency_binary_diffusion(table):
+    errs = []
+    for nx, ny in ((26, 20), (52, 40), (104, 80)):
+        cfg = _mms_box(nx, ny, "cneq")
+        cfg.update(T_inf=300.0, p_inf=2000.0, reynolds=20.0)
+        case = F.make_case(cfg, table)
+        point_state, fluxes, exact = _binary_reference(cfg, case)
+        g = case.grid
+        nd = _nodes(g)
+        fields = {}
+        Xc, Yc = nd["c"]
+        _, _, (rho, Ys, E) = fluxes(Xc.ravel(), Yc.ravel())
+        fields["rho"] = rho.reshape(Xc.shape)
+        fields["rs1"] = (rho * Ys[1]).reshape(Xc.shape)
+        for s in range(2, 5):
+            fields[f"rs{s}"] = 0.0 * Xc
+        fields["rhoE"] = (rho * E).reshape(Xc.shape)
+        for name, node, key in (("rhou", "xf", "u"), ("rhov", "yf", "v")):
+            Xn, Yn = nd[node]
+            r, _, _ = point_state(Xn.ravel(), Yn.ravel())
+            _, _, (rr, _, _) = fluxes(Xn.ravel(), Yn.ravel())
+            Fx, Fy, _ = fluxes(Xn.ravel(), Yn.ravel())
+            vel = Fx["rho"] / rr if key == "u" else Fy["rho"] / rr
+            fields[name] = (rr * vel).reshape(Xn.shape)
+        U = F.pack(5, g.nx, g.ny, fields)
+        R = F.unpack(5, g.nx, g.ny, F.rhs(case, U))
+        e = {}
+        for name, node in (("rho", "c"), ("rs1", "c"), ("rhoE", "c"), ("rhou", "xf"), ("rhov", "yf")):
+            Xn, Yn = nd[node]
+            ex = exact(name, Xn.ravel(), Yn.ravel()).reshape(Xn.shape)
+            d = R[name] - ex
+            if name == "rhou":
+                d, ex = d[:, 1:-1], ex[:, 1:-1]
+            if name == "rhov":
+                d, ex = d[1:-1, :], ex[1:-1, :]
+            e[name] = np.abs(d).max() / np.abs(ex).max()
+        errs.append(e)
+    for name in errs[0]:
+        order = math.log2(errs[1][name] / errs[2][name])
+        assert errs[2][name] < 5e-3, (name, errs)
+        assert order > 2.8, (name, [x[name] for x in errs])
