@@ -1,0 +1,180 @@
+/*
+ * hyp.h -- C ABI of the GB300 library for the right-hand side and explicit stage update of the
+ * compressible multi-species Navier-Stokes equations for air in chemical nonequilibrium
+ * (arXiv 2210.05547: Eqs. 1-11 for the equations, Sec. 2.2 for the closure, Sec. 3.1-3.3 for
+ * the discretisation, Eq. 26 for the sponge).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Return value: HYP_OK (0) on success, a negative HYP_ERR_* code otherwise; the message of the
+ *   last error on the calling thread is available from hyp_last_error().
+ * - Device pointers are CUDA global-memory pointers of the current device; host pointers are
+ *   ordinary process memory. Each argument says which it is.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream). Calls that take
+ *   a stream are asynchronous with respect to the host: they enqueue kernels and return. Device
+ *   status flags (Newton failure, clamped temperature, non-physical state) are read with
+ *   hyp_grid_status(), which synchronises the grid's stream.
+ * - Ownership: the caller owns every field buffer it passes (state, right-hand side, the
+ *   thermo_eval inputs and outputs). The library owns the opaque handles and everything inside
+ *   them (gas tables, metrics, sponge, reference state, scratch), and frees them in *_free.
+ * - Floating point: FP64 throughout (precision argument HYP_FP64). No call falls back to the
+ *   CPU: every arithmetic step of rhs / rk_stage / thermo_eval runs in CUDA kernels.
+ * - A grid handle carries scratch memory: calls that use the same grid (rhs, rk_stage) must not
+ *   overlap on the device; serialise them on one stream.
+ *
+ * State vector layout (2D, ns species, the first species of the table omitted, Sec. 2.1):
+ *   centres  (ny rows x nx columns, x fastest): rho, rho_s for s = 1..ns-1, rho*E
+ *   x-faces  (ny rows x (nx+1) columns):       rho*u
+ *   y-faces  ((ny+1) rows x nx columns):       rho*v
+ * concatenated in that order, FP64, nondimensional per Eq. (7). Total length from
+ * hyp_state_size(). The right-hand side has the same layout.
+ */
+#ifndef HYP_H
+#define HYP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HYP_MAX_SPECIES 5
+
+enum hyp_gas_kind {
+    HYP_GAS_CNEQ = 0,    /* finite-rate chemistry with algebraic diffusion (Sec. 2.2.1) */
+    HYP_GAS_FROZEN = 1,  /* frozen composition: no reactions, no diffusion (Sec. 2.2.1) */
+    HYP_GAS_CPG = 2      /* calorically perfect gas, Sutherland viscosity (Eqs. 22, 24) */
+};
+
+enum hyp_precision { HYP_FP64 = 0 };
+
+enum hyp_error {
+    HYP_OK = 0,
+    HYP_ERR_ARG = -1,       /* invalid argument (null handle, bad size, unknown kind) */
+    HYP_ERR_CUDA = -2,      /* a CUDA runtime call failed (message has the CUDA error) */
+    HYP_ERR_IO = -3,        /* gas table could not be read or parsed */
+    HYP_ERR_OOM = -4,       /* device allocation failed */
+    HYP_ERR_STATUS = -5     /* device status flags set (see hyp_grid_status) */
+};
+
+/* Per-point status bits (thermo_eval status mask, hyp_grid_status flags). */
+#define HYP_STATUS_NOT_CONVERGED 1u  /* Newton inversion for T did not converge */
+#define HYP_STATUS_T_CLAMPED 2u      /* internal energy outside [e(50 K), e(1e5 K)]: T clamped */
+#define HYP_STATUS_NONPHYSICAL 4u    /* rho <= 0 */
+
+typedef struct hyp_gas hyp_gas;
+typedef struct hyp_grid hyp_grid;
+typedef struct hyp_state hyp_state;
+
+/* Freestream that defines the nondimensionalisation of Eq. (7) and the numbers of Eq. (11).
+ * reynolds is Re_inf = rho_inf a_inf L_ref / mu_inf (Eq. 11), which fixes L_ref. */
+typedef struct {
+    double T_inf;                      /* K */
+    double p_inf;                      /* Pa */
+    double Y_inf[HYP_MAX_SPECIES];     /* mass fractions, table order */
+    double mach;                       /* U_inf / a_inf */
+    double reynolds;                   /* Re_inf of Eq. (11) */
+    double prandtl_cpg;                /* Prandtl number, used by HYP_GAS_CPG only */
+} hyp_freestream;
+
+/* Structured grid: nx x ny cells; x uniform on [x0, x1]; y on [y0, y1] with
+ * y_stretch 0 = uniform, 1 = tanh wall clustering y = y0 + (y1-y0)(1 - tanh(q(1-s))/tanh q),
+ * 2 = the cubic map of Eq. (27) with kappa_y = q; s = j/ny at grid (tau) nodes. */
+typedef struct {
+    int32_t nx, ny;
+    double x0, x1, y0, y1;
+    int32_t y_stretch;
+    double y_param;
+} hyp_grid_desc;
+
+/* Case: boundary conditions (Sec. 3.2, Fig. 2), sponge (Eq. 26), shock capturing (Sec. 3.3),
+ * and the synthetic initial / reference state. */
+typedef struct {
+    int32_t flow;                  /* 0 flat-plate boundary layer, 1 oblique shock impinging on it */
+    int32_t wall;                  /* 1: isothermal no-slip non-catalytic wall at y0; 0: far field */
+    double T_wall;                 /* K */
+    double delta_coef;             /* boundary-layer thickness delta(x) = delta_coef sqrt(x/(Re Ma)) */
+    double minor_species;          /* NO/N/O seeded inside the layer, peak mass fraction scale */
+    double shock_deflection_deg;   /* flow deflection of the incident shock (flow = 1) */
+    double shock_x;                /* x where the inviscid shock line meets the wall */
+    double shock_width;            /* tanh smoothing width of the shock in the initial state */
+    double sponge_sigma;           /* sigma_max of the cubic sponge ramps */
+    double sponge_in, sponge_out;  /* x-lengths of the inflow / outflow sponges (0 = none) */
+    int32_t sponge_top_cells;      /* number of cells in the top sponge */
+    int32_t artificial_diffusivity;
+    double C_mu, C_beta, C_kappa, C_D;
+    double noise_amp;              /* initial state = reference * (1 + noise_amp * noise) */
+    const double* noise;           /* HOST, nullable; hyp_state_size() values in [-1, 1] */
+} hyp_case;
+
+/* Load a gas table (plain-text SPECIES / LEVEL / REACTION lines, see data/air5.dat) and build
+ * the closure of Sec. 2.2 for `kind`, nondimensionalised with `fs` (Eq. 7). The table must list
+ * HYP_MAX_SPECIES species; its first species is the omitted one (Sec. 2.1).
+ * path: HOST string. fs: HOST. *out: new handle, free with hyp_gas_free. */
+int hyp_gas_model_load(const char* path, int kind, const hyp_freestream* fs, hyp_gas** out);
+
+/* Reference scales (HOST array of 13 doubles): rho_inf, a_inf, T_inf, p_inf, mu_inf, k_inf,
+ * cp_inf, gamma_inf, R_inf, T_ref, L_ref, Re_inf, Pr_inf (Eqs. 7, 11). n_species may be NULL. */
+int hyp_gas_scales(const hyp_gas* gas, int* n_species, double* scales13);
+
+void hyp_gas_free(hyp_gas* gas);
+
+/* Number of doubles in the state vector for this gas and grid. */
+int hyp_state_size(const hyp_gas* gas, const hyp_grid_desc* desc, int64_t* n);
+
+/* Build the grid (metrics), sponge strength, reference state Q_ref of Eq. (26) and scratch, and
+ * write the initial state into U. U, dQ: DEVICE, caller-owned, hyp_state_size() doubles each;
+ * the state handle keeps both pointers as the two Runge-Kutta registers (dQ is zeroed).
+ * desc, cas (and cas->noise): HOST. Enqueued on `stream`; the handle's grid uses that stream
+ * for its status flag. */
+int hyp_state_init(const hyp_gas* gas, const hyp_grid_desc* desc, const hyp_case* cas,
+                   double* U, double* dQ, void* stream, hyp_state** out);
+
+/* The grid of a state (valid while the state lives). */
+const hyp_grid* hyp_state_grid(const hyp_state* st);
+
+/* Copy grid data to HOST buffers of hyp_state_size() doubles (either may be NULL):
+ * U_ref = reference state of Eq. (26); sigma = sponge strength at the node of each entry. */
+int hyp_grid_reference(const hyp_grid* grid, double* U_ref_host, double* sigma_host);
+
+/* Read and optionally clear the OR of the per-point status bits raised since the last clear.
+ * Synchronises the grid's stream. */
+int hyp_grid_status(const hyp_grid* grid, uint32_t* flags, int clear);
+
+void hyp_state_free(hyp_state* st);
+
+/* dU/dt = -div F_C + div F_D + S - sigma (U - U_ref)  (Eqs. 5, 6, 26) on the staggered grid,
+ * with the closure of Sec. 2.2 at every cell centre, sixth-order compact staggered operators
+ * (Sec. 3.1), the boundary conditions of Sec. 3.2 and, if the case enables it, artificial
+ * diffusivity (Sec. 3.3). Entries on Dirichlet boundary faces (x-faces at x0 and x1, y-faces at
+ * y0 and y1) are set to 0. U, dUdt: DEVICE, caller-owned, hyp_state_size() doubles, must not
+ * alias. Uses the grid's scratch. */
+int hyp_rhs(const hyp_gas* gas, const hyp_grid* grid, const double* U, double* dUdt,
+            int precision, void* stream);
+
+/* One stage (0, 1, 2) of the low-storage two-register third-order Runge-Kutta scheme (Sec. 3.1):
+ * dQ <- A_k dQ + dt R(U); U <- U + B_k dQ with A = (0, -5/9, -153/128), B = (1/3, 15/16, 8/15),
+ * on the registers given to hyp_state_init. dt nondimensional (time unit L_ref / a_inf). */
+int hyp_rk_stage(hyp_state* st, int stage, double dt, int precision, void* stream);
+
+/* Pointwise closure of Sec. 2.2 in SI units for n independent states (the work the paper hands
+ * to its real-gas library, Sec. 3.4). Inputs (DEVICE): rho[n] kg/m^3, e[n] J/kg internal energy
+ * including formation enthalpy (298.15 K reference), Y[ns*n] mass fractions species-major
+ * (Y[s*n + i]). Outputs (DEVICE, each nullable): T[n] K, p[n] Pa, wdot[ns*n] kg/(m^3 s) (Eq. 15),
+ * mu[n] Pa s, k[n] W/(m K) (frozen), D[ns*n] m^2/s (Eq. 19), status[n] HYP_STATUS_* bits. */
+int hyp_thermo_eval(const hyp_gas* gas, int64_t n, const double* rho, const double* e,
+                    const double* Y, double* T, double* p, double* wdot, double* mu, double* k,
+                    double* D, uint8_t* status, int precision, void* stream);
+
+/* Mixture internal energy e = sum_s Y_s e_s(T) (Eq. 12), J/kg. T[n], Y[ns*n], e[n]: DEVICE. */
+int hyp_thermo_energy(const hyp_gas* gas, int64_t n, const double* T, const double* Y, double* e,
+                      void* stream);
+
+/* Message of the last failed call on this thread ("" if none). Owned by the library. */
+const char* hyp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HYP_H */

@@ -366,7 +366,7 @@ def wilke_mix(tab: GasTable, X, mu_s, prop_s):
 def collision_integral_diffusion(Tstar):
     """Reduced Lennard-Jones collision integral Omega^(1,1)* (Neufeld, Janzen and Aziz fit)."""
     A, B, C, D, E, F, G, H = 1.06036, 0.15610, 0.19300, 0.47635, 1.03587, 1.52996, 1.76474, 3.89411
-    return A / Tstar ** B + C / np.exp(D * Tstar) + E / np.exp(F * Tstar) + G / np.exp(H * Tstar)
+    return A / Tstar ** B + C * np.exp(-D * Tstar) + E * np.exp(-F * Tstar) + G * np.exp(-H * Tstar)
 
 
 def binary_diffusion(tab: GasTable, T, p):

@@ -1,0 +1,266 @@
+"""Thin Python binding of the C ABI in ``include/hyp.h`` (argument marshalling only).
+
+Every arithmetic step of ``rhs``, ``rk_stage``, ``thermo_eval`` and ``thermo_energy`` runs in the
+CUDA library ``_lib/libhyp.so``; this module only checks tensors, converts case dictionaries into
+the C structs and forwards raw pointers. If the library has not been built, every call raises.
+PyTorch supplies device memory and the current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MAX_SPECIES = 5
+GAS_KINDS = {"cneq": 0, "frozen": 1, "cpg": 2}
+STRETCH = {"uniform": 0, "tanh": 1, "cubic": 2}
+FLOWS = {"bl": 0, "sbli": 1}
+FP64 = 0
+TABLE_AIR5 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data", "air5.dat")
+SCALE_NAMES = ("rho_inf", "a_inf", "T_inf", "p_inf", "mu_inf", "k_inf", "cp_inf", "gamma_inf",
+               "R_inf", "T_ref", "L_ref", "Re", "Pr")
+
+
+class Freestream(ctypes.Structure):
+    _fields_ = [("T_inf", ctypes.c_double), ("p_inf", ctypes.c_double),
+                ("Y_inf", ctypes.c_double * MAX_SPECIES), ("mach", ctypes.c_double),
+                ("reynolds", ctypes.c_double), ("prandtl_cpg", ctypes.c_double)]
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("x0", ctypes.c_double),
+                ("x1", ctypes.c_double), ("y0", ctypes.c_double), ("y1", ctypes.c_double),
+                ("y_stretch", ctypes.c_int32), ("y_param", ctypes.c_double)]
+
+
+class CaseDesc(ctypes.Structure):
+    _fields_ = [("flow", ctypes.c_int32), ("wall", ctypes.c_int32), ("T_wall", ctypes.c_double),
+                ("delta_coef", ctypes.c_double), ("minor_species", ctypes.c_double),
+                ("shock_deflection_deg", ctypes.c_double), ("shock_x", ctypes.c_double),
+                ("shock_width", ctypes.c_double), ("sponge_sigma", ctypes.c_double),
+                ("sponge_in", ctypes.c_double), ("sponge_out", ctypes.c_double),
+                ("sponge_top_cells", ctypes.c_int32), ("artificial_diffusivity", ctypes.c_int32),
+                ("C_mu", ctypes.c_double), ("C_beta", ctypes.c_double),
+                ("C_kappa", ctypes.c_double), ("C_D", ctypes.c_double),
+                ("noise_amp", ctypes.c_double), ("noise", ctypes.POINTER(ctypes.c_double))]
+
+
+_LIB = None
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+_I = ctypes.c_int
+_I64 = ctypes.c_int64
+
+EXPORTS = {
+    "hyp_gas_model_load": (_I, [ctypes.c_char_p, _I, ctypes.POINTER(Freestream), ctypes.POINTER(_P)]),
+    "hyp_gas_scales": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "hyp_gas_free": (None, [_P]),
+    "hyp_state_size": (_I, [_P, ctypes.POINTER(GridDesc), ctypes.POINTER(_I64)]),
+    "hyp_state_init": (_I, [_P, ctypes.POINTER(GridDesc), ctypes.POINTER(CaseDesc), _P, _P, _P,
+                            ctypes.POINTER(_P)]),
+    "hyp_state_grid": (_P, [_P]),
+    "hyp_grid_reference": (_I, [_P, _P, _P]),
+    "hyp_grid_status": (_I, [_P, ctypes.POINTER(ctypes.c_uint32), _I]),
+    "hyp_state_free": (None, [_P]),
+    "hyp_rhs": (_I, [_P, _P, _P, _P, _I, _P]),
+    "hyp_rk_stage": (_I, [_P, _I, _D, _I, _P]),
+    "hyp_thermo_eval": (_I, [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I, _P]),
+    "hyp_thermo_energy": (_I, [_P, _I64, _P, _P, _P, _P]),
+    "hyp_last_error": (ctypes.c_char_p, []),
+}
+
+
+class HypError(RuntimeError):
+    pass
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise HypError(f"CUDA library not built ({path}); run python -m paper_2210_05547_gb300.build")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in EXPORTS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _check(rc):
+    if rc != 0:
+        raise HypError(f"hyp error {rc}: {lib().hyp_last_error().decode()}")
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t, n=None, dtype=None):
+    import torch
+    if t is None:
+        return None
+    if not (t.is_cuda and t.is_contiguous()):
+        raise HypError("expected a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise HypError(f"expected dtype {dtype}, got {t.dtype}")
+    if n is not None and t.numel() != n:
+        raise HypError(f"expected {n} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ---------------------------------------------------------------------------------------------
+# structs from the case dictionaries of paper_2210_05547_gb300.inputs
+# ---------------------------------------------------------------------------------------------
+
+def freestream_struct(cfg):
+    fs = Freestream()
+    fs.T_inf, fs.p_inf = cfg["T_inf"], cfg["p_inf"]
+    for i, y in enumerate(cfg["Y_inf"]):
+        fs.Y_inf[i] = y
+    fs.mach, fs.reynolds, fs.prandtl_cpg = cfg["mach"], cfg["reynolds"], cfg["prandtl_cpg"]
+    return fs
+
+
+def grid_struct(cfg):
+    return GridDesc(cfg["nx"], cfg["ny"], cfg["x0"], cfg["x1"], cfg["y0"], cfg["y1"],
+                    STRETCH[cfg["y_stretch"]], cfg["y_param"])
+
+
+def case_struct(cfg, noise=None):
+    c = CaseDesc()
+    c.flow, c.wall, c.T_wall = FLOWS[cfg["flow"]], int(cfg["wall"]), cfg["T_wall"]
+    c.delta_coef, c.minor_species = cfg["delta_coef"], cfg["minor_species"]
+    c.shock_deflection_deg, c.shock_x = cfg["shock_deflection_deg"], cfg["shock_x"]
+    c.shock_width = cfg["shock_width"] if cfg["shock_width"] > 0 else 1.0
+    c.sponge_sigma, c.sponge_in, c.sponge_out = cfg["sponge_sigma"], cfg["sponge_in"], cfg["sponge_out"]
+    c.sponge_top_cells = int(cfg["sponge_top_cells"])
+    c.artificial_diffusivity = int(cfg["artificial_diffusivity"])
+    c.C_mu, c.C_beta, c.C_kappa, c.C_D = cfg["C_mu"], cfg["C_beta"], cfg["C_kappa"], cfg["C_D"]
+    c.noise_amp = cfg["noise_amp"]
+    if noise is not None:
+        arr = np.ascontiguousarray(noise, dtype=np.float64)
+        c.noise = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        c._keep = arr
+    return c
+
+
+# ---------------------------------------------------------------------------------------------
+# handles
+# ---------------------------------------------------------------------------------------------
+
+class Gas:
+    def __init__(self, handle):
+        self.handle = handle
+        ns = ctypes.c_int()
+        buf = (ctypes.c_double * 13)()
+        _check(lib().hyp_gas_scales(handle, ctypes.byref(ns), buf))
+        self.ns = ns.value
+        self.scales = dict(zip(SCALE_NAMES, list(buf)))
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _LIB is not None:
+            _LIB.hyp_gas_free(self.handle)
+            self.handle = None
+
+
+class State:
+    def __init__(self, handle, U, dQ, gas):
+        self.handle = handle
+        self.U = U
+        self.dQ = dQ
+        self.gas = gas
+        self.grid = lib().hyp_state_grid(handle)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _LIB is not None:
+            _LIB.hyp_state_free(self.handle)
+            self.handle = None
+
+
+def gas_model_load(cfg, kind=None, path=TABLE_AIR5):
+    """hyp_gas_model_load: gas table + kind + freestream (from a case dictionary)."""
+    h = ctypes.c_void_p()
+    fs = freestream_struct(cfg)
+    k = GAS_KINDS[kind or cfg["kind"]]
+    _check(lib().hyp_gas_model_load(path.encode(), k, ctypes.byref(fs), ctypes.byref(h)))
+    return Gas(h)
+
+
+def state_size(gas, cfg):
+    n = ctypes.c_int64()
+    _check(lib().hyp_state_size(gas.handle, ctypes.byref(grid_struct(cfg)), ctypes.byref(n)))
+    return n.value
+
+
+def state_init(gas, cfg, U, dQ, noise=None, stream=None):
+    """hyp_state_init: builds the grid handle and writes the initial state into U (device)."""
+    import torch
+    n = state_size(gas, cfg)
+    h = ctypes.c_void_p()
+    desc = grid_struct(cfg)
+    cas = case_struct(cfg, noise)
+    _check(lib().hyp_state_init(gas.handle, ctypes.byref(desc), ctypes.byref(cas),
+                                _dptr(U, n, torch.float64), _dptr(dQ, n, torch.float64),
+                                _stream(stream), ctypes.byref(h)))
+    return State(h, U, dQ, gas)
+
+
+def rhs(gas, grid, U, dUdt, precision=FP64, stream=None):
+    """hyp_rhs: dU/dt of the state U (device tensors, same length)."""
+    _check(lib().hyp_rhs(gas.handle, grid, _dptr(U), _dptr(dUdt, U.numel()), precision,
+                         _stream(stream)))
+
+
+def rk_stage(state, stage, dt, precision=FP64, stream=None):
+    """hyp_rk_stage: one stage of the two-register RK3 on the state's registers."""
+    _check(lib().hyp_rk_stage(state.handle, stage, dt, precision, _stream(stream)))
+
+
+def grid_reference(grid, n):
+    Uref = np.empty(n)
+    sigma = np.empty(n)
+    _check(lib().hyp_grid_reference(grid, Uref.ctypes.data_as(ctypes.c_void_p),
+                                    sigma.ctypes.data_as(ctypes.c_void_p)))
+    return Uref, sigma
+
+
+def grid_status(grid, clear=False):
+    flags = ctypes.c_uint32()
+    _check(lib().hyp_grid_status(grid, ctypes.byref(flags), int(clear)))
+    return flags.value
+
+
+def thermo_eval(gas, rho, e, Y, T=None, p=None, wdot=None, mu=None, k=None, D=None,
+                status=None, precision=FP64, stream=None):
+    """hyp_thermo_eval on device tensors (SI). Y and the per-species outputs are (ns, n)."""
+    import torch
+    n = rho.numel()
+    ns = gas.ns
+    _check(lib().hyp_thermo_eval(
+        gas.handle, n, _dptr(rho, n, torch.float64), _dptr(e, n, torch.float64),
+        _dptr(Y, ns * n, torch.float64), _dptr(T, n), _dptr(p, n), _dptr(wdot, ns * n),
+        _dptr(mu, n), _dptr(k, n), _dptr(D, ns * n),
+        _dptr(status, n, torch.uint8) if status is not None else None, precision,
+        _stream(stream)))
+
+
+def thermo_energy(gas, T, Y, e, stream=None):
+    import torch
+    n = T.numel()
+    _check(lib().hyp_thermo_energy(gas.handle, n, _dptr(T, n, torch.float64),
+                                   _dptr(Y, gas.ns * n, torch.float64), _dptr(e, n, torch.float64),
+                                   _stream(stream)))

@@ -1,0 +1,374 @@
+// Gas model loading (Sec. 2.2 closure data) and the pointwise thermochemistry kernels.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <fstream>
+#include <map>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "thermo.cuh"
+
+namespace hyp {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+int fail(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t err, const char* what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(err);
+    return err == cudaErrorMemoryAllocation ? HYP_ERR_OOM : HYP_ERR_CUDA;
+}
+
+namespace table {
+
+constexpr double K_B = 1.380649e-23;
+constexpr double N_A = 6.02214076e23;
+constexpr double H_P = 6.62607015e-34;
+constexpr double PI = 3.14159265358979323846;
+
+struct SpeciesRow {
+    std::string name;
+    double M, hf, theta_v, theta_r, sym, bA, bB, bC, lj_s, lj_e;
+    int linear, nN, nO;
+    std::vector<std::pair<double, double>> levels;
+};
+
+struct ReactionRow {
+    double C_cgs, n, Ta;
+    std::vector<std::string> lhs, rhs;
+};
+
+int parse_table(const char* path, std::vector<SpeciesRow>& sp, std::vector<ReactionRow>& rx) {
+    std::ifstream in(path);
+    if (!in) return fail(HYP_ERR_IO, std::string("cannot open gas table ") + path);
+    std::string line;
+    while (std::getline(in, line)) {
+        auto hash = line.find('#');
+        if (hash != std::string::npos) line = line.substr(0, hash);
+        std::istringstream ss(line);
+        std::string key;
+        if (!(ss >> key)) continue;
+        if (key == "SPECIES") {
+            SpeciesRow r;
+            if (!(ss >> r.name >> r.M >> r.hf >> r.linear >> r.theta_v >> r.theta_r >> r.sym >>
+                  r.bA >> r.bB >> r.bC >> r.lj_s >> r.lj_e >> r.nN >> r.nO))
+                return fail(HYP_ERR_IO, "bad SPECIES line: " + line);
+            sp.push_back(r);
+        } else if (key == "LEVEL") {
+            std::string name;
+            double gdeg, th;
+            if (!(ss >> name >> gdeg >> th)) return fail(HYP_ERR_IO, "bad LEVEL line: " + line);
+            bool found = false;
+            for (auto& r : sp)
+                if (r.name == name) {
+                    r.levels.push_back({gdeg, th});
+                    found = true;
+                }
+            if (!found) return fail(HYP_ERR_IO, "LEVEL for unknown species " + name);
+        } else if (key == "REACTION") {
+            ReactionRow r;
+            std::string colon, tok;
+            if (!(ss >> r.C_cgs >> r.n >> r.Ta >> colon) || colon != ":")
+                return fail(HYP_ERR_IO, "bad REACTION line: " + line);
+            bool right = false;
+            while (ss >> tok) {
+                if (tok == "=>") {
+                    right = true;
+                    continue;
+                }
+                (right ? r.rhs : r.lhs).push_back(tok);
+            }
+            if (!right || r.lhs.empty() || r.rhs.empty())
+                return fail(HYP_ERR_IO, "bad REACTION line: " + line);
+            rx.push_back(r);
+        } else {
+            return fail(HYP_ERR_IO, "unknown keyword " + key);
+        }
+    }
+    return HYP_OK;
+}
+
+// Sensible molar enthalpy / R_u from 0 K (used once, at 298.15 K, for the formation offset).
+double h_sens_over_r(const SpeciesRow& r, double T) {
+    double q = 0.0, m1 = 0.0;
+    for (auto& l : r.levels) {
+        double w = l.first * exp(-l.second / T);
+        q += w;
+        m1 += w * l.second;
+    }
+    double h = 2.5 * T + m1 / q;
+    if (r.linear) h += T + r.theta_v / expm1(r.theta_v / T);
+    return h;
+}
+
+}  // namespace table
+}  // namespace hyp
+
+using namespace hyp;
+using namespace hyp::table;
+
+extern "C" int hyp_gas_model_load(const char* path, int kind, const hyp_freestream* fs,
+                                  hyp_gas** out) {
+    if (!path || !fs || !out) return fail(HYP_ERR_ARG, "null argument");
+    if (kind < HYP_GAS_CNEQ || kind > HYP_GAS_CPG) return fail(HYP_ERR_ARG, "unknown gas kind");
+    std::vector<SpeciesRow> sp;
+    std::vector<ReactionRow> rx;
+    int rc = parse_table(path, sp, rx);
+    if (rc) return rc;
+    if ((int)sp.size() != NSP) return fail(HYP_ERR_IO, "gas table must list 5 species");
+    if ((int)rx.size() > MAXR) return fail(HYP_ERR_IO, "too many reactions");
+    hyp_gas* g = new hyp_gas();
+    GasDev& d = g->dev;
+    memset(&d, 0, sizeof(d));
+    d.kind = kind;
+    for (int i = 0; i < NSP; ++i) {
+        const SpeciesRow& r = sp[i];
+        g->names.push_back(r.name);
+        if ((int)r.levels.size() > MAXLEV || r.levels.empty()) {
+            delete g;
+            return fail(HYP_ERR_IO, "species " + r.name + ": 1 to 6 electronic levels required");
+        }
+        d.M[i] = r.M;
+        d.invM[i] = 1.0 / r.M;
+        d.Rs[i] = R_U / r.M;
+        d.e0[i] = (r.hf - R_U * h_sens_over_r(r, 298.15)) / r.M;
+        d.linear[i] = r.linear;
+        d.theta_v[i] = r.theta_v;
+        d.nlev[i] = (int)r.levels.size();
+        for (size_t l = 0; l < r.levels.size(); ++l) {
+            d.lev_g[i][l] = r.levels[l].first;
+            d.lev_th[i][l] = r.levels[l].second;
+        }
+        const double m = r.M / N_A;
+        double s0 = 1.5 * log(2.0 * PI * m * K_B / (H_P * H_P)) + log(K_B / P_STD) + 2.5;
+        if (r.linear) s0 += 1.0 - log(r.sym * r.theta_r);
+        d.s0[i] = s0;
+        d.blA[i] = r.bA;
+        d.blB[i] = r.bB;
+        d.blC[i] = r.bC;
+    }
+    std::vector<double> eps_list;
+    for (int i = 0; i < NSP; ++i)
+        for (int j = 0; j < NSP; ++j) {
+            const SpeciesRow &a = sp[i], &b = sp[j];
+            d.wilke_q[i][j] = pow(b.M / a.M, 0.25);
+            d.wilke_d[i][j] = 1.0 / sqrt(8.0 * (1.0 + a.M / b.M));
+            const double m_sr = (a.M * b.M / (a.M + b.M)) / N_A;
+            const double sig = 0.5 * (a.lj_s + b.lj_s) * 1.0e-10;
+            d.dinv[i][j] = PI * sig * sig / (3.0 / 16.0 * sqrt(2.0 * PI * K_B * K_B * K_B / m_sr));
+            const double eps = a.lj_e * b.lj_e;
+            int q = -1;
+            for (size_t k = 0; k < eps_list.size(); ++k)
+                if (eps_list[k] == eps) q = (int)k;
+            if (q < 0) {
+                if ((int)eps_list.size() == MAXEPS) {
+                    delete g;
+                    return fail(HYP_ERR_IO, "too many distinct well depths");
+                }
+                eps_list.push_back(eps);
+                q = (int)eps_list.size() - 1;
+            }
+            d.eps_group[i][j] = q;
+        }
+    d.neps = (int)eps_list.size();
+    for (int q = 0; q < d.neps; ++q) d.ln_eps[q] = 0.5 * log(eps_list[q]);
+    // reactions, grouped by (n, T_a, net stoichiometry): one k_f exponential and one K_c per group
+    d.nr = (int)rx.size();
+    for (int r = 0; r < d.nr; ++r) {
+        int order = 0;
+        for (auto& nm : rx[r].lhs) {
+            int idx = -1;
+            for (int i = 0; i < NSP; ++i)
+                if (sp[i].name == nm) idx = i;
+            if (idx < 0) {
+                delete g;
+                return fail(HYP_ERR_IO, "reaction uses unknown species " + nm);
+            }
+            d.nu_f[r][idx] += 1;
+            ++order;
+        }
+        for (auto& nm : rx[r].rhs) {
+            int idx = -1;
+            for (int i = 0; i < NSP; ++i)
+                if (sp[i].name == nm) idx = i;
+            if (idx < 0) {
+                delete g;
+                return fail(HYP_ERR_IO, "reaction uses unknown species " + nm);
+            }
+            d.nu_b[r][idx] += 1;
+        }
+        d.C[r] = rx[r].C_cgs * pow(1.0e-6, order - 1);
+        int grp = -1;
+        for (int k = 0; k < d.ngroup; ++k) {
+            bool same = d.g_n[k] == rx[r].n && d.g_Ta[k] == rx[r].Ta;
+            for (int i = 0; i < NSP; ++i) same = same && d.g_nu[k][i] == d.nu_b[r][i] - d.nu_f[r][i];
+            if (same) grp = k;
+        }
+        if (grp < 0) {
+            if (d.ngroup == MAXG) {
+                delete g;
+                return fail(HYP_ERR_IO, "too many reaction groups");
+            }
+            grp = d.ngroup++;
+            d.g_n[grp] = rx[r].n;
+            d.g_Ta[grp] = rx[r].Ta;
+            int dnu = 0;
+            for (int i = 0; i < NSP; ++i) {
+                d.g_nu[grp][i] = (signed char)(d.nu_b[r][i] - d.nu_f[r][i]);
+                dnu += d.nu_b[r][i] - d.nu_f[r][i];
+            }
+            d.g_dnu[grp] = dnu;
+        }
+        d.group[r] = grp;
+    }
+    // freestream scales (Eqs. 7, 11)
+    double Y[NSP], ym = 0.0, ysum = 0.0;
+    for (int i = 0; i < NSP; ++i) {
+        Y[i] = fs->Y_inf[i];
+        d.Y_inf[i] = fs->Y_inf[i];
+        ym += Y[i] * d.invM[i];
+        ysum += Y[i];
+    }
+    if (!(fs->T_inf > 0 && fs->p_inf > 0 && fs->reynolds > 0 && fabs(ysum - 1.0) < 1e-12)) {
+        delete g;
+        return fail(HYP_ERR_ARG, "freestream needs T, p, Re > 0 and mass fractions summing to 1");
+    }
+    SpeciesState s;
+    species_state(d, fs->T_inf, s);
+    double cv = 0.0;
+    for (int i = 0; i < NSP; ++i) cv += Y[i] * s.cv[i];
+    const double R = R_U * ym;
+    d.R_inf = R;
+    d.cp_inf = cv + R;
+    d.gamma_inf = (cv + R) / cv;
+    d.T_inf = fs->T_inf;
+    d.p_inf = fs->p_inf;
+    d.rho_inf = fs->p_inf / (R * fs->T_inf);
+    d.a_inf = sqrt(d.gamma_inf * R * fs->T_inf);
+    d.prandtl_cpg = fs->prandtl_cpg;
+    d.mach = fs->mach;
+    if (kind == HYP_GAS_CPG) {
+        d.mu_inf = SUTH_C1 * pow(fs->T_inf, 1.5) / (fs->T_inf + SUTH_TS);
+        d.k_inf = d.mu_inf * d.cp_inf / fs->prandtl_cpg;
+    } else {
+        ClosureOut o;
+        const double e = mixture_energy(d, fs->T_inf, Y);
+        closure_si(d, d.rho_inf, e, Y, fs->T_inf, false, false, o);
+        d.mu_inf = o.mu;
+        d.k_inf = o.k;
+    }
+    d.Re = fs->reynolds;
+    d.Pr = d.mu_inf * d.cp_inf / d.k_inf;
+    d.T_ref = (d.gamma_inf - 1.0) * fs->T_inf;
+    d.L_ref = d.Re * d.mu_inf / (d.rho_inf * d.a_inf);
+    *out = g;
+    return HYP_OK;
+}
+
+extern "C" int hyp_gas_scales(const hyp_gas* gas, int* n_species, double* sc) {
+    if (!gas) return fail(HYP_ERR_ARG, "null gas");
+    if (n_species) *n_species = NSP;
+    if (sc) {
+        const GasDev& d = gas->dev;
+        const double v[13] = {d.rho_inf, d.a_inf, d.T_inf, d.p_inf, d.mu_inf, d.k_inf, d.cp_inf,
+                              d.gamma_inf, d.R_inf, d.T_ref, d.L_ref, d.Re, d.Pr};
+        memcpy(sc, v, sizeof(v));
+    }
+    return HYP_OK;
+}
+
+extern "C" void hyp_gas_free(hyp_gas* gas) { delete gas; }
+
+extern "C" const char* hyp_last_error(void) { return g_last_error.c_str(); }
+
+// ---------------------------------------------------------------------------------------------
+// Pointwise kernels
+// ---------------------------------------------------------------------------------------------
+
+namespace gaskern {
+
+__global__ void __launch_bounds__(128) k_thermo_eval(
+    GasDev g, int64_t n, const double* __restrict__ rho, const double* __restrict__ e,
+    const double* __restrict__ Y, double* __restrict__ T, double* __restrict__ p,
+    double* __restrict__ wdot, double* __restrict__ mu, double* __restrict__ kk,
+    double* __restrict__ D, uint8_t* __restrict__ status) {
+    const bool reactions = g.kind == HYP_GAS_CNEQ;
+    const bool diffusion = g.kind == HYP_GAS_CNEQ;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double y[NSP];
+#pragma unroll
+        for (int s = 0; s < NSP; ++s) y[s] = Y[s * n + i];
+        ClosureOut o;
+        closure_si(g, rho[i], e[i], y, 1000.0, reactions && wdot, diffusion && D, o);
+        if (T) T[i] = o.T;
+        if (p) p[i] = o.p;
+        if (mu) mu[i] = o.mu;
+        if (kk) kk[i] = o.k;
+        if (wdot)
+#pragma unroll
+            for (int s = 0; s < NSP; ++s) wdot[s * n + i] = o.wdot[s];
+        if (D)
+#pragma unroll
+            for (int s = 0; s < NSP; ++s) D[s * n + i] = o.D[s];
+        if (status) status[i] = (uint8_t)o.status;
+    }
+}
+
+__global__ void k_thermo_energy(GasDev g, int64_t n, const double* __restrict__ T,
+                                const double* __restrict__ Y, double* __restrict__ e) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double y[NSP];
+#pragma unroll
+        for (int s = 0; s < NSP; ++s) y[s] = Y[s * n + i];
+        e[i] = mixture_energy(g, T[i], y);
+    }
+}
+
+int grid_for(int64_t n, int block) {
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t blocks = (n + block - 1) / block;
+    int64_t cap = (int64_t)sms * 16;
+    return (int)(blocks < cap ? (blocks > 0 ? blocks : 1) : cap);
+}
+
+}  // namespace gaskern
+using namespace gaskern;
+
+extern "C" int hyp_thermo_eval(const hyp_gas* gas, int64_t n, const double* rho, const double* e,
+                               const double* Y, double* T, double* p, double* wdot, double* mu,
+                               double* k, double* D, uint8_t* status, int precision,
+                               void* stream) {
+    if (!gas || n < 0) return fail(HYP_ERR_ARG, "null gas or negative n");
+    if (precision != HYP_FP64) return fail(HYP_ERR_ARG, "only HYP_FP64 is available");
+    if (n == 0) return HYP_OK;
+    if (!rho || !e || !Y) return fail(HYP_ERR_ARG, "null input");
+    const int block = 128;
+    k_thermo_eval<<<grid_for(n, block), block, 0, (cudaStream_t)stream>>>(
+        gas->dev, n, rho, e, Y, T, p, wdot, mu, k, D, status);
+    HYP_CUDA(cudaGetLastError());
+    return HYP_OK;
+}
+
+extern "C" int hyp_thermo_energy(const hyp_gas* gas, int64_t n, const double* T, const double* Y,
+                                 double* e, void* stream) {
+    if (!gas || n < 0) return fail(HYP_ERR_ARG, "null gas or negative n");
+    if (n == 0) return HYP_OK;
+    if (!T || !Y || !e) return fail(HYP_ERR_ARG, "null pointer");
+    const int block = 256;
+    k_thermo_energy<<<grid_for(n, block), block, 0, (cudaStream_t)stream>>>(gas->dev, n, T, Y, e);
+    HYP_CUDA(cudaGetLastError());
+    return HYP_OK;
+}

@@ -1,0 +1,107 @@
+// Internal declarations of the GB300 library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/hyp.h"
+
+#define NSP HYP_MAX_SPECIES   // species count the kernels are compiled for
+#define MAXR 24                // elementary reactions
+#define MAXG 12                // reaction groups sharing (n, T_a, net stoichiometry)
+#define MAXLEV 6               // electronic levels per species
+#define MAXEPS 16              // distinct Lennard-Jones well depths of species pairs
+
+namespace hyp {
+
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t err, const char* what);
+
+#define HYP_CUDA(call)                                         \
+    do {                                                       \
+        cudaError_t _e = (call);                               \
+        if (_e != cudaSuccess) return ::hyp::cuda_fail(_e, #call); \
+    } while (0)
+
+// Gas model as seen by the kernels: a plain struct passed by value as a kernel parameter.
+struct GasDev {
+    int kind;                    // hyp_gas_kind
+    int nr, ngroup, neps;
+    // species thermodynamics (rigid rotor / harmonic oscillator, Sec. 2.2.1)
+    double M[NSP], invM[NSP], Rs[NSP];
+    double e0[NSP];              // (hf298 - H_sens(298.15)) / M, J/kg
+    int linear[NSP];
+    double theta_v[NSP];
+    int nlev[NSP];
+    double lev_g[NSP][MAXLEV], lev_th[NSP][MAXLEV];
+    double s0[NSP];              // temperature-independent part of S/R at p_std
+    // transport
+    double blA[NSP], blB[NSP], blC[NSP];
+    double wilke_q[NSP][NSP];    // (M_r / M_s)^(1/4)
+    double wilke_d[NSP][NSP];    // 1 / sqrt(8 (1 + M_s / M_r))
+    double dinv[NSP][NSP];       // pi sigma_sr^2 / ((3/16) sqrt(2 pi k^3 / m_sr))
+    int eps_group[NSP][NSP];
+    double ln_eps[MAXEPS];
+    // kinetics (Eqs. 13-15): elementary reactions with explicit colliders
+    int group[MAXR];
+    double C[MAXR];              // SI pre-exponential factor
+    signed char nu_f[MAXR][NSP], nu_b[MAXR][NSP];
+    double g_n[MAXG], g_Ta[MAXG], g_dnu[MAXG];
+    signed char g_nu[MAXG][NSP]; // net stoichiometry nu'' - nu' of the group
+    // nondimensionalisation (Eqs. 7, 11)
+    double rho_inf, a_inf, T_inf, p_inf, mu_inf, k_inf, cp_inf, gamma_inf, R_inf, T_ref, L_ref,
+        Re, Pr;
+    double prandtl_cpg;
+    double mach;
+    double Y_inf[NSP];
+};
+
+}  // namespace hyp
+
+struct hyp_gas {
+    hyp::GasDev dev;
+    std::vector<std::string> names;
+};
+
+namespace hyp {
+
+// One compact line operator (Sec. 3.1): tridiagonal left-hand side with precomputed Thomas
+// factors, interior right-hand-side weights and explicit closure rows.
+struct LineOp {
+    int m, n_in;                 // output and input points along the line
+    int dir;                     // 0 centre->face, 1 face->centre
+    int kind;                    // 0 interpolation, 1 first derivative
+    int wall;                    // 1: known value at position 0 enters the closure rows
+    int first_interior, last_interior;
+    double wi[4];                // interior weights on inputs at offsets -3/2, -1/2, +1/2, +3/2
+    const double* lower;         // device: sub-diagonal of each row
+    const double* cprime;        // device: Thomas c'
+    const double* minv;          // device: Thomas 1 / pivot
+    int ncl;                     // closure rows (<= 4)
+    int crow[4], cstart[4], cnum[4];
+    double cw[4][5];
+    double gw[4];                // weight of the wall value
+};
+
+struct LineJob {
+    const LineOp* op;            // device pointer
+    const double* in;            // input field, or an element offset into the state when in_state
+    int in_state;
+    double* out;
+    double* tmp;                 // forward-sweep storage (out if null and not accumulating)
+    long long in_ls, in_es, out_ls, out_es;
+    int nlines;
+    int accumulate;
+    double wall_value;
+    double scale;
+    const double* metric;        // per output element along the line, nullable
+};
+
+cudaError_t launch_lines(const LineJob* d_jobs, int njobs, int max_lines, const double* U,
+                         cudaStream_t s);
+
+}  // namespace hyp

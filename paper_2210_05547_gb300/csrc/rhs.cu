@@ -1,0 +1,1153 @@
+// Right-hand side of the reacting Navier-Stokes equations on the staggered grid (Eqs. 1-11, 26;
+// Secs. 3.1-3.3) and the two-register RK3 stage update, plus the grid / state set-up.
+//
+// Device data of a grid: metrics, sponge strength and reference state in state layout, a
+// Dirichlet mask, the compact operators, and one block of scratch fields (cell centres, x-faces,
+// y-faces and corners). The right-hand side is a fixed sequence of launches: batched line
+// operators (lines.cu) alternate with pointwise kernels defined here.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "thermo.cuh"
+
+using namespace hyp;
+
+namespace {
+
+constexpr double RECOVERY = 0.85;
+constexpr double DUCROS_EPS = 1.0e-32;
+const double RK_A[3] = {0.0, -5.0 / 9.0, -153.0 / 128.0};
+const double RK_B[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};
+// nine-point truncated Gaussian filter weights (centre, +-1, +-2, +-3, +-4)
+__constant__ double c_gauss[5] = {3565.0 / 10368.0, 3091.0 / 12960.0, 1997.0 / 25920.0,
+                                  149.0 / 12960.0, 107.0 / 103680.0};
+
+enum Node { NC = 0, NXF = 1, NYF = 2, NCN = 3 };
+
+struct Dims {
+    int nx, ny;
+    int rows(Node t) const { return (t == NC || t == NXF) ? ny : ny + 1; }
+    int pitch(Node t) const { return (t == NC || t == NYF) ? nx : nx + 1; }
+    long long size(Node t) const { return (long long)rows(t) * pitch(t); }
+};
+
+struct Scratch {
+    // cell centres
+    double *ru_c, *rv_c, *T, *p, *H, *u_c, *v_c, *e, *a, *mu_e, *K, *beta, *Tcache;
+    double *Y[NSP], *X[NSP], *h[NSP], *Wd[NSP], *W[NSP], *G[NSP];
+    double *dudx, *dvdy, *tau_xx, *tau_yy, *Gxx, *Gyy;
+    double *dudy_c, *dvdx_c, *S, *div, *fsw, *raw[8], *filt[8];
+    // x-faces
+    double *rho_xf, *u_xf, *Yx[NSP], *Gx[NSP], *hx[NSP], *Hx, *Kx, *txx_x, *v_x, *dTdx,
+        *dXdx[NSP], *txy_x, *Fsx[NSP], *FEx, *mu_xf, *dudy_t, *dvdx_t;
+    // y-faces
+    double *rho_yf, *v_yf, *Yy[NSP], *Gy[NSP], *hy[NSP], *Hy, *Ky, *tyy_y, *u_y, *dTdy,
+        *dXdy[NSP], *txy_y, *Fsy[NSP], *FEy;
+    // corners
+    double *dudy_cn, *dvdx_cn, *u_cn, *v_cn, *rho_cn, *mu_cn, *tau_xy, *Gxy;
+    // state-sized
+    double *DX, *DY, *SRC, *R;
+};
+
+// Kernel-side view of a grid (passed by value).
+struct GridView {
+    int nx, ny, wall, ad, nstate;
+    long long off[NSP + 3];
+    double Tw_nd;
+    double C_mu, C_beta, C_kappa, C_D;
+    const double *xi_c, *eta_c;
+    unsigned* status;
+};
+
+enum Phase {
+    PH_P1, PH_P3, PH_AD1, PH_AD2, PH_MU1, PH_MU2, PH_FACE, PH_DIV, PH_COUNT
+};
+
+}  // namespace
+
+struct hyp_grid {
+    Dims d;
+    hyp_case cas;
+    GasDev gas;
+    int nstate;
+    long long off[NSP + 3];
+    double *xi_c, *xi_f, *eta_c, *eta_f;
+    double *Uref, *sigma;
+    uint8_t* mask;
+    unsigned* status;
+    double* pool;
+    Scratch s;
+    LineOp* ops;
+    double* opdata;
+    LineJob* jobs;
+    int ph_start[PH_COUNT], ph_count[PH_COUNT], ph_lines[PH_COUNT];
+    cudaStream_t stream;
+    double Tw_nd;
+    GridView view() const {
+        GridView v;
+        v.nx = d.nx;
+        v.ny = d.ny;
+        v.wall = cas.wall;
+        v.ad = cas.artificial_diffusivity;
+        v.nstate = nstate;
+        for (int i = 0; i < NSP + 3; ++i) v.off[i] = off[i];
+        v.Tw_nd = Tw_nd;
+        v.C_mu = cas.C_mu;
+        v.C_beta = cas.C_beta;
+        v.C_kappa = cas.C_kappa;
+        v.C_D = cas.C_D;
+        v.xi_c = xi_c;
+        v.eta_c = eta_c;
+        v.status = status;
+        return v;
+    }
+};
+
+struct hyp_state {
+    hyp_grid* grid;
+    double *U, *dQ;
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------------------------
+// Host: grid maps, oblique shock, reference profile
+// ---------------------------------------------------------------------------------------------
+
+void y_map(const hyp_grid_desc& d, double eta, double& y, double& dyde) {
+    const double s = eta / d.ny;
+    const double L = d.y1 - d.y0, q = d.y_param;
+    if (d.y_stretch == 1) {
+        y = d.y0 + L * (1.0 - tanh(q * (1.0 - s)) / tanh(q));
+        const double ch = cosh(q * (1.0 - s));
+        dyde = L * q / (ch * ch) / tanh(q) / d.ny;
+    } else if (d.y_stretch == 2) {
+        y = d.y0 + L * ((1.0 - q) * s * s * s + q * s);
+        dyde = L * (3.0 * (1.0 - q) * s * s + q) / d.ny;
+    } else {
+        y = d.y0 + L * s;
+        dyde = L / d.ny;
+    }
+}
+
+struct Shock {
+    double beta, p21, r21, T21, M2;
+};
+
+// Weak oblique shock for deflection theta: theta-beta-M relation by bisection on the rising
+// branch, then the Rankine-Hugoniot jumps of a perfect gas.
+Shock oblique_shock(double M1, double theta, double gam) {
+    auto defl = [&](double b) {
+        return atan(2.0 / tan(b) * (M1 * M1 * sin(b) * sin(b) - 1.0) /
+                    (M1 * M1 * (gam + cos(2.0 * b)) + 2.0));
+    };
+    double lo = asin(1.0 / M1) + 1e-12, hi = lo;
+    const double step = 1.0e-3;
+    while (defl(hi + step) > defl(hi)) hi += step;
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (defl(mid) < theta) lo = mid; else hi = mid;
+    }
+    Shock s;
+    s.beta = 0.5 * (lo + hi);
+    const double mn1 = M1 * sin(s.beta);
+    s.p21 = 1.0 + 2.0 * gam / (gam + 1.0) * (mn1 * mn1 - 1.0);
+    s.r21 = (gam + 1.0) * mn1 * mn1 / ((gam - 1.0) * mn1 * mn1 + 2.0);
+    s.T21 = s.p21 / s.r21;
+    const double mn2 =
+        sqrt((1.0 + 0.5 * (gam - 1.0) * mn1 * mn1) / (gam * mn1 * mn1 - 0.5 * (gam - 1.0)));
+    s.M2 = mn2 / sin(s.beta - theta);
+    return s;
+}
+
+struct Profile {
+    const GasDev* g;
+    hyp_case c;
+    double y0;
+    int iN2, iO2, iNO, iN, iO;
+    bool shock;
+    Shock sh;
+    double theta;
+    double Yinf[NSP];
+
+    // Boundary-layer profile below an edge state: u/u_e = erf(2 y / delta(x)), Crocco-Busemann T.
+    void edge(double x, double y, double Te, double pe, double ue, double ve, double Me,
+              double& T, double& p, double& u, double& v, double& f) const {
+        if (c.wall) {
+            const double delta = c.delta_coef * sqrt(x / (g->Re * g->mach));
+            f = erf(2.0 * (y - y0) / delta);
+            const double Tr = Te * (1.0 + RECOVERY * 0.5 * (g->gamma_inf - 1.0) * Me * Me);
+            T = c.T_wall + (Tr - c.T_wall) * f - (Tr - Te) * f * f;
+        } else {
+            f = 1.0;
+            T = Te;
+        }
+        p = pe;
+        u = ue * f;
+        v = ve * f;
+    }
+
+    // primitive reference state: T [K], p [Pa], u, v nondimensional, Y
+    void at(double x, double y, double& T, double& p, double& u, double& v, double* Y) const {
+        double f;
+        edge(x, y, g->T_inf, g->p_inf, g->mach, 0.0, g->mach, T, p, u, v, f);
+        if (shock) {
+            const double V2 = sh.M2 * sqrt(sh.T21);
+            double T2, p2, u2, v2, f2;
+            edge(x, y, g->T_inf * sh.T21, g->p_inf * sh.p21, V2 * cos(theta), -V2 * sin(theta),
+                 sh.M2, T2, p2, u2, v2, f2);
+            const double ys = (c.shock_x - x) * tan(sh.beta);
+            const double H = 0.5 * (1.0 + tanh((y - ys) / c.shock_width));
+            T = (1.0 - H) * T + H * T2;
+            p = (1.0 - H) * p + H * p2;
+            u = (1.0 - H) * u + H * u2;
+            v = (1.0 - H) * v + H * v2;
+        }
+        for (int s = 0; s < NSP; ++s) Y[s] = Yinf[s];
+        const bool seed = c.wall && g->kind != HYP_GAS_CPG && iN2 >= 0 && iO2 >= 0 && iNO >= 0 &&
+                          iN >= 0 && iO >= 0;
+        if (seed) {
+            const double m = c.minor_species * 4.0 * f * (1.0 - f);
+            Y[iN2] = Yinf[iN2] * (1.0 - m);
+            Y[iO2] = Yinf[iO2] * (1.0 - m);
+            Y[iNO] = 0.5 * m;
+            Y[iN] = 0.2 * m;
+            Y[iO] = 0.3 * m;
+        }
+    }
+
+    // nondimensional rho, rho_s (all species), rho*E
+    void conserved(double T, double p, double u, double v, const double* Y, double& rho,
+                   double* rhoY, double& rhoE) const {
+        double rho_si, e_nd;
+        if (g->kind == HYP_GAS_CPG) {
+            rho_si = p / (g->R_inf * T);
+            e_nd = (T / g->T_ref) / g->gamma_inf;
+        } else {
+            double ym = 0.0;
+            for (int s = 0; s < NSP; ++s) ym += Y[s] * g->invM[s];
+            rho_si = p / (R_U * ym * T);
+            e_nd = mixture_energy(*g, T, Y) / (g->a_inf * g->a_inf);
+        }
+        rho = rho_si / g->rho_inf;
+        for (int s = 0; s < NSP; ++s) rhoY[s] = rho * Y[s];
+        rhoE = rho * (e_nd + 0.5 * (u * u + v * v));
+    }
+};
+
+// ---------------------------------------------------------------------------------------------
+// Host: compact operators
+// ---------------------------------------------------------------------------------------------
+
+void lagrange(const double* nodes, int n, double x, bool deriv, double* w) {
+    for (int k = 0; k < n; ++k) {
+        double den = 1.0;
+        for (int m = 0; m < n; ++m)
+            if (m != k) den *= nodes[k] - nodes[m];
+        double num;
+        if (!deriv) {
+            num = 1.0;
+            for (int m = 0; m < n; ++m)
+                if (m != k) num *= x - nodes[m];
+        } else {
+            num = 0.0;
+            for (int skip = 0; skip < n; ++skip) {
+                if (skip == k) continue;
+                double t = 1.0;
+                for (int m = 0; m < n; ++m)
+                    if (m != k && m != skip) t *= x - nodes[m];
+                num += t;
+            }
+        }
+        w[k] = num / den;
+    }
+}
+
+// Build one operator: kind 0 interpolation / 1 derivative; dir 0 centre->face / 1 face->centre.
+LineOp make_op(int kind, int dir, int n, int wall, std::vector<double>& data) {
+    LineOp op;
+    memset(&op, 0, sizeof(op));
+    op.kind = kind;
+    op.dir = dir;
+    op.wall = wall;
+    double alpha, a, b;
+    if (kind == 0) { alpha = 3.0 / 10.0; a = 3.0 / 2.0; b = 1.0 / 10.0; }
+    else { alpha = 9.0 / 62.0; a = 63.0 / 62.0; b = 17.0 / 62.0; }
+    if (kind == 0) {
+        op.wi[0] = b / 2.0; op.wi[1] = a / 2.0; op.wi[2] = a / 2.0; op.wi[3] = b / 2.0;
+    } else {
+        op.wi[0] = -b / 3.0; op.wi[1] = -a; op.wi[2] = a; op.wi[3] = b / 3.0;
+    }
+    std::vector<double> in_pos, out_pos;
+    if (dir == 0) {
+        op.m = n + 1;
+        op.n_in = n;
+        for (int k = 0; k < n; ++k) in_pos.push_back(k + 0.5);
+        for (int i = 0; i <= n; ++i) out_pos.push_back(i);
+        op.first_interior = 2;
+        op.last_interior = n - 2;
+    } else {
+        op.m = n;
+        op.n_in = n + 1;
+        for (int i = 0; i <= n; ++i) in_pos.push_back(i);
+        for (int k = 0; k < n; ++k) out_pos.push_back(k + 0.5);
+        op.first_interior = 1;
+        op.last_interior = n - 2;
+    }
+    const int m = op.m;
+    std::vector<double> lower(m, 0.0), upper(m, 0.0);
+    for (int r = 0; r < m; ++r) {
+        const bool interior = r >= op.first_interior && r <= op.last_interior;
+        if (interior) {
+            if (r > 0) lower[r] = alpha;
+            if (r < m - 1) upper[r] = alpha;
+            continue;
+        }
+        const int c = op.ncl++;
+        op.crow[c] = r;
+        const bool left = r < op.first_interior;
+        double nodes[5], w[5];
+        if (left && wall) {
+            nodes[0] = 0.0;
+            for (int k = 0; k < 4; ++k) nodes[k + 1] = in_pos[k];
+            lagrange(nodes, 5, out_pos[r], kind == 1, w);
+            op.gw[c] = w[0];
+            op.cstart[c] = 0;
+            op.cnum[c] = 4;
+            for (int k = 0; k < 4; ++k) op.cw[c][k] = w[k + 1];
+        } else {
+            const int start = left ? 0 : (int)in_pos.size() - 5;
+            for (int k = 0; k < 5; ++k) nodes[k] = in_pos[start + k];
+            lagrange(nodes, 5, out_pos[r], kind == 1, w);
+            op.gw[c] = 0.0;
+            op.cstart[c] = start;
+            op.cnum[c] = 5;
+            for (int k = 0; k < 5; ++k) op.cw[c][k] = w[k];
+        }
+    }
+    // Thomas factors of the unit-diagonal tridiagonal matrix
+    std::vector<double> cp(m), mi(m);
+    for (int r = 0; r < m; ++r) {
+        const double piv = 1.0 - (r > 0 ? lower[r] * cp[r - 1] : 0.0);
+        mi[r] = 1.0 / piv;
+        cp[r] = upper[r] * mi[r];
+    }
+    // store offsets into data (fixed up to device pointers later)
+    const size_t base = data.size();
+    data.insert(data.end(), lower.begin(), lower.end());
+    data.insert(data.end(), cp.begin(), cp.end());
+    data.insert(data.end(), mi.begin(), mi.end());
+    op.lower = (const double*)(base);
+    op.cprime = (const double*)(base + m);
+    op.minv = (const double*)(base + 2 * m);
+    return op;
+}
+
+enum OpId { OX_ICF, OX_DCF, OX_IFC, OX_DFC, OY_ICF, OY_DCF, OY_IFC, OY_DFC, OY_ICFW, OY_DCFW, NOPS };
+
+// ---------------------------------------------------------------------------------------------
+// Pointwise kernels
+// ---------------------------------------------------------------------------------------------
+
+__device__ __forceinline__ void atomic_status(unsigned* st, unsigned bits) {
+    if (bits) atomicOr(st, bits);
+}
+
+// (A) primitives and the closure at every cell centre
+__global__ void __launch_bounds__(128) k_closure(GasDev g, GridView v, const double* __restrict__ U,
+                                                 Scratch s) {
+    const int n = v.nx * v.ny;
+    const bool cpg = g.kind == HYP_GAS_CPG;
+    const bool cneq = g.kind == HYP_GAS_CNEQ;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+        const double rho = U[v.off[0] + idx];
+        double Y[NSP];
+        double rest = rho;
+#pragma unroll
+        for (int sp = 1; sp < NSP; ++sp) {
+            const double r = U[v.off[sp] + idx];
+            Y[sp] = r / rho;
+            rest -= r;
+        }
+        Y[0] = rest / rho;
+        const double rhoE = U[v.off[NSP] + idx];
+        const double u = s.ru_c[idx] / rho;
+        const double vv = s.rv_c[idx] / rho;
+        const double e = rhoE / rho - 0.5 * (u * u + vv * vv);
+        double T, p, mu, k, a;
+        double h[NSP], wd[NSP], X[NSP], W[NSP], Wd[NSP];
+        if (cpg) {
+            T = g.gamma_inf * e;
+            p = rho * (g.gamma_inf - 1.0) / g.gamma_inf * T;
+            const double Td = T * g.T_ref;
+            mu = SUTH_C1 * Td * sqrt(Td) / (Td + SUTH_TS) / g.mu_inf;
+            k = mu;
+            a = sqrt(g.gamma_inf * p / rho);
+#pragma unroll
+            for (int sp = 0; sp < NSP; ++sp) h[sp] = wd[sp] = X[sp] = W[sp] = Wd[sp] = 0.0;
+        } else {
+            ClosureOut o;
+            closure_si(g, rho * g.rho_inf, e * g.a_inf * g.a_inf, Y, s.Tcache[idx], cneq, cneq, o);
+            atomic_status(v.status, o.status);
+            s.Tcache[idx] = o.T;
+            T = o.T / g.T_ref;
+            p = o.p / (g.rho_inf * g.a_inf * g.a_inf);
+            mu = o.mu / g.mu_inf;
+            k = o.k / g.k_inf;
+            a = o.a / g.a_inf;
+            double ym = 0.0;
+#pragma unroll
+            for (int sp = 0; sp < NSP; ++sp) ym += Y[sp] * g.invM[sp];
+            const double wscale = g.L_ref / (g.rho_inf * g.a_inf);
+            const double inva2 = 1.0 / (g.a_inf * g.a_inf);
+#pragma unroll
+            for (int sp = 0; sp < NSP; ++sp) {
+                h[sp] = o.h[sp] * inva2;
+                wd[sp] = o.wdot[sp] * wscale;
+                X[sp] = o.X[sp];
+                W[sp] = cneq ? rho * g.M[sp] * ym : 0.0;
+                Wd[sp] = cneq ? W[sp] * (o.D[sp] * g.rho_inf / g.mu_inf) / g.Re : 0.0;
+            }
+        }
+        s.T[idx] = T;
+        s.p[idx] = p;
+        s.H[idx] = (rhoE + p) / rho;
+        s.u_c[idx] = u;
+        s.v_c[idx] = vv;
+        s.e[idx] = e;
+        s.a[idx] = a;
+        s.mu_e[idx] = mu / g.Re;
+        s.K[idx] = k / (g.Re * g.Pr);
+        if (!v.ad) s.beta[idx] = 0.0;
+#pragma unroll
+        for (int sp = 0; sp < NSP; ++sp) {
+            s.Y[sp][idx] = Y[sp];
+            s.X[sp][idx] = X[sp];
+            s.h[sp][idx] = h[sp];
+            s.Wd[sp][idx] = Wd[sp];
+            s.W[sp][idx] = W[sp];
+            if (!v.ad) s.G[sp][idx] = Wd[sp];
+        }
+#pragma unroll
+        for (int sp = 1; sp < NSP; ++sp) s.SRC[v.off[sp] + idx] = wd[sp];
+    }
+}
+
+// (B) face velocities
+__global__ void k_face_vel(GridView v, const double* __restrict__ U, Scratch s) {
+    const int nxf = v.ny * (v.nx + 1), nyf = (v.ny + 1) * v.nx;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nxf + nyf; i += gridDim.x * blockDim.x) {
+        if (i < nxf) s.u_xf[i] = U[v.off[NSP + 1] + i] / s.rho_xf[i];
+        else {
+            const int j = i - nxf;
+            s.v_yf[j] = U[v.off[NSP + 2] + j] / s.rho_yf[j];
+        }
+    }
+}
+
+// (D) artificial diffusivity: strain-rate magnitude, dilatation, Ducros switch
+__global__ void k_ad_prep(GridView v, Scratch s) {
+    const int n = v.nx * v.ny;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double ux = s.dudx[i], vy = s.dvdy[i], uy = s.dudy_c[i], vx = s.dvdx_c[i];
+        const double sxy = uy + vx;
+        s.S[i] = sqrt(ux * ux + vy * vy + 0.5 * sxy * sxy);
+        const double dv = ux + vy;
+        const double om = vx - uy;
+        s.div[i] = dv;
+        s.fsw[i] = dv < 0.0 ? dv * dv / (dv * dv + om * om + DUCROS_EPS) : 0.0;
+    }
+}
+
+__device__ __forceinline__ double d4x(const double* f, int j, int i, int nx) {
+    const int c = min(max(i, 2), nx - 3);
+    const double* r = f + (long long)j * nx + c;
+    return r[-2] - 4.0 * r[-1] + 6.0 * r[0] - 4.0 * r[1] + r[2];
+}
+
+__device__ __forceinline__ double d4y(const double* f, int j, int i, int nx, int ny) {
+    const int c = min(max(j, 2), ny - 3);
+    const double* r = f + (long long)c * nx + i;
+    return r[-2 * nx] - 4.0 * r[-nx] + 6.0 * r[0] - 4.0 * r[nx] + r[2 * nx];
+}
+
+__global__ void k_ad_raw(GasDev g, GridView v, const double* __restrict__ U, Scratch s) {
+    const int n = v.nx * v.ny;
+    const bool cneq = g.kind == HYP_GAS_CNEQ;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+        const int j = idx / v.nx, i = idx - j * v.nx;
+        const double dx = 1.0 / v.xi_c[i], dy = 1.0 / v.eta_c[j];
+        const double rho = U[v.off[0] + idx];
+        s.raw[0][idx] = v.C_mu * rho *
+                        fabs(d4x(s.S, j, i, v.nx) * dx * dx + d4y(s.S, j, i, v.nx, v.ny) * dy * dy);
+        s.raw[1][idx] = v.C_beta * rho * s.fsw[idx] *
+                        fabs(d4x(s.div, j, i, v.nx) * dx * dx + d4y(s.div, j, i, v.nx, v.ny) * dy * dy);
+        s.raw[2][idx] = v.C_kappa * rho * s.a[idx] / s.T[idx] *
+                        fabs(d4x(s.e, j, i, v.nx) * dx + d4y(s.e, j, i, v.nx, v.ny) * dy);
+#pragma unroll
+        for (int sp = 0; sp < NSP; ++sp)
+            s.raw[3 + sp][idx] =
+                cneq ? v.C_D * s.a[idx] *
+                           fabs(d4x(s.Y[sp], j, i, v.nx) * dx + d4y(s.Y[sp], j, i, v.nx, v.ny) * dy)
+                     : 0.0;
+    }
+}
+
+// Gaussian filter of the eight raw diffusivities along x (dir 0) or y (dir 1); indices clamp.
+__global__ void k_gauss(GridView v, Scratch s, int dir) {
+    const int n = v.nx * v.ny;
+    const int f = blockIdx.y;
+    const double* __restrict__ in = dir == 0 ? s.raw[f] : s.filt[f];
+    double* __restrict__ out = dir == 0 ? s.filt[f] : s.raw[f];
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+        const int j = idx / v.nx, i = idx - j * v.nx;
+        double acc = c_gauss[0] * in[idx];
+        if (dir == 0) {
+            const double* r = in + (long long)j * v.nx;
+#pragma unroll
+            for (int d = 1; d <= 4; ++d)
+                acc += c_gauss[d] * (r[max(i - d, 0)] + r[min(i + d, v.nx - 1)]);
+        } else {
+#pragma unroll
+            for (int d = 1; d <= 4; ++d)
+                acc += c_gauss[d] * (in[(long long)max(j - d, 0) * v.nx + i] +
+                                     in[(long long)min(j + d, v.ny - 1) * v.nx + i]);
+        }
+        out[idx] = acc;
+    }
+}
+
+__global__ void k_ad_combine(GridView v, Scratch s) {
+    const int n = v.nx * v.ny;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        s.mu_e[i] += s.raw[0][i];
+        s.beta[i] = s.raw[1][i];
+        s.K[i] += s.raw[2][i];
+#pragma unroll
+        for (int sp = 0; sp < NSP; ++sp) s.G[sp][i] = s.Wd[sp][i] + s.W[sp][i] * s.raw[3 + sp][i];
+    }
+}
+
+// (F, I) normal stresses and momentum fluxes at centres
+__global__ void k_stress_c(GridView v, Scratch s) {
+    const int n = v.nx * v.ny;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double ux = s.dudx[i], vy = s.dvdy[i];
+        const double dv = ux + vy;
+        const double mu = s.mu_e[i], b = s.beta[i];
+        const double txx = mu * (2.0 * ux - 2.0 / 3.0 * dv) + b * dv;
+        const double tyy = mu * (2.0 * vy - 2.0 / 3.0 * dv) + b * dv;
+        s.tau_xx[i] = txx;
+        s.tau_yy[i] = tyy;
+        s.Gxx[i] = s.ru_c[i] * s.u_c[i] + s.p[i] - txx;
+        s.Gyy[i] = s.rv_c[i] * s.v_c[i] + s.p[i] - tyy;
+    }
+}
+
+// (F, I) shear stress and cross momentum flux at corners
+__global__ void k_stress_cn(GridView v, Scratch s) {
+    const int n = (v.nx + 1) * (v.ny + 1);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double txy = s.mu_cn[i] * (s.dudy_cn[i] + s.dvdx_cn[i]);
+        s.tau_xy[i] = txy;
+        s.Gxy[i] = s.rho_cn[i] * s.u_cn[i] * s.v_cn[i] - txy;
+    }
+}
+
+// (G, H) species and energy fluxes at x-faces (dir 0) or y-faces (dir 1)
+__global__ void k_flux(GridView v, const double* __restrict__ U, Scratch s, int dir) {
+    const int n = dir == 0 ? v.ny * (v.nx + 1) : (v.ny + 1) * v.nx;
+    const double* __restrict__ mom = U + v.off[NSP + 1 + dir];
+    double* const* Yf = dir == 0 ? s.Yx : s.Yy;
+    double* const* Gf = dir == 0 ? s.Gx : s.Gy;
+    double* const* hf = dir == 0 ? s.hx : s.hy;
+    double* const* dX = dir == 0 ? s.dXdx : s.dXdy;
+    double* const* Fs = dir == 0 ? s.Fsx : s.Fsy;
+    const double* Hf = dir == 0 ? s.Hx : s.Hy;
+    const double* Kf = dir == 0 ? s.Kx : s.Ky;
+    const double* dT = dir == 0 ? s.dTdx : s.dTdy;
+    const double* tn = dir == 0 ? s.txx_x : s.tyy_y;      // normal stress at the face
+    const double* tsh = dir == 0 ? s.txy_x : s.txy_y;     // shear stress at the face
+    const double* un = dir == 0 ? s.u_xf : s.v_yf;        // velocity normal to the face
+    const double* ut = dir == 0 ? s.v_x : s.u_y;          // tangential velocity
+    double* FE = dir == 0 ? s.FEx : s.FEy;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const bool wallface = dir == 1 && v.wall && i < v.nx;
+        double g[NSP], J[NSP], sum = 0.0;
+#pragma unroll
+        for (int sp = 0; sp < NSP; ++sp) {
+            g[sp] = Gf[sp][i] * dX[sp][i];
+            sum += g[sp];
+        }
+        double q = -Kf[i] * dT[i];
+        const double m = mom[i];
+#pragma unroll
+        for (int sp = 0; sp < NSP; ++sp) {
+            J[sp] = wallface ? 0.0 : -(g[sp] - Yf[sp][i] * sum);
+            q += hf[sp][i] * J[sp];
+        }
+#pragma unroll
+        for (int sp = 1; sp < NSP; ++sp) Fs[sp][i] = m * Yf[sp][i] + J[sp];
+        // tau . u normal component: x-face tau_xx u + tau_xy v; y-face tau_xy u + tau_yy v
+        const double work = dir == 0 ? tn[i] * un[i] + tsh[i] * ut[i] : tsh[i] * ut[i] + tn[i] * un[i];
+        FE[i] = m * Hf[i] + q - work;
+    }
+}
+
+// (J) sum of divergences, sources and sponge; Dirichlet rows; optional RK stage update
+__global__ void k_assemble(int n, const double* __restrict__ DX, const double* __restrict__ DY,
+                           const double* __restrict__ SRC, const double* __restrict__ sigma,
+                           const double* __restrict__ Uref, const uint8_t* __restrict__ mask,
+                           double* __restrict__ U, double* __restrict__ out, double* __restrict__ dQ,
+                           int rk, double A, double B, double dt) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double u = U[i];
+        double r = DX[i] + DY[i] + SRC[i] - sigma[i] * (u - Uref[i]);
+        if (mask[i]) r = 0.0;
+        if (rk) {
+            const double q = A * dQ[i] + dt * r;
+            dQ[i] = q;
+            U[i] = u + B * q;
+        } else {
+            out[i] = r;
+        }
+    }
+}
+
+__global__ void k_fill(double* p, long long n, double val) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        p[i] = val;
+}
+
+int blocks_for(long long n, int block) {
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long b = (n + block - 1) / block;
+    long long cap = (long long)sms * 8;
+    if (b < 1) b = 1;
+    return (int)std::min(b, cap);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Host: job plans
+// ---------------------------------------------------------------------------------------------
+
+struct PlanBuilder {
+    const hyp_grid* G;
+    const LineOp* dops;  // device operator array
+    std::vector<LineJob> jobs;
+    int ph_start[PH_COUNT], ph_count[PH_COUNT], ph_lines[PH_COUNT];
+    int cur = -1;
+
+    void begin(int ph) {
+        cur = ph;
+        ph_start[ph] = (int)jobs.size();
+        ph_count[ph] = 0;
+        ph_lines[ph] = 0;
+    }
+    // axis 0: along x (lines are rows), 1: along y (lines are columns)
+    void add(OpId op, const double* in, Node tin, double* out, Node tout, const double* metric,
+             double scale = 1.0, double wall_value = 0.0, int in_state = 0) {
+        const Dims& d = G->d;
+        const bool alongx = op <= OX_DFC;
+        LineJob j;
+        memset(&j, 0, sizeof(j));
+        j.op = dops + op;
+        j.in = in;
+        j.in_state = in_state;
+        j.out = out;
+        j.tmp = nullptr;
+        if (alongx) {
+            j.in_ls = d.pitch(tin);
+            j.in_es = 1;
+            j.out_ls = d.pitch(tout);
+            j.out_es = 1;
+            j.nlines = d.rows(tin);
+        } else {
+            j.in_ls = 1;
+            j.in_es = d.pitch(tin);
+            j.out_ls = 1;
+            j.out_es = d.pitch(tout);
+            j.nlines = d.pitch(tin);
+        }
+        j.accumulate = 0;
+        j.wall_value = wall_value;
+        j.scale = scale;
+        j.metric = metric;
+        jobs.push_back(j);
+        ph_count[cur]++;
+        ph_lines[cur] = std::max(ph_lines[cur], j.nlines);
+    }
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------------------------
+
+static int check_desc(const hyp_grid_desc* d) {
+    if (!d) return fail(HYP_ERR_ARG, "null grid descriptor");
+    if (d->nx < 8 || d->ny < 8) return fail(HYP_ERR_ARG, "grid needs at least 8 cells per direction");
+    if ((long long)d->nx * d->ny > (1LL << 28)) return fail(HYP_ERR_ARG, "grid too large");
+    if (!(d->x1 > d->x0) || !(d->y1 > d->y0)) return fail(HYP_ERR_ARG, "empty domain");
+    if (d->y_stretch < 0 || d->y_stretch > 2) return fail(HYP_ERR_ARG, "unknown y stretching");
+    return HYP_OK;
+}
+
+extern "C" int hyp_state_size(const hyp_gas* gas, const hyp_grid_desc* desc, int64_t* n) {
+    if (!gas || !n) return fail(HYP_ERR_ARG, "null argument");
+    int rc = check_desc(desc);
+    if (rc) return rc;
+    const long long nc = (long long)desc->nx * desc->ny;
+    *n = (NSP + 1) * nc + (long long)(desc->nx + 1) * desc->ny + (long long)desc->nx * (desc->ny + 1);
+    return HYP_OK;
+}
+
+static void free_grid(hyp_grid* G) {
+    if (!G) return;
+    cudaFree(G->pool);
+    cudaFree(G->mask);
+    cudaFree(G->status);
+    cudaFree(G->ops);
+    cudaFree(G->opdata);
+    cudaFree(G->jobs);
+    delete G;
+}
+
+extern "C" int hyp_state_init(const hyp_gas* gas, const hyp_grid_desc* desc, const hyp_case* cas,
+                              double* U, double* dQ, void* stream, hyp_state** out) {
+    if (!gas || !cas || !U || !dQ || !out) return fail(HYP_ERR_ARG, "null argument");
+    int rc = check_desc(desc);
+    if (rc) return rc;
+    if (cas->flow == 1 && !(cas->shock_width > 0)) return fail(HYP_ERR_ARG, "shock_width must be > 0");
+    if (cas->wall && !(cas->T_wall > 0)) return fail(HYP_ERR_ARG, "T_wall must be > 0");
+    if (cas->sponge_top_cells < 0 || cas->sponge_top_cells >= desc->ny)
+        return fail(HYP_ERR_ARG, "sponge_top_cells out of range");
+    cudaStream_t s = (cudaStream_t)stream;
+    const GasDev& g = gas->dev;
+    hyp_grid* G = new hyp_grid();
+    memset((void*)G, 0, sizeof(hyp_grid));
+    G->d.nx = desc->nx;
+    G->d.ny = desc->ny;
+    G->cas = *cas;
+    G->cas.noise = nullptr;
+    G->gas = g;
+    G->stream = s;
+    const Dims& d = G->d;
+    const int nx = d.nx, ny = d.ny;
+    const long long nc = d.size(NC), nxf = d.size(NXF), nyf = d.size(NYF), ncn = d.size(NCN);
+    long long o = 0;
+    for (int f = 0; f < NSP + 1; ++f) {
+        G->off[f] = o;
+        o += nc;
+    }
+    G->off[NSP + 1] = o;
+    o += nxf;
+    G->off[NSP + 2] = o;
+    o += nyf;
+    G->nstate = (int)o;
+    const long long ns_ = o;
+    G->Tw_nd = cas->T_wall / g.T_ref;
+
+    // ---------------- host set-up: metrics, sponge, reference, initial state ----------------
+    std::vector<double> xc(nx), xf(nx + 1), yc(ny), yf(ny + 1), xi_c(nx), xi_f(nx + 1),
+        eta_c(ny), eta_f(ny + 1);
+    const double dx = (desc->x1 - desc->x0) / nx;
+    for (int i = 0; i <= nx; ++i) {
+        xf[i] = desc->x0 + dx * i;
+        xi_f[i] = 1.0 / dx;
+    }
+    for (int i = 0; i < nx; ++i) {
+        xc[i] = desc->x0 + dx * (i + 0.5);
+        xi_c[i] = 1.0 / dx;
+    }
+    for (int j = 0; j <= ny; ++j) {
+        double y, dy;
+        y_map(*desc, (double)j, y, dy);
+        yf[j] = y;
+        eta_f[j] = 1.0 / dy;
+    }
+    for (int j = 0; j < ny; ++j) {
+        double y, dy;
+        y_map(*desc, j + 0.5, y, dy);
+        yc[j] = y;
+        eta_c[j] = 1.0 / dy;
+    }
+    auto sponge = [&](double x, double y) {
+        double sg = 0.0;
+        if (cas->sponge_in > 0) {
+            double r = std::min(std::max((desc->x0 + cas->sponge_in - x) / cas->sponge_in, 0.0), 1.0);
+            sg += r * r * r;
+        }
+        if (cas->sponge_out > 0) {
+            double r = std::min(std::max((x - (desc->x1 - cas->sponge_out)) / cas->sponge_out, 0.0), 1.0);
+            sg += r * r * r;
+        }
+        if (cas->sponge_top_cells > 0) {
+            const double ytop = yf[ny - cas->sponge_top_cells];
+            double r = std::min(std::max((y - ytop) / (desc->y1 - ytop), 0.0), 1.0);
+            sg += r * r * r;
+        }
+        return cas->sponge_sigma * sg;
+    };
+    Profile P;
+    P.g = &g;
+    P.c = *cas;
+    P.y0 = desc->y0;
+    P.iN2 = P.iO2 = P.iNO = P.iN = P.iO = -1;
+    for (int sp = 0; sp < NSP; ++sp) {
+        const std::string& nm = gas->names[sp];
+        if (nm == "N2") P.iN2 = sp;
+        if (nm == "O2") P.iO2 = sp;
+        if (nm == "NO") P.iNO = sp;
+        if (nm == "N") P.iN = sp;
+        if (nm == "O") P.iO = sp;
+        P.Yinf[sp] = 0.0;
+    }
+    P.shock = cas->flow == 1;
+    P.theta = cas->shock_deflection_deg * 3.14159265358979323846 / 180.0;
+    if (P.shock) P.sh = oblique_shock(g.mach, P.theta, g.gamma_inf);
+    for (int sp = 0; sp < NSP; ++sp) P.Yinf[sp] = g.Y_inf[sp];
+    std::vector<double> Uref(ns_), sig(ns_), U0(ns_);
+    std::vector<uint8_t> mask(ns_, 0);
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            double T, p, u, v, Y[NSP], rho, rY[NSP], rE;
+            P.at(xc[i], yc[j], T, p, u, v, Y);
+            P.conserved(T, p, u, v, Y, rho, rY, rE);
+            const long long k = (long long)j * nx + i;
+            Uref[G->off[0] + k] = rho;
+            for (int sp = 1; sp < NSP; ++sp) Uref[G->off[sp] + k] = rY[sp];
+            Uref[G->off[NSP] + k] = rE;
+            const double sg = sponge(xc[i], yc[j]);
+            for (int f = 0; f <= NSP; ++f) sig[G->off[f] + k] = sg;
+        }
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i <= nx; ++i) {
+            double T, p, u, v, Y[NSP], rho, rY[NSP], rE;
+            P.at(xf[i], yc[j], T, p, u, v, Y);
+            P.conserved(T, p, u, v, Y, rho, rY, rE);
+            const long long k = G->off[NSP + 1] + (long long)j * (nx + 1) + i;
+            Uref[k] = rho * u;
+            sig[k] = sponge(xf[i], yc[j]);
+            if (i == 0 || i == nx) mask[k] = 1;
+        }
+    for (int j = 0; j <= ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            double T, p, u, v, Y[NSP], rho, rY[NSP], rE;
+            P.at(xc[i], yf[j], T, p, u, v, Y);
+            P.conserved(T, p, u, v, Y, rho, rY, rE);
+            const long long k = G->off[NSP + 2] + (long long)j * nx + i;
+            Uref[k] = rho * v;
+            sig[k] = sponge(xc[i], yf[j]);
+            if (j == 0 || j == ny) mask[k] = 1;
+        }
+    for (long long k = 0; k < ns_; ++k) {
+        U0[k] = Uref[k];
+        if (cas->noise && cas->noise_amp > 0 && !mask[k]) U0[k] = Uref[k] * (1.0 + cas->noise_amp * cas->noise[k]);
+    }
+
+    // ---------------- device memory ----------------
+    const long long n_c_fields = 13 + 6 * NSP + 6 + 5 + 16;
+    const long long n_xf_fields = 2 + 6 * NSP + 8 + 3;
+    const long long n_yf_fields = 2 + 6 * NSP + 8;
+    const long long n_cn_fields = 8;
+    const long long pool_n = n_c_fields * nc + n_xf_fields * nxf + n_yf_fields * nyf +
+                             n_cn_fields * ncn + 6 * ns_ + (2 * nx + 1) + (2 * ny + 1) + 4;
+    cudaError_t err = cudaMalloc(&G->pool, pool_n * sizeof(double));
+    if (err != cudaSuccess) {
+        free_grid(G);
+        return cuda_fail(err, "cudaMalloc(grid pool)");
+    }
+    double* cur = G->pool;
+    auto take = [&](long long n) {
+        double* p = cur;
+        cur += n;
+        return p;
+    };
+    Scratch& S = G->s;
+    double** cfields[] = {&S.ru_c, &S.rv_c, &S.T, &S.p, &S.H, &S.u_c, &S.v_c, &S.e, &S.a,
+                          &S.mu_e, &S.K, &S.beta, &S.Tcache};
+    for (double** f : cfields) *f = take(nc);
+    for (int sp = 0; sp < NSP; ++sp) {
+        S.Y[sp] = take(nc);
+        S.X[sp] = take(nc);
+        S.h[sp] = take(nc);
+        S.Wd[sp] = take(nc);
+        S.W[sp] = take(nc);
+        S.G[sp] = take(nc);
+    }
+    double** c2[] = {&S.dudx, &S.dvdy, &S.tau_xx, &S.tau_yy, &S.Gxx, &S.Gyy,
+                     &S.dudy_c, &S.dvdx_c, &S.S, &S.div, &S.fsw};
+    for (double** f : c2) *f = take(nc);
+    for (int q = 0; q < 8; ++q) {
+        S.raw[q] = take(nc);
+        S.filt[q] = take(nc);
+    }
+    double** xfields[] = {&S.rho_xf, &S.u_xf, &S.Hx, &S.Kx, &S.txx_x, &S.v_x, &S.dTdx, &S.txy_x,
+                          &S.FEx, &S.mu_xf, &S.dudy_t, &S.dvdx_t};
+    for (double** f : xfields) *f = take(nxf);
+    for (int sp = 0; sp < NSP; ++sp) {
+        S.Yx[sp] = take(nxf);
+        S.Gx[sp] = take(nxf);
+        S.hx[sp] = take(nxf);
+        S.dXdx[sp] = take(nxf);
+        S.Fsx[sp] = take(nxf);
+    }
+    double** yfields[] = {&S.rho_yf, &S.v_yf, &S.Hy, &S.Ky, &S.tyy_y, &S.u_y, &S.dTdy, &S.txy_y,
+                          &S.FEy};
+    for (double** f : yfields) *f = take(nyf);
+    for (int sp = 0; sp < NSP; ++sp) {
+        S.Yy[sp] = take(nyf);
+        S.Gy[sp] = take(nyf);
+        S.hy[sp] = take(nyf);
+        S.dXdy[sp] = take(nyf);
+        S.Fsy[sp] = take(nyf);
+    }
+    double** cnf[] = {&S.dudy_cn, &S.dvdx_cn, &S.u_cn, &S.v_cn, &S.rho_cn, &S.mu_cn, &S.tau_xy,
+                      &S.Gxy};
+    for (double** f : cnf) *f = take(ncn);
+    S.DX = take(ns_);
+    S.DY = take(ns_);
+    S.SRC = take(ns_);
+    S.R = take(ns_);
+    G->Uref = take(ns_);
+    G->sigma = take(ns_);
+    G->xi_c = take(nx);
+    G->xi_f = take(nx + 1);
+    G->eta_c = take(ny);
+    G->eta_f = take(ny + 1);
+    if (cur - G->pool > pool_n) {
+        free_grid(G);
+        return fail(HYP_ERR_ARG, "internal: scratch pool too small");
+    }
+    err = cudaMalloc(&G->mask, ns_);
+    if (err == cudaSuccess) err = cudaMalloc(&G->status, sizeof(unsigned));
+    if (err != cudaSuccess) {
+        free_grid(G);
+        return cuda_fail(err, "cudaMalloc(grid)");
+    }
+    // operators
+    std::vector<double> opdata;
+    std::vector<LineOp> hops(NOPS);
+    hops[OX_ICF] = make_op(0, 0, nx, 0, opdata);
+    hops[OX_DCF] = make_op(1, 0, nx, 0, opdata);
+    hops[OX_IFC] = make_op(0, 1, nx, 0, opdata);
+    hops[OX_DFC] = make_op(1, 1, nx, 0, opdata);
+    hops[OY_ICF] = make_op(0, 0, ny, 0, opdata);
+    hops[OY_DCF] = make_op(1, 0, ny, 0, opdata);
+    hops[OY_IFC] = make_op(0, 1, ny, 0, opdata);
+    hops[OY_DFC] = make_op(1, 1, ny, 0, opdata);
+    hops[OY_ICFW] = make_op(0, 0, ny, 1, opdata);
+    hops[OY_DCFW] = make_op(1, 0, ny, 1, opdata);
+    err = cudaMalloc(&G->opdata, opdata.size() * sizeof(double));
+    if (err == cudaSuccess) err = cudaMalloc(&G->ops, NOPS * sizeof(LineOp));
+    if (err != cudaSuccess) {
+        free_grid(G);
+        return cuda_fail(err, "cudaMalloc(operators)");
+    }
+    for (auto& op : hops) {
+        op.lower = G->opdata + (size_t)op.lower;
+        op.cprime = G->opdata + (size_t)op.cprime;
+        op.minv = G->opdata + (size_t)op.minv;
+    }
+    // plans
+    PlanBuilder B;
+    B.G = G;
+    B.dops = G->ops;
+    const bool wall = cas->wall != 0;
+    const OpId y_icf_u = wall ? OY_ICFW : OY_ICF;
+    const OpId y_dcf_u = wall ? OY_DCFW : OY_DCF;
+    B.begin(PH_P3);
+    B.add(OX_DFC, S.u_xf, NXF, S.dudx, NC, G->xi_c);
+    B.add(OY_DFC, S.v_yf, NYF, S.dvdy, NC, G->eta_c);
+    B.add(y_dcf_u, S.u_xf, NXF, S.dudy_cn, NCN, G->eta_f, 1.0, 0.0);
+    B.add(OX_DCF, S.v_yf, NYF, S.dvdx_cn, NCN, G->xi_f);
+    B.add(y_icf_u, S.u_xf, NXF, S.u_cn, NCN, nullptr, 1.0, 0.0);
+    B.add(OX_ICF, S.v_yf, NYF, S.v_cn, NCN, nullptr);
+    B.add(OY_ICF, S.rho_xf, NXF, S.rho_cn, NCN, nullptr);
+    B.begin(PH_AD1);
+    B.add(OY_IFC, S.dudy_cn, NCN, S.dudy_t, NXF, nullptr);
+    B.add(OY_IFC, S.dvdx_cn, NCN, S.dvdx_t, NXF, nullptr);
+    B.begin(PH_AD2);
+    B.add(OX_IFC, S.dudy_t, NXF, S.dudy_c, NC, nullptr);
+    B.add(OX_IFC, S.dvdx_t, NXF, S.dvdx_c, NC, nullptr);
+    B.begin(PH_MU1);
+    B.add(OX_ICF, S.mu_e, NC, S.mu_xf, NXF, nullptr);
+    B.begin(PH_MU2);
+    B.add(OY_ICF, S.mu_xf, NXF, S.mu_cn, NCN, nullptr);
+    B.begin(PH_FACE);
+    for (int sp = 0; sp < NSP; ++sp) {
+        B.add(OX_ICF, S.Y[sp], NC, S.Yx[sp], NXF, nullptr);
+        B.add(OX_ICF, S.G[sp], NC, S.Gx[sp], NXF, nullptr);
+        B.add(OX_ICF, S.h[sp], NC, S.hx[sp], NXF, nullptr);
+        B.add(OX_DCF, S.X[sp], NC, S.dXdx[sp], NXF, G->xi_f);
+        B.add(OY_ICF, S.Y[sp], NC, S.Yy[sp], NYF, nullptr);
+        B.add(OY_ICF, S.G[sp], NC, S.Gy[sp], NYF, nullptr);
+        B.add(OY_ICF, S.h[sp], NC, S.hy[sp], NYF, nullptr);
+        B.add(OY_DCF, S.X[sp], NC, S.dXdy[sp], NYF, G->eta_f);
+    }
+    B.add(OX_ICF, S.H, NC, S.Hx, NXF, nullptr);
+    B.add(OX_ICF, S.K, NC, S.Kx, NXF, nullptr);
+    B.add(OX_ICF, S.tau_xx, NC, S.txx_x, NXF, nullptr);
+    B.add(OX_ICF, S.v_c, NC, S.v_x, NXF, nullptr);
+    B.add(OX_DCF, S.T, NC, S.dTdx, NXF, G->xi_f);
+    B.add(OY_IFC, S.tau_xy, NCN, S.txy_x, NXF, nullptr);
+    B.add(OY_ICF, S.H, NC, S.Hy, NYF, nullptr);
+    B.add(OY_ICF, S.K, NC, S.Ky, NYF, nullptr);
+    B.add(OY_ICF, S.tau_yy, NC, S.tyy_y, NYF, nullptr);
+    B.add(y_icf_u, S.u_c, NC, S.u_y, NYF, nullptr, 1.0, 0.0);
+    B.add(wall ? OY_DCFW : OY_DCF, S.T, NC, S.dTdy, NYF, G->eta_f, 1.0, G->Tw_nd);
+    B.add(OX_IFC, S.tau_xy, NCN, S.txy_y, NYF, nullptr);
+    B.begin(PH_DIV);
+    for (int sp = 1; sp < NSP; ++sp) {
+        B.add(OX_DFC, S.Fsx[sp], NXF, S.DX + G->off[sp], NC, G->xi_c, -1.0);
+        B.add(OY_DFC, S.Fsy[sp], NYF, S.DY + G->off[sp], NC, G->eta_c, -1.0);
+    }
+    B.add(OX_DFC, S.FEx, NXF, S.DX + G->off[NSP], NC, G->xi_c, -1.0);
+    B.add(OY_DFC, S.FEy, NYF, S.DY + G->off[NSP], NC, G->eta_c, -1.0);
+    B.add(OX_DCF, S.Gxx, NC, S.DX + G->off[NSP + 1], NXF, G->xi_f, -1.0);
+    B.add(OY_DFC, S.Gxy, NCN, S.DY + G->off[NSP + 1], NXF, G->eta_c, -1.0);
+    B.add(OX_DFC, S.Gxy, NCN, S.DX + G->off[NSP + 2], NYF, G->xi_c, -1.0);
+    B.add(OY_DCF, S.Gyy, NC, S.DY + G->off[NSP + 2], NYF, G->eta_f, -1.0);
+    // jobs reading the state: face momenta to centres, density to faces, continuity divergence
+    B.begin(PH_P1);
+    auto soff = [&](int f) { return (const double*)(size_t)G->off[f]; };
+    B.add(OX_IFC, soff(NSP + 1), NXF, S.ru_c, NC, nullptr, 1.0, 0.0, 1);
+    B.add(OY_IFC, soff(NSP + 2), NYF, S.rv_c, NC, nullptr, 1.0, 0.0, 1);
+    B.add(OX_ICF, soff(0), NC, S.rho_xf, NXF, nullptr, 1.0, 0.0, 1);
+    B.add(OY_ICF, soff(0), NC, S.rho_yf, NYF, nullptr, 1.0, 0.0, 1);
+    B.add(OX_DFC, soff(NSP + 1), NXF, S.DX + G->off[0], NC, G->xi_c, -1.0, 0.0, 1);
+    B.add(OY_DFC, soff(NSP + 2), NYF, S.DY + G->off[0], NC, G->eta_c, -1.0, 0.0, 1);
+    memcpy(G->ph_start, B.ph_start, sizeof(B.ph_start));
+    memcpy(G->ph_count, B.ph_count, sizeof(B.ph_count));
+    memcpy(G->ph_lines, B.ph_lines, sizeof(B.ph_lines));
+    err = cudaMalloc(&G->jobs, B.jobs.size() * sizeof(LineJob));
+    if (err != cudaSuccess) {
+        free_grid(G);
+        return cuda_fail(err, "cudaMalloc(jobs)");
+    }
+    // uploads
+#define UP(dst, src, bytes) HYP_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s))
+    UP(G->opdata, opdata.data(), opdata.size() * sizeof(double));
+    UP(G->ops, hops.data(), NOPS * sizeof(LineOp));
+    UP(G->jobs, B.jobs.data(), B.jobs.size() * sizeof(LineJob));
+    UP(G->xi_c, xi_c.data(), nx * sizeof(double));
+    UP(G->xi_f, xi_f.data(), (nx + 1) * sizeof(double));
+    UP(G->eta_c, eta_c.data(), ny * sizeof(double));
+    UP(G->eta_f, eta_f.data(), (ny + 1) * sizeof(double));
+    UP(G->Uref, Uref.data(), ns_ * sizeof(double));
+    UP(G->sigma, sig.data(), ns_ * sizeof(double));
+    UP(G->mask, mask.data(), ns_);
+    UP(U, U0.data(), ns_ * sizeof(double));
+#undef UP
+    HYP_CUDA(cudaMemsetAsync(dQ, 0, ns_ * sizeof(double), s));
+    HYP_CUDA(cudaMemsetAsync(G->s.SRC, 0, ns_ * sizeof(double), s));
+    HYP_CUDA(cudaMemsetAsync(G->status, 0, sizeof(unsigned), s));
+    k_fill<<<blocks_for(nc, 256), 256, 0, s>>>(G->s.Tcache, nc, 1000.0);
+    HYP_CUDA(cudaGetLastError());
+    // host vectors must outlive the async copies
+    HYP_CUDA(cudaStreamSynchronize(s));
+    hyp_state* st = new hyp_state();
+    st->grid = G;
+    st->U = U;
+    st->dQ = dQ;
+    *out = st;
+    return HYP_OK;
+}
+
+extern "C" const hyp_grid* hyp_state_grid(const hyp_state* st) { return st ? st->grid : nullptr; }
+
+extern "C" void hyp_state_free(hyp_state* st) {
+    if (!st) return;
+    free_grid(st->grid);
+    delete st;
+}
+
+extern "C" int hyp_grid_reference(const hyp_grid* G, double* Uref, double* sigma) {
+    if (!G) return fail(HYP_ERR_ARG, "null grid");
+    HYP_CUDA(cudaStreamSynchronize(G->stream));
+    if (Uref) HYP_CUDA(cudaMemcpy(Uref, G->Uref, G->nstate * sizeof(double), cudaMemcpyDeviceToHost));
+    if (sigma) HYP_CUDA(cudaMemcpy(sigma, G->sigma, G->nstate * sizeof(double), cudaMemcpyDeviceToHost));
+    return HYP_OK;
+}
+
+extern "C" int hyp_grid_status(const hyp_grid* G, uint32_t* flags, int clear) {
+    if (!G || !flags) return fail(HYP_ERR_ARG, "null argument");
+    HYP_CUDA(cudaStreamSynchronize(G->stream));
+    unsigned v = 0;
+    HYP_CUDA(cudaMemcpy(&v, G->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    *flags = v;
+    if (clear) HYP_CUDA(cudaMemset(G->status, 0, sizeof(unsigned)));
+    return HYP_OK;
+}
+
+// The whole right-hand side; with rk != 0 the assemble step performs the stage update instead
+// of writing dUdt.
+static int run_rhs(const hyp_gas* gas, hyp_grid* G, const double* U, double* dUdt, int rk,
+                   double A, double Bc, double dt, double* Urk, double* dQ, cudaStream_t s) {
+    const GasDev& g = gas->dev;
+    const GridView v = G->view();
+    Scratch& S = G->s;
+    const Dims& d = G->d;
+    const long long nc = d.size(NC);
+    HYP_CUDA(launch_lines(G->jobs + G->ph_start[PH_P1], G->ph_count[PH_P1], G->ph_lines[PH_P1], U, s));
+    k_face_vel<<<blocks_for(d.size(NXF) + d.size(NYF), 256), 256, 0, s>>>(v, U, S);
+    k_closure<<<blocks_for(nc, 128), 128, 0, s>>>(g, v, U, S);
+    HYP_CUDA(cudaGetLastError());
+    HYP_CUDA(launch_lines(G->jobs + G->ph_start[PH_P3], G->ph_count[PH_P3], G->ph_lines[PH_P3], U, s));
+    if (v.ad) {
+        HYP_CUDA(launch_lines(G->jobs + G->ph_start[PH_AD1], 2, G->ph_lines[PH_AD1], U, s));
+        HYP_CUDA(launch_lines(G->jobs + G->ph_start[PH_AD2], 2, G->ph_lines[PH_AD2], U, s));
+        k_ad_prep<<<blocks_for(nc, 256), 256, 0, s>>>(v, S);
+        k_ad_raw<<<blocks_for(nc, 256), 256, 0, s>>>(g, v, U, S);
+        dim3 gg(blocks_for(nc, 256), 8);
+        k_gauss<<<gg, 256, 0, s>>>(v, S, 0);
+        k_gauss<<<gg, 256, 0, s>>>(v, S, 1);
+        k_ad_combine<<<blocks_for(nc, 256), 256, 0, s>>>(v, S);
+        HYP_CUDA(cudaGetLastError());
+    }
+    k_stress_c<<<blocks_for(nc, 256), 256, 0, s>>>(v, S);
+    HYP_CUDA(launch_lines(G->jobs + G->ph_start[PH_MU1], 1, G->ph_lines[PH_MU1], U, s));
+    HYP_CUDA(launch_lines(G->jobs + G->ph_start[PH_MU2], 1, G->ph_lines[PH_MU2], U, s));
+    k_stress_cn<<<blocks_for(d.size(NCN), 256), 256, 0, s>>>(v, S);
+    HYP_CUDA(launch_lines(G->jobs + G->ph_start[PH_FACE], G->ph_count[PH_FACE],
+                          G->ph_lines[PH_FACE], U, s));
+    k_flux<<<blocks_for(d.size(NXF), 128), 128, 0, s>>>(v, U, S, 0);
+    k_flux<<<blocks_for(d.size(NYF), 128), 128, 0, s>>>(v, U, S, 1);
+    HYP_CUDA(launch_lines(G->jobs + G->ph_start[PH_DIV], G->ph_count[PH_DIV], G->ph_lines[PH_DIV], U, s));
+    k_assemble<<<blocks_for(G->nstate, 256), 256, 0, s>>>(G->nstate, S.DX, S.DY, S.SRC, G->sigma,
+                                                           G->Uref, G->mask, rk ? Urk : (double*)U,
+                                                           dUdt, dQ, rk, A, Bc, dt);
+    HYP_CUDA(cudaGetLastError());
+    return HYP_OK;
+}
+
+extern "C" int hyp_rhs(const hyp_gas* gas, const hyp_grid* grid, const double* U, double* dUdt,
+                       int precision, void* stream) {
+    if (!gas || !grid || !U || !dUdt) return fail(HYP_ERR_ARG, "null argument");
+    if (precision != HYP_FP64) return fail(HYP_ERR_ARG, "only HYP_FP64 is available");
+    if (U == dUdt) return fail(HYP_ERR_ARG, "U and dUdt must not alias");
+    hyp_grid* G = const_cast<hyp_grid*>(grid);
+    return run_rhs(gas, G, U, dUdt, 0, 0.0, 0.0, 0.0, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+extern "C" int hyp_rk_stage(hyp_state* st, int stage, double dt, int precision, void* stream) {
+    if (!st) return fail(HYP_ERR_ARG, "null state");
+    if (stage < 0 || stage > 2) return fail(HYP_ERR_ARG, "stage must be 0, 1 or 2");
+    if (precision != HYP_FP64) return fail(HYP_ERR_ARG, "only HYP_FP64 is available");
+    hyp_grid* G = st->grid;
+    // the gas handle is not stored in the state: the grid keeps a copy of the device tables
+    hyp_gas tmp;
+    tmp.dev = G->gas;
+    return run_rhs(&tmp, G, st->U, nullptr, 1, RK_A[stage], RK_B[stage], dt, st->U, st->dQ,
+                   (cudaStream_t)stream);
+}
