@@ -1,0 +1,324 @@
+#!/usr/bin/env python
+"""Benchmark: FP64 RK3 time steps of the reacting Navier-Stokes right-hand side on one GB300.
+
+Workload: the oblique-shock / boundary-layer interaction on 2048 x 256 cells (five-species air,
+17 reactions, artificial diffusivity on; paper_2210_05547_gb300.inputs.sbli_case). One step is a
+full two-register RK3 step: three right-hand sides and three stage updates, every kernel of the
+hot path. Metric: Mpts*RHS/s = cells x right-hand sides per second over all GPUs.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 the script is launched by torch.distributed.run, one process per GPU; each rank runs
+an independent replica (seed = rank), no collective on the data path ("weak" scaling). Inputs
+are resident in HBM for `value`; `e2e` repeats the measurement through the public API with the
+state copied from pinned host memory and back every step. The L2 cache is flushed between timed
+steps by writing a 256 MiB buffer outside the timed events.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import resource
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpts*RHS/s FP64"
+UNIT = "Mpts*RHS/s"
+STAGES = 3
+L2_FLUSH_BYTES = 256 << 20
+# FP64 operations per cell-centre point executed by k_closure (DADD + DMUL + 2 DFMA), from the
+# ncu instruction counts recorded in profiles/k_closure_sbli.md; 0 until measured.
+CLOSURE_FP64_FLOP_PER_POINT = 0.0
+# DRAM bytes (read + write) per k_closure launch at 2048 x 256 from the same capture; None until
+# measured on the current kernel.
+CLOSURE_DRAM_BYTES = None
+# GB300 FP64 peak derived from the unit counts: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--nx", type=int, default=2048, help="cells in x (profiling of small cases)")
+    ap.add_argument("--ny", type=int, default=256, help="cells in y (profiling of small cases)")
+    return ap.parse_args()
+
+
+def workload_config(cfg, world):
+    return {"workload": f"sbli_{cfg['nx']}x{cfg['ny']}_cneq5_fp64_rk3", "nx": cfg["nx"],
+            "ny": cfg["ny"], "points": cfg["nx"] * cfg["ny"], "species": 5, "reactions": 17,
+            "gas": cfg["kind"], "artificial_diffusivity": bool(cfg["artificial_diffusivity"]),
+            "mach": round(cfg["mach"], 4), "shock_deflection_deg": round(cfg["shock_deflection_deg"], 4),
+            "rhs_per_step": STAGES, "l2": "flushed between timed steps (256 MiB write)",
+            "replicas": world, "parallelism": "replicas" if world > 1 else "single"}
+
+
+# ------------------------------------------------------------------------------------------------
+# clocks sampled with nvidia-smi during the timed region
+# ------------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.proc = None
+        self.lines = []
+        try:
+            import torch
+            p = torch.cuda.get_device_properties(device_index)
+            target = f"{p.pci_domain_id:08X}:{p.pci_bus_id:02X}:{p.pci_device_id:02X}.0"
+        except Exception:
+            target = str(device_index)
+        self.target = target
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.target, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands, on a bounded sample of the same case
+# ------------------------------------------------------------------------------------------------
+
+def oracle_step_rate(nx, ny, steps=1):
+    """Run `steps` oracle RK3 steps on the SBLI case at nx x ny; return (Mpts*RHS/s, cores, s)."""
+    from oracle import flow as F
+    from oracle import gas as G
+    from paper_2210_05547_gb300 import inputs as I
+    from paper_2210_05547_gb300.abi import TABLE_AIR5
+    cfg = I.sbli_case(nx, ny)
+    tab = G.load_table(TABLE_AIR5)
+    n = sum(a * b for _, (a, b) in F.state_layout(5, nx, ny))
+    case = F.make_case(cfg, tab, I.state_noise(n, cfg["seed"]))
+    U, dQ = case.U0.copy(), case.U0 * 0.0
+    r0 = resource.getrusage(resource.RUSAGE_SELF)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        for k in range(STAGES):
+            U, dQ, _ = F.rk_stage(case, U, dQ, k, cfg["dt"])
+    wall = time.perf_counter() - t0
+    r1 = resource.getrusage(resource.RUSAGE_SELF)
+    cpu = (r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime)
+    cores = max(1, round(cpu / wall))
+    return nx * ny * STAGES * steps / wall / 1e6, cores, wall
+
+
+# ------------------------------------------------------------------------------------------------
+# arms
+# ------------------------------------------------------------------------------------------------
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return 0
+    from paper_2210_05547_gb300 import inputs as I
+    cfg = I.sbli_case()
+    nx, ny = 160, 64          # bounded sample: one RK3 step takes a few seconds on one core
+    for _ in range(args.warmup):
+        oracle_step_rate(nx, ny)
+    rates, walls, cores = [], [], 1
+    for _ in range(args.steps):
+        r, cores, w = oracle_step_rate(nx, ny)
+        rates.append(r)
+        walls.append(w)
+    total = sum(walls)
+    value = nx * ny * STAGES * args.steps / total / 1e6
+    sample = (f"oracle RK3 steps on the same shock/boundary-layer case at {nx}x{ny} cells "
+              f"(full workload 2048x256), one step per timed iteration")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(cfg, 1),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def ours_arm(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_2210_05547_gb300 import abi as A
+    from paper_2210_05547_gb300 import inputs as I
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    cfg = I.sbli_case(args.nx, args.ny, seed=rank)
+    gas = A.gas_model_load(cfg)
+    n = A.state_size(gas, cfg)
+    U = torch.empty(n, dtype=torch.float64, device=dev)
+    dQ = torch.empty_like(U)
+    st = A.state_init(gas, cfg, U, dQ, I.state_noise(n, cfg["seed"]))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    dt = cfg["dt"]
+    points = cfg["nx"] * cfg["ny"]
+
+    def step():
+        for k in range(STAGES):
+            A.rk_stage(st, k, dt)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---------------- device-timed region ----------------
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    A.grid_profile(st.grid, True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier()
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        ev[i][0].record()
+        step()
+        ev[i][1].record()
+        flush.fill_(float(i))
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    A.grid_profile(st.grid, False)
+    prof = A.grid_profile_read(st.grid)
+    clk = clocks.stop()
+    dev_ms = sum(a.elapsed_time(b) for a, b in ev)
+    t = torch.tensor([dev_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+    value = world * points * STAGES * args.steps / (max_ms / 1e3) / 1e6
+    launches = sum(c for _, c in prof.values())
+    status = A.grid_status(st.grid)
+
+    # ---------------- end to end through the public API, host buffers ----------------
+    e2e = None
+    if not args.no_e2e:
+        Uh = torch.empty(n, dtype=torch.float64, pin_memory=True)
+        Uh.copy_(U)
+        torch.cuda.synchronize()
+        ee = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        barrier()
+        for i in range(args.steps):
+            ee[i][0].record()
+            U.copy_(Uh, non_blocking=True)
+            step()
+            Uh.copy_(U, non_blocking=True)
+            ee[i][1].record()
+            flush.fill_(float(i))
+        barrier()
+        e_ms = sum(a.elapsed_time(b) for a, b in ee)
+        te = torch.tensor([e_ms], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * points * STAGES * args.steps / (float(te.item()) / 1e3) / 1e6,
+               "unit": UNIT, "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8}
+
+    # ---------------- roofline of the dominant kernel ----------------
+    name, (kms, kcount) = max(prof.items(), key=lambda kv: kv[1][0])
+    avg_s = kms / max(kcount, 1) / 1e3
+    roof = {"kernel": name, "launches": kcount, "avg_launch_ms": avg_s * 1e3,
+            "share_of_step": kms / max(dev_ms, 1e-30)}
+    if name == "k_closure" and CLOSURE_FP64_FLOP_PER_POINT > 0:
+        ach = CLOSURE_FP64_FLOP_PER_POINT * points / avg_s / 1e12
+        roof.update(bound="alu", achieved=ach, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
+                    frac=ach / FP64_PEAK_TFLOPS,
+                    traffic=CLOSURE_DRAM_BYTES, peak_source="derived: 152 SMs x 2 DFMA/clk x 2.07 GHz")
+    else:
+        roof.update(bound="alu", achieved=None, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s", frac=None,
+                    traffic=None, note="per-point FP64 count not yet measured for this kernel")
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        r, cores, w = oracle_step_rate(320, 128)
+        cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"one oracle RK3 step (3 RHS) of the same case at 320x128 cells, {w:.1f} s"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": workload_config(cfg, world), "e2e": e2e,
+                "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+                "wall_s_timed": t_wall, "status_flags": status,
+                "kernels": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1]}}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != args.gpus and "RANK" in os.environ:
+        world = int(os.environ["WORLD_SIZE"])
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+    return ours_arm(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

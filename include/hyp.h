@@ -170,6 +170,17 @@ int hyp_thermo_eval(const hyp_gas* gas, int64_t n, const double* rho, const doub
 int hyp_thermo_energy(const hyp_gas* gas, int64_t n, const double* T, const double* Y, double* e,
                       void* stream);
 
+/* Event profile of the launches that hyp_rhs / hyp_rk_stage make on a grid (diagnostics; no
+ * counterpart in the paper). hyp_grid_profile(grid, 1) clears the totals and starts recording a
+ * pair of CUDA events around every launch on the caller's stream; (grid, 0) stops. Reading
+ * synchronises on the recorded events and returns, for the first n kernel ids, the summed
+ * device time in ms and the launch count (HOST arrays, nullable). Kernel ids run from 0 to
+ * hyp_profile_count() - 1; hyp_profile_name(id) is a static string. */
+int hyp_grid_profile(const hyp_grid* grid, int enable);
+int hyp_grid_profile_read(const hyp_grid* grid, int n, double* ms, int64_t* launches);
+int hyp_profile_count(void);
+const char* hyp_profile_name(int id);
+
 /* Message of the last failed call on this thread ("" if none). Owned by the library. */
 const char* hyp_last_error(void);
 

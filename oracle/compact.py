@@ -145,7 +145,8 @@ def apply(f, axis, kind, direction, wall_value=None):
     A, B = operator_matrices(kind, direction, n, wall)
     x = fm.reshape(n_in, -1)
     if wall:
-        x = np.vstack([np.full((1, x.shape[1]), float(wall_value)), x])
+        wv = np.broadcast_to(np.asarray(wall_value, dtype=np.float64).reshape(1, -1), (1, x.shape[1]))
+        x = np.vstack([wv, x])
     rhs = B @ x
     y = scipy.linalg.solve_banded((1, 1), A, rhs)
     out = y.reshape((A.shape[1],) + shape[1:])

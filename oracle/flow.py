@@ -311,6 +311,10 @@ def make_case(cfg, tab, noise=None) -> Case:
     T, p, u, v, Y = _primitive_profile(cfg, sc, tab, kind, Xv, Yv)
     rho_v, _, _ = _conserved_from_primitive(tab, kind, sc, T, p, u, v, Y)
     ref["rhov"] = rho_v * v
+    T, p, u, v, Y = _primitive_profile(cfg, sc, tab, kind, Xu[:, :1], Yu[:, :1])
+    rho_in, rhoY_in, rhoE_in = _conserved_from_primitive(tab, kind, sc, T, p, u, v, Y)
+    p_nd = p / (sc.rho * sc.a ** 2)
+    inflow = dict(rho=rho_in[:, 0], Y=Y[:, :, 0], H=((rhoE_in + p_nd) / rho_in)[:, 0])
     sigma = dict(c=sponge(cfg, g, Xc, Yc), xf=sponge(cfg, g, Xu, Yu), yf=sponge(cfg, g, Xv, Yv))
     U_ref = pack(ns, nx, ny, ref)
     U0 = U_ref.copy()
@@ -322,7 +326,9 @@ def make_case(cfg, tab, noise=None) -> Case:
         f["rhou"][:, nx] = r["rhou"][:, nx]
         f["rhov"][0, :] = r["rhov"][0, :]
         f["rhov"][ny, :] = r["rhov"][ny, :]
-    return Case(cfg=cfg, tab=tab, kind=kind, sc=sc, grid=g, U_ref=U_ref, sigma=sigma, U0=U0)
+    case = Case(cfg=cfg, tab=tab, kind=kind, sc=sc, grid=g, U_ref=U_ref, sigma=sigma, U0=U0)
+    case.inflow = inflow
+    return case
 
 
 # ---------------------------------------------------------------------------------------------
@@ -355,7 +361,7 @@ def closure_nd(case: Case, rho, e, Y):
                    mu=th["mu"] / sc.mu, k=th["k"] / sc.k,
                    D=(th["D"] * sc.rho / sc.mu) if diffusive else np.zeros_like(Y1),
                    X=th["X"], W=(r1 * M / Mmix) if diffusive else np.zeros_like(Y1),
-                   a=th["a"] / sc.a)
+                   a=th["a"] / sc.a, cv=th["cv"])
     res = {}
     for key, val in out.items():
         res[key] = val.reshape((ns,) + shape) if val.ndim == 2 else val.reshape(shape)
@@ -425,7 +431,8 @@ def rhs(case: Case, U, return_parts=False):
     H = (rhoE + p) / rho
 
     # (B) face velocities
-    rho_xf = C.icf(rho, 1)
+    inf = case.inflow if cfg.get("_inflow_dirichlet") else None
+    rho_xf = C.icf(rho, 1, None if inf is None else inf["rho"])
     u_xf = rhou / rho_xf
     rho_yf = C.icf(rho, 0)
     v_yf = rhov / rho_yf
@@ -475,11 +482,11 @@ def rhs(case: Case, U, return_parts=False):
     tau_xy = mu_cn * (dudy_cn + dvdx_cn)
 
     # (G) x-fluxes at x-faces
-    Yx = np.stack([C.icf(Y[s], 1) for s in range(ns)])
+    Yx = np.stack([C.icf(Y[s], 1, None if inf is None else inf["Y"][s]) for s in range(ns)])
     Gx = np.stack([C.icf(Gd[s], 1) for s in range(ns)])
     hx = np.stack([C.icf(th["h_s"][s], 1) for s in range(ns)])
     dXdx = np.stack([xi_f * C.dcf(th["X"][s], 1) for s in range(ns)])
-    Hx = C.icf(H, 1)
+    Hx = C.icf(H, 1, None if inf is None else inf["H"])
     Kx = C.icf(K, 1)
     dTdx = xi_f * C.dcf(T, 1)
     txx_x = C.icf(tau_xx, 1)
@@ -511,9 +518,12 @@ def rhs(case: Case, U, return_parts=False):
     qy = -Ky * dTdy + np.sum(hy * Jy, axis=0)
     FEy = rhov * Hy + qy - (txy_y * u_y + tyy_y * v_yf)
 
-    # (I) momentum fluxes
-    Gxx = ru_c * u_c + p - tau_xx
-    Gyy = rv_c * v_c + p - tau_yy
+    # (I) momentum fluxes. The normal flux rho u u is formed on the faces from the face momentum
+    # and the face velocity, then interpolated to the centres: with the centre product
+    # (I_fc m)^2 / rho the linearised scheme is unstable for supersonic flow even on a periodic
+    # grid, because I_cf I_fc differs from 1 at grid scale while the energy flux sees m directly.
+    Gxx = C.ifc(rhou * u_xf, 1) + p - tau_xx
+    Gyy = C.ifc(rhov * v_yf, 0) + p - tau_yy
     rho_cn = C.icf(rho_xf, 0)
     Gxy = rho_cn * u_cn * v_cn - tau_xy
 
@@ -530,14 +540,63 @@ def rhs(case: Case, U, return_parts=False):
         sig = case.sigma["xf" if name == "rhou" else "yf" if name == "rhov" else "c"]
         R[name] = R[name] - sig * (q[name] - ref[name])
     R["rhou"][:, 0] = 0.0
-    R["rhou"][:, nx] = 0.0
-    R["rhov"][0, :] = 0.0
-    R["rhov"][ny, :] = 0.0
+    for c in range(cfg.get("_fix_cols", 0)):
+        for name in R:
+            if name == "rhou":
+                R[name][:, c + 1] = 0.0
+            else:
+                R[name][:, c] = 0.0
+    if not cfg.get("_free_outflow"):
+        R["rhou"][:, nx] = 0.0
+    if wall or not cfg.get("_free_bottom"):
+        R["rhov"][0, :] = 0.0
+    if not cfg.get("_free_top"):
+        R["rhov"][ny, :] = 0.0
     out = pack(ns, nx, ny, R)
     if return_parts:
+        # largest |flux| x |metric| entering each field's divergence (for rounding-floor bounds)
+        xm, ym = g.xi_f.max(), g.eta_f.max()
+        gross = {"rho": max(np.abs(rhou).max() * xm, np.abs(rhov).max() * ym),
+                 "rhoE": max(np.abs(FEx).max() * xm, np.abs(FEy).max() * ym),
+                 "rhou": max(np.abs(Gxx).max() * xm, np.abs(Gxy).max() * ym),
+                 "rhov": max(np.abs(Gxy).max() * xm, np.abs(Gyy).max() * ym)}
+        for s in range(1, ns):
+            gross[f"rs{s}"] = max(np.abs(Fsx[s]).max() * xm, np.abs(Fsy[s]).max() * ym)
         return out, dict(T=T, p=p, th=th, mu_st=mu_st, beta_st=beta_st, kap_st=kap_st, D_st=D_st,
-                         tau_xy=tau_xy, dTdy=dTdy)
+                         tau_xy=tau_xy, dTdy=dTdy, gross=gross, E=rhoE / rho, e=e,
+                         ke=0.5 * (u_c * u_c + v_c * v_c))
     return out
+
+
+# Parity criterion for a computed right-hand side against this oracle (test infrastructure).
+# One FP64 evaluation of -metric * D(F) is off by up to about 8 eps ||D||_inf max|F| max|metric|,
+# so two that round in different orders differ by up to twice that; ||D||_inf <= 6 bounds the compact derivative with its
+# closures (row sums of |B| <= 4.3, ||A^-1||_inf <= 1/(1 - 2 alpha) = 1.41). The stated
+# 1e-12 normwise tolerance applies on top of that floor.
+PARITY_RTOL = 1.0e-12
+PARITY_FLOOR = 16.0 * 2.0 ** -53 * 6.0
+
+
+# The species sources w_s carry exp(-T_a/T): a relative temperature difference dT/T between two
+# converged inversions changes them by (T_a/T) dT/T. Two FP64 evaluations of e = E - |u|^2/2 and
+# of the Newton residual differ by a few eps (|E| + |e| + |u|^2/2) a_inf^2, which moves T by that
+# over c_v; the tolerance adds max_i |w_s,i| (T_a,max / T_i) (dT/T)_i with that estimate (times 8).
+def parity_tolerance(case: Case, U):
+    """Per-field absolute tolerance: 1e-12 max|R_f| + 8 eps ||D|| max|F_f| max|metric|, plus for
+    species the temperature conditioning of the Arrhenius sources."""
+    R, parts = rhs(case, U, return_parts=True)
+    g = case.grid
+    f = unpack(case.tab.ns, g.nx, g.ny, R)
+    tol = {k: PARITY_RTOL * np.abs(v).max() + PARITY_FLOOR * parts["gross"][k]
+           for k, v in f.items()}
+    if case.kind == KIND_CNEQ and case.tab.reactions:
+        ta_max = max(r.Ta for r in case.tab.reactions)
+        T_si = parts["T"] * case.sc.T_ref
+        scale = np.abs(parts["E"]) + np.abs(parts["e"]) + parts["ke"]
+        dT_rel = 8.0 * 2.0 ** -53 * scale * case.sc.a ** 2 / (parts["th"]["cv"] * T_si)
+        for s in range(1, case.tab.ns):
+            tol[f"rs{s}"] += np.max(np.abs(parts["th"]["wdot"][s]) * ta_max / T_si * dT_rel)
+    return tol, R
 
 
 def rk_stage(case: Case, U, dQ, stage, dt):

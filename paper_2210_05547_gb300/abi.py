@@ -69,6 +69,10 @@ EXPORTS = {
     "hyp_rk_stage": (_I, [_P, _I, _D, _I, _P]),
     "hyp_thermo_eval": (_I, [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I, _P]),
     "hyp_thermo_energy": (_I, [_P, _I64, _P, _P, _P, _P]),
+    "hyp_grid_profile": (_I, [_P, _I]),
+    "hyp_grid_profile_read": (_I, [_P, _I, _P, _P]),
+    "hyp_profile_count": (_I, []),
+    "hyp_profile_name": (ctypes.c_char_p, [_I]),
     "hyp_last_error": (ctypes.c_char_p, []),
 }
 
@@ -264,3 +268,23 @@ def thermo_energy(gas, T, Y, e, stream=None):
     _check(lib().hyp_thermo_energy(gas.handle, n, _dptr(T, n, torch.float64),
                                    _dptr(Y, gas.ns * n, torch.float64), _dptr(e, n, torch.float64),
                                    _stream(stream)))
+
+
+def grid_profile(grid, enable):
+    """hyp_grid_profile: start (clears totals) or stop the per-launch event profile of a grid."""
+    _check(lib().hyp_grid_profile(grid, int(bool(enable))))
+
+
+def grid_profile_read(grid):
+    """hyp_grid_profile_read: {kernel name: (total ms, launches)} since the profile was started."""
+    n = lib().hyp_profile_count()
+    ms = np.zeros(n)
+    cnt = np.zeros(n, dtype=np.int64)
+    _check(lib().hyp_grid_profile_read(grid, n, ms.ctypes.data_as(ctypes.c_void_p),
+                                       cnt.ctypes.data_as(ctypes.c_void_p)))
+    out = {}
+    for k in range(n):
+        name = lib().hyp_profile_name(k).decode()
+        t, c = out.get(name, (0.0, 0))
+        out[name] = (t + float(ms[k]), c + int(cnt[k]))
+    return out

@@ -92,16 +92,16 @@ struct LineJob {
     const double* in;            // input field, or an element offset into the state when in_state
     int in_state;
     double* out;
-    double* tmp;                 // forward-sweep storage (out if null and not accumulating)
+    double* tmp;                 // forward-sweep storage, same layout as out, distinct from it
     long long in_ls, in_es, out_ls, out_es;
     int nlines;
-    int accumulate;
+    int nseg;                    // segments per line (power of two dividing the block size)
     double wall_value;
     double scale;
     const double* metric;        // per output element along the line, nullable
 };
 
-cudaError_t launch_lines(const LineJob* d_jobs, int njobs, int max_lines, const double* U,
+cudaError_t launch_lines(const LineJob* d_jobs, int njobs, int max_blocks, const double* U,
                          cudaStream_t s);
 
 }  // namespace hyp

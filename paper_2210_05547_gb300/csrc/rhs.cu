@@ -40,14 +40,14 @@ struct Scratch {
     // cell centres
     double *ru_c, *rv_c, *T, *p, *H, *u_c, *v_c, *e, *a, *mu_e, *K, *beta, *Tcache;
     double *Y[NSP], *X[NSP], *h[NSP], *Wd[NSP], *W[NSP], *G[NSP];
-    double *dudx, *dvdy, *tau_xx, *tau_yy, *Gxx, *Gyy;
+    double *dudx, *dvdy, *tau_xx, *tau_yy, *Gxx, *Gyy, *mux_c, *mvy_c;
     double *dudy_c, *dvdx_c, *S, *div, *fsw, *raw[8], *filt[8];
     // x-faces
     double *rho_xf, *u_xf, *Yx[NSP], *Gx[NSP], *hx[NSP], *Hx, *Kx, *txx_x, *v_x, *dTdx,
-        *dXdx[NSP], *txy_x, *Fsx[NSP], *FEx, *mu_xf, *dudy_t, *dvdx_t;
+        *dXdx[NSP], *txy_x, *Fsx[NSP], *FEx, *mu_xf, *dudy_t, *dvdx_t, *mux_f;
     // y-faces
     double *rho_yf, *v_yf, *Yy[NSP], *Gy[NSP], *hy[NSP], *Hy, *Ky, *tyy_y, *u_y, *dTdy,
-        *dXdy[NSP], *txy_y, *Fsy[NSP], *FEy;
+        *dXdy[NSP], *txy_y, *Fsy[NSP], *FEy, *mvy_f;
     // corners
     double *dudy_cn, *dvdx_cn, *u_cn, *v_cn, *rho_cn, *mu_cn, *tau_xy, *Gxy;
     // state-sized
@@ -68,6 +68,26 @@ enum Phase {
     PH_P1, PH_P3, PH_AD1, PH_AD2, PH_MU1, PH_MU2, PH_FACE, PH_DIV, PH_COUNT
 };
 
+// Launches of one right-hand side, as reported by the optional event profile.
+enum KernelId {
+    KID_LINES_STATE, KID_FACE_VEL, KID_CLOSURE, KID_LINES_VELGRAD, KID_LINES_AD, KID_AD_PREP,
+    KID_AD_RAW, KID_AD_GAUSS, KID_AD_COMBINE, KID_STRESS_C, KID_LINES_MU, KID_STRESS_CN,
+    KID_LINES_FACE, KID_FLUX, KID_LINES_DIV, KID_ASSEMBLE, KID_COUNT
+};
+const char* const KERNEL_NAMES[KID_COUNT] = {
+    "k_lines:state", "k_face_vel", "k_closure", "k_lines:velgrad", "k_lines:ad", "k_ad_prep",
+    "k_ad_raw", "k_gauss", "k_ad_combine", "k_stress_c", "k_lines:mu", "k_stress_cn",
+    "k_lines:face", "k_flux", "k_lines:div", "k_assemble"};
+
+struct EventProfile {
+    bool on = false;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> id;
+    size_t used = 0;
+    double ms[KID_COUNT] = {};
+    long long count[KID_COUNT] = {};
+};
+
 }  // namespace
 
 struct hyp_grid {
@@ -85,9 +105,11 @@ struct hyp_grid {
     LineOp* ops;
     double* opdata;
     LineJob* jobs;
-    int ph_start[PH_COUNT], ph_count[PH_COUNT], ph_lines[PH_COUNT];
+    int ph_start[PH_COUNT], ph_count[PH_COUNT], ph_blocks[PH_COUNT];
+    double* linetmp;
     cudaStream_t stream;
     double Tw_nd;
+    EventProfile* prof;
     GridView view() const {
         GridView v;
         v.nx = d.nx;
@@ -442,10 +464,17 @@ __global__ void __launch_bounds__(128) k_closure(GasDev g, GridView v, const dou
 __global__ void k_face_vel(GridView v, const double* __restrict__ U, Scratch s) {
     const int nxf = v.ny * (v.nx + 1), nyf = (v.ny + 1) * v.nx;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nxf + nyf; i += gridDim.x * blockDim.x) {
-        if (i < nxf) s.u_xf[i] = U[v.off[NSP + 1] + i] / s.rho_xf[i];
-        else {
+        if (i < nxf) {
+            const double m = U[v.off[NSP + 1] + i];
+            const double u = m / s.rho_xf[i];
+            s.u_xf[i] = u;
+            s.mux_f[i] = m * u;
+        } else {
             const int j = i - nxf;
-            s.v_yf[j] = U[v.off[NSP + 2] + j] / s.rho_yf[j];
+            const double m = U[v.off[NSP + 2] + j];
+            const double vv = m / s.rho_yf[j];
+            s.v_yf[j] = vv;
+            s.mvy_f[j] = m * vv;
         }
     }
 }
@@ -533,7 +562,7 @@ __global__ void k_ad_combine(GridView v, Scratch s) {
     }
 }
 
-// (F, I) normal stresses and momentum fluxes at centres
+// (F, I) normal stresses and momentum fluxes at centres (Eqs. 5, 6, 9)
 __global__ void k_stress_c(GridView v, Scratch s) {
     const int n = v.nx * v.ny;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -544,8 +573,9 @@ __global__ void k_stress_c(GridView v, Scratch s) {
         const double tyy = mu * (2.0 * vy - 2.0 / 3.0 * dv) + b * dv;
         s.tau_xx[i] = txx;
         s.tau_yy[i] = tyy;
-        s.Gxx[i] = s.ru_c[i] * s.u_c[i] + s.p[i] - txx;
-        s.Gyy[i] = s.rv_c[i] * s.v_c[i] + s.p[i] - tyy;
+        // normal momentum fluxes: rho u u formed on the faces, interpolated to the centres
+        s.Gxx[i] = s.mux_c[i] + s.p[i] - txx;
+        s.Gyy[i] = s.mvy_c[i] + s.p[i] - tyy;
     }
 }
 
@@ -641,18 +671,19 @@ int blocks_for(long long n, int block) {
 
 struct PlanBuilder {
     const hyp_grid* G;
-    const LineOp* dops;  // device operator array
+    const LineOp* dops;   // device operator array
+    const LineOp* hops;   // host copies (line lengths)
     std::vector<LineJob> jobs;
-    int ph_start[PH_COUNT], ph_count[PH_COUNT], ph_lines[PH_COUNT];
+    std::vector<long long> out_size;
+    int ph_start[PH_COUNT], ph_count[PH_COUNT], ph_blocks[PH_COUNT];
     int cur = -1;
 
     void begin(int ph) {
         cur = ph;
         ph_start[ph] = (int)jobs.size();
         ph_count[ph] = 0;
-        ph_lines[ph] = 0;
+        ph_blocks[ph] = 0;
     }
-    // axis 0: along x (lines are rows), 1: along y (lines are columns)
     void add(OpId op, const double* in, Node tin, double* out, Node tout, const double* metric,
              double scale = 1.0, double wall_value = 0.0, int in_state = 0) {
         const Dims& d = G->d;
@@ -663,7 +694,6 @@ struct PlanBuilder {
         j.in = in;
         j.in_state = in_state;
         j.out = out;
-        j.tmp = nullptr;
         if (alongx) {
             j.in_ls = d.pitch(tin);
             j.in_es = 1;
@@ -677,13 +707,54 @@ struct PlanBuilder {
             j.out_es = d.pitch(tout);
             j.nlines = d.pitch(tin);
         }
-        j.accumulate = 0;
+        j.nseg = hops[op].m;   // line length for now; replaced by the segment count in finish()
         j.wall_value = wall_value;
         j.scale = scale;
         j.metric = metric;
         jobs.push_back(j);
+        out_size.push_back(d.size(tout));
         ph_count[cur]++;
-        ph_lines[cur] = std::max(ph_lines[cur], j.nlines);
+    }
+    // Segment counts (about 129 points per segment, more segments when a phase has too few
+    // threads to occupy the GPU), forward-sweep storage and block counts per phase. Returns the
+    // tmp doubles needed by the largest phase.
+    long long finish() {
+        long long need = 0;
+        for (int ph = 0; ph < PH_COUNT; ++ph) {
+            const int a = ph_start[ph], b = a + ph_count[ph];
+            std::vector<int> nseg(ph_count[ph]);
+            long long threads = 0;
+            for (int k = a; k < b; ++k) {
+                const int m = jobs[k].nseg;
+                int ns = 1;
+                while (ns < 64 && (m + ns - 1) / ns > 129) ns *= 2;
+                nseg[k - a] = ns;
+                threads += (long long)jobs[k].nlines * ns;
+            }
+            while (threads < 40960) {
+                bool grew = false;
+                threads = 0;
+                for (int k = a; k < b; ++k) {
+                    const int m = jobs[k].nseg;
+                    if (nseg[k - a] < 64 && (m + 2 * nseg[k - a] - 1) / (2 * nseg[k - a]) >= 32) {
+                        nseg[k - a] *= 2;
+                        grew = true;
+                    }
+                    threads += (long long)jobs[k].nlines * nseg[k - a];
+                }
+                if (!grew) break;
+            }
+            long long off = 0;
+            for (int k = a; k < b; ++k) {
+                jobs[k].nseg = nseg[k - a];
+                jobs[k].tmp = (double*)(size_t)off;   // relative; fixed up by the caller
+                off += out_size[k];
+                const int lpb = 128 / jobs[k].nseg;
+                ph_blocks[ph] = std::max(ph_blocks[ph], (jobs[k].nlines + lpb - 1) / lpb);
+            }
+            need = std::max(need, off);
+        }
+        return need;
     }
 };
 
@@ -719,6 +790,11 @@ static void free_grid(hyp_grid* G) {
     cudaFree(G->ops);
     cudaFree(G->opdata);
     cudaFree(G->jobs);
+    cudaFree(G->linetmp);
+    if (G->prof) {
+        for (auto e : G->prof->ev) cudaEventDestroy(e);
+        delete G->prof;
+    }
     delete G;
 }
 
@@ -856,7 +932,7 @@ extern "C" int hyp_state_init(const hyp_gas* gas, const hyp_grid_desc* desc, con
     }
 
     // ---------------- device memory ----------------
-    const long long n_c_fields = 13 + 6 * NSP + 6 + 5 + 16;
+    const long long n_c_fields = 13 + 6 * NSP + 8 + 5 + 16;
     const long long n_xf_fields = 2 + 6 * NSP + 8 + 3;
     const long long n_yf_fields = 2 + 6 * NSP + 8;
     const long long n_cn_fields = 8;
@@ -885,7 +961,7 @@ extern "C" int hyp_state_init(const hyp_gas* gas, const hyp_grid_desc* desc, con
         S.W[sp] = take(nc);
         S.G[sp] = take(nc);
     }
-    double** c2[] = {&S.dudx, &S.dvdy, &S.tau_xx, &S.tau_yy, &S.Gxx, &S.Gyy,
+    double** c2[] = {&S.dudx, &S.dvdy, &S.tau_xx, &S.tau_yy, &S.Gxx, &S.Gyy, &S.mux_c, &S.mvy_c,
                      &S.dudy_c, &S.dvdx_c, &S.S, &S.div, &S.fsw};
     for (double** f : c2) *f = take(nc);
     for (int q = 0; q < 8; ++q) {
@@ -893,7 +969,7 @@ extern "C" int hyp_state_init(const hyp_gas* gas, const hyp_grid_desc* desc, con
         S.filt[q] = take(nc);
     }
     double** xfields[] = {&S.rho_xf, &S.u_xf, &S.Hx, &S.Kx, &S.txx_x, &S.v_x, &S.dTdx, &S.txy_x,
-                          &S.FEx, &S.mu_xf, &S.dudy_t, &S.dvdx_t};
+                          &S.FEx, &S.mu_xf, &S.dudy_t, &S.dvdx_t, &S.mux_f};
     for (double** f : xfields) *f = take(nxf);
     for (int sp = 0; sp < NSP; ++sp) {
         S.Yx[sp] = take(nxf);
@@ -903,7 +979,7 @@ extern "C" int hyp_state_init(const hyp_gas* gas, const hyp_grid_desc* desc, con
         S.Fsx[sp] = take(nxf);
     }
     double** yfields[] = {&S.rho_yf, &S.v_yf, &S.Hy, &S.Ky, &S.tyy_y, &S.u_y, &S.dTdy, &S.txy_y,
-                          &S.FEy};
+                          &S.FEy, &S.mvy_f};
     for (double** f : yfields) *f = take(nyf);
     for (int sp = 0; sp < NSP; ++sp) {
         S.Yy[sp] = take(nyf);
@@ -963,6 +1039,7 @@ extern "C" int hyp_state_init(const hyp_gas* gas, const hyp_grid_desc* desc, con
     PlanBuilder B;
     B.G = G;
     B.dops = G->ops;
+    B.hops = hops.data();
     const bool wall = cas->wall != 0;
     const OpId y_icf_u = wall ? OY_ICFW : OY_ICF;
     const OpId y_dcf_u = wall ? OY_DCFW : OY_DCF;
@@ -974,6 +1051,8 @@ extern "C" int hyp_state_init(const hyp_gas* gas, const hyp_grid_desc* desc, con
     B.add(y_icf_u, S.u_xf, NXF, S.u_cn, NCN, nullptr, 1.0, 0.0);
     B.add(OX_ICF, S.v_yf, NYF, S.v_cn, NCN, nullptr);
     B.add(OY_ICF, S.rho_xf, NXF, S.rho_cn, NCN, nullptr);
+    B.add(OX_IFC, S.mux_f, NXF, S.mux_c, NC, nullptr);
+    B.add(OY_IFC, S.mvy_f, NYF, S.mvy_c, NC, nullptr);
     B.begin(PH_AD1);
     B.add(OY_IFC, S.dudy_cn, NCN, S.dudy_t, NXF, nullptr);
     B.add(OY_IFC, S.dvdx_cn, NCN, S.dvdx_t, NXF, nullptr);
@@ -1027,14 +1106,17 @@ extern "C" int hyp_state_init(const hyp_gas* gas, const hyp_grid_desc* desc, con
     B.add(OY_ICF, soff(0), NC, S.rho_yf, NYF, nullptr, 1.0, 0.0, 1);
     B.add(OX_DFC, soff(NSP + 1), NXF, S.DX + G->off[0], NC, G->xi_c, -1.0, 0.0, 1);
     B.add(OY_DFC, soff(NSP + 2), NYF, S.DY + G->off[0], NC, G->eta_c, -1.0, 0.0, 1);
+    const long long tmp_need = B.finish();
     memcpy(G->ph_start, B.ph_start, sizeof(B.ph_start));
     memcpy(G->ph_count, B.ph_count, sizeof(B.ph_count));
-    memcpy(G->ph_lines, B.ph_lines, sizeof(B.ph_lines));
-    err = cudaMalloc(&G->jobs, B.jobs.size() * sizeof(LineJob));
+    memcpy(G->ph_blocks, B.ph_blocks, sizeof(B.ph_blocks));
+    err = cudaMalloc(&G->linetmp, tmp_need * sizeof(double));
+    if (err == cudaSuccess) err = cudaMalloc(&G->jobs, B.jobs.size() * sizeof(LineJob));
     if (err != cudaSuccess) {
         free_grid(G);
         return cuda_fail(err, "cudaMalloc(jobs)");
     }
+    for (auto& j : B.jobs) j.tmp = G->linetmp + (size_t)j.tmp;
     // uploads
 #define UP(dst, src, bytes) HYP_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s))
     UP(G->opdata, opdata.data(), opdata.size() * sizeof(double));
@@ -1090,6 +1172,35 @@ extern "C" int hyp_grid_status(const hyp_grid* G, uint32_t* flags, int clear) {
     return HYP_OK;
 }
 
+static int prof_begin(hyp_grid* G, int kid, cudaStream_t s) {
+    EventProfile* P = G->prof;
+    if (!P || !P->on) return -1;
+    if (P->used + 2 > P->ev.size()) {
+        for (int k = 0; k < 256; ++k) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return -1;
+            P->ev.push_back(e);
+        }
+        P->id.resize(P->ev.size() / 2);
+    }
+    const size_t slot = P->used;
+    P->used += 2;
+    P->id[slot / 2] = kid;
+    cudaEventRecord(P->ev[slot], s);
+    return (int)slot;
+}
+
+static void prof_end(hyp_grid* G, int slot, cudaStream_t s) {
+    if (slot >= 0) cudaEventRecord(G->prof->ev[slot + 1], s);
+}
+
+#define TIMED(kid, ...)                               \
+    do {                                              \
+        const int _slot = prof_begin(G, kid, s);      \
+        __VA_ARGS__;                                  \
+        prof_end(G, _slot, s);                        \
+    } while (0)
+
 // The whole right-hand side; with rk != 0 the assemble step performs the stage update instead
 // of writing dUdt.
 static int run_rhs(const hyp_gas* gas, hyp_grid* G, const double* U, double* dUdt, int rk,
@@ -1099,34 +1210,46 @@ static int run_rhs(const hyp_gas* gas, hyp_grid* G, const double* U, double* dUd
     Scratch& S = G->s;
     const Dims& d = G->d;
     const long long nc = d.size(NC);
-    HYP_CUDA(launch_lines(G->jobs + G->ph_start[PH_P1], G->ph_count[PH_P1], G->ph_lines[PH_P1], U, s));
-    k_face_vel<<<blocks_for(d.size(NXF) + d.size(NYF), 256), 256, 0, s>>>(v, U, S);
-    k_closure<<<blocks_for(nc, 128), 128, 0, s>>>(g, v, U, S);
+    cudaError_t e1 = cudaSuccess;
+    TIMED(KID_LINES_STATE, e1 = launch_lines(G->jobs + G->ph_start[PH_P1], G->ph_count[PH_P1],
+                                             G->ph_blocks[PH_P1], U, s));
+    HYP_CUDA(e1);
+    TIMED(KID_FACE_VEL, (k_face_vel<<<blocks_for(d.size(NXF) + d.size(NYF), 256), 256, 0, s>>>(v, U, S)));
+    TIMED(KID_CLOSURE, (k_closure<<<blocks_for(nc, 128), 128, 0, s>>>(g, v, U, S)));
     HYP_CUDA(cudaGetLastError());
-    HYP_CUDA(launch_lines(G->jobs + G->ph_start[PH_P3], G->ph_count[PH_P3], G->ph_lines[PH_P3], U, s));
+    TIMED(KID_LINES_VELGRAD, e1 = launch_lines(G->jobs + G->ph_start[PH_P3], G->ph_count[PH_P3],
+                                               G->ph_blocks[PH_P3], U, s));
+    HYP_CUDA(e1);
     if (v.ad) {
-        HYP_CUDA(launch_lines(G->jobs + G->ph_start[PH_AD1], 2, G->ph_lines[PH_AD1], U, s));
-        HYP_CUDA(launch_lines(G->jobs + G->ph_start[PH_AD2], 2, G->ph_lines[PH_AD2], U, s));
-        k_ad_prep<<<blocks_for(nc, 256), 256, 0, s>>>(v, S);
-        k_ad_raw<<<blocks_for(nc, 256), 256, 0, s>>>(g, v, U, S);
+        TIMED(KID_LINES_AD, e1 = launch_lines(G->jobs + G->ph_start[PH_AD1], 2, G->ph_blocks[PH_AD1], U, s));
+        HYP_CUDA(e1);
+        TIMED(KID_LINES_AD, e1 = launch_lines(G->jobs + G->ph_start[PH_AD2], 2, G->ph_blocks[PH_AD2], U, s));
+        HYP_CUDA(e1);
+        TIMED(KID_AD_PREP, (k_ad_prep<<<blocks_for(nc, 256), 256, 0, s>>>(v, S)));
+        TIMED(KID_AD_RAW, (k_ad_raw<<<blocks_for(nc, 256), 256, 0, s>>>(g, v, U, S)));
         dim3 gg(blocks_for(nc, 256), 8);
-        k_gauss<<<gg, 256, 0, s>>>(v, S, 0);
-        k_gauss<<<gg, 256, 0, s>>>(v, S, 1);
-        k_ad_combine<<<blocks_for(nc, 256), 256, 0, s>>>(v, S);
+        TIMED(KID_AD_GAUSS, (k_gauss<<<gg, 256, 0, s>>>(v, S, 0)));
+        TIMED(KID_AD_GAUSS, (k_gauss<<<gg, 256, 0, s>>>(v, S, 1)));
+        TIMED(KID_AD_COMBINE, (k_ad_combine<<<blocks_for(nc, 256), 256, 0, s>>>(v, S)));
         HYP_CUDA(cudaGetLastError());
     }
-    k_stress_c<<<blocks_for(nc, 256), 256, 0, s>>>(v, S);
-    HYP_CUDA(launch_lines(G->jobs + G->ph_start[PH_MU1], 1, G->ph_lines[PH_MU1], U, s));
-    HYP_CUDA(launch_lines(G->jobs + G->ph_start[PH_MU2], 1, G->ph_lines[PH_MU2], U, s));
-    k_stress_cn<<<blocks_for(d.size(NCN), 256), 256, 0, s>>>(v, S);
-    HYP_CUDA(launch_lines(G->jobs + G->ph_start[PH_FACE], G->ph_count[PH_FACE],
-                          G->ph_lines[PH_FACE], U, s));
-    k_flux<<<blocks_for(d.size(NXF), 128), 128, 0, s>>>(v, U, S, 0);
-    k_flux<<<blocks_for(d.size(NYF), 128), 128, 0, s>>>(v, U, S, 1);
-    HYP_CUDA(launch_lines(G->jobs + G->ph_start[PH_DIV], G->ph_count[PH_DIV], G->ph_lines[PH_DIV], U, s));
-    k_assemble<<<blocks_for(G->nstate, 256), 256, 0, s>>>(G->nstate, S.DX, S.DY, S.SRC, G->sigma,
-                                                           G->Uref, G->mask, rk ? Urk : (double*)U,
-                                                           dUdt, dQ, rk, A, Bc, dt);
+    TIMED(KID_STRESS_C, (k_stress_c<<<blocks_for(nc, 256), 256, 0, s>>>(v, S)));
+    TIMED(KID_LINES_MU, e1 = launch_lines(G->jobs + G->ph_start[PH_MU1], 1, G->ph_blocks[PH_MU1], U, s));
+    HYP_CUDA(e1);
+    TIMED(KID_LINES_MU, e1 = launch_lines(G->jobs + G->ph_start[PH_MU2], 1, G->ph_blocks[PH_MU2], U, s));
+    HYP_CUDA(e1);
+    TIMED(KID_STRESS_CN, (k_stress_cn<<<blocks_for(d.size(NCN), 256), 256, 0, s>>>(v, S)));
+    TIMED(KID_LINES_FACE, e1 = launch_lines(G->jobs + G->ph_start[PH_FACE], G->ph_count[PH_FACE],
+                                            G->ph_blocks[PH_FACE], U, s));
+    HYP_CUDA(e1);
+    TIMED(KID_FLUX, (k_flux<<<blocks_for(d.size(NXF), 128), 128, 0, s>>>(v, U, S, 0)));
+    TIMED(KID_FLUX, (k_flux<<<blocks_for(d.size(NYF), 128), 128, 0, s>>>(v, U, S, 1)));
+    TIMED(KID_LINES_DIV, e1 = launch_lines(G->jobs + G->ph_start[PH_DIV], G->ph_count[PH_DIV],
+                                           G->ph_blocks[PH_DIV], U, s));
+    HYP_CUDA(e1);
+    TIMED(KID_ASSEMBLE, (k_assemble<<<blocks_for(G->nstate, 256), 256, 0, s>>>(
+                            G->nstate, S.DX, S.DY, S.SRC, G->sigma, G->Uref, G->mask,
+                            rk ? Urk : (double*)U, dUdt, dQ, rk, A, Bc, dt)));
     HYP_CUDA(cudaGetLastError());
     return HYP_OK;
 }
@@ -1150,4 +1273,48 @@ extern "C" int hyp_rk_stage(hyp_state* st, int stage, double dt, int precision, 
     tmp.dev = G->gas;
     return run_rhs(&tmp, G, st->U, nullptr, 1, RK_A[stage], RK_B[stage], dt, st->U, st->dQ,
                    (cudaStream_t)stream);
+}
+
+extern "C" int hyp_profile_count(void) { return KID_COUNT; }
+
+extern "C" const char* hyp_profile_name(int id) {
+    return (id >= 0 && id < KID_COUNT) ? KERNEL_NAMES[id] : "";
+}
+
+extern "C" int hyp_grid_profile(const hyp_grid* grid, int enable) {
+    if (!grid) return fail(HYP_ERR_ARG, "null grid");
+    hyp_grid* G = const_cast<hyp_grid*>(grid);
+    if (!G->prof) G->prof = new EventProfile();
+    EventProfile* P = G->prof;
+    if (enable) {
+        HYP_CUDA(cudaStreamSynchronize(G->stream));
+        P->used = 0;
+        for (int k = 0; k < KID_COUNT; ++k) {
+            P->ms[k] = 0.0;
+            P->count[k] = 0;
+        }
+    }
+    P->on = enable != 0;
+    return HYP_OK;
+}
+
+extern "C" int hyp_grid_profile_read(const hyp_grid* grid, int n, double* ms, int64_t* launches) {
+    if (!grid || n < 0) return fail(HYP_ERR_ARG, "bad argument");
+    hyp_grid* G = const_cast<hyp_grid*>(grid);
+    EventProfile* P = G->prof;
+    if (P) {
+        for (size_t slot = 0; slot < P->used; slot += 2) {
+            HYP_CUDA(cudaEventSynchronize(P->ev[slot + 1]));
+            float t = 0.0f;
+            HYP_CUDA(cudaEventElapsedTime(&t, P->ev[slot], P->ev[slot + 1]));
+            P->ms[P->id[slot / 2]] += t;
+            P->count[P->id[slot / 2]] += 1;
+        }
+        P->used = 0;
+    }
+    for (int k = 0; k < n && k < KID_COUNT; ++k) {
+        if (ms) ms[k] = P ? P->ms[k] : 0.0;
+        if (launches) launches[k] = P ? P->count[k] : 0;
+    }
+    return HYP_OK;
 }

@@ -30,7 +30,7 @@ def bl_case(nx=256, ny=64, seed=0, kind="cneq"):
         T_inf=350.0, p_inf=3000.0, Y_inf=AIR_Y, mach=10.0, reynolds=1.0e5, prandtl_cpg=0.72,
         flow="bl", wall=1, T_wall=1000.0, delta_coef=70.0, minor_species=0.02,
         shock_deflection_deg=0.0, shock_x=0.0, shock_width=0.0,
-        sponge_sigma=2.0, sponge_in=5.0, sponge_out=15.0, sponge_top_cells=max(2, (26 * ny) // 211),
+        sponge_sigma=200.0, sponge_in=5.0, sponge_out=15.0, sponge_top_cells=max(2, (26 * ny) // 211),
         artificial_diffusivity=0, C_mu=0.002, C_beta=1.75, C_kappa=0.01, C_D=0.0,
         noise_amp=1.0e-4, dt=2.0e-4,
     )
@@ -47,7 +47,7 @@ def sbli_case(nx=2048, ny=256, seed=0, kind="cneq"):
         T_inf=1110.5, p_inf=60967.0, Y_inf=AIR_Y, mach=mach, reynolds=2000.0, prandtl_cpg=0.72,
         flow="sbli", wall=1, T_wall=1500.0, delta_coef=5.0 * 4.0, minor_species=0.02,
         shock_deflection_deg=deflection, shock_x=120.0, shock_width=1.0,
-        sponge_sigma=2.0, sponge_in=10.0, sponge_out=30.0, sponge_top_cells=max(2, (26 * ny) // 211),
+        sponge_sigma=200.0, sponge_in=10.0, sponge_out=30.0, sponge_top_cells=max(2, (26 * ny) // 211),
         artificial_diffusivity=1, C_mu=0.002, C_beta=1.75, C_kappa=0.01, C_D=0.01,
         noise_amp=1.0e-4, dt=2.0e-3,
     )

@@ -46,3 +46,15 @@ def gpu_rhs(gas, st, U_host):
     A.rhs(gas, st.grid, U, R)
     torch.cuda.synchronize()
     return R.cpu().numpy()
+
+
+def check_rhs(case, U, g):
+    """Parity of a computed RHS g with the oracle at state U: per field,
+    max|g - o| <= 1e-12 max|o| + rounding floor of the flux divergence (oracle.flow)."""
+    tol, o = F.parity_tolerance(case, U)
+    cfg = case.cfg
+    fg = F.unpack(5, cfg["nx"], cfg["ny"], np.asarray(g))
+    fo = F.unpack(5, cfg["nx"], cfg["ny"], o)
+    bad = {k: (float(np.abs(fg[k] - fo[k]).max()), float(tol[k])) for k in fo
+           if not np.abs(fg[k] - fo[k]).max() <= tol[k]}
+    return bad, o
