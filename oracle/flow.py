@@ -589,6 +589,12 @@ def parity_tolerance(case: Case, U):
     f = unpack(case.tab.ns, g.nx, g.ny, R)
     tol = {k: PARITY_RTOL * np.abs(v).max() + PARITY_FLOOR * parts["gross"][k]
            for k, v in f.items()}
+    # sponge term sigma (U - U_ref): U and U_ref agree to the seeded noise, so the difference
+    # carries the rounding of U itself (a few eps |U|) times sigma
+    q = unpack(case.tab.ns, g.nx, g.ny, np.asarray(U, dtype=np.float64))
+    sig_max = max(float(np.max(v)) for v in case.sigma.values())
+    for k in tol:
+        tol[k] += 16.0 * 2.0 ** -53 * sig_max * np.abs(q[k]).max()
     if case.kind == KIND_CNEQ and case.tab.reactions:
         ta_max = max(r.Ta for r in case.tab.reactions)
         T_si = parts["T"] * case.sc.T_ref
