@@ -170,6 +170,26 @@ int hyp_thermo_eval(const hyp_gas* gas, int64_t n, const double* rho, const doub
 int hyp_thermo_energy(const hyp_gas* gas, int64_t n, const double* T, const double* Y, double* e,
                       void* stream);
 
+/* hyp_rhs without any device allocation of its own scratch (the paper has no counterpart; this
+ * is an interface for callers that may not allocate device memory while they run: work enqueued
+ * during CUDA stream capture, real-time loops that forbid allocation after start-up, hosts that
+ * own all device memory through their own allocator). It computes the same right-hand side as
+ * hyp_rhs for the same gas, grid and U, within rounding (the Newton inversion starts from 1000 K
+ * instead of the grid's previous temperatures). Arguments as for hyp_rhs, always FP64.
+ * - Scratch: every per-call scratch field, the line-sweep storage and the launch plan live in one
+ *   file-scope device array of 12 MiB (1,572,864 doubles) that every GPU loading the library holds
+ *   until exit. Grids needing more (a few thousand cells, e.g. up to 64 x 64) are rejected with
+ *   HYP_ERR_ARG and the required size in hyp_last_error(). The grid's own scratch is not touched;
+ *   its read-only data (metrics, reference state, sponge, operators) are used.
+ * - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ *   that device current; make that first call before any stream capture.
+ * - Each call reads the grid's launch plan back to the host and synchronises `stream` once, then
+ *   enqueues asynchronously. It calls no cudaMalloc, cudaFree or other allocating routine.
+ * - All calls on a device share the array: it keeps the last call's contents (the parts that must
+ *   start at zero are cleared on every call), and calls that overlap on the GPU race. */
+int hyp_rhs_noalloc(const hyp_gas* gas, const hyp_grid* grid, const double* U, double* dUdt,
+                    void* stream);
+
 /* Event profile of the launches that hyp_rhs / hyp_rk_stage make on a grid (diagnostics; no
  * counterpart in the paper). hyp_grid_profile(grid, 1) clears the totals and starts recording a
  * pair of CUDA events around every launch on the caller's stream; (grid, 0) stops. Reading

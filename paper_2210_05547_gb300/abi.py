@@ -69,6 +69,7 @@ EXPORTS = {
     "hyp_rk_stage": (_I, [_P, _I, _D, _I, _P]),
     "hyp_thermo_eval": (_I, [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I, _P]),
     "hyp_thermo_energy": (_I, [_P, _I64, _P, _P, _P, _P]),
+    "hyp_rhs_noalloc": (_I, [_P, _P, _P, _P, _P]),
     "hyp_grid_profile": (_I, [_P, _I]),
     "hyp_grid_profile_read": (_I, [_P, _I, _P, _P]),
     "hyp_profile_count": (_I, []),
@@ -227,6 +228,12 @@ def rhs(gas, grid, U, dUdt, precision=FP64, stream=None):
     """hyp_rhs: dU/dt of the state U (device tensors, same length)."""
     _check(lib().hyp_rhs(gas.handle, grid, _dptr(U), _dptr(dUdt, U.numel()), precision,
                          _stream(stream)))
+
+
+def rhs_noalloc(gas, grid, U, dUdt, stream=None):
+    """hyp_rhs_noalloc: the right-hand side with its scratch in the library's static device array."""
+    _check(lib().hyp_rhs_noalloc(gas.handle, grid, _dptr(U), _dptr(dUdt, U.numel()),
+                                 _stream(stream)))
 
 
 def rk_stage(state, stage, dt, precision=FP64, stream=None):

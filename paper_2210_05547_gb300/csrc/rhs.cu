@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -107,6 +108,7 @@ struct hyp_grid {
     LineJob* jobs;
     int ph_start[PH_COUNT], ph_count[PH_COUNT], ph_blocks[PH_COUNT];
     double* linetmp;
+    long long linetmp_n;
     cudaStream_t stream;
     double Tw_nd;
     EventProfile* prof;
@@ -1110,6 +1112,7 @@ extern "C" int hyp_state_init(const hyp_gas* gas, const hyp_grid_desc* desc, con
     memcpy(G->ph_start, B.ph_start, sizeof(B.ph_start));
     memcpy(G->ph_count, B.ph_count, sizeof(B.ph_count));
     memcpy(G->ph_blocks, B.ph_blocks, sizeof(B.ph_blocks));
+    G->linetmp_n = tmp_need;
     err = cudaMalloc(&G->linetmp, tmp_need * sizeof(double));
     if (err == cudaSuccess) err = cudaMalloc(&G->jobs, B.jobs.size() * sizeof(LineJob));
     if (err != cudaSuccess) {
@@ -1316,5 +1319,123 @@ extern "C" int hyp_grid_profile_read(const hyp_grid* grid, int n, double* ms, in
         if (ms) ms[k] = P ? P->ms[k] : 0.0;
         if (launches) launches[k] = P ? P->count[k] : 0;
     }
+    return HYP_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// hyp_rhs_noalloc: the right-hand side with all per-call scratch in one static device array.
+//
+// Some callers may not allocate device memory once they are running: code that enqueues work
+// while a CUDA stream is being captured into a graph (an allocation there breaks or invalidates
+// the capture), real-time solver loops that forbid allocation after start-up, and hosts that own
+// all device memory through their own allocator. hyp_rhs never allocates either, but it keeps
+// its scratch inside the grid handle; this variant instead takes every scratch field, the line
+// sweep storage and its launch plan from the file-scope array below, so a grid's scratch is not
+// touched. The grid's read-only data (metrics, reference state, sponge, operators) are used as is.
+// ---------------------------------------------------------------------------------------------
+
+#define HYP_NOALLOC_DOUBLES (3LL << 19)   // 1,572,864 doubles = 12 MiB per GPU
+#define HYP_NOALLOC_MAX_JOBS 160
+#define HYP_NOALLOC_MAX_DEVICES 64
+
+static __device__ __align__(256) double g_noalloc_scratch[HYP_NOALLOC_DOUBLES];
+static double* g_noalloc_base[HYP_NOALLOC_MAX_DEVICES];
+static std::mutex g_noalloc_mutex;
+
+// Device address of the static array on the current device, looked up once per device. The
+// array's name in host code is only a host-side stand-in, so the address must come from
+// cudaGetSymbolAddress with the device current.
+static int noalloc_base(double** base) {
+    int dev = 0;
+    HYP_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= HYP_NOALLOC_MAX_DEVICES) return fail(HYP_ERR_ARG, "device index too large");
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_base[dev]) {
+        void* p = nullptr;
+        HYP_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_base[dev] = (double*)p;
+    }
+    *base = g_noalloc_base[dev];
+    return HYP_OK;
+}
+
+extern "C" int hyp_rhs_noalloc(const hyp_gas* gas, const hyp_grid* grid, const double* U,
+                               double* dUdt, void* stream) {
+    if (!gas || !grid || !U || !dUdt) return fail(HYP_ERR_ARG, "null argument");
+    if (U == dUdt) return fail(HYP_ERR_ARG, "U and dUdt must not alias");
+    hyp_grid* G = const_cast<hyp_grid*>(grid);
+    cudaStream_t s = (cudaStream_t)stream;
+    int njobs = 0;
+    for (int ph = 0; ph < PH_COUNT; ++ph) njobs = std::max(njobs, G->ph_start[ph] + G->ph_count[ph]);
+    const long long scratch_n = G->Uref - G->pool;    // scratch fields, DX, DY, SRC, R
+    const long long jobs_n = ((long long)njobs * (long long)sizeof(LineJob) + 255) / 256 * 32;
+    const long long need = scratch_n + G->linetmp_n + jobs_n;
+    if (njobs > HYP_NOALLOC_MAX_JOBS || need > HYP_NOALLOC_DOUBLES)
+        return fail(HYP_ERR_ARG, "grid too large for hyp_rhs_noalloc: needs " +
+                                     std::to_string(need) + " doubles of scratch, the static array holds " +
+                                     std::to_string((long long)HYP_NOALLOC_DOUBLES));
+    double* base = nullptr;
+    int rc = noalloc_base(&base);
+    if (rc) return rc;
+    double* tmp_base = base + scratch_n;
+    LineJob* djobs = (LineJob*)(base + scratch_n + G->linetmp_n);
+    auto relocate = [&](const double* p) -> double* {
+        if (p >= G->pool && p < G->pool + scratch_n) return base + (p - G->pool);
+        if (p >= G->linetmp && p < G->linetmp + G->linetmp_n) return tmp_base + (p - G->linetmp);
+        return const_cast<double*>(p);
+    };
+    // the grid's launch plan, with its scratch pointers moved into the static array
+    LineJob jobs[HYP_NOALLOC_MAX_JOBS];
+    HYP_CUDA(cudaMemcpyAsync(jobs, G->jobs, njobs * sizeof(LineJob), cudaMemcpyDeviceToHost, s));
+    HYP_CUDA(cudaStreamSynchronize(s));
+    for (int k = 0; k < njobs; ++k) {
+        if (!jobs[k].in_state) jobs[k].in = relocate(jobs[k].in);
+        jobs[k].out = relocate(jobs[k].out);
+        jobs[k].tmp = relocate(jobs[k].tmp);
+    }
+    HYP_CUDA(cudaMemcpyAsync(djobs, jobs, njobs * sizeof(LineJob), cudaMemcpyHostToDevice, s));
+    Scratch S = G->s;
+    double** fields = reinterpret_cast<double**>(&S);
+    for (size_t k = 0; k < sizeof(Scratch) / sizeof(double*); ++k) fields[k] = relocate(fields[k]);
+    // state carried between calls is reset: species sources start at zero, Newton starts at 1000 K
+    HYP_CUDA(cudaMemsetAsync(S.SRC, 0, G->nstate * sizeof(double), s));
+    const long long nc = G->d.size(NC);
+    k_fill<<<blocks_for(nc, 256), 256, 0, s>>>(S.Tcache, nc, 1000.0);
+    HYP_CUDA(cudaGetLastError());
+
+    const GasDev& g = gas->dev;
+    const GridView v = G->view();
+    const Dims& d = G->d;
+    auto lines = [&](int ph, int count) {
+        return launch_lines(djobs + G->ph_start[ph], count, G->ph_blocks[ph], U, s);
+    };
+    HYP_CUDA(lines(PH_P1, G->ph_count[PH_P1]));
+    k_face_vel<<<blocks_for(d.size(NXF) + d.size(NYF), 256), 256, 0, s>>>(v, U, S);
+    k_closure<<<blocks_for(nc, 128), 128, 0, s>>>(g, v, U, S);
+    HYP_CUDA(cudaGetLastError());
+    HYP_CUDA(lines(PH_P3, G->ph_count[PH_P3]));
+    if (v.ad) {
+        HYP_CUDA(lines(PH_AD1, 2));
+        HYP_CUDA(lines(PH_AD2, 2));
+        k_ad_prep<<<blocks_for(nc, 256), 256, 0, s>>>(v, S);
+        k_ad_raw<<<blocks_for(nc, 256), 256, 0, s>>>(g, v, U, S);
+        dim3 gg(blocks_for(nc, 256), 8);
+        k_gauss<<<gg, 256, 0, s>>>(v, S, 0);
+        k_gauss<<<gg, 256, 0, s>>>(v, S, 1);
+        k_ad_combine<<<blocks_for(nc, 256), 256, 0, s>>>(v, S);
+        HYP_CUDA(cudaGetLastError());
+    }
+    k_stress_c<<<blocks_for(nc, 256), 256, 0, s>>>(v, S);
+    HYP_CUDA(lines(PH_MU1, 1));
+    HYP_CUDA(lines(PH_MU2, 1));
+    k_stress_cn<<<blocks_for(d.size(NCN), 256), 256, 0, s>>>(v, S);
+    HYP_CUDA(lines(PH_FACE, G->ph_count[PH_FACE]));
+    k_flux<<<blocks_for(d.size(NXF), 128), 128, 0, s>>>(v, U, S, 0);
+    k_flux<<<blocks_for(d.size(NYF), 128), 128, 0, s>>>(v, U, S, 1);
+    HYP_CUDA(lines(PH_DIV, G->ph_count[PH_DIV]));
+    k_assemble<<<blocks_for(G->nstate, 256), 256, 0, s>>>(G->nstate, S.DX, S.DY, S.SRC, G->sigma,
+                                                           G->Uref, G->mask, (double*)U, dUdt,
+                                                           nullptr, 0, 0.0, 0.0, 0.0);
+    HYP_CUDA(cudaGetLastError());
     return HYP_OK;
 }
