@@ -35,9 +35,10 @@ STAGES = 3
 L2_FLUSH_BYTES = 256 << 20
 # FP64 operations per cell-centre point executed by k_closure (DADD + DMUL + 2 DFMA), from the
 # ncu instruction counts recorded in profiles/k_closure_sbli.md.
-CLOSURE_FP64_FLOP_PER_POINT = 8498.0
-# DRAM bytes (read + write) per k_closure launch at 2048 x 256 (profiles/k_closure_sbli.md).
-CLOSURE_DRAM_BYTES = 153.73e6
+CLOSURE_FP64_FLOP_PER_POINT = 4123.0
+# DRAM bytes (read + write) per k_closure launch at 2048 x 256 (profiles/k_closure_sbli.md);
+# None while the counters predate the current kernel.
+CLOSURE_DRAM_BYTES = None
 # GB300 FP64 peak derived from the unit counts: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 

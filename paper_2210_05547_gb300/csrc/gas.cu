@@ -3,6 +3,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <fstream>
 #include <map>
 #include <sstream>
@@ -143,92 +144,132 @@ extern "C" int hyp_gas_model_load(const char* path, int kind, const hyp_freestre
         d.e0[i] = (r.hf - R_U * h_sens_over_r(r, 298.15)) / r.M;
         d.linear[i] = r.linear;
         d.theta_v[i] = r.theta_v;
-        d.nlev[i] = (int)r.levels.size();
-        for (size_t l = 0; l < r.levels.size(); ++l) {
-            d.lev_g[i][l] = r.levels[l].first;
-            d.lev_th[i][l] = r.levels[l].second;
+        std::vector<std::pair<double, double>> lev = r.levels;   // (g, theta), ascending theta
+        std::stable_sort(lev.begin(), lev.end(),
+                         [](const std::pair<double, double>& a, const std::pair<double, double>& b) {
+                             return a.second < b.second;
+                         });
+        d.nlev[i] = (int)lev.size();
+        for (size_t l = 0; l < lev.size(); ++l) {
+            d.lev_g[i][l] = lev[l].first;
+            d.lev_th[i][l] = lev[l].second;
         }
         const double m = r.M / N_A;
-        double s0 = 1.5 * log(2.0 * PI * m * K_B / (H_P * H_P)) + log(K_B / P_STD) + 2.5;
-        if (r.linear) s0 += 1.0 - log(r.sym * r.theta_r);
-        d.s0[i] = s0;
+        d.A_tr[i] = pow(2.0 * PI * m * K_B / (H_P * H_P), 1.5) / N_A;
+        d.inv_sr[i] = r.linear ? 1.0 / (r.sym * r.theta_r) : 0.0;
         d.blA[i] = r.bA;
         d.blB[i] = r.bB;
         d.blC[i] = r.bC;
     }
-    std::vector<double> eps_list;
     for (int i = 0; i < NSP; ++i)
         for (int j = 0; j < NSP; ++j) {
-            const SpeciesRow &a = sp[i], &b = sp[j];
-            d.wilke_q[i][j] = pow(b.M / a.M, 0.25);
-            d.wilke_d[i][j] = 1.0 / sqrt(8.0 * (1.0 + a.M / b.M));
-            const double m_sr = (a.M * b.M / (a.M + b.M)) / N_A;
-            const double sig = 0.5 * (a.lj_s + b.lj_s) * 1.0e-10;
-            d.dinv[i][j] = PI * sig * sig / (3.0 / 16.0 * sqrt(2.0 * PI * K_B * K_B * K_B / m_sr));
-            const double eps = a.lj_e * b.lj_e;
-            int q = -1;
-            for (size_t k = 0; k < eps_list.size(); ++k)
-                if (eps_list[k] == eps) q = (int)k;
-            if (q < 0) {
-                if ((int)eps_list.size() == MAXEPS) {
-                    delete g;
-                    return fail(HYP_ERR_IO, "too many distinct well depths");
+            d.wilke_q[i][j] = pow(sp[j].M / sp[i].M, 0.25);
+            d.wilke_d[i][j] = 1.0 / sqrt(8.0 * (1.0 + sp[i].M / sp[j].M));
+        }
+    // unordered pairs grouped by well depth: one collision integral per distinct depth
+    {
+        std::vector<double> eps_list;
+        std::vector<std::vector<int>> members;
+        for (int i = 0; i < NSP; ++i)
+            for (int j = i + 1; j < NSP; ++j) {
+                const double eps = sp[i].lj_e * sp[j].lj_e;
+                int q = -1;
+                for (size_t k = 0; k < eps_list.size(); ++k)
+                    if (eps_list[k] == eps) q = (int)k;
+                if (q < 0) {
+                    if ((int)eps_list.size() == MAXEPS) {
+                        delete g;
+                        return fail(HYP_ERR_IO, "too many distinct well depths");
+                    }
+                    eps_list.push_back(eps);
+                    members.emplace_back();
+                    q = (int)eps_list.size() - 1;
                 }
-                eps_list.push_back(eps);
-                q = (int)eps_list.size() - 1;
+                members[q].push_back(i * NSP + j);
             }
-            d.eps_group[i][j] = q;
-        }
-    d.neps = (int)eps_list.size();
-    for (int q = 0; q < d.neps; ++q) d.ln_eps[q] = 0.5 * log(eps_list[q]);
-    // reactions, grouped by (n, T_a, net stoichiometry): one k_f exponential and one K_c per group
-    d.nr = (int)rx.size();
-    for (int r = 0; r < d.nr; ++r) {
-        int order = 0;
-        for (auto& nm : rx[r].lhs) {
-            int idx = -1;
-            for (int i = 0; i < NSP; ++i)
-                if (sp[i].name == nm) idx = i;
-            if (idx < 0) {
-                delete g;
-                return fail(HYP_ERR_IO, "reaction uses unknown species " + nm);
+        d.neps = (int)eps_list.size();
+        int np = 0;
+        for (int q = 0; q < d.neps; ++q) {
+            d.pstart[q] = np;
+            d.eps_inv[q] = 1.0 / sqrt(eps_list[q]);
+            d.eps_powB[q] = pow(sqrt(eps_list[q]), 0.15610);
+            for (int code : members[q]) {
+                const int i = code / NSP, j = code % NSP;
+                const SpeciesRow &a = sp[i], &b = sp[j];
+                const double m_sr = (a.M * b.M / (a.M + b.M)) / N_A;
+                const double sig = 0.5 * (a.lj_s + b.lj_s) * 1.0e-10;
+                d.pair_i[np] = i;
+                d.pair_r[np] = j;
+                d.pair_dinv[np] = PI * sig * sig / (3.0 / 16.0 * sqrt(2.0 * PI * K_B * K_B * K_B / m_sr));
+                ++np;
             }
-            d.nu_f[r][idx] += 1;
-            ++order;
         }
-        for (auto& nm : rx[r].rhs) {
-            int idx = -1;
-            for (int i = 0; i < NSP; ++i)
-                if (sp[i].name == nm) idx = i;
-            if (idx < 0) {
-                delete g;
-                return fail(HYP_ERR_IO, "reaction uses unknown species " + nm);
+        d.pstart[d.neps] = np;
+        d.npair = np;
+    }
+    // reactions, grouped by (n, T_a, net stoichiometry): one k_f exponential and one K_c per group;
+    // stored sorted by group
+    {
+        const int nr = (int)rx.size();
+        std::vector<int> grp(nr), order_f(nr * NSP, 0), order_b(nr * NSP, 0);
+        std::vector<double> Cs(nr);
+        for (int r = 0; r < nr; ++r) {
+            int order = 0;
+            for (int side = 0; side < 2; ++side)
+                for (auto& nm : side == 0 ? rx[r].lhs : rx[r].rhs) {
+                    int idx = -1;
+                    for (int i = 0; i < NSP; ++i)
+                        if (sp[i].name == nm) idx = i;
+                    if (idx < 0) {
+                        delete g;
+                        return fail(HYP_ERR_IO, "reaction uses unknown species " + nm);
+                    }
+                    (side == 0 ? order_f : order_b)[r * NSP + idx] += 1;
+                    if (side == 0) ++order;
+                }
+            Cs[r] = rx[r].C_cgs * pow(1.0e-6, order - 1);
+            int k = -1;
+            for (int q = 0; q < d.ngroup; ++q) {
+                bool same = d.g_n[q] == rx[r].n && d.g_Ta[q] == rx[r].Ta;
+                for (int i = 0; i < NSP; ++i)
+                    same = same && d.g_nu[q][i] == order_b[r * NSP + i] - order_f[r * NSP + i];
+                if (same) k = q;
             }
-            d.nu_b[r][idx] += 1;
+            if (k < 0) {
+                if (d.ngroup == MAXG) {
+                    delete g;
+                    return fail(HYP_ERR_IO, "too many reaction groups");
+                }
+                k = d.ngroup++;
+                d.g_n[k] = rx[r].n;
+                d.g_Ta[k] = rx[r].Ta;
+                double theta_d = 0.0;
+                for (int i = 0; i < NSP; ++i) {
+                    const int nu = order_b[r * NSP + i] - order_f[r * NSP + i];
+                    d.g_nu[k][i] = (signed char)nu;
+                    d.g_nud[k][i] = nu;
+                    // E0 / R_u of species i: formation enthalpy minus the sensible part at 298.15 K
+                    theta_d += nu * (sp[i].hf / R_U - h_sens_over_r(sp[i], 298.15));
+                }
+                d.g_theta_d[k] = theta_d;
+            }
+            grp[r] = k;
         }
-        d.C[r] = rx[r].C_cgs * pow(1.0e-6, order - 1);
-        int grp = -1;
+        d.nr = nr;
+        int pos = 0;
         for (int k = 0; k < d.ngroup; ++k) {
-            bool same = d.g_n[k] == rx[r].n && d.g_Ta[k] == rx[r].Ta;
-            for (int i = 0; i < NSP; ++i) same = same && d.g_nu[k][i] == d.nu_b[r][i] - d.nu_f[r][i];
-            if (same) grp = k;
+            d.gstart[k] = pos;
+            for (int r = 0; r < nr; ++r)
+                if (grp[r] == k) {
+                    d.C[pos] = Cs[r];
+                    for (int i = 0; i < NSP; ++i) {
+                        d.nu_f[pos][i] = (signed char)order_f[r * NSP + i];
+                        d.nu_b[pos][i] = (signed char)order_b[r * NSP + i];
+                    }
+                    ++pos;
+                }
         }
-        if (grp < 0) {
-            if (d.ngroup == MAXG) {
-                delete g;
-                return fail(HYP_ERR_IO, "too many reaction groups");
-            }
-            grp = d.ngroup++;
-            d.g_n[grp] = rx[r].n;
-            d.g_Ta[grp] = rx[r].Ta;
-            int dnu = 0;
-            for (int i = 0; i < NSP; ++i) {
-                d.g_nu[grp][i] = (signed char)(d.nu_b[r][i] - d.nu_f[r][i]);
-                dnu += d.nu_b[r][i] - d.nu_f[r][i];
-            }
-            d.g_dnu[grp] = dnu;
-        }
-        d.group[r] = grp;
+        d.gstart[d.ngroup] = pos;
     }
     // freestream scales (Eqs. 7, 11)
     double Y[NSP], ym = 0.0, ysum = 0.0;

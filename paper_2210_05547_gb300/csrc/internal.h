@@ -30,28 +30,34 @@ int cuda_fail(cudaError_t err, const char* what);
 // Gas model as seen by the kernels: a plain struct passed by value as a kernel parameter.
 struct GasDev {
     int kind;                    // hyp_gas_kind
-    int nr, ngroup, neps;
+    int nr, ngroup, neps, npair;
     // species thermodynamics (rigid rotor / harmonic oscillator, Sec. 2.2.1)
     double M[NSP], invM[NSP], Rs[NSP];
-    double e0[NSP];              // (hf298 - H_sens(298.15)) / M, J/kg
+    double e0[NSP];              // (hf298 - H_sens(298.15)) / M, J/kg: internal energy at 0 K
     int linear[NSP];
     double theta_v[NSP];
-    int nlev[NSP];
+    int nlev[NSP];               // electronic levels, ascending theta (ground level first)
     double lev_g[NSP][MAXLEV], lev_th[NSP][MAXLEV];
-    double s0[NSP];              // temperature-independent part of S/R at p_std
+    double A_tr[NSP];            // (2 pi m k / h^2)^(3/2) / N_A: molar translational factor
+    double inv_sr[NSP];          // 1 / (sigma theta_r) for linear molecules
     // transport
     double blA[NSP], blB[NSP], blC[NSP];
     double wilke_q[NSP][NSP];    // (M_r / M_s)^(1/4)
     double wilke_d[NSP][NSP];    // 1 / sqrt(8 (1 + M_s / M_r))
-    double dinv[NSP][NSP];       // pi sigma_sr^2 / ((3/16) sqrt(2 pi k^3 / m_sr))
-    int eps_group[NSP][NSP];
-    double ln_eps[MAXEPS];
-    // kinetics (Eqs. 13-15): elementary reactions with explicit colliders
-    int group[MAXR];
+    // unordered species pairs grouped by their Lennard-Jones well depth
+    int pstart[MAXEPS + 1];
+    int pair_i[NSP * (NSP - 1) / 2], pair_r[NSP * (NSP - 1) / 2];
+    double pair_dinv[NSP * (NSP - 1) / 2];   // pi sigma^2 / ((3/16) sqrt(2 pi k^3 / m_sr))
+    double eps_inv[MAXEPS];      // 1 / sqrt(eps_s eps_r)
+    double eps_powB[MAXEPS];     // sqrt(eps_s eps_r)^B of the collision-integral fit
+    // kinetics (Eqs. 13-15): elementary reactions with explicit colliders, sorted by group
+    int gstart[MAXG + 1];        // reactions of group k: [gstart[k], gstart[k+1])
     double C[MAXR];              // SI pre-exponential factor
     signed char nu_f[MAXR][NSP], nu_b[MAXR][NSP];
-    double g_n[MAXG], g_Ta[MAXG], g_dnu[MAXG];
+    double g_n[MAXG], g_Ta[MAXG];
+    double g_theta_d[MAXG];      // sum_s nu_s E0_s / R_u (K): 0 K reaction energy of the group
     signed char g_nu[MAXG][NSP]; // net stoichiometry nu'' - nu' of the group
+    double g_nud[MAXG][NSP];     // the same, as doubles
     // nondimensionalisation (Eqs. 7, 11)
     double rho_inf, a_inf, T_inf, p_inf, mu_inf, k_inf, cp_inf, gamma_inf, R_inf, T_ref, L_ref,
         Re, Pr;

@@ -41,6 +41,7 @@ struct Scratch {
     // cell centres
     double *ru_c, *rv_c, *T, *p, *H, *u_c, *v_c, *e, *a, *mu_e, *K, *beta, *Tcache;
     double *Y[NSP], *X[NSP], *h[NSP], *Wd[NSP], *W[NSP], *G[NSP];
+    double *esc[NSP], *cvsc[NSP];   // species e, c_v at the cached temperature (Newton predictor)
     double *dudx, *dvdy, *tau_xx, *tau_yy, *Gxx, *Gyy, *mux_c, *mvy_c;
     double *dudy_c, *dvdx_c, *S, *div, *fsw, *raw[8], *filt[8];
     // x-faces
@@ -58,6 +59,7 @@ struct Scratch {
 // Kernel-side view of a grid (passed by value).
 struct GridView {
     int nx, ny, wall, ad, nstate;
+    int predict;                 // Newton starts from a step off the cached species state
     long long off[NSP + 3];
     double Tw_nd;
     double C_mu, C_beta, C_kappa, C_D;
@@ -112,6 +114,8 @@ struct hyp_grid {
     cudaStream_t stream;
     double Tw_nd;
     EventProfile* prof;
+    int cache_valid;             // the closure caches hold a previous evaluation
+    int closure_blocks;          // resident blocks of k_closure on this GPU
     GridView view() const {
         GridView v;
         v.nx = d.nx;
@@ -119,6 +123,7 @@ struct hyp_grid {
         v.wall = cas.wall;
         v.ad = cas.artificial_diffusivity;
         v.nstate = nstate;
+        v.predict = cache_valid;
         for (int i = 0; i < NSP + 3; ++i) v.off[i] = off[i];
         v.Tw_nd = Tw_nd;
         v.C_mu = cas.C_mu;
@@ -415,10 +420,27 @@ __global__ void __launch_bounds__(128) k_closure(GasDev g, GridView v, const dou
 #pragma unroll
             for (int sp = 0; sp < NSP; ++sp) h[sp] = wd[sp] = X[sp] = W[sp] = Wd[sp] = 0.0;
         } else {
+            const double e_si = e * g.a_inf * g.a_inf;
+            double T0 = s.Tcache[idx];
+            if (v.predict) {
+                // one Newton step from the cached species state with the new composition
+                double ec = 0.0, cvc = 0.0;
+#pragma unroll
+                for (int sp = 0; sp < NSP; ++sp) {
+                    ec += Y[sp] * s.esc[sp][idx];
+                    cvc += Y[sp] * s.cvsc[sp][idx];
+                }
+                T0 += (e_si - ec) / cvc;
+            }
             ClosureOut o;
-            closure_si(g, rho * g.rho_inf, e * g.a_inf * g.a_inf, Y, s.Tcache[idx], cneq, cneq, o);
+            closure_si(g, rho * g.rho_inf, e_si, Y, T0, cneq, cneq, o);
             atomic_status(v.status, o.status);
             s.Tcache[idx] = o.T;
+#pragma unroll
+            for (int sp = 0; sp < NSP; ++sp) {
+                s.esc[sp][idx] = o.es[sp];
+                s.cvsc[sp][idx] = o.cvs[sp];
+            }
             T = o.T / g.T_ref;
             p = o.p / (g.rho_inf * g.a_inf * g.a_inf);
             mu = o.mu / g.mu_inf;
@@ -934,7 +956,7 @@ extern "C" int hyp_state_init(const hyp_gas* gas, const hyp_grid_desc* desc, con
     }
 
     // ---------------- device memory ----------------
-    const long long n_c_fields = 13 + 6 * NSP + 8 + 5 + 16;
+    const long long n_c_fields = 13 + 8 * NSP + 8 + 5 + 16;
     const long long n_xf_fields = 2 + 6 * NSP + 8 + 3;
     const long long n_yf_fields = 2 + 6 * NSP + 8;
     const long long n_cn_fields = 8;
@@ -956,6 +978,8 @@ extern "C" int hyp_state_init(const hyp_gas* gas, const hyp_grid_desc* desc, con
                           &S.mu_e, &S.K, &S.beta, &S.Tcache};
     for (double** f : cfields) *f = take(nc);
     for (int sp = 0; sp < NSP; ++sp) {
+        S.esc[sp] = take(nc);
+        S.cvsc[sp] = take(nc);
         S.Y[sp] = take(nc);
         S.X[sp] = take(nc);
         S.h[sp] = take(nc);
@@ -1138,6 +1162,13 @@ extern "C" int hyp_state_init(const hyp_gas* gas, const hyp_grid_desc* desc, con
     HYP_CUDA(cudaMemsetAsync(G->s.SRC, 0, ns_ * sizeof(double), s));
     HYP_CUDA(cudaMemsetAsync(G->status, 0, sizeof(unsigned), s));
     k_fill<<<blocks_for(nc, 256), 256, 0, s>>>(G->s.Tcache, nc, 1000.0);
+    {
+        int dev = 0, sms = 0, per_sm = 0;
+        HYP_CUDA(cudaGetDevice(&dev));
+        HYP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        HYP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_closure, 128, 0));
+        G->closure_blocks = std::max(1, per_sm * sms);
+    }
     HYP_CUDA(cudaGetLastError());
     // host vectors must outlive the async copies
     HYP_CUDA(cudaStreamSynchronize(s));
@@ -1218,8 +1249,10 @@ static int run_rhs(const hyp_gas* gas, hyp_grid* G, const double* U, double* dUd
                                              G->ph_blocks[PH_P1], U, s));
     HYP_CUDA(e1);
     TIMED(KID_FACE_VEL, (k_face_vel<<<blocks_for(d.size(NXF) + d.size(NYF), 256), 256, 0, s>>>(v, U, S)));
-    TIMED(KID_CLOSURE, (k_closure<<<blocks_for(nc, 128), 128, 0, s>>>(g, v, U, S)));
+    const int cb = (int)std::min<long long>(G->closure_blocks, (nc + 127) / 128);
+    TIMED(KID_CLOSURE, (k_closure<<<cb, 128, 0, s>>>(g, v, U, S)));
     HYP_CUDA(cudaGetLastError());
+    G->cache_valid = 1;
     TIMED(KID_LINES_VELGRAD, e1 = launch_lines(G->jobs + G->ph_start[PH_P3], G->ph_count[PH_P3],
                                                G->ph_blocks[PH_P3], U, s));
     HYP_CUDA(e1);
@@ -1404,7 +1437,8 @@ extern "C" int hyp_rhs_noalloc(const hyp_gas* gas, const hyp_grid* grid, const d
     HYP_CUDA(cudaGetLastError());
 
     const GasDev& g = gas->dev;
-    const GridView v = G->view();
+    GridView v = G->view();
+    v.predict = 0;
     const Dims& d = G->d;
     auto lines = [&](int ph, int count) {
         return launch_lines(djobs + G->ph_start[ph], count, G->ph_blocks[ph], U, s);

@@ -1,5 +1,12 @@
 // Per-point thermochemistry closure (Sec. 2.2), FP64, shared by the host set-up code and the
 // kernels of this library. All quantities SI unless stated.
+//
+// On GB300 the FP64 pipe (two FMAs per clock per SM) bounds this code, so it avoids FP64 work
+// that cannot change a result: electronic levels whose Boltzmann factor is below e^-45 of the
+// ground level are not evaluated (relative contribution under 1e-19), the equilibrium constants
+// come from molar partition functions instead of logarithms of Gibbs energies, reactions sharing
+// (n, T_a, net stoichiometry) share their exponentials, and collision-integral terms below e^-40
+// of the fit are skipped.
 #pragma once
 
 #include <math.h>
@@ -13,19 +20,24 @@ constexpr double P_STD = 1.0e5;
 constexpr double T_LO = 50.0;
 constexpr double T_HI = 100000.0;
 constexpr int NEWTON_MAXIT = 60;
-constexpr double NEWTON_RTOL = 1.0e-11;
+// Stop after a Newton step of at most 1e-8 T: the error left after that step is of order
+// (dT/T)^2 ~ 1e-16 relative.
+constexpr double NEWTON_RTOL = 1.0e-8;
 constexpr double SUTH_C1 = 1.458e-6;   // Eq. (24)
 constexpr double SUTH_TS = 110.4;      // Eq. (24)
+constexpr double LEVEL_CUT = 45.0;     // skip electronic levels with theta / T above this
+constexpr double OMEGA_CUT = 40.0;     // skip collision-integral exponentials below e^-40
+// Neufeld-Janzen-Aziz fit of the reduced diffusion collision integral Omega^(1,1)*
+constexpr double NJA_A = 1.06036, NJA_B = 0.15610, NJA_C = 0.19300, NJA_D = 0.47635;
+constexpr double NJA_E = 1.03587, NJA_F = 1.52996, NJA_G = 1.76474, NJA_H = 3.89411;
 
 // Species modal sums at temperature T: energies (J/kg), heat capacities, and the electronic
-// partition function / mean level used by the entropy.
+// partition function / vibrational factor used by the equilibrium constants.
 struct SpeciesState {
     double e[NSP];      // internal energy including formation, J/kg
     double cv[NSP];     // J/(kg K)
     double qel[NSP];    // electronic partition function
-    double m1[NSP];     // Boltzmann mean of theta_el
-    double xv[NSP];     // theta_v / T (molecules)
-    double em1[NSP];    // expm1(theta_v / T) (molecules)
+    double iem1[NSP];   // 1 / expm1(theta_v / T) (molecules): q_vib = 1 + iem1
 };
 
 __host__ __device__ inline void species_state(const GasDev& g, double T, SpeciesState& s) {
@@ -35,28 +47,29 @@ __host__ __device__ inline void species_state(const GasDev& g, double T, Species
         double q = 0.0, m1 = 0.0, m2 = 0.0;
         for (int l = 0; l < g.nlev[i]; ++l) {
             const double th = g.lev_th[i][l];
-            const double w = g.lev_g[i][l] * exp(-th * invT);
+            const double x = th * invT;
+            if (x > LEVEL_CUT) break;
+            const double w = th == 0.0 ? g.lev_g[i][l] : g.lev_g[i][l] * exp(-x);
             q += w;
             m1 += w * th;
             m2 += w * th * th;
         }
-        m1 /= q;
-        m2 /= q;
+        const double iq = 1.0 / q;
+        m1 *= iq;
+        m2 *= iq;
         double eo = 1.5 * T + m1;
         double cvo = 1.5 + (m2 - m1 * m1) * invT * invT;
-        double xv = 0.0, em1 = 0.0;
+        double r = 0.0;
         if (g.linear[i]) {
-            xv = g.theta_v[i] * invT;
-            em1 = expm1(xv);
-            eo += T + g.theta_v[i] / em1;
-            cvo += 1.0 + xv * xv * (em1 + 1.0) / (em1 * em1);
+            const double xv = g.theta_v[i] * invT;
+            r = 1.0 / expm1(xv);
+            eo += T + g.theta_v[i] * r;
+            cvo += 1.0 + xv * xv * (1.0 + r) * r;      // x^2 e^x / (e^x - 1)^2
         }
         s.e[i] = g.e0[i] + g.Rs[i] * eo;
         s.cv[i] = g.Rs[i] * cvo;
         s.qel[i] = q;
-        s.m1[i] = m1;
-        s.xv[i] = xv;
-        s.em1[i] = em1;
+        s.iem1[i] = r;
     }
 }
 
@@ -69,7 +82,7 @@ __host__ __device__ inline double mixture_energy(const GasDev& g, double T, cons
     return e;
 }
 
-// Safeguarded Newton for sum_s Y_s e_s(T) = e, same stopping rule for every caller.
+// Safeguarded Newton for sum_s Y_s e_s(T) = e; s holds the species state at the returned T.
 __host__ __device__ inline double temperature_from_energy(const GasDev& g, double e,
                                                           const double* Y, double T0,
                                                           unsigned& status, SpeciesState& s) {
@@ -117,11 +130,13 @@ struct ClosureOut {
     double wdot[NSP];   // kg/(m^3 s)
     double X[NSP];
     double D[NSP];      // m^2/s
+    double es[NSP];     // species energies at T (J/kg), kept as the next Newton predictor
+    double cvs[NSP];    // species heat capacities at T
     double mu, k;
     unsigned status;
 };
 
-// Full closure (SI). reactions: evaluate w_s; transport: evaluate mu, k, D_s.
+// Full closure (SI). reactions: evaluate w_s; diffusion: evaluate D_s.
 __host__ __device__ inline void closure_si(const GasDev& g, double rho, double e, const double* Y,
                                            double T0, bool reactions, bool diffusion,
                                            ClosureOut& o) {
@@ -136,6 +151,7 @@ __host__ __device__ inline void closure_si(const GasDev& g, double rho, double e
     }
     const double Rmix = R_U * ym;
     const double p = rho * Rmix * T;
+    const double iym = 1.0 / ym;
     o.T = T;
     o.p = p;
     o.cv = cv;
@@ -144,60 +160,69 @@ __host__ __device__ inline void closure_si(const GasDev& g, double rho, double e
 #pragma unroll
     for (int i = 0; i < NSP; ++i) {
         o.h[i] = s.e[i] + g.Rs[i] * T;
-        o.X[i] = Y[i] * g.invM[i] / ym;
+        o.X[i] = Y[i] * g.invM[i] * iym;
+        o.es[i] = s.e[i];
+        o.cvs[i] = s.cv[i];
     }
     const double lnT = log(T);
     const double invT = 1.0 / T;
 
     // ---- kinetics (Eqs. 14, 15) ----
+    // K_c = exp(-sum_s nu_s G_s/(R T)) (p_std/(R T))^dnu with G_s/(R T) = E0_s/(R T) - ln q_s, so
+    // K_c = exp(-theta_d/T) prod_s r_s^nu_s with the molar partition functions
+    // r_s = A_s T^(3/2) q_rot q_vib q_el, and k_b = C T^n exp(-(T_a - theta_d)/T) / prod r_s^nu_s.
 #pragma unroll
     for (int i = 0; i < NSP; ++i) o.wdot[i] = 0.0;
     if (reactions) {
-        double grt[NSP];      // G_s / (R_u T) at p_std
+        const double T15 = T * sqrt(T);
+        double r[NSP];
 #pragma unroll
         for (int i = 0; i < NSP; ++i) {
-            double S = g.s0[i] + 2.5 * lnT + log(s.qel[i]) + s.m1[i] * invT;
-            if (g.linear[i]) S += lnT + s.xv[i] / s.em1[i] - log(-expm1(-s.xv[i]));
-            grt[i] = o.h[i] / (g.Rs[i] * T) - S;
+            double q = g.A_tr[i] * T15 * s.qel[i];
+            if (g.linear[i]) q *= T * g.inv_sr[i] * (1.0 + s.iem1[i]);
+            r[i] = q;
         }
-        const double ln_pref = log(P_STD / (R_U * T));
-        double Ef[MAXG], Eb[MAXG];
+        double conc[NSP], molar[NSP];
+#pragma unroll
+        for (int i = 0; i < NSP; ++i) {
+            conc[i] = rho * Y[i] * g.invM[i];
+            molar[i] = 0.0;
+        }
         for (int k = 0; k < g.ngroup; ++k) {
-            double lnkc = g.g_dnu[k] * ln_pref;
-#pragma unroll
-            for (int i = 0; i < NSP; ++i) lnkc -= g.g_nu[k][i] * grt[i];
-            const double base = g.g_n[k] * lnT - g.g_Ta[k] * invT;
-            Ef[k] = exp(base);
-            Eb[k] = exp(base - lnkc);
-        }
-        double conc[NSP];
-#pragma unroll
-        for (int i = 0; i < NSP; ++i) conc[i] = rho * Y[i] * g.invM[i];
-        double molar[NSP];
-#pragma unroll
-        for (int i = 0; i < NSP; ++i) molar[i] = 0.0;
-        for (int r = 0; r < g.nr; ++r) {
-            double fwd = 1.0, bwd = 1.0;
+            double num = 1.0, den = 1.0;
 #pragma unroll
             for (int i = 0; i < NSP; ++i) {
-                for (int q = 0; q < g.nu_f[r][i]; ++q) fwd *= conc[i];
-                for (int q = 0; q < g.nu_b[r][i]; ++q) bwd *= conc[i];
+                const int nu = g.g_nu[k][i];
+                for (int q = 0; q < nu; ++q) num *= r[i];
+                for (int q = 0; q < -nu; ++q) den *= r[i];
             }
-            const int k = g.group[r];
-            const double R = g.C[r] * Ef[k] * fwd - g.C[r] * Eb[k] * bwd;
+            const double base = g.g_n[k] * lnT;
+            const double Ef = exp(base - g.g_Ta[k] * invT);
+            const double Eb = exp(base - (g.g_Ta[k] - g.g_theta_d[k]) * invT) * den / num;
+            double Rg = 0.0;   // every reaction of a group has the group's net stoichiometry
+            for (int rx = g.gstart[k]; rx < g.gstart[k + 1]; ++rx) {
+                double fwd = 1.0, bwd = 1.0;
 #pragma unroll
-            for (int i = 0; i < NSP; ++i) molar[i] += (g.nu_b[r][i] - g.nu_f[r][i]) * R;
+                for (int i = 0; i < NSP; ++i) {
+                    for (int q = 0; q < g.nu_f[rx][i]; ++q) fwd *= conc[i];
+                    for (int q = 0; q < g.nu_b[rx][i]; ++q) bwd *= conc[i];
+                }
+                Rg += g.C[rx] * (Ef * fwd - Eb * bwd);
+            }
+#pragma unroll
+            for (int i = 0; i < NSP; ++i) molar[i] += g.g_nud[k][i] * Rg;
         }
 #pragma unroll
         for (int i = 0; i < NSP; ++i) o.wdot[i] = g.M[i] * molar[i];
     }
 
-    // ---- transport ----
-    double mu_s[NSP], sq[NSP], k_s[NSP];
+    // ---- transport: Blottner, Eucken, Wilke ----
+    double mu_s[NSP], sq[NSP], isq[NSP], k_s[NSP];
 #pragma unroll
     for (int i = 0; i < NSP; ++i) {
         mu_s[i] = 0.1 * exp((g.blA[i] * lnT + g.blB[i]) * lnT + g.blC[i]);
         sq[i] = sqrt(mu_s[i]);
+        isq[i] = 1.0 / sq[i];
         const double cv_tr = 1.5 * g.Rs[i];
         k_s[i] = mu_s[i] * (2.5 * cv_tr + (s.cv[i] - cv_tr));
     }
@@ -207,34 +232,41 @@ __host__ __device__ inline void closure_si(const GasDev& g, double rho, double e
         double phi = 0.0;
 #pragma unroll
         for (int r = 0; r < NSP; ++r) {
-            const double t = 1.0 + sq[i] / sq[r] * g.wilke_q[i][r];
+            const double t = 1.0 + sq[i] * isq[r] * g.wilke_q[i][r];
             phi += o.X[r] * t * t * g.wilke_d[i][r];
         }
-        mu += o.X[i] * mu_s[i] / phi;
-        kk += o.X[i] * k_s[i] / phi;
+        const double w = o.X[i] / phi;
+        mu += w * mu_s[i];
+        kk += w * k_s[i];
     }
     o.mu = mu;
     o.k = kk;
+
+    // ---- averaged diffusion coefficients (Eq. 19) from Chapman-Enskog binary coefficients ----
 #pragma unroll
     for (int i = 0; i < NSP; ++i) o.D[i] = 0.0;
     if (diffusion) {
-        // Neufeld-Janzen-Aziz fit of Omega^(1,1)* per distinct well depth
-        double om[MAXEPS];
+        double den[NSP];
+#pragma unroll
+        for (int i = 0; i < NSP; ++i) den[i] = 0.0;
+        const double TmB = exp(-NJA_B * lnT);               // T^-B, shared by every well depth
+        const double c = p / (T * sqrt(T));                  // 1/D_sr = c Omega dinv_sr
         for (int q = 0; q < g.neps; ++q) {
-            const double lts = lnT - g.ln_eps[q];
-            const double ts = exp(lts);
-            om[q] = 1.06036 * exp(-0.15610 * lts) + 0.19300 * exp(-0.47635 * ts) +
-                    1.03587 * exp(-1.52996 * ts) + 1.76474 * exp(-3.89411 * ts);
+            const double ts = T * g.eps_inv[q];
+            double om = NJA_A * TmB * g.eps_powB[q];
+            if (NJA_D * ts < OMEGA_CUT) om += NJA_C * exp(-NJA_D * ts);
+            if (NJA_F * ts < OMEGA_CUT) om += NJA_E * exp(-NJA_F * ts);
+            if (NJA_H * ts < OMEGA_CUT) om += NJA_G * exp(-NJA_H * ts);
+            const double com = c * om;
+            for (int pr = g.pstart[q]; pr < g.pstart[q + 1]; ++pr) {
+                const int i = g.pair_i[pr], r = g.pair_r[pr];
+                const double inv_d = com * g.pair_dinv[pr];
+                den[i] += o.X[r] * inv_d;
+                den[r] += o.X[i] * inv_d;
+            }
         }
-        const double c = p / (T * sqrt(T));
 #pragma unroll
-        for (int i = 0; i < NSP; ++i) {
-            double den = 0.0;
-#pragma unroll
-            for (int r = 0; r < NSP; ++r)
-                if (r != i) den += o.X[r] * (c * om[g.eps_group[i][r]] * g.dinv[i][r]);
-            o.D[i] = den != 0.0 ? (1.0 - o.X[i]) / den : 0.0;
-        }
+        for (int i = 0; i < NSP; ++i) o.D[i] = den[i] != 0.0 ? (1.0 - o.X[i]) / den[i] : 0.0;
     }
 }
 
