@@ -35,7 +35,7 @@ STAGES = 3
 L2_FLUSH_BYTES = 256 << 20
 # FP64 operations per cell-centre point executed by k_closure (DADD + DMUL + 2 DFMA), from the
 # ncu instruction counts recorded in profiles/k_closure_sbli.md.
-CLOSURE_FP64_FLOP_PER_POINT = 4123.0
+CLOSURE_FP64_FLOP_PER_POINT = 3177.0
 # DRAM bytes (read + write) per k_closure launch at 2048 x 256 (profiles/k_closure_sbli.md);
 # None while the counters predate the current kernel.
 CLOSURE_DRAM_BYTES = None

@@ -259,13 +259,27 @@ extern "C" int hyp_gas_model_load(const char* path, int kind, const hyp_freestre
         int pos = 0;
         for (int k = 0; k < d.ngroup; ++k) {
             d.gstart[k] = pos;
+            bool first = true;
             for (int r = 0; r < nr; ++r)
                 if (grp[r] == k) {
-                    d.C[pos] = Cs[r];
+                    // the collider: first species on both sides; the rest must match the group's
+                    int spec = -1;
+                    for (int i = 0; i < NSP && spec < 0; ++i)
+                        if (order_f[r * NSP + i] > 0 && order_b[r * NSP + i] > 0) spec = i;
                     for (int i = 0; i < NSP; ++i) {
-                        d.nu_f[pos][i] = (signed char)order_f[r * NSP + i];
-                        d.nu_b[pos][i] = (signed char)order_b[r * NSP + i];
+                        const int rf = order_f[r * NSP + i] - (i == spec);
+                        const int rb = order_b[r * NSP + i] - (i == spec);
+                        if (first) {
+                            d.g_rf[k][i] = (signed char)rf;
+                            d.g_rb[k][i] = (signed char)rb;
+                        } else if (d.g_rf[k][i] != rf || d.g_rb[k][i] != rb) {
+                            delete g;
+                            return fail(HYP_ERR_IO, "reactions of one rate group must differ only in their collider");
+                        }
                     }
+                    first = false;
+                    d.C[pos] = Cs[r];
+                    d.spec[pos] = spec;
                     ++pos;
                 }
         }

@@ -53,7 +53,8 @@ struct GasDev {
     // kinetics (Eqs. 13-15): elementary reactions with explicit colliders, sorted by group
     int gstart[MAXG + 1];        // reactions of group k: [gstart[k], gstart[k+1])
     double C[MAXR];              // SI pre-exponential factor
-    signed char nu_f[MAXR][NSP], nu_b[MAXR][NSP];
+    int spec[MAXR];              // species on both sides of the reaction (collider), -1 if none
+    signed char g_rf[MAXG][NSP], g_rb[MAXG][NSP];   // group reactants / products without collider
     double g_n[MAXG], g_Ta[MAXG];
     double g_theta_d[MAXG];      // sum_s nu_s E0_s / R_u (K): 0 K reaction energy of the group
     signed char g_nu[MAXG][NSP]; // net stoichiometry nu'' - nu' of the group

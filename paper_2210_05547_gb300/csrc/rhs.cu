@@ -41,7 +41,7 @@ struct Scratch {
     // cell centres
     double *ru_c, *rv_c, *T, *p, *H, *u_c, *v_c, *e, *a, *mu_e, *K, *beta, *Tcache;
     double *Y[NSP], *X[NSP], *h[NSP], *Wd[NSP], *W[NSP], *G[NSP];
-    double *esc[NSP], *cvsc[NSP];   // species e, c_v at the cached temperature (Newton predictor)
+    double *esc[NSP], *cvsc[NSP], *cvpc[NSP];   // species e, c_v, dc_v/dT at the cached T
     double *dudx, *dvdy, *tau_xx, *tau_yy, *Gxx, *Gyy, *mux_c, *mvy_c;
     double *dudy_c, *dvdx_c, *S, *div, *fsw, *raw[8], *filt[8];
     // x-faces
@@ -395,19 +395,20 @@ __global__ void __launch_bounds__(128) k_closure(GasDev g, GridView v, const dou
     const bool cneq = g.kind == HYP_GAS_CNEQ;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
         const double rho = U[v.off[0] + idx];
+        const double irho = 1.0 / rho;
         double Y[NSP];
         double rest = rho;
 #pragma unroll
         for (int sp = 1; sp < NSP; ++sp) {
             const double r = U[v.off[sp] + idx];
-            Y[sp] = r / rho;
+            Y[sp] = r * irho;
             rest -= r;
         }
-        Y[0] = rest / rho;
+        Y[0] = rest * irho;
         const double rhoE = U[v.off[NSP] + idx];
-        const double u = s.ru_c[idx] / rho;
-        const double vv = s.rv_c[idx] / rho;
-        const double e = rhoE / rho - 0.5 * (u * u + vv * vv);
+        const double u = s.ru_c[idx] * irho;
+        const double vv = s.rv_c[idx] * irho;
+        const double e = rhoE * irho - 0.5 * (u * u + vv * vv);
         double T, p, mu, k, a;
         double h[NSP], wd[NSP], X[NSP], W[NSP], Wd[NSP];
         if (cpg) {
@@ -423,14 +424,18 @@ __global__ void __launch_bounds__(128) k_closure(GasDev g, GridView v, const dou
             const double e_si = e * g.a_inf * g.a_inf;
             double T0 = s.Tcache[idx];
             if (v.predict) {
-                // one Newton step from the cached species state with the new composition
-                double ec = 0.0, cvc = 0.0;
+                // second-order step from the cached species state with the new composition:
+                // e(Tc + d) ~ ec + cv d + cvp d^2 / 2 = e
+                double ec = 0.0, cvc = 0.0, cvpc = 0.0;
 #pragma unroll
                 for (int sp = 0; sp < NSP; ++sp) {
                     ec += Y[sp] * s.esc[sp][idx];
                     cvc += Y[sp] * s.cvsc[sp][idx];
+                    cvpc += Y[sp] * s.cvpc[sp][idx];
                 }
-                T0 += (e_si - ec) / cvc;
+                const double icv = 1.0 / cvc;
+                const double d1 = (e_si - ec) * icv;
+                T0 += d1 - 0.5 * cvpc * d1 * d1 * icv;
             }
             ClosureOut o;
             closure_si(g, rho * g.rho_inf, e_si, Y, T0, cneq, cneq, o);
@@ -440,6 +445,7 @@ __global__ void __launch_bounds__(128) k_closure(GasDev g, GridView v, const dou
             for (int sp = 0; sp < NSP; ++sp) {
                 s.esc[sp][idx] = o.es[sp];
                 s.cvsc[sp][idx] = o.cvs[sp];
+                s.cvpc[sp][idx] = o.cvps[sp];
             }
             T = o.T / g.T_ref;
             p = o.p / (g.rho_inf * g.a_inf * g.a_inf);
@@ -462,7 +468,7 @@ __global__ void __launch_bounds__(128) k_closure(GasDev g, GridView v, const dou
         }
         s.T[idx] = T;
         s.p[idx] = p;
-        s.H[idx] = (rhoE + p) / rho;
+        s.H[idx] = (rhoE + p) * irho;
         s.u_c[idx] = u;
         s.v_c[idx] = vv;
         s.e[idx] = e;
@@ -956,7 +962,7 @@ extern "C" int hyp_state_init(const hyp_gas* gas, const hyp_grid_desc* desc, con
     }
 
     // ---------------- device memory ----------------
-    const long long n_c_fields = 13 + 8 * NSP + 8 + 5 + 16;
+    const long long n_c_fields = 13 + 9 * NSP + 8 + 5 + 16;
     const long long n_xf_fields = 2 + 6 * NSP + 8 + 3;
     const long long n_yf_fields = 2 + 6 * NSP + 8;
     const long long n_cn_fields = 8;
@@ -980,6 +986,7 @@ extern "C" int hyp_state_init(const hyp_gas* gas, const hyp_grid_desc* desc, con
     for (int sp = 0; sp < NSP; ++sp) {
         S.esc[sp] = take(nc);
         S.cvsc[sp] = take(nc);
+        S.cvpc[sp] = take(nc);
         S.Y[sp] = take(nc);
         S.X[sp] = take(nc);
         S.h[sp] = take(nc);

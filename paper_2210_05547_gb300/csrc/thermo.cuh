@@ -31,45 +31,79 @@ constexpr double OMEGA_CUT = 40.0;     // skip collision-integral exponentials b
 constexpr double NJA_A = 1.06036, NJA_B = 0.15610, NJA_C = 0.19300, NJA_D = 0.47635;
 constexpr double NJA_E = 1.03587, NJA_F = 1.52996, NJA_G = 1.76474, NJA_H = 3.89411;
 
-// Species modal sums at temperature T: energies (J/kg), heat capacities, and the electronic
-// partition function / vibrational factor used by the equilibrium constants.
+// Species modal sums at temperature T: energies (J/kg), heat capacities and their temperature
+// derivative, and the electronic partition function / vibrational factor used by the equilibrium
+// constants, with what a first-order shift in T needs.
 struct SpeciesState {
     double e[NSP];      // internal energy including formation, J/kg
     double cv[NSP];     // J/(kg K)
+    double cvp[NSP];    // d c_v / dT
     double qel[NSP];    // electronic partition function
+    double m1[NSP];     // Boltzmann mean of theta_el (d ln q_el / dT = m1 / T^2)
     double iem1[NSP];   // 1 / expm1(theta_v / T) (molecules): q_vib = 1 + iem1
+    double xv[NSP];     // theta_v / T
 };
 
 __host__ __device__ inline void species_state(const GasDev& g, double T, SpeciesState& s) {
     const double invT = 1.0 / T;
+    const double invT2 = invT * invT;
 #pragma unroll
     for (int i = 0; i < NSP; ++i) {
-        double q = 0.0, m1 = 0.0, m2 = 0.0;
+        double q = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0;
         for (int l = 0; l < g.nlev[i]; ++l) {
             const double th = g.lev_th[i][l];
             const double x = th * invT;
             if (x > LEVEL_CUT) break;
             const double w = th == 0.0 ? g.lev_g[i][l] : g.lev_g[i][l] * exp(-x);
+            const double wt = w * th;
             q += w;
-            m1 += w * th;
-            m2 += w * th * th;
+            m1 += wt;
+            m2 += wt * th;
+            m3 += wt * th * th;
         }
         const double iq = 1.0 / q;
         m1 *= iq;
         m2 *= iq;
+        m3 *= iq;
+        const double var = m2 - m1 * m1;
         double eo = 1.5 * T + m1;
-        double cvo = 1.5 + (m2 - m1 * m1) * invT * invT;
-        double r = 0.0;
+        double cvo = 1.5 + var * invT2;
+        // d/dT of var / T^2 with d m1/dT = var / T^2, d m2/dT = (m3 - m1 m2) / T^2
+        double cvpo = ((m3 - m1 * m2) - 2.0 * m1 * var) * invT2 * invT2 - 2.0 * var * invT2 * invT;
+        double r = 0.0, xv = 0.0;
         if (g.linear[i]) {
-            const double xv = g.theta_v[i] * invT;
+            xv = g.theta_v[i] * invT;
             r = 1.0 / expm1(xv);
+            const double b = (1.0 + r) * r;                  // e^x / (e^x - 1)^2
             eo += T + g.theta_v[i] * r;
-            cvo += 1.0 + xv * xv * (1.0 + r) * r;      // x^2 e^x / (e^x - 1)^2
+            cvo += 1.0 + xv * xv * b;
+            // d/dT [x^2 e^x / (e^x - 1)^2] = -(x / T) x b (2 - x - 2 x r)
+            cvpo -= xv * invT * xv * b * (2.0 - xv - 2.0 * xv * r);
         }
         s.e[i] = g.e0[i] + g.Rs[i] * eo;
         s.cv[i] = g.Rs[i] * cvo;
+        s.cvp[i] = g.Rs[i] * cvpo;
         s.qel[i] = q;
+        s.m1[i] = m1;
         s.iem1[i] = r;
+        s.xv[i] = xv;
+    }
+}
+
+// First-order shift of a species state from T to T + dT (used after a Newton step of at most
+// 1e-8 T, where the neglected second-order terms are below 1e-16 relative).
+__host__ __device__ inline void species_shift(const GasDev& g, double T, double dT, SpeciesState& s) {
+    const double invT = 1.0 / T;
+#pragma unroll
+    for (int i = 0; i < NSP; ++i) {
+        s.e[i] += s.cv[i] * dT;
+        s.cv[i] += s.cvp[i] * dT;
+        s.qel[i] += s.qel[i] * s.m1[i] * invT * invT * dT;
+        if (g.linear[i]) {
+            const double r = s.iem1[i];
+            s.iem1[i] = r + s.xv[i] * invT * (1.0 + r) * r * dT;   // d/dT 1/(e^x - 1)
+            s.xv[i] -= s.xv[i] * invT * dT;
+        }
     }
 }
 
@@ -88,7 +122,6 @@ __host__ __device__ inline double temperature_from_energy(const GasDev& g, doubl
                                                           unsigned& status, SpeciesState& s) {
     double T = fmin(fmax(T0, T_LO), T_HI);
     double lo = T_LO, hi = T_HI;
-    bool converged = false;
     for (int it = 0; it < NEWTON_MAXIT; ++it) {
         species_state(g, T, s);
         double f = -e, cv = 0.0;
@@ -100,14 +133,13 @@ __host__ __device__ inline double temperature_from_energy(const GasDev& g, doubl
         if (f > 0.0) hi = T; else lo = T;
         double Tn = T - f / cv;
         if (fabs(Tn - T) <= NEWTON_RTOL * T) {
-            T = Tn;
-            converged = true;
-            break;
+            species_shift(g, T, Tn - T, s);
+            return Tn;
         }
         if (!(Tn > lo && Tn < hi)) Tn = 0.5 * (lo + hi);
         T = Tn;
     }
-    if (!converged) {
+    {
         const double elo = mixture_energy(g, T_LO, Y);
         const double ehi = mixture_energy(g, T_HI, Y);
         if (e <= elo) {
@@ -132,6 +164,7 @@ struct ClosureOut {
     double D[NSP];      // m^2/s
     double es[NSP];     // species energies at T (J/kg), kept as the next Newton predictor
     double cvs[NSP];    // species heat capacities at T
+    double cvps[NSP];   // their temperature derivatives
     double mu, k;
     unsigned status;
 };
@@ -163,6 +196,7 @@ __host__ __device__ inline void closure_si(const GasDev& g, double rho, double e
         o.X[i] = Y[i] * g.invM[i] * iym;
         o.es[i] = s.e[i];
         o.cvs[i] = s.cv[i];
+        o.cvps[i] = s.cvp[i];
     }
     const double lnT = log(T);
     const double invT = 1.0 / T;
@@ -189,26 +223,24 @@ __host__ __device__ inline void closure_si(const GasDev& g, double rho, double e
             molar[i] = 0.0;
         }
         for (int k = 0; k < g.ngroup; ++k) {
-            double num = 1.0, den = 1.0;
+            double num = 1.0, den = 1.0, fwd = 1.0, bwd = 1.0;
 #pragma unroll
             for (int i = 0; i < NSP; ++i) {
                 const int nu = g.g_nu[k][i];
                 for (int q = 0; q < nu; ++q) num *= r[i];
                 for (int q = 0; q < -nu; ++q) den *= r[i];
+                for (int q = 0; q < g.g_rf[k][i]; ++q) fwd *= conc[i];
+                for (int q = 0; q < g.g_rb[k][i]; ++q) bwd *= conc[i];
             }
+            // the group's reactions differ only in the collider, a species present on both sides:
+            // R_group = (sum_r C_r [M_r]) (k_f prod [reactants] - k_b prod [products]) / C factors
+            double w = 0.0;
+            for (int rx = g.gstart[k]; rx < g.gstart[k + 1]; ++rx)
+                w += g.C[rx] * (g.spec[rx] >= 0 ? conc[g.spec[rx]] : 1.0);
             const double base = g.g_n[k] * lnT;
             const double Ef = exp(base - g.g_Ta[k] * invT);
             const double Eb = exp(base - (g.g_Ta[k] - g.g_theta_d[k]) * invT) * den / num;
-            double Rg = 0.0;   // every reaction of a group has the group's net stoichiometry
-            for (int rx = g.gstart[k]; rx < g.gstart[k + 1]; ++rx) {
-                double fwd = 1.0, bwd = 1.0;
-#pragma unroll
-                for (int i = 0; i < NSP; ++i) {
-                    for (int q = 0; q < g.nu_f[rx][i]; ++q) fwd *= conc[i];
-                    for (int q = 0; q < g.nu_b[rx][i]; ++q) bwd *= conc[i];
-                }
-                Rg += g.C[rx] * (Ef * fwd - Eb * bwd);
-            }
+            const double Rg = w * (Ef * fwd - Eb * bwd);
 #pragma unroll
             for (int i = 0; i < NSP; ++i) molar[i] += g.g_nud[k][i] * Rg;
         }
