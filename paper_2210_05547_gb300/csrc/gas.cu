@@ -163,7 +163,8 @@ extern "C" int hyp_gas_model_load(const char* path, int kind, const hyp_freestre
     }
     for (int i = 0; i < NSP; ++i)
         for (int j = 0; j < NSP; ++j) {
-            d.wilke_q[i][j] = pow(sp[j].M / sp[i].M, 0.25);
+            d.Mq[i] = pow(sp[i].M, 0.25);
+            d.iMq[i] = 1.0 / d.Mq[i];
             d.wilke_d[i][j] = 1.0 / sqrt(8.0 * (1.0 + sp[i].M / sp[j].M));
         }
     // unordered pairs grouped by well depth: one collision integral per distinct depth

@@ -14,6 +14,7 @@
 #define MAXG 12                // reaction groups sharing (n, T_a, net stoichiometry)
 #define MAXLEV 6               // electronic levels per species
 #define MAXEPS 16              // distinct Lennard-Jones well depths of species pairs
+#define LINE_BLOCK 128         // threads per block of the line-operator kernel
 
 namespace hyp {
 
@@ -42,7 +43,7 @@ struct GasDev {
     double inv_sr[NSP];          // 1 / (sigma theta_r) for linear molecules
     // transport
     double blA[NSP], blB[NSP], blC[NSP];
-    double wilke_q[NSP][NSP];    // (M_r / M_s)^(1/4)
+    double Mq[NSP], iMq[NSP];    // M_s^(1/4) and its reciprocal (Wilke's rule)
     double wilke_d[NSP][NSP];    // 1 / sqrt(8 (1 + M_s / M_r))
     // unordered species pairs grouped by their Lennard-Jones well depth
     int pstart[MAXEPS + 1];
@@ -88,6 +89,9 @@ struct LineOp {
     const double* lower;         // device: sub-diagonal of each row
     const double* cprime;        // device: Thomas c'
     const double* minv;          // device: Thomas 1 / pivot
+    const double* wa;            // device, interior rows: weight of (f_{+1/2} +/- f_{-1/2}) / pivot
+    const double* wb;            // device, interior rows: weight of (f_{+3/2} +/- f_{-3/2}) / pivot
+    const double* lm;            // device: sub-diagonal / pivot
     int ncl;                     // closure rows (<= 4)
     int crow[4], cstart[4], cnum[4];
     double cw[4][5];
@@ -104,7 +108,7 @@ struct LineJob {
     int nlines;
     int nseg;                    // segments per line (power of two dividing the block size)
     double wall_value;
-    double scale;
+    double scale;                // +1 or -1
     const double* metric;        // per output element along the line, nullable
 };
 

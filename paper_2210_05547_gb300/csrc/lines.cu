@@ -21,14 +21,9 @@
 namespace hyp {
 namespace {
 
-__device__ __forceinline__ double row_rhs(const LineOp& op, const double* __restrict__ in,
-                                          long long ies, int r, int base, double wall, int& c) {
-    if (r >= op.first_interior && r <= op.last_interior) {
-        const double* p = in + (long long)(r + base) * ies;
-        const double p0 = p[0], p1 = p[ies], p2 = p[2 * ies], p3 = p[3 * ies];
-        if (op.kind == 0) return op.wi[1] * (p1 + p2) + op.wi[0] * (p0 + p3);
-        return op.wi[2] * (p2 - p1) + op.wi[3] * (p3 - p0);
-    }
+__device__ __forceinline__ double closure_rhs(const LineOp& op, const double* __restrict__ in,
+                                              long long ies, int r, double wall) {
+    int c = 0;
     while (op.crow[c] != r) ++c;
     double v = op.gw[c] * wall;
     const double* p = in + (long long)op.cstart[c] * ies;
@@ -36,7 +31,7 @@ __device__ __forceinline__ double row_rhs(const LineOp& op, const double* __rest
     return v;
 }
 
-__global__ void __launch_bounds__(128) k_lines(const LineJob* __restrict__ jobs,
+__global__ void __launch_bounds__(LINE_BLOCK) k_lines(const LineJob* __restrict__ jobs,
                                                const double* __restrict__ U) {
     const LineJob& J = jobs[blockIdx.y];
     const int nseg = J.nseg;
@@ -59,13 +54,53 @@ __global__ void __launch_bounds__(128) k_lines(const LineJob* __restrict__ jobs,
     const double* __restrict__ lower = op.lower;
     const double* __restrict__ minv = op.minv;
     const double* __restrict__ cpr = op.cprime;
+    const int fi = op.first_interior, li = op.last_interior;
     if (active && s <= e) {
-        int c = 0;
         const int fs = max(0, s - W);
         double d = 0.0;
-        for (int r = fs; r <= e; ++r) {
-            const double rhs = row_rhs(op, in, ies, r, base, J.wall_value, c);
-            d = (rhs - lower[r] * d) * minv[r];
+        int r = fs;
+        // left closure rows
+        for (; r <= e && r < fi; ++r) {
+            d = (closure_rhs(op, in, ies, r, J.wall_value) - lower[r] * d) * minv[r];
+            if (r >= s) tmp[(long long)r * oes] = d;
+        }
+        // interior rows: a sliding window of the four inputs, one new load per row, weights
+        // already divided by the pivot
+        const int ie = min(e, li);
+        if (r <= ie) {
+            const double* p = in + (long long)(r + base) * ies;
+            double p0 = p[0], p1 = p[ies], p2 = p[2 * ies];
+            p += 3 * ies;
+            const double* __restrict__ wa = op.wa;
+            const double* __restrict__ wb = op.wb;
+            const double* __restrict__ lm = op.lm;
+            if (op.kind == 0) {
+#pragma unroll 4
+                for (; r <= ie; ++r) {
+                    const double p3 = *p;
+                    p += ies;
+                    d = fma(-lm[r], d, fma(wa[r], p1 + p2, wb[r] * (p0 + p3)));
+                    if (r >= s) tmp[(long long)r * oes] = d;
+                    p0 = p1;
+                    p1 = p2;
+                    p2 = p3;
+                }
+            } else {
+#pragma unroll 4
+                for (; r <= ie; ++r) {
+                    const double p3 = *p;
+                    p += ies;
+                    d = fma(-lm[r], d, fma(wa[r], p2 - p1, wb[r] * (p3 - p0)));
+                    if (r >= s) tmp[(long long)r * oes] = d;
+                    p0 = p1;
+                    p1 = p2;
+                    p2 = p3;
+                }
+            }
+        }
+        // right closure rows
+        for (; r <= e; ++r) {
+            d = (closure_rhs(op, in, ies, r, J.wall_value) - lower[r] * d) * minv[r];
             if (r >= s) tmp[(long long)r * oes] = d;
         }
     }
@@ -73,19 +108,32 @@ __global__ void __launch_bounds__(128) k_lines(const LineJob* __restrict__ jobs,
     if (active && s <= e) {
         const int be = min(e + W, m - 1);
         const double* __restrict__ met = J.metric;
-        const double sc = J.scale;
+        const bool neg = J.scale < 0.0;
         double y = tmp[(long long)be * oes];
         if (be <= e) {
-            double v = sc * y;
-            if (met) v *= met[be];
-            out[(long long)be * oes] = v;
+            const double v = met ? y * met[be] : y;
+            out[(long long)be * oes] = neg ? -v : v;
         }
-        for (int r = be - 1; r >= s; --r) {
-            y = tmp[(long long)r * oes] - cpr[r] * y;
-            if (r <= e) {
-                double v = sc * y;
-                if (met) v *= met[r];
-                out[(long long)r * oes] = v;
+        int r = be - 1;
+        // warm-up rows beyond the segment
+        for (; r > e; --r) y = tmp[(long long)r * oes] - cpr[r] * y;
+        if (met && neg) {
+#pragma unroll 4
+            for (; r >= s; --r) {
+                y = tmp[(long long)r * oes] - cpr[r] * y;
+                out[(long long)r * oes] = -y * met[r];
+            }
+        } else if (met) {
+#pragma unroll 4
+            for (; r >= s; --r) {
+                y = tmp[(long long)r * oes] - cpr[r] * y;
+                out[(long long)r * oes] = y * met[r];
+            }
+        } else {
+#pragma unroll 4
+            for (; r >= s; --r) {
+                y = tmp[(long long)r * oes] - cpr[r] * y;
+                out[(long long)r * oes] = neg ? -y : y;
             }
         }
     }
@@ -96,7 +144,7 @@ __global__ void __launch_bounds__(128) k_lines(const LineJob* __restrict__ jobs,
 cudaError_t launch_lines(const LineJob* d_jobs, int njobs, int max_blocks, const double* U,
                          cudaStream_t s) {
     if (njobs == 0) return cudaSuccess;
-    dim3 block(128);
+    dim3 block(LINE_BLOCK);
     dim3 grid(max_blocks, njobs);
     k_lines<<<grid, block, 0, s>>>(d_jobs, U);
     return cudaGetLastError();

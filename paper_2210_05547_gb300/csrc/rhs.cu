@@ -68,7 +68,7 @@ struct GridView {
 };
 
 enum Phase {
-    PH_P1, PH_P3, PH_AD1, PH_AD2, PH_MU1, PH_MU2, PH_FACE, PH_DIV, PH_COUNT
+    PH_P1, PH_P3, PH_AD1, PH_AD2, PH_MU1, PH_MU2, PH_FACE, PH_FACEB, PH_DIV, PH_COUNT
 };
 
 // Launches of one right-hand side, as reported by the optional event profile.
@@ -115,6 +115,8 @@ struct hyp_grid {
     double Tw_nd;
     EventProfile* prof;
     int cache_valid;             // the closure caches hold a previous evaluation
+    cudaStream_t side;           // second stream for phases that do not wait on the closure
+    cudaEvent_t fork[2], join[2];
     int closure_blocks;          // resident blocks of k_closure on this GPU
     GridView view() const {
         GridView v;
@@ -366,14 +368,22 @@ LineOp make_op(int kind, int dir, int n, int wall, std::vector<double>& data) {
         mi[r] = 1.0 / piv;
         cp[r] = upper[r] * mi[r];
     }
+    // interior weights folded with the pivot: d_r = wa_r (f1 +/- f0) + wb_r (f3 +/- f_-1) - lm_r d_{r-1}
+    std::vector<double> wa(m), wb(m), lm(m);
+    for (int r = 0; r < m; ++r) {
+        wa[r] = (kind == 0 ? op.wi[1] : op.wi[2]) * mi[r];
+        wb[r] = (kind == 0 ? op.wi[0] : op.wi[3]) * mi[r];
+        lm[r] = lower[r] * mi[r];
+    }
     // store offsets into data (fixed up to device pointers later)
     const size_t base = data.size();
-    data.insert(data.end(), lower.begin(), lower.end());
-    data.insert(data.end(), cp.begin(), cp.end());
-    data.insert(data.end(), mi.begin(), mi.end());
+    for (auto* v : {&lower, &cp, &mi, &wa, &wb, &lm}) data.insert(data.end(), v->begin(), v->end());
     op.lower = (const double*)(base);
     op.cprime = (const double*)(base + m);
     op.minv = (const double*)(base + 2 * m);
+    op.wa = (const double*)(base + 3 * m);
+    op.wb = (const double*)(base + 4 * m);
+    op.lm = (const double*)(base + 5 * m);
     return op;
 }
 
@@ -745,11 +755,14 @@ struct PlanBuilder {
         out_size.push_back(d.size(tout));
         ph_count[cur]++;
     }
-    // Segment counts (about 129 points per segment, more segments when a phase has too few
+    // Segment counts (at most 260 points per segment, more segments when a phase has too few
     // threads to occupy the GPU), forward-sweep storage and block counts per phase. Returns the
     // tmp doubles needed by the largest phase.
     long long finish() {
         long long need = 0;
+        long long face_need = 0;
+        for (int k = ph_start[PH_FACE]; k < ph_start[PH_FACE] + ph_count[PH_FACE]; ++k)
+            face_need += out_size[k];
         for (int ph = 0; ph < PH_COUNT; ++ph) {
             const int a = ph_start[ph], b = a + ph_count[ph];
             std::vector<int> nseg(ph_count[ph]);
@@ -757,7 +770,7 @@ struct PlanBuilder {
             for (int k = a; k < b; ++k) {
                 const int m = jobs[k].nseg;
                 int ns = 1;
-                while (ns < 64 && (m + ns - 1) / ns > 129) ns *= 2;
+                while (ns < LINE_BLOCK / 2 && (m + ns - 1) / ns > 260) ns *= 2;
                 nseg[k - a] = ns;
                 threads += (long long)jobs[k].nlines * ns;
             }
@@ -766,7 +779,7 @@ struct PlanBuilder {
                 threads = 0;
                 for (int k = a; k < b; ++k) {
                     const int m = jobs[k].nseg;
-                    if (nseg[k - a] < 64 && (m + 2 * nseg[k - a] - 1) / (2 * nseg[k - a]) >= 32) {
+                    if (nseg[k - a] < LINE_BLOCK / 2 && (m + 2 * nseg[k - a] - 1) / (2 * nseg[k - a]) >= 32) {
                         nseg[k - a] *= 2;
                         grew = true;
                     }
@@ -774,12 +787,14 @@ struct PlanBuilder {
                 }
                 if (!grew) break;
             }
-            long long off = 0;
+            // phases that run beside the face phase on the second stream take storage past it
+            const bool beside_face = ph == PH_MU1 || ph == PH_MU2 || ph == PH_FACEB;
+            long long off = beside_face ? face_need : 0;
             for (int k = a; k < b; ++k) {
                 jobs[k].nseg = nseg[k - a];
                 jobs[k].tmp = (double*)(size_t)off;   // relative; fixed up by the caller
                 off += out_size[k];
-                const int lpb = 128 / jobs[k].nseg;
+                const int lpb = LINE_BLOCK / jobs[k].nseg;
                 ph_blocks[ph] = std::max(ph_blocks[ph], (jobs[k].nlines + lpb - 1) / lpb);
             }
             need = std::max(need, off);
@@ -821,6 +836,11 @@ static void free_grid(hyp_grid* G) {
     cudaFree(G->opdata);
     cudaFree(G->jobs);
     cudaFree(G->linetmp);
+    if (G->side) cudaStreamDestroy(G->side);
+    for (int k = 0; k < 2; ++k) {
+        if (G->fork[k]) cudaEventDestroy(G->fork[k]);
+        if (G->join[k]) cudaEventDestroy(G->join[k]);
+    }
     if (G->prof) {
         for (auto e : G->prof->ev) cudaEventDestroy(e);
         delete G->prof;
@@ -1067,6 +1087,9 @@ extern "C" int hyp_state_init(const hyp_gas* gas, const hyp_grid_desc* desc, con
         op.lower = G->opdata + (size_t)op.lower;
         op.cprime = G->opdata + (size_t)op.cprime;
         op.minv = G->opdata + (size_t)op.minv;
+        op.wa = G->opdata + (size_t)op.wa;
+        op.wb = G->opdata + (size_t)op.wb;
+        op.lm = G->opdata + (size_t)op.lm;
     }
     // plans
     PlanBuilder B;
@@ -1112,12 +1135,13 @@ extern "C" int hyp_state_init(const hyp_gas* gas, const hyp_grid_desc* desc, con
     B.add(OX_ICF, S.tau_xx, NC, S.txx_x, NXF, nullptr);
     B.add(OX_ICF, S.v_c, NC, S.v_x, NXF, nullptr);
     B.add(OX_DCF, S.T, NC, S.dTdx, NXF, G->xi_f);
-    B.add(OY_IFC, S.tau_xy, NCN, S.txy_x, NXF, nullptr);
     B.add(OY_ICF, S.H, NC, S.Hy, NYF, nullptr);
     B.add(OY_ICF, S.K, NC, S.Ky, NYF, nullptr);
     B.add(OY_ICF, S.tau_yy, NC, S.tyy_y, NYF, nullptr);
     B.add(y_icf_u, S.u_c, NC, S.u_y, NYF, nullptr, 1.0, 0.0);
     B.add(wall ? OY_DCFW : OY_DCF, S.T, NC, S.dTdy, NYF, G->eta_f, 1.0, G->Tw_nd);
+    B.begin(PH_FACEB);
+    B.add(OY_IFC, S.tau_xy, NCN, S.txy_x, NXF, nullptr);
     B.add(OX_IFC, S.tau_xy, NCN, S.txy_y, NYF, nullptr);
     B.begin(PH_DIV);
     for (int sp = 1; sp < NSP; ++sp) {
@@ -1169,6 +1193,11 @@ extern "C" int hyp_state_init(const hyp_gas* gas, const hyp_grid_desc* desc, con
     HYP_CUDA(cudaMemsetAsync(G->s.SRC, 0, ns_ * sizeof(double), s));
     HYP_CUDA(cudaMemsetAsync(G->status, 0, sizeof(unsigned), s));
     k_fill<<<blocks_for(nc, 256), 256, 0, s>>>(G->s.Tcache, nc, 1000.0);
+    HYP_CUDA(cudaStreamCreateWithFlags(&G->side, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; ++k) {
+        HYP_CUDA(cudaEventCreateWithFlags(&G->fork[k], cudaEventDisableTiming));
+        HYP_CUDA(cudaEventCreateWithFlags(&G->join[k], cudaEventDisableTiming));
+    }
     {
         int dev = 0, sms = 0, per_sm = 0;
         HYP_CUDA(cudaGetDevice(&dev));
@@ -1235,12 +1264,13 @@ static void prof_end(hyp_grid* G, int slot, cudaStream_t s) {
     if (slot >= 0) cudaEventRecord(G->prof->ev[slot + 1], s);
 }
 
-#define TIMED(kid, ...)                               \
+#define TIMED_ON(st, kid, ...)                        \
     do {                                              \
-        const int _slot = prof_begin(G, kid, s);      \
+        const int _slot = prof_begin(G, kid, st);     \
         __VA_ARGS__;                                  \
-        prof_end(G, _slot, s);                        \
+        prof_end(G, _slot, st);                       \
     } while (0)
+#define TIMED(kid, ...) TIMED_ON(s, kid, __VA_ARGS__)
 
 // The whole right-hand side; with rk != 0 the assemble step performs the stage update instead
 // of writing dUdt.
@@ -1256,19 +1286,27 @@ static int run_rhs(const hyp_gas* gas, hyp_grid* G, const double* U, double* dUd
                                              G->ph_blocks[PH_P1], U, s));
     HYP_CUDA(e1);
     TIMED(KID_FACE_VEL, (k_face_vel<<<blocks_for(d.size(NXF) + d.size(NYF), 256), 256, 0, s>>>(v, U, S)));
+    // fork: velocity gradients and the artificial-diffusivity line phases do not need the closure
+    cudaStream_t s2 = G->side;
+    HYP_CUDA(cudaEventRecord(G->fork[0], s));
+    HYP_CUDA(cudaStreamWaitEvent(s2, G->fork[0], 0));
     const int cb = (int)std::min<long long>(G->closure_blocks, (nc + 127) / 128);
     TIMED(KID_CLOSURE, (k_closure<<<cb, 128, 0, s>>>(g, v, U, S)));
     HYP_CUDA(cudaGetLastError());
     G->cache_valid = 1;
-    TIMED(KID_LINES_VELGRAD, e1 = launch_lines(G->jobs + G->ph_start[PH_P3], G->ph_count[PH_P3],
-                                               G->ph_blocks[PH_P3], U, s));
+    TIMED_ON(s2, KID_LINES_VELGRAD, e1 = launch_lines(G->jobs + G->ph_start[PH_P3], G->ph_count[PH_P3],
+                                                      G->ph_blocks[PH_P3], U, s2));
     HYP_CUDA(e1);
     if (v.ad) {
-        TIMED(KID_LINES_AD, e1 = launch_lines(G->jobs + G->ph_start[PH_AD1], 2, G->ph_blocks[PH_AD1], U, s));
+        TIMED_ON(s2, KID_LINES_AD, e1 = launch_lines(G->jobs + G->ph_start[PH_AD1], 2, G->ph_blocks[PH_AD1], U, s2));
         HYP_CUDA(e1);
-        TIMED(KID_LINES_AD, e1 = launch_lines(G->jobs + G->ph_start[PH_AD2], 2, G->ph_blocks[PH_AD2], U, s));
+        TIMED_ON(s2, KID_LINES_AD, e1 = launch_lines(G->jobs + G->ph_start[PH_AD2], 2, G->ph_blocks[PH_AD2], U, s2));
         HYP_CUDA(e1);
-        TIMED(KID_AD_PREP, (k_ad_prep<<<blocks_for(nc, 256), 256, 0, s>>>(v, S)));
+        TIMED_ON(s2, KID_AD_PREP, (k_ad_prep<<<blocks_for(nc, 256), 256, 0, s2>>>(v, S)));
+    }
+    HYP_CUDA(cudaEventRecord(G->join[0], s2));
+    HYP_CUDA(cudaStreamWaitEvent(s, G->join[0], 0));
+    if (v.ad) {
         TIMED(KID_AD_RAW, (k_ad_raw<<<blocks_for(nc, 256), 256, 0, s>>>(g, v, U, S)));
         dim3 gg(blocks_for(nc, 256), 8);
         TIMED(KID_AD_GAUSS, (k_gauss<<<gg, 256, 0, s>>>(v, S, 0)));
@@ -1277,14 +1315,22 @@ static int run_rhs(const hyp_gas* gas, hyp_grid* G, const double* U, double* dUd
         HYP_CUDA(cudaGetLastError());
     }
     TIMED(KID_STRESS_C, (k_stress_c<<<blocks_for(nc, 256), 256, 0, s>>>(v, S)));
-    TIMED(KID_LINES_MU, e1 = launch_lines(G->jobs + G->ph_start[PH_MU1], 1, G->ph_blocks[PH_MU1], U, s));
+    // fork: viscosity to the corners, shear stress and its face interpolants beside the face phase
+    HYP_CUDA(cudaEventRecord(G->fork[1], s));
+    HYP_CUDA(cudaStreamWaitEvent(s2, G->fork[1], 0));
+    TIMED_ON(s2, KID_LINES_MU, e1 = launch_lines(G->jobs + G->ph_start[PH_MU1], 1, G->ph_blocks[PH_MU1], U, s2));
     HYP_CUDA(e1);
-    TIMED(KID_LINES_MU, e1 = launch_lines(G->jobs + G->ph_start[PH_MU2], 1, G->ph_blocks[PH_MU2], U, s));
+    TIMED_ON(s2, KID_LINES_MU, e1 = launch_lines(G->jobs + G->ph_start[PH_MU2], 1, G->ph_blocks[PH_MU2], U, s2));
     HYP_CUDA(e1);
-    TIMED(KID_STRESS_CN, (k_stress_cn<<<blocks_for(d.size(NCN), 256), 256, 0, s>>>(v, S)));
+    TIMED_ON(s2, KID_STRESS_CN, (k_stress_cn<<<blocks_for(d.size(NCN), 256), 256, 0, s2>>>(v, S)));
+    TIMED_ON(s2, KID_LINES_FACE, e1 = launch_lines(G->jobs + G->ph_start[PH_FACEB], G->ph_count[PH_FACEB],
+                                                   G->ph_blocks[PH_FACEB], U, s2));
+    HYP_CUDA(e1);
+    HYP_CUDA(cudaEventRecord(G->join[1], s2));
     TIMED(KID_LINES_FACE, e1 = launch_lines(G->jobs + G->ph_start[PH_FACE], G->ph_count[PH_FACE],
                                             G->ph_blocks[PH_FACE], U, s));
     HYP_CUDA(e1);
+    HYP_CUDA(cudaStreamWaitEvent(s, G->join[1], 0));
     TIMED(KID_FLUX, (k_flux<<<blocks_for(d.size(NXF), 128), 128, 0, s>>>(v, U, S, 0)));
     TIMED(KID_FLUX, (k_flux<<<blocks_for(d.size(NYF), 128), 128, 0, s>>>(v, U, S, 1)));
     TIMED(KID_LINES_DIV, e1 = launch_lines(G->jobs + G->ph_start[PH_DIV], G->ph_count[PH_DIV],
@@ -1471,6 +1517,7 @@ extern "C" int hyp_rhs_noalloc(const hyp_gas* gas, const hyp_grid* grid, const d
     HYP_CUDA(lines(PH_MU2, 1));
     k_stress_cn<<<blocks_for(d.size(NCN), 256), 256, 0, s>>>(v, S);
     HYP_CUDA(lines(PH_FACE, G->ph_count[PH_FACE]));
+    HYP_CUDA(lines(PH_FACEB, G->ph_count[PH_FACEB]));
     k_flux<<<blocks_for(d.size(NXF), 128), 128, 0, s>>>(v, U, S, 0);
     k_flux<<<blocks_for(d.size(NYF), 128), 128, 0, s>>>(v, U, S, 1);
     HYP_CUDA(lines(PH_DIV, G->ph_count[PH_DIV]));

@@ -249,12 +249,15 @@ __host__ __device__ inline void closure_si(const GasDev& g, double rho, double e
     }
 
     // ---- transport: Blottner, Eucken, Wilke ----
-    double mu_s[NSP], sq[NSP], isq[NSP], k_s[NSP];
+    // sqrt(mu_i / mu_r) (M_r / M_i)^(1/4) = a_i b_r with a_i = sqrt(mu_i) M_i^(-1/4),
+    // b_r = M_r^(1/4) / sqrt(mu_r)
+    double mu_s[NSP], a[NSP], b[NSP], k_s[NSP];
 #pragma unroll
     for (int i = 0; i < NSP; ++i) {
         mu_s[i] = 0.1 * exp((g.blA[i] * lnT + g.blB[i]) * lnT + g.blC[i]);
-        sq[i] = sqrt(mu_s[i]);
-        isq[i] = 1.0 / sq[i];
+        const double sq = sqrt(mu_s[i]);
+        a[i] = sq * g.iMq[i];
+        b[i] = g.Mq[i] / sq;
         const double cv_tr = 1.5 * g.Rs[i];
         k_s[i] = mu_s[i] * (2.5 * cv_tr + (s.cv[i] - cv_tr));
     }
@@ -264,7 +267,7 @@ __host__ __device__ inline void closure_si(const GasDev& g, double rho, double e
         double phi = 0.0;
 #pragma unroll
         for (int r = 0; r < NSP; ++r) {
-            const double t = 1.0 + sq[i] * isq[r] * g.wilke_q[i][r];
+            const double t = 1.0 + a[i] * b[r];
             phi += o.X[r] * t * t * g.wilke_d[i][r];
         }
         const double w = o.X[i] / phi;
