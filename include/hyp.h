@@ -17,8 +17,9 @@
  * - Ownership: the caller owns every field buffer it passes (state, right-hand side, the
  *   thermo_eval inputs and outputs). The library owns the opaque handles and everything inside
  *   them (gas tables, metrics, sponge, reference state, scratch), and frees them in *_free.
- * - Floating point: FP64 throughout (precision argument HYP_FP64). No call falls back to the
- *   CPU: every arithmetic step of rhs / rk_stage / thermo_eval runs in CUDA kernels.
+ * - Floating point: FP64 throughout with precision HYP_FP64; HYP_MIXED moves the parts listed at
+ *   enum hyp_precision to binary32. No call falls back to the CPU: every arithmetic step of
+ *   rhs / rk_stage / thermo_eval runs in CUDA kernels.
  * - A grid handle carries scratch memory: calls that use the same grid (rhs, rk_stage) must not
  *   overlap on the device; serialise them on one stream.
  *
@@ -46,7 +47,11 @@ enum hyp_gas_kind {
     HYP_GAS_CPG = 2      /* calorically perfect gas, Sutherland viscosity (Eqs. 22, 24) */
 };
 
-enum hyp_precision { HYP_FP64 = 0 };
+/* HYP_FP64: every step in binary64. HYP_MIXED: the transport and diffusion coefficients (Blottner,
+ * Eucken, Wilke, Chapman-Enskog; Sec. 2.2.1, Eq. 19) and the forward-rate exponentials (Eq. 13) in
+ * binary32; temperature inversion, species thermodynamics, equilibrium constants and backward
+ * rates, the derivative operators, fluxes and the stage update in binary64. */
+enum hyp_precision { HYP_FP64 = 0, HYP_MIXED = 1 };
 
 enum hyp_error {
     HYP_OK = 0,
@@ -156,6 +161,21 @@ int hyp_rhs(const hyp_gas* gas, const hyp_grid* grid, const double* U, double* d
  * dQ <- A_k dQ + dt R(U); U <- U + B_k dQ with A = (0, -5/9, -153/128), B = (1/3, 15/16, 8/15),
  * on the registers given to hyp_state_init. dt nondimensional (time unit L_ref / a_inf). */
 int hyp_rk_stage(hyp_state* st, int stage, double dt, int precision, void* stream);
+
+/* Wall heat flux and wall shear stress of state U (nondimensional, Eq. 7): evaluates the
+ * right-hand side on U with the grid's scratch (the result is discarded) and writes
+ * q_w[i] = -K dT/dy at the nx wall faces (Eq. 10, K including the artificial conductivity) and
+ * tau_w[i] = tau_xy at the nx + 1 wall corners (Eq. 9). U: DEVICE, hyp_state_size() doubles;
+ * q_w[nx], tau_w[nx+1]: DEVICE, caller-owned. Skin friction C_f = 2 tau_w / Ma_inf^2.
+ * HYP_ERR_ARG if the case has no wall. Uses the grid's scratch like hyp_rhs. */
+int hyp_wall_fluxes(const hyp_gas* gas, const hyp_grid* grid, const double* U, double* q_w,
+                    double* tau_w, int precision, void* stream);
+
+/* The binary64 -> binary32 rounding (nearest, ties to even; magnitudes below 1.18e-38 to signed
+ * zero) and the exact widening back that HYP_MIXED uses between its binary64 and binary32
+ * parts, done with integer instructions. x[n]: DEVICE input; y[n] (binary32) and back[n]
+ * (binary64): DEVICE outputs, each nullable. */
+int hyp_round_f32(int64_t n, const double* x, float* y, double* back, void* stream);
 
 /* Pointwise closure of Sec. 2.2 in SI units for n independent states (the work the paper hands
  * to its real-gas library, Sec. 3.4). Inputs (DEVICE): rho[n] kg/m^3, e[n] J/kg internal energy

@@ -19,6 +19,7 @@ GAS_KINDS = {"cneq": 0, "frozen": 1, "cpg": 2}
 STRETCH = {"uniform": 0, "tanh": 1, "cubic": 2}
 FLOWS = {"bl": 0, "sbli": 1}
 FP64 = 0
+MIXED = 1
 TABLE_AIR5 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data", "air5.dat")
 SCALE_NAMES = ("rho_inf", "a_inf", "T_inf", "p_inf", "mu_inf", "k_inf", "cp_inf", "gamma_inf",
                "R_inf", "T_ref", "L_ref", "Re", "Pr")
@@ -70,6 +71,8 @@ EXPORTS = {
     "hyp_thermo_eval": (_I, [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I, _P]),
     "hyp_thermo_energy": (_I, [_P, _I64, _P, _P, _P, _P]),
     "hyp_rhs_noalloc": (_I, [_P, _P, _P, _P, _P]),
+    "hyp_wall_fluxes": (_I, [_P, _P, _P, _P, _P, _I, _P]),
+    "hyp_round_f32": (_I, [_I64, _P, _P, _P, _P]),
     "hyp_grid_profile": (_I, [_P, _I]),
     "hyp_grid_profile_read": (_I, [_P, _I, _P, _P]),
     "hyp_profile_count": (_I, []),
@@ -239,6 +242,25 @@ def rhs_noalloc(gas, grid, U, dUdt, stream=None):
 def rk_stage(state, stage, dt, precision=FP64, stream=None):
     """hyp_rk_stage: one stage of the two-register RK3 on the state's registers."""
     _check(lib().hyp_rk_stage(state.handle, stage, dt, precision, _stream(stream)))
+
+
+def wall_fluxes(gas, grid, U, q_w, tau_w, precision=FP64, stream=None):
+    """hyp_wall_fluxes: wall heat flux q_w (nx) and wall shear tau_w (nx + 1) of state U."""
+    import torch
+    if tau_w.numel() != q_w.numel() + 1:
+        raise HypError("tau_w needs one entry more than q_w (nx + 1 wall corners, nx wall faces)")
+    _check(lib().hyp_wall_fluxes(gas.handle, grid, _dptr(U), _dptr(q_w, None, torch.float64),
+                                 _dptr(tau_w, None, torch.float64), precision, _stream(stream)))
+
+
+def round_f32(x, y=None, back=None, stream=None):
+    """hyp_round_f32: binary64 -> binary32 rounding (y) and the widening back (back), device."""
+    import torch
+    n = x.numel()
+    _check(lib().hyp_round_f32(n, _dptr(x, n, torch.float64),
+                               _dptr(y, n, torch.float32) if y is not None else None,
+                               _dptr(back, n, torch.float64) if back is not None else None,
+                               _stream(stream)))
 
 
 def grid_reference(grid, n):

@@ -322,6 +322,20 @@ extern "C" int hyp_gas_model_load(const char* path, int kind, const hyp_freestre
         d.mu_inf = o.mu;
         d.k_inf = o.k;
     }
+    for (int i = 0; i < NSP; ++i) {
+        d.f_blA[i] = (float)d.blA[i];
+        d.f_blB[i] = (float)d.blB[i];
+        d.f_blC[i] = (float)d.blC[i];
+        d.f_Mq[i] = (float)d.Mq[i];
+        d.f_iMq[i] = (float)d.iMq[i];
+        d.f_Rs[i] = (float)d.Rs[i];
+        for (int j = 0; j < NSP; ++j) d.f_wilke_d[i][j] = (float)d.wilke_d[i][j];
+    }
+    for (int q = 0; q < NSP * (NSP - 1) / 2; ++q) d.f_pair_dinv[q] = (float)d.pair_dinv[q];
+    for (int q = 0; q < MAXEPS; ++q) {
+        d.f_eps_inv[q] = (float)d.eps_inv[q];
+        d.f_eps_powB[q] = (float)d.eps_powB[q];
+    }
     d.Re = fs->reynolds;
     d.Pr = d.mu_inf * d.cp_inf / d.k_inf;
     d.T_ref = (d.gamma_inf - 1.0) * fs->T_inf;
@@ -352,6 +366,7 @@ extern "C" const char* hyp_last_error(void) { return g_last_error.c_str(); }
 
 namespace gaskern {
 
+template <bool MIXED>
 __global__ void __launch_bounds__(128) k_thermo_eval(
     GasDev g, int64_t n, const double* __restrict__ rho, const double* __restrict__ e,
     const double* __restrict__ Y, double* __restrict__ T, double* __restrict__ p,
@@ -365,7 +380,7 @@ __global__ void __launch_bounds__(128) k_thermo_eval(
 #pragma unroll
         for (int s = 0; s < NSP; ++s) y[s] = Y[s * n + i];
         ClosureOut o;
-        closure_si(g, rho[i], e[i], y, 1000.0, reactions && wdot, diffusion && D, o);
+        closure_si_p<MIXED>(g, rho[i], e[i], y, 1000.0, reactions && wdot, diffusion && D, o);
         if (T) T[i] = o.T;
         if (p) p[i] = o.p;
         if (mu) mu[i] = o.mu;
@@ -408,12 +423,16 @@ extern "C" int hyp_thermo_eval(const hyp_gas* gas, int64_t n, const double* rho,
                                double* k, double* D, uint8_t* status, int precision,
                                void* stream) {
     if (!gas || n < 0) return fail(HYP_ERR_ARG, "null gas or negative n");
-    if (precision != HYP_FP64) return fail(HYP_ERR_ARG, "only HYP_FP64 is available");
+    if (precision != HYP_FP64 && precision != HYP_MIXED) return fail(HYP_ERR_ARG, "unknown precision");
     if (n == 0) return HYP_OK;
     if (!rho || !e || !Y) return fail(HYP_ERR_ARG, "null input");
     const int block = 128;
-    k_thermo_eval<<<grid_for(n, block), block, 0, (cudaStream_t)stream>>>(
-        gas->dev, n, rho, e, Y, T, p, wdot, mu, k, D, status);
+    if (precision == HYP_MIXED)
+        k_thermo_eval<true><<<grid_for(n, block), block, 0, (cudaStream_t)stream>>>(
+            gas->dev, n, rho, e, Y, T, p, wdot, mu, k, D, status);
+    else
+        k_thermo_eval<false><<<grid_for(n, block), block, 0, (cudaStream_t)stream>>>(
+            gas->dev, n, rho, e, Y, T, p, wdot, mu, k, D, status);
     HYP_CUDA(cudaGetLastError());
     return HYP_OK;
 }

@@ -51,6 +51,11 @@ struct GasDev {
     double pair_dinv[NSP * (NSP - 1) / 2];   // pi sigma^2 / ((3/16) sqrt(2 pi k^3 / m_sr))
     double eps_inv[MAXEPS];      // 1 / sqrt(eps_s eps_r)
     double eps_powB[MAXEPS];     // sqrt(eps_s eps_r)^B of the collision-integral fit
+    // binary32 copies of the transport constants for the mixed-precision closure (HYP_MIXED)
+    float f_blA[NSP], f_blB[NSP], f_blC[NSP], f_Mq[NSP], f_iMq[NSP], f_Rs[NSP];
+    float f_wilke_d[NSP][NSP];
+    float f_pair_dinv[NSP * (NSP - 1) / 2];
+    float f_eps_inv[MAXEPS], f_eps_powB[MAXEPS];
     // kinetics (Eqs. 13-15): elementary reactions with explicit colliders, sorted by group
     int gstart[MAXG + 1];        // reactions of group k: [gstart[k], gstart[k+1])
     double C[MAXR];              // SI pre-exponential factor
@@ -92,6 +97,10 @@ struct LineOp {
     const double* wa;            // device, interior rows: weight of (f_{+1/2} +/- f_{-1/2}) / pivot
     const double* wb;            // device, interior rows: weight of (f_{+3/2} +/- f_{-3/2}) / pivot
     const double* lm;            // device: sub-diagonal / pivot
+    // Interior rows rc..last_interior have bitwise-constant factors (the Thomas recurrence of the
+    // Toeplitz interior reaches its fixed point within about 20 rows): wa, wb, lm, cprime there.
+    int rc;
+    double wac, wbc, lmc, cpc;
     int ncl;                     // closure rows (<= 4)
     int crow[4], cstart[4], cnum[4];
     double cw[4][5];

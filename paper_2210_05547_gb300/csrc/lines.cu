@@ -16,10 +16,18 @@
 // W = 26 (derivative, alpha = 9/62, factor <= 0.148) leave it below 1e-19 of the values, under
 // FP64 rounding. Each segment reads only values written before the barrier by threads of its own
 // block, so results are deterministic.
+//
+// Past the first ~20 interior rows the Thomas factors are bitwise constant (LineOp::rc), so those
+// rows take their factors from registers and only the field values come from memory. A thread
+// has only a few FP64 instructions per row and the grid holds a few warps per sub-partition, so
+// the rows of that constant stretch are software-pipelined: the loads for row r + 8 are issued
+// while row r is computed.
 #include "internal.h"
 
 namespace hyp {
 namespace {
+
+constexpr int PF = 8;   // prefetch distance (rows) of the constant-factor loops
 
 __device__ __forceinline__ double closure_rhs(const LineOp& op, const double* __restrict__ in,
                                               long long ies, int r, double wall) {
@@ -29,6 +37,221 @@ __device__ __forceinline__ double closure_rhs(const LineOp& op, const double* __
     const double* p = in + (long long)op.cstart[c] * ies;
     for (int k = 0; k < op.cnum[c]; ++k) v += op.cw[c][k] * p[(long long)k * ies];
     return v;
+}
+
+// Sliding window of the four inputs of an interior row: p0..p2 held, p3 the new one.
+struct Window {
+    double p0, p1, p2;
+};
+
+template <int KIND>
+__device__ __forceinline__ double interior_row(double d, const Window& w, double p3, double wa,
+                                               double wb, double lm) {
+    if (KIND == 0) return fma(-lm, d, fma(wa, w.p1 + w.p2, wb * (w.p0 + p3)));
+    return fma(-lm, d, fma(wa, w.p2 - w.p1, wb * (p3 - w.p0)));
+}
+
+__device__ __forceinline__ void shift(Window& w, double p3) {
+    w.p0 = w.p1;
+    w.p1 = w.p2;
+    w.p2 = p3;
+}
+
+// Interior rows r..r1 with per-row factors; `p` points at the new input of row r and is advanced
+// past row r1.
+template <int KIND, bool STORE>
+__device__ __forceinline__ void fwd_rows_var(int r, int r1, double& d, Window& w,
+                                             const double* __restrict__& p, long long ies,
+                                             const LineOp& op, double* __restrict__ tmp,
+                                             long long oes) {
+    const double* __restrict__ wa = op.wa;
+    const double* __restrict__ wb = op.wb;
+    const double* __restrict__ lm = op.lm;
+#pragma unroll 2
+    for (; r <= r1; ++r) {
+        const double p3 = *p;
+        p += ies;
+        d = interior_row<KIND>(d, w, p3, wa[r], wb[r], lm[r]);
+        if (STORE) tmp[(long long)r * oes] = d;
+        shift(w, p3);
+    }
+}
+
+// Interior rows r..r1 with the constant factors, inputs prefetched PF rows ahead.
+template <int KIND, bool STORE>
+__device__ __forceinline__ void fwd_rows_const(int r, int r1, double& d, Window& w,
+                                               const double* __restrict__& p, long long ies,
+                                               const LineOp& op, double* __restrict__ tmp,
+                                               long long oes) {
+    const int n = r1 - r + 1;
+    if (n <= 0) return;
+    const double wa = op.wac, wb = op.wbc, lm = op.lmc;
+    const double* __restrict__ pp = p;
+    double q[PF];
+#pragma unroll
+    for (int k = 0; k < PF; ++k) q[k] = k < n ? pp[(long long)k * ies] : 0.0;
+    for (; r + PF - 1 <= r1; r += PF) {
+#pragma unroll
+        for (int k = 0; k < PF; ++k) {
+            const double p3 = q[k];
+            q[k] = r + PF + k <= r1 ? pp[(long long)(PF + k) * ies] : 0.0;
+            d = interior_row<KIND>(d, w, p3, wa, wb, lm);
+            if (STORE) tmp[(long long)(r + k) * oes] = d;
+            shift(w, p3);
+        }
+        pp += PF * ies;
+    }
+#pragma unroll
+    for (int k = 0; k < PF - 1; ++k) {
+        if (r + k <= r1) {
+            const double p3 = q[k];
+            d = interior_row<KIND>(d, w, p3, wa, wb, lm);
+            if (STORE) tmp[(long long)(r + k) * oes] = d;
+            shift(w, p3);
+        }
+    }
+    p += (long long)n * ies;
+}
+
+// Forward sweep over rows r..r1 of one kind of region (closure / per-row / constant interior).
+template <int KIND, bool STORE>
+__device__ __forceinline__ void fwd_span(int r, int r1, double& d, Window& w,
+                                         const double* __restrict__ in,
+                                         const double* __restrict__& p, long long ies,
+                                         const LineOp& op, double wall, double* __restrict__ tmp,
+                                         long long oes) {
+    if (r > r1) return;
+    const int fi = op.first_interior, li = op.last_interior, rc = op.rc;
+    const int base = op.dir == 0 ? -2 : -1;
+    // left closure rows
+    for (; r <= r1 && r < fi; ++r) {
+        d = (closure_rhs(op, in, ies, r, wall) - op.lower[r] * d) * op.minv[r];
+        if (STORE) tmp[(long long)r * oes] = d;
+    }
+    if (r > r1) return;
+    if (r <= li) {
+        // (re)load the window when entering the interior here
+        if (p == nullptr) {
+            const double* q = in + (long long)(r + base) * ies;
+            w.p0 = q[0];
+            w.p1 = q[ies];
+            w.p2 = q[2 * ies];
+            p = q + 3 * ies;
+        }
+        const int rv = min(r1, min(li, rc - 1));
+        if (r <= rv) {
+            fwd_rows_var<KIND, STORE>(r, rv, d, w, p, ies, op, tmp, oes);
+            r = rv + 1;
+        }
+        const int rcn = min(r1, li);
+        if (r <= rcn) {
+            fwd_rows_const<KIND, STORE>(r, rcn, d, w, p, ies, op, tmp, oes);
+            r = rcn + 1;
+        }
+    }
+    // right closure rows
+    for (; r <= r1; ++r) {
+        d = (closure_rhs(op, in, ies, r, wall) - op.lower[r] * d) * op.minv[r];
+        if (STORE) tmp[(long long)r * oes] = d;
+    }
+}
+
+// Output modes of the back substitution: 0 none (warm-up rows), 1 y, 2 -y, 3 y met, 4 -y met.
+template <int OM>
+__device__ __forceinline__ void put(double* __restrict__ out, long long oes, int r, double y,
+                                    double m) {
+    if (OM == 1) out[(long long)r * oes] = y;
+    if (OM == 2) out[(long long)r * oes] = -y;
+    if (OM == 3) out[(long long)r * oes] = y * m;
+    if (OM == 4) out[(long long)r * oes] = -y * m;
+}
+
+// Back substitution over rows r0 >= r >= r1 (descending) with per-row c'.
+template <int OM>
+__device__ __forceinline__ void back_rows_var(int r0, int r1, double& y,
+                                              const double* __restrict__ tmp, long long oes,
+                                              const double* __restrict__ cpr,
+                                              const double* __restrict__ met,
+                                              double* __restrict__ out) {
+#pragma unroll 2
+    for (int r = r0; r >= r1; --r) {
+        y = tmp[(long long)r * oes] - cpr[r] * y;
+        put<OM>(out, oes, r, y, OM >= 3 ? met[r] : 0.0);
+    }
+}
+
+// Back substitution over rows r0 >= r >= r1 with the constant c', loads prefetched PF rows ahead.
+template <int OM>
+__device__ __forceinline__ void back_rows_const(int r0, int r1, double& y,
+                                                const double* __restrict__ tmp, long long oes,
+                                                double cc, const double* __restrict__ met,
+                                                double* __restrict__ out) {
+    const int n = r0 - r1 + 1;
+    if (n <= 0) return;
+    double q[PF], mq[PF];
+#pragma unroll
+    for (int k = 0; k < PF; ++k) {
+        q[k] = k < n ? tmp[(long long)(r0 - k) * oes] : 0.0;
+        mq[k] = (OM >= 3 && k < n) ? met[r0 - k] : 0.0;
+    }
+    int r = r0;
+    for (; r - PF + 1 >= r1; r -= PF) {
+#pragma unroll
+        for (int k = 0; k < PF; ++k) {
+            const double t = q[k], m = mq[k];
+            const int rn = r - PF - k;
+            q[k] = rn >= r1 ? tmp[(long long)rn * oes] : 0.0;
+            if (OM >= 3) mq[k] = rn >= r1 ? met[rn] : 0.0;
+            y = fma(-cc, y, t);
+            put<OM>(out, oes, r - k, y, m);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < PF - 1; ++k) {
+        if (r - k >= r1) {
+            y = fma(-cc, y, q[k]);
+            put<OM>(out, oes, r - k, y, mq[k]);
+        }
+    }
+}
+
+// Back substitution over rows r0 >= r >= r1, split at the constant-factor stretch.
+template <int OM>
+__device__ __forceinline__ void back_span(int r0, int r1, double& y, const LineOp& op,
+                                          const double* __restrict__ tmp, long long oes,
+                                          const double* __restrict__ met,
+                                          double* __restrict__ out) {
+    if (r0 < r1) return;
+    const int li = op.last_interior, rc = op.rc;
+    const int a = max(r1, li + 1);            // rows above the interior (right closure)
+    if (r0 >= a) back_rows_var<OM>(r0, a, y, tmp, oes, op.cprime, met, out);
+    const int c0 = min(r0, li), c1 = max(r1, rc);
+    if (c0 >= c1) back_rows_const<OM>(c0, c1, y, tmp, oes, op.cpc, met, out);
+    const int v0 = min(r0, rc - 1);
+    if (v0 >= r1) back_rows_var<OM>(v0, r1, y, tmp, oes, op.cprime, met, out);
+}
+
+template <int KIND>
+__device__ __forceinline__ void forward(const LineJob& J, const LineOp& op,
+                                        const double* __restrict__ in, double* __restrict__ tmp,
+                                        int s, int e, int W) {
+    const int fs = max(0, s - W);
+    const long long ies = J.in_es, oes = J.out_es;
+    double d = 0.0;
+    Window w{0.0, 0.0, 0.0};
+    const double* __restrict__ p = nullptr;
+    fwd_span<KIND, false>(fs, s - 1, d, w, in, p, ies, op, J.wall_value, tmp, oes);
+    fwd_span<KIND, true>(s, e, d, w, in, p, ies, op, J.wall_value, tmp, oes);
+}
+
+template <int OM>
+__device__ __forceinline__ void backward(const LineOp& op, const double* __restrict__ tmp,
+                                         long long oes, const double* __restrict__ met,
+                                         double* __restrict__ out, int s, int e, int be) {
+    double y = tmp[(long long)be * oes];
+    if (be <= e) put<OM>(out, oes, be, y, OM >= 3 ? met[be] : 0.0);
+    back_span<0>(be - 1, e + 1, y, op, tmp, oes, met, out);     // warm-up rows past the segment
+    back_span<OM>(min(be - 1, e), s, y, op, tmp, oes, met, out);
 }
 
 __global__ void __launch_bounds__(LINE_BLOCK) k_lines(const LineJob* __restrict__ jobs,
@@ -45,96 +268,26 @@ __global__ void __launch_bounds__(LINE_BLOCK) k_lines(const LineJob* __restrict_
     const int s = seg * L;
     const int e = min(s + L, m) - 1;
     const int W = op.kind == 0 ? 40 : 26;
-    const long long ies = J.in_es, oes = J.out_es;
     const double* __restrict__ in =
         (J.in_state ? U + (size_t)J.in : J.in) + (long long)line * J.in_ls;
     double* __restrict__ out = J.out + (long long)line * J.out_ls;
     double* __restrict__ tmp = J.tmp + (long long)line * J.out_ls;
-    const int base = op.dir == 0 ? -2 : -1;
-    const double* __restrict__ lower = op.lower;
-    const double* __restrict__ minv = op.minv;
-    const double* __restrict__ cpr = op.cprime;
-    const int fi = op.first_interior, li = op.last_interior;
     if (active && s <= e) {
-        const int fs = max(0, s - W);
-        double d = 0.0;
-        int r = fs;
-        // left closure rows
-        for (; r <= e && r < fi; ++r) {
-            d = (closure_rhs(op, in, ies, r, J.wall_value) - lower[r] * d) * minv[r];
-            if (r >= s) tmp[(long long)r * oes] = d;
-        }
-        // interior rows: a sliding window of the four inputs, one new load per row, weights
-        // already divided by the pivot
-        const int ie = min(e, li);
-        if (r <= ie) {
-            const double* p = in + (long long)(r + base) * ies;
-            double p0 = p[0], p1 = p[ies], p2 = p[2 * ies];
-            p += 3 * ies;
-            const double* __restrict__ wa = op.wa;
-            const double* __restrict__ wb = op.wb;
-            const double* __restrict__ lm = op.lm;
-            if (op.kind == 0) {
-#pragma unroll 4
-                for (; r <= ie; ++r) {
-                    const double p3 = *p;
-                    p += ies;
-                    d = fma(-lm[r], d, fma(wa[r], p1 + p2, wb[r] * (p0 + p3)));
-                    if (r >= s) tmp[(long long)r * oes] = d;
-                    p0 = p1;
-                    p1 = p2;
-                    p2 = p3;
-                }
-            } else {
-#pragma unroll 4
-                for (; r <= ie; ++r) {
-                    const double p3 = *p;
-                    p += ies;
-                    d = fma(-lm[r], d, fma(wa[r], p2 - p1, wb[r] * (p3 - p0)));
-                    if (r >= s) tmp[(long long)r * oes] = d;
-                    p0 = p1;
-                    p1 = p2;
-                    p2 = p3;
-                }
-            }
-        }
-        // right closure rows
-        for (; r <= e; ++r) {
-            d = (closure_rhs(op, in, ies, r, J.wall_value) - lower[r] * d) * minv[r];
-            if (r >= s) tmp[(long long)r * oes] = d;
-        }
+        if (op.kind == 0) forward<0>(J, op, in, tmp, s, e, W);
+        else forward<1>(J, op, in, tmp, s, e, W);
     }
     __syncthreads();
     if (active && s <= e) {
         const int be = min(e + W, m - 1);
         const double* __restrict__ met = J.metric;
         const bool neg = J.scale < 0.0;
-        double y = tmp[(long long)be * oes];
-        if (be <= e) {
-            const double v = met ? y * met[be] : y;
-            out[(long long)be * oes] = neg ? -v : v;
-        }
-        int r = be - 1;
-        // warm-up rows beyond the segment
-        for (; r > e; --r) y = tmp[(long long)r * oes] - cpr[r] * y;
-        if (met && neg) {
-#pragma unroll 4
-            for (; r >= s; --r) {
-                y = tmp[(long long)r * oes] - cpr[r] * y;
-                out[(long long)r * oes] = -y * met[r];
-            }
-        } else if (met) {
-#pragma unroll 4
-            for (; r >= s; --r) {
-                y = tmp[(long long)r * oes] - cpr[r] * y;
-                out[(long long)r * oes] = y * met[r];
-            }
+        const long long oes = J.out_es;
+        if (met) {
+            if (neg) backward<4>(op, tmp, oes, met, out, s, e, be);
+            else backward<3>(op, tmp, oes, met, out, s, e, be);
         } else {
-#pragma unroll 4
-            for (; r >= s; --r) {
-                y = tmp[(long long)r * oes] - cpr[r] * y;
-                out[(long long)r * oes] = neg ? -y : y;
-            }
+            if (neg) backward<2>(op, tmp, oes, met, out, s, e, be);
+            else backward<1>(op, tmp, oes, met, out, s, e, be);
         }
     }
 }

@@ -118,6 +118,7 @@ struct hyp_grid {
     cudaStream_t side;           // second stream for phases that do not wait on the closure
     cudaEvent_t fork[2], join[2];
     int closure_blocks;          // resident blocks of k_closure on this GPU
+    int closure_blocks_mixed;    // the same for the mixed-precision closure
     GridView view() const {
         GridView v;
         v.nx = d.nx;
@@ -375,6 +376,20 @@ LineOp make_op(int kind, int dir, int n, int wall, std::vector<double>& data) {
         wb[r] = (kind == 0 ? op.wi[0] : op.wi[3]) * mi[r];
         lm[r] = lower[r] * mi[r];
     }
+    // first row of the constant tail of the interior factors
+    const int li = op.last_interior;
+    op.rc = li + 1;
+    if (li >= op.first_interior) {
+        int r = li;
+        while (r - 1 >= op.first_interior && wa[r - 1] == wa[li] && wb[r - 1] == wb[li] &&
+               lm[r - 1] == lm[li] && cp[r - 1] == cp[li])
+            --r;
+        op.rc = r;
+        op.wac = wa[li];
+        op.wbc = wb[li];
+        op.lmc = lm[li];
+        op.cpc = cp[li];
+    }
     // store offsets into data (fixed up to device pointers later)
     const size_t base = data.size();
     for (auto* v : {&lower, &cp, &mi, &wa, &wb, &lm}) data.insert(data.end(), v->begin(), v->end());
@@ -397,7 +412,8 @@ __device__ __forceinline__ void atomic_status(unsigned* st, unsigned bits) {
     if (bits) atomicOr(st, bits);
 }
 
-// (A) primitives and the closure at every cell centre
+// (A) primitives and the closure at every cell centre (MIXED: binary32 transport, Sec. 2.2)
+template <bool MIXED>
 __global__ void __launch_bounds__(128) k_closure(GasDev g, GridView v, const double* __restrict__ U,
                                                  Scratch s) {
     const int n = v.nx * v.ny;
@@ -448,7 +464,7 @@ __global__ void __launch_bounds__(128) k_closure(GasDev g, GridView v, const dou
                 T0 += d1 - 0.5 * cvpc * d1 * d1 * icv;
             }
             ClosureOut o;
-            closure_si(g, rho * g.rho_inf, e_si, Y, T0, cneq, cneq, o);
+            closure_si_p<MIXED>(g, rho * g.rho_inf, e_si, Y, T0, cneq, cneq, o);
             atomic_status(v.status, o.status);
             s.Tcache[idx] = o.T;
 #pragma unroll
@@ -1202,8 +1218,10 @@ extern "C" int hyp_state_init(const hyp_gas* gas, const hyp_grid_desc* desc, con
         int dev = 0, sms = 0, per_sm = 0;
         HYP_CUDA(cudaGetDevice(&dev));
         HYP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        HYP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_closure, 128, 0));
+        HYP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_closure<false>, 128, 0));
         G->closure_blocks = std::max(1, per_sm * sms);
+        HYP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_closure<true>, 128, 0));
+        G->closure_blocks_mixed = std::max(1, per_sm * sms);
     }
     HYP_CUDA(cudaGetLastError());
     // host vectors must outlive the async copies
@@ -1275,7 +1293,8 @@ static void prof_end(hyp_grid* G, int slot, cudaStream_t s) {
 // The whole right-hand side; with rk != 0 the assemble step performs the stage update instead
 // of writing dUdt.
 static int run_rhs(const hyp_gas* gas, hyp_grid* G, const double* U, double* dUdt, int rk,
-                   double A, double Bc, double dt, double* Urk, double* dQ, cudaStream_t s) {
+                   double A, double Bc, double dt, double* Urk, double* dQ, int precision,
+                   cudaStream_t s) {
     const GasDev& g = gas->dev;
     const GridView v = G->view();
     Scratch& S = G->s;
@@ -1290,8 +1309,11 @@ static int run_rhs(const hyp_gas* gas, hyp_grid* G, const double* U, double* dUd
     cudaStream_t s2 = G->side;
     HYP_CUDA(cudaEventRecord(G->fork[0], s));
     HYP_CUDA(cudaStreamWaitEvent(s2, G->fork[0], 0));
-    const int cb = (int)std::min<long long>(G->closure_blocks, (nc + 127) / 128);
-    TIMED(KID_CLOSURE, (k_closure<<<cb, 128, 0, s>>>(g, v, U, S)));
+    const bool mixed = precision == HYP_MIXED;
+    const int cb = (int)std::min<long long>(mixed ? G->closure_blocks_mixed : G->closure_blocks,
+                                            (nc + 127) / 128);
+    if (mixed) TIMED(KID_CLOSURE, (k_closure<true><<<cb, 128, 0, s>>>(g, v, U, S)));
+    else TIMED(KID_CLOSURE, (k_closure<false><<<cb, 128, 0, s>>>(g, v, U, S)));
     HYP_CUDA(cudaGetLastError());
     G->cache_valid = 1;
     TIMED_ON(s2, KID_LINES_VELGRAD, e1 = launch_lines(G->jobs + G->ph_start[PH_P3], G->ph_count[PH_P3],
@@ -1346,22 +1368,68 @@ static int run_rhs(const hyp_gas* gas, hyp_grid* G, const double* U, double* dUd
 extern "C" int hyp_rhs(const hyp_gas* gas, const hyp_grid* grid, const double* U, double* dUdt,
                        int precision, void* stream) {
     if (!gas || !grid || !U || !dUdt) return fail(HYP_ERR_ARG, "null argument");
-    if (precision != HYP_FP64) return fail(HYP_ERR_ARG, "only HYP_FP64 is available");
+    if (precision != HYP_FP64 && precision != HYP_MIXED) return fail(HYP_ERR_ARG, "unknown precision");
     if (U == dUdt) return fail(HYP_ERR_ARG, "U and dUdt must not alias");
     hyp_grid* G = const_cast<hyp_grid*>(grid);
-    return run_rhs(gas, G, U, dUdt, 0, 0.0, 0.0, 0.0, nullptr, nullptr, (cudaStream_t)stream);
+    return run_rhs(gas, G, U, dUdt, 0, 0.0, 0.0, 0.0, nullptr, nullptr, precision,
+                   (cudaStream_t)stream);
 }
 
 extern "C" int hyp_rk_stage(hyp_state* st, int stage, double dt, int precision, void* stream) {
     if (!st) return fail(HYP_ERR_ARG, "null state");
     if (stage < 0 || stage > 2) return fail(HYP_ERR_ARG, "stage must be 0, 1 or 2");
-    if (precision != HYP_FP64) return fail(HYP_ERR_ARG, "only HYP_FP64 is available");
+    if (precision != HYP_FP64 && precision != HYP_MIXED) return fail(HYP_ERR_ARG, "unknown precision");
     hyp_grid* G = st->grid;
     // the gas handle is not stored in the state: the grid keeps a copy of the device tables
     hyp_gas tmp;
     tmp.dev = G->gas;
     return run_rhs(&tmp, G, st->U, nullptr, 1, RK_A[stage], RK_B[stage], dt, st->U, st->dQ,
-                   (cudaStream_t)stream);
+                   precision, (cudaStream_t)stream);
+}
+
+// Wall heat flux q_w = -K dT/dy and wall shear stress tau_w = tau_xy on the wall row of the
+// scratch left by the right-hand side just evaluated (the same face and corner values that enter
+// the fluxes of Eq. 10 and Eq. 9).
+__global__ void k_wall_out(GridView v, Scratch s, double* __restrict__ q_w,
+                           double* __restrict__ tau_w) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < v.nx) q_w[i] = -s.Ky[i] * s.dTdy[i];
+    if (i <= v.nx) tau_w[i] = s.tau_xy[i];
+}
+
+extern "C" int hyp_wall_fluxes(const hyp_gas* gas, const hyp_grid* grid, const double* U,
+                               double* q_w, double* tau_w, int precision, void* stream) {
+    if (!gas || !grid || !U || !q_w || !tau_w) return fail(HYP_ERR_ARG, "null argument");
+    if (precision != HYP_FP64 && precision != HYP_MIXED) return fail(HYP_ERR_ARG, "unknown precision");
+    hyp_grid* G = const_cast<hyp_grid*>(grid);
+    const GridView v = G->view();
+    if (!v.wall) return fail(HYP_ERR_ARG, "the case has no wall");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int rc = run_rhs(gas, G, U, G->s.R, 0, 0.0, 0.0, 0.0, nullptr, nullptr, precision, s);
+    if (rc) return rc;
+    k_wall_out<<<(v.nx + 1 + 127) / 128, 128, 0, s>>>(v, G->s, q_w, tau_w);
+    HYP_CUDA(cudaGetLastError());
+    return HYP_OK;
+}
+
+// The binary64 -> binary32 -> binary64 round trip of the mixed-precision path (fp32.cuh).
+__global__ void k_round_f32(int64_t n, const double* __restrict__ x, float* __restrict__ y,
+                            double* __restrict__ back) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float f = f32_of(x[i]);
+        if (y) y[i] = f;
+        if (back) back[i] = f64_of(f);
+    }
+}
+
+extern "C" int hyp_round_f32(int64_t n, const double* x, float* y, double* back, void* stream) {
+    if (n < 0 || (n > 0 && !x)) return fail(HYP_ERR_ARG, "null input or negative n");
+    if (n == 0) return HYP_OK;
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 16);
+    k_round_f32<<<(int)blocks, 256, 0, (cudaStream_t)stream>>>(n, x, y, back);
+    HYP_CUDA(cudaGetLastError());
+    return HYP_OK;
 }
 
 extern "C" int hyp_profile_count(void) { return KID_COUNT; }
@@ -1498,7 +1566,7 @@ extern "C" int hyp_rhs_noalloc(const hyp_gas* gas, const hyp_grid* grid, const d
     };
     HYP_CUDA(lines(PH_P1, G->ph_count[PH_P1]));
     k_face_vel<<<blocks_for(d.size(NXF) + d.size(NYF), 256), 256, 0, s>>>(v, U, S);
-    k_closure<<<blocks_for(nc, 128), 128, 0, s>>>(g, v, U, S);
+    k_closure<false><<<blocks_for(nc, 128), 128, 0, s>>>(g, v, U, S);
     HYP_CUDA(cudaGetLastError());
     HYP_CUDA(lines(PH_P3, G->ph_count[PH_P3]));
     if (v.ad) {

@@ -12,6 +12,9 @@
 #include <math.h>
 
 #include "internal.h"
+#ifdef __CUDACC__
+#include "fp32.cuh"
+#endif
 
 namespace hyp {
 
@@ -169,10 +172,136 @@ struct ClosureOut {
     unsigned status;
 };
 
-// Full closure (SI). reactions: evaluate w_s; diffusion: evaluate D_s.
-__host__ __device__ inline void closure_si(const GasDev& g, double rho, double e, const double* Y,
-                                           double T0, bool reactions, bool diffusion,
-                                           ClosureOut& o) {
+#ifdef __CUDACC__
+// Transport and diffusion in binary32 for the mixed-precision closure (HYP_MIXED): the same
+// Blottner, Eucken, Wilke and Chapman-Enskog formulas as the FP64 code in closure_si, on binary32
+// copies of the constants. Inputs and outputs cross with the integer conversions of fp32.cuh.
+__device__ inline void transport_f32(const GasDev& g, double T, double lnT, double p,
+                                     const SpeciesState& s, bool diffusion, ClosureOut& o) {
+    const float lnTf = f32_of(lnT);
+    float Xf[NSP], mu_s[NSP], a[NSP], b[NSP], k_s[NSP];
+#pragma unroll
+    for (int i = 0; i < NSP; ++i) {
+        Xf[i] = f32_of(o.X[i]);
+        mu_s[i] = 0.1f * expf((g.f_blA[i] * lnTf + g.f_blB[i]) * lnTf + g.f_blC[i]);
+        const float ir = rsqrtf(mu_s[i]);
+        a[i] = mu_s[i] * ir * g.f_iMq[i];
+        b[i] = g.f_Mq[i] * ir;
+        const float cv_tr = 1.5f * g.f_Rs[i];
+        k_s[i] = mu_s[i] * (2.5f * cv_tr + (f32_of(s.cv[i]) - cv_tr));
+    }
+    float mu = 0.0f, kk = 0.0f;
+#pragma unroll
+    for (int i = 0; i < NSP; ++i) {
+        float phi = 0.0f;
+#pragma unroll
+        for (int r = 0; r < NSP; ++r) {
+            const float t = 1.0f + a[i] * b[r];
+            phi += Xf[r] * t * t * g.f_wilke_d[i][r];
+        }
+        const float w = Xf[i] / phi;
+        mu += w * mu_s[i];
+        kk += w * k_s[i];
+    }
+    o.mu = f64_of(mu);
+    o.k = f64_of(kk);
+#pragma unroll
+    for (int i = 0; i < NSP; ++i) o.D[i] = 0.0;
+    if (!diffusion) return;
+    float den[NSP];
+#pragma unroll
+    for (int i = 0; i < NSP; ++i) den[i] = 0.0f;
+    const float Tf = f32_of(T);
+    const float TmB = expf(-(float)NJA_B * lnTf);
+    const float c = f32_of(p) / (Tf * sqrtf(Tf));
+    for (int q = 0; q < g.neps; ++q) {
+        const float ts = Tf * g.f_eps_inv[q];
+        float om = (float)NJA_A * TmB * g.f_eps_powB[q];
+        if ((float)NJA_D * ts < (float)OMEGA_CUT) om += (float)NJA_C * expf(-(float)NJA_D * ts);
+        if ((float)NJA_F * ts < (float)OMEGA_CUT) om += (float)NJA_E * expf(-(float)NJA_F * ts);
+        if ((float)NJA_H * ts < (float)OMEGA_CUT) om += (float)NJA_G * expf(-(float)NJA_H * ts);
+        const float com = c * om;
+        for (int pr = g.pstart[q]; pr < g.pstart[q + 1]; ++pr) {
+            const int i = g.pair_i[pr], r = g.pair_r[pr];
+            const float inv_d = com * g.f_pair_dinv[pr];
+            den[i] += Xf[r] * inv_d;
+            den[r] += Xf[i] * inv_d;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < NSP; ++i) o.D[i] = den[i] != 0.0f ? f64_of((1.0f - Xf[i]) / den[i]) : 0.0;
+}
+#endif
+
+// Transport and diffusion in FP64: Blottner species viscosities, Eucken conductivities, Wilke's
+// mixing rule and the averaged diffusion coefficients of Eq. (19).
+__host__ __device__ inline void transport_f64(const GasDev& g, double T, double lnT, double p,
+                                              const SpeciesState& s, bool diffusion,
+                                              ClosureOut& o) {
+    // ---- transport: Blottner, Eucken, Wilke ----
+    // sqrt(mu_i / mu_r) (M_r / M_i)^(1/4) = a_i b_r with a_i = sqrt(mu_i) M_i^(-1/4),
+    // b_r = M_r^(1/4) / sqrt(mu_r)
+    double mu_s[NSP], a[NSP], b[NSP], k_s[NSP];
+#pragma unroll
+    for (int i = 0; i < NSP; ++i) {
+        mu_s[i] = 0.1 * exp((g.blA[i] * lnT + g.blB[i]) * lnT + g.blC[i]);
+        const double sq = sqrt(mu_s[i]);
+        a[i] = sq * g.iMq[i];
+        b[i] = g.Mq[i] / sq;
+        const double cv_tr = 1.5 * g.Rs[i];
+        k_s[i] = mu_s[i] * (2.5 * cv_tr + (s.cv[i] - cv_tr));
+    }
+    double mu = 0.0, kk = 0.0;
+#pragma unroll
+    for (int i = 0; i < NSP; ++i) {
+        double phi = 0.0;
+#pragma unroll
+        for (int r = 0; r < NSP; ++r) {
+            const double t = 1.0 + a[i] * b[r];
+            phi += o.X[r] * t * t * g.wilke_d[i][r];
+        }
+        const double w = o.X[i] / phi;
+        mu += w * mu_s[i];
+        kk += w * k_s[i];
+    }
+    o.mu = mu;
+    o.k = kk;
+
+    // ---- averaged diffusion coefficients (Eq. 19) from Chapman-Enskog binary coefficients ----
+#pragma unroll
+    for (int i = 0; i < NSP; ++i) o.D[i] = 0.0;
+    if (diffusion) {
+        double den[NSP];
+#pragma unroll
+        for (int i = 0; i < NSP; ++i) den[i] = 0.0;
+        const double TmB = exp(-NJA_B * lnT);               // T^-B, shared by every well depth
+        const double c = p / (T * sqrt(T));                  // 1/D_sr = c Omega dinv_sr
+        for (int q = 0; q < g.neps; ++q) {
+            const double ts = T * g.eps_inv[q];
+            double om = NJA_A * TmB * g.eps_powB[q];
+            if (NJA_D * ts < OMEGA_CUT) om += NJA_C * exp(-NJA_D * ts);
+            if (NJA_F * ts < OMEGA_CUT) om += NJA_E * exp(-NJA_F * ts);
+            if (NJA_H * ts < OMEGA_CUT) om += NJA_G * exp(-NJA_H * ts);
+            const double com = c * om;
+            for (int pr = g.pstart[q]; pr < g.pstart[q + 1]; ++pr) {
+                const int i = g.pair_i[pr], r = g.pair_r[pr];
+                const double inv_d = com * g.pair_dinv[pr];
+                den[i] += o.X[r] * inv_d;
+                den[r] += o.X[i] * inv_d;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NSP; ++i) o.D[i] = den[i] != 0.0 ? (1.0 - o.X[i]) / den[i] : 0.0;
+    }
+}
+
+// Full closure (SI). reactions: evaluate w_s; diffusion: evaluate D_s. MIXED (device only): the
+// forward rate exponentials, transport and diffusion in binary32; temperature inversion, species
+// thermodynamics, equilibrium constants and backward rates stay FP64.
+template <bool MIXED>
+__host__ __device__ inline void closure_si_p(const GasDev& g, double rho, double e,
+                                             const double* Y, double T0, bool reactions,
+                                             bool diffusion, ClosureOut& o) {
     SpeciesState s;
     o.status = rho > 0.0 ? 0u : HYP_STATUS_NONPHYSICAL;
     const double T = temperature_from_energy(g, e, Y, T0, o.status, s);
@@ -238,7 +367,12 @@ __host__ __device__ inline void closure_si(const GasDev& g, double rho, double e
             for (int rx = g.gstart[k]; rx < g.gstart[k + 1]; ++rx)
                 w += g.C[rx] * (g.spec[rx] >= 0 ? conc[g.spec[rx]] : 1.0);
             const double base = g.g_n[k] * lnT;
-            const double Ef = exp(base - g.g_Ta[k] * invT);
+            double Ef;
+#ifdef __CUDA_ARCH__
+            if (MIXED) Ef = f64_of(expf(f32_of(base - g.g_Ta[k] * invT)));
+            else
+#endif
+                Ef = exp(base - g.g_Ta[k] * invT);
             const double Eb = exp(base - (g.g_Ta[k] - g.g_theta_d[k]) * invT) * den / num;
             const double Rg = w * (Ef * fwd - Eb * bwd);
 #pragma unroll
@@ -248,61 +382,19 @@ __host__ __device__ inline void closure_si(const GasDev& g, double rho, double e
         for (int i = 0; i < NSP; ++i) o.wdot[i] = g.M[i] * molar[i];
     }
 
-    // ---- transport: Blottner, Eucken, Wilke ----
-    // sqrt(mu_i / mu_r) (M_r / M_i)^(1/4) = a_i b_r with a_i = sqrt(mu_i) M_i^(-1/4),
-    // b_r = M_r^(1/4) / sqrt(mu_r)
-    double mu_s[NSP], a[NSP], b[NSP], k_s[NSP];
-#pragma unroll
-    for (int i = 0; i < NSP; ++i) {
-        mu_s[i] = 0.1 * exp((g.blA[i] * lnT + g.blB[i]) * lnT + g.blC[i]);
-        const double sq = sqrt(mu_s[i]);
-        a[i] = sq * g.iMq[i];
-        b[i] = g.Mq[i] / sq;
-        const double cv_tr = 1.5 * g.Rs[i];
-        k_s[i] = mu_s[i] * (2.5 * cv_tr + (s.cv[i] - cv_tr));
+    if constexpr (MIXED) {
+#ifdef __CUDA_ARCH__
+        transport_f32(g, T, lnT, p, s, diffusion, o);
+#endif
+    } else {
+        transport_f64(g, T, lnT, p, s, diffusion, o);
     }
-    double mu = 0.0, kk = 0.0;
-#pragma unroll
-    for (int i = 0; i < NSP; ++i) {
-        double phi = 0.0;
-#pragma unroll
-        for (int r = 0; r < NSP; ++r) {
-            const double t = 1.0 + a[i] * b[r];
-            phi += o.X[r] * t * t * g.wilke_d[i][r];
-        }
-        const double w = o.X[i] / phi;
-        mu += w * mu_s[i];
-        kk += w * k_s[i];
-    }
-    o.mu = mu;
-    o.k = kk;
+}
 
-    // ---- averaged diffusion coefficients (Eq. 19) from Chapman-Enskog binary coefficients ----
-#pragma unroll
-    for (int i = 0; i < NSP; ++i) o.D[i] = 0.0;
-    if (diffusion) {
-        double den[NSP];
-#pragma unroll
-        for (int i = 0; i < NSP; ++i) den[i] = 0.0;
-        const double TmB = exp(-NJA_B * lnT);               // T^-B, shared by every well depth
-        const double c = p / (T * sqrt(T));                  // 1/D_sr = c Omega dinv_sr
-        for (int q = 0; q < g.neps; ++q) {
-            const double ts = T * g.eps_inv[q];
-            double om = NJA_A * TmB * g.eps_powB[q];
-            if (NJA_D * ts < OMEGA_CUT) om += NJA_C * exp(-NJA_D * ts);
-            if (NJA_F * ts < OMEGA_CUT) om += NJA_E * exp(-NJA_F * ts);
-            if (NJA_H * ts < OMEGA_CUT) om += NJA_G * exp(-NJA_H * ts);
-            const double com = c * om;
-            for (int pr = g.pstart[q]; pr < g.pstart[q + 1]; ++pr) {
-                const int i = g.pair_i[pr], r = g.pair_r[pr];
-                const double inv_d = com * g.pair_dinv[pr];
-                den[i] += o.X[r] * inv_d;
-                den[r] += o.X[i] * inv_d;
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < NSP; ++i) o.D[i] = den[i] != 0.0 ? (1.0 - o.X[i]) / den[i] : 0.0;
-    }
+__host__ __device__ inline void closure_si(const GasDev& g, double rho, double e, const double* Y,
+                                           double T0, bool reactions, bool diffusion,
+                                           ClosureOut& o) {
+    closure_si_p<false>(g, rho, e, Y, T0, reactions, diffusion, o);
 }
 
 }  // namespace hyp
