@@ -110,6 +110,8 @@ typedef struct {
     double C_mu, C_beta, C_kappa, C_D;
     double noise_amp;              /* initial state = reference * (1 + noise_amp * noise) */
     const double* noise;           /* HOST, nullable; hyp_state_size() values in [-1, 1] */
+    double filter_sigma;           /* > 0: low-pass filter of the state after each RK step, with
+                                      this damping of the grid-to-grid mode (see hyp_rk_stage) */
 } hyp_case;
 
 /* Load a gas table (plain-text SPECIES / LEVEL / REACTION lines, see data/air5.dat) and build
@@ -159,7 +161,11 @@ int hyp_rhs(const hyp_gas* gas, const hyp_grid* grid, const double* U, double* d
 
 /* One stage (0, 1, 2) of the low-storage two-register third-order Runge-Kutta scheme (Sec. 3.1):
  * dQ <- A_k dQ + dt R(U); U <- U + B_k dQ with A = (0, -5/9, -153/128), B = (1/3, 15/16, 8/15),
- * on the registers given to hyp_state_init. dt nondimensional (time unit L_ref / a_inf). */
+ * on the registers given to hyp_state_init. dt nondimensional (time unit L_ref / a_inf).
+ * If the case sets filter_sigma > 0, stage 2 ends with the low-pass filter of the high-order
+ * shock-capturing practice the paper cites (Sec. 3.3): along every grid line of every field,
+ * f_i <- f_i - sigma 4^-m sum_{n=-m..m} (-1)^n C(2m, m+n) f_{i+n}, m = 5, or m = d at distance
+ * d < 5 from an end of the line (end points unchanged); x lines first, then y lines. */
 int hyp_rk_stage(hyp_state* st, int stage, double dt, int precision, void* stream);
 
 /* Wall heat flux and wall shear stress of state U (nondimensional, Eq. 7): evaluates the

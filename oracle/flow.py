@@ -605,11 +605,57 @@ def parity_tolerance(case: Case, U):
     return tol, R
 
 
+# ---------------------------------------------------------------------------------------------
+# Low-pass filter of the conserved state (after each RK step when the case sets filter_sigma)
+# ---------------------------------------------------------------------------------------------
+# The shock capturing of Sec. 3.3 follows the localized-artificial-diffusivity papers it cites,
+# which run their non-dissipative compact schemes together with a high-order low-pass filter of
+# the conserved variables; the paper does not spell one out. Reading: along every grid line of
+# every field, f_i <- f_i - sigma (D_m f)_i with the 2m-th order difference
+#     (D_m f)_i = 4^-m sum_{n=-m..m} (-1)^n C(2m, m+n) f_{i+n},
+# whose Fourier symbol is sin^(2m)(theta/2) (1 at the grid-to-grid mode, O(theta^(2m)) for smooth
+# data). m = 5 where the stencil fits; at distance d < 5 from either end of the line m = d, and
+# the end points themselves are left unchanged. The x pass runs first, the y pass on its result.
+FILTER_ORDER_HALF = 5
+
+
+def filter_weights(m):
+    """Weights of (D_m f)_i on f_{i-m} .. f_{i+m}."""
+    return np.array([(-1) ** n * math.comb(2 * m, m + n) for n in range(-m, m + 1)],
+                    dtype=np.float64) / 4.0 ** m
+
+
+def filter_line(f, axis, sigma):
+    """One pass of the filter along ``axis`` of f (a new array)."""
+    fm = np.moveaxis(np.asarray(f, dtype=np.float64), axis, 0)
+    n = fm.shape[0]
+    out = fm.copy()
+    for i in range(1, n - 1):
+        m = min(i, n - 1 - i, FILTER_ORDER_HALF)
+        w = filter_weights(m)
+        d = sum(w[k] * fm[i - m + k] for k in range(2 * m + 1))
+        out[i] = fm[i] - sigma * d
+    return np.moveaxis(out, 0, axis)
+
+
+def filter_state(case: Case, U, sigma=None):
+    """The filter applied to every field of the state vector (x pass, then y pass)."""
+    sigma = case.cfg.get("filter_sigma", 0.0) if sigma is None else sigma
+    g = case.grid
+    q = unpack(case.tab.ns, g.nx, g.ny, np.asarray(U, dtype=np.float64))
+    out = {k: filter_line(filter_line(v, 1, sigma), 0, sigma) for k, v in q.items()}
+    return pack(case.tab.ns, g.nx, g.ny, out)
+
+
 def rk_stage(case: Case, U, dQ, stage, dt):
-    """One stage of the two-register RK3: returns (U_new, dQ_new, R)."""
+    """One stage of the two-register RK3: returns (U_new, dQ_new, R). After the last stage the
+    state is filtered when the case sets filter_sigma > 0."""
     R = rhs(case, U)
     dQ = RK_A[stage] * dQ + dt * R
-    return U + RK_B[stage] * dQ, dQ, R
+    U = U + RK_B[stage] * dQ
+    if stage == 2 and case is not None and case.cfg.get("filter_sigma", 0.0) > 0.0:
+        U = filter_state(case, U)
+    return U, dQ, R
 
 
 def wall_fluxes(case: Case, U):

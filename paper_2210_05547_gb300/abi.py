@@ -46,7 +46,8 @@ class CaseDesc(ctypes.Structure):
                 ("sponge_top_cells", ctypes.c_int32), ("artificial_diffusivity", ctypes.c_int32),
                 ("C_mu", ctypes.c_double), ("C_beta", ctypes.c_double),
                 ("C_kappa", ctypes.c_double), ("C_D", ctypes.c_double),
-                ("noise_amp", ctypes.c_double), ("noise", ctypes.POINTER(ctypes.c_double))]
+                ("noise_amp", ctypes.c_double), ("noise", ctypes.POINTER(ctypes.c_double)),
+                ("filter_sigma", ctypes.c_double)]
 
 
 _LIB = None
@@ -159,6 +160,7 @@ def case_struct(cfg, noise=None):
     c.artificial_diffusivity = int(cfg["artificial_diffusivity"])
     c.C_mu, c.C_beta, c.C_kappa, c.C_D = cfg["C_mu"], cfg["C_beta"], cfg["C_kappa"], cfg["C_D"]
     c.noise_amp = cfg["noise_amp"]
+    c.filter_sigma = cfg.get("filter_sigma", 0.0)
     if noise is not None:
         arr = np.ascontiguousarray(noise, dtype=np.float64)
         c.noise = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))

@@ -75,12 +75,12 @@ enum Phase {
 enum KernelId {
     KID_LINES_STATE, KID_FACE_VEL, KID_CLOSURE, KID_LINES_VELGRAD, KID_LINES_AD, KID_AD_PREP,
     KID_AD_RAW, KID_AD_GAUSS, KID_AD_COMBINE, KID_STRESS_C, KID_LINES_MU, KID_STRESS_CN,
-    KID_LINES_FACE, KID_FLUX, KID_LINES_DIV, KID_ASSEMBLE, KID_COUNT
+    KID_LINES_FACE, KID_FLUX, KID_LINES_DIV, KID_ASSEMBLE, KID_FILTER, KID_COUNT
 };
 const char* const KERNEL_NAMES[KID_COUNT] = {
     "k_lines:state", "k_face_vel", "k_closure", "k_lines:velgrad", "k_lines:ad", "k_ad_prep",
     "k_ad_raw", "k_gauss", "k_ad_combine", "k_stress_c", "k_lines:mu", "k_stress_cn",
-    "k_lines:face", "k_flux", "k_lines:div", "k_assemble"};
+    "k_lines:face", "k_flux", "k_lines:div", "k_assemble", "k_filter"};
 
 struct EventProfile {
     bool on = false;
@@ -1375,6 +1375,74 @@ extern "C" int hyp_rhs(const hyp_gas* gas, const hyp_grid* grid, const double* U
                    (cudaStream_t)stream);
 }
 
+// Low-pass filter of the conserved state along x (dir 0) or y (dir 1) lines of every field:
+// out_i = in_i - sigma (D_m in)_i with the binomial 2m-th difference of weights c_filter_w,
+// m = min(5, distance to the nearer end of the line); end points copied. HBM-bound: one read of
+// the line neighbours (cached) and one write per entry.
+__constant__ double c_filter_w[5][11];   // [m - 1][n + m] = (-1)^n C(2m, m + n) / 4^m
+
+__global__ void k_filter(int nx, int ny, long long nstate, const double* __restrict__ in,
+                         double* __restrict__ out, int dir, double sigma) {
+    const long long nc = (long long)nx * ny;
+    const long long nxf = (long long)(nx + 1) * ny;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nstate;
+         idx += (long long)gridDim.x * blockDim.x) {
+        long long local;
+        int pitch, rows;
+        if (idx < (NSP + 1) * nc) {
+            local = idx % nc;
+            pitch = nx;
+            rows = ny;
+        } else if (idx < (NSP + 1) * nc + nxf) {
+            local = idx - (NSP + 1) * nc;
+            pitch = nx + 1;
+            rows = ny;
+        } else {
+            local = idx - (NSP + 1) * nc - nxf;
+            pitch = nx;
+            rows = ny + 1;
+        }
+        const int row = (int)(local / pitch), col = (int)(local - (long long)row * pitch);
+        const int pos = dir == 0 ? col : row;
+        const int n = dir == 0 ? pitch : rows;
+        const long long stride = dir == 0 ? 1 : pitch;
+        const int m = min(min(pos, n - 1 - pos), 5);
+        const double f = in[idx];
+        if (m == 0) {
+            out[idx] = f;
+            continue;
+        }
+        const double* w = c_filter_w[m - 1];
+        const double* p = in + idx - m * stride;
+        double acc = 0.0;
+        for (int k = 0; k <= 2 * m; ++k) acc = fma(w[k], p[k * stride], acc);
+        out[idx] = fma(-sigma, acc, f);
+    }
+}
+
+static int launch_filter(hyp_grid* G, double* U, cudaStream_t s) {
+    static std::once_flag once;
+    static cudaError_t werr = cudaSuccess;
+    std::call_once(once, [] {
+        double w[5][11] = {};
+        for (int m = 1; m <= 5; ++m) {
+            double c = 1.0;                                   // C(2m, 0)
+            for (int k = 0; k <= 2 * m; ++k) {
+                w[m - 1][k] = ((k - m) % 2 == 0 ? c : -c) / (double)(1 << (2 * m));
+                c = c * (2 * m - k) / (k + 1);                // C(2m, k + 1), exact in binary64
+            }
+        }
+        werr = cudaMemcpyToSymbol(c_filter_w, w, sizeof(w));
+    });
+    HYP_CUDA(werr);
+    const double sigma = G->cas.filter_sigma;
+    const int blocks = blocks_for(G->nstate, 256);
+    TIMED(KID_FILTER, (k_filter<<<blocks, 256, 0, s>>>(G->d.nx, G->d.ny, G->nstate, U, G->s.R, 0, sigma)));
+    TIMED(KID_FILTER, (k_filter<<<blocks, 256, 0, s>>>(G->d.nx, G->d.ny, G->nstate, G->s.R, U, 1, sigma)));
+    HYP_CUDA(cudaGetLastError());
+    return HYP_OK;
+}
+
 extern "C" int hyp_rk_stage(hyp_state* st, int stage, double dt, int precision, void* stream) {
     if (!st) return fail(HYP_ERR_ARG, "null state");
     if (stage < 0 || stage > 2) return fail(HYP_ERR_ARG, "stage must be 0, 1 or 2");
@@ -1383,8 +1451,10 @@ extern "C" int hyp_rk_stage(hyp_state* st, int stage, double dt, int precision, 
     // the gas handle is not stored in the state: the grid keeps a copy of the device tables
     hyp_gas tmp;
     tmp.dev = G->gas;
-    return run_rhs(&tmp, G, st->U, nullptr, 1, RK_A[stage], RK_B[stage], dt, st->U, st->dQ,
-                   precision, (cudaStream_t)stream);
+    const int rc = run_rhs(&tmp, G, st->U, nullptr, 1, RK_A[stage], RK_B[stage], dt, st->U, st->dQ,
+                           precision, (cudaStream_t)stream);
+    if (rc || stage != 2 || !(G->cas.filter_sigma > 0.0)) return rc;
+    return launch_filter(G, st->U, (cudaStream_t)stream);
 }
 
 // Wall heat flux q_w = -K dT/dy and wall shear stress tau_w = tau_xy on the wall row of the

@@ -11,7 +11,8 @@ Workloads (shapes follow the paper's cases; there is no dataset):
 * ``sbli_case`` -- oblique-shock / boundary-layer interaction, 2048 x 256 cells, domain and
   freestream of the Mach 5.92 case of Table 3 (x 19-254, y 0-36, kappa_y = 0.15, T_inf = 1110.5 K,
   p_inf = 60967 Pa); Mach number drawn in [6, 9] and flow deflection in [8, 14] degrees from the seed;
-  artificial diffusivity on.
+  artificial diffusivity on; the conserved state is low-pass filtered after every RK step
+  (strength 0.05 on the grid-to-grid mode).
 * ``thermo_states`` -- independent thermochemical states: T log-uniform in [300, 15000] K,
   rho log-uniform in [1e-4, 1] kg/m^3, mass fractions Dirichlet(1).
 """
@@ -32,7 +33,7 @@ def bl_case(nx=256, ny=64, seed=0, kind="cneq"):
         shock_deflection_deg=0.0, shock_x=0.0, shock_width=0.0,
         sponge_sigma=200.0, sponge_in=5.0, sponge_out=15.0, sponge_top_cells=max(2, (26 * ny) // 211),
         artificial_diffusivity=0, C_mu=0.002, C_beta=1.75, C_kappa=0.01, C_D=0.0,
-        noise_amp=1.0e-4, dt=2.0e-4,
+        noise_amp=1.0e-4, dt=2.0e-4, filter_sigma=0.0,
     )
 
 
@@ -49,7 +50,7 @@ def sbli_case(nx=2048, ny=256, seed=0, kind="cneq"):
         shock_deflection_deg=deflection, shock_x=120.0, shock_width=1.0,
         sponge_sigma=200.0, sponge_in=10.0, sponge_out=30.0, sponge_top_cells=max(2, (26 * ny) // 211),
         artificial_diffusivity=1, C_mu=0.002, C_beta=1.75, C_kappa=0.01, C_D=0.01,
-        noise_amp=1.0e-4, dt=2.0e-3,
+        noise_amp=1.0e-4, dt=2.0e-3, filter_sigma=0.05,
     )
 
 

@@ -106,6 +106,56 @@ def test_rk3_ten_steps_boundary_layer(table):
     assert A.grid_status(st.grid) == 0
 
 
+def test_state_filter_parity(table):
+    """Stage 2 with dt = 0 on a fresh state (dQ = 0) leaves U unchanged and then applies the
+    low-pass filter of the case: equal to the oracle's filter to rounding, and not a no-op."""
+    import torch
+    from paper_2210_05547_gb300 import abi as A
+    cfg = I.sbli_case(160, 48, seed=2)
+    cfg["noise_amp"] = 1e-2
+    cfg["filter_sigma"] = 0.2
+    gas, st = gpu_state(cfg)
+    case = oracle_case(table, cfg)
+    U0 = st.U.cpu().numpy()
+    A.rk_stage(st, 2, 0.0)
+    torch.cuda.synchronize()
+    got = F.unpack(5, cfg["nx"], cfg["ny"], st.U.cpu().numpy())
+    ref = F.unpack(5, cfg["nx"], cfg["ny"], F.filter_state(case, U0))
+    before = F.unpack(5, cfg["nx"], cfg["ny"], U0)
+    for k in ref:
+        scale = np.abs(ref[k]).max()
+        assert np.abs(got[k] - ref[k]).max() <= 2e-15 * scale, k
+        assert np.abs(ref[k] - before[k]).max() > 1e-6 * scale, k
+
+
+def test_rk3_steps_with_filter_sbli(table):
+    """Shock / boundary-layer case with the state filter on: 3 RK steps, GPU state against the
+    oracle's within 1e-13 plus the RHS tolerance carried through the stages (the filter is a
+    contraction: it adds only its own rounding)."""
+    import torch
+    from paper_2210_05547_gb300 import abi as A
+    cfg = I.sbli_case(128, 48, seed=1)
+    assert cfg["filter_sigma"] > 0
+    gas, st = gpu_state(cfg)
+    case = oracle_case(table, cfg)
+    U = st.U.cpu().numpy()
+    dQ = np.zeros_like(U)
+    carried = {name: 0.0 for name, _ in F.state_layout(5, cfg["nx"], cfg["ny"])}
+    for step in range(3):
+        for k in range(3):
+            tol, _ = F.parity_tolerance(case, U)
+            for name in carried:
+                carried[name] = 2.2 * carried[name] + cfg["dt"] * tol[name]
+            U, dQ, _ = F.rk_stage(case, U, dQ, k, cfg["dt"])
+            A.rk_stage(st, k, cfg["dt"])
+    torch.cuda.synchronize()
+    fg = F.unpack(5, cfg["nx"], cfg["ny"], st.U.cpu().numpy())
+    fo = F.unpack(5, cfg["nx"], cfg["ny"], U)
+    for name in fo:
+        err = np.abs(fg[name] - fo[name]).max()
+        assert err <= 1e-13 * np.abs(fo[name]).max() + carried[name], (name, err, carried[name])
+
+
 def test_full_size_sbli_rhs(table):
     """The timed workload (2048 x 256, artificial diffusivity on): one full RHS against the
     oracle, every entry."""
