@@ -47,10 +47,13 @@ enum hyp_gas_kind {
     HYP_GAS_CPG = 2      /* calorically perfect gas, Sutherland viscosity (Eqs. 22, 24) */
 };
 
-/* HYP_FP64: every step in binary64. HYP_MIXED: the transport and diffusion coefficients (Blottner,
- * Eucken, Wilke, Chapman-Enskog; Sec. 2.2.1, Eq. 19) and the forward-rate exponentials (Eq. 13) in
- * binary32; temperature inversion, species thermodynamics, equilibrium constants and backward
- * rates, the derivative operators, fluxes and the stage update in binary64. */
+/* HYP_FP64: every step in binary64. HYP_MIXED: in binary32 the transport and diffusion
+ * coefficients (Blottner, Eucken, Wilke, Chapman-Enskog; Sec. 2.2.1, Eq. 19), the forward-rate
+ * exponentials (Eq. 13) and the interior rows of the compact interpolations and derivatives that
+ * feed only the diffusive fluxes (Sec. 3.1); in binary64 the temperature inversion, species
+ * thermodynamics, equilibrium constants and backward rates, the operators feeding the convective
+ * fluxes, pressure and the artificial-diffusivity sensors, every divergence, the fluxes themselves
+ * and the stage update. */
 enum hyp_precision { HYP_FP64 = 0, HYP_MIXED = 1 };
 
 enum hyp_error {

@@ -101,6 +101,7 @@ struct LineOp {
     // Toeplitz interior reaches its fixed point within about 20 rows): wa, wb, lm, cprime there.
     int rc;
     double wac, wbc, lmc, cpc;
+    float wac_f, wbc_f, lmc_f, cpc_f;   // the same in binary32 (HYP_MIXED jobs)
     int ncl;                     // closure rows (<= 4)
     int crow[4], cstart[4], cnum[4];
     double cw[4][5];
@@ -119,9 +120,11 @@ struct LineJob {
     double wall_value;
     double scale;                // +1 or -1
     const double* metric;        // per output element along the line, nullable
+    const float* metric_f;       // binary32 copy of metric (HYP_MIXED jobs)
+    int f32ok;                   // under HYP_MIXED the constant-factor rows may run in binary32
 };
 
 cudaError_t launch_lines(const LineJob* d_jobs, int njobs, int max_blocks, const double* U,
-                         cudaStream_t s);
+                         cudaStream_t s, int mixed = 0);
 
 }  // namespace hyp

@@ -22,6 +22,13 @@
 // has only a few FP64 instructions per row and the grid holds a few warps per sub-partition, so
 // the rows of that constant stretch are software-pipelined: the loads for row r + 8 are issued
 // while row r is computed.
+//
+// Jobs marked f32ok run that constant stretch in binary32 under HYP_MIXED (the interpolations and
+// derivatives that feed only the diffusive fluxes): inputs are rounded with integer instructions,
+// the recurrences run on the FP32 pipe, the forward values of those rows are kept as binary32 in
+// the first half of their 8-byte storage slot, and outputs are widened back to binary64. Closure
+// rows and the first interior rows stay FP64.
+#include "fp32.cuh"
 #include "internal.h"
 
 namespace hyp {
@@ -113,8 +120,65 @@ __device__ __forceinline__ void fwd_rows_const(int r, int r1, double& d, Window&
     p += (long long)n * ies;
 }
 
-// Forward sweep over rows r..r1 of one kind of region (closure / per-row / constant interior).
+__device__ __forceinline__ float* slot32(double* p) { return reinterpret_cast<float*>(p); }
+__device__ __forceinline__ const float* slot32(const double* p) {
+    return reinterpret_cast<const float*>(p);
+}
+
+template <int KIND>
+__device__ __forceinline__ float interior_row32(float d, float p0, float p1, float p2, float p3,
+                                                float wa, float wb, float lm) {
+    if (KIND == 0) return fmaf(-lm, d, fmaf(wa, p1 + p2, wb * (p0 + p3)));
+    return fmaf(-lm, d, fmaf(wa, p2 - p1, wb * (p3 - p0)));
+}
+
+// The constant-factor rows r..r1 in binary32 (f32ok jobs under HYP_MIXED).
 template <int KIND, bool STORE>
+__device__ __forceinline__ void fwd_rows_const32(int r, int r1, double& d, Window& w,
+                                                 const double* __restrict__& p, long long ies,
+                                                 const LineOp& op, double* __restrict__ tmp,
+                                                 long long oes) {
+    const int n = r1 - r + 1;
+    if (n <= 0) return;
+    const float wa = op.wac_f, wb = op.wbc_f, lm = op.lmc_f;
+    const double* __restrict__ pp = p;
+    float df = f32_of(d), p0 = f32_of(w.p0), p1 = f32_of(w.p1), p2 = f32_of(w.p2);
+    double q[PF];   // raw prefetched inputs; rounded when used so the load latency stays hidden
+#pragma unroll
+    for (int k = 0; k < PF; ++k) q[k] = k < n ? pp[(long long)k * ies] : 0.0;
+    for (; r + PF - 1 <= r1; r += PF) {
+#pragma unroll
+        for (int k = 0; k < PF; ++k) {
+            const float p3 = f32_of(q[k]);
+            q[k] = r + PF + k <= r1 ? pp[(long long)(PF + k) * ies] : 0.0;
+            df = interior_row32<KIND>(df, p0, p1, p2, p3, wa, wb, lm);
+            if (STORE) *slot32(tmp + (long long)(r + k) * oes) = df;
+            p0 = p1;
+            p1 = p2;
+            p2 = p3;
+        }
+        pp += PF * ies;
+    }
+#pragma unroll
+    for (int k = 0; k < PF - 1; ++k) {
+        if (r + k <= r1) {
+            const float p3 = f32_of(q[k]);
+            df = interior_row32<KIND>(df, p0, p1, p2, p3, wa, wb, lm);
+            if (STORE) *slot32(tmp + (long long)(r + k) * oes) = df;
+            p0 = p1;
+            p1 = p2;
+            p2 = p3;
+        }
+    }
+    d = f64_of(df);
+    w.p0 = f64_of(p0);
+    w.p1 = f64_of(p1);
+    w.p2 = f64_of(p2);
+    p += (long long)n * ies;
+}
+
+// Forward sweep over rows r..r1 of one kind of region (closure / per-row / constant interior).
+template <int KIND, bool STORE, bool F32>
 __device__ __forceinline__ void fwd_span(int r, int r1, double& d, Window& w,
                                          const double* __restrict__ in,
                                          const double* __restrict__& p, long long ies,
@@ -145,7 +209,8 @@ __device__ __forceinline__ void fwd_span(int r, int r1, double& d, Window& w,
         }
         const int rcn = min(r1, li);
         if (r <= rcn) {
-            fwd_rows_const<KIND, STORE>(r, rcn, d, w, p, ies, op, tmp, oes);
+            if (F32) fwd_rows_const32<KIND, STORE>(r, rcn, d, w, p, ies, op, tmp, oes);
+            else fwd_rows_const<KIND, STORE>(r, rcn, d, w, p, ies, op, tmp, oes);
             r = rcn + 1;
         }
     }
@@ -215,23 +280,73 @@ __device__ __forceinline__ void back_rows_const(int r0, int r1, double& y,
     }
 }
 
-// Back substitution over rows r0 >= r >= r1, split at the constant-factor stretch.
 template <int OM>
+__device__ __forceinline__ void put32(double* __restrict__ out, long long oes, int r, float y,
+                                      float m) {
+    if (OM == 1) out[(long long)r * oes] = f64_of(y);
+    if (OM == 2) out[(long long)r * oes] = f64_of(-y);
+    if (OM == 3) out[(long long)r * oes] = f64_of(y * m);
+    if (OM == 4) out[(long long)r * oes] = f64_of(-y * m);
+}
+
+// The constant-factor rows r0 >= r >= r1 in binary32, reading the binary32 forward values.
+template <int OM>
+__device__ __forceinline__ void back_rows_const32(int r0, int r1, double& y,
+                                                  const double* __restrict__ tmp, long long oes,
+                                                  float cc, const float* __restrict__ met,
+                                                  double* __restrict__ out) {
+    const int n = r0 - r1 + 1;
+    if (n <= 0) return;
+    float yf = f32_of(y);
+    float q[PF], mq[PF];
+#pragma unroll
+    for (int k = 0; k < PF; ++k) {
+        q[k] = k < n ? *slot32(tmp + (long long)(r0 - k) * oes) : 0.0f;
+        mq[k] = (OM >= 3 && k < n) ? met[r0 - k] : 0.0f;
+    }
+    int r = r0;
+    for (; r - PF + 1 >= r1; r -= PF) {
+#pragma unroll
+        for (int k = 0; k < PF; ++k) {
+            const float t = q[k], m = mq[k];
+            const int rn = r - PF - k;
+            q[k] = rn >= r1 ? *slot32(tmp + (long long)rn * oes) : 0.0f;
+            if (OM >= 3) mq[k] = rn >= r1 ? met[rn] : 0.0f;
+            yf = fmaf(-cc, yf, t);
+            put32<OM>(out, oes, r - k, yf, m);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < PF - 1; ++k) {
+        if (r - k >= r1) {
+            yf = fmaf(-cc, yf, q[k]);
+            put32<OM>(out, oes, r - k, yf, mq[k]);
+        }
+    }
+    y = f64_of(yf);
+}
+
+// Back substitution over rows r0 >= r >= r1, split at the constant-factor stretch.
+template <int OM, bool F32>
 __device__ __forceinline__ void back_span(int r0, int r1, double& y, const LineOp& op,
                                           const double* __restrict__ tmp, long long oes,
                                           const double* __restrict__ met,
+                                          const float* __restrict__ met_f,
                                           double* __restrict__ out) {
     if (r0 < r1) return;
     const int li = op.last_interior, rc = op.rc;
     const int a = max(r1, li + 1);            // rows above the interior (right closure)
     if (r0 >= a) back_rows_var<OM>(r0, a, y, tmp, oes, op.cprime, met, out);
     const int c0 = min(r0, li), c1 = max(r1, rc);
-    if (c0 >= c1) back_rows_const<OM>(c0, c1, y, tmp, oes, op.cpc, met, out);
+    if (c0 >= c1) {
+        if (F32) back_rows_const32<OM>(c0, c1, y, tmp, oes, op.cpc_f, met_f, out);
+        else back_rows_const<OM>(c0, c1, y, tmp, oes, op.cpc, met, out);
+    }
     const int v0 = min(r0, rc - 1);
     if (v0 >= r1) back_rows_var<OM>(v0, r1, y, tmp, oes, op.cprime, met, out);
 }
 
-template <int KIND>
+template <int KIND, bool F32>
 __device__ __forceinline__ void forward(const LineJob& J, const LineOp& op,
                                         const double* __restrict__ in, double* __restrict__ tmp,
                                         int s, int e, int W) {
@@ -240,22 +355,51 @@ __device__ __forceinline__ void forward(const LineJob& J, const LineOp& op,
     double d = 0.0;
     Window w{0.0, 0.0, 0.0};
     const double* __restrict__ p = nullptr;
-    fwd_span<KIND, false>(fs, s - 1, d, w, in, p, ies, op, J.wall_value, tmp, oes);
-    fwd_span<KIND, true>(s, e, d, w, in, p, ies, op, J.wall_value, tmp, oes);
+    fwd_span<KIND, false, F32>(fs, s - 1, d, w, in, p, ies, op, J.wall_value, tmp, oes);
+    fwd_span<KIND, true, F32>(s, e, d, w, in, p, ies, op, J.wall_value, tmp, oes);
 }
 
-template <int OM>
+template <int OM, bool F32>
 __device__ __forceinline__ void backward(const LineOp& op, const double* __restrict__ tmp,
                                          long long oes, const double* __restrict__ met,
+                                         const float* __restrict__ met_f,
                                          double* __restrict__ out, int s, int e, int be) {
-    double y = tmp[(long long)be * oes];
+    // the last row is a closure row (FP64 storage) or, for lines without one, an interior row
+    const bool last32 = F32 && be >= op.rc && be <= op.last_interior;
+    double y = last32 ? f64_of(*slot32(tmp + (long long)be * oes)) : tmp[(long long)be * oes];
     if (be <= e) put<OM>(out, oes, be, y, OM >= 3 ? met[be] : 0.0);
-    back_span<0>(be - 1, e + 1, y, op, tmp, oes, met, out);     // warm-up rows past the segment
-    back_span<OM>(min(be - 1, e), s, y, op, tmp, oes, met, out);
+    back_span<0, F32>(be - 1, e + 1, y, op, tmp, oes, met, met_f, out);   // warm-up rows
+    back_span<OM, F32>(min(be - 1, e), s, y, op, tmp, oes, met, met_f, out);
+}
+
+template <bool F32>
+__device__ __forceinline__ void run_line(const LineJob& J, const LineOp& op,
+                                         const double* __restrict__ in, double* __restrict__ out,
+                                         double* __restrict__ tmp, int s, int e, int m, int W,
+                                         bool active) {
+    if (active && s <= e) {
+        if (op.kind == 0) forward<0, F32>(J, op, in, tmp, s, e, W);
+        else forward<1, F32>(J, op, in, tmp, s, e, W);
+    }
+    __syncthreads();
+    if (active && s <= e) {
+        const int be = min(e + W, m - 1);
+        const double* __restrict__ met = J.metric;
+        const float* __restrict__ met_f = J.metric_f;
+        const bool neg = J.scale < 0.0;
+        const long long oes = J.out_es;
+        if (met) {
+            if (neg) backward<4, F32>(op, tmp, oes, met, met_f, out, s, e, be);
+            else backward<3, F32>(op, tmp, oes, met, met_f, out, s, e, be);
+        } else {
+            if (neg) backward<2, F32>(op, tmp, oes, met, met_f, out, s, e, be);
+            else backward<1, F32>(op, tmp, oes, met, met_f, out, s, e, be);
+        }
+    }
 }
 
 __global__ void __launch_bounds__(LINE_BLOCK) k_lines(const LineJob* __restrict__ jobs,
-                                               const double* __restrict__ U) {
+                                               const double* __restrict__ U, int mixed) {
     const LineJob& J = jobs[blockIdx.y];
     const int nseg = J.nseg;
     const int lpb = blockDim.x / nseg;                  // lines per block
@@ -272,34 +416,19 @@ __global__ void __launch_bounds__(LINE_BLOCK) k_lines(const LineJob* __restrict_
         (J.in_state ? U + (size_t)J.in : J.in) + (long long)line * J.in_ls;
     double* __restrict__ out = J.out + (long long)line * J.out_ls;
     double* __restrict__ tmp = J.tmp + (long long)line * J.out_ls;
-    if (active && s <= e) {
-        if (op.kind == 0) forward<0>(J, op, in, tmp, s, e, W);
-        else forward<1>(J, op, in, tmp, s, e, W);
-    }
-    __syncthreads();
-    if (active && s <= e) {
-        const int be = min(e + W, m - 1);
-        const double* __restrict__ met = J.metric;
-        const bool neg = J.scale < 0.0;
-        const long long oes = J.out_es;
-        if (met) {
-            if (neg) backward<4>(op, tmp, oes, met, out, s, e, be);
-            else backward<3>(op, tmp, oes, met, out, s, e, be);
-        } else {
-            if (neg) backward<2>(op, tmp, oes, met, out, s, e, be);
-            else backward<1>(op, tmp, oes, met, out, s, e, be);
-        }
-    }
+    // uniform per block: every thread of a block works on the same job
+    if (mixed && J.f32ok) run_line<true>(J, op, in, out, tmp, s, e, m, W, active);
+    else run_line<false>(J, op, in, out, tmp, s, e, m, W, active);
 }
 
 }  // namespace
 
 cudaError_t launch_lines(const LineJob* d_jobs, int njobs, int max_blocks, const double* U,
-                         cudaStream_t s) {
+                         cudaStream_t s, int mixed) {
     if (njobs == 0) return cudaSuccess;
     dim3 block(LINE_BLOCK);
     dim3 grid(max_blocks, njobs);
-    k_lines<<<grid, block, 0, s>>>(d_jobs, U);
+    k_lines<<<grid, block, 0, s>>>(d_jobs, U, mixed);
     return cudaGetLastError();
 }
 

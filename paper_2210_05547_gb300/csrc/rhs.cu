@@ -100,6 +100,7 @@ struct hyp_grid {
     int nstate;
     long long off[NSP + 3];
     double *xi_c, *xi_f, *eta_c, *eta_f;
+    float* metf;                 // binary32 copies of the four metric arrays, in that order
     double *Uref, *sigma;
     uint8_t* mask;
     unsigned* status;
@@ -389,6 +390,10 @@ LineOp make_op(int kind, int dir, int n, int wall, std::vector<double>& data) {
         op.wbc = wb[li];
         op.lmc = lm[li];
         op.cpc = cp[li];
+        op.wac_f = (float)op.wac;
+        op.wbc_f = (float)op.wbc;
+        op.lmc_f = (float)op.lmc;
+        op.cpc_f = (float)op.cpc;
     }
     // store offsets into data (fixed up to device pointers later)
     const size_t base = data.size();
@@ -771,6 +776,8 @@ struct PlanBuilder {
         out_size.push_back(d.size(tout));
         ph_count[cur]++;
     }
+    // the last job added feeds only diffusive fluxes: binary32 allowed under HYP_MIXED
+    void f32() { jobs.back().f32ok = 1; }
     // Segment counts (at most 260 points per segment, more segments when a phase has too few
     // threads to occupy the GPU), forward-sweep storage and block counts per phase. Returns the
     // tmp doubles needed by the largest phase.
@@ -852,6 +859,7 @@ static void free_grid(hyp_grid* G) {
     cudaFree(G->opdata);
     cudaFree(G->jobs);
     cudaFree(G->linetmp);
+    cudaFree(G->metf);
     if (G->side) cudaStreamDestroy(G->side);
     for (int k = 0; k < 2; ++k) {
         if (G->fork[k]) cudaEventDestroy(G->fork[k]);
@@ -1125,6 +1133,8 @@ extern "C" int hyp_state_init(const hyp_gas* gas, const hyp_grid_desc* desc, con
     B.add(OY_ICF, S.rho_xf, NXF, S.rho_cn, NCN, nullptr);
     B.add(OX_IFC, S.mux_f, NXF, S.mux_c, NC, nullptr);
     B.add(OY_IFC, S.mvy_f, NYF, S.mvy_c, NC, nullptr);
+    // (the velocity gradients feed the artificial-diffusivity sensors, whose fourth differences
+    // would amplify binary32 rounding: they stay FP64 in every mode)
     B.begin(PH_AD1);
     B.add(OY_IFC, S.dudy_cn, NCN, S.dudy_t, NXF, nullptr);
     B.add(OY_IFC, S.dvdx_cn, NCN, S.dvdx_t, NXF, nullptr);
@@ -1133,32 +1143,50 @@ extern "C" int hyp_state_init(const hyp_gas* gas, const hyp_grid_desc* desc, con
     B.add(OX_IFC, S.dvdx_t, NXF, S.dvdx_c, NC, nullptr);
     B.begin(PH_MU1);
     B.add(OX_ICF, S.mu_e, NC, S.mu_xf, NXF, nullptr);
+    B.f32();
     B.begin(PH_MU2);
     B.add(OY_ICF, S.mu_xf, NXF, S.mu_cn, NCN, nullptr);
+    B.f32();
     B.begin(PH_FACE);
     for (int sp = 0; sp < NSP; ++sp) {
         B.add(OX_ICF, S.Y[sp], NC, S.Yx[sp], NXF, nullptr);
         B.add(OX_ICF, S.G[sp], NC, S.Gx[sp], NXF, nullptr);
+        B.f32();
         B.add(OX_ICF, S.h[sp], NC, S.hx[sp], NXF, nullptr);
+        B.f32();
         B.add(OX_DCF, S.X[sp], NC, S.dXdx[sp], NXF, G->xi_f);
+        B.f32();
         B.add(OY_ICF, S.Y[sp], NC, S.Yy[sp], NYF, nullptr);
         B.add(OY_ICF, S.G[sp], NC, S.Gy[sp], NYF, nullptr);
+        B.f32();
         B.add(OY_ICF, S.h[sp], NC, S.hy[sp], NYF, nullptr);
+        B.f32();
         B.add(OY_DCF, S.X[sp], NC, S.dXdy[sp], NYF, G->eta_f);
+        B.f32();
     }
     B.add(OX_ICF, S.H, NC, S.Hx, NXF, nullptr);
     B.add(OX_ICF, S.K, NC, S.Kx, NXF, nullptr);
+    B.f32();
     B.add(OX_ICF, S.tau_xx, NC, S.txx_x, NXF, nullptr);
+    B.f32();
     B.add(OX_ICF, S.v_c, NC, S.v_x, NXF, nullptr);
+    B.f32();
     B.add(OX_DCF, S.T, NC, S.dTdx, NXF, G->xi_f);
+    B.f32();
     B.add(OY_ICF, S.H, NC, S.Hy, NYF, nullptr);
     B.add(OY_ICF, S.K, NC, S.Ky, NYF, nullptr);
+    B.f32();
     B.add(OY_ICF, S.tau_yy, NC, S.tyy_y, NYF, nullptr);
+    B.f32();
     B.add(y_icf_u, S.u_c, NC, S.u_y, NYF, nullptr, 1.0, 0.0);
+    B.f32();
     B.add(wall ? OY_DCFW : OY_DCF, S.T, NC, S.dTdy, NYF, G->eta_f, 1.0, G->Tw_nd);
+    B.f32();
     B.begin(PH_FACEB);
     B.add(OY_IFC, S.tau_xy, NCN, S.txy_x, NXF, nullptr);
+    B.f32();
     B.add(OX_IFC, S.tau_xy, NCN, S.txy_y, NYF, nullptr);
+    B.f32();
     B.begin(PH_DIV);
     for (int sp = 1; sp < NSP; ++sp) {
         B.add(OX_DFC, S.Fsx[sp], NXF, S.DX + G->off[sp], NC, G->xi_c, -1.0);
@@ -1190,12 +1218,27 @@ extern "C" int hyp_state_init(const hyp_gas* gas, const hyp_grid_desc* desc, con
         free_grid(G);
         return cuda_fail(err, "cudaMalloc(jobs)");
     }
-    for (auto& j : B.jobs) j.tmp = G->linetmp + (size_t)j.tmp;
+    if (err == cudaSuccess) err = cudaMalloc(&G->metf, (2 * (nx + ny) + 2) * sizeof(float));
+    if (err != cudaSuccess) {
+        free_grid(G);
+        return cuda_fail(err, "cudaMalloc(metrics)");
+    }
+    std::vector<float> metf_h;
+    for (const auto* v : {&xi_c, &xi_f, &eta_c, &eta_f})
+        for (double x : *v) metf_h.push_back((float)x);
+    const double* met_d[4] = {G->xi_c, G->xi_f, G->eta_c, G->eta_f};
+    const long long met_off[4] = {0, nx, 2LL * nx + 1, 2LL * nx + 1 + ny};
+    for (auto& j : B.jobs) {
+        j.tmp = G->linetmp + (size_t)j.tmp;
+        for (int k = 0; k < 4; ++k)
+            if (j.metric == met_d[k]) j.metric_f = G->metf + met_off[k];
+    }
     // uploads
 #define UP(dst, src, bytes) HYP_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s))
     UP(G->opdata, opdata.data(), opdata.size() * sizeof(double));
     UP(G->ops, hops.data(), NOPS * sizeof(LineOp));
     UP(G->jobs, B.jobs.data(), B.jobs.size() * sizeof(LineJob));
+    UP(G->metf, metf_h.data(), metf_h.size() * sizeof(float));
     UP(G->xi_c, xi_c.data(), nx * sizeof(double));
     UP(G->xi_f, xi_f.data(), (nx + 1) * sizeof(double));
     UP(G->eta_c, eta_c.data(), ny * sizeof(double));
@@ -1301,15 +1344,16 @@ static int run_rhs(const hyp_gas* gas, hyp_grid* G, const double* U, double* dUd
     const Dims& d = G->d;
     const long long nc = d.size(NC);
     cudaError_t e1 = cudaSuccess;
+    const bool mixed = precision == HYP_MIXED;
+    const int mx = mixed ? 1 : 0;
     TIMED(KID_LINES_STATE, e1 = launch_lines(G->jobs + G->ph_start[PH_P1], G->ph_count[PH_P1],
-                                             G->ph_blocks[PH_P1], U, s));
+                                             G->ph_blocks[PH_P1], U, s, mx));
     HYP_CUDA(e1);
     TIMED(KID_FACE_VEL, (k_face_vel<<<blocks_for(d.size(NXF) + d.size(NYF), 256), 256, 0, s>>>(v, U, S)));
     // fork: velocity gradients and the artificial-diffusivity line phases do not need the closure
     cudaStream_t s2 = G->side;
     HYP_CUDA(cudaEventRecord(G->fork[0], s));
     HYP_CUDA(cudaStreamWaitEvent(s2, G->fork[0], 0));
-    const bool mixed = precision == HYP_MIXED;
     const int cb = (int)std::min<long long>(mixed ? G->closure_blocks_mixed : G->closure_blocks,
                                             (nc + 127) / 128);
     if (mixed) TIMED(KID_CLOSURE, (k_closure<true><<<cb, 128, 0, s>>>(g, v, U, S)));
@@ -1317,12 +1361,12 @@ static int run_rhs(const hyp_gas* gas, hyp_grid* G, const double* U, double* dUd
     HYP_CUDA(cudaGetLastError());
     G->cache_valid = 1;
     TIMED_ON(s2, KID_LINES_VELGRAD, e1 = launch_lines(G->jobs + G->ph_start[PH_P3], G->ph_count[PH_P3],
-                                                      G->ph_blocks[PH_P3], U, s2));
+                                                      G->ph_blocks[PH_P3], U, s2, mx));
     HYP_CUDA(e1);
     if (v.ad) {
-        TIMED_ON(s2, KID_LINES_AD, e1 = launch_lines(G->jobs + G->ph_start[PH_AD1], 2, G->ph_blocks[PH_AD1], U, s2));
+        TIMED_ON(s2, KID_LINES_AD, e1 = launch_lines(G->jobs + G->ph_start[PH_AD1], 2, G->ph_blocks[PH_AD1], U, s2, mx));
         HYP_CUDA(e1);
-        TIMED_ON(s2, KID_LINES_AD, e1 = launch_lines(G->jobs + G->ph_start[PH_AD2], 2, G->ph_blocks[PH_AD2], U, s2));
+        TIMED_ON(s2, KID_LINES_AD, e1 = launch_lines(G->jobs + G->ph_start[PH_AD2], 2, G->ph_blocks[PH_AD2], U, s2, mx));
         HYP_CUDA(e1);
         TIMED_ON(s2, KID_AD_PREP, (k_ad_prep<<<blocks_for(nc, 256), 256, 0, s2>>>(v, S)));
     }
@@ -1340,23 +1384,23 @@ static int run_rhs(const hyp_gas* gas, hyp_grid* G, const double* U, double* dUd
     // fork: viscosity to the corners, shear stress and its face interpolants beside the face phase
     HYP_CUDA(cudaEventRecord(G->fork[1], s));
     HYP_CUDA(cudaStreamWaitEvent(s2, G->fork[1], 0));
-    TIMED_ON(s2, KID_LINES_MU, e1 = launch_lines(G->jobs + G->ph_start[PH_MU1], 1, G->ph_blocks[PH_MU1], U, s2));
+    TIMED_ON(s2, KID_LINES_MU, e1 = launch_lines(G->jobs + G->ph_start[PH_MU1], 1, G->ph_blocks[PH_MU1], U, s2, mx));
     HYP_CUDA(e1);
-    TIMED_ON(s2, KID_LINES_MU, e1 = launch_lines(G->jobs + G->ph_start[PH_MU2], 1, G->ph_blocks[PH_MU2], U, s2));
+    TIMED_ON(s2, KID_LINES_MU, e1 = launch_lines(G->jobs + G->ph_start[PH_MU2], 1, G->ph_blocks[PH_MU2], U, s2, mx));
     HYP_CUDA(e1);
     TIMED_ON(s2, KID_STRESS_CN, (k_stress_cn<<<blocks_for(d.size(NCN), 256), 256, 0, s2>>>(v, S)));
     TIMED_ON(s2, KID_LINES_FACE, e1 = launch_lines(G->jobs + G->ph_start[PH_FACEB], G->ph_count[PH_FACEB],
-                                                   G->ph_blocks[PH_FACEB], U, s2));
+                                                   G->ph_blocks[PH_FACEB], U, s2, mx));
     HYP_CUDA(e1);
     HYP_CUDA(cudaEventRecord(G->join[1], s2));
     TIMED(KID_LINES_FACE, e1 = launch_lines(G->jobs + G->ph_start[PH_FACE], G->ph_count[PH_FACE],
-                                            G->ph_blocks[PH_FACE], U, s));
+                                            G->ph_blocks[PH_FACE], U, s, mx));
     HYP_CUDA(e1);
     HYP_CUDA(cudaStreamWaitEvent(s, G->join[1], 0));
     TIMED(KID_FLUX, (k_flux<<<blocks_for(d.size(NXF), 128), 128, 0, s>>>(v, U, S, 0)));
     TIMED(KID_FLUX, (k_flux<<<blocks_for(d.size(NYF), 128), 128, 0, s>>>(v, U, S, 1)));
     TIMED(KID_LINES_DIV, e1 = launch_lines(G->jobs + G->ph_start[PH_DIV], G->ph_count[PH_DIV],
-                                           G->ph_blocks[PH_DIV], U, s));
+                                           G->ph_blocks[PH_DIV], U, s, mx));
     HYP_CUDA(e1);
     TIMED(KID_ASSEMBLE, (k_assemble<<<blocks_for(G->nstate, 256), 256, 0, s>>>(
                             G->nstate, S.DX, S.DY, S.SRC, G->sigma, G->Uref, G->mask,

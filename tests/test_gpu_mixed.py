@@ -1,10 +1,11 @@
 """Mixed-precision path (HYP_MIXED) through the C ABI, against the FP64 oracle.
 
 HYP_MIXED evaluates the transport and diffusion coefficients (Blottner, Eucken, Wilke,
-Chapman-Enskog; Sec. 2.2.1, Eq. 19) and the forward-rate exponentials (Eq. 13) in binary32 and
-everything else (temperature inversion, species thermodynamics, equilibrium constants, backward
-rates, derivative operators, fluxes, stage update) in binary64. The stated error of each output
-and the bound held here:
+Chapman-Enskog; Sec. 2.2.1, Eq. 19), the forward-rate exponentials (Eq. 13) and the interior rows
+of the compact operators that feed only the diffusive fluxes in binary32, and everything else
+(temperature inversion, species thermodynamics, equilibrium constants, backward rates, the
+operators feeding convective fluxes and pressure, divergences, fluxes, stage update) in binary64.
+The stated error of each output and the bound held here:
 
 * conversion (hyp_round_f32): equal to the hardware round-to-nearest-even for every result in the
   normal binary32 range, widening back exact;
