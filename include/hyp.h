@@ -180,6 +180,45 @@ int hyp_rk_stage(hyp_state* st, int stage, double dt, int precision, void* strea
 int hyp_wall_fluxes(const hyp_gas* gas, const hyp_grid* grid, const double* U, double* q_w,
                     double* tau_w, int precision, void* stream);
 
+/* ---- Batched execution (serving many independent solves on one GPU) ----
+ * A batch advances several states, each with its own grid size, freestream, case and time step,
+ * with every step of the hot path in shared launches: one compact-operator launch per phase over
+ * the members' joined line jobs, and one persistent kernel per pointwise step whose blocks walk
+ * fixed-size tiles of the members. The kernels run the same arithmetic on each member's own
+ * scratch and caches as hyp_rk_stage, so a member's states are bit-identical alone and in any
+ * batch. Members must come from gases built from the same table and kind. A batch and its
+ * members are used from one host thread; a state may be in one batch at a time and must not be
+ * stepped by other calls while it is a member. */
+typedef struct hyp_batch hyp_batch;
+
+/* New empty batch computing in `precision` (HYP_FP64 or HYP_MIXED). Free with hyp_batch_free. */
+int hyp_batch_create(int precision, hyp_batch** out);
+
+/* Add (remove) a member. dt: the member's nondimensional time step. The state stays owned by the
+ * caller; removing it leaves its registers at the last completed step. */
+int hyp_batch_add(hyp_batch* b, hyp_state* st, double dt);
+int hyp_batch_remove(hyp_batch* b, hyp_state* st);
+
+/* use_graph != 0: capture one step into a CUDA graph and replay it while the membership stays
+ * the same. tile: points per persistent-kernel tile, a positive multiple of 128, or 0 (the
+ * default) for the autotuner: after each change of membership the next steps run one untimed
+ * step and then one timed step for each tile size in {256, 512, 1024, 2048}, and the fastest is
+ * kept. Those are real steps of every member; the tile size does not change any result. */
+int hyp_batch_configure(hyp_batch* b, int use_graph, int tile);
+
+/* Number of members (HOST int). */
+int hyp_batch_size(const hyp_batch* b, int* members);
+
+/* Current tile size and whether the autotuner has settled for this membership (HOST ints,
+ * each nullable). */
+int hyp_batch_tile(const hyp_batch* b, int* tile, int* tuned);
+
+/* nsteps full RK3 steps (three stages and, for members whose case sets it, the state filter)
+ * of every member, enqueued on `stream`. */
+int hyp_batch_step(hyp_batch* b, int nsteps, void* stream);
+
+void hyp_batch_free(hyp_batch* b);
+
 /* The binary64 -> binary32 rounding (nearest, ties to even; magnitudes below 1.18e-38 to signed
  * zero) and the exact widening back that HYP_MIXED uses between its binary64 and binary32
  * parts, done with integer instructions. x[n]: DEVICE input; y[n] (binary32) and back[n]

@@ -74,6 +74,14 @@ EXPORTS = {
     "hyp_rhs_noalloc": (_I, [_P, _P, _P, _P, _P]),
     "hyp_wall_fluxes": (_I, [_P, _P, _P, _P, _P, _I, _P]),
     "hyp_round_f32": (_I, [_I64, _P, _P, _P, _P]),
+    "hyp_batch_create": (_I, [_I, ctypes.POINTER(_P)]),
+    "hyp_batch_add": (_I, [_P, _P, _D]),
+    "hyp_batch_remove": (_I, [_P, _P]),
+    "hyp_batch_configure": (_I, [_P, _I, _I]),
+    "hyp_batch_size": (_I, [_P, ctypes.POINTER(_I)]),
+    "hyp_batch_tile": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "hyp_batch_step": (_I, [_P, _I, _P]),
+    "hyp_batch_free": (None, [_P]),
     "hyp_grid_profile": (_I, [_P, _I]),
     "hyp_grid_profile_read": (_I, [_P, _I, _P, _P]),
     "hyp_profile_count": (_I, []),
@@ -263,6 +271,47 @@ def round_f32(x, y=None, back=None, stream=None):
                                _dptr(y, n, torch.float32) if y is not None else None,
                                _dptr(back, n, torch.float64) if back is not None else None,
                                _stream(stream)))
+
+
+class Batch:
+    """hyp_batch: many states stepped in shared launches (members keep their own dt)."""
+
+    def __init__(self, precision=FP64, use_graph=False, tile=0):
+        h = ctypes.c_void_p()
+        _check(lib().hyp_batch_create(precision, ctypes.byref(h)))
+        self.handle = h
+        self.members = []
+        if use_graph or tile:
+            self.configure(use_graph, tile)
+
+    def configure(self, use_graph=False, tile=0):
+        _check(lib().hyp_batch_configure(self.handle, int(bool(use_graph)), int(tile)))
+
+    def add(self, state, dt):
+        _check(lib().hyp_batch_add(self.handle, state.handle, float(dt)))
+        self.members.append(state)
+
+    def remove(self, state):
+        _check(lib().hyp_batch_remove(self.handle, state.handle))
+        self.members.remove(state)
+
+    def size(self):
+        n = ctypes.c_int()
+        _check(lib().hyp_batch_size(self.handle, ctypes.byref(n)))
+        return n.value
+
+    def tile(self):
+        t, tuned = ctypes.c_int(), ctypes.c_int()
+        _check(lib().hyp_batch_tile(self.handle, ctypes.byref(t), ctypes.byref(tuned)))
+        return t.value, bool(tuned.value)
+
+    def step(self, nsteps=1, stream=None):
+        _check(lib().hyp_batch_step(self.handle, int(nsteps), _stream(stream)))
+
+    def __del__(self):
+        if getattr(self, "handle", None) is not None and _LIB is not None:
+            _LIB.hyp_batch_free(self.handle)
+            self.handle = None
 
 
 def grid_reference(grid, n):

@@ -13,138 +13,13 @@
 #include <string>
 #include <vector>
 
+#include "grid.h"
 #include "internal.h"
+#include "pointwise.cuh"
 #include "thermo.cuh"
 
 using namespace hyp;
 
-namespace {
-
-constexpr double RECOVERY = 0.85;
-constexpr double DUCROS_EPS = 1.0e-32;
-const double RK_A[3] = {0.0, -5.0 / 9.0, -153.0 / 128.0};
-const double RK_B[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};
-// nine-point truncated Gaussian filter weights (centre, +-1, +-2, +-3, +-4)
-__constant__ double c_gauss[5] = {3565.0 / 10368.0, 3091.0 / 12960.0, 1997.0 / 25920.0,
-                                  149.0 / 12960.0, 107.0 / 103680.0};
-
-enum Node { NC = 0, NXF = 1, NYF = 2, NCN = 3 };
-
-struct Dims {
-    int nx, ny;
-    int rows(Node t) const { return (t == NC || t == NXF) ? ny : ny + 1; }
-    int pitch(Node t) const { return (t == NC || t == NYF) ? nx : nx + 1; }
-    long long size(Node t) const { return (long long)rows(t) * pitch(t); }
-};
-
-struct Scratch {
-    // cell centres
-    double *ru_c, *rv_c, *T, *p, *H, *u_c, *v_c, *e, *a, *mu_e, *K, *beta, *Tcache;
-    double *Y[NSP], *X[NSP], *h[NSP], *Wd[NSP], *W[NSP], *G[NSP];
-    double *esc[NSP], *cvsc[NSP], *cvpc[NSP];   // species e, c_v, dc_v/dT at the cached T
-    double *dudx, *dvdy, *tau_xx, *tau_yy, *Gxx, *Gyy, *mux_c, *mvy_c;
-    double *dudy_c, *dvdx_c, *S, *div, *fsw, *raw[8], *filt[8];
-    // x-faces
-    double *rho_xf, *u_xf, *Yx[NSP], *Gx[NSP], *hx[NSP], *Hx, *Kx, *txx_x, *v_x, *dTdx,
-        *dXdx[NSP], *txy_x, *Fsx[NSP], *FEx, *mu_xf, *dudy_t, *dvdx_t, *mux_f;
-    // y-faces
-    double *rho_yf, *v_yf, *Yy[NSP], *Gy[NSP], *hy[NSP], *Hy, *Ky, *tyy_y, *u_y, *dTdy,
-        *dXdy[NSP], *txy_y, *Fsy[NSP], *FEy, *mvy_f;
-    // corners
-    double *dudy_cn, *dvdx_cn, *u_cn, *v_cn, *rho_cn, *mu_cn, *tau_xy, *Gxy;
-    // state-sized
-    double *DX, *DY, *SRC, *R;
-};
-
-// Kernel-side view of a grid (passed by value).
-struct GridView {
-    int nx, ny, wall, ad, nstate;
-    int predict;                 // Newton starts from a step off the cached species state
-    long long off[NSP + 3];
-    double Tw_nd;
-    double C_mu, C_beta, C_kappa, C_D;
-    const double *xi_c, *eta_c;
-    unsigned* status;
-};
-
-enum Phase {
-    PH_P1, PH_P3, PH_AD1, PH_AD2, PH_MU1, PH_MU2, PH_FACE, PH_FACEB, PH_DIV, PH_COUNT
-};
-
-// Launches of one right-hand side, as reported by the optional event profile.
-enum KernelId {
-    KID_LINES_STATE, KID_FACE_VEL, KID_CLOSURE, KID_LINES_VELGRAD, KID_LINES_AD, KID_AD_PREP,
-    KID_AD_RAW, KID_AD_GAUSS, KID_AD_COMBINE, KID_STRESS_C, KID_LINES_MU, KID_STRESS_CN,
-    KID_LINES_FACE, KID_FLUX, KID_LINES_DIV, KID_ASSEMBLE, KID_FILTER, KID_COUNT
-};
-const char* const KERNEL_NAMES[KID_COUNT] = {
-    "k_lines:state", "k_face_vel", "k_closure", "k_lines:velgrad", "k_lines:ad", "k_ad_prep",
-    "k_ad_raw", "k_gauss", "k_ad_combine", "k_stress_c", "k_lines:mu", "k_stress_cn",
-    "k_lines:face", "k_flux", "k_lines:div", "k_assemble", "k_filter"};
-
-struct EventProfile {
-    bool on = false;
-    std::vector<cudaEvent_t> ev;
-    std::vector<int> id;
-    size_t used = 0;
-    double ms[KID_COUNT] = {};
-    long long count[KID_COUNT] = {};
-};
-
-}  // namespace
-
-struct hyp_grid {
-    Dims d;
-    hyp_case cas;
-    GasDev gas;
-    int nstate;
-    long long off[NSP + 3];
-    double *xi_c, *xi_f, *eta_c, *eta_f;
-    float* metf;                 // binary32 copies of the four metric arrays, in that order
-    double *Uref, *sigma;
-    uint8_t* mask;
-    unsigned* status;
-    double* pool;
-    Scratch s;
-    LineOp* ops;
-    double* opdata;
-    LineJob* jobs;
-    int ph_start[PH_COUNT], ph_count[PH_COUNT], ph_blocks[PH_COUNT];
-    double* linetmp;
-    long long linetmp_n;
-    cudaStream_t stream;
-    double Tw_nd;
-    EventProfile* prof;
-    int cache_valid;             // the closure caches hold a previous evaluation
-    cudaStream_t side;           // second stream for phases that do not wait on the closure
-    cudaEvent_t fork[2], join[2];
-    int closure_blocks;          // resident blocks of k_closure on this GPU
-    int closure_blocks_mixed;    // the same for the mixed-precision closure
-    GridView view() const {
-        GridView v;
-        v.nx = d.nx;
-        v.ny = d.ny;
-        v.wall = cas.wall;
-        v.ad = cas.artificial_diffusivity;
-        v.nstate = nstate;
-        v.predict = cache_valid;
-        for (int i = 0; i < NSP + 3; ++i) v.off[i] = off[i];
-        v.Tw_nd = Tw_nd;
-        v.C_mu = cas.C_mu;
-        v.C_beta = cas.C_beta;
-        v.C_kappa = cas.C_kappa;
-        v.C_D = cas.C_D;
-        v.xi_c = xi_c;
-        v.eta_c = eta_c;
-        v.status = status;
-        return v;
-    }
-};
-
-struct hyp_state {
-    hyp_grid* grid;
-    double *U, *dQ;
-};
 
 namespace {
 
@@ -413,301 +288,52 @@ enum OpId { OX_ICF, OX_DCF, OX_IFC, OX_DFC, OY_ICF, OY_DCF, OY_IFC, OY_DFC, OY_I
 // Pointwise kernels
 // ---------------------------------------------------------------------------------------------
 
-__device__ __forceinline__ void atomic_status(unsigned* st, unsigned bits) {
-    if (bits) atomicOr(st, bits);
-}
+// Single-grid kernels: grid-stride loops over the bodies of pointwise.cuh.
+#define GRID_RANGE(n) (long long)blockIdx.x * blockDim.x, (long long)(n), (long long)gridDim.x * blockDim.x
 
-// (A) primitives and the closure at every cell centre (MIXED: binary32 transport, Sec. 2.2)
 template <bool MIXED>
-__global__ void __launch_bounds__(128) k_closure(GasDev g, GridView v, const double* __restrict__ U,
-                                                 Scratch s) {
-    const int n = v.nx * v.ny;
-    const bool cpg = g.kind == HYP_GAS_CPG;
-    const bool cneq = g.kind == HYP_GAS_CNEQ;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
-        const double rho = U[v.off[0] + idx];
-        const double irho = 1.0 / rho;
-        double Y[NSP];
-        double rest = rho;
-#pragma unroll
-        for (int sp = 1; sp < NSP; ++sp) {
-            const double r = U[v.off[sp] + idx];
-            Y[sp] = r * irho;
-            rest -= r;
-        }
-        Y[0] = rest * irho;
-        const double rhoE = U[v.off[NSP] + idx];
-        const double u = s.ru_c[idx] * irho;
-        const double vv = s.rv_c[idx] * irho;
-        const double e = rhoE * irho - 0.5 * (u * u + vv * vv);
-        double T, p, mu, k, a;
-        double h[NSP], wd[NSP], X[NSP], W[NSP], Wd[NSP];
-        if (cpg) {
-            T = g.gamma_inf * e;
-            p = rho * (g.gamma_inf - 1.0) / g.gamma_inf * T;
-            const double Td = T * g.T_ref;
-            mu = SUTH_C1 * Td * sqrt(Td) / (Td + SUTH_TS) / g.mu_inf;
-            k = mu;
-            a = sqrt(g.gamma_inf * p / rho);
-#pragma unroll
-            for (int sp = 0; sp < NSP; ++sp) h[sp] = wd[sp] = X[sp] = W[sp] = Wd[sp] = 0.0;
-        } else {
-            const double e_si = e * g.a_inf * g.a_inf;
-            double T0 = s.Tcache[idx];
-            if (v.predict) {
-                // second-order step from the cached species state with the new composition:
-                // e(Tc + d) ~ ec + cv d + cvp d^2 / 2 = e
-                double ec = 0.0, cvc = 0.0, cvpc = 0.0;
-#pragma unroll
-                for (int sp = 0; sp < NSP; ++sp) {
-                    ec += Y[sp] * s.esc[sp][idx];
-                    cvc += Y[sp] * s.cvsc[sp][idx];
-                    cvpc += Y[sp] * s.cvpc[sp][idx];
-                }
-                const double icv = 1.0 / cvc;
-                const double d1 = (e_si - ec) * icv;
-                T0 += d1 - 0.5 * cvpc * d1 * d1 * icv;
-            }
-            ClosureOut o;
-            closure_si_p<MIXED>(g, rho * g.rho_inf, e_si, Y, T0, cneq, cneq, o);
-            atomic_status(v.status, o.status);
-            s.Tcache[idx] = o.T;
-#pragma unroll
-            for (int sp = 0; sp < NSP; ++sp) {
-                s.esc[sp][idx] = o.es[sp];
-                s.cvsc[sp][idx] = o.cvs[sp];
-                s.cvpc[sp][idx] = o.cvps[sp];
-            }
-            T = o.T / g.T_ref;
-            p = o.p / (g.rho_inf * g.a_inf * g.a_inf);
-            mu = o.mu / g.mu_inf;
-            k = o.k / g.k_inf;
-            a = o.a / g.a_inf;
-            double ym = 0.0;
-#pragma unroll
-            for (int sp = 0; sp < NSP; ++sp) ym += Y[sp] * g.invM[sp];
-            const double wscale = g.L_ref / (g.rho_inf * g.a_inf);
-            const double inva2 = 1.0 / (g.a_inf * g.a_inf);
-#pragma unroll
-            for (int sp = 0; sp < NSP; ++sp) {
-                h[sp] = o.h[sp] * inva2;
-                wd[sp] = o.wdot[sp] * wscale;
-                X[sp] = o.X[sp];
-                W[sp] = cneq ? rho * g.M[sp] * ym : 0.0;
-                Wd[sp] = cneq ? W[sp] * (o.D[sp] * g.rho_inf / g.mu_inf) / g.Re : 0.0;
-            }
-        }
-        s.T[idx] = T;
-        s.p[idx] = p;
-        s.H[idx] = (rhoE + p) * irho;
-        s.u_c[idx] = u;
-        s.v_c[idx] = vv;
-        s.e[idx] = e;
-        s.a[idx] = a;
-        s.mu_e[idx] = mu / g.Re;
-        s.K[idx] = k / (g.Re * g.Pr);
-        if (!v.ad) s.beta[idx] = 0.0;
-#pragma unroll
-        for (int sp = 0; sp < NSP; ++sp) {
-            s.Y[sp][idx] = Y[sp];
-            s.X[sp][idx] = X[sp];
-            s.h[sp][idx] = h[sp];
-            s.Wd[sp][idx] = Wd[sp];
-            s.W[sp][idx] = W[sp];
-            if (!v.ad) s.G[sp][idx] = Wd[sp];
-        }
-#pragma unroll
-        for (int sp = 1; sp < NSP; ++sp) s.SRC[v.off[sp] + idx] = wd[sp];
-    }
+__global__ void __launch_bounds__(128) k_closure(GasDev g, Scales sc, GridView v,
+                                                 const double* __restrict__ U, Scratch s) {
+    closure_body<MIXED>(g, sc, v, U, s, GRID_RANGE((long long)v.nx * v.ny));
 }
 
-// (B) face velocities
 __global__ void k_face_vel(GridView v, const double* __restrict__ U, Scratch s) {
-    const int nxf = v.ny * (v.nx + 1), nyf = (v.ny + 1) * v.nx;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nxf + nyf; i += gridDim.x * blockDim.x) {
-        if (i < nxf) {
-            const double m = U[v.off[NSP + 1] + i];
-            const double u = m / s.rho_xf[i];
-            s.u_xf[i] = u;
-            s.mux_f[i] = m * u;
-        } else {
-            const int j = i - nxf;
-            const double m = U[v.off[NSP + 2] + j];
-            const double vv = m / s.rho_yf[j];
-            s.v_yf[j] = vv;
-            s.mvy_f[j] = m * vv;
-        }
-    }
+    face_vel_body(v, U, s, GRID_RANGE((long long)v.ny * (v.nx + 1) + (long long)(v.ny + 1) * v.nx));
 }
 
-// (D) artificial diffusivity: strain-rate magnitude, dilatation, Ducros switch
 __global__ void k_ad_prep(GridView v, Scratch s) {
-    const int n = v.nx * v.ny;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const double ux = s.dudx[i], vy = s.dvdy[i], uy = s.dudy_c[i], vx = s.dvdx_c[i];
-        const double sxy = uy + vx;
-        s.S[i] = sqrt(ux * ux + vy * vy + 0.5 * sxy * sxy);
-        const double dv = ux + vy;
-        const double om = vx - uy;
-        s.div[i] = dv;
-        s.fsw[i] = dv < 0.0 ? dv * dv / (dv * dv + om * om + DUCROS_EPS) : 0.0;
-    }
+    ad_prep_body(s, GRID_RANGE((long long)v.nx * v.ny));
 }
 
-__device__ __forceinline__ double d4x(const double* f, int j, int i, int nx) {
-    const int c = min(max(i, 2), nx - 3);
-    const double* r = f + (long long)j * nx + c;
-    return r[-2] - 4.0 * r[-1] + 6.0 * r[0] - 4.0 * r[1] + r[2];
+__global__ void k_ad_raw(int cneq, GridView v, const double* __restrict__ U, Scratch s) {
+    ad_raw_body(cneq != 0, v, U, s, GRID_RANGE((long long)v.nx * v.ny));
 }
 
-__device__ __forceinline__ double d4y(const double* f, int j, int i, int nx, int ny) {
-    const int c = min(max(j, 2), ny - 3);
-    const double* r = f + (long long)c * nx + i;
-    return r[-2 * nx] - 4.0 * r[-nx] + 6.0 * r[0] - 4.0 * r[nx] + r[2 * nx];
-}
-
-__global__ void k_ad_raw(GasDev g, GridView v, const double* __restrict__ U, Scratch s) {
-    const int n = v.nx * v.ny;
-    const bool cneq = g.kind == HYP_GAS_CNEQ;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
-        const int j = idx / v.nx, i = idx - j * v.nx;
-        const double dx = 1.0 / v.xi_c[i], dy = 1.0 / v.eta_c[j];
-        const double rho = U[v.off[0] + idx];
-        s.raw[0][idx] = v.C_mu * rho *
-                        fabs(d4x(s.S, j, i, v.nx) * dx * dx + d4y(s.S, j, i, v.nx, v.ny) * dy * dy);
-        s.raw[1][idx] = v.C_beta * rho * s.fsw[idx] *
-                        fabs(d4x(s.div, j, i, v.nx) * dx * dx + d4y(s.div, j, i, v.nx, v.ny) * dy * dy);
-        s.raw[2][idx] = v.C_kappa * rho * s.a[idx] / s.T[idx] *
-                        fabs(d4x(s.e, j, i, v.nx) * dx + d4y(s.e, j, i, v.nx, v.ny) * dy);
-#pragma unroll
-        for (int sp = 0; sp < NSP; ++sp)
-            s.raw[3 + sp][idx] =
-                cneq ? v.C_D * s.a[idx] *
-                           fabs(d4x(s.Y[sp], j, i, v.nx) * dx + d4y(s.Y[sp], j, i, v.nx, v.ny) * dy)
-                     : 0.0;
-    }
-}
-
-// Gaussian filter of the eight raw diffusivities along x (dir 0) or y (dir 1); indices clamp.
 __global__ void k_gauss(GridView v, Scratch s, int dir) {
-    const int n = v.nx * v.ny;
-    const int f = blockIdx.y;
-    const double* __restrict__ in = dir == 0 ? s.raw[f] : s.filt[f];
-    double* __restrict__ out = dir == 0 ? s.filt[f] : s.raw[f];
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
-        const int j = idx / v.nx, i = idx - j * v.nx;
-        double acc = c_gauss[0] * in[idx];
-        if (dir == 0) {
-            const double* r = in + (long long)j * v.nx;
-#pragma unroll
-            for (int d = 1; d <= 4; ++d)
-                acc += c_gauss[d] * (r[max(i - d, 0)] + r[min(i + d, v.nx - 1)]);
-        } else {
-#pragma unroll
-            for (int d = 1; d <= 4; ++d)
-                acc += c_gauss[d] * (in[(long long)max(j - d, 0) * v.nx + i] +
-                                     in[(long long)min(j + d, v.ny - 1) * v.nx + i]);
-        }
-        out[idx] = acc;
-    }
+    gauss_body(v, s, dir, GRID_RANGE(8LL * v.nx * v.ny));
 }
 
 __global__ void k_ad_combine(GridView v, Scratch s) {
-    const int n = v.nx * v.ny;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        s.mu_e[i] += s.raw[0][i];
-        s.beta[i] = s.raw[1][i];
-        s.K[i] += s.raw[2][i];
-#pragma unroll
-        for (int sp = 0; sp < NSP; ++sp) s.G[sp][i] = s.Wd[sp][i] + s.W[sp][i] * s.raw[3 + sp][i];
-    }
+    ad_combine_body(s, GRID_RANGE((long long)v.nx * v.ny));
 }
 
-// (F, I) normal stresses and momentum fluxes at centres (Eqs. 5, 6, 9)
 __global__ void k_stress_c(GridView v, Scratch s) {
-    const int n = v.nx * v.ny;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const double ux = s.dudx[i], vy = s.dvdy[i];
-        const double dv = ux + vy;
-        const double mu = s.mu_e[i], b = s.beta[i];
-        const double txx = mu * (2.0 * ux - 2.0 / 3.0 * dv) + b * dv;
-        const double tyy = mu * (2.0 * vy - 2.0 / 3.0 * dv) + b * dv;
-        s.tau_xx[i] = txx;
-        s.tau_yy[i] = tyy;
-        // normal momentum fluxes: rho u u formed on the faces, interpolated to the centres
-        s.Gxx[i] = s.mux_c[i] + s.p[i] - txx;
-        s.Gyy[i] = s.mvy_c[i] + s.p[i] - tyy;
-    }
+    stress_c_body(s, GRID_RANGE((long long)v.nx * v.ny));
 }
 
-// (F, I) shear stress and cross momentum flux at corners
 __global__ void k_stress_cn(GridView v, Scratch s) {
-    const int n = (v.nx + 1) * (v.ny + 1);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const double txy = s.mu_cn[i] * (s.dudy_cn[i] + s.dvdx_cn[i]);
-        s.tau_xy[i] = txy;
-        s.Gxy[i] = s.rho_cn[i] * s.u_cn[i] * s.v_cn[i] - txy;
-    }
+    stress_cn_body(s, GRID_RANGE((long long)(v.nx + 1) * (v.ny + 1)));
 }
 
-// (G, H) species and energy fluxes at x-faces (dir 0) or y-faces (dir 1)
 __global__ void k_flux(GridView v, const double* __restrict__ U, Scratch s, int dir) {
-    const int n = dir == 0 ? v.ny * (v.nx + 1) : (v.ny + 1) * v.nx;
-    const double* __restrict__ mom = U + v.off[NSP + 1 + dir];
-    double* const* Yf = dir == 0 ? s.Yx : s.Yy;
-    double* const* Gf = dir == 0 ? s.Gx : s.Gy;
-    double* const* hf = dir == 0 ? s.hx : s.hy;
-    double* const* dX = dir == 0 ? s.dXdx : s.dXdy;
-    double* const* Fs = dir == 0 ? s.Fsx : s.Fsy;
-    const double* Hf = dir == 0 ? s.Hx : s.Hy;
-    const double* Kf = dir == 0 ? s.Kx : s.Ky;
-    const double* dT = dir == 0 ? s.dTdx : s.dTdy;
-    const double* tn = dir == 0 ? s.txx_x : s.tyy_y;      // normal stress at the face
-    const double* tsh = dir == 0 ? s.txy_x : s.txy_y;     // shear stress at the face
-    const double* un = dir == 0 ? s.u_xf : s.v_yf;        // velocity normal to the face
-    const double* ut = dir == 0 ? s.v_x : s.u_y;          // tangential velocity
-    double* FE = dir == 0 ? s.FEx : s.FEy;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const bool wallface = dir == 1 && v.wall && i < v.nx;
-        double g[NSP], J[NSP], sum = 0.0;
-#pragma unroll
-        for (int sp = 0; sp < NSP; ++sp) {
-            g[sp] = Gf[sp][i] * dX[sp][i];
-            sum += g[sp];
-        }
-        double q = -Kf[i] * dT[i];
-        const double m = mom[i];
-#pragma unroll
-        for (int sp = 0; sp < NSP; ++sp) {
-            J[sp] = wallface ? 0.0 : -(g[sp] - Yf[sp][i] * sum);
-            q += hf[sp][i] * J[sp];
-        }
-#pragma unroll
-        for (int sp = 1; sp < NSP; ++sp) Fs[sp][i] = m * Yf[sp][i] + J[sp];
-        // tau . u normal component: x-face tau_xx u + tau_xy v; y-face tau_xy u + tau_yy v
-        const double work = dir == 0 ? tn[i] * un[i] + tsh[i] * ut[i] : tsh[i] * ut[i] + tn[i] * un[i];
-        FE[i] = m * Hf[i] + q - work;
-    }
+    flux_body(v, U, s, dir, GRID_RANGE(dir == 0 ? (long long)v.ny * (v.nx + 1) : (long long)(v.ny + 1) * v.nx));
 }
 
-// (J) sum of divergences, sources and sponge; Dirichlet rows; optional RK stage update
-__global__ void k_assemble(int n, const double* __restrict__ DX, const double* __restrict__ DY,
-                           const double* __restrict__ SRC, const double* __restrict__ sigma,
-                           const double* __restrict__ Uref, const uint8_t* __restrict__ mask,
-                           double* __restrict__ U, double* __restrict__ out, double* __restrict__ dQ,
-                           int rk, double A, double B, double dt) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const double u = U[i];
-        double r = DX[i] + DY[i] + SRC[i] - sigma[i] * (u - Uref[i]);
-        if (mask[i]) r = 0.0;
-        if (rk) {
-            const double q = A * dQ[i] + dt * r;
-            dQ[i] = q;
-            U[i] = u + B * q;
-        } else {
-            out[i] = r;
-        }
-    }
+__global__ void k_assemble(long long n, AssembleArgs a) { assemble_body(a, GRID_RANGE(n)); }
+
+__global__ void k_filter(int nx, int ny, long long nstate, const double* __restrict__ in,
+                         double* __restrict__ out, int dir, double sigma) {
+    filter_body(nx, ny, in, out, dir, sigma, GRID_RANGE(nstate));
 }
 
 __global__ void k_fill(double* p, long long n, double val) {
@@ -1238,6 +864,7 @@ extern "C" int hyp_state_init(const hyp_gas* gas, const hyp_grid_desc* desc, con
     UP(G->opdata, opdata.data(), opdata.size() * sizeof(double));
     UP(G->ops, hops.data(), NOPS * sizeof(LineOp));
     UP(G->jobs, B.jobs.data(), B.jobs.size() * sizeof(LineJob));
+    G->hjobs = B.jobs;
     UP(G->metf, metf_h.data(), metf_h.size() * sizeof(float));
     UP(G->xi_c, xi_c.data(), nx * sizeof(double));
     UP(G->xi_f, xi_f.data(), (nx + 1) * sizeof(double));
@@ -1356,8 +983,9 @@ static int run_rhs(const hyp_gas* gas, hyp_grid* G, const double* U, double* dUd
     HYP_CUDA(cudaStreamWaitEvent(s2, G->fork[0], 0));
     const int cb = (int)std::min<long long>(mixed ? G->closure_blocks_mixed : G->closure_blocks,
                                             (nc + 127) / 128);
-    if (mixed) TIMED(KID_CLOSURE, (k_closure<true><<<cb, 128, 0, s>>>(g, v, U, S)));
-    else TIMED(KID_CLOSURE, (k_closure<false><<<cb, 128, 0, s>>>(g, v, U, S)));
+    const Scales sc = scales_of(g);
+    if (mixed) TIMED(KID_CLOSURE, (k_closure<true><<<cb, 128, 0, s>>>(g, sc, v, U, S)));
+    else TIMED(KID_CLOSURE, (k_closure<false><<<cb, 128, 0, s>>>(g, sc, v, U, S)));
     HYP_CUDA(cudaGetLastError());
     G->cache_valid = 1;
     TIMED_ON(s2, KID_LINES_VELGRAD, e1 = launch_lines(G->jobs + G->ph_start[PH_P3], G->ph_count[PH_P3],
@@ -1373,8 +1001,8 @@ static int run_rhs(const hyp_gas* gas, hyp_grid* G, const double* U, double* dUd
     HYP_CUDA(cudaEventRecord(G->join[0], s2));
     HYP_CUDA(cudaStreamWaitEvent(s, G->join[0], 0));
     if (v.ad) {
-        TIMED(KID_AD_RAW, (k_ad_raw<<<blocks_for(nc, 256), 256, 0, s>>>(g, v, U, S)));
-        dim3 gg(blocks_for(nc, 256), 8);
+        TIMED(KID_AD_RAW, (k_ad_raw<<<blocks_for(nc, 256), 256, 0, s>>>(g.kind == HYP_GAS_CNEQ, v, U, S)));
+        const int gg = blocks_for(8 * nc, 256);
         TIMED(KID_AD_GAUSS, (k_gauss<<<gg, 256, 0, s>>>(v, S, 0)));
         TIMED(KID_AD_GAUSS, (k_gauss<<<gg, 256, 0, s>>>(v, S, 1)));
         TIMED(KID_AD_COMBINE, (k_ad_combine<<<blocks_for(nc, 256), 256, 0, s>>>(v, S)));
@@ -1402,9 +1030,9 @@ static int run_rhs(const hyp_gas* gas, hyp_grid* G, const double* U, double* dUd
     TIMED(KID_LINES_DIV, e1 = launch_lines(G->jobs + G->ph_start[PH_DIV], G->ph_count[PH_DIV],
                                            G->ph_blocks[PH_DIV], U, s, mx));
     HYP_CUDA(e1);
-    TIMED(KID_ASSEMBLE, (k_assemble<<<blocks_for(G->nstate, 256), 256, 0, s>>>(
-                            G->nstate, S.DX, S.DY, S.SRC, G->sigma, G->Uref, G->mask,
-                            rk ? Urk : (double*)U, dUdt, dQ, rk, A, Bc, dt)));
+    const AssembleArgs aa{S.DX, S.DY, S.SRC, G->sigma, G->Uref, G->mask,
+                          rk ? Urk : (double*)U, dUdt, dQ, rk, A, Bc, dt};
+    TIMED(KID_ASSEMBLE, (k_assemble<<<blocks_for(G->nstate, 256), 256, 0, s>>>(G->nstate, aa)));
     HYP_CUDA(cudaGetLastError());
     return HYP_OK;
 }
@@ -1419,66 +1047,8 @@ extern "C" int hyp_rhs(const hyp_gas* gas, const hyp_grid* grid, const double* U
                    (cudaStream_t)stream);
 }
 
-// Low-pass filter of the conserved state along x (dir 0) or y (dir 1) lines of every field:
-// out_i = in_i - sigma (D_m in)_i with the binomial 2m-th difference of weights c_filter_w,
-// m = min(5, distance to the nearer end of the line); end points copied. HBM-bound: one read of
-// the line neighbours (cached) and one write per entry.
-__constant__ double c_filter_w[5][11];   // [m - 1][n + m] = (-1)^n C(2m, m + n) / 4^m
-
-__global__ void k_filter(int nx, int ny, long long nstate, const double* __restrict__ in,
-                         double* __restrict__ out, int dir, double sigma) {
-    const long long nc = (long long)nx * ny;
-    const long long nxf = (long long)(nx + 1) * ny;
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nstate;
-         idx += (long long)gridDim.x * blockDim.x) {
-        long long local;
-        int pitch, rows;
-        if (idx < (NSP + 1) * nc) {
-            local = idx % nc;
-            pitch = nx;
-            rows = ny;
-        } else if (idx < (NSP + 1) * nc + nxf) {
-            local = idx - (NSP + 1) * nc;
-            pitch = nx + 1;
-            rows = ny;
-        } else {
-            local = idx - (NSP + 1) * nc - nxf;
-            pitch = nx;
-            rows = ny + 1;
-        }
-        const int row = (int)(local / pitch), col = (int)(local - (long long)row * pitch);
-        const int pos = dir == 0 ? col : row;
-        const int n = dir == 0 ? pitch : rows;
-        const long long stride = dir == 0 ? 1 : pitch;
-        const int m = min(min(pos, n - 1 - pos), 5);
-        const double f = in[idx];
-        if (m == 0) {
-            out[idx] = f;
-            continue;
-        }
-        const double* w = c_filter_w[m - 1];
-        const double* p = in + idx - m * stride;
-        double acc = 0.0;
-        for (int k = 0; k <= 2 * m; ++k) acc = fma(w[k], p[k * stride], acc);
-        out[idx] = fma(-sigma, acc, f);
-    }
-}
-
+// The state filter after the last RK stage: x pass into the scratch state vector, y pass back.
 static int launch_filter(hyp_grid* G, double* U, cudaStream_t s) {
-    static std::once_flag once;
-    static cudaError_t werr = cudaSuccess;
-    std::call_once(once, [] {
-        double w[5][11] = {};
-        for (int m = 1; m <= 5; ++m) {
-            double c = 1.0;                                   // C(2m, 0)
-            for (int k = 0; k <= 2 * m; ++k) {
-                w[m - 1][k] = ((k - m) % 2 == 0 ? c : -c) / (double)(1 << (2 * m));
-                c = c * (2 * m - k) / (k + 1);                // C(2m, k + 1), exact in binary64
-            }
-        }
-        werr = cudaMemcpyToSymbol(c_filter_w, w, sizeof(w));
-    });
-    HYP_CUDA(werr);
     const double sigma = G->cas.filter_sigma;
     const int blocks = blocks_for(G->nstate, 256);
     TIMED(KID_FILTER, (k_filter<<<blocks, 256, 0, s>>>(G->d.nx, G->d.ny, G->nstate, U, G->s.R, 0, sigma)));
@@ -1680,15 +1250,15 @@ extern "C" int hyp_rhs_noalloc(const hyp_gas* gas, const hyp_grid* grid, const d
     };
     HYP_CUDA(lines(PH_P1, G->ph_count[PH_P1]));
     k_face_vel<<<blocks_for(d.size(NXF) + d.size(NYF), 256), 256, 0, s>>>(v, U, S);
-    k_closure<false><<<blocks_for(nc, 128), 128, 0, s>>>(g, v, U, S);
+    k_closure<false><<<blocks_for(nc, 128), 128, 0, s>>>(g, scales_of(g), v, U, S);
     HYP_CUDA(cudaGetLastError());
     HYP_CUDA(lines(PH_P3, G->ph_count[PH_P3]));
     if (v.ad) {
         HYP_CUDA(lines(PH_AD1, 2));
         HYP_CUDA(lines(PH_AD2, 2));
         k_ad_prep<<<blocks_for(nc, 256), 256, 0, s>>>(v, S);
-        k_ad_raw<<<blocks_for(nc, 256), 256, 0, s>>>(g, v, U, S);
-        dim3 gg(blocks_for(nc, 256), 8);
+        k_ad_raw<<<blocks_for(nc, 256), 256, 0, s>>>(g.kind == HYP_GAS_CNEQ, v, U, S);
+        const int gg = blocks_for(8 * nc, 256);
         k_gauss<<<gg, 256, 0, s>>>(v, S, 0);
         k_gauss<<<gg, 256, 0, s>>>(v, S, 1);
         k_ad_combine<<<blocks_for(nc, 256), 256, 0, s>>>(v, S);
@@ -1703,9 +1273,9 @@ extern "C" int hyp_rhs_noalloc(const hyp_gas* gas, const hyp_grid* grid, const d
     k_flux<<<blocks_for(d.size(NXF), 128), 128, 0, s>>>(v, U, S, 0);
     k_flux<<<blocks_for(d.size(NYF), 128), 128, 0, s>>>(v, U, S, 1);
     HYP_CUDA(lines(PH_DIV, G->ph_count[PH_DIV]));
-    k_assemble<<<blocks_for(G->nstate, 256), 256, 0, s>>>(G->nstate, S.DX, S.DY, S.SRC, G->sigma,
-                                                           G->Uref, G->mask, (double*)U, dUdt,
-                                                           nullptr, 0, 0.0, 0.0, 0.0);
+    const AssembleArgs aa{S.DX, S.DY, S.SRC, G->sigma, G->Uref, G->mask, (double*)U, dUdt,
+                          nullptr, 0, 0.0, 0.0, 0.0};
+    k_assemble<<<blocks_for(G->nstate, 256), 256, 0, s>>>(G->nstate, aa);
     HYP_CUDA(cudaGetLastError());
     return HYP_OK;
 }
