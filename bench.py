@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--nx", type=int, default=2048, help="cells in x (profiling of small cases)")
     ap.add_argument("--ny", type=int, default=256, help="cells in y (profiling of small cases)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
+    ap.add_argument("--serve-requests", type=int, default=48,
+                    help="requests of the serving measurement (0 skips it)")
     ap.add_argument("--thermo-states", type=float, default=1e8,
                     help="states of the pointwise thermochemistry sweep (0 skips it)")
     return ap.parse_args()
@@ -245,6 +247,60 @@ def thermo_sweep(A, gas, dev, n, seed, reps=2):
             "inputs": "T log-uniform 300-15000 K, rho log-uniform 1e-4-1 kg/m^3, Y Dirichlet(1)"}
 
 
+def serving_bench(A, I, nreq, seed, precision):
+    """Continuous batching of a stream of independent solves (serving workload): a closed-loop
+    burst measures capacity, then nreq requests arrive as a Poisson process at 0.8 x capacity.
+    Reports time-to-solution percentiles and the throughput over the serving window."""
+    import numpy as np
+
+    def work(r):
+        c, n, _ = r
+        return c["nx"] * c["ny"] * 3 * n
+
+    calib = I.serving_requests(12, seed=seed + 1, steps=(20, 80))
+    sv = A.Server(precision=precision, max_members=64)
+    t0 = time.perf_counter()
+    for c, n, _ in calib:
+        sv.submit(c, n)
+    sv.wait(timeout=900)
+    cap = sum(work(r) for r in calib) / (time.perf_counter() - t0)      # points*RHS per second
+    sv.close()
+    reqs = I.serving_requests(nreq, seed=seed, steps=(20, 80))
+    mean_work = sum(work(r) for r in reqs) / len(reqs)
+    lam = 0.8 * cap / mean_work                                            # requests per second
+    sv = A.Server(precision=precision, max_members=64)
+    ids = []
+    t_start = time.perf_counter()
+    t_next = t_start
+    for c, n, gap in reqs:
+        t_next += gap / lam
+        delay = t_next - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        ids.append(sv.submit(c, n))
+    sv.wait(timeout=1800)
+    st = [sv.stats(i) for i in ids]
+    cnt = sv.counters()
+    sv.close()
+    tts = np.array([s["t_finish"] - s["t_submit"] for s in st])
+    wait = np.array([s["t_admit"] - s["t_submit"] for s in st])
+    span = max(s["t_finish"] for s in st) - min(s["t_submit"] for s in st)
+    total = sum(work(r) for r in reqs)
+    return {"requests": nreq, "precision": "mixed" if precision else "fp64",
+            "arrivals": "Poisson at 0.8 x measured capacity",
+            "capacity_mpts_rhs_s": cap / 1e6, "rate_req_s": lam,
+            "tts_p50_s": float(np.percentile(tts, 50)), "tts_p99_s": float(np.percentile(tts, 99)),
+            "queue_wait_p50_s": float(np.percentile(wait, 50)),
+            "throughput_mpts_rhs_s": total / span / 1e6,
+            "busy_throughput_mpts_rhs_s": total / max(cnt["busy_s"], 1e-30) / 1e6,
+            "mean_batch": cnt["member_steps"] / max(cnt["batch_steps"], 1),
+            "max_batch": cnt["max_members"],
+            "errors": int(sum(1 for s in st if s["error"])),
+            "status_nonzero": int(sum(1 for s in st if s["status"])),
+            "workload": "grids 128x32 to 1024x256, boundary layers Mach 5-20 (wall 300-1500 K) and "
+                        "shock interactions, 20-80 RK3 steps each"}
+
+
 def ours_arm(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -397,6 +453,10 @@ def ours_arm(args, rank, world, local_rank):
         roof.update(bound="alu", achieved=None, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s", frac=None,
                     traffic=None, note="per-point FP64 count not yet measured for this kernel")
 
+    serving = None
+    if args.serve_requests > 0:
+        serving = serving_bench(A, I, args.serve_requests, 100 + rank, A.MIXED)
+
     sweep = None
     if args.thermo_states > 0:
         del flush
@@ -416,6 +476,7 @@ def ours_arm(args, rank, world, local_rank):
                 "data": "synthetic", "config": workload_config(cfg, world), "e2e": e2e,
                 "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
                 "wall_s_timed": t_wall, "status_flags": status, "mixed": mixed,
+                "serving": serving,
                 "thermo_sweep": sweep,
                 "kernels": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1]}}
         print(json.dumps(line), flush=True)

@@ -219,6 +219,65 @@ int hyp_batch_step(hyp_batch* b, int nsteps, void* stream);
 
 void hyp_batch_free(hyp_batch* b);
 
+/* ---- Serving: continuous batching of independent solves ----
+ * A server owns one worker thread, one stream and one batch (hyp_batch_*). Requests (a grid, a
+ * case, a freestream, a time step and a step count) are submitted from any host thread and queued
+ * in arrival order. Between batch steps the worker admits queued requests while the GPU's free
+ * memory stays above the reserve after the request's estimated footprint and the member limit
+ * is not reached (it builds the gas, the state and the registers on the device), advances the
+ * batch by as many steps as the nearest completion allows (at most 8), and retires finished
+ * members (status read, registers optionally copied to host memory, device memory freed).
+ * Requests that arrive while others run join at the next step boundary. Times are seconds since
+ * the server was created, from the host's steady clock. */
+typedef struct hyp_server hyp_server;
+
+typedef struct {
+    hyp_freestream fs;
+    hyp_grid_desc grid;
+    hyp_case cas;                  /* cas.noise, if set, is copied at submission */
+    double dt;                     /* nondimensional time step */
+    int32_t nsteps;                /* RK3 steps to run */
+    int32_t keep_result;           /* 1: keep the final state for hyp_server_result */
+} hyp_request;
+
+typedef struct {
+    double t_submit, t_admit, t_finish;   /* -1 while not reached */
+    int32_t done;                         /* 1 when finished */
+    uint32_t status;                      /* HYP_STATUS_* bits raised during the solve */
+    int32_t error;                        /* HYP_OK, or the error that ended the request */
+    int64_t points;                       /* cells of the grid */
+    int64_t bytes;                        /* device bytes reserved for it at admission */
+} hyp_request_stats;
+
+/* New server. table: gas table path (HOST string) shared by all requests; kind: hyp_gas_kind;
+ * precision: HYP_FP64 or HYP_MIXED; reserve_bytes: free device memory kept back at admission;
+ * max_members: upper bound on concurrently admitted requests (> 0). */
+int hyp_server_create(const char* table, int kind, int precision, int64_t reserve_bytes,
+                      int max_members, hyp_server** out);
+
+/* Queue a request (HOST struct, copied). *id: its identifier (0, 1, 2, ... in submission order).
+ * Returns immediately. HYP_ERR_ARG for an invalid request (checked here: sizes, dt, nsteps). */
+int hyp_server_submit(hyp_server* sv, const hyp_request* req, int64_t* id);
+
+/* Block until request id (or, with id < 0, every request submitted so far) has finished, or
+ * timeout_s seconds passed (HYP_ERR_ARG then). */
+int hyp_server_wait(hyp_server* sv, int64_t id, double timeout_s);
+
+/* Statistics of one request (HOST struct). */
+int hyp_server_stats(hyp_server* sv, int64_t id, hyp_request_stats* out);
+
+/* Final state of a finished request submitted with keep_result (HOST buffer of
+ * hyp_state_size() doubles); the server drops its copy afterwards. */
+int hyp_server_result(hyp_server* sv, int64_t id, double* U_host);
+
+/* Server-wide counters (HOST, each nullable): steps run by the batch, sum over steps of the
+ * member count, device seconds of the steps, largest member count. */
+int hyp_server_counters(hyp_server* sv, int64_t* batch_steps, int64_t* member_steps,
+                        double* busy_s, int32_t* max_members);
+
+/* Stop the worker after the requests in flight finish and queued ones are dropped, and free. */
+void hyp_server_free(hyp_server* sv);
+
 /* The binary64 -> binary32 rounding (nearest, ties to even; magnitudes below 1.18e-38 to signed
  * zero) and the exact widening back that HYP_MIXED uses between its binary64 and binary32
  * parts, done with integer instructions. x[n]: DEVICE input; y[n] (binary32) and back[n]

@@ -50,6 +50,18 @@ class CaseDesc(ctypes.Structure):
                 ("filter_sigma", ctypes.c_double)]
 
 
+class Request(ctypes.Structure):
+    _fields_ = [("fs", Freestream), ("grid", GridDesc), ("cas", CaseDesc), ("dt", ctypes.c_double),
+                ("nsteps", ctypes.c_int32), ("keep_result", ctypes.c_int32)]
+
+
+class RequestStats(ctypes.Structure):
+    _fields_ = [("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_finish", ctypes.c_double), ("done", ctypes.c_int32),
+                ("status", ctypes.c_uint32), ("error", ctypes.c_int32),
+                ("points", ctypes.c_int64), ("bytes", ctypes.c_int64)]
+
+
 _LIB = None
 _P = ctypes.c_void_p
 _D = ctypes.c_double
@@ -82,6 +94,14 @@ EXPORTS = {
     "hyp_batch_tile": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "hyp_batch_step": (_I, [_P, _I, _P]),
     "hyp_batch_free": (None, [_P]),
+    "hyp_server_create": (_I, [ctypes.c_char_p, _I, _I, _I64, _I, ctypes.POINTER(_P)]),
+    "hyp_server_submit": (_I, [_P, ctypes.POINTER(Request), ctypes.POINTER(_I64)]),
+    "hyp_server_wait": (_I, [_P, _I64, _D]),
+    "hyp_server_stats": (_I, [_P, _I64, ctypes.POINTER(RequestStats)]),
+    "hyp_server_result": (_I, [_P, _I64, _P]),
+    "hyp_server_counters": (_I, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_D),
+                                 ctypes.POINTER(ctypes.c_int32)]),
+    "hyp_server_free": (None, [_P]),
     "hyp_grid_profile": (_I, [_P, _I]),
     "hyp_grid_profile_read": (_I, [_P, _I, _P, _P]),
     "hyp_profile_count": (_I, []),
@@ -312,6 +332,63 @@ class Batch:
         if getattr(self, "handle", None) is not None and _LIB is not None:
             _LIB.hyp_batch_free(self.handle)
             self.handle = None
+
+
+def state_len(cfg, ns=5):
+    """Length of the state vector of a case (layout of include/hyp.h)."""
+    nx, ny = cfg["nx"], cfg["ny"]
+    return (ns + 1) * nx * ny + (nx + 1) * ny + nx * (ny + 1)
+
+
+class Server:
+    """hyp_server: continuous batching of independent solves on the current GPU."""
+
+    def __init__(self, precision=FP64, reserve_bytes=4 << 30, max_members=64, kind="cneq",
+                 path=TABLE_AIR5):
+        h = ctypes.c_void_p()
+        _check(lib().hyp_server_create(path.encode(), GAS_KINDS[kind], precision, int(reserve_bytes),
+                                       int(max_members), ctypes.byref(h)))
+        self.handle = h
+
+    def submit(self, cfg, nsteps, dt=None, noise=None, keep_result=False):
+        r = Request()
+        r.fs = freestream_struct(cfg)
+        r.grid = grid_struct(cfg)
+        r.cas = case_struct(cfg, noise)
+        r.dt = cfg["dt"] if dt is None else dt
+        r.nsteps = int(nsteps)
+        r.keep_result = int(bool(keep_result))
+        i = ctypes.c_int64()
+        _check(lib().hyp_server_submit(self.handle, ctypes.byref(r), ctypes.byref(i)))
+        return i.value
+
+    def wait(self, rid=-1, timeout=3600.0):
+        _check(lib().hyp_server_wait(self.handle, int(rid), float(timeout)))
+
+    def stats(self, rid):
+        st = RequestStats()
+        _check(lib().hyp_server_stats(self.handle, int(rid), ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in RequestStats._fields_}
+
+    def result(self, rid, cfg):
+        out = np.empty(state_len(cfg))
+        _check(lib().hyp_server_result(self.handle, int(rid), out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def counters(self):
+        a, b, c, d = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_int32()
+        _check(lib().hyp_server_counters(self.handle, ctypes.byref(a), ctypes.byref(b),
+                                         ctypes.byref(c), ctypes.byref(d)))
+        return {"batch_steps": a.value, "member_steps": b.value, "busy_s": c.value,
+                "max_members": d.value}
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and _LIB is not None:
+            _LIB.hyp_server_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
 
 
 def grid_reference(grid, n):

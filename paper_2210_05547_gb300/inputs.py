@@ -13,6 +13,10 @@ Workloads (shapes follow the paper's cases; there is no dataset):
   p_inf = 60967 Pa); Mach number drawn in [6, 9] and flow deflection in [8, 14] degrees from the seed;
   artificial diffusivity on; the conserved state is low-pass filtered after every RK step
   (strength 0.05 on the grid-to-grid mode).
+* ``serving_requests`` -- a stream of independent boundary-layer and shock / boundary-layer
+  solves for the serving path: grids from 128 x 32 to 1024 x 256, boundary layers at Mach 5-20
+  with wall temperature 300-1500 K, interactions at the Mach and deflection their seed draws,
+  seeded step counts and unit-rate exponential inter-arrival gaps (scaled by the caller).
 * ``thermo_states`` -- independent thermochemical states: T log-uniform in [300, 15000] K,
   rho log-uniform in [1e-4, 1] kg/m^3, mass fractions Dirichlet(1).
 """
@@ -60,6 +64,25 @@ def box_case(nx=32, ny=24, seed=0, kind="cneq"):
     c.update(name=f"box_{nx}x{ny}", wall=0, y_stretch="tanh", minor_species=0.0, noise_amp=0.0,
              sponge_in=0.0, sponge_out=0.0)
     return c
+
+
+def serving_requests(n, seed=0, steps=(500, 2000)):
+    """n requests: (case dictionary, step count, unit-rate inter-arrival gap)."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0x5e7e]))
+    nxs, nys = (128, 256, 512, 1024), (32, 64, 128, 256)
+    out = []
+    for k in range(n):
+        nx, ny = int(rng.choice(nxs)), int(rng.choice(nys))
+        if rng.random() < 0.5:
+            c = bl_case(nx, ny, seed=int(rng.integers(1 << 30)))
+            mach = float(rng.uniform(5.0, 20.0))
+            c.update(mach=mach, T_wall=float(rng.uniform(300.0, 1500.0)),
+                     dt=2.0e-4 * min(1.0, 10.0 / mach))
+        else:
+            c = sbli_case(nx, ny, seed=int(rng.integers(1 << 30)))
+        c["name"] = f"req{k}_{c['name']}"
+        out.append((c, int(rng.integers(steps[0], steps[1] + 1)), float(rng.exponential(1.0))))
+    return out
 
 
 def state_noise(n, seed):
