@@ -201,9 +201,10 @@ int hyp_batch_remove(hyp_batch* b, hyp_state* st);
 
 /* use_graph != 0: capture one step into a CUDA graph and replay it while the membership stays
  * the same. tile: points per persistent-kernel tile, a positive multiple of 128, or 0 (the
- * default) for the autotuner: after each change of membership the next steps run one untimed
- * step and then one timed step for each tile size in {256, 512, 1024, 2048}, and the fastest is
- * kept. Those are real steps of every member; the tile size does not change any result. */
+ * default) for the autotuner: after a change of membership to a size class (power of two of the
+ * total cell count) not seen before, the next steps run one untimed step and then one timed step
+ * for each tile size in {256, 512, 1024, 2048}, and the fastest is kept for that class. Those are
+ * real steps of every member; the tile size does not change any result. */
 int hyp_batch_configure(hyp_batch* b, int use_graph, int tile);
 
 /* Number of members (HOST int). */

@@ -12,6 +12,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -176,6 +177,7 @@ struct hyp_batch {
     int tile = 512;
     int tile_auto = 1;           // pick the tile size by timing real steps after each change
     int tuned = 0;               // the tile size has been chosen for the current membership
+    std::map<int, int> tile_cache;   // chosen tile per batch size class (log2 of the cell count)
     int use_graph = 0;
     GasDev table;                // gas tables shared by the members (freestream scales per member)
     bool have_table = false;
@@ -469,6 +471,21 @@ extern "C" int hyp_batch_step(hyp_batch* b, int nsteps, void* stream) {
     // Autotuner: the tile size only distributes work (every point is computed the same way), so
     // candidate tiles are timed on real steps of the solution: one untimed step after a change
     // of membership, then one timed step per candidate, then the fastest is kept.
+    long long cells = 0;
+    for (const auto& m : b->members) cells += m.st->grid->d.size(hyp::NC);
+    int size_class = 0;
+    while ((2LL << size_class) <= cells) ++size_class;
+    if (b->tile_auto && !b->tuned) {
+        auto hit = b->tile_cache.find(size_class);
+        if (hit != b->tile_cache.end()) {
+            b->tuned = 1;
+            if (b->tile != hit->second) {
+                b->tile = hit->second;
+                const int rc = rebuild(b, s);
+                if (rc) return rc;
+            }
+        }
+    }
     if (b->tile_auto && !b->tuned) {
         static const int cand[] = {256, 512, 1024, 2048};
         float best_ms = 0.0f;
@@ -495,7 +512,10 @@ extern "C" int hyp_batch_step(hyp_batch* b, int nsteps, void* stream) {
                 best = cand[c];
             }
             --nsteps;
-            if (c == 3) b->tuned = 1;
+            if (c == 3) {
+                b->tuned = 1;
+                b->tile_cache[size_class] = best;
+            }
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);

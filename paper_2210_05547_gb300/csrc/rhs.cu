@@ -27,7 +27,7 @@ namespace {
 // Host: grid maps, oblique shock, reference profile
 // ---------------------------------------------------------------------------------------------
 
-void y_map(const hyp_grid_desc& d, double eta, double& y, double& dyde) {
+__host__ __device__ void y_map(const hyp_grid_desc& d, double eta, double& y, double& dyde) {
     const double s = eta / d.ny;
     const double L = d.y1 - d.y0, q = d.y_param;
     if (d.y_stretch == 1) {
@@ -74,7 +74,6 @@ Shock oblique_shock(double M1, double theta, double gam) {
 }
 
 struct Profile {
-    const GasDev* g;
     hyp_case c;
     double y0;
     int iN2, iO2, iNO, iN, iO;
@@ -84,12 +83,12 @@ struct Profile {
     double Yinf[NSP];
 
     // Boundary-layer profile below an edge state: u/u_e = erf(2 y / delta(x)), Crocco-Busemann T.
-    void edge(double x, double y, double Te, double pe, double ue, double ve, double Me,
+    __host__ __device__ void edge(const GasDev& g, double x, double y, double Te, double pe, double ue, double ve, double Me,
               double& T, double& p, double& u, double& v, double& f) const {
         if (c.wall) {
-            const double delta = c.delta_coef * sqrt(x / (g->Re * g->mach));
+            const double delta = c.delta_coef * sqrt(x / (g.Re * g.mach));
             f = erf(2.0 * (y - y0) / delta);
-            const double Tr = Te * (1.0 + RECOVERY * 0.5 * (g->gamma_inf - 1.0) * Me * Me);
+            const double Tr = Te * (1.0 + RECOVERY * 0.5 * (g.gamma_inf - 1.0) * Me * Me);
             T = c.T_wall + (Tr - c.T_wall) * f - (Tr - Te) * f * f;
         } else {
             f = 1.0;
@@ -101,13 +100,13 @@ struct Profile {
     }
 
     // primitive reference state: T [K], p [Pa], u, v nondimensional, Y
-    void at(double x, double y, double& T, double& p, double& u, double& v, double* Y) const {
+    __host__ __device__ void at(const GasDev& g, double x, double y, double& T, double& p, double& u, double& v, double* Y) const {
         double f;
-        edge(x, y, g->T_inf, g->p_inf, g->mach, 0.0, g->mach, T, p, u, v, f);
+        edge(g, x, y, g.T_inf, g.p_inf, g.mach, 0.0, g.mach, T, p, u, v, f);
         if (shock) {
             const double V2 = sh.M2 * sqrt(sh.T21);
             double T2, p2, u2, v2, f2;
-            edge(x, y, g->T_inf * sh.T21, g->p_inf * sh.p21, V2 * cos(theta), -V2 * sin(theta),
+            edge(g, x, y, g.T_inf * sh.T21, g.p_inf * sh.p21, V2 * cos(theta), -V2 * sin(theta),
                  sh.M2, T2, p2, u2, v2, f2);
             const double ys = (c.shock_x - x) * tan(sh.beta);
             const double H = 0.5 * (1.0 + tanh((y - ys) / c.shock_width));
@@ -117,7 +116,7 @@ struct Profile {
             v = (1.0 - H) * v + H * v2;
         }
         for (int s = 0; s < NSP; ++s) Y[s] = Yinf[s];
-        const bool seed = c.wall && g->kind != HYP_GAS_CPG && iN2 >= 0 && iO2 >= 0 && iNO >= 0 &&
+        const bool seed = c.wall && g.kind != HYP_GAS_CPG && iN2 >= 0 && iO2 >= 0 && iNO >= 0 &&
                           iN >= 0 && iO >= 0;
         if (seed) {
             const double m = c.minor_species * 4.0 * f * (1.0 - f);
@@ -130,23 +129,104 @@ struct Profile {
     }
 
     // nondimensional rho, rho_s (all species), rho*E
-    void conserved(double T, double p, double u, double v, const double* Y, double& rho,
+    __host__ __device__ void conserved(const GasDev& g, double T, double p, double u, double v, const double* Y, double& rho,
                    double* rhoY, double& rhoE) const {
         double rho_si, e_nd;
-        if (g->kind == HYP_GAS_CPG) {
-            rho_si = p / (g->R_inf * T);
-            e_nd = (T / g->T_ref) / g->gamma_inf;
+        if (g.kind == HYP_GAS_CPG) {
+            rho_si = p / (g.R_inf * T);
+            e_nd = (T / g.T_ref) / g.gamma_inf;
         } else {
             double ym = 0.0;
-            for (int s = 0; s < NSP; ++s) ym += Y[s] * g->invM[s];
+            for (int s = 0; s < NSP; ++s) ym += Y[s] * g.invM[s];
             rho_si = p / (R_U * ym * T);
-            e_nd = mixture_energy(*g, T, Y) / (g->a_inf * g->a_inf);
+            e_nd = mixture_energy(g, T, Y) / (g.a_inf * g.a_inf);
         }
-        rho = rho_si / g->rho_inf;
+        rho = rho_si / g.rho_inf;
         for (int s = 0; s < NSP; ++s) rhoY[s] = rho * Y[s];
         rhoE = rho * (e_nd + 0.5 * (u * u + v * v));
     }
 };
+
+// Sponge strength of Eq. (26) at (x, y): cubic ramps over the inflow, outflow and top zones.
+__host__ __device__ inline double sponge_at(const hyp_grid_desc& d, const hyp_case& c, double x,
+                                            double y) {
+    double sg = 0.0;
+    if (c.sponge_in > 0) {
+        const double r = fmin(fmax((d.x0 + c.sponge_in - x) / c.sponge_in, 0.0), 1.0);
+        sg += r * r * r;
+    }
+    if (c.sponge_out > 0) {
+        const double r = fmin(fmax((x - (d.x1 - c.sponge_out)) / c.sponge_out, 0.0), 1.0);
+        sg += r * r * r;
+    }
+    if (c.sponge_top_cells > 0) {
+        double ytop, dy;
+        y_map(d, (double)(d.ny - c.sponge_top_cells), ytop, dy);
+        const double r = fmin(fmax((y - ytop) / (d.y1 - ytop), 0.0), 1.0);
+        sg += r * r * r;
+    }
+    return c.sponge_sigma * sg;
+}
+
+// Reference state Q_ref (Eq. 26), sponge strength and the Dirichlet mask at every state entry:
+// one thread per cell centre, x-face and y-face.
+__global__ void k_reference(GasDev g, Profile P, hyp_grid_desc d, long long off_xf, long long off_yf,
+                            double* __restrict__ Uref, double* __restrict__ sig,
+                            uint8_t* __restrict__ mask) {
+    const int nx = d.nx, ny = d.ny;
+    const long long nc = (long long)nx * ny, nxf = (long long)(nx + 1) * ny;
+    const long long n = nc + nxf + (long long)nx * (ny + 1);
+    const double dx = (d.x1 - d.x0) / nx;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        int node, i, j;
+        if (k < nc) {
+            node = 0; j = (int)(k / nx); i = (int)(k - (long long)j * nx);
+        } else if (k < nc + nxf) {
+            node = 1; const long long q = k - nc; j = (int)(q / (nx + 1)); i = (int)(q - (long long)j * (nx + 1));
+        } else {
+            node = 2; const long long q = k - nc - nxf; j = (int)(q / nx); i = (int)(q - (long long)j * nx);
+        }
+        const double x = d.x0 + dx * (node == 1 ? (double)i : i + 0.5);
+        double y, dy;
+        y_map(d, node == 2 ? (double)j : j + 0.5, y, dy);
+        double T, p, u, v, Y[NSP], rho, rY[NSP], rE;
+        P.at(g, x, y, T, p, u, v, Y);
+        P.conserved(g, T, p, u, v, Y, rho, rY, rE);
+        const double sg = sponge_at(d, P.c, x, y);
+        if (node == 0) {
+            Uref[k] = rho;
+            sig[k] = sg;
+            mask[k] = 0;
+            for (int sp = 1; sp < NSP; ++sp) {
+                Uref[sp * nc + k] = rY[sp];
+                sig[sp * nc + k] = sg;
+                mask[sp * nc + k] = 0;
+            }
+            Uref[NSP * nc + k] = rE;
+            sig[NSP * nc + k] = sg;
+            mask[NSP * nc + k] = 0;
+        } else if (node == 1) {
+            const long long e = off_xf + (k - nc);
+            Uref[e] = rho * u;
+            sig[e] = sg;
+            mask[e] = (i == 0 || i == nx) ? 1 : 0;
+        } else {
+            const long long e = off_yf + (k - nc - nxf);
+            Uref[e] = rho * v;
+            sig[e] = sg;
+            mask[e] = (j == 0 || j == ny) ? 1 : 0;
+        }
+    }
+}
+
+// Initial state: the reference with the seeded multiplicative noise on every entry not held.
+__global__ void k_initial(long long n, const double* __restrict__ Uref, const uint8_t* __restrict__ mask,
+                          const double* __restrict__ noise, double amp, double* __restrict__ U) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x)
+        U[k] = (noise && !mask[k]) ? Uref[k] * (1.0 + amp * noise[k]) : Uref[k];
+}
 
 // ---------------------------------------------------------------------------------------------
 // Host: compact operators
@@ -557,26 +637,9 @@ extern "C" int hyp_state_init(const hyp_gas* gas, const hyp_grid_desc* desc, con
         yc[j] = y;
         eta_c[j] = 1.0 / dy;
     }
-    auto sponge = [&](double x, double y) {
-        double sg = 0.0;
-        if (cas->sponge_in > 0) {
-            double r = std::min(std::max((desc->x0 + cas->sponge_in - x) / cas->sponge_in, 0.0), 1.0);
-            sg += r * r * r;
-        }
-        if (cas->sponge_out > 0) {
-            double r = std::min(std::max((x - (desc->x1 - cas->sponge_out)) / cas->sponge_out, 0.0), 1.0);
-            sg += r * r * r;
-        }
-        if (cas->sponge_top_cells > 0) {
-            const double ytop = yf[ny - cas->sponge_top_cells];
-            double r = std::min(std::max((y - ytop) / (desc->y1 - ytop), 0.0), 1.0);
-            sg += r * r * r;
-        }
-        return cas->sponge_sigma * sg;
-    };
     Profile P;
-    P.g = &g;
     P.c = *cas;
+    P.c.noise = nullptr;
     P.y0 = desc->y0;
     P.iN2 = P.iO2 = P.iNO = P.iN = P.iO = -1;
     for (int sp = 0; sp < NSP; ++sp) {
@@ -592,45 +655,6 @@ extern "C" int hyp_state_init(const hyp_gas* gas, const hyp_grid_desc* desc, con
     P.theta = cas->shock_deflection_deg * 3.14159265358979323846 / 180.0;
     if (P.shock) P.sh = oblique_shock(g.mach, P.theta, g.gamma_inf);
     for (int sp = 0; sp < NSP; ++sp) P.Yinf[sp] = g.Y_inf[sp];
-    std::vector<double> Uref(ns_), sig(ns_), U0(ns_);
-    std::vector<uint8_t> mask(ns_, 0);
-    for (int j = 0; j < ny; ++j)
-        for (int i = 0; i < nx; ++i) {
-            double T, p, u, v, Y[NSP], rho, rY[NSP], rE;
-            P.at(xc[i], yc[j], T, p, u, v, Y);
-            P.conserved(T, p, u, v, Y, rho, rY, rE);
-            const long long k = (long long)j * nx + i;
-            Uref[G->off[0] + k] = rho;
-            for (int sp = 1; sp < NSP; ++sp) Uref[G->off[sp] + k] = rY[sp];
-            Uref[G->off[NSP] + k] = rE;
-            const double sg = sponge(xc[i], yc[j]);
-            for (int f = 0; f <= NSP; ++f) sig[G->off[f] + k] = sg;
-        }
-    for (int j = 0; j < ny; ++j)
-        for (int i = 0; i <= nx; ++i) {
-            double T, p, u, v, Y[NSP], rho, rY[NSP], rE;
-            P.at(xf[i], yc[j], T, p, u, v, Y);
-            P.conserved(T, p, u, v, Y, rho, rY, rE);
-            const long long k = G->off[NSP + 1] + (long long)j * (nx + 1) + i;
-            Uref[k] = rho * u;
-            sig[k] = sponge(xf[i], yc[j]);
-            if (i == 0 || i == nx) mask[k] = 1;
-        }
-    for (int j = 0; j <= ny; ++j)
-        for (int i = 0; i < nx; ++i) {
-            double T, p, u, v, Y[NSP], rho, rY[NSP], rE;
-            P.at(xc[i], yf[j], T, p, u, v, Y);
-            P.conserved(T, p, u, v, Y, rho, rY, rE);
-            const long long k = G->off[NSP + 2] + (long long)j * nx + i;
-            Uref[k] = rho * v;
-            sig[k] = sponge(xc[i], yf[j]);
-            if (j == 0 || j == ny) mask[k] = 1;
-        }
-    for (long long k = 0; k < ns_; ++k) {
-        U0[k] = Uref[k];
-        if (cas->noise && cas->noise_amp > 0 && !mask[k]) U0[k] = Uref[k] * (1.0 + cas->noise_amp * cas->noise[k]);
-    }
-
     // ---------------- device memory ----------------
     const long long n_c_fields = 13 + 9 * NSP + 8 + 5 + 16;
     const long long n_xf_fields = 2 + 6 * NSP + 8 + 3;
@@ -870,10 +894,16 @@ extern "C" int hyp_state_init(const hyp_gas* gas, const hyp_grid_desc* desc, con
     UP(G->xi_f, xi_f.data(), (nx + 1) * sizeof(double));
     UP(G->eta_c, eta_c.data(), ny * sizeof(double));
     UP(G->eta_f, eta_f.data(), (ny + 1) * sizeof(double));
-    UP(G->Uref, Uref.data(), ns_ * sizeof(double));
-    UP(G->sigma, sig.data(), ns_ * sizeof(double));
-    UP(G->mask, mask.data(), ns_);
-    UP(U, U0.data(), ns_ * sizeof(double));
+    // reference state, sponge, mask and the initial state, computed on the device; the seeded
+    // noise travels through the state-sized scratch vector
+    k_reference<<<blocks_for(nc + nxf + nyf, 128), 128, 0, s>>>(g, P, *desc, G->off[NSP + 1],
+                                                                 G->off[NSP + 2], G->Uref, G->sigma,
+                                                                 G->mask);
+    const bool noisy = cas->noise && cas->noise_amp > 0;
+    if (noisy) UP(G->s.R, cas->noise, ns_ * sizeof(double));
+    k_initial<<<blocks_for(ns_, 256), 256, 0, s>>>(ns_, G->Uref, G->mask, noisy ? G->s.R : nullptr,
+                                                   cas->noise_amp, U);
+    HYP_CUDA(cudaGetLastError());
 #undef UP
     HYP_CUDA(cudaMemsetAsync(dQ, 0, ns_ * sizeof(double), s));
     HYP_CUDA(cudaMemsetAsync(G->s.SRC, 0, ns_ * sizeof(double), s));
