@@ -453,9 +453,10 @@ def ours_arm(args, rank, world, local_rank):
         roof.update(bound="alu", achieved=None, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s", frac=None,
                     traffic=None, note="per-point FP64 count not yet measured for this kernel")
 
-    serving = None
+    serving = serving_fp64 = None
     if args.serve_requests > 0:
         serving = serving_bench(A, I, args.serve_requests, 100 + rank, A.MIXED)
+        serving_fp64 = serving_bench(A, I, args.serve_requests, 100 + rank, A.FP64)
 
     sweep = None
     if args.thermo_states > 0:
@@ -476,7 +477,7 @@ def ours_arm(args, rank, world, local_rank):
                 "data": "synthetic", "config": workload_config(cfg, world), "e2e": e2e,
                 "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
                 "wall_s_timed": t_wall, "status_flags": status, "mixed": mixed,
-                "serving": serving,
+                "serving": serving, "serving_fp64": serving_fp64,
                 "thermo_sweep": sweep,
                 "kernels": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1]}}
         print(json.dumps(line), flush=True)
