@@ -27,7 +27,8 @@ from scipy.special import erf
 from . import compact as C
 from . import gas as G
 
-KIND_CNEQ, KIND_FROZEN, KIND_CPG = "cneq", "frozen", "cpg"
+KIND_CNEQ, KIND_FROZEN, KIND_CPG, KIND_TPG = "cneq", "frozen", "cpg", "tpg"
+PERFECT_KINDS = (KIND_CPG, KIND_TPG)      # composition irrelevant, no reactions or diffusion
 
 SUTHERLAND_C1 = 1.458e-6      # kg m^-1 s^-1 K^-1/2 (Eq. 24)
 SUTHERLAND_TS = 110.4         # K (Eq. 24)
@@ -40,9 +41,60 @@ RK_A = (0.0, -5.0 / 9.0, -153.0 / 128.0)
 RK_B = (1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0)
 
 
+KEYES_C2 = 2.646e-3           # W m^-1 K^-3/2 (Eq. 25)
+KEYES_C3 = 245.4              # K (Eq. 25)
+KEYES_C4 = 12.0               # K (Eq. 25)
+TPG_THETA = 3055.0            # K (Eq. 23)
+
+
 def sutherland(T):
     """Eq. (24)."""
     return SUTHERLAND_C1 * T ** 1.5 / (T + SUTHERLAND_TS)
+
+
+def keyes(T):
+    """Thermal conductivity of the thermally perfect gas, Eq. (25)."""
+    return KEYES_C2 * np.sqrt(T) / (1.0 + (KEYES_C3 / T) * 10.0 ** (-KEYES_C4 / T))
+
+
+# Thermally perfect gas (Eq. 23), read as the harmonic-oscillator heat capacity
+#     c_p(T) = c_p0 (1 + (gamma - 1)/gamma (Theta/T)^2 e^(Theta/T) / (e^(Theta/T) - 1)^2),
+# with c_p0 fixed by c_p(T_inf) = c_p,inf. Its integral from 0 is the enthalpy
+#     h(T) = c_p0 (T + (gamma - 1)/gamma Theta / (e^(Theta/T) - 1)),
+# and the internal energy is e = h - R T with the freestream gas constant R.
+def _tpg_shape(x):
+    """x^2 e^x / (e^x - 1)^2, written as x^2 e^-x / (1 - e^-x)^2 (no overflow at large x)."""
+    x = np.asarray(x, dtype=np.float64)
+    d = -np.expm1(-x)
+    return x * x * np.exp(-x) / (d * d)
+
+
+def tpg_cp0(sc):
+    return sc.cp / (1.0 + (sc.gamma - 1.0) / sc.gamma * float(_tpg_shape(TPG_THETA / sc.T)))
+
+
+def tpg_cp(sc, T):
+    """c_p(T) of Eq. (23), J/(kg K)."""
+    return tpg_cp0(sc) * (1.0 + (sc.gamma - 1.0) / sc.gamma * _tpg_shape(TPG_THETA / T))
+
+
+def tpg_energy(sc, T):
+    """Internal energy e(T) = h(T) - R T of the thermally perfect gas, J/kg."""
+    x = TPG_THETA / np.asarray(T, dtype=np.float64)
+    h = tpg_cp0(sc) * (T + (sc.gamma - 1.0) / sc.gamma * TPG_THETA * np.exp(-x) / -np.expm1(-x))
+    return h - sc.R * T
+
+
+def tpg_temperature(sc, e, T0=None, rtol=1e-14, maxit=60):
+    """Newton inversion of e(T) for the thermally perfect gas (de/dT = c_p - R > 0)."""
+    e = np.asarray(e, dtype=np.float64)
+    T = np.full(e.shape, sc.T) if T0 is None else np.array(T0, dtype=np.float64)
+    for _ in range(maxit):
+        dT = (tpg_energy(sc, T) - e) / (tpg_cp(sc, T) - sc.R)
+        T = T - dT
+        if np.all(np.abs(dT) <= rtol * T):
+            break
+    return T
 
 
 @dataclasses.dataclass
@@ -76,6 +128,9 @@ def freestream_scales(tab, kind, cfg) -> Scales:
     if kind == KIND_CPG:
         mu = float(sutherland(cfg["T_inf"]))
         k = mu * cp / cfg["prandtl_cpg"]
+    elif kind == KIND_TPG:
+        mu = float(sutherland(cfg["T_inf"]))
+        k = float(keyes(cfg["T_inf"]))
     else:
         X = G.mole_fractions(tab, Y)
         mu_s = G.species_viscosity(tab, T)
@@ -218,7 +273,7 @@ def _primitive_profile(case_cfg, sc, tab, kind, x, y):
         v = (1.0 - H) * v + H * v2
     Yinf = np.array(cfg["Y_inf"], dtype=np.float64)
     Y = np.zeros((tab.ns,) + shape)
-    m = cfg["minor_species"] * 4.0 * f * (1.0 - f) if (cfg["wall"] and kind != KIND_CPG) else 0.0 * f
+    m = cfg["minor_species"] * 4.0 * f * (1.0 - f) if (cfg["wall"] and kind not in PERFECT_KINDS) else 0.0 * f
     names = [s.name for s in tab.species]
     Y[:] = Yinf.reshape((-1,) + (1,) * len(shape))
     Y[names.index("N2")] = Yinf[names.index("N2")] * (1.0 - m)
@@ -236,6 +291,9 @@ def _conserved_from_primitive(tab, kind, sc, T, p, u, v, Y):
     if kind == KIND_CPG:
         rho_si = p.ravel() / (sc.R * flatT)
         e_nd = (flatT / sc.T_ref) / sc.gamma
+    elif kind == KIND_TPG:
+        rho_si = p.ravel() / (sc.R * flatT)
+        e_nd = tpg_energy(sc, flatT) / sc.a ** 2
     else:
         rho_si = p.ravel() / (G.mixture_gas_constant(tab, flatY) * flatT)
         e_nd = G.mixture_energy(tab, flatT, flatY) / sc.a ** 2
@@ -350,6 +408,16 @@ def closure_nd(case: Case, rho, e, Y):
         out = dict(T=T, p=p, h_s=np.zeros_like(Y1), wdot=np.zeros_like(Y1), mu=mu, k=mu,
                    D=np.zeros_like(Y1), X=np.zeros_like(Y1), W=np.zeros_like(Y1),
                    a=np.sqrt(sc.gamma * p / r1))
+    elif kind == KIND_TPG:
+        T_si = tpg_temperature(sc, e1 * sc.a ** 2)
+        T = T_si / sc.T_ref
+        p = r1 * (sc.gamma - 1.0) / sc.gamma * T                  # Eq. (22)
+        cp = tpg_cp(sc, T_si)
+        gam = cp / (cp - sc.R)
+        out = dict(T=T, p=p, h_s=np.zeros_like(Y1), wdot=np.zeros_like(Y1),
+                   mu=sutherland(T_si) / sc.mu, k=keyes(T_si) / sc.k,
+                   D=np.zeros_like(Y1), X=np.zeros_like(Y1), W=np.zeros_like(Y1),
+                   a=np.sqrt(gam * p / r1))
     else:
         th = G.thermo_eval(tab, r1 * sc.rho, e1 * sc.a ** 2, Y1, reactions=(kind == KIND_CNEQ))
         M = tab.M()[:, None]
