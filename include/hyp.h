@@ -44,7 +44,9 @@ extern "C" {
 enum hyp_gas_kind {
     HYP_GAS_CNEQ = 0,    /* finite-rate chemistry with algebraic diffusion (Sec. 2.2.1) */
     HYP_GAS_FROZEN = 1,  /* frozen composition: no reactions, no diffusion (Sec. 2.2.1) */
-    HYP_GAS_CPG = 2      /* calorically perfect gas, Sutherland viscosity (Eqs. 22, 24) */
+    HYP_GAS_CPG = 2,     /* calorically perfect gas, Sutherland viscosity (Eqs. 22, 24) */
+    HYP_GAS_TPG = 3      /* thermally perfect gas: c_p(T) of Eq. 23, Sutherland viscosity,
+                            Keyes conductivity (Eqs. 22-25) */
 };
 
 /* HYP_FP64: every step in binary64. HYP_MIXED: in binary32 the transport and diffusion

@@ -715,15 +715,46 @@ def filter_state(case: Case, U, sigma=None):
     return pack(case.tab.ns, g.nx, g.ny, out)
 
 
+# Time integrators of Sec. 3.1 besides the two-register RK3: the TVD RK3 of Shu and Osher and
+# the five-stage fourth-order 2N-storage scheme of Carpenter and Kennedy (the paper cites both
+# families; its text gives no coefficients, so the published ones are used).
+#   TVD RK3: U1 = U0 + dt R(U0); U2 = 3/4 U0 + 1/4 (U1 + dt R(U1));
+#            U^{n+1} = 1/3 U0 + 2/3 (U2 + dt R(U2)); the second register keeps U0.
+#   2N schemes (RK3 above, CK RK4): dQ <- A_k dQ + dt R(U); U <- U + B_k dQ.
+TVD3_W = (0.0, 3.0 / 4.0, 1.0 / 3.0)     # weight of the step's start state
+TVD3_S = (1.0, 1.0 / 4.0, 2.0 / 3.0)     # weight of the Euler update of the current stage
+CK4_A = (0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+         -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0)
+CK4_B = (1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+         1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+         2277821191437.0 / 14882151754819.0)
+RK_SCHEMES = ("rk3", "tvd3", "ck4")
+RK_STAGES = {"rk3": 3, "tvd3": 3, "ck4": 5}
+
+
+def rk_stage_scheme(case: Case, U, W, stage, dt, scheme):
+    """One stage of `scheme`: returns (U_new, W_new, R). W is the second register (dQ of the 2N
+    schemes, the step's start state of TVD RK3). After the last stage the state is filtered when
+    the case sets filter_sigma > 0."""
+    R = rhs(case, U)
+    if scheme == "tvd3":
+        if stage == 0:
+            W = U
+        U = TVD3_W[stage] * W + TVD3_S[stage] * (U + dt * R)
+    else:
+        A, B = (RK_A, RK_B) if scheme == "rk3" else (CK4_A, CK4_B)
+        W = A[stage] * W + dt * R
+        U = U + B[stage] * W
+    if (stage == RK_STAGES[scheme] - 1 and case is not None
+            and case.cfg.get("filter_sigma", 0.0) > 0.0):
+        U = filter_state(case, U)
+    return U, W, R
+
+
 def rk_stage(case: Case, U, dQ, stage, dt):
     """One stage of the two-register RK3: returns (U_new, dQ_new, R). After the last stage the
     state is filtered when the case sets filter_sigma > 0."""
-    R = rhs(case, U)
-    dQ = RK_A[stage] * dQ + dt * R
-    U = U + RK_B[stage] * dQ
-    if stage == 2 and case is not None and case.cfg.get("filter_sigma", 0.0) > 0.0:
-        U = filter_state(case, U)
-    return U, dQ, R
+    return rk_stage_scheme(case, U, dQ, stage, dt, "rk3")
 
 
 def wall_fluxes(case: Case, U):

@@ -15,7 +15,7 @@ import numpy as np
 from . import build as _build
 
 MAX_SPECIES = 5
-GAS_KINDS = {"cneq": 0, "frozen": 1, "cpg": 2}
+GAS_KINDS = {"cneq": 0, "frozen": 1, "cpg": 2, "tpg": 3}
 STRETCH = {"uniform": 0, "tanh": 1, "cubic": 2}
 FLOWS = {"bl": 0, "sbli": 1}
 FP64 = 0

@@ -120,7 +120,7 @@ using namespace hyp::table;
 extern "C" int hyp_gas_model_load(const char* path, int kind, const hyp_freestream* fs,
                                   hyp_gas** out) {
     if (!path || !fs || !out) return fail(HYP_ERR_ARG, "null argument");
-    if (kind < HYP_GAS_CNEQ || kind > HYP_GAS_CPG) return fail(HYP_ERR_ARG, "unknown gas kind");
+    if (kind < HYP_GAS_CNEQ || kind > HYP_GAS_TPG) return fail(HYP_ERR_ARG, "unknown gas kind");
     std::vector<SpeciesRow> sp;
     std::vector<ReactionRow> rx;
     int rc = parse_table(path, sp, rx);
@@ -312,9 +312,14 @@ extern "C" int hyp_gas_model_load(const char* path, int kind, const hyp_freestre
     d.a_inf = sqrt(d.gamma_inf * R * fs->T_inf);
     d.prandtl_cpg = fs->prandtl_cpg;
     d.mach = fs->mach;
+    d.tpg_theta = TPG_THETA;
+    d.tpg_cp0 = d.cp_inf / (1.0 + (d.gamma_inf - 1.0) / d.gamma_inf * tpg_shape(TPG_THETA / fs->T_inf));
     if (kind == HYP_GAS_CPG) {
         d.mu_inf = SUTH_C1 * pow(fs->T_inf, 1.5) / (fs->T_inf + SUTH_TS);
         d.k_inf = d.mu_inf * d.cp_inf / fs->prandtl_cpg;
+    } else if (kind == HYP_GAS_TPG) {
+        d.mu_inf = SUTH_C1 * pow(fs->T_inf, 1.5) / (fs->T_inf + SUTH_TS);
+        d.k_inf = keyes(fs->T_inf);
     } else {
         ClosureOut o;
         const double e = mixture_energy(d, fs->T_inf, Y);

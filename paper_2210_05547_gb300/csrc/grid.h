@@ -89,6 +89,7 @@ struct EventProfile {
 struct Scales {
     int kind;
     double rho_inf, a_inf, T_ref, mu_inf, k_inf, L_ref, Re, Pr, gamma_inf;
+    double R_inf, tpg_cp0, tpg_theta;   // thermally perfect gas (HYP_GAS_TPG)
 };
 
 inline Scales scales_of(const GasDev& g) {
@@ -103,6 +104,9 @@ inline Scales scales_of(const GasDev& g) {
     sc.Re = g.Re;
     sc.Pr = g.Pr;
     sc.gamma_inf = g.gamma_inf;
+    sc.R_inf = g.R_inf;
+    sc.tpg_cp0 = g.tpg_cp0;
+    sc.tpg_theta = g.tpg_theta;
     return sc;
 }
 

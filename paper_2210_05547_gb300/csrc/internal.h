@@ -71,6 +71,7 @@ struct GasDev {
     double prandtl_cpg;
     double mach;
     double Y_inf[NSP];
+    double tpg_cp0, tpg_theta;   // thermally perfect gas (Eq. 23): c_p0 (J/(kg K)) and Theta (K)
 };
 
 }  // namespace hyp

@@ -20,6 +20,7 @@ __device__ __forceinline__ void closure_body(const GasDev& g, const Scales& sc, 
                                              const double* __restrict__ U, const Scratch& s,
                                              long long lo, long long hi, long long stride) {
     const bool cpg = sc.kind == HYP_GAS_CPG;
+    const bool tpg = sc.kind == HYP_GAS_TPG;
     const bool cneq = sc.kind == HYP_GAS_CNEQ;
     for (long long li = lo + threadIdx.x; li < hi; li += stride) {
         const int idx = (int)li;
@@ -47,6 +48,22 @@ __device__ __forceinline__ void closure_body(const GasDev& g, const Scales& sc, 
             mu = SUTH_C1 * Td * sqrt(Td) / (Td + SUTH_TS) / sc.mu_inf;
             k = mu;
             a = sqrt(sc.gamma_inf * p / rho);
+#pragma unroll
+            for (int sp = 0; sp < NSP; ++sp) h[sp] = wd[sp] = X[sp] = W[sp] = Wd[sp] = 0.0;
+        } else if (tpg) {
+            // thermally perfect gas (Eqs. 22-25): Newton on e(T) from the cached temperature
+            const TpgModel m{sc.tpg_cp0, (sc.gamma_inf - 1.0) / sc.gamma_inf, sc.tpg_theta, sc.R_inf};
+            unsigned st = rho > 0.0 ? 0u : HYP_STATUS_NONPHYSICAL;
+            const double T0 = v.predict ? s.Tcache[idx] : sc.gamma_inf * e * sc.T_ref;
+            const double Tk = m.temperature(e * sc.a_inf * sc.a_inf, T0, st);
+            atomic_status(v.status, st);
+            s.Tcache[idx] = Tk;
+            T = Tk / sc.T_ref;
+            p = rho * (sc.gamma_inf - 1.0) / sc.gamma_inf * T;
+            mu = SUTH_C1 * Tk * sqrt(Tk) / (Tk + SUTH_TS) / sc.mu_inf;
+            k = keyes(Tk) / sc.k_inf;
+            const double cp = m.cp(Tk);
+            a = sqrt(cp / (cp - sc.R_inf) * p / rho);
 #pragma unroll
             for (int sp = 0; sp < NSP; ++sp) h[sp] = wd[sp] = X[sp] = W[sp] = Wd[sp] = 0.0;
         } else {

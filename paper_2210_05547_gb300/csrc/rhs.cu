@@ -116,7 +116,7 @@ struct Profile {
             v = (1.0 - H) * v + H * v2;
         }
         for (int s = 0; s < NSP; ++s) Y[s] = Yinf[s];
-        const bool seed = c.wall && g.kind != HYP_GAS_CPG && iN2 >= 0 && iO2 >= 0 && iNO >= 0 &&
+        const bool seed = c.wall && g.kind != HYP_GAS_CPG && g.kind != HYP_GAS_TPG && iN2 >= 0 && iO2 >= 0 && iNO >= 0 &&
                           iN >= 0 && iO >= 0;
         if (seed) {
             const double m = c.minor_species * 4.0 * f * (1.0 - f);
@@ -132,7 +132,11 @@ struct Profile {
     __host__ __device__ void conserved(const GasDev& g, double T, double p, double u, double v, const double* Y, double& rho,
                    double* rhoY, double& rhoE) const {
         double rho_si, e_nd;
-        if (g.kind == HYP_GAS_CPG) {
+        if (g.kind == HYP_GAS_TPG) {
+            const TpgModel m{g.tpg_cp0, (g.gamma_inf - 1.0) / g.gamma_inf, g.tpg_theta, g.R_inf};
+            rho_si = p / (g.R_inf * T);
+            e_nd = m.energy(T) / (g.a_inf * g.a_inf);
+        } else if (g.kind == HYP_GAS_CPG) {
             rho_si = p / (g.R_inf * T);
             e_nd = (T / g.T_ref) / g.gamma_inf;
         } else {

@@ -397,4 +397,46 @@ __host__ __device__ inline void closure_si(const GasDev& g, double rho, double e
     closure_si_p<false>(g, rho, e, Y, T0, reactions, diffusion, o);
 }
 
+// ---- thermally perfect gas (HYP_GAS_TPG; Eqs. 22-25) ----
+// c_p(T) = c_p0 (1 + g1 s(Theta/T)) with g1 = (gamma_inf - 1)/gamma_inf and the harmonic-oscillator
+// shape s(x) = x^2 e^x / (e^x - 1)^2 (the reading of Eq. 23); its integral from 0 gives
+// h(T) = c_p0 (T + g1 Theta / (e^(Theta/T) - 1)); e = h - R T with the freestream gas constant.
+constexpr double TPG_THETA = 3055.0;   // K (Eq. 23)
+constexpr double KEYES_C2 = 2.646e-3, KEYES_C3 = 245.4, KEYES_C4 = 12.0;   // Eq. (25), SI
+
+__host__ __device__ inline double tpg_shape(double x) {
+    const double d = -expm1(-x);
+    return x * x * exp(-x) / (d * d);
+}
+
+__host__ __device__ inline double keyes(double T) {
+    return KEYES_C2 * sqrt(T) / (1.0 + (KEYES_C3 / T) * exp(-KEYES_C4 * 2.302585092994045684 / T));
+}
+
+struct TpgModel {
+    double cp0, g1, theta, R;
+    __host__ __device__ double cp(double T) const { return cp0 * (1.0 + g1 * tpg_shape(theta / T)); }
+    __host__ __device__ double energy(double T) const {
+        const double x = theta / T;
+        return cp0 * (T + g1 * theta * exp(-x) / -expm1(-x)) - R * T;
+    }
+    // Newton on e(T) = e (de/dT = c_p - R > 0), from T0; T in K.
+    __host__ __device__ double temperature(double e, double T0, unsigned& status) const {
+        double T = fmin(fmax(T0, T_LO), T_HI);
+        for (int it = 0; it < NEWTON_MAXIT; ++it) {
+            const double dT = (energy(T) - e) / (cp(T) - R);
+            T -= dT;
+            if (!(T > T_LO)) {
+                T = T_LO;
+                status |= HYP_STATUS_T_CLAMPED;
+                return T;
+            }
+            if (fabs(dT) <= 1e-14 * T) return T;
+        }
+        status |= HYP_STATUS_NOT_CONVERGED;
+        return T;
+    }
+};
+
 }  // namespace hyp
+

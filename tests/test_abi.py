@@ -33,7 +33,8 @@ def test_exports_every_declared_symbol(A):
 
 
 @pytest.mark.parametrize("maker,kind", [(I.bl_case, "cneq"), (I.sbli_case, "cneq"),
-                                        (I.bl_case, "frozen"), (I.bl_case, "cpg")])
+                                        (I.bl_case, "frozen"), (I.bl_case, "cpg"),
+                                        (I.sbli_case, "tpg")])
 def test_freestream_scales_match_oracle(A, table, maker, kind):
     cfg = maker(kind=kind)
     g = A.gas_model_load(cfg)

@@ -32,6 +32,8 @@ def _cases():
         "sbli_100x37": I.sbli_case(100, 37, seed=1),
         "sbli_cpg_96x40": sbli_cpg,
         "sbli_frozen_64x33": I.sbli_case(64, 33, seed=2, kind="frozen"),
+        "bl_tpg_48x32": I.bl_case(48, 32, seed=4, kind="tpg"),
+        "sbli_tpg_96x40": I.sbli_case(96, 40, seed=5, kind="tpg"),
     }
 
 

@@ -297,3 +297,40 @@ def test_pde_consistency_binary_diffusion(table):
         order = math.log2(errs[1][name] / errs[2][name])
         assert errs[2][name] < 5e-3, (name, errs)
         assert order > 2.8, (name, [x[name] for x in errs])
+
+
+# ------------------------------------------------------------------------------------------
+# Time integrators: TVD RK3 and the 2N-storage RK4
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("scheme,taylor", [("tvd3", 3), ("ck4", 4), ("rk3", 3)])
+def test_scheme_amplification_matches_exponential(monkeypatch, scheme, taylor):
+    """On y' = z y one step multiplies y by a polynomial that agrees with e^z through z^order."""
+    zs = np.array([0.1, -0.2, 0.15j, -0.1 + 0.05j])
+    monkeypatch.setattr(F, "rhs", lambda case, U: zs * U)
+    U = np.ones(4, dtype=complex)
+    W = np.zeros_like(U)
+    for k in range(F.RK_STAGES[scheme]):
+        U, W, _ = F.rk_stage_scheme(None, U, W, k, 1.0, scheme)
+    taylor_sum = sum(zs ** n / math.factorial(n) for n in range(taylor + 1))
+    # remainder of order z^(taylor+1): small for |z| <= 0.22, and far from it for a wrong scheme
+    assert np.all(np.abs(U - taylor_sum) < 2.0 * np.abs(zs) ** (taylor + 1) / math.factorial(taylor + 1))
+    assert np.all(np.abs(U - np.exp(zs)) < np.abs(zs) ** (taylor + 1))
+
+
+@pytest.mark.parametrize("scheme,order", [("tvd3", 3), ("ck4", 4), ("rk3", 3)])
+def test_scheme_order_on_nonlinear_ode(monkeypatch, scheme, order):
+    """Logistic equation y' = y (1 - y): observed convergence order with the exact solution
+    (a nonlinear problem checks order conditions the linear test cannot)."""
+    monkeypatch.setattr(F, "rhs", lambda case, U: U * (1.0 - U))
+    y0, t_end = 0.1, 2.0
+    exact = 1.0 / (1.0 + (1.0 / y0 - 1.0) * math.exp(-t_end))
+    errs = []
+    for n in (10, 20, 40):
+        U, W = np.array([y0]), np.zeros(1)
+        for _ in range(n):
+            for k in range(F.RK_STAGES[scheme]):
+                U, W, _ = F.rk_stage_scheme(None, U, W, k, t_end / n, scheme)
+        errs.append(abs(U[0] - exact))
+    observed = math.log2(errs[1] / errs[2])
+    assert abs(observed - order) < 0.3, (errs, observed)
