@@ -173,6 +173,18 @@ int hyp_rhs(const hyp_gas* gas, const hyp_grid* grid, const double* U, double* d
  * d < 5 from an end of the line (end points unchanged); x lines first, then y lines. */
 int hyp_rk_stage(hyp_state* st, int stage, double dt, int precision, void* stream);
 
+/* Time integrators of Sec. 3.1. HYP_RK3_2N: the scheme of hyp_rk_stage. HYP_RK3_TVD: the TVD RK3
+ * of Shu and Osher, U1 = U0 + dt R(U0), U2 = 3/4 U0 + 1/4 (U1 + dt R(U1)),
+ * U^{n+1} = 1/3 U0 + 2/3 (U2 + dt R(U2)), with the step's start state U0 kept in the second
+ * register (dQ). HYP_RK4_2N: the five-stage fourth-order 2N-storage scheme of Carpenter and
+ * Kennedy (dQ <- A_k dQ + dt R; U <- U + B_k dQ with their published coefficients). */
+enum hyp_rk_scheme { HYP_RK3_2N = 0, HYP_RK3_TVD = 1, HYP_RK4_2N = 2 };
+
+/* One stage (0..2, or 0..4 for HYP_RK4_2N) of `scheme` on the state's two registers; the case's
+ * state filter runs after the scheme's last stage. Otherwise as hyp_rk_stage. */
+int hyp_rk_stage_scheme(hyp_state* st, int scheme, int stage, double dt, int precision,
+                        void* stream);
+
 /* Wall heat flux and wall shear stress of state U (nondimensional, Eq. 7): evaluates the
  * right-hand side on U with the grid's scratch (the result is discarded) and writes
  * q_w[i] = -K dT/dy at the nx wall faces (Eq. 10, K including the artificial conductivity) and

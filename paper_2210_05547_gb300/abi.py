@@ -81,6 +81,7 @@ EXPORTS = {
     "hyp_state_free": (None, [_P]),
     "hyp_rhs": (_I, [_P, _P, _P, _P, _I, _P]),
     "hyp_rk_stage": (_I, [_P, _I, _D, _I, _P]),
+    "hyp_rk_stage_scheme": (_I, [_P, _I, _I, _D, _I, _P]),
     "hyp_thermo_eval": (_I, [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I, _P]),
     "hyp_thermo_energy": (_I, [_P, _I64, _P, _P, _P, _P]),
     "hyp_rhs_noalloc": (_I, [_P, _P, _P, _P, _P]),
@@ -272,6 +273,16 @@ def rhs_noalloc(gas, grid, U, dUdt, stream=None):
 def rk_stage(state, stage, dt, precision=FP64, stream=None):
     """hyp_rk_stage: one stage of the two-register RK3 on the state's registers."""
     _check(lib().hyp_rk_stage(state.handle, stage, dt, precision, _stream(stream)))
+
+
+RK_SCHEMES = {"rk3": 0, "tvd3": 1, "ck4": 2}
+RK_STAGES = {"rk3": 3, "tvd3": 3, "ck4": 5}
+
+
+def rk_stage_scheme(state, scheme, stage, dt, precision=FP64, stream=None):
+    """hyp_rk_stage_scheme: one stage of "rk3", "tvd3" or "ck4" on the state's registers."""
+    _check(lib().hyp_rk_stage_scheme(state.handle, RK_SCHEMES[scheme], stage, dt, precision,
+                                     _stream(stream)))
 
 
 def wall_fluxes(gas, grid, U, q_w, tau_w, precision=FP64, stream=None):

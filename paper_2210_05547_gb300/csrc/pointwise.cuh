@@ -329,6 +329,8 @@ __device__ __forceinline__ void flux_body(const GridView& v, const double* __res
 }
 
 // (J) sum of divergences, sources and sponge; Dirichlet rows; optional RK stage update
+// rk: 0 right-hand side only, 1 2N-storage stage (dQ <- A dQ + dt R, U <- U + B dQ),
+// 2 TVD stage, 3 first TVD stage (also stores the start state)
 struct AssembleArgs {
     const double *DX, *DY, *SRC, *sigma, *Uref;
     const uint8_t* mask;
@@ -344,7 +346,13 @@ __device__ __forceinline__ void assemble_body(const AssembleArgs& a, long long l
         const double u = a.U[i];
         double r = a.DX[i] + a.DY[i] + a.SRC[i] - a.sigma[i] * (u - a.Uref[i]);
         if (a.mask[i]) r = 0.0;
-        if (a.rk) {
+        if (a.rk >= 2) {
+            // TVD RK3 stage: U <- A W + B (U + dt R) with W the step's start state, which the
+            // first stage (rk == 3) stores in the second register
+            const double w = a.rk == 3 ? u : a.dQ[i];
+            if (a.rk == 3) a.dQ[i] = u;
+            a.U[i] = a.A * w + a.B * (u + a.dt * r);
+        } else if (a.rk) {
             const double q = a.A * a.dQ[i] + a.dt * r;
             a.dQ[i] = q;
             a.U[i] = u + a.B * q;

@@ -1091,18 +1091,48 @@ static int launch_filter(hyp_grid* G, double* U, cudaStream_t s) {
     return HYP_OK;
 }
 
-extern "C" int hyp_rk_stage(hyp_state* st, int stage, double dt, int precision, void* stream) {
+// Coefficients of the other schemes of Sec. 3.1: TVD RK3 (Shu-Osher) weights of the start state
+// and of the Euler update, and the (5,4) 2N-storage RK4 of Carpenter and Kennedy.
+constexpr double TVD3_W[3] = {0.0, 3.0 / 4.0, 1.0 / 3.0};
+constexpr double TVD3_S[3] = {1.0, 1.0 / 4.0, 2.0 / 3.0};
+constexpr double CK4_A[5] = {0.0, -567301805773.0 / 1357537059087.0,
+                             -2404267990393.0 / 2016746695238.0,
+                             -3550918686646.0 / 2091501179385.0,
+                             -1275806237668.0 / 842570457699.0};
+constexpr double CK4_B[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                             1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                             2277821191437.0 / 14882151754819.0};
+
+extern "C" int hyp_rk_stage_scheme(hyp_state* st, int scheme, int stage, double dt, int precision,
+                                   void* stream) {
     if (!st) return fail(HYP_ERR_ARG, "null state");
-    if (stage < 0 || stage > 2) return fail(HYP_ERR_ARG, "stage must be 0, 1 or 2");
+    if (scheme < HYP_RK3_2N || scheme > HYP_RK4_2N) return fail(HYP_ERR_ARG, "unknown scheme");
+    const int nst = scheme == HYP_RK4_2N ? 5 : 3;
+    if (stage < 0 || stage >= nst) return fail(HYP_ERR_ARG, "stage out of range for the scheme");
     if (precision != HYP_FP64 && precision != HYP_MIXED) return fail(HYP_ERR_ARG, "unknown precision");
     hyp_grid* G = st->grid;
     // the gas handle is not stored in the state: the grid keeps a copy of the device tables
     hyp_gas tmp;
     tmp.dev = G->gas;
-    const int rc = run_rhs(&tmp, G, st->U, nullptr, 1, RK_A[stage], RK_B[stage], dt, st->U, st->dQ,
-                           precision, (cudaStream_t)stream);
-    if (rc || stage != 2 || !(G->cas.filter_sigma > 0.0)) return rc;
+    int mode = 1;
+    double A = RK_A[stage < 3 ? stage : 0], B = RK_B[stage < 3 ? stage : 0];
+    if (scheme == HYP_RK3_TVD) {
+        mode = stage == 0 ? 3 : 2;
+        A = TVD3_W[stage];
+        B = TVD3_S[stage];
+    } else if (scheme == HYP_RK4_2N) {
+        A = CK4_A[stage];
+        B = CK4_B[stage];
+    }
+    const int rc = run_rhs(&tmp, G, st->U, nullptr, mode, A, B, dt, st->U, st->dQ, precision,
+                           (cudaStream_t)stream);
+    if (rc || stage != nst - 1 || !(G->cas.filter_sigma > 0.0)) return rc;
     return launch_filter(G, st->U, (cudaStream_t)stream);
+}
+
+extern "C" int hyp_rk_stage(hyp_state* st, int stage, double dt, int precision, void* stream) {
+    if (st && (stage < 0 || stage > 2)) return fail(HYP_ERR_ARG, "stage must be 0, 1 or 2");
+    return hyp_rk_stage_scheme(st, HYP_RK3_2N, stage, dt, precision, stream);
 }
 
 // Wall heat flux q_w = -K dT/dy and wall shear stress tau_w = tau_xy on the wall row of the

@@ -158,6 +158,38 @@ def test_rk3_steps_with_filter_sbli(table):
         assert err <= 1e-13 * np.abs(fo[name]).max() + carried[name], (name, err, carried[name])
 
 
+@pytest.mark.parametrize("scheme", ["tvd3", "ck4"])
+@pytest.mark.parametrize("cfg", [I.bl_case(64, 40, seed=6), I.sbli_case(96, 40, seed=7)],
+                         ids=["bl_64x40", "sbli_96x40"])
+def test_other_schemes_parity(table, scheme, cfg):
+    """TVD RK3 and the 2N-storage RK4 (Sec. 3.1) through hyp_rk_stage_scheme: 2 steps, GPU state
+    against the oracle's within 1e-13 plus the right-hand-side tolerance carried through the
+    stages (per stage the registers combine with weights of at most 1.6 in magnitude)."""
+    import torch
+    from paper_2210_05547_gb300 import abi as A
+    gas, st = gpu_state(cfg)
+    case = oracle_case(table, cfg)
+    U = st.U.cpu().numpy()
+    W = np.zeros_like(U)
+    carried = {name: 0.0 for name, _ in F.state_layout(5, cfg["nx"], cfg["ny"])}
+    for step in range(2):
+        for k in range(F.RK_STAGES[scheme]):
+            tol, _ = F.parity_tolerance(case, U)
+            for name in carried:
+                carried[name] = 2.6 * carried[name] + cfg["dt"] * tol[name]
+            U, W, _ = F.rk_stage_scheme(case, U, W, k, cfg["dt"], scheme)
+            A.rk_stage_scheme(st, scheme, k, cfg["dt"])
+    torch.cuda.synchronize()
+    fg = F.unpack(5, cfg["nx"], cfg["ny"], st.U.cpu().numpy())
+    fo = F.unpack(5, cfg["nx"], cfg["ny"], U)
+    for name in fo:
+        err = np.abs(fg[name] - fo[name]).max()
+        assert err <= 1e-13 * np.abs(fo[name]).max() + carried[name], (name, err, carried[name])
+    assert A.grid_status(st.grid) == 0
+    with pytest.raises(A.HypError, match="stage out of range"):
+        A.rk_stage_scheme(st, scheme, F.RK_STAGES[scheme], cfg["dt"])
+
+
 def test_full_size_sbli_rhs(table):
     """The timed workload (2048 x 256, artificial diffusivity on): one full RHS against the
     oracle, every entry."""
