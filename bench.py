@@ -209,7 +209,7 @@ def field_ranges(cfg, ns=5):
     return out
 
 
-def thermo_sweep(A, gas, dev, n, seed, reps=2):
+def thermo_sweep(A, gas, dev, n, seed, reps=2, precision=0):
     """Throughput of hyp_thermo_eval on n independent states resident in HBM: T log-uniform in
     [300, 15000] K, rho log-uniform in [1e-4, 1] kg/m^3, mass fractions Dirichlet(1), e = e(T, Y)
     from hyp_thermo_energy. All outputs requested (T, p, wdot, mu, k, D, status)."""
@@ -230,12 +230,12 @@ def thermo_sweep(A, gas, dev, n, seed, reps=2):
     T, p, mu, k = (torch.empty(n, device=dev, dtype=torch.float64) for _ in range(4))
     wdot, D = (torch.empty((ns, n), device=dev, dtype=torch.float64) for _ in range(2))
     status = torch.empty(n, device=dev, dtype=torch.uint8)
-    A.thermo_eval(gas, rho, e, Y, T, p, wdot, mu, k, D, status)      # warm-up
+    A.thermo_eval(gas, rho, e, Y, T, p, wdot, mu, k, D, status, precision=precision)   # warm-up
     torch.cuda.synchronize()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     ev[0].record()
     for _ in range(reps):
-        A.thermo_eval(gas, rho, e, Y, T, p, wdot, mu, k, D, status)
+        A.thermo_eval(gas, rho, e, Y, T, p, wdot, mu, k, D, status, precision=precision)
     ev[1].record()
     torch.cuda.synchronize()
     ms = ev[0].elapsed_time(ev[1]) / reps
@@ -463,6 +463,8 @@ def ours_arm(args, rank, world, local_rank):
         del flush
         torch.cuda.empty_cache()
         sweep = thermo_sweep(A, gas, dev, int(args.thermo_states), 1000 + rank)
+        sweep["mixed"] = thermo_sweep(A, gas, dev, int(args.thermo_states), 1000 + rank,
+                                      precision=A.MIXED)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
