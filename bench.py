@@ -194,6 +194,21 @@ def reference_arm(args, rank, world):
     return 0
 
 
+def max_over_ranks(ms, world, device=None):
+    """Time of the slowest rank, which is the whole job's time (MAX all-reduce when world > 1)."""
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, points, steps, ms):
+    """Whole-job Mpts*RHS/s: every rank advances its own replica of `points` cells."""
+    return world * points * STAGES * steps / (ms / 1e3) / 1e6
+
+
 def field_ranges(cfg, ns=5):
     """Offsets of each conserved field in the state vector (layout of include/hyp.h)."""
     nx, ny = cfg["nx"], cfg["ny"]
@@ -355,11 +370,8 @@ def ours_arm(args, rank, world, local_rank):
     prof = A.grid_profile_read(st.grid)
     clk = clocks.stop()
     dev_ms = sum(a.elapsed_time(b) for a, b in ev)
-    t = torch.tensor([dev_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    max_ms = float(t.item())
-    value = world * points * STAGES * args.steps / (max_ms / 1e3) / 1e6
+    max_ms = max_over_ranks(dev_ms, world, dev)
+    value = job_rate(world, points, args.steps, max_ms)
     launches = sum(c for _, c in prof.values())
     status = A.grid_status(st.grid)
 
@@ -383,10 +395,7 @@ def ours_arm(args, rank, world, local_rank):
         barrier()
         A.grid_profile(st.grid, False)
         mprof = A.grid_profile_read(st.grid)
-        m_ms = sum(a.elapsed_time(b) for a, b in em)
-        tm = torch.tensor([m_ms], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        m_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in em), world, dev)
         # error of one mixed right-hand side against the FP64 path at the current state
         R64 = torch.empty_like(U)
         R32 = torch.empty_like(U)
@@ -398,8 +407,8 @@ def ours_arm(args, rank, world, local_rank):
             ref = R64[a0:a1]
             errs[name] = float((R32[a0:a1] - ref).abs().max() / ref.abs().max().clamp_min(1e-300))
         del R64, R32
-        mixed = {"value": world * points * STAGES * args.steps / (float(tm.item()) / 1e3) / 1e6,
-                 "unit": UNIT, "ms_per_step": float(tm.item()) / args.steps,
+        mixed = {"value": job_rate(world, points, args.steps, m_ms),
+                 "unit": UNIT, "ms_per_step": m_ms / args.steps,
                  "dtype": "f64 with f32 transport, diffusion and forward-rate exponentials",
                  "rhs_err_vs_fp64_path": errs, "max_rhs_err": max(errs.values()),
                  "err_bound": "1e-6 of max|R| per field against the FP64 oracle "
@@ -424,11 +433,8 @@ def ours_arm(args, rank, world, local_rank):
             ee[i][1].record()
             flush.fill_(float(i))
         barrier()
-        e_ms = sum(a.elapsed_time(b) for a, b in ee)
-        te = torch.tensor([e_ms], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * points * STAGES * args.steps / (float(te.item()) / 1e3) / 1e6,
+        e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ee), world, dev)
+        e2e = {"value": job_rate(world, points, args.steps, e_ms),
                "unit": UNIT, "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8}
 
     # ---------------- roofline of the dominant kernel ----------------
