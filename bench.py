@@ -40,6 +40,9 @@ CLOSURE_FP64_FLOP_PER_POINT = 3177.0
 # (one-pass dram__bytes counters, profiles/k_closure_sbli.md) scaled by the point count.
 CLOSURE_DRAM_BYTES = 2 * (50.94e6 + 100.45e6)
 CLOSURE_DRAM_POINTS = 2048 * 256
+# FP64 operations (2 DFMA + DADD + DMUL) per cell centre and right-hand side over every kernel of
+# a step, from the ncu instruction counts in profiles/fp64_flops_sbli_1024x256.md.
+RHS_FP64_FLOP_PER_POINT = 5142.0
 # GB300 FP64 peak derived from the unit counts: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
@@ -484,6 +487,10 @@ def ours_arm(args, rank, world, local_rank):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic", "config": workload_config(cfg, world), "e2e": e2e,
                 "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+                "whole_rhs": {"bound": "alu", "fp64_flop_per_point": RHS_FP64_FLOP_PER_POINT,
+                              "achieved": value * 1e6 * RHS_FP64_FLOP_PER_POINT / 1e12,
+                              "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                              "frac": value * 1e6 * RHS_FP64_FLOP_PER_POINT / 1e12 / FP64_PEAK_TFLOPS},
                 "wall_s_timed": t_wall, "status_flags": status, "mixed": mixed,
                 "serving": serving, "serving_fp64": serving_fp64,
                 "thermo_sweep": sweep,
