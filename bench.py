@@ -488,9 +488,9 @@ def ours_arm(args, rank, world, local_rank):
                 "data": "synthetic", "config": workload_config(cfg, world), "e2e": e2e,
                 "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
                 "whole_rhs": {"bound": "alu", "fp64_flop_per_point": RHS_FP64_FLOP_PER_POINT,
-                              "achieved": value * 1e6 * RHS_FP64_FLOP_PER_POINT / 1e12,
-                              "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                              "frac": value * 1e6 * RHS_FP64_FLOP_PER_POINT / 1e12 / FP64_PEAK_TFLOPS},
+                              "achieved": value / world * RHS_FP64_FLOP_PER_POINT / 1e6,
+                              "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s (per GPU)",
+                              "frac": value / world * RHS_FP64_FLOP_PER_POINT / 1e6 / FP64_PEAK_TFLOPS},
                 "wall_s_timed": t_wall, "status_flags": status, "mixed": mixed,
                 "serving": serving, "serving_fp64": serving_fp64,
                 "thermo_sweep": sweep,
