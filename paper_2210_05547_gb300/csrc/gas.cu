@@ -341,6 +341,16 @@ extern "C" int hyp_gas_model_load(const char* path, int kind, const hyp_freestre
         d.f_eps_inv[q] = (float)d.eps_inv[q];
         d.f_eps_powB[q] = (float)d.eps_powB[q];
     }
+    d.etab_lnT0 = log(T_LO);
+    d.etab_dlnT = (log(T_HI) - log(T_LO)) / (ETAB_N - 1);
+    for (int k = 0; k < ETAB_N; ++k) {
+        SpeciesState st;
+        species_state(d, exp(d.etab_lnT0 + k * d.etab_dlnT), st);
+        for (int i = 0; i < NSP; ++i) {
+            d.etab_e[i][k] = st.e[i];
+            d.etab_cv[i][k] = st.cv[i];
+        }
+    }
     d.Re = fs->reynolds;
     d.Pr = d.mu_inf * d.cp_inf / d.k_inf;
     d.T_ref = (d.gamma_inf - 1.0) * fs->T_inf;
@@ -385,7 +395,8 @@ __global__ void __launch_bounds__(128) k_thermo_eval(
 #pragma unroll
         for (int s = 0; s < NSP; ++s) y[s] = Y[s * n + i];
         ClosureOut o;
-        closure_si_p<MIXED>(g, rho[i], e[i], y, 1000.0, reactions && wdot, diffusion && D, o);
+        closure_si_p<MIXED>(g, rho[i], e[i], y, temperature_guess(g, e[i], y), reactions && wdot,
+                            diffusion && D, o);
         if (T) T[i] = o.T;
         if (p) p[i] = o.p;
         if (mu) mu[i] = o.mu;

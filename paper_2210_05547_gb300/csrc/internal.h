@@ -14,6 +14,7 @@
 #define MAXG 12                // reaction groups sharing (n, T_a, net stoichiometry)
 #define MAXLEV 6               // electronic levels per species
 #define MAXEPS 16              // distinct Lennard-Jones well depths of species pairs
+#define ETAB_N 64              // temperatures of the species-energy table (start of the T inversion)
 #define LINE_BLOCK 128         // threads per block of the line-operator kernel
 
 namespace hyp {
@@ -56,6 +57,11 @@ struct GasDev {
     float f_wilke_d[NSP][NSP];
     float f_pair_dinv[NSP * (NSP - 1) / 2];
     float f_eps_inv[MAXEPS], f_eps_powB[MAXEPS];
+    // species energies e_s and heat capacities c_v,s (J/kg, J/(kg K)) at ETAB_N temperatures
+    // spaced evenly in ln T from 50 K to 1e5 K: a starting temperature for the inversion when no
+    // earlier temperature is known
+    double etab_lnT0, etab_dlnT;
+    double etab_e[NSP][ETAB_N], etab_cv[NSP][ETAB_N];
     // kinetics (Eqs. 13-15): elementary reactions with explicit colliders, sorted by group
     int gstart[MAXG + 1];        // reactions of group k: [gstart[k], gstart[k+1])
     double C[MAXR];              // SI pre-exponential factor

@@ -119,6 +119,48 @@ __host__ __device__ inline double mixture_energy(const GasDev& g, double T, cons
     return e;
 }
 
+// Starting temperature for the inversion of e = sum_s Y_s e_s(T) from the tabulated species
+// energies: bisection over the table's temperatures for the bracketing interval, then the cubic
+// Hermite model of e(T) on it (values and heat capacities at its ends) inverted by three Newton
+// steps. Only the starting point of the safeguarded Newton iteration below: the temperature it
+// returns does not depend on it beyond the iteration's tolerance.
+__host__ __device__ inline double temperature_guess(const GasDev& g, double e, const double* Y) {
+    auto emix = [&](int k) {
+        double s = 0.0;
+#pragma unroll
+        for (int i = 0; i < NSP; ++i) s += Y[i] * g.etab_e[i][k];
+        return s;
+    };
+    int lo = 0, hi = ETAB_N - 1;
+    if (!(e > emix(lo))) return T_LO;
+    if (!(e < emix(hi))) return T_HI;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) / 2;
+        if (emix(mid) <= e) lo = mid; else hi = mid;
+    }
+    const double Ta = exp(g.etab_lnT0 + lo * g.etab_dlnT), Tb = exp(g.etab_lnT0 + hi * g.etab_dlnT);
+    const double ea = emix(lo), eb = emix(hi);
+    double ca = 0.0, cb = 0.0;
+#pragma unroll
+    for (int i = 0; i < NSP; ++i) {
+        ca += Y[i] * g.etab_cv[i][lo];
+        cb += Y[i] * g.etab_cv[i][hi];
+    }
+    const double h = Tb - Ta;
+    double t = (e - ea) / (eb - ea);                 // linear start
+    for (int it = 0; it < 3; ++it) {
+        const double t2 = t * t, t3 = t2 * t;
+        const double h00 = 2 * t3 - 3 * t2 + 1, h10 = t3 - 2 * t2 + t;
+        const double h01 = -2 * t3 + 3 * t2, h11 = t3 - t2;
+        const double f = h00 * ea + h10 * h * ca + h01 * eb + h11 * h * cb - e;
+        const double df = (6 * t2 - 6 * t) * ea + (3 * t2 - 4 * t + 1) * h * ca +
+                          (-6 * t2 + 6 * t) * eb + (3 * t2 - 2 * t) * h * cb;
+        if (df > 0.0) t -= f / df;
+        t = fmin(fmax(t, 0.0), 1.0);
+    }
+    return Ta + t * h;
+}
+
 // Safeguarded Newton for sum_s Y_s e_s(T) = e; s holds the species state at the returned T.
 __host__ __device__ inline double temperature_from_energy(const GasDev& g, double e,
                                                           const double* Y, double T0,
