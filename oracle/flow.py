@@ -437,6 +437,53 @@ def closure_nd(case: Case, rho, e, Y):
 
 
 # ---------------------------------------------------------------------------------------------
+# Stefan-Maxwell diffusion (Eq. 17), the alternative to the algebraic model of Eq. (18)
+# ---------------------------------------------------------------------------------------------
+# Eq. (17) with the interaction coefficients of the Stefan-Maxwell relations,
+#     d_s = sum_{i != s} X_s X_i (V_i - V_s) / D_si,   d_s = grad X_s (Eq. 16),
+# written for the fluxes J_s = rho Y_s V_s (X_i / Y_i = Mbar / M_i), which stays regular for
+# vanishing mole fractions:
+#     sum_{i != s} (X_s J_i / M_i - X_i J_s / M_s) / D_si = (rho / Mbar) d_s,
+# with the equation of the first species (the omitted, most abundant one) replaced by the
+# mass constraint sum_s J_s = 0. Nondimensional D_si = D_si rho_inf / (mu_inf Re), so J carries
+# 1/Re like the algebraic flux. Evaluated at the faces from the interpolated density and mass
+# fractions, the face gradients of X and binary coefficients at the interpolated T and p.
+DIFF_RAMSHAW, DIFF_SM = "ramshaw", "stefan_maxwell"
+
+
+def stefan_maxwell_fluxes(tab, rho_f, Y_f, dX_f, Dnd):
+    """J_s at face points. rho_f (n,), Y_f and dX_f (ns, n), Dnd (ns, ns, n) nondimensional
+    binary coefficients including 1/Re. Returns (ns, n)."""
+    ns = tab.ns
+    M = tab.M()
+    n = rho_f.size
+    inv = Y_f / M[:, None]
+    Mbar = 1.0 / np.sum(inv, axis=0)
+    X = inv * Mbar
+    A = np.zeros((n, ns, ns))
+    b = np.zeros((n, ns))
+    for s in range(1, ns):
+        for i in range(ns):
+            if i != s:
+                A[:, s, i] += X[s] / (M[i] * Dnd[s, i])
+                A[:, s, s] -= X[i] / (M[s] * Dnd[s, i])
+        b[:, s] = rho_f / Mbar * dX_f[s]
+    A[:, 0, :] = 1.0
+    return np.linalg.solve(A, b[..., None])[..., 0].T
+
+
+def _sm_face_fluxes(case, rho_f, Y_f, dX_f, T_f, p_f):
+    sc, tab = case.sc, case.tab
+    shape = rho_f.shape
+    T_si = T_f.ravel() * sc.T_ref
+    p_si = p_f.ravel() * sc.rho * sc.a ** 2
+    Dnd = G.binary_diffusion(tab, T_si, p_si) * sc.rho / sc.mu / sc.Re
+    J = stefan_maxwell_fluxes(tab, rho_f.ravel(), Y_f.reshape(tab.ns, -1),
+                              dX_f.reshape(tab.ns, -1), Dnd)
+    return J.reshape((tab.ns,) + shape)
+
+
+# ---------------------------------------------------------------------------------------------
 # Artificial diffusivity helpers (Sec. 3.3)
 # ---------------------------------------------------------------------------------------------
 
@@ -541,7 +588,9 @@ def rhs(case: Case, U, return_parts=False):
     # (E) transport coefficients (viscous scale 1/Re, conduction 1/(Re Pr Ec), diffusion 1/Re)
     mu_e = th["mu"] / Re + mu_st
     K = th["k"] / (Re * Pr) + kap_st
-    Gd = th["W"] * (th["D"] / Re + D_st)
+    sm = case.kind == KIND_CNEQ and cfg.get("diffusion_model", DIFF_RAMSHAW) == DIFF_SM
+    # with Stefan-Maxwell diffusion the algebraic form keeps only the artificial diffusivity
+    Gd = th["W"] * ((0.0 if sm else th["D"] / Re) + D_st)
 
     # (F) viscous stresses, Eq. (9) with the Stokes 2/3 and the artificial bulk viscosity
     tau_xx = mu_e * (2.0 * dudx - 2.0 / 3.0 * div) + beta_st * div
@@ -562,6 +611,8 @@ def rhs(case: Case, U, return_parts=False):
     txy_x = C.ifc(tau_xy, 0)
     sumx = np.sum(Gx * dXdx, axis=0)
     Jx = -(Gx * dXdx - Yx * sumx)                            # Eq. (18), gradient of X (Eq. 16)
+    if sm:
+        Jx = Jx + _sm_face_fluxes(case, rho_xf, Yx, dXdx, C.icf(T, 1), C.icf(p, 1))
     Fsx = [rhou * Yx[s] + Jx[s] for s in range(ns)]
     qx = -Kx * dTdx + np.sum(hx * Jx, axis=0)                # Eq. (10)
     FEx = rhou * Hx + qx - (txx_x * u_xf + txy_x * v_x)
@@ -580,6 +631,8 @@ def rhs(case: Case, U, return_parts=False):
     txy_y = C.ifc(tau_xy, 1)
     sumy = np.sum(Gy * dXdy, axis=0)
     Jy = -(Gy * dXdy - Yy * sumy)
+    if sm:
+        Jy = Jy + _sm_face_fluxes(case, rho_yf, Yy, dXdy, C.icf(T, 0), C.icf(p, 0))
     if wall:
         Jy[:, 0, :] = 0.0
     Fsy = [rhov * Yy[s] + Jy[s] for s in range(ns)]

@@ -37,7 +37,7 @@ def bl_case(nx=256, ny=64, seed=0, kind="cneq"):
         shock_deflection_deg=0.0, shock_x=0.0, shock_width=0.0,
         sponge_sigma=200.0, sponge_in=5.0, sponge_out=15.0, sponge_top_cells=max(2, (26 * ny) // 211),
         artificial_diffusivity=0, C_mu=0.002, C_beta=1.75, C_kappa=0.01, C_D=0.0,
-        noise_amp=1.0e-4, dt=2.0e-4, filter_sigma=0.0,
+        noise_amp=1.0e-4, dt=2.0e-4, filter_sigma=0.0, diffusion_model="ramshaw",
     )
 
 
@@ -54,7 +54,7 @@ def sbli_case(nx=2048, ny=256, seed=0, kind="cneq"):
         shock_deflection_deg=deflection, shock_x=120.0, shock_width=1.0,
         sponge_sigma=200.0, sponge_in=10.0, sponge_out=30.0, sponge_top_cells=max(2, (26 * ny) // 211),
         artificial_diffusivity=1, C_mu=0.002, C_beta=1.75, C_kappa=0.01, C_D=0.01,
-        noise_amp=1.0e-4, dt=2.0e-3, filter_sigma=0.05,
+        noise_amp=1.0e-4, dt=2.0e-3, filter_sigma=0.05, diffusion_model="ramshaw",
     )
 
 

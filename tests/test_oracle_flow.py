@@ -256,11 +256,12 @@ def _binary_reference(cfg, case):
     return point_state, fluxes, exact
 
 
-def test_pde_consistency_binary_diffusion(table):
+@pytest.mark.parametrize("model", [F.DIFF_RAMSHAW, F.DIFF_SM])
+def test_pde_consistency_binary_diffusion(table, model):
     errs = []
     for nx, ny in ((26, 20), (52, 40), (104, 80)):
         cfg = _mms_box(nx, ny, "cneq")
-        cfg.update(T_inf=300.0, p_inf=2000.0, reynolds=20.0)
+        cfg.update(T_inf=300.0, p_inf=2000.0, reynolds=20.0, diffusion_model=model)
         case = F.make_case(cfg, table)
         point_state, fluxes, exact = _binary_reference(cfg, case)
         g = case.grid
