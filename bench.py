@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--nx", type=int, default=2048, help="cells in x (profiling of small cases)")
     ap.add_argument("--ny", type=int, default=256, help="cells in y (profiling of small cases)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
+    ap.add_argument("--no-sm", action="store_true", help="skip the Stefan-Maxwell measurement")
     ap.add_argument("--serve-requests", type=int, default=48,
                     help="requests of the serving measurement (0 skips it)")
     ap.add_argument("--thermo-states", type=float, default=1e8,
@@ -462,6 +463,36 @@ def ours_arm(args, rank, world, local_rank):
         roof.update(bound="alu", achieved=None, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s", frac=None,
                     traffic=None, note="per-point FP64 count not yet measured for this kernel")
 
+    # ---------------- Stefan-Maxwell diffusion on the same workload ----------------
+    smd = None
+    if not args.no_sm:
+        cfg_sm = dict(cfg, diffusion_model="stefan_maxwell")
+        gas_sm = A.gas_model_load(cfg_sm)
+        U2 = torch.empty(n, dtype=torch.float64, device=dev)
+        dQ2 = torch.empty_like(U2)
+        st2 = A.state_init(gas_sm, cfg_sm, U2, dQ2, I.state_noise(n, cfg["seed"]))
+        for _ in range(args.warmup):
+            for k in range(STAGES):
+                A.rk_stage(st2, k, dt)
+        es = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        barrier()
+        for i in range(args.steps):
+            es[i][0].record()
+            for k in range(STAGES):
+                A.rk_stage(st2, k, dt)
+            es[i][1].record()
+            flush.fill_(float(i))
+        barrier()
+        s_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in es), world, dev)
+        smd = {"value": job_rate(world, points, args.steps, s_ms), "unit": UNIT,
+               "ms_per_step": s_ms / args.steps,
+               "cost_vs_algebraic": s_ms / max_ms,
+               "status_flags": A.grid_status(st2.grid),
+               "note": "Stefan-Maxwell system (Eq. 17) solved at every face instead of the "
+                       "algebraic model (Eq. 18); same case, FP64"}
+        del st2, U2, dQ2
+
     serving = serving_fp64 = None
     if args.serve_requests > 0:
         serving = serving_bench(A, I, args.serve_requests, 100 + rank, A.MIXED)
@@ -492,7 +523,7 @@ def ours_arm(args, rank, world, local_rank):
                               "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s (per GPU)",
                               "frac": value / world * RHS_FP64_FLOP_PER_POINT / 1e6 / FP64_PEAK_TFLOPS},
                 "wall_s_timed": t_wall, "status_flags": status, "mixed": mixed,
-                "serving": serving, "serving_fp64": serving_fp64,
+                "serving": serving, "serving_fp64": serving_fp64, "stefan_maxwell": smd,
                 "thermo_sweep": sweep,
                 "kernels": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1]}}
         print(json.dumps(line), flush=True)

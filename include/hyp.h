@@ -117,6 +117,8 @@ typedef struct {
     const double* noise;           /* HOST, nullable; hyp_state_size() values in [-1, 1] */
     double filter_sigma;           /* > 0: low-pass filter of the state after each RK step, with
                                       this damping of the grid-to-grid mode (see hyp_rk_stage) */
+    int32_t diffusion_model;       /* HYP_GAS_CNEQ: 0 the algebraic model of Eq. 18, 1 the
+                                      Stefan-Maxwell system of Eq. 17 solved at every face */
 } hyp_case;
 
 /* Load a gas table (plain-text SPECIES / LEVEL / REACTION lines, see data/air5.dat) and build

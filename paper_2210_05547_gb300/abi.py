@@ -18,6 +18,7 @@ MAX_SPECIES = 5
 GAS_KINDS = {"cneq": 0, "frozen": 1, "cpg": 2, "tpg": 3}
 STRETCH = {"uniform": 0, "tanh": 1, "cubic": 2}
 FLOWS = {"bl": 0, "sbli": 1}
+DIFFUSION_MODELS = {"ramshaw": 0, "stefan_maxwell": 1}
 FP64 = 0
 MIXED = 1
 TABLE_AIR5 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data", "air5.dat")
@@ -47,7 +48,7 @@ class CaseDesc(ctypes.Structure):
                 ("C_mu", ctypes.c_double), ("C_beta", ctypes.c_double),
                 ("C_kappa", ctypes.c_double), ("C_D", ctypes.c_double),
                 ("noise_amp", ctypes.c_double), ("noise", ctypes.POINTER(ctypes.c_double)),
-                ("filter_sigma", ctypes.c_double)]
+                ("filter_sigma", ctypes.c_double), ("diffusion_model", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):
@@ -190,6 +191,7 @@ def case_struct(cfg, noise=None):
     c.C_mu, c.C_beta, c.C_kappa, c.C_D = cfg["C_mu"], cfg["C_beta"], cfg["C_kappa"], cfg["C_D"]
     c.noise_amp = cfg["noise_amp"]
     c.filter_sigma = cfg.get("filter_sigma", 0.0)
+    c.diffusion_model = DIFFUSION_MODELS[cfg.get("diffusion_model", "ramshaw")]
     if noise is not None:
         arr = np.ascontiguousarray(noise, dtype=np.float64)
         c.noise = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))

@@ -132,9 +132,10 @@ __global__ void kb_stress_cn(const BatchItem* __restrict__ items, BatchDev B) {
     });
 }
 
-__global__ void kb_flux(const BatchItem* __restrict__ items, BatchDev B) {
+template <bool SMK>
+__global__ void kb_flux(GasDev g, const BatchItem* __restrict__ items, BatchDev B) {
     for_tiles(items, B, SP_FACES, [&](const BatchItem& it, long long lo, long long hi) {
-        flux_body(it.v, it.U, it.s, -1, lo, hi, blockDim.x);
+        flux_body<SMK>(g, it.sc, it.v, it.U, it.s, -1, lo, hi, blockDim.x);
     });
 }
 
@@ -198,6 +199,7 @@ struct hyp_batch {
     int ph_start[PH_COUNT] = {}, ph_count[PH_COUNT] = {}, ph_blocks[PH_COUNT] = {};
     int tiles[SP_COUNT] = {};
     int closure_blocks[2] = {0, 0};
+    bool any_sm = false;         // a member uses Stefan-Maxwell diffusion
     int pw_blocks = 0;
     cudaStream_t side = nullptr;
     cudaEvent_t fork[2] = {}, join[2] = {};
@@ -232,11 +234,13 @@ int rebuild(hyp_batch* b, cudaStream_t s) {
     b->h_items.assign(n, BatchItem());
     b->h_tstart.assign((size_t)SP_COUNT * (n + 1), 0);
     b->h_jobs.clear();
+    b->any_sm = false;
     for (int k = 0; k < n; ++k) {
         hyp_grid* G = b->members[k].st->grid;
         BatchItem& it = b->h_items[k];
         memset(&it, 0, sizeof(it));
         it.v = G->view();
+        b->any_sm = b->any_sm || it.v.sm;
         it.s = G->s;
         it.sc = scales_of(G->gas);
         it.U = b->members[k].st->U;
@@ -358,7 +362,8 @@ int launch_step(hyp_batch* b, cudaStream_t s) {
         HYP_CUDA(cudaEventRecord(b->join[1], s2));
         HYP_CUDA(lines(PH_FACE, s));
         HYP_CUDA(cudaStreamWaitEvent(s, b->join[1], 0));
-        kb_flux<<<grid_for_tiles(b, SP_FACES, pw), 128, 0, s>>>(b->d_items, B);
+        if (b->any_sm) kb_flux<true><<<grid_for_tiles(b, SP_FACES, pw), 128, 0, s>>>(b->table, b->d_items, B);
+        else kb_flux<false><<<grid_for_tiles(b, SP_FACES, pw), 128, 0, s>>>(b->table, b->d_items, B);
         HYP_CUDA(lines(PH_DIV, s));
         kb_assemble<<<grid_for_tiles(b, SP_STATE, pw), 256, 0, s>>>(b->d_items, B, RK_A[stage], RK_B[stage]);
         HYP_CUDA(cudaGetLastError());

@@ -37,10 +37,10 @@ struct Scratch {
     double *dudy_c, *dvdx_c, *S, *div, *fsw, *raw[8], *filt[8];
     // x-faces
     double *rho_xf, *u_xf, *Yx[NSP], *Gx[NSP], *hx[NSP], *Hx, *Kx, *txx_x, *v_x, *dTdx,
-        *dXdx[NSP], *txy_x, *Fsx[NSP], *FEx, *mu_xf, *dudy_t, *dvdx_t, *mux_f;
+        *dXdx[NSP], *txy_x, *Fsx[NSP], *FEx, *mu_xf, *dudy_t, *dvdx_t, *mux_f, *Tx, *px;
     // y-faces
     double *rho_yf, *v_yf, *Yy[NSP], *Gy[NSP], *hy[NSP], *Hy, *Ky, *tyy_y, *u_y, *dTdy,
-        *dXdy[NSP], *txy_y, *Fsy[NSP], *FEy, *mvy_f;
+        *dXdy[NSP], *txy_y, *Fsy[NSP], *FEy, *mvy_f, *Ty, *py;
     // corners
     double *dudy_cn, *dvdx_cn, *u_cn, *v_cn, *rho_cn, *mu_cn, *tau_xy, *Gxy;
     // state-sized
@@ -50,6 +50,7 @@ struct Scratch {
 // Kernel-side view of a grid (passed by value).
 struct GridView {
     int nx, ny, wall, ad, nstate;
+    int sm;                      // Stefan-Maxwell diffusion (Eq. 17) instead of Eq. (18)
     int predict;                 // Newton starts from a step off the cached species state
     long long off[NSP + 3];
     double Tw_nd;
@@ -163,6 +164,7 @@ struct hyp_grid {
         v.C_beta = cas.C_beta;
         v.C_kappa = cas.C_kappa;
         v.C_D = cas.C_D;
+        v.sm = cas.diffusion_model == 1 && gas.kind == HYP_GAS_CNEQ;
         v.xi_c = xi_c;
         v.eta_c = eta_c;
         v.status = status;

@@ -84,7 +84,7 @@ __device__ __forceinline__ void closure_body(const GasDev& g, const Scales& sc, 
                 T0 += d1 - 0.5 * cvpc * d1 * d1 * icv;
             }
             ClosureOut o;
-            closure_si_p<MIXED>(g, rho * sc.rho_inf, e_si, Y, T0, cneq, cneq, o);
+            closure_si_p<MIXED>(g, rho * sc.rho_inf, e_si, Y, T0, cneq, cneq && !v.sm, o);
             atomic_status(v.status, o.status);
             s.Tcache[idx] = o.T;
 #pragma unroll
@@ -277,9 +277,12 @@ __device__ __forceinline__ void stress_cn_body(const Scratch& s, long long lo, l
     }
 }
 
-// (G, H) species and energy fluxes at the x-faces (dir 0) or y-faces (dir 1) of face index i
-__device__ __forceinline__ void flux_point(const GridView& v, const double* __restrict__ U,
-                                           const Scratch& s, int dir, int i) {
+// (G, H) species and energy fluxes at the x-faces (dir 0) or y-faces (dir 1) of face index i;
+// SMK: the kernel carries the Stefan-Maxwell solve (used by grids with v.sm)
+template <bool SMK>
+__device__ __forceinline__ void flux_point(const GasDev& gd, const Scales& sc, const GridView& v,
+                                           const double* __restrict__ U, const Scratch& s, int dir,
+                                           int i) {
     const double* __restrict__ mom = U + v.off[NSP + 1 + dir];
     double* const* Yf = dir == 0 ? s.Yx : s.Yy;
     double* const* Gf = dir == 0 ? s.Gx : s.Gy;
@@ -303,9 +306,29 @@ __device__ __forceinline__ void flux_point(const GridView& v, const double* __re
     }
     double q = -Kf[i] * dT[i];
     const double m = mom[i];
+    if (SMK && v.sm && !wallface) {
+        // Stefan-Maxwell fluxes (Eq. 17); the algebraic part above carries only the artificial
+        // diffusivity in this mode
+        double Yl[NSP], dXl[NSP], Jsm[NSP];
+#pragma unroll
+        for (int sp = 0; sp < NSP; ++sp) {
+            Yl[sp] = Yf[sp][i];
+            dXl[sp] = dX[sp][i];
+        }
+        const double* Tf = dir == 0 ? s.Tx : s.Ty;
+        const double* pf = dir == 0 ? s.px : s.py;
+        const double* rf = dir == 0 ? s.rho_xf : s.rho_yf;
+        stefan_maxwell_face(gd, Tf[i] * sc.T_ref, pf[i] * sc.rho_inf * sc.a_inf * sc.a_inf,
+                            sc.mu_inf * sc.Re / sc.rho_inf, rf[i], Yl, dXl, Jsm);
+#pragma unroll
+        for (int sp = 0; sp < NSP; ++sp) J[sp] = Jsm[sp];
+    } else {
+#pragma unroll
+        for (int sp = 0; sp < NSP; ++sp) J[sp] = 0.0;
+    }
 #pragma unroll
     for (int sp = 0; sp < NSP; ++sp) {
-        J[sp] = wallface ? 0.0 : -(g[sp] - Yf[sp][i] * sum);
+        J[sp] = wallface ? 0.0 : J[sp] - (g[sp] - Yf[sp][i] * sum);
         q += hf[sp][i] * J[sp];
     }
 #pragma unroll
@@ -316,15 +339,16 @@ __device__ __forceinline__ void flux_point(const GridView& v, const double* __re
 }
 
 // Index range: the x-faces, then the y-faces (dir < 0), or the faces of one direction.
-__device__ __forceinline__ void flux_body(const GridView& v, const double* __restrict__ U,
-                                          const Scratch& s, int dir, long long lo, long long hi,
-                                          long long stride) {
+template <bool SMK>
+__device__ __forceinline__ void flux_body(const GasDev& gd, const Scales& sc, const GridView& v,
+                                          const double* __restrict__ U, const Scratch& s, int dir,
+                                          long long lo, long long hi, long long stride) {
     const int nxf = v.ny * (v.nx + 1);
     for (long long li = lo + threadIdx.x; li < hi; li += stride) {
         const int i = (int)li;
-        if (dir >= 0) flux_point(v, U, s, dir, i);
-        else if (i < nxf) flux_point(v, U, s, 0, i);
-        else flux_point(v, U, s, 1, i - nxf);
+        if (dir >= 0) flux_point<SMK>(gd, sc, v, U, s, dir, i);
+        else if (i < nxf) flux_point<SMK>(gd, sc, v, U, s, 0, i);
+        else flux_point<SMK>(gd, sc, v, U, s, 1, i - nxf);
     }
 }
 

@@ -409,8 +409,10 @@ __global__ void k_stress_cn(GridView v, Scratch s) {
     stress_cn_body(s, GRID_RANGE((long long)(v.nx + 1) * (v.ny + 1)));
 }
 
-__global__ void k_flux(GridView v, const double* __restrict__ U, Scratch s, int dir) {
-    flux_body(v, U, s, dir, GRID_RANGE(dir == 0 ? (long long)v.ny * (v.nx + 1) : (long long)(v.ny + 1) * v.nx));
+template <bool SMK>
+__global__ void k_flux(GasDev g, Scales sc, GridView v, const double* __restrict__ U, Scratch s,
+                       int dir) {
+    flux_body<SMK>(g, sc, v, U, s, dir, GRID_RANGE(dir == 0 ? (long long)v.ny * (v.nx + 1) : (long long)(v.ny + 1) * v.nx));
 }
 
 __global__ void k_assemble(long long n, AssembleArgs a) { assemble_body(a, GRID_RANGE(n)); }
@@ -700,7 +702,7 @@ extern "C" int hyp_state_init(const hyp_gas* gas, const hyp_grid_desc* desc, con
         S.filt[q] = take(nc);
     }
     double** xfields[] = {&S.rho_xf, &S.u_xf, &S.Hx, &S.Kx, &S.txx_x, &S.v_x, &S.dTdx, &S.txy_x,
-                          &S.FEx, &S.mu_xf, &S.dudy_t, &S.dvdx_t, &S.mux_f};
+                          &S.FEx, &S.mu_xf, &S.dudy_t, &S.dvdx_t, &S.mux_f, &S.Tx, &S.px};
     for (double** f : xfields) *f = take(nxf);
     for (int sp = 0; sp < NSP; ++sp) {
         S.Yx[sp] = take(nxf);
@@ -710,7 +712,7 @@ extern "C" int hyp_state_init(const hyp_gas* gas, const hyp_grid_desc* desc, con
         S.Fsx[sp] = take(nxf);
     }
     double** yfields[] = {&S.rho_yf, &S.v_yf, &S.Hy, &S.Ky, &S.tyy_y, &S.u_y, &S.dTdy, &S.txy_y,
-                          &S.FEy, &S.mvy_f};
+                          &S.FEy, &S.mvy_f, &S.Ty, &S.py};
     for (double** f : yfields) *f = take(nyf);
     for (int sp = 0; sp < NSP; ++sp) {
         S.Yy[sp] = take(nyf);
@@ -836,6 +838,17 @@ extern "C" int hyp_state_init(const hyp_gas* gas, const hyp_grid_desc* desc, con
     B.f32();
     B.add(wall ? OY_DCFW : OY_DCF, S.T, NC, S.dTdy, NYF, G->eta_f, 1.0, G->Tw_nd);
     B.f32();
+    if (G->view().sm) {
+        // face temperature and pressure for the binary coefficients of Eq. (17)
+        B.add(OX_ICF, S.T, NC, S.Tx, NXF, nullptr);
+        B.f32();
+        B.add(OX_ICF, S.p, NC, S.px, NXF, nullptr);
+        B.f32();
+        B.add(OY_ICF, S.T, NC, S.Ty, NYF, nullptr);
+        B.f32();
+        B.add(OY_ICF, S.p, NC, S.py, NYF, nullptr);
+        B.f32();
+    }
     B.begin(PH_FACEB);
     B.add(OY_IFC, S.tau_xy, NCN, S.txy_x, NXF, nullptr);
     B.f32();
@@ -1059,8 +1072,13 @@ static int run_rhs(const hyp_gas* gas, hyp_grid* G, const double* U, double* dUd
                                             G->ph_blocks[PH_FACE], U, s, mx));
     HYP_CUDA(e1);
     HYP_CUDA(cudaStreamWaitEvent(s, G->join[1], 0));
-    TIMED(KID_FLUX, (k_flux<<<blocks_for(d.size(NXF), 128), 128, 0, s>>>(v, U, S, 0)));
-    TIMED(KID_FLUX, (k_flux<<<blocks_for(d.size(NYF), 128), 128, 0, s>>>(v, U, S, 1)));
+    if (v.sm) {
+        TIMED(KID_FLUX, (k_flux<true><<<blocks_for(d.size(NXF), 128), 128, 0, s>>>(g, sc, v, U, S, 0)));
+        TIMED(KID_FLUX, (k_flux<true><<<blocks_for(d.size(NYF), 128), 128, 0, s>>>(g, sc, v, U, S, 1)));
+    } else {
+        TIMED(KID_FLUX, (k_flux<false><<<blocks_for(d.size(NXF), 128), 128, 0, s>>>(g, sc, v, U, S, 0)));
+        TIMED(KID_FLUX, (k_flux<false><<<blocks_for(d.size(NYF), 128), 128, 0, s>>>(g, sc, v, U, S, 1)));
+    }
     TIMED(KID_LINES_DIV, e1 = launch_lines(G->jobs + G->ph_start[PH_DIV], G->ph_count[PH_DIV],
                                            G->ph_blocks[PH_DIV], U, s, mx));
     HYP_CUDA(e1);
@@ -1334,8 +1352,13 @@ extern "C" int hyp_rhs_noalloc(const hyp_gas* gas, const hyp_grid* grid, const d
     k_stress_cn<<<blocks_for(d.size(NCN), 256), 256, 0, s>>>(v, S);
     HYP_CUDA(lines(PH_FACE, G->ph_count[PH_FACE]));
     HYP_CUDA(lines(PH_FACEB, G->ph_count[PH_FACEB]));
-    k_flux<<<blocks_for(d.size(NXF), 128), 128, 0, s>>>(v, U, S, 0);
-    k_flux<<<blocks_for(d.size(NYF), 128), 128, 0, s>>>(v, U, S, 1);
+    if (v.sm) {
+        k_flux<true><<<blocks_for(d.size(NXF), 128), 128, 0, s>>>(g, scales_of(g), v, U, S, 0);
+        k_flux<true><<<blocks_for(d.size(NYF), 128), 128, 0, s>>>(g, scales_of(g), v, U, S, 1);
+    } else {
+        k_flux<false><<<blocks_for(d.size(NXF), 128), 128, 0, s>>>(g, scales_of(g), v, U, S, 0);
+        k_flux<false><<<blocks_for(d.size(NYF), 128), 128, 0, s>>>(g, scales_of(g), v, U, S, 1);
+    }
     HYP_CUDA(lines(PH_DIV, G->ph_count[PH_DIV]));
     const AssembleArgs aa{S.DX, S.DY, S.SRC, G->sigma, G->Uref, G->mask, (double*)U, dUdt,
                           nullptr, 0, 0.0, 0.0, 0.0};

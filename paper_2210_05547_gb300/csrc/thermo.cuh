@@ -480,5 +480,103 @@ struct TpgModel {
     }
 };
 
+// ---- Stefan-Maxwell diffusion (Eq. 17) at one face ----
+// Flux form of the Stefan-Maxwell relations, regular for vanishing mole fractions:
+//     sum_{i != s} (X_s J_i / M_i - X_i J_s / M_s) / D_si = (rho / Mbar) grad X_s,  s >= 1,
+// with the first (omitted, most abundant) species' equation replaced by sum_s J_s = 0, solved by
+// Gaussian elimination with partial pivoting (5 x 5, in registers). Tsi, psi: SI temperature and
+// pressure for the binary coefficients (Chapman-Enskog, the collision-integral fit of the
+// closure); dscale converts 1/D_si (SI) to the nondimensional 1/(D_si rho_inf / (mu_inf Re)).
+// rho, dX and the returned J are nondimensional.
+__device__ inline void stefan_maxwell_face(const GasDev& g, double Tsi, double psi, double dscale,
+                                           double rho, const double* Yf, const double* dX,
+                                           double* J) {
+    double inv[NSP], X[NSP], ym = 0.0;
+#pragma unroll
+    for (int s = 0; s < NSP; ++s) {
+        inv[s] = Yf[s] * g.invM[s];
+        ym += inv[s];
+    }
+    const double Mbar = 1.0 / ym;
+#pragma unroll
+    for (int s = 0; s < NSP; ++s) X[s] = inv[s] * Mbar;
+    double a[NSP][NSP], b[NSP];
+#pragma unroll
+    for (int r = 0; r < NSP; ++r) {
+#pragma unroll
+        for (int c = 0; c < NSP; ++c) a[r][c] = 0.0;
+        b[r] = r == 0 ? 0.0 : rho * ym * dX[r];
+    }
+    const double lnT = log(Tsi);
+    const double TmB = exp(-NJA_B * lnT);
+    const double cc = psi / (Tsi * sqrt(Tsi)) * dscale;
+    for (int q = 0; q < g.neps; ++q) {
+        const double ts = Tsi * g.eps_inv[q];
+        double om = NJA_A * TmB * g.eps_powB[q];
+        if (NJA_D * ts < OMEGA_CUT) om += NJA_C * exp(-NJA_D * ts);
+        if (NJA_F * ts < OMEGA_CUT) om += NJA_E * exp(-NJA_F * ts);
+        if (NJA_H * ts < OMEGA_CUT) om += NJA_G * exp(-NJA_H * ts);
+        for (int pr = g.pstart[q]; pr < g.pstart[q + 1]; ++pr) {
+            const int i = g.pair_i[pr], r = g.pair_r[pr];
+            const double w = cc * om * g.pair_dinv[pr];          // nondimensional 1 / D_ir
+#pragma unroll
+            for (int s = 1; s < NSP; ++s) {
+                if (s == i) {
+                    a[s][r] += X[i] * w * g.invM[r];
+                    a[s][s] -= X[r] * w * g.invM[i];
+                }
+                if (s == r) {
+                    a[s][i] += X[r] * w * g.invM[i];
+                    a[s][s] -= X[i] * w * g.invM[r];
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < NSP; ++c) a[0][c] = 1.0;
+    // elimination with partial pivoting (all indices static after unrolling)
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) {
+        int p = k;
+        double best = fabs(a[k][k]);
+#pragma unroll
+        for (int r = k + 1; r < NSP; ++r) {
+            if (fabs(a[r][k]) > best) {
+                best = fabs(a[r][k]);
+                p = r;
+            }
+        }
+#pragma unroll
+        for (int r = k + 1; r < NSP; ++r) {
+            if (r == p) {
+#pragma unroll
+                for (int c = 0; c < NSP; ++c) {
+                    const double t = a[k][c];
+                    a[k][c] = a[r][c];
+                    a[r][c] = t;
+                }
+                const double t = b[k];
+                b[k] = b[r];
+                b[r] = t;
+            }
+        }
+        const double ip = 1.0 / a[k][k];
+#pragma unroll
+        for (int r = k + 1; r < NSP; ++r) {
+            const double f = a[r][k] * ip;
+#pragma unroll
+            for (int c = k + 1; c < NSP; ++c) a[r][c] -= f * a[k][c];
+            b[r] -= f * b[k];
+        }
+    }
+#pragma unroll
+    for (int k = NSP - 1; k >= 0; --k) {
+        double t = b[k];
+#pragma unroll
+        for (int c = k + 1; c < NSP; ++c) t -= a[k][c] * J[c];
+        J[k] = t / a[k][k];
+    }
+}
+
 }  // namespace hyp
 

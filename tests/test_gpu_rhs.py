@@ -34,6 +34,8 @@ def _cases():
         "sbli_frozen_64x33": I.sbli_case(64, 33, seed=2, kind="frozen"),
         "bl_tpg_48x32": I.bl_case(48, 32, seed=4, kind="tpg"),
         "sbli_tpg_96x40": I.sbli_case(96, 40, seed=5, kind="tpg"),
+        "bl_sm_64x40": dict(I.bl_case(64, 40, seed=8), diffusion_model="stefan_maxwell"),
+        "sbli_sm_96x40": dict(I.sbli_case(96, 40, seed=9), diffusion_model="stefan_maxwell"),
     }
 
 
