@@ -27,8 +27,11 @@ from scipy.special import erf
 from . import compact as C
 from . import gas as G
 
-KIND_CNEQ, KIND_FROZEN, KIND_CPG, KIND_TPG = "cneq", "frozen", "cpg", "tpg"
+KIND_CNEQ, KIND_FROZEN, KIND_CPG, KIND_TPG, KIND_LTE = "cneq", "frozen", "cpg", "tpg", "lte"
 PERFECT_KINDS = (KIND_CPG, KIND_TPG)      # composition irrelevant, no reactions or diffusion
+# Local thermodynamic equilibrium (Sec. 2.2.2): the composition follows from (rho, e) and the
+# element content of the freestream air; the species fields of the state are carried as passive
+# scalars (no diffusion, no sources) and do not enter the closure.
 
 SUTHERLAND_C1 = 1.458e-6      # kg m^-1 s^-1 K^-1/2 (Eq. 24)
 SUTHERLAND_TS = 110.4         # K (Eq. 24)
@@ -273,7 +276,8 @@ def _primitive_profile(case_cfg, sc, tab, kind, x, y):
         v = (1.0 - H) * v + H * v2
     Yinf = np.array(cfg["Y_inf"], dtype=np.float64)
     Y = np.zeros((tab.ns,) + shape)
-    m = cfg["minor_species"] * 4.0 * f * (1.0 - f) if (cfg["wall"] and kind not in PERFECT_KINDS) else 0.0 * f
+    seeded = cfg["wall"] and kind in (KIND_CNEQ, KIND_FROZEN)
+    m = cfg["minor_species"] * 4.0 * f * (1.0 - f) if seeded else 0.0 * f
     names = [s.name for s in tab.species]
     Y[:] = Yinf.reshape((-1,) + (1,) * len(shape))
     Y[names.index("N2")] = Yinf[names.index("N2")] * (1.0 - m)
@@ -294,6 +298,14 @@ def _conserved_from_primitive(tab, kind, sc, T, p, u, v, Y):
     elif kind == KIND_TPG:
         rho_si = p.ravel() / (sc.R * flatT)
         e_nd = tpg_energy(sc, flatT) / sc.a ** 2
+    elif kind == KIND_LTE:
+        # density from the profile's T and p with the gas constant of the air, then the
+        # equilibrium composition and energy at that (T, rho)
+        rho_si = p.ravel() / (G.mixture_gas_constant(tab, flatY) * flatT)
+        Yeq, e_si, _, _ = G.equilibrium_at(tab, flatT, rho_si, G.element_content(tab, flatY))
+        flatY = Yeq
+        e_nd = e_si / sc.a ** 2
+        Y = Yeq.reshape(Y.shape)
     else:
         rho_si = p.ravel() / (G.mixture_gas_constant(tab, flatY) * flatT)
         e_nd = G.mixture_energy(tab, flatT, flatY) / sc.a ** 2
@@ -372,7 +384,8 @@ def make_case(cfg, tab, noise=None) -> Case:
     T, p, u, v, Y = _primitive_profile(cfg, sc, tab, kind, Xu[:, :1], Yu[:, :1])
     rho_in, rhoY_in, rhoE_in = _conserved_from_primitive(tab, kind, sc, T, p, u, v, Y)
     p_nd = p / (sc.rho * sc.a ** 2)
-    inflow = dict(rho=rho_in[:, 0], Y=Y[:, :, 0], H=((rhoE_in + p_nd) / rho_in)[:, 0])
+    inflow = dict(rho=rho_in[:, 0], Y=(rhoY_in / rho_in)[:, :, 0],
+                  H=((rhoE_in + p_nd) / rho_in)[:, 0])
     sigma = dict(c=sponge(cfg, g, Xc, Yc), xf=sponge(cfg, g, Xu, Yu), yf=sponge(cfg, g, Xv, Yv))
     U_ref = pack(ns, nx, ny, ref)
     U0 = U_ref.copy()
@@ -418,6 +431,13 @@ def closure_nd(case: Case, rho, e, Y):
                    mu=sutherland(T_si) / sc.mu, k=keyes(T_si) / sc.k,
                    D=np.zeros_like(Y1), X=np.zeros_like(Y1), W=np.zeros_like(Y1),
                    a=np.sqrt(gam * p / r1))
+    elif kind == KIND_LTE:
+        bm = G.element_content(tab, np.array(case.cfg["Y_inf"], dtype=np.float64))
+        th = G.lte_eval(tab, r1 * sc.rho, e1 * sc.a ** 2, bm)
+        out = dict(T=th["T"] / sc.T_ref, p=th["p"] / (sc.rho * sc.a ** 2),
+                   h_s=np.zeros_like(Y1), wdot=np.zeros_like(Y1), mu=th["mu"] / sc.mu,
+                   k=th["k"] / sc.k, D=np.zeros_like(Y1), X=th["X"], W=np.zeros_like(Y1),
+                   a=th["a"] / sc.a, cv=th["cv"])
     else:
         th = G.thermo_eval(tab, r1 * sc.rho, e1 * sc.a ** 2, Y1, reactions=(kind == KIND_CNEQ))
         M = tab.M()[:, None]

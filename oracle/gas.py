@@ -430,3 +430,202 @@ def thermo_eval(tab: GasTable, rho, e, Y, T0=None, reactions=True):
     a = np.sqrt(gamma * p / rho)
     return dict(T=T, p=p, cv=cv, R=Rmix, h_s=h_s, wdot=w, X=X, mu=mu, k=k, D=D, a=a,
                 status=status)
+
+
+# ---------------------------------------------------------------------------------------------
+# Local thermodynamic equilibrium (Sec. 2.2.2, special cases): the composition is the one of
+# minimum Gibbs energy for the element content of the mixture, a function of the thermodynamic
+# state alone
+# ---------------------------------------------------------------------------------------------
+
+EQ_MAX_ITER = 100
+EQ_TOL = 1.0e-11            # Newton step in the element potentials that ends the iteration
+EQ_MAX_STEP = 25.0          # largest change of an element potential in one step
+
+
+def element_matrix(tab: GasTable):
+    """a_es: atoms of element e (N, O) in one particle of species s, shape (2, ns)."""
+    return np.array([[s.atoms[e] for s in tab.species] for e in range(2)], dtype=np.float64)
+
+
+def element_content(tab: GasTable, Y):
+    """mol of each element per kg of mixture, b_e = sum_s a_es Y_s / M_s."""
+    Y = np.asarray(Y, dtype=np.float64)
+    M = tab.M().reshape((-1,) + (1,) * (Y.ndim - 1))
+    return np.tensordot(element_matrix(tab), Y / M, axes=1)
+
+
+def equilibrium_concentrations(tab: GasTable, T, b):
+    """Composition of minimum Gibbs energy at temperature T for element totals b (mol/m^3).
+
+    At the constrained minimum of G = sum_s n_s mu_s (element totals fixed) the chemical potential
+    of each species equals the sum of the element potentials of its atoms, mu_s / (R T) =
+    sum_e a_es lambda_e. With the ideal-gas chemical potential
+        mu_s / (R T) = G_s / (R T) + ln(c_s R T / p_std)
+    each concentration is
+        c_s = (p_std / (R T)) exp(a_s . lambda - G_s / (R T)),
+    and lambda follows from the element totals sum_s a_es c_s = b_e, solved by Newton's method on
+    ln(sum_s a_es c_s) - ln b_e. The start is, for each element, the smallest lambda_e at which one
+    species made of that element alone would hold all of it: an upper bound of the solution.
+    T (n,), b (2, n). Returns c (ns, n) in mol/m^3, lambda (2, n) and a convergence mask (n,).
+    """
+    T = np.asarray(T, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    A = element_matrix(tab)
+    g = np.stack([species_gibbs_over_rt(s, T) for s in tab.species])     # (ns, n)
+    lnP = np.log(P_STANDARD / (R_UNIV * T))
+    lam = np.full(b.shape, np.inf)
+    for s in range(tab.ns):
+        for e in range(2):
+            others = [k for k in range(2) if k != e]
+            if A[e, s] > 0 and all(A[k, s] == 0 for k in others):
+                # a_es lambda_e - g_s + ln P = ln(b_e / a_es)
+                lam[e] = np.minimum(lam[e], (np.log(b[e] / A[e, s]) + g[s] - lnP) / A[e, s])
+    n = T.shape[0]
+    active = np.ones(n, dtype=bool)
+    for _ in range(EQ_MAX_ITER):
+        if not active.any():
+            break
+        i = np.nonzero(active)[0]
+        c = np.exp(A.T @ lam[:, i] - g[:, i] + lnP[i])                 # (ns, m)
+        S = A @ c                                                       # (2, m)
+        F = np.log(S) - np.log(b[:, i])
+        J = np.einsum("es,js,sm->mej", A, A, c) / S.T[:, :, None]       # (m, 2, 2)
+        d = -np.linalg.solve(J, F.T[:, :, None])[:, :, 0].T             # (2, m)
+        d = np.clip(d, -EQ_MAX_STEP, EQ_MAX_STEP)
+        lam[:, i] += d
+        active[i[np.max(np.abs(d), axis=0) <= EQ_TOL]] = False
+    c = np.exp(A.T @ lam - g + lnP)
+    return c, lam, ~active
+
+
+def equilibrium_dlnc_dT(tab: GasTable, T, c, hold):
+    """d ln c_s / dT along the equilibrium at fixed density (hold="rho") or at fixed pressure
+    (hold="p"), element ratios fixed.
+
+    Differentiating c_s = (p_std/(R T)) exp(a_s . lambda - G_s/(R T)) with d(G_s/(R T))/dT =
+    -H_s/(R T^2) gives d ln c_s/dT = a_s . lambda' + E_s/(R T^2), E_s = H_s - R T the molar
+    internal energy. At fixed density the element totals stay fixed: sum_s a_es c_s d ln c_s/dT = 0.
+    At fixed pressure they scale by a common factor, sum_s a_es c_s d ln c_s/dT = s' b_e, and the
+    total concentration follows p = c_tot R T: sum_s c_s d ln c_s/dT = -c_tot / T.
+    """
+    T = np.asarray(T, dtype=np.float64)
+    A = element_matrix(tab)
+    E = np.stack([species_molar_enthalpy(s, T) - R_UNIV * T for s in tab.species])
+    eps = E / (R_UNIV * T * T)                                          # (ns, n)
+    n = T.shape[0]
+    b = A @ c
+    if hold == "rho":
+        M = np.einsum("es,js,sn->nej", A, A, c)                         # (n, 2, 2)
+        rhs = -np.einsum("es,sn->ne", A, c * eps)
+        lam_d = np.linalg.solve(M, rhs[:, :, None])[:, :, 0].T          # (2, n)
+    elif hold == "p":
+        M = np.zeros((n, 3, 3))
+        M[:, :2, :2] = np.einsum("es,js,sn->nej", A, A, c)
+        M[:, :2, 2] = -b.T
+        M[:, 2, :2] = (A @ c).T
+        rhs = np.zeros((n, 3))
+        rhs[:, :2] = -np.einsum("es,sn->ne", A, c * eps)
+        rhs[:, 2] = -c.sum(axis=0) / T - np.sum(c * eps, axis=0)
+        lam_d = np.linalg.solve(M, rhs[:, :, None])[:, :2, 0].T
+    else:
+        raise ValueError(hold)
+    return A.T @ lam_d + eps
+
+
+def equilibrium_at(tab: GasTable, T, rho, bm):
+    """Equilibrium mixture at temperature T and density rho (kg/m^3) with element content bm
+    (mol/kg, shape (2,) or (2, n)). Returns Y (ns, n), e (J/kg) and the equilibrium heat capacity
+    c_v,eq = de/dT at fixed rho (J/(kg K))."""
+    T = np.asarray(T, dtype=np.float64)
+    rho = np.asarray(rho, dtype=np.float64)
+    bm = np.asarray(bm, dtype=np.float64)
+    b = (bm if bm.ndim == 2 else bm[:, None]) * rho[None, :]
+    c, _, ok = equilibrium_concentrations(tab, T, b)
+    M = tab.M()[:, None]
+    Y = c * M / rho
+    E = np.stack([species_molar_enthalpy(s, T) - R_UNIV * T for s in tab.species])
+    Cv = np.stack([species_molar_cv(s, T) for s in tab.species])
+    e = np.sum(c * E, axis=0) / rho
+    dlnc = equilibrium_dlnc_dT(tab, T, c, "rho")
+    cv_eq = (np.sum(c * Cv, axis=0) + np.sum(E * c * dlnc, axis=0)) / rho
+    return Y, e, cv_eq, ok
+
+
+def lte_temperature(tab: GasTable, rho, e, bm, T0=None):
+    """Solve e_eq(T; rho) = e for T: the safeguarded Newton iteration of temperature_from_energy
+    with the equilibrium energy and heat capacity at fixed density. Returns (T, status)."""
+    rho = np.asarray(rho, dtype=np.float64)
+    e = np.asarray(e, dtype=np.float64)
+    n = e.shape[0]
+    T = np.full(n, 1000.0) if T0 is None else np.clip(np.asarray(T0, dtype=np.float64), T_MIN, T_MAX)
+    lo = np.full(n, T_MIN)
+    hi = np.full(n, T_MAX)
+    status = np.zeros(n, dtype=np.int32)
+    _, e_lo, _, _ = equilibrium_at(tab, lo, rho, bm)
+    _, e_hi, _, _ = equilibrium_at(tab, hi, rho, bm)
+    below = e <= e_lo
+    above = e >= e_hi
+    status[below | above] |= STATUS_T_CLAMPED
+    active = ~(below | above)
+    T[below] = T_MIN
+    T[above] = T_MAX
+    bm = np.asarray(bm, dtype=np.float64)
+    for _ in range(NEWTON_MAX_ITER):
+        if not active.any():
+            break
+        idx = np.nonzero(active)[0]
+        Ti = T[idx]
+        bi = bm[:, idx] if bm.ndim == 2 else bm
+        _, ei, cvi, ok = equilibrium_at(tab, Ti, rho[idx], bi)
+        status[idx[~ok]] |= STATUS_NOT_CONVERGED
+        f = ei - e[idx]
+        hi[idx] = np.where(f > 0, Ti, hi[idx])
+        lo[idx] = np.where(f <= 0, Ti, lo[idx])
+        Tn = Ti - f / cvi
+        done = np.abs(Tn - Ti) <= NEWTON_RTOL * Ti
+        outside = ~((Tn > lo[idx]) & (Tn < hi[idx]))
+        Tn = np.where(outside & ~done, 0.5 * (lo[idx] + hi[idx]), Tn)
+        T[idx] = Tn
+        active[idx[done]] = False
+    status[active] |= STATUS_NOT_CONVERGED
+    return T, status
+
+
+def lte_eval(tab: GasTable, rho, e, bm, T0=None):
+    """Closure of a mixture in local thermodynamic equilibrium at (rho, e) with element content bm.
+
+    T from the equilibrium energy, the equilibrium composition at (T, rho), p = rho R_mix T, the
+    mixture viscosity and frozen conductivity of that composition (Wilke), and the equilibrium
+    conductivity k = k_frozen + k_reactive. The reactive part is the heat the algebraic
+    diffusion of Eq. (18) carries when the mole fractions follow the equilibrium at the local
+    pressure: with grad X_s = (dX_s/dT)_p grad T the diffusive heat flux sum_s h_s J_s equals
+    -k_reactive grad T,
+        k_reactive = (rho / M_mix) sum_s M_s D_s (dX_s/dT)_p (h_s - h),   h = sum_s Y_s h_s,
+    with D_s of Eq. (19). Returns a dict of SI arrays.
+    """
+    rho = np.asarray(rho, dtype=np.float64)
+    e = np.asarray(e, dtype=np.float64)
+    bm = np.asarray(bm, dtype=np.float64)
+    T, status = lte_temperature(tab, rho, e, bm, T0)
+    status = status | np.where(rho > 0, 0, STATUS_NONPHYSICAL).astype(np.int32)
+    Y, _, cv_eq, _ = equilibrium_at(tab, T, rho, bm)
+    M = tab.M()[:, None]
+    c = rho * Y / M
+    Rmix = mixture_gas_constant(tab, Y)
+    p = rho * Rmix * T
+    cv = mixture_cv(tab, T, Y)
+    X = mole_fractions(tab, Y)
+    mu_s = species_viscosity(tab, T)
+    k_s = species_conductivity(tab, T, mu_s)
+    mu = wilke_mix(tab, X, mu_s, mu_s)
+    k_f = wilke_mix(tab, X, mu_s, k_s)
+    D = averaged_diffusion(tab, X, binary_diffusion(tab, T, p))
+    dX = X * (equilibrium_dlnc_dT(tab, T, c, "p") + 1.0 / T)
+    h_s = enthalpy_species(tab, T)
+    h = np.sum(Y * h_s, axis=0)
+    Mmix = 1.0 / np.sum(Y / M, axis=0)
+    k_r = rho / Mmix * np.sum(M * D * dX * (h_s - h), axis=0)
+    gamma = (cv + Rmix) / cv
+    return dict(T=T, p=p, Y=Y, X=X, dXdT=dX, cv=cv, cv_eq=cv_eq, R=Rmix, mu=mu, k_frozen=k_f,
+                k_reactive=k_r, k=k_f + k_r, D=D, a=np.sqrt(gamma * p / rho), status=status)
