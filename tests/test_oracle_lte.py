@@ -54,6 +54,10 @@ def test_composition_is_the_gibbs_minimum(table, bm):
         X_ref = n / n.sum()
         assert np.allclose(r["X"][:, i], X_ref, rtol=1e-9, atol=1e-13 * X_ref.max()), i
     assert np.allclose(r["Y"].sum(axis=0), 1.0, rtol=0, atol=1e-14)
+    # frozen transport of that composition: the finite-rate closure's at the same state
+    fz = G.thermo_eval(table, rho, G.mixture_energy(table, r["T"], r["Y"]), r["Y"])
+    for key, ref in (("mu", "mu"), ("k_frozen", "k"), ("p", "p"), ("D", "D")):
+        assert np.allclose(r[key], fz[ref], rtol=1e-12, atol=0), key
     assert np.allclose(G.element_content(table, r["Y"]), bm[:, None], rtol=1e-14, atol=0)
 
 
@@ -130,6 +134,8 @@ def test_reactive_conductivity_for_equal_diffusivities(table, bm, monkeypatch):
         expect = rho[i] * D * (cp_eq - cp_f)
         assert abs(r["k_reactive"][i] - expect) < 1e-6 * abs(expect) + 1e-12 * r["k_frozen"][i], i
         assert r["k_reactive"][i] > 0.0
+        # the conductivity the heat flux uses is the frozen one plus that reactive part
+        assert abs(r["k"][i] - (r["k_frozen"][i] + expect)) < 1e-6 * r["k"][i], i
 
 
 def test_cold_limit_is_frozen_air(table, bm):
