@@ -554,7 +554,11 @@ def equilibrium_at(tab: GasTable, T, rho, bm):
 
 def lte_temperature(tab: GasTable, rho, e, bm, T0=None):
     """Solve e_eq(T; rho) = e for T: the safeguarded Newton iteration of temperature_from_energy
-    with the equilibrium energy and heat capacity at fixed density. Returns (T, status)."""
+    with the equilibrium energy and heat capacity at fixed density. The equilibrium energy is
+    S-shaped in T (c_v,eq peaks where a molecule dissociates), where plain Newton steps can cycle
+    between the two shoulders without leaving the bracket; so a Newton step is also replaced by
+    bisection when |f| has not fallen below half the previous step times c_v,eq (the iteration
+    does not contract). Returns (T, status)."""
     rho = np.asarray(rho, dtype=np.float64)
     e = np.asarray(e, dtype=np.float64)
     n = e.shape[0]
@@ -571,6 +575,7 @@ def lte_temperature(tab: GasTable, rho, e, bm, T0=None):
     T[below] = T_MIN
     T[above] = T_MAX
     bm = np.asarray(bm, dtype=np.float64)
+    dx_old = np.full(n, T_MAX - T_MIN)
     for _ in range(NEWTON_MAX_ITER):
         if not active.any():
             break
@@ -585,7 +590,9 @@ def lte_temperature(tab: GasTable, rho, e, bm, T0=None):
         Tn = Ti - f / cvi
         done = np.abs(Tn - Ti) <= NEWTON_RTOL * Ti
         outside = ~((Tn > lo[idx]) & (Tn < hi[idx]))
-        Tn = np.where(outside & ~done, 0.5 * (lo[idx] + hi[idx]), Tn)
+        slow = np.abs(2.0 * f) > np.abs(dx_old[idx] * cvi)
+        Tn = np.where((outside | slow) & ~done, 0.5 * (lo[idx] + hi[idx]), Tn)
+        dx_old[idx] = np.abs(Tn - Ti)
         T[idx] = Tn
         active[idx[done]] = False
     status[active] |= STATUS_NOT_CONVERGED
