@@ -743,6 +743,18 @@ def parity_tolerance(case: Case, U):
         dT_rel = 8.0 * 2.0 ** -53 * scale * case.sc.a ** 2 / (parts["th"]["cv"] * T_si)
         for s in range(1, case.tab.ns):
             tol[f"rs{s}"] += np.max(np.abs(parts["th"]["wdot"][s]) * ta_max / T_si * dT_rel)
+    if case.kind == KIND_LTE:
+        # The reference partial densities of an LTE case are an equilibrium composition,
+        # c_s = (p_std / (R T)) exp(a_s . lambda - G_s / (R T)). Two correct evaluations round
+        # that exponent differently by a few eps times its size (|G_s / (R T)| reaches ~200 for
+        # the atoms near 300 K), which moves each c_s relatively by as much; the sponge term
+        # sigma (Q - Q_ref) carries it into the passive species fields.
+        T_si = parts["T"] * case.sc.T_ref
+        g_max = max(float(np.max(np.abs(G.species_gibbs_over_rt(sp, np.array([T_si.min(), T_si.max()])))))
+                    for sp in case.tab.species)
+        ref = unpack(case.tab.ns, g.nx, g.ny, case.U_ref)
+        for s in range(1, case.tab.ns):
+            tol[f"rs{s}"] += sig_max * 8.0 * 2.0 ** -53 * g_max * np.abs(ref[f"rs{s}"]).max()
     return tol, R
 
 

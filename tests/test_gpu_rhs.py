@@ -36,6 +36,8 @@ def _cases():
         "sbli_tpg_96x40": I.sbli_case(96, 40, seed=5, kind="tpg"),
         "bl_sm_64x40": dict(I.bl_case(64, 40, seed=8), diffusion_model="stefan_maxwell"),
         "sbli_sm_96x40": dict(I.sbli_case(96, 40, seed=9), diffusion_model="stefan_maxwell"),
+        "bl_lte_64x40": I.bl_case(64, 40, seed=10, kind="lte"),
+        "sbli_lte_96x40": I.sbli_case(96, 40, seed=11, kind="lte"),
     }
 
 
