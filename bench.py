@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--ny", type=int, default=256, help="cells in y (profiling of small cases)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
     ap.add_argument("--no-sm", action="store_true", help="skip the Stefan-Maxwell measurement")
+    ap.add_argument("--no-lte", action="store_true", help="skip the LTE measurement")
     ap.add_argument("--serve-requests", type=int, default=48,
                     help="requests of the serving measurement (0 skips it)")
     ap.add_argument("--thermo-states", type=float, default=1e8,
@@ -463,35 +464,44 @@ def ours_arm(args, rank, world, local_rank):
         roof.update(bound="alu", achieved=None, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s", frac=None,
                     traffic=None, note="per-point FP64 count not yet measured for this kernel")
 
-    # ---------------- Stefan-Maxwell diffusion on the same workload ----------------
-    smd = None
-    if not args.no_sm:
-        cfg_sm = dict(cfg, diffusion_model="stefan_maxwell")
-        gas_sm = A.gas_model_load(cfg_sm)
-        U2 = torch.empty(n, dtype=torch.float64, device=dev)
-        dQ2 = torch.empty_like(U2)
-        st2 = A.state_init(gas_sm, cfg_sm, U2, dQ2, I.state_noise(n, cfg["seed"]))
+    # ---------------- model variants on the same workload (FP64, same steps) ----------------
+    def variant(cfg_v):
+        gas_v = A.gas_model_load(cfg_v)
+        Uv = torch.empty(n, dtype=torch.float64, device=dev)
+        dQv = torch.empty_like(Uv)
+        stv = A.state_init(gas_v, cfg_v, Uv, dQv, I.state_noise(n, cfg["seed"]))
         for _ in range(args.warmup):
             for k in range(STAGES):
-                A.rk_stage(st2, k, dt)
+                A.rk_stage(stv, k, dt)
         es = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)]
         barrier()
         for i in range(args.steps):
             es[i][0].record()
             for k in range(STAGES):
-                A.rk_stage(st2, k, dt)
+                A.rk_stage(stv, k, dt)
             es[i][1].record()
             flush.fill_(float(i))
         barrier()
-        s_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in es), world, dev)
-        smd = {"value": job_rate(world, points, args.steps, s_ms), "unit": UNIT,
-               "ms_per_step": s_ms / args.steps,
-               "cost_vs_algebraic": s_ms / max_ms,
-               "status_flags": A.grid_status(st2.grid),
-               "note": "Stefan-Maxwell system (Eq. 17) solved at every face instead of the "
-                       "algebraic model (Eq. 18); same case, FP64"}
-        del st2, U2, dQ2
+        v_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in es), world, dev)
+        out = {"value": job_rate(world, points, args.steps, v_ms), "unit": UNIT,
+               "ms_per_step": v_ms / args.steps, "status_flags": A.grid_status(stv.grid)}
+        del stv, Uv, dQv
+        return out, v_ms
+
+    smd = None
+    if not args.no_sm:
+        smd, s_ms = variant(dict(cfg, diffusion_model="stefan_maxwell"))
+        smd.update(cost_vs_algebraic=s_ms / max_ms,
+                   note="Stefan-Maxwell system (Eq. 17) solved at every face instead of the "
+                        "algebraic model (Eq. 18); same case, FP64")
+    lte = None
+    if not args.no_lte:
+        lte, l_ms = variant(dict(cfg, kind="lte"))
+        lte.update(cost_vs_cneq=l_ms / max_ms,
+                   note="local thermodynamic equilibrium (Sec. 2.2.2): Gibbs-minimum composition "
+                        "and equilibrium conductivity per point, no species equations; same "
+                        "case, FP64")
 
     serving = serving_fp64 = None
     if args.serve_requests > 0:
@@ -524,7 +534,7 @@ def ours_arm(args, rank, world, local_rank):
                               "frac": value / world * RHS_FP64_FLOP_PER_POINT / 1e6 / FP64_PEAK_TFLOPS},
                 "wall_s_timed": t_wall, "status_flags": status, "mixed": mixed,
                 "serving": serving, "serving_fp64": serving_fp64, "stefan_maxwell": smd,
-                "thermo_sweep": sweep,
+                "lte": lte, "thermo_sweep": sweep,
                 "kernels": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1]}}
         print(json.dumps(line), flush=True)
     if world > 1:
