@@ -45,8 +45,14 @@ enum hyp_gas_kind {
     HYP_GAS_CNEQ = 0,    /* finite-rate chemistry with algebraic diffusion (Sec. 2.2.1) */
     HYP_GAS_FROZEN = 1,  /* frozen composition: no reactions, no diffusion (Sec. 2.2.1) */
     HYP_GAS_CPG = 2,     /* calorically perfect gas, Sutherland viscosity (Eqs. 22, 24) */
-    HYP_GAS_TPG = 3      /* thermally perfect gas: c_p(T) of Eq. 23, Sutherland viscosity,
+    HYP_GAS_TPG = 3,     /* thermally perfect gas: c_p(T) of Eq. 23, Sutherland viscosity,
                             Keyes conductivity (Eqs. 22-25) */
+    HYP_GAS_LTE = 4      /* local thermodynamic equilibrium (Sec. 2.2.2, special cases): the
+                            composition of minimum Gibbs energy for the element content of the
+                            freestream Y_inf, found per point from (rho, e); no species equations
+                            (the species fields are carried as passive scalars, unread), heat
+                            flux -k_eq grad T with the equilibrium conductivity (see
+                            hyp_lte_eval) */
 };
 
 /* HYP_FP64: every step in binary64. HYP_MIXED: in binary32 the transport and diffusion
@@ -305,7 +311,8 @@ int hyp_round_f32(int64_t n, const double* x, float* y, double* back, void* stre
  * to its real-gas library, Sec. 3.4). Inputs (DEVICE): rho[n] kg/m^3, e[n] J/kg internal energy
  * including formation enthalpy (298.15 K reference), Y[ns*n] mass fractions species-major
  * (Y[s*n + i]). Outputs (DEVICE, each nullable): T[n] K, p[n] Pa, wdot[ns*n] kg/(m^3 s) (Eq. 15),
- * mu[n] Pa s, k[n] W/(m K) (frozen), D[ns*n] m^2/s (Eq. 19), status[n] HYP_STATUS_* bits. */
+ * mu[n] Pa s, k[n] W/(m K) (frozen), D[ns*n] m^2/s (Eq. 19), status[n] HYP_STATUS_* bits.
+ * HYP_ERR_ARG for an HYP_GAS_LTE gas, whose composition is not an input (hyp_lte_eval). */
 int hyp_thermo_eval(const hyp_gas* gas, int64_t n, const double* rho, const double* e,
                     const double* Y, double* T, double* p, double* wdot, double* mu, double* k,
                     double* D, uint8_t* status, int precision, void* stream);
@@ -313,6 +320,22 @@ int hyp_thermo_eval(const hyp_gas* gas, int64_t n, const double* rho, const doub
 /* Mixture internal energy e = sum_s Y_s e_s(T) (Eq. 12), J/kg. T[n], Y[ns*n], e[n]: DEVICE. */
 int hyp_thermo_energy(const hyp_gas* gas, int64_t n, const double* T, const double* Y, double* e,
                       void* stream);
+
+/* Closure of a mixture in local thermodynamic equilibrium at n states (HYP_GAS_LTE gas only;
+ * Sec. 2.2.2): the temperature from the equilibrium energy at fixed density (safeguarded Newton
+ * iteration, relative step 1e-8, from a tabulated start), the composition of minimum Gibbs energy
+ * at (T, rho) for the element content of the gas's Y_inf (element potentials by Newton's method),
+ * p = rho R_mix T, the Wilke viscosity and frozen conductivity of that composition, and the
+ * equilibrium conductivity k_eq = k_frozen + k_reactive, where k_reactive is the heat the
+ * algebraic diffusion of Eq. (18) carries when the mole fractions follow the equilibrium at the
+ * local pressure: k_reactive = (rho / M_mix) sum_s M_s D_s (dX_s/dT)_p (h_s - h).
+ * rho[n] (kg/m^3), e[n] (J/kg): DEVICE inputs. Outputs, DEVICE, each nullable: T[n] (K), p[n]
+ * (Pa), Y[ns*n] (mass fractions, species-major), mu[n] (Pa s), k[n] (k_eq, W/(m K)),
+ * k_reactive[n], status[n] (HYP_STATUS_* bits). precision: HYP_MIXED takes the transport in
+ * binary32 as hyp_thermo_eval does. HYP_ERR_ARG if the gas is not HYP_GAS_LTE. */
+int hyp_lte_eval(const hyp_gas* gas, int64_t n, const double* rho, const double* e, double* T,
+                 double* p, double* Y, double* mu, double* k, double* k_reactive,
+                 uint8_t* status, int precision, void* stream);
 
 /* hyp_rhs without any device allocation of its own scratch (the paper has no counterpart; this
  * is an interface for callers that may not allocate device memory while they run: work enqueued

@@ -15,7 +15,7 @@ import numpy as np
 from . import build as _build
 
 MAX_SPECIES = 5
-GAS_KINDS = {"cneq": 0, "frozen": 1, "cpg": 2, "tpg": 3}
+GAS_KINDS = {"cneq": 0, "frozen": 1, "cpg": 2, "tpg": 3, "lte": 4}
 STRETCH = {"uniform": 0, "tanh": 1, "cubic": 2}
 FLOWS = {"bl": 0, "sbli": 1}
 DIFFUSION_MODELS = {"ramshaw": 0, "stefan_maxwell": 1}
@@ -85,6 +85,7 @@ EXPORTS = {
     "hyp_rk_stage_scheme": (_I, [_P, _I, _I, _D, _I, _P]),
     "hyp_thermo_eval": (_I, [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I, _P]),
     "hyp_thermo_energy": (_I, [_P, _I64, _P, _P, _P, _P]),
+    "hyp_lte_eval": (_I, [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I, _P]),
     "hyp_rhs_noalloc": (_I, [_P, _P, _P, _P, _P]),
     "hyp_wall_fluxes": (_I, [_P, _P, _P, _P, _P, _I, _P]),
     "hyp_round_f32": (_I, [_I64, _P, _P, _P, _P]),
@@ -428,6 +429,18 @@ def thermo_eval(gas, rho, e, Y, T=None, p=None, wdot=None, mu=None, k=None, D=No
         gas.handle, n, _dptr(rho, n, torch.float64), _dptr(e, n, torch.float64),
         _dptr(Y, ns * n, torch.float64), _dptr(T, n), _dptr(p, n), _dptr(wdot, ns * n),
         _dptr(mu, n), _dptr(k, n), _dptr(D, ns * n),
+        _dptr(status, n, torch.uint8) if status is not None else None, precision,
+        _stream(stream)))
+
+
+def lte_eval(gas, rho, e, T=None, p=None, Y=None, mu=None, k=None, k_reactive=None, status=None,
+             precision=FP64, stream=None):
+    """hyp_lte_eval on device tensors (SI) for an "lte" gas. Y (output) is (ns, n)."""
+    import torch
+    n = rho.numel()
+    _check(lib().hyp_lte_eval(
+        gas.handle, n, _dptr(rho, n, torch.float64), _dptr(e, n, torch.float64), _dptr(T, n),
+        _dptr(p, n), _dptr(Y, gas.ns * n), _dptr(mu, n), _dptr(k, n), _dptr(k_reactive, n),
         _dptr(status, n, torch.uint8) if status is not None else None, precision,
         _stream(stream)))
 

@@ -67,7 +67,7 @@ __device__ __forceinline__ void for_tiles(const BatchItem* __restrict__ items, c
 // The closure touches about sixty fields of its member: the block copies the member's item into
 // shared memory when it moves to a tile of another member, and the body reads the field
 // pointers from there (no aliasing with the global stores, no registers held across the point).
-template <bool MIXED>
+template <bool MIXED, bool LTE>
 __global__ void __launch_bounds__(128) kb_closure(GasDev g, const BatchItem* __restrict__ items,
                                                   BatchDev B) {
     __shared__ BatchItem sh;
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(128) kb_closure(GasDev g, const BatchItem* __r
         }
         const long long lo = (long long)(t - ts[k]) * B.tile;
         const long long hi = min(lo + B.tile, sh.n[SP_NC]);
-        closure_body<MIXED>(g, sh.sc, sh.v, sh.U, sh.s, lo, hi, blockDim.x);
+        closure_body<MIXED, LTE>(g, sh.sc, sh.v, sh.U, sh.s, lo, hi, blockDim.x);
     }
 }
 
@@ -198,7 +198,7 @@ struct hyp_batch {
     size_t cap_items = 0, cap_jobs = 0;
     int ph_start[PH_COUNT] = {}, ph_count[PH_COUNT] = {}, ph_blocks[PH_COUNT] = {};
     int tiles[SP_COUNT] = {};
-    int closure_blocks[2] = {0, 0};
+    int closure_blocks[4] = {0, 0, 0, 0};   // [mixed + 2 lte]: resident blocks of kb_closure
     bool any_sm = false;         // a member uses Stefan-Maxwell diffusion
     int pw_blocks = 0;
     cudaStream_t side = nullptr;
@@ -337,9 +337,15 @@ int launch_step(hyp_batch* b, cudaStream_t s) {
         kb_face_vel<<<grid_for_tiles(b, SP_FACES, pw), 256, 0, s>>>(b->d_items, B);
         HYP_CUDA(cudaEventRecord(b->fork[0], s));
         HYP_CUDA(cudaStreamWaitEvent(s2, b->fork[0], 0));
-        const int cb = grid_for_tiles(b, SP_NC, b->closure_blocks[mixed]);
-        if (mixed) kb_closure<true><<<cb, 128, 0, s>>>(b->table, b->d_items, B);
-        else kb_closure<false><<<cb, 128, 0, s>>>(b->table, b->d_items, B);
+        const int cb = grid_for_tiles(
+            b, SP_NC, b->closure_blocks[mixed + (b->table.kind == HYP_GAS_LTE ? 2 : 0)]);
+        if (b->table.kind == HYP_GAS_LTE) {
+            if (mixed) kb_closure<true, true><<<cb, 128, 0, s>>>(b->table, b->d_items, B);
+            else kb_closure<false, true><<<cb, 128, 0, s>>>(b->table, b->d_items, B);
+        } else {
+            if (mixed) kb_closure<true, false><<<cb, 128, 0, s>>>(b->table, b->d_items, B);
+            else kb_closure<false, false><<<cb, 128, 0, s>>>(b->table, b->d_items, B);
+        }
         kb_set_predict<<<(B.nitems + 127) / 128, 128, 0, s>>>(b->d_items, B.nitems);
         HYP_CUDA(lines(PH_P3, s2));
         HYP_CUDA(lines(PH_AD1, s2));
@@ -393,10 +399,15 @@ extern "C" int hyp_batch_create(int precision, hyp_batch** out) {
     }
     int per_sm = 0;
     const int sms = device_sms();
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb_closure<false>, 128, 0);
-    b->closure_blocks[0] = std::max(1, per_sm * sms);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb_closure<true>, 128, 0);
-    b->closure_blocks[1] = std::max(1, per_sm * sms);
+    {
+        void (*const kern[4])(GasDev, const BatchItem*, BatchDev) = {
+            kb_closure<false, false>, kb_closure<true, false>, kb_closure<false, true>,
+            kb_closure<true, true>};
+        for (int q = 0; q < 4; ++q) {
+            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern[q], 128, 0);
+            b->closure_blocks[q] = std::max(1, per_sm * sms);
+        }
+    }
     b->pw_blocks = sms * 8;
     if (e != cudaSuccess) {
         hyp_batch_free(b);

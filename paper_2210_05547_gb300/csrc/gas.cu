@@ -120,7 +120,7 @@ using namespace hyp::table;
 extern "C" int hyp_gas_model_load(const char* path, int kind, const hyp_freestream* fs,
                                   hyp_gas** out) {
     if (!path || !fs || !out) return fail(HYP_ERR_ARG, "null argument");
-    if (kind < HYP_GAS_CNEQ || kind > HYP_GAS_TPG) return fail(HYP_ERR_ARG, "unknown gas kind");
+    if (kind < HYP_GAS_CNEQ || kind > HYP_GAS_LTE) return fail(HYP_ERR_ARG, "unknown gas kind");
     std::vector<SpeciesRow> sp;
     std::vector<ReactionRow> rx;
     int rc = parse_table(path, sp, rx);
@@ -157,6 +157,11 @@ extern "C" int hyp_gas_model_load(const char* path, int kind, const hyp_freestre
         const double m = r.M / N_A;
         d.A_tr[i] = pow(2.0 * PI * m * K_B / (H_P * H_P), 1.5) / N_A;
         d.inv_sr[i] = r.linear ? 1.0 / (r.sym * r.theta_r) : 0.0;
+        d.lnA_tr[i] = log(d.A_tr[i]);
+        d.ln_isr[i] = r.linear ? -log(r.sym * r.theta_r) : 0.0;
+        d.theta0[i] = r.hf / R_U - h_sens_over_r(r, 298.15);
+        d.atoms[i][0] = r.nN;
+        d.atoms[i][1] = r.nO;
         d.blA[i] = r.bA;
         d.blB[i] = r.bB;
         d.blC[i] = r.bC;
@@ -298,6 +303,19 @@ extern "C" int hyp_gas_model_load(const char* path, int kind, const hyp_freestre
         delete g;
         return fail(HYP_ERR_ARG, "freestream needs T, p, Re > 0 and mass fractions summing to 1");
     }
+    for (int e = 0; e < 2; ++e) {
+        d.elem_b[e] = 0.0;
+        bool pure = false;
+        for (int i = 0; i < NSP; ++i) {
+            d.elem_b[e] += d.atoms[i][e] * Y[i] * d.invM[i];
+            pure = pure || (d.atoms[i][e] > 0 && d.atoms[i][1 - e] == 0);
+        }
+        if (kind == HYP_GAS_LTE && !(pure && d.elem_b[e] > 0.0)) {
+            delete g;
+            return fail(HYP_ERR_ARG, "LTE needs both elements in Y_inf and a species made of each "
+                                     "element alone");
+        }
+    }
     SpeciesState s;
     species_state(d, fs->T_inf, s);
     double cv = 0.0;
@@ -411,6 +429,29 @@ __global__ void __launch_bounds__(128) k_thermo_eval(
     }
 }
 
+template <bool MIXED>
+__global__ void __launch_bounds__(128) k_lte_eval(
+    GasDev g, int64_t n, const double* __restrict__ rho, const double* __restrict__ e,
+    double* __restrict__ T, double* __restrict__ p, double* __restrict__ Y,
+    double* __restrict__ mu, double* __restrict__ kk, double* __restrict__ kr,
+    uint8_t* __restrict__ status) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        ClosureOut o;
+        double y[NSP], k_r;
+        lte_closure<MIXED>(g, rho[i], e[i], temperature_guess(g, e[i], g.Y_inf), y, k_r, o);
+        if (T) T[i] = o.T;
+        if (p) p[i] = o.p;
+        if (mu) mu[i] = o.mu;
+        if (kk) kk[i] = o.k;
+        if (kr) kr[i] = k_r;
+        if (Y)
+#pragma unroll
+            for (int s = 0; s < NSP; ++s) Y[s * n + i] = y[s];
+        if (status) status[i] = (uint8_t)o.status;
+    }
+}
+
 __global__ void k_thermo_energy(GasDev g, int64_t n, const double* __restrict__ T,
                                 const double* __restrict__ Y, double* __restrict__ e) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -440,6 +481,8 @@ extern "C" int hyp_thermo_eval(const hyp_gas* gas, int64_t n, const double* rho,
                                void* stream) {
     if (!gas || n < 0) return fail(HYP_ERR_ARG, "null gas or negative n");
     if (precision != HYP_FP64 && precision != HYP_MIXED) return fail(HYP_ERR_ARG, "unknown precision");
+    if (gas->dev.kind == HYP_GAS_LTE)
+        return fail(HYP_ERR_ARG, "an LTE gas has no independent composition: use hyp_lte_eval");
     if (n == 0) return HYP_OK;
     if (!rho || !e || !Y) return fail(HYP_ERR_ARG, "null input");
     const int block = 128;
@@ -460,6 +503,25 @@ extern "C" int hyp_thermo_energy(const hyp_gas* gas, int64_t n, const double* T,
     if (!T || !Y || !e) return fail(HYP_ERR_ARG, "null pointer");
     const int block = 256;
     k_thermo_energy<<<grid_for(n, block), block, 0, (cudaStream_t)stream>>>(gas->dev, n, T, Y, e);
+    HYP_CUDA(cudaGetLastError());
+    return HYP_OK;
+}
+
+extern "C" int hyp_lte_eval(const hyp_gas* gas, int64_t n, const double* rho, const double* e,
+                            double* T, double* p, double* Y, double* mu, double* k,
+                            double* k_reactive, uint8_t* status, int precision, void* stream) {
+    if (!gas || n < 0) return fail(HYP_ERR_ARG, "null gas or negative n");
+    if (gas->dev.kind != HYP_GAS_LTE) return fail(HYP_ERR_ARG, "hyp_lte_eval needs an LTE gas");
+    if (precision != HYP_FP64 && precision != HYP_MIXED) return fail(HYP_ERR_ARG, "unknown precision");
+    if (n == 0) return HYP_OK;
+    if (!rho || !e) return fail(HYP_ERR_ARG, "null input");
+    const int block = 128;
+    if (precision == HYP_MIXED)
+        k_lte_eval<true><<<grid_for(n, block), block, 0, (cudaStream_t)stream>>>(
+            gas->dev, n, rho, e, T, p, Y, mu, k, k_reactive, status);
+    else
+        k_lte_eval<false><<<grid_for(n, block), block, 0, (cudaStream_t)stream>>>(
+            gas->dev, n, rho, e, T, p, Y, mu, k, k_reactive, status);
     HYP_CUDA(cudaGetLastError());
     return HYP_OK;
 }

@@ -78,6 +78,14 @@ struct GasDev {
     double mach;
     double Y_inf[NSP];
     double tpg_cp0, tpg_theta;   // thermally perfect gas (Eq. 23): c_p0 (J/(kg K)) and Theta (K)
+    // local thermodynamic equilibrium (HYP_GAS_LTE): atoms of N and O per particle, element
+    // content of the freestream air (mol/kg), and the partition-function constants of
+    // c_s = exp(a_s . lambda - theta0_s / T + ln r_s)
+    double atoms[NSP][2];
+    double elem_b[2];
+    double lnA_tr[NSP];          // ln A_tr
+    double ln_isr[NSP];          // ln(1 / (sigma theta_r)) for linear molecules
+    double theta0[NSP];          // E0_s / R_u (K): ground-state energy incl. formation
 };
 
 }  // namespace hyp

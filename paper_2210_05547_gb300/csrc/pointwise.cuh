@@ -14,8 +14,10 @@ __device__ __forceinline__ void atomic_status(unsigned* st, unsigned bits) {
     if (bits) atomicOr(st, bits);
 }
 
-// (A) primitives and the closure at every cell centre (MIXED: binary32 transport, Sec. 2.2)
-template <bool MIXED>
+// (A) primitives and the closure at every cell centre (MIXED: binary32 transport, Sec. 2.2).
+// LTE: the gas is in local thermodynamic equilibrium (its own instantiation, so that the other
+// kinds' code keeps its registers); the species fields are passive and the closure ignores them.
+template <bool MIXED, bool LTE = false>
 __device__ __forceinline__ void closure_body(const GasDev& g, const Scales& sc, const GridView& v,
                                              const double* __restrict__ U, const Scratch& s,
                                              long long lo, long long hi, long long stride) {
@@ -41,7 +43,23 @@ __device__ __forceinline__ void closure_body(const GasDev& g, const Scales& sc, 
         const double e = rhoE * irho - 0.5 * (u * u + vv * vv);
         double T, p, mu, k, a;
         double h[NSP], wd[NSP], X[NSP], W[NSP], Wd[NSP];
-        if (cpg) {
+        if constexpr (LTE) {
+            ClosureOut o;
+            double Yeq[NSP], kr;
+            lte_closure<MIXED>(g, rho * sc.rho_inf, e * sc.a_inf * sc.a_inf, s.Tcache[idx], Yeq, kr, o);
+            atomic_status(v.status, o.status);
+            s.Tcache[idx] = o.T;
+            T = o.T / sc.T_ref;
+            p = o.p / (sc.rho_inf * sc.a_inf * sc.a_inf);
+            mu = o.mu / sc.mu_inf;
+            k = o.k / sc.k_inf;
+            a = o.a / sc.a_inf;
+#pragma unroll
+            for (int sp = 0; sp < NSP; ++sp) {
+                h[sp] = wd[sp] = W[sp] = Wd[sp] = 0.0;
+                X[sp] = o.X[sp];
+            }
+        } else if (cpg) {
             T = sc.gamma_inf * e;
             p = rho * (sc.gamma_inf - 1.0) / sc.gamma_inf * T;
             const double Td = T * sc.T_ref;

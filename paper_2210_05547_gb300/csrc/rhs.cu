@@ -116,7 +116,7 @@ struct Profile {
             v = (1.0 - H) * v + H * v2;
         }
         for (int s = 0; s < NSP; ++s) Y[s] = Yinf[s];
-        const bool seed = c.wall && g.kind != HYP_GAS_CPG && g.kind != HYP_GAS_TPG && iN2 >= 0 && iO2 >= 0 && iNO >= 0 &&
+        const bool seed = c.wall && (g.kind == HYP_GAS_CNEQ || g.kind == HYP_GAS_FROZEN) && iN2 >= 0 && iO2 >= 0 && iNO >= 0 &&
                           iN >= 0 && iO >= 0;
         if (seed) {
             const double m = c.minor_species * 4.0 * f * (1.0 - f);
@@ -139,6 +139,21 @@ struct Profile {
         } else if (g.kind == HYP_GAS_CPG) {
             rho_si = p / (g.R_inf * T);
             e_nd = (T / g.T_ref) / g.gamma_inf;
+        } else if (g.kind == HYP_GAS_LTE) {
+            // density from T and p with the gas constant of Y, then the equilibrium composition
+            // and energy at that (T, rho)
+            double ym = 0.0;
+            for (int s = 0; s < NSP; ++s) ym += Y[s] * g.invM[s];
+            rho_si = p / (R_U * ym * T);
+            const double b[2] = {rho_si * g.elem_b[0], rho_si * g.elem_b[1]};
+            const double lnb[2] = {log(b[0]), log(b[1])};
+            LteState q;
+            lte_at(g, T, rho_si, b, lnb, false, q);
+            e_nd = q.e / (g.a_inf * g.a_inf);
+            rho = rho_si / g.rho_inf;
+            for (int s = 0; s < NSP; ++s) rhoY[s] = rho * (q.c[s] * g.M[s] / rho_si);
+            rhoE = rho * (e_nd + 0.5 * (u * u + v * v));
+            return;
         } else {
             double ym = 0.0;
             for (int s = 0; s < NSP; ++s) ym += Y[s] * g.invM[s];
@@ -375,10 +390,22 @@ enum OpId { OX_ICF, OX_DCF, OX_IFC, OX_DFC, OY_ICF, OY_DCF, OY_IFC, OY_DFC, OY_I
 // Single-grid kernels: grid-stride loops over the bodies of pointwise.cuh.
 #define GRID_RANGE(n) (long long)blockIdx.x * blockDim.x, (long long)(n), (long long)gridDim.x * blockDim.x
 
-template <bool MIXED>
+template <bool MIXED, bool LTE>
 __global__ void __launch_bounds__(128) k_closure(GasDev g, Scales sc, GridView v,
                                                  const double* __restrict__ U, Scratch s) {
-    closure_body<MIXED>(g, sc, v, U, s, GRID_RANGE((long long)v.nx * v.ny));
+    closure_body<MIXED, LTE>(g, sc, v, U, s, GRID_RANGE((long long)v.nx * v.ny));
+}
+
+// the closure kernel for the gas kind and precision
+static void launch_closure(const GasDev& g, const Scales& sc, const GridView& v, const double* U,
+                           const Scratch& S, bool mixed, int blocks, cudaStream_t s) {
+    if (g.kind == HYP_GAS_LTE) {
+        if (mixed) k_closure<true, true><<<blocks, 128, 0, s>>>(g, sc, v, U, S);
+        else k_closure<false, true><<<blocks, 128, 0, s>>>(g, sc, v, U, S);
+    } else {
+        if (mixed) k_closure<true, false><<<blocks, 128, 0, s>>>(g, sc, v, U, S);
+        else k_closure<false, false><<<blocks, 128, 0, s>>>(g, sc, v, U, S);
+    }
 }
 
 __global__ void k_face_vel(GridView v, const double* __restrict__ U, Scratch s) {
@@ -935,9 +962,12 @@ extern "C" int hyp_state_init(const hyp_gas* gas, const hyp_grid_desc* desc, con
         int dev = 0, sms = 0, per_sm = 0;
         HYP_CUDA(cudaGetDevice(&dev));
         HYP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        HYP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_closure<false>, 128, 0));
+        const bool lte = gas->dev.kind == HYP_GAS_LTE;
+        HYP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, lte ? k_closure<false, true> : k_closure<false, false>, 128, 0));
         G->closure_blocks = std::max(1, per_sm * sms);
-        HYP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_closure<true>, 128, 0));
+        HYP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, lte ? k_closure<true, true> : k_closure<true, false>, 128, 0));
         G->closure_blocks_mixed = std::max(1, per_sm * sms);
     }
     HYP_CUDA(cudaGetLastError());
@@ -1031,8 +1061,7 @@ static int run_rhs(const hyp_gas* gas, hyp_grid* G, const double* U, double* dUd
     const int cb = (int)std::min<long long>(mixed ? G->closure_blocks_mixed : G->closure_blocks,
                                             (nc + 127) / 128);
     const Scales sc = scales_of(g);
-    if (mixed) TIMED(KID_CLOSURE, (k_closure<true><<<cb, 128, 0, s>>>(g, sc, v, U, S)));
-    else TIMED(KID_CLOSURE, (k_closure<false><<<cb, 128, 0, s>>>(g, sc, v, U, S)));
+    TIMED(KID_CLOSURE, launch_closure(g, sc, v, U, S, mixed, cb, s));
     HYP_CUDA(cudaGetLastError());
     G->cache_valid = 1;
     TIMED_ON(s2, KID_LINES_VELGRAD, e1 = launch_lines(G->jobs + G->ph_start[PH_P3], G->ph_count[PH_P3],
@@ -1332,7 +1361,7 @@ extern "C" int hyp_rhs_noalloc(const hyp_gas* gas, const hyp_grid* grid, const d
     };
     HYP_CUDA(lines(PH_P1, G->ph_count[PH_P1]));
     k_face_vel<<<blocks_for(d.size(NXF) + d.size(NYF), 256), 256, 0, s>>>(v, U, S);
-    k_closure<false><<<blocks_for(nc, 128), 128, 0, s>>>(g, scales_of(g), v, U, S);
+    launch_closure(g, scales_of(g), v, U, S, false, (int)blocks_for(nc, 128), s);
     HYP_CUDA(cudaGetLastError());
     HYP_CUDA(lines(PH_P3, G->ph_count[PH_P3]));
     if (v.ad) {

@@ -578,5 +578,247 @@ __device__ inline void stefan_maxwell_face(const GasDev& g, double Tsi, double p
     }
 }
 
-}  // namespace hyp
+// ---- local thermodynamic equilibrium (HYP_GAS_LTE; Sec. 2.2.2, special cases) ----
+// The composition is the one of minimum Gibbs energy for the element content of the air. At that
+// minimum the chemical potential of each species is the sum of its atoms' element potentials
+// lambda_e (units of R T); with the molar partition function r_s of the closure (translation per
+// unit volume, rotation, vibration, electronic levels) and the ground-state energy R theta0_s,
+// the ideal-gas chemical potential gives
+//     c_s = exp(a_s . lambda - gam_s),   gam_s = theta0_s / T - ln r_s        (mol/m^3),
+// and lambda follows from the element totals sum_s a_es c_s = b_e (Newton on ln of the sums).
+constexpr int EQ_MAXIT = 100;
+constexpr double EQ_TOL = 1.0e-11;        // element-potential step that ends the iteration
+constexpr double EQ_MAX_STEP = 25.0;      // largest change of an element potential in one step
 
+__host__ __device__ inline void lte_gammas(const GasDev& g, double T, double lnT,
+                                           const SpeciesState& s, double* gam) {
+    const double invT = 1.0 / T;
+#pragma unroll
+    for (int i = 0; i < NSP; ++i) {
+        double lr = g.lnA_tr[i] + 1.5 * lnT + log(s.qel[i]);
+        if (g.linear[i]) lr += lnT + g.ln_isr[i] + log1p(s.iem1[i]);
+        gam[i] = g.theta0[i] * invT - lr;
+    }
+}
+
+// Element potentials for element totals b (mol/m^3, lnb = ln b). warm: start from lam; else from
+// the smallest value at which one species made of that element alone would hold all of it (an
+// upper bound of the solution). c receives the concentrations at the returned lam.
+__host__ __device__ inline bool lte_solve(const GasDev& g, const double* gam, const double* b,
+                                          const double* lnb, bool warm, double* lam, double* c) {
+    if (!warm) {
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            double best = HUGE_VAL;
+#pragma unroll
+            for (int i = 0; i < NSP; ++i) {
+                const double a = g.atoms[i][e], o = g.atoms[i][1 - e];
+                if (a > 0.0 && o == 0.0) best = fmin(best, (lnb[e] - log(a) + gam[i]) / a);
+            }
+            lam[e] = best;
+        }
+    }
+    for (int it = 0; it < EQ_MAXIT; ++it) {
+        double S0 = 0.0, S1 = 0.0, J00 = 0.0, J01 = 0.0, J11 = 0.0;
+#pragma unroll
+        for (int i = 0; i < NSP; ++i) {
+            const double a0 = g.atoms[i][0], a1 = g.atoms[i][1];
+            const double ci = exp(a0 * lam[0] + a1 * lam[1] - gam[i]);
+            S0 += a0 * ci;
+            S1 += a1 * ci;
+            J00 += a0 * a0 * ci;
+            J01 += a0 * a1 * ci;
+            J11 += a1 * a1 * ci;
+        }
+        // rows of the Jacobian of ln S_e: (sum_s a_es a_js c_s) / S_e
+        const double F0 = log(S0) - lnb[0], F1 = log(S1) - lnb[1];
+        const double j00 = J00 / S0, j01 = J01 / S0, j10 = J01 / S1, j11 = J11 / S1;
+        const double idet = 1.0 / (j00 * j11 - j01 * j10);
+        double d0 = -(F0 * j11 - F1 * j01) * idet;
+        double d1 = -(F1 * j00 - F0 * j10) * idet;
+        d0 = fmin(fmax(d0, -EQ_MAX_STEP), EQ_MAX_STEP);
+        d1 = fmin(fmax(d1, -EQ_MAX_STEP), EQ_MAX_STEP);
+        lam[0] += d0;
+        lam[1] += d1;
+        if (fmax(fabs(d0), fabs(d1)) <= EQ_TOL) {
+#pragma unroll
+            for (int i = 0; i < NSP; ++i)
+                c[i] = exp(g.atoms[i][0] * lam[0] + g.atoms[i][1] * lam[1] - gam[i]);
+            return true;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < NSP; ++i) c[i] = exp(g.atoms[i][0] * lam[0] + g.atoms[i][1] * lam[1] - gam[i]);
+    return false;
+}
+
+// Equilibrium at (T, rho): species state, concentrations and the temperature derivatives along
+// the equilibrium at fixed density, d ln c_s/dT = a_s . lambda'_rho + eps_s with eps_s =
+// E_s / (R T^2) (E_s the molar internal energy) and sum_s a_es c_s d ln c_s/dT = 0.
+struct LteState {
+    SpeciesState s;
+    double c[NSP];       // mol/m^3
+    double lam[2];
+    double eps[NSP];     // E_s / (R T^2)
+    double dlnc[NSP];    // d ln c_s / dT at fixed density
+    double H[3];         // sum_s c_s a_s a_s^T: (0,0), (0,1), (1,1)
+    double e, cv_eq;     // J/kg, de/dT at fixed density
+    bool ok;
+};
+
+__host__ __device__ inline void lte_at(const GasDev& g, double T, double rho, const double* b,
+                                       const double* lnb, bool warm, LteState& q) {
+    species_state(g, T, q.s);
+    const double lnT = log(T);
+    double gam[NSP];
+    lte_gammas(g, T, lnT, q.s, gam);
+    q.ok = lte_solve(g, gam, b, lnb, warm, q.lam, q.c);
+    const double iRT2 = 1.0 / (R_U * T * T);
+    double H00 = 0.0, H01 = 0.0, H11 = 0.0, r0 = 0.0, r1 = 0.0;
+#pragma unroll
+    for (int i = 0; i < NSP; ++i) {
+        const double a0 = g.atoms[i][0], a1 = g.atoms[i][1], ci = q.c[i];
+        q.eps[i] = g.M[i] * q.s.e[i] * iRT2;
+        H00 += a0 * a0 * ci;
+        H01 += a0 * a1 * ci;
+        H11 += a1 * a1 * ci;
+        r0 -= a0 * ci * q.eps[i];
+        r1 -= a1 * ci * q.eps[i];
+    }
+    q.H[0] = H00;
+    q.H[1] = H01;
+    q.H[2] = H11;
+    const double idet = 1.0 / (H00 * H11 - H01 * H01);
+    const double l0 = (r0 * H11 - r1 * H01) * idet, l1 = (r1 * H00 - r0 * H01) * idet;
+    double ce = 0.0, ccv = 0.0, cedl = 0.0;
+#pragma unroll
+    for (int i = 0; i < NSP; ++i) {
+        q.dlnc[i] = g.atoms[i][0] * l0 + g.atoms[i][1] * l1 + q.eps[i];
+        const double Ei = g.M[i] * q.s.e[i];
+        ce += q.c[i] * Ei;
+        ccv += q.c[i] * g.M[i] * q.s.cv[i];
+        cedl += q.c[i] * Ei * q.dlnc[i];
+    }
+    const double irho = 1.0 / rho;
+    q.e = ce * irho;
+    q.cv_eq = (ccv + cedl) * irho;
+}
+
+// Closure in local thermodynamic equilibrium at (rho, e) (SI), from the temperature T0. T from
+// the safeguarded Newton iteration of temperature_from_energy on the equilibrium energy at fixed
+// density, which also bisects when the iteration does not contract; then the equilibrium composition at T, p = rho R_mix T, the frozen transport of that
+// composition and the equilibrium conductivity k = k_frozen + k_reactive,
+//     k_reactive = (rho / M_mix) sum_s M_s D_s (dX_s/dT)_p (h_s - h),   h = sum_s Y_s h_s,
+// the heat carried by the algebraic diffusion of Eq. (18) when the mole fractions follow the
+// equilibrium at the local pressure. (dX_s/dT)_p: at fixed pressure the element totals scale by
+// a common factor s' (d ln c_s/dT = d ln c_s/dT|_rho + s' a_s . H^-1 b) fixed by
+// sum_s c_s d ln c_s/dT = -c_tot / T; X_s' = X_s (d ln c_s/dT + 1/T). Yout receives the mass
+// fractions, o.X the mole fractions, o.D the averaged diffusion coefficients of the composition,
+// o.k the equilibrium conductivity; o.h and o.wdot are zero.
+template <bool MIXED>
+__host__ __device__ inline void lte_closure(const GasDev& g, double rho, double e, double T0,
+                                            double* Yout, double& k_reactive, ClosureOut& o) {
+    o.status = rho > 0.0 ? 0u : HYP_STATUS_NONPHYSICAL;
+    const double b[2] = {rho * g.elem_b[0], rho * g.elem_b[1]};
+    const double lnb[2] = {log(b[0]), log(b[1])};
+    LteState q;
+    double T = fmin(fmax(T0, T_LO), T_HI);
+    double lo = T_LO, hi = T_HI, dx_old = T_HI - T_LO;
+    bool warm = false, conv = false;
+    for (int it = 0; it < NEWTON_MAXIT; ++it) {
+        lte_at(g, T, rho, b, lnb, warm, q);
+        warm = true;
+        if (!q.ok) o.status |= HYP_STATUS_NOT_CONVERGED;
+        const double f = q.e - e;
+        if (f > 0.0) hi = T; else lo = T;
+        double Tn = T - f / q.cv_eq;
+        if (fabs(Tn - T) <= NEWTON_RTOL * T) {
+            T = Tn;
+            conv = true;
+            break;
+        }
+        // e_eq(T) is S-shaped (c_v,eq peaks where a molecule dissociates): bisect when the step
+        // leaves the bracket or the iteration does not contract, |f| > |dx_old c_v,eq| / 2
+        if (!(Tn > lo && Tn < hi) || fabs(2.0 * f) > fabs(dx_old * q.cv_eq)) Tn = 0.5 * (lo + hi);
+        dx_old = fabs(Tn - T);
+        T = Tn;
+    }
+    if (!conv) {
+        LteState qe;
+        lte_at(g, T_LO, rho, b, lnb, false, qe);
+        if (e <= qe.e) {
+            T = T_LO;
+            o.status |= HYP_STATUS_T_CLAMPED;
+        } else {
+            lte_at(g, T_HI, rho, b, lnb, false, qe);
+            if (e >= qe.e) {
+                T = T_HI;
+                o.status |= HYP_STATUS_T_CLAMPED;
+            } else {
+                o.status |= HYP_STATUS_NOT_CONVERGED;
+            }
+        }
+        warm = false;
+    }
+    lte_at(g, T, rho, b, lnb, warm, q);
+    if (!q.ok) o.status |= HYP_STATUS_NOT_CONVERGED;
+
+    double ctot = 0.0, cv = 0.0;
+#pragma unroll
+    for (int i = 0; i < NSP; ++i) ctot += q.c[i];
+    const double irho = 1.0 / rho, ict = 1.0 / ctot;
+#pragma unroll
+    for (int i = 0; i < NSP; ++i) {
+        Yout[i] = q.c[i] * g.M[i] * irho;
+        o.X[i] = q.c[i] * ict;
+        cv += Yout[i] * q.s.cv[i];
+        o.h[i] = 0.0;
+        o.wdot[i] = 0.0;
+        o.es[i] = q.s.e[i];
+        o.cvs[i] = q.s.cv[i];
+        o.cvps[i] = q.s.cvp[i];
+    }
+    const double Rmix = R_U * ctot * irho;
+    const double p = rho * Rmix * T;
+    o.T = T;
+    o.p = p;
+    o.cv = cv;
+    o.Rmix = Rmix;
+    o.a = sqrt((cv + Rmix) / cv * p * irho);
+    const double lnT = log(T);
+    if constexpr (MIXED) {
+#ifdef __CUDA_ARCH__
+        transport_f32(g, T, lnT, p, q.s, true, o);
+#endif
+    } else {
+        transport_f64(g, T, lnT, p, q.s, true, o);
+    }
+
+    // (dX_s/dT)_p with u = H^-1 b
+    const double idet = 1.0 / (q.H[0] * q.H[2] - q.H[1] * q.H[1]);
+    const double u0 = (b[0] * q.H[2] - b[1] * q.H[1]) * idet;
+    const double u1 = (b[1] * q.H[0] - b[0] * q.H[1]) * idet;
+    double cdl = 0.0;
+#pragma unroll
+    for (int i = 0; i < NSP; ++i) cdl += q.c[i] * q.dlnc[i];
+    const double sp = (-ctot / T - cdl) / (b[0] * u0 + b[1] * u1);
+    double h = 0.0;
+    double hs[NSP];
+#pragma unroll
+    for (int i = 0; i < NSP; ++i) {
+        hs[i] = q.s.e[i] + g.Rs[i] * T;
+        h += Yout[i] * hs[i];
+    }
+    double kr = 0.0;
+    const double invT = 1.0 / T;
+#pragma unroll
+    for (int i = 0; i < NSP; ++i) {
+        const double dlp = q.dlnc[i] + sp * (g.atoms[i][0] * u0 + g.atoms[i][1] * u1);
+        const double dX = o.X[i] * (dlp + invT);
+        kr += g.M[i] * o.D[i] * dX * (hs[i] - h);
+    }
+    k_reactive = ctot * kr;
+    o.k += k_reactive;
+}
+
+}  // namespace hyp

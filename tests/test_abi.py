@@ -34,7 +34,7 @@ def test_exports_every_declared_symbol(A):
 
 @pytest.mark.parametrize("maker,kind", [(I.bl_case, "cneq"), (I.sbli_case, "cneq"),
                                         (I.bl_case, "frozen"), (I.bl_case, "cpg"),
-                                        (I.sbli_case, "tpg")])
+                                        (I.sbli_case, "tpg"), (I.sbli_case, "lte")])
 def test_freestream_scales_match_oracle(A, table, maker, kind):
     cfg = maker(kind=kind)
     g = A.gas_model_load(cfg)
@@ -74,3 +74,5 @@ def test_argument_errors(A):
     bad_fs = dict(cfg, Y_inf=(0.5, 0.2, 0.0, 0.0, 0.0))
     with pytest.raises(A.HypError, match="mass fractions"):
         A.gas_model_load(bad_fs)
+    with pytest.raises(A.HypError, match="LTE needs both elements"):
+        A.gas_model_load(dict(cfg, Y_inf=(1.0, 0.0, 0.0, 0.0, 0.0)), kind="lte")
