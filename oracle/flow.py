@@ -362,6 +362,10 @@ def sponge(cfg, grid, x, y):
 
 def make_case(cfg, tab, noise=None) -> Case:
     kind = cfg["kind"]
+    if kind == KIND_LTE and tab.electron() is not None:
+        raise ValueError("the LTE closure conserves N and O only: no charged species")
+    if len(cfg["Y_inf"]) != tab.ns:
+        raise ValueError("Y_inf must list one mass fraction per species of the table")
     sc = freestream_scales(tab, kind, cfg)
     g = make_grid(cfg)
     nx, ny, ns = g.nx, g.ny, tab.ns
@@ -507,6 +511,26 @@ def _sm_face_fluxes(case, rho_f, Y_f, dX_f, T_f, p_f):
 # Artificial diffusivity helpers (Sec. 3.3)
 # ---------------------------------------------------------------------------------------------
 
+def zero_current(tab, J):
+    """Charged mixtures (reading; the paper treats neutral air only): the electrons diffuse with
+    the ions, so the conduction current vanishes, J_e = M_e sum_ions J_i / M_i, and the omitted
+    first species takes J_0 = -sum_{s >= 1} J_s so that the diffusive mass fluxes still sum to
+    zero. J: (ns, ...) fluxes of Eq. (18) with ambipolar ion coefficients."""
+    ie = tab.electron()
+    M = tab.M()
+    J = np.array(J, dtype=np.float64, copy=True)
+    acc = np.zeros_like(J[0])
+    for i in range(tab.ns):
+        if tab.species[i].charge > 0:
+            acc = acc + J[i] / M[i]
+    J[ie] = M[ie] * acc
+    tot = np.zeros_like(J[0])
+    for i in range(1, tab.ns):
+        tot = tot + J[i]
+    J[0] = -tot
+    return J
+
+
 def delta4(f, axis):
     """Fourth index difference (1, -4, 6, -4, 1); the two rows nearest each end reuse the
     stencil centred on the nearest row where it fits."""
@@ -604,11 +628,16 @@ def rhs(case: Case, U, return_parts=False):
         D_st = np.zeros_like(Y)
     if case.kind != KIND_CNEQ:
         D_st = np.zeros_like(Y)
+    ie = tab.electron()
+    if ie is not None:
+        D_st[ie] = 0.0          # the electron flux follows the ions (zero_current)
 
     # (E) transport coefficients (viscous scale 1/Re, conduction 1/(Re Pr Ec), diffusion 1/Re)
     mu_e = th["mu"] / Re + mu_st
     K = th["k"] / (Re * Pr) + kap_st
     sm = case.kind == KIND_CNEQ and cfg.get("diffusion_model", DIFF_RAMSHAW) == DIFF_SM
+    if sm and ie is not None:
+        raise ValueError("Stefan-Maxwell diffusion is not defined here for charged mixtures")
     # with Stefan-Maxwell diffusion the algebraic form keeps only the artificial diffusivity
     Gd = th["W"] * ((0.0 if sm else th["D"] / Re) + D_st)
 
@@ -633,6 +662,8 @@ def rhs(case: Case, U, return_parts=False):
     Jx = -(Gx * dXdx - Yx * sumx)                            # Eq. (18), gradient of X (Eq. 16)
     if sm:
         Jx = Jx + _sm_face_fluxes(case, rho_xf, Yx, dXdx, C.icf(T, 1), C.icf(p, 1))
+    if ie is not None:
+        Jx = zero_current(tab, Jx)
     Fsx = [rhou * Yx[s] + Jx[s] for s in range(ns)]
     qx = -Kx * dTdx + np.sum(hx * Jx, axis=0)                # Eq. (10)
     FEx = rhou * Hx + qx - (txx_x * u_xf + txy_x * v_x)
@@ -653,6 +684,8 @@ def rhs(case: Case, U, return_parts=False):
     Jy = -(Gy * dXdy - Yy * sumy)
     if sm:
         Jy = Jy + _sm_face_fluxes(case, rho_yf, Yy, dXdy, C.icf(T, 0), C.icf(p, 0))
+    if ie is not None:
+        Jy = zero_current(tab, Jy)
     if wall:
         Jy[:, 0, :] = 0.0
     Fsy = [rhov * Yy[s] + Jy[s] for s in range(ns)]

@@ -62,6 +62,7 @@ class Species:
     lj_eps: float         # K
     atoms: tuple          # (N, O)
     levels: list = dataclasses.field(default_factory=list)   # [(g, theta_el)]
+    charge: int = 0       # elementary charges (+1 ions, -1 the electron)
 
 
 @dataclasses.dataclass
@@ -85,6 +86,22 @@ class GasTable:
     def M(self):
         return np.array([s.M for s in self.species])
 
+    def charge(self):
+        return np.array([s.charge for s in self.species], dtype=np.float64)
+
+    def heavy(self):
+        """Species that take part in the mixing rules and the binary diffusion pairs: all but
+        the electron (it has no Blottner or Lennard-Jones data; its diffusive flux follows from
+        zero conduction current)."""
+        return np.array([s.charge >= 0 for s in self.species])
+
+    def electron(self):
+        """Index of the electron, or None."""
+        for i, s in enumerate(self.species):
+            if s.charge < 0:
+                return i
+        return None
+
 
 def load_table(path) -> GasTable:
     """Parse the plain-text gas table (SPECIES / LEVEL / REACTION lines)."""
@@ -100,7 +117,8 @@ def load_table(path) -> GasTable:
                 species.append(Species(name=tok[1], M=v[0], hf298=v[1], linear=int(v[2]),
                                        theta_v=v[3], theta_r=v[4], symmetry=v[5],
                                        blottner=(v[6], v[7], v[8]), lj_sigma=v[9], lj_eps=v[10],
-                                       atoms=(int(v[11]), int(v[12]))))
+                                       atoms=(int(v[11]), int(v[12])),
+                                       charge=int(v[13]) if len(v) > 13 else 0))
             elif tok[0] == 'LEVEL':
                 sp = next(s for s in species if s.name == tok[1])
                 sp.levels.append((float(tok[2]), float(tok[3])))
@@ -350,13 +368,14 @@ def mole_fractions(tab: GasTable, Y):
 
 def wilke_mix(tab: GasTable, X, mu_s, prop_s):
     """Wilke's rule: prop = sum_s X_s prop_s / phi_s,
-    phi_s = sum_r X_r [1 + sqrt(mu_s/mu_r) (M_r/M_s)^(1/4)]^2 / sqrt(8 (1 + M_s/M_r))."""
+    phi_s = sum_r X_r [1 + sqrt(mu_s/mu_r) (M_r/M_s)^(1/4)]^2 / sqrt(8 (1 + M_s/M_r)),
+    both sums over the heavy species."""
     M = tab.M()
-    ns = tab.ns
+    heavy = [s for s in range(tab.ns) if tab.heavy()[s]]
     out = np.zeros_like(X[0])
-    for s in range(ns):
+    for s in heavy:
         phi = np.zeros_like(X[0])
-        for r in range(ns):
+        for r in heavy:
             num = (1.0 + np.sqrt(mu_s[s] / mu_s[r]) * (M[r] / M[s]) ** 0.25) ** 2
             phi += X[r] * num / np.sqrt(8.0 * (1.0 + M[s] / M[r]))
         out += X[s] * prop_s[s] / phi
@@ -372,11 +391,15 @@ def collision_integral_diffusion(Tstar):
 def binary_diffusion(tab: GasTable, T, p):
     """Chapman-Enskog first approximation:
     D_sr = (3/16) sqrt(2 pi (k T)^3 / m_sr) / (p pi sigma_sr^2 Omega(T*)),
-    m_sr the reduced mass, sigma_sr the mean diameter, T* = T / sqrt(eps_s eps_r)."""
+    m_sr the reduced mass, sigma_sr the mean diameter, T* = T / sqrt(eps_s eps_r). Pairs with
+    the electron are not formed (infinite here: they drop out of Eq. 19)."""
     ns = tab.ns
-    D = np.zeros((ns, ns) + np.shape(T))
+    heavy = tab.heavy()
+    D = np.full((ns, ns) + np.shape(T), np.inf)
     for s in range(ns):
         for r in range(ns):
+            if not (heavy[s] and heavy[r]):
+                continue
             a, b = tab.species[s], tab.species[r]
             m_sr = (a.M * b.M / (a.M + b.M)) / N_AVOGADRO
             sigma = 0.5 * (a.lj_sigma + b.lj_sigma) * 1.0e-10
@@ -387,16 +410,23 @@ def binary_diffusion(tab: GasTable, T, p):
 
 
 def averaged_diffusion(tab: GasTable, X, Dbin):
-    """D_s = (1 - X_s) / sum_{r != s} X_r / D_sr (Eq. 19); 0 where the sum vanishes."""
+    """D_s = (1 - X_s) / sum_{r != s} X_r / D_sr (Eq. 19) over the heavy species; 0 where the
+    sum vanishes. Ions diffuse ambipolarly, with twice that coefficient (electrons and ions at
+    one temperature); the electron's entry is 0 (its flux follows from zero current)."""
     ns = tab.ns
+    heavy = tab.heavy()
     out = np.zeros_like(X)
     for s in range(ns):
+        if not heavy[s]:
+            continue
         den = np.zeros_like(X[0])
         for r in range(ns):
-            if r != s:
+            if r != s and heavy[r]:
                 den += X[r] / Dbin[s, r]
         safe = np.where(den != 0.0, den, 1.0)
         out[s] = np.where(den != 0.0, (1.0 - X[s]) / safe, 0.0)
+        if tab.species[s].charge > 0:
+            out[s] = 2.0 * out[s]
     return out
 
 

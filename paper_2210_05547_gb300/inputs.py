@@ -18,13 +18,17 @@ Workloads (shapes follow the paper's cases; there is no dataset):
   with wall temperature 300-1500 K, interactions at the Mach and deflection their seed draws,
   seeded step counts and unit-rate exponential inter-arrival gaps (scaled by the caller).
 * ``thermo_states`` -- independent thermochemical states: T log-uniform in [300, 15000] K,
-  rho log-uniform in [1e-4, 1] kg/m^3, mass fractions Dirichlet(1).
+  rho log-uniform in [1e-4, 1] kg/m^3, mass fractions Dirichlet(1); ``charged_states`` the same
+  for a table with ions and electrons, Dirichlet(1) over the heavy species and the electrons that
+  make each state neutral.
+* ``with_species`` -- any case on the eleven-species table (ions and electrons start at zero).
 """
 from __future__ import annotations
 
 import numpy as np
 
 AIR_Y = (0.767, 0.233, 0.0, 0.0, 0.0)      # N2, O2, NO, N, O
+TABLE_SPECIES = {"air5": 5, "air11": 11}
 
 
 def bl_case(nx=256, ny=64, seed=0, kind="cneq"):
@@ -37,7 +41,7 @@ def bl_case(nx=256, ny=64, seed=0, kind="cneq"):
         shock_deflection_deg=0.0, shock_x=0.0, shock_width=0.0,
         sponge_sigma=200.0, sponge_in=5.0, sponge_out=15.0, sponge_top_cells=max(2, (26 * ny) // 211),
         artificial_diffusivity=0, C_mu=0.002, C_beta=1.75, C_kappa=0.01, C_D=0.0,
-        noise_amp=1.0e-4, dt=2.0e-4, filter_sigma=0.0, diffusion_model="ramshaw",
+        noise_amp=1.0e-4, dt=2.0e-4, filter_sigma=0.0, diffusion_model="ramshaw", table="air5",
     )
 
 
@@ -54,8 +58,18 @@ def sbli_case(nx=2048, ny=256, seed=0, kind="cneq"):
         shock_deflection_deg=deflection, shock_x=120.0, shock_width=1.0,
         sponge_sigma=200.0, sponge_in=10.0, sponge_out=30.0, sponge_top_cells=max(2, (26 * ny) // 211),
         artificial_diffusivity=1, C_mu=0.002, C_beta=1.75, C_kappa=0.01, C_D=0.01,
-        noise_amp=1.0e-4, dt=2.0e-3, filter_sigma=0.05, diffusion_model="ramshaw",
+        noise_amp=1.0e-4, dt=2.0e-3, filter_sigma=0.05, diffusion_model="ramshaw", table="air5",
     )
+
+
+def with_species(cfg, table="air11"):
+    """The case on another gas table: the freestream mass fractions padded with zeros (the extra
+    species of air11 are the ions and the electron)."""
+    ns = TABLE_SPECIES[table]
+    c = dict(cfg)
+    c.update(table=table, Y_inf=tuple(cfg["Y_inf"]) + (0.0,) * (ns - len(cfg["Y_inf"])),
+             name=f"{cfg['name']}_{table}")
+    return c
 
 
 def box_case(nx=32, ny=24, seed=0, kind="cneq"):
@@ -96,4 +110,24 @@ def thermo_states(n, seed=0, ns=5):
     T = np.exp(rng.uniform(np.log(300.0), np.log(15000.0), n))
     rho = np.exp(rng.uniform(np.log(1.0e-4), np.log(1.0), n))
     Y = rng.dirichlet(np.ones(ns), n).T.copy()
+    return T, rho, Y
+
+
+def charged_states(n, M, charge, seed=0):
+    """States for a table with charged species: (T, rho, Y[ns, n]) with T and rho as in
+    thermo_states, heavy-species mass fractions Dirichlet(1) and the electron mass fraction that
+    makes each state neutral, M_e sum_ions Y_i / M_i (then all renormalised to sum 1). M, charge:
+    the table's molar masses and charges (one negative entry, the electron)."""
+    M = np.asarray(M, dtype=np.float64)
+    charge = np.asarray(charge)
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0x10e5]))
+    T = np.exp(rng.uniform(np.log(300.0), np.log(15000.0), n))
+    rho = np.exp(rng.uniform(np.log(1.0e-4), np.log(1.0), n))
+    heavy = np.nonzero(charge >= 0)[0]
+    ie = int(np.nonzero(charge < 0)[0][0])
+    Y = np.zeros((M.size, n))
+    Y[heavy] = rng.dirichlet(np.ones(heavy.size), n).T
+    ions = np.nonzero(charge > 0)[0]
+    Y[ie] = M[ie] * np.sum(Y[ions] / M[ions, None], axis=0)
+    Y /= Y.sum(axis=0)
     return T, rho, Y

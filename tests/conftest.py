@@ -8,6 +8,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 TABLE = os.path.join(ROOT, "paper_2210_05547_gb300", "data", "air5.dat")
+TABLE11 = os.path.join(ROOT, "paper_2210_05547_gb300", "data", "air11.dat")
 GOLDEN = os.path.join(ROOT, "tests", "golden")
 
 
@@ -30,3 +31,9 @@ def read_golden(name):
 def table():
     from oracle import gas
     return gas.load_table(TABLE)
+
+
+@pytest.fixture(scope="session")
+def table11():
+    from oracle import gas
+    return gas.load_table(TABLE11)
