@@ -39,7 +39,11 @@
 extern "C" {
 #endif
 
-#define HYP_MAX_SPECIES 5
+/* Capacity of the species arrays of the ABI structs. The library is built for one species
+ * count: libhyp.so for five-species air (N2, O2, NO, N, O; data/air5.dat), libhyp11.so for
+ * eleven-species air with ions and electrons (data/air11.dat); a gas table must list exactly the
+ * count of the library that loads it. */
+#define HYP_MAX_SPECIES 11
 
 enum hyp_gas_kind {
     HYP_GAS_CNEQ = 0,    /* finite-rate chemistry with algebraic diffusion (Sec. 2.2.1) */
@@ -129,7 +133,12 @@ typedef struct {
 
 /* Load a gas table (plain-text SPECIES / LEVEL / REACTION lines, see data/air5.dat) and build
  * the closure of Sec. 2.2 for `kind`, nondimensionalised with `fs` (Eq. 7). The table must list
- * HYP_MAX_SPECIES species; its first species is the omitted one (Sec. 2.1).
+ * the library's species count (5 or 11, see HYP_MAX_SPECIES); its first species is the omitted
+ * one (Sec. 2.1). Charged species (an optional last SPECIES column, the charge) need the
+ * eleven-species build: ions diffuse ambipolarly (twice their Eq. 19 coefficient), the electron
+ * stays out of the mixing rules and binary pairs and its diffusive flux follows from zero
+ * conduction current, J_e = M_e sum_ions J_i / M_i, with the omitted species taking
+ * J_0 = -sum_{s>=1} J_s. HYP_GAS_LTE rejects charged species (it conserves N and O only).
  * path: HOST string. fs: HOST. *out: new handle, free with hyp_gas_free. */
 int hyp_gas_model_load(const char* path, int kind, const hyp_freestream* fs, hyp_gas** out);
 

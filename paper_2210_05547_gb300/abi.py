@@ -1,9 +1,11 @@
 """Thin Python binding of the C ABI in ``include/hyp.h`` (argument marshalling only).
 
 Every arithmetic step of ``rhs``, ``rk_stage``, ``thermo_eval`` and ``thermo_energy`` runs in the
-CUDA library ``_lib/libhyp.so``; this module only checks tensors, converts case dictionaries into
-the C structs and forwards raw pointers. If the library has not been built, every call raises.
-PyTorch supplies device memory and the current CUDA stream.
+CUDA library (``_lib/libhyp.so`` for five-species tables, ``_lib/libhyp11.so`` for eleven-species
+tables; a gas handle and everything made from it stay with the library that loaded its table);
+this module only checks tensors, converts case dictionaries into the C structs and forwards raw
+pointers. If a library has not been built, every call that needs it raises. PyTorch supplies
+device memory and the current CUDA stream.
 """
 from __future__ import annotations
 
@@ -14,14 +16,16 @@ import numpy as np
 
 from . import build as _build
 
-MAX_SPECIES = 5
+MAX_SPECIES = 11
 GAS_KINDS = {"cneq": 0, "frozen": 1, "cpg": 2, "tpg": 3, "lte": 4}
 STRETCH = {"uniform": 0, "tanh": 1, "cubic": 2}
 FLOWS = {"bl": 0, "sbli": 1}
 DIFFUSION_MODELS = {"ramshaw": 0, "stefan_maxwell": 1}
 FP64 = 0
 MIXED = 1
-TABLE_AIR5 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data", "air5.dat")
+DATA = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data")
+TABLE_AIR5 = os.path.join(DATA, "air5.dat")
+TABLE_AIR11 = os.path.join(DATA, "air11.dat")
 SCALE_NAMES = ("rho_inf", "a_inf", "T_inf", "p_inf", "mu_inf", "k_inf", "cp_inf", "gamma_inf",
                "R_inf", "T_ref", "L_ref", "Re", "Pr")
 
@@ -63,7 +67,7 @@ class RequestStats(ctypes.Structure):
                 ("points", ctypes.c_int64), ("bytes", ctypes.c_int64)]
 
 
-_LIB = None
+_LIBS = {}
 _P = ctypes.c_void_p
 _D = ctypes.c_double
 _I = ctypes.c_int
@@ -117,15 +121,14 @@ class HypError(RuntimeError):
     pass
 
 
-def library_path():
-    return _build.LIB
+def library_path(ns=5):
+    return _build.VARIANTS[ns]
 
 
-def lib():
-    """Load the CUDA library (raises if it has not been built)."""
-    global _LIB
-    if _LIB is None:
-        path = library_path()
+def lib(ns=5):
+    """Load the CUDA library built for ns species (raises if it has not been built)."""
+    if ns not in _LIBS:
+        path = library_path(ns)
         if not os.path.exists(path):
             raise HypError(f"CUDA library not built ({path}); run python -m paper_2210_05547_gb300.build")
         L = ctypes.CDLL(path)
@@ -133,13 +136,25 @@ def lib():
             fn = getattr(L, name)
             fn.restype = res
             fn.argtypes = args
-        _LIB = L
-    return _LIB
+        _LIBS[ns] = L
+    return _LIBS[ns]
 
 
-def _check(rc):
+def table_path(cfg):
+    """The gas table file of a case dictionary (key "table", default five-species air)."""
+    return os.path.join(DATA, cfg.get("table", "air5") + ".dat")
+
+
+def table_species(path):
+    """Number of SPECIES lines of a gas table: which library loads it."""
+    with open(path) as fh:
+        return sum(1 for line in fh if line.split("#", 1)[0].split()[:1] == ["SPECIES"])
+
+
+def _check(rc, L=None):
     if rc != 0:
-        raise HypError(f"hyp error {rc}: {lib().hyp_last_error().decode()}")
+        L = L or lib()
+        raise HypError(f"hyp error {rc}: {L.hyp_last_error().decode()}")
 
 
 def _stream(stream):
@@ -205,18 +220,29 @@ def case_struct(cfg, noise=None):
 # ---------------------------------------------------------------------------------------------
 
 class Gas:
-    def __init__(self, handle):
+    def __init__(self, handle, L, path):
         self.handle = handle
+        self.L = L
+        self.path = path
         ns = ctypes.c_int()
         buf = (ctypes.c_double * 13)()
-        _check(lib().hyp_gas_scales(handle, ctypes.byref(ns), buf))
+        _check(L.hyp_gas_scales(handle, ctypes.byref(ns), buf), L)
         self.ns = ns.value
         self.scales = dict(zip(SCALE_NAMES, list(buf)))
 
     def __del__(self):
-        if getattr(self, "handle", None) and _LIB is not None:
-            _LIB.hyp_gas_free(self.handle)
+        if getattr(self, "handle", None):
+            self.L.hyp_gas_free(self.handle)
             self.handle = None
+
+
+class Grid:
+    """A grid handle (owned by its state) and the library it belongs to; passes as the raw
+    pointer in calls."""
+
+    def __init__(self, ptr, L):
+        self._as_parameter_ = ptr
+        self.L = L
 
 
 class State:
@@ -225,26 +251,34 @@ class State:
         self.U = U
         self.dQ = dQ
         self.gas = gas
-        self.grid = lib().hyp_state_grid(handle)
+        self.L = gas.L
+        self.grid = Grid(gas.L.hyp_state_grid(handle), gas.L)
 
     def __del__(self):
-        if getattr(self, "handle", None) and _LIB is not None:
-            _LIB.hyp_state_free(self.handle)
+        if getattr(self, "handle", None):
+            self.L.hyp_state_free(self.handle)
             self.handle = None
 
 
-def gas_model_load(cfg, kind=None, path=TABLE_AIR5):
-    """hyp_gas_model_load: gas table + kind + freestream (from a case dictionary)."""
+def _grid_lib(grid):
+    return grid.L if isinstance(grid, Grid) else lib()
+
+
+def gas_model_load(cfg, kind=None, path=None):
+    """hyp_gas_model_load: gas table + kind + freestream (from a case dictionary). The table is
+    the case's (key "table") unless a path is given; its species count picks the library."""
+    path = path or table_path(cfg)
+    L = lib(table_species(path)) if os.path.exists(path) else lib()
     h = ctypes.c_void_p()
     fs = freestream_struct(cfg)
     k = GAS_KINDS[kind or cfg["kind"]]
-    _check(lib().hyp_gas_model_load(path.encode(), k, ctypes.byref(fs), ctypes.byref(h)))
-    return Gas(h)
+    _check(L.hyp_gas_model_load(path.encode(), k, ctypes.byref(fs), ctypes.byref(h)), L)
+    return Gas(h, L, path)
 
 
 def state_size(gas, cfg):
     n = ctypes.c_int64()
-    _check(lib().hyp_state_size(gas.handle, ctypes.byref(grid_struct(cfg)), ctypes.byref(n)))
+    _check(gas.L.hyp_state_size(gas.handle, ctypes.byref(grid_struct(cfg)), ctypes.byref(n)), gas.L)
     return n.value
 
 
@@ -255,27 +289,27 @@ def state_init(gas, cfg, U, dQ, noise=None, stream=None):
     h = ctypes.c_void_p()
     desc = grid_struct(cfg)
     cas = case_struct(cfg, noise)
-    _check(lib().hyp_state_init(gas.handle, ctypes.byref(desc), ctypes.byref(cas),
+    _check(gas.L.hyp_state_init(gas.handle, ctypes.byref(desc), ctypes.byref(cas),
                                 _dptr(U, n, torch.float64), _dptr(dQ, n, torch.float64),
-                                _stream(stream), ctypes.byref(h)))
+                                _stream(stream), ctypes.byref(h)), gas.L)
     return State(h, U, dQ, gas)
 
 
 def rhs(gas, grid, U, dUdt, precision=FP64, stream=None):
     """hyp_rhs: dU/dt of the state U (device tensors, same length)."""
-    _check(lib().hyp_rhs(gas.handle, grid, _dptr(U), _dptr(dUdt, U.numel()), precision,
-                         _stream(stream)))
+    _check(gas.L.hyp_rhs(gas.handle, grid, _dptr(U), _dptr(dUdt, U.numel()), precision,
+                         _stream(stream)), gas.L)
 
 
 def rhs_noalloc(gas, grid, U, dUdt, stream=None):
     """hyp_rhs_noalloc: the right-hand side with its scratch in the library's static device array."""
-    _check(lib().hyp_rhs_noalloc(gas.handle, grid, _dptr(U), _dptr(dUdt, U.numel()),
-                                 _stream(stream)))
+    _check(gas.L.hyp_rhs_noalloc(gas.handle, grid, _dptr(U), _dptr(dUdt, U.numel()),
+                                 _stream(stream)), gas.L)
 
 
 def rk_stage(state, stage, dt, precision=FP64, stream=None):
     """hyp_rk_stage: one stage of the two-register RK3 on the state's registers."""
-    _check(lib().hyp_rk_stage(state.handle, stage, dt, precision, _stream(stream)))
+    _check(state.L.hyp_rk_stage(state.handle, stage, dt, precision, _stream(stream)), state.L)
 
 
 RK_SCHEMES = {"rk3": 0, "tvd3": 1, "ck4": 2}
@@ -284,8 +318,8 @@ RK_STAGES = {"rk3": 3, "tvd3": 3, "ck4": 5}
 
 def rk_stage_scheme(state, scheme, stage, dt, precision=FP64, stream=None):
     """hyp_rk_stage_scheme: one stage of "rk3", "tvd3" or "ck4" on the state's registers."""
-    _check(lib().hyp_rk_stage_scheme(state.handle, RK_SCHEMES[scheme], stage, dt, precision,
-                                     _stream(stream)))
+    _check(state.L.hyp_rk_stage_scheme(state.handle, RK_SCHEMES[scheme], stage, dt, precision,
+                                       _stream(stream)), state.L)
 
 
 def wall_fluxes(gas, grid, U, q_w, tau_w, precision=FP64, stream=None):
@@ -293,8 +327,9 @@ def wall_fluxes(gas, grid, U, q_w, tau_w, precision=FP64, stream=None):
     import torch
     if tau_w.numel() != q_w.numel() + 1:
         raise HypError("tau_w needs one entry more than q_w (nx + 1 wall corners, nx wall faces)")
-    _check(lib().hyp_wall_fluxes(gas.handle, grid, _dptr(U), _dptr(q_w, None, torch.float64),
-                                 _dptr(tau_w, None, torch.float64), precision, _stream(stream)))
+    _check(gas.L.hyp_wall_fluxes(gas.handle, grid, _dptr(U), _dptr(q_w, None, torch.float64),
+                                 _dptr(tau_w, None, torch.float64), precision, _stream(stream)),
+           gas.L)
 
 
 def round_f32(x, y=None, back=None, stream=None):
@@ -308,60 +343,69 @@ def round_f32(x, y=None, back=None, stream=None):
 
 
 class Batch:
-    """hyp_batch: many states stepped in shared launches (members keep their own dt)."""
+    """hyp_batch: many states stepped in shared launches (members keep their own dt). species:
+    the species count of the members' gas tables (which library runs the batch)."""
 
-    def __init__(self, precision=FP64, use_graph=False, tile=0):
+    def __init__(self, precision=FP64, use_graph=False, tile=0, species=5):
+        self.L = lib(species)
         h = ctypes.c_void_p()
-        _check(lib().hyp_batch_create(precision, ctypes.byref(h)))
+        _check(self.L.hyp_batch_create(precision, ctypes.byref(h)), self.L)
         self.handle = h
         self.members = []
         if use_graph or tile:
             self.configure(use_graph, tile)
 
     def configure(self, use_graph=False, tile=0):
-        _check(lib().hyp_batch_configure(self.handle, int(bool(use_graph)), int(tile)))
+        _check(self.L.hyp_batch_configure(self.handle, int(bool(use_graph)), int(tile)), self.L)
 
     def add(self, state, dt):
-        _check(lib().hyp_batch_add(self.handle, state.handle, float(dt)))
+        if state.L is not self.L:
+            raise HypError("the state's gas table has another species count than the batch")
+        _check(self.L.hyp_batch_add(self.handle, state.handle, float(dt)), self.L)
         self.members.append(state)
 
     def remove(self, state):
-        _check(lib().hyp_batch_remove(self.handle, state.handle))
+        _check(self.L.hyp_batch_remove(self.handle, state.handle), self.L)
         self.members.remove(state)
 
     def size(self):
         n = ctypes.c_int()
-        _check(lib().hyp_batch_size(self.handle, ctypes.byref(n)))
+        _check(self.L.hyp_batch_size(self.handle, ctypes.byref(n)), self.L)
         return n.value
 
     def tile(self):
         t, tuned = ctypes.c_int(), ctypes.c_int()
-        _check(lib().hyp_batch_tile(self.handle, ctypes.byref(t), ctypes.byref(tuned)))
+        _check(self.L.hyp_batch_tile(self.handle, ctypes.byref(t), ctypes.byref(tuned)), self.L)
         return t.value, bool(tuned.value)
 
     def step(self, nsteps=1, stream=None):
-        _check(lib().hyp_batch_step(self.handle, int(nsteps), _stream(stream)))
+        _check(self.L.hyp_batch_step(self.handle, int(nsteps), _stream(stream)), self.L)
 
     def __del__(self):
-        if getattr(self, "handle", None) is not None and _LIB is not None:
-            _LIB.hyp_batch_free(self.handle)
+        if getattr(self, "handle", None) is not None:
+            self.L.hyp_batch_free(self.handle)
             self.handle = None
 
 
-def state_len(cfg, ns=5):
+def state_len(cfg, ns=None):
     """Length of the state vector of a case (layout of include/hyp.h)."""
+    from .inputs import TABLE_SPECIES
+    ns = ns or TABLE_SPECIES[cfg.get("table", "air5")]
     nx, ny = cfg["nx"], cfg["ny"]
     return (ns + 1) * nx * ny + (nx + 1) * ny + nx * (ny + 1)
 
 
 class Server:
-    """hyp_server: continuous batching of independent solves on the current GPU."""
+    """hyp_server: continuous batching of independent solves on the current GPU, all on the gas
+    table at `path` (its species count picks the library)."""
 
     def __init__(self, precision=FP64, reserve_bytes=4 << 30, max_members=64, kind="cneq",
                  path=TABLE_AIR5):
+        self.L = lib(table_species(path))
         h = ctypes.c_void_p()
-        _check(lib().hyp_server_create(path.encode(), GAS_KINDS[kind], precision, int(reserve_bytes),
-                                       int(max_members), ctypes.byref(h)))
+        _check(self.L.hyp_server_create(path.encode(), GAS_KINDS[kind], precision,
+                                         int(reserve_bytes), int(max_members), ctypes.byref(h)),
+               self.L)
         self.handle = h
 
     def submit(self, cfg, nsteps, dt=None, noise=None, keep_result=False):
@@ -373,32 +417,33 @@ class Server:
         r.nsteps = int(nsteps)
         r.keep_result = int(bool(keep_result))
         i = ctypes.c_int64()
-        _check(lib().hyp_server_submit(self.handle, ctypes.byref(r), ctypes.byref(i)))
+        _check(self.L.hyp_server_submit(self.handle, ctypes.byref(r), ctypes.byref(i)), self.L)
         return i.value
 
     def wait(self, rid=-1, timeout=3600.0):
-        _check(lib().hyp_server_wait(self.handle, int(rid), float(timeout)))
+        _check(self.L.hyp_server_wait(self.handle, int(rid), float(timeout)), self.L)
 
     def stats(self, rid):
         st = RequestStats()
-        _check(lib().hyp_server_stats(self.handle, int(rid), ctypes.byref(st)))
+        _check(self.L.hyp_server_stats(self.handle, int(rid), ctypes.byref(st)), self.L)
         return {k: getattr(st, k) for k, _ in RequestStats._fields_}
 
     def result(self, rid, cfg):
         out = np.empty(state_len(cfg))
-        _check(lib().hyp_server_result(self.handle, int(rid), out.ctypes.data_as(ctypes.c_void_p)))
+        _check(self.L.hyp_server_result(self.handle, int(rid), out.ctypes.data_as(ctypes.c_void_p)),
+               self.L)
         return out
 
     def counters(self):
         a, b, c, d = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_int32()
-        _check(lib().hyp_server_counters(self.handle, ctypes.byref(a), ctypes.byref(b),
-                                         ctypes.byref(c), ctypes.byref(d)))
+        _check(self.L.hyp_server_counters(self.handle, ctypes.byref(a), ctypes.byref(b),
+                                          ctypes.byref(c), ctypes.byref(d)), self.L)
         return {"batch_steps": a.value, "member_steps": b.value, "busy_s": c.value,
                 "max_members": d.value}
 
     def close(self):
-        if getattr(self, "handle", None) is not None and _LIB is not None:
-            _LIB.hyp_server_free(self.handle)
+        if getattr(self, "handle", None) is not None:
+            self.L.hyp_server_free(self.handle)
             self.handle = None
 
     def __del__(self):
@@ -406,16 +451,18 @@ class Server:
 
 
 def grid_reference(grid, n):
+    L = _grid_lib(grid)
     Uref = np.empty(n)
     sigma = np.empty(n)
-    _check(lib().hyp_grid_reference(grid, Uref.ctypes.data_as(ctypes.c_void_p),
-                                    sigma.ctypes.data_as(ctypes.c_void_p)))
+    _check(L.hyp_grid_reference(grid, Uref.ctypes.data_as(ctypes.c_void_p),
+                                sigma.ctypes.data_as(ctypes.c_void_p)), L)
     return Uref, sigma
 
 
 def grid_status(grid, clear=False):
+    L = _grid_lib(grid)
     flags = ctypes.c_uint32()
-    _check(lib().hyp_grid_status(grid, ctypes.byref(flags), int(clear)))
+    _check(L.hyp_grid_status(grid, ctypes.byref(flags), int(clear)), L)
     return flags.value
 
 
@@ -425,12 +472,12 @@ def thermo_eval(gas, rho, e, Y, T=None, p=None, wdot=None, mu=None, k=None, D=No
     import torch
     n = rho.numel()
     ns = gas.ns
-    _check(lib().hyp_thermo_eval(
+    _check(gas.L.hyp_thermo_eval(
         gas.handle, n, _dptr(rho, n, torch.float64), _dptr(e, n, torch.float64),
         _dptr(Y, ns * n, torch.float64), _dptr(T, n), _dptr(p, n), _dptr(wdot, ns * n),
         _dptr(mu, n), _dptr(k, n), _dptr(D, ns * n),
         _dptr(status, n, torch.uint8) if status is not None else None, precision,
-        _stream(stream)))
+        _stream(stream)), gas.L)
 
 
 def lte_eval(gas, rho, e, T=None, p=None, Y=None, mu=None, k=None, k_reactive=None, status=None,
@@ -438,36 +485,38 @@ def lte_eval(gas, rho, e, T=None, p=None, Y=None, mu=None, k=None, k_reactive=No
     """hyp_lte_eval on device tensors (SI) for an "lte" gas. Y (output) is (ns, n)."""
     import torch
     n = rho.numel()
-    _check(lib().hyp_lte_eval(
+    _check(gas.L.hyp_lte_eval(
         gas.handle, n, _dptr(rho, n, torch.float64), _dptr(e, n, torch.float64), _dptr(T, n),
         _dptr(p, n), _dptr(Y, gas.ns * n), _dptr(mu, n), _dptr(k, n), _dptr(k_reactive, n),
         _dptr(status, n, torch.uint8) if status is not None else None, precision,
-        _stream(stream)))
+        _stream(stream)), gas.L)
 
 
 def thermo_energy(gas, T, Y, e, stream=None):
     import torch
     n = T.numel()
-    _check(lib().hyp_thermo_energy(gas.handle, n, _dptr(T, n, torch.float64),
+    _check(gas.L.hyp_thermo_energy(gas.handle, n, _dptr(T, n, torch.float64),
                                    _dptr(Y, gas.ns * n, torch.float64), _dptr(e, n, torch.float64),
-                                   _stream(stream)))
+                                   _stream(stream)), gas.L)
 
 
 def grid_profile(grid, enable):
     """hyp_grid_profile: start (clears totals) or stop the per-launch event profile of a grid."""
-    _check(lib().hyp_grid_profile(grid, int(bool(enable))))
+    L = _grid_lib(grid)
+    _check(L.hyp_grid_profile(grid, int(bool(enable))), L)
 
 
 def grid_profile_read(grid):
     """hyp_grid_profile_read: {kernel name: (total ms, launches)} since the profile was started."""
-    n = lib().hyp_profile_count()
+    L = _grid_lib(grid)
+    n = L.hyp_profile_count()
     ms = np.zeros(n)
     cnt = np.zeros(n, dtype=np.int64)
-    _check(lib().hyp_grid_profile_read(grid, n, ms.ctypes.data_as(ctypes.c_void_p),
-                                       cnt.ctypes.data_as(ctypes.c_void_p)))
+    _check(L.hyp_grid_profile_read(grid, n, ms.ctypes.data_as(ctypes.c_void_p),
+                                   cnt.ctypes.data_as(ctypes.c_void_p)), L)
     out = {}
     for k in range(n):
-        name = lib().hyp_profile_name(k).decode()
+        name = L.hyp_profile_name(k).decode()
         t, c = out.get(name, (0.0, 0))
         out[name] = (t + float(ms[k]), c + int(cnt[k]))
     return out

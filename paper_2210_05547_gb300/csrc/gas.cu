@@ -39,7 +39,7 @@ constexpr double PI = 3.14159265358979323846;
 struct SpeciesRow {
     std::string name;
     double M, hf, theta_v, theta_r, sym, bA, bB, bC, lj_s, lj_e;
-    int linear, nN, nO;
+    int linear, nN, nO, charge = 0;
     std::vector<std::pair<double, double>> levels;
 };
 
@@ -63,6 +63,8 @@ int parse_table(const char* path, std::vector<SpeciesRow>& sp, std::vector<React
             if (!(ss >> r.name >> r.M >> r.hf >> r.linear >> r.theta_v >> r.theta_r >> r.sym >>
                   r.bA >> r.bB >> r.bC >> r.lj_s >> r.lj_e >> r.nN >> r.nO))
                 return fail(HYP_ERR_IO, "bad SPECIES line: " + line);
+            int ch;
+            if (ss >> ch) r.charge = ch;              // optional last column
             sp.push_back(r);
         } else if (key == "LEVEL") {
             std::string name;
@@ -125,7 +127,9 @@ extern "C" int hyp_gas_model_load(const char* path, int kind, const hyp_freestre
     std::vector<ReactionRow> rx;
     int rc = parse_table(path, sp, rx);
     if (rc) return rc;
-    if ((int)sp.size() != NSP) return fail(HYP_ERR_IO, "gas table must list 5 species");
+    if ((int)sp.size() != NSP)
+        return fail(HYP_ERR_IO, "gas table must list " + std::to_string(NSP) +
+                                    " species (the species count this library is built for)");
     if ((int)rx.size() > MAXR) return fail(HYP_ERR_IO, "too many reactions");
     hyp_gas* g = new hyp_gas();
     GasDev& d = g->dev;
@@ -162,9 +166,36 @@ extern "C" int hyp_gas_model_load(const char* path, int kind, const hyp_freestre
         d.theta0[i] = r.hf / R_U - h_sens_over_r(r, 298.15);
         d.atoms[i][0] = r.nN;
         d.atoms[i][1] = r.nO;
+        d.charge[i] = r.charge;
+        d.heavy[i] = r.charge >= 0;
+        d.dfac[i] = r.charge > 0 ? 2.0 : (r.charge < 0 ? 0.0 : 1.0);
         d.blA[i] = r.bA;
         d.blB[i] = r.bB;
         d.blC[i] = r.bC;
+    }
+    d.ie = -1;
+    for (int i = 0; i < NSP; ++i) {
+        if (sp[i].charge != 0 && !HAS_CHARGE) {
+            delete g;
+            return fail(HYP_ERR_IO, "charged species need the eleven-species build (libhyp11)");
+        }
+        if (sp[i].charge < 0) {
+            if (d.ie >= 0 || sp[i].charge != -1 || i == 0) {
+                delete g;
+                return fail(HYP_ERR_IO, "one electron species (charge -1, not the first) at most");
+            }
+            d.ie = i;
+        }
+        if (sp[i].charge > 1) {
+            delete g;
+            return fail(HYP_ERR_IO, "ions must be singly charged");
+        }
+    }
+    bool charged = false;
+    for (int i = 0; i < NSP; ++i) charged = charged || sp[i].charge != 0;
+    if (kind == HYP_GAS_LTE && charged) {
+        delete g;
+        return fail(HYP_ERR_ARG, "LTE conserves N and O only: no charged species");
     }
     for (int i = 0; i < NSP; ++i)
         for (int j = 0; j < NSP; ++j) {
@@ -178,6 +209,7 @@ extern "C" int hyp_gas_model_load(const char* path, int kind, const hyp_freestre
         std::vector<std::vector<int>> members;
         for (int i = 0; i < NSP; ++i)
             for (int j = i + 1; j < NSP; ++j) {
+                if (!d.heavy[i] || !d.heavy[j]) continue;     // no binary pairs with the electron
                 const double eps = sp[i].lj_e * sp[j].lj_e;
                 int q = -1;
                 for (size_t k = 0; k < eps_list.size(); ++k)

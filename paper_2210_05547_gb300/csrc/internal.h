@@ -9,15 +9,25 @@
 
 #include "../../include/hyp.h"
 
-#define NSP HYP_MAX_SPECIES   // species count the kernels are compiled for
-#define MAXR 24                // elementary reactions
-#define MAXG 12                // reaction groups sharing (n, T_a, net stoichiometry)
+// Species count the kernels are compiled for: the library is built once for five-species air
+// (libhyp.so) and once for eleven-species air with ions and electrons (libhyp11.so).
+#ifndef HYP_NSP
+#define HYP_NSP 5
+#endif
+#define NSP HYP_NSP
+#define MAXR 64                // elementary reactions
+#define MAXG 24                // reaction groups sharing (n, T_a, net stoichiometry)
 #define MAXLEV 6               // electronic levels per species
 #define MAXEPS 16              // distinct Lennard-Jones well depths of species pairs
 #define ETAB_N 64              // temperatures of the species-energy table (start of the T inversion)
 #define LINE_BLOCK 128         // threads per block of the line-operator kernel
 
 namespace hyp {
+
+static_assert(NSP <= HYP_MAX_SPECIES, "species count above the C ABI's capacity");
+// Only the eleven-species build accepts charged species (ions, the electron): in the five-species
+// build the mixing rules, diffusion and fluxes compile without the charge handling.
+constexpr bool HAS_CHARGE = NSP > 5;
 
 void set_error(const std::string& msg);
 int fail(int code, const std::string& msg);
@@ -81,6 +91,12 @@ struct GasDev {
     // local thermodynamic equilibrium (HYP_GAS_LTE): atoms of N and O per particle, element
     // content of the freestream air (mol/kg), and the partition-function constants of
     // c_s = exp(a_s . lambda - theta0_s / T + ln r_s)
+    // charged species (eleven-species build): charge per species, 1 for the species in the mixing
+    // rules and binary pairs (all but the electron), the factor on the averaged diffusion
+    // coefficient (2: ambipolar ions, 1 neutrals, 0 the electron), the electron's index or -1
+    int charge[NSP], heavy[NSP];
+    double dfac[NSP];
+    int ie;
     double atoms[NSP][2];
     double elem_b[2];
     double lnA_tr[NSP];          // ln A_tr

@@ -126,7 +126,8 @@ __device__ __forceinline__ void closure_body(const GasDev& g, const Scales& sc, 
                 h[sp] = o.h[sp] * inva2;
                 wd[sp] = o.wdot[sp] * wscale;
                 X[sp] = o.X[sp];
-                W[sp] = cneq ? rho * g.M[sp] * ym : 0.0;
+                // the electron's diffusive flux follows the ions (flux_point): no coefficient
+                W[sp] = cneq && (!HAS_CHARGE || g.heavy[sp]) ? rho * g.M[sp] * ym : 0.0;
                 Wd[sp] = cneq ? W[sp] * (o.D[sp] * sc.rho_inf / sc.mu_inf) / sc.Re : 0.0;
             }
         }
@@ -345,10 +346,24 @@ __device__ __forceinline__ void flux_point(const GasDev& gd, const Scales& sc, c
         for (int sp = 0; sp < NSP; ++sp) J[sp] = 0.0;
     }
 #pragma unroll
-    for (int sp = 0; sp < NSP; ++sp) {
-        J[sp] = wallface ? 0.0 : J[sp] - (g[sp] - Yf[sp][i] * sum);
-        q += hf[sp][i] * J[sp];
+    for (int sp = 0; sp < NSP; ++sp) J[sp] = wallface ? 0.0 : J[sp] - (g[sp] - Yf[sp][i] * sum);
+    if (HAS_CHARGE && gd.ie >= 0 && !wallface) {
+        // zero conduction current: J_e = M_e sum_ions J_i / M_i; the omitted first species
+        // takes J_0 = -sum_{s >= 1} J_s (the diffusive mass fluxes sum to zero)
+        double acc = 0.0;
+#pragma unroll
+        for (int sp = 0; sp < NSP; ++sp)
+            if (gd.charge[sp] > 0) acc += J[sp] / gd.M[sp];
+        double tot = 0.0;
+#pragma unroll
+        for (int sp = 1; sp < NSP; ++sp) {
+            if (sp == gd.ie) J[sp] = gd.M[sp] * acc;
+            tot += J[sp];
+        }
+        J[0] = -tot;
     }
+#pragma unroll
+    for (int sp = 0; sp < NSP; ++sp) q += hf[sp][i] * J[sp];
 #pragma unroll
     for (int sp = 1; sp < NSP; ++sp) Fs[sp][i] = m * Yf[sp][i] + J[sp];
     // tau . u normal component: x-face tau_xx u + tau_xy v; y-face tau_xy u + tau_yy v

@@ -620,6 +620,8 @@ extern "C" int hyp_state_init(const hyp_gas* gas, const hyp_grid_desc* desc, con
     if (cas->wall && !(cas->T_wall > 0)) return fail(HYP_ERR_ARG, "T_wall must be > 0");
     if (cas->sponge_top_cells < 0 || cas->sponge_top_cells >= desc->ny)
         return fail(HYP_ERR_ARG, "sponge_top_cells out of range");
+    if (cas->diffusion_model == 1 && gas->dev.ie >= 0)
+        return fail(HYP_ERR_ARG, "Stefan-Maxwell diffusion is not defined for charged mixtures");
     cudaStream_t s = (cudaStream_t)stream;
     const GasDev& g = gas->dev;
     hyp_grid* G = new hyp_grid();

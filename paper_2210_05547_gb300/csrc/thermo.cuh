@@ -235,9 +235,11 @@ __device__ inline void transport_f32(const GasDev& g, double T, double lnT, doub
     float mu = 0.0f, kk = 0.0f;
 #pragma unroll
     for (int i = 0; i < NSP; ++i) {
+        if (HAS_CHARGE && !g.heavy[i]) continue;      // the electron is not in the mixing rule
         float phi = 0.0f;
 #pragma unroll
         for (int r = 0; r < NSP; ++r) {
+            if (HAS_CHARGE && !g.heavy[r]) continue;
             const float t = 1.0f + a[i] * b[r];
             phi += Xf[r] * t * t * g.f_wilke_d[i][r];
         }
@@ -271,7 +273,10 @@ __device__ inline void transport_f32(const GasDev& g, double T, double lnT, doub
         }
     }
 #pragma unroll
-    for (int i = 0; i < NSP; ++i) o.D[i] = den[i] != 0.0f ? f64_of((1.0f - Xf[i]) / den[i]) : 0.0;
+    for (int i = 0; i < NSP; ++i) {
+        o.D[i] = den[i] != 0.0f ? f64_of((1.0f - Xf[i]) / den[i]) : 0.0;
+        if (HAS_CHARGE) o.D[i] *= g.dfac[i];       // ambipolar ions, no electron coefficient
+    }
 }
 #endif
 
@@ -296,9 +301,11 @@ __host__ __device__ inline void transport_f64(const GasDev& g, double T, double 
     double mu = 0.0, kk = 0.0;
 #pragma unroll
     for (int i = 0; i < NSP; ++i) {
+        if (HAS_CHARGE && !g.heavy[i]) continue;      // the electron is not in the mixing rule
         double phi = 0.0;
 #pragma unroll
         for (int r = 0; r < NSP; ++r) {
+            if (HAS_CHARGE && !g.heavy[r]) continue;
             const double t = 1.0 + a[i] * b[r];
             phi += o.X[r] * t * t * g.wilke_d[i][r];
         }
@@ -333,7 +340,10 @@ __host__ __device__ inline void transport_f64(const GasDev& g, double T, double 
             }
         }
 #pragma unroll
-        for (int i = 0; i < NSP; ++i) o.D[i] = den[i] != 0.0 ? (1.0 - o.X[i]) / den[i] : 0.0;
+        for (int i = 0; i < NSP; ++i) {
+            o.D[i] = den[i] != 0.0 ? (1.0 - o.X[i]) / den[i] : 0.0;
+            if (HAS_CHARGE) o.D[i] *= g.dfac[i];   // ambipolar ions, no electron coefficient
+        }
     }
 }
 

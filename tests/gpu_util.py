@@ -24,7 +24,7 @@ def nstate(cfg, ns=5):
 
 
 def oracle_case(table, cfg):
-    return F.make_case(cfg, table, I.state_noise(nstate(cfg), cfg["seed"]))
+    return F.make_case(cfg, table, I.state_noise(nstate(cfg, table.ns), cfg["seed"]))
 
 
 def gpu_state(cfg):
@@ -53,8 +53,9 @@ def check_rhs(case, U, g):
     max|g - o| <= 1e-12 max|o| + rounding floor of the flux divergence (oracle.flow)."""
     tol, o = F.parity_tolerance(case, U)
     cfg = case.cfg
-    fg = F.unpack(5, cfg["nx"], cfg["ny"], np.asarray(g))
-    fo = F.unpack(5, cfg["nx"], cfg["ny"], o)
+    ns = case.tab.ns
+    fg = F.unpack(ns, cfg["nx"], cfg["ny"], np.asarray(g))
+    fo = F.unpack(ns, cfg["nx"], cfg["ny"], o)
     bad = {k: (float(np.abs(fg[k] - fo[k]).max()), float(tol[k])) for k in fo
            if not np.abs(fg[k] - fo[k]).max() <= tol[k]}
     return bad, o

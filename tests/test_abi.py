@@ -22,11 +22,12 @@ def A():
     return abi
 
 
-def test_exports_every_declared_symbol(A):
+@pytest.mark.parametrize("ns", [5, 11])
+def test_exports_every_declared_symbol(A, ns):
     hdr = open(os.path.join(ROOT, "include", "hyp.h")).read()
     declared = set(re.findall(r"\b(hyp_[a-z0-9_]+)\s*\(", hdr))
     assert len(declared) >= 14
-    L = A.lib()
+    L = A.lib(ns)
     for name in declared:
         assert hasattr(L, name), name
     assert declared == set(A.EXPORTS)
@@ -44,6 +45,28 @@ def test_freestream_scales_match_oracle(A, table, maker, kind):
                Re=sc.Re, Pr=sc.Pr)
     for k, v in ref.items():
         assert abs(g.scales[k] / v - 1.0) < 1e-14, k
+
+
+@pytest.mark.parametrize("maker", [I.bl_case, I.sbli_case])
+def test_freestream_scales_eleven_species(A, table11, maker):
+    cfg = I.with_species(maker())
+    g = A.gas_model_load(cfg)
+    assert g.ns == 11 and g.L is A.lib(11)
+    sc = F.freestream_scales(table11, "cneq", cfg)
+    ref = dict(rho_inf=sc.rho, a_inf=sc.a, mu_inf=sc.mu, k_inf=sc.k, cp_inf=sc.cp, Pr=sc.Pr)
+    for k, v in ref.items():
+        assert abs(g.scales[k] / v - 1.0) < 1e-14, k
+    assert A.state_size(g, cfg) == A.state_len(cfg)
+
+
+def test_species_count_and_charge_rules(A):
+    cfg = I.bl_case()
+    rc = A.lib(5).hyp_gas_model_load(A.TABLE_AIR11.encode(), 0,
+                                     ctypes.byref(A.freestream_struct(cfg)),
+                                     ctypes.byref(ctypes.c_void_p()))
+    assert rc == -3 and b"must list 5 species" in A.lib(5).hyp_last_error()
+    with pytest.raises(A.HypError, match="LTE conserves N and O only"):
+        A.gas_model_load(I.with_species(cfg), kind="lte")
 
 
 def test_eckert_number_is_one(A):
