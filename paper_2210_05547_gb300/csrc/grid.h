@@ -28,13 +28,16 @@ struct Dims {
     long long size(Node t) const { return (long long)rows(t) * pitch(t); }
 };
 
+// raw and filtered artificial diffusivities per cell: mu*, beta*, kappa* and D*_s per species
+constexpr int AD_FIELDS = 3 + NSP;
+
 struct Scratch {
     // cell centres
     double *ru_c, *rv_c, *T, *p, *H, *u_c, *v_c, *e, *a, *mu_e, *K, *beta, *Tcache;
     double *Y[NSP], *X[NSP], *h[NSP], *Wd[NSP], *W[NSP], *G[NSP];
     double *esc[NSP], *cvsc[NSP], *cvpc[NSP];   // species e, c_v, dc_v/dT at the cached T
     double *dudx, *dvdy, *tau_xx, *tau_yy, *Gxx, *Gyy, *mux_c, *mvy_c;
-    double *dudy_c, *dvdx_c, *S, *div, *fsw, *raw[8], *filt[8];
+    double *dudy_c, *dvdx_c, *S, *div, *fsw, *raw[AD_FIELDS], *filt[AD_FIELDS];
     // x-faces
     double *rho_xf, *u_xf, *Yx[NSP], *Gx[NSP], *hx[NSP], *Hx, *Kx, *txx_x, *v_x, *dTdx,
         *dXdx[NSP], *txy_x, *Fsx[NSP], *FEx, *mu_xf, *dudy_t, *dvdx_t, *mux_f, *Tx, *px;

@@ -421,7 +421,7 @@ __global__ void k_ad_raw(int cneq, GridView v, const double* __restrict__ U, Scr
 }
 
 __global__ void k_gauss(GridView v, Scratch s, int dir) {
-    gauss_body(v, s, dir, GRID_RANGE(8LL * v.nx * v.ny));
+    gauss_body(v, s, dir, GRID_RANGE((long long)AD_FIELDS * v.nx * v.ny));
 }
 
 __global__ void k_ad_combine(GridView v, Scratch s) {
@@ -691,7 +691,7 @@ extern "C" int hyp_state_init(const hyp_gas* gas, const hyp_grid_desc* desc, con
     if (P.shock) P.sh = oblique_shock(g.mach, P.theta, g.gamma_inf);
     for (int sp = 0; sp < NSP; ++sp) P.Yinf[sp] = g.Y_inf[sp];
     // ---------------- device memory ----------------
-    const long long n_c_fields = 13 + 9 * NSP + 8 + 5 + 16;
+    const long long n_c_fields = 13 + 9 * NSP + 13 + 2 * AD_FIELDS;
     const long long n_xf_fields = 2 + 6 * NSP + 8 + 3;
     const long long n_yf_fields = 2 + 6 * NSP + 8;
     const long long n_cn_fields = 8;
@@ -726,7 +726,7 @@ extern "C" int hyp_state_init(const hyp_gas* gas, const hyp_grid_desc* desc, con
     double** c2[] = {&S.dudx, &S.dvdy, &S.tau_xx, &S.tau_yy, &S.Gxx, &S.Gyy, &S.mux_c, &S.mvy_c,
                      &S.dudy_c, &S.dvdx_c, &S.S, &S.div, &S.fsw};
     for (double** f : c2) *f = take(nc);
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < AD_FIELDS; ++q) {
         S.raw[q] = take(nc);
         S.filt[q] = take(nc);
     }
@@ -1080,7 +1080,7 @@ static int run_rhs(const hyp_gas* gas, hyp_grid* G, const double* U, double* dUd
     HYP_CUDA(cudaStreamWaitEvent(s, G->join[0], 0));
     if (v.ad) {
         TIMED(KID_AD_RAW, (k_ad_raw<<<blocks_for(nc, 256), 256, 0, s>>>(g.kind == HYP_GAS_CNEQ, v, U, S)));
-        const int gg = blocks_for(8 * nc, 256);
+        const int gg = blocks_for(AD_FIELDS * nc, 256);
         TIMED(KID_AD_GAUSS, (k_gauss<<<gg, 256, 0, s>>>(v, S, 0)));
         TIMED(KID_AD_GAUSS, (k_gauss<<<gg, 256, 0, s>>>(v, S, 1)));
         TIMED(KID_AD_COMBINE, (k_ad_combine<<<blocks_for(nc, 256), 256, 0, s>>>(v, S)));
@@ -1371,7 +1371,7 @@ extern "C" int hyp_rhs_noalloc(const hyp_gas* gas, const hyp_grid* grid, const d
         HYP_CUDA(lines(PH_AD2, 2));
         k_ad_prep<<<blocks_for(nc, 256), 256, 0, s>>>(v, S);
         k_ad_raw<<<blocks_for(nc, 256), 256, 0, s>>>(g.kind == HYP_GAS_CNEQ, v, U, S);
-        const int gg = blocks_for(8 * nc, 256);
+        const int gg = blocks_for(AD_FIELDS * nc, 256);
         k_gauss<<<gg, 256, 0, s>>>(v, S, 0);
         k_gauss<<<gg, 256, 0, s>>>(v, S, 1);
         k_ad_combine<<<blocks_for(nc, 256), 256, 0, s>>>(v, S);

@@ -24,10 +24,12 @@ namespace {
 constexpr int MAX_CHUNK = 8;   // steps between admission / retirement checks
 
 // Device bytes of one admitted request per cell: the grid's scratch pool (about 216 doubles per
-// cell: centre, face and corner fields and six state-sized vectors), the line-sweep storage of
-// its largest phase (about 54 doubles per cell), the two RK registers (16 doubles) and the mask,
-// rounded up; plus a fixed allowance for tables and plans.
-constexpr long long BYTES_PER_CELL = 2400;
+// cell for five species: centre, face and corner fields and six state-sized vectors), the
+// line-sweep storage of its largest phase (about 54 doubles per cell), the two RK registers (16
+// doubles) and the mask, rounded up; each further species adds about 29 doubles (nine centre
+// fields, two artificial-diffusivity fields, six on each face family, six state-sized vectors);
+// plus a fixed allowance for tables and plans.
+constexpr long long BYTES_PER_CELL = 2400 + 240 * (NSP - 5);
 constexpr long long BYTES_FIXED = 4LL << 20;
 
 struct Request {
