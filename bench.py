@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
     ap.add_argument("--no-sm", action="store_true", help="skip the Stefan-Maxwell measurement")
     ap.add_argument("--no-lte", action="store_true", help="skip the LTE measurement")
+    ap.add_argument("--no-air11", action="store_true",
+                    help="skip the eleven-species measurements")
     ap.add_argument("--serve-requests", type=int, default=48,
                     help="requests of the serving measurement (0 skips it)")
     ap.add_argument("--thermo-states", type=float, default=1e8,
@@ -229,10 +231,25 @@ def field_ranges(cfg, ns=5):
     return out
 
 
+def table_columns(path):
+    """Molar masses and charges of a gas table's species (SPECIES lines: M is the first value,
+    the optional charge the fifteenth)."""
+    M, q = [], []
+    with open(path) as fh:
+        for line in fh:
+            tok = line.split("#", 1)[0].split()
+            if tok[:1] == ["SPECIES"]:
+                M.append(float(tok[2]))
+                q.append(int(tok[15]) if len(tok) > 15 else 0)
+    return M, q
+
+
 def thermo_sweep(A, gas, dev, n, seed, reps=2, precision=0):
     """Throughput of hyp_thermo_eval on n independent states resident in HBM: T log-uniform in
-    [300, 15000] K, rho log-uniform in [1e-4, 1] kg/m^3, mass fractions Dirichlet(1), e = e(T, Y)
-    from hyp_thermo_energy. All outputs requested (T, p, wdot, mu, k, D, status)."""
+    [300, 15000] K, rho log-uniform in [1e-4, 1] kg/m^3, mass fractions Dirichlet(1) (for a table
+    with charged species: Dirichlet(1) over the heavy species and the electrons that make the
+    state neutral), e = e(T, Y) from hyp_thermo_energy. All outputs requested (T, p, wdot, mu, k,
+    D, status)."""
     import math
     import torch
     g = torch.Generator(device=dev)
@@ -244,6 +261,12 @@ def thermo_sweep(A, gas, dev, n, seed, reps=2, precision=0):
     rho = torch.exp(math.log(1e-4) + u * math.log(1e4))
     del u
     Y = torch.empty((ns, n), device=dev, dtype=torch.float64).exponential_(generator=g)
+    M, q = table_columns(gas.path)
+    if any(c < 0 for c in q):
+        ie = q.index(-1)
+        Y[ie] = 0.0
+        Y /= Y.sum(dim=0, keepdim=True)
+        Y[ie] = M[ie] * sum(Y[s] / M[s] for s in range(ns) if q[s] > 0)
     Y /= Y.sum(dim=0, keepdim=True)
     e = torch.empty(n, device=dev, dtype=torch.float64)
     A.thermo_energy(gas, T0, Y, e)
@@ -264,7 +287,9 @@ def thermo_sweep(A, gas, dev, n, seed, reps=2, precision=0):
     return {"value": n / (ms / 1e3) / 1e6, "unit": "Mstates/s", "states": n, "ms_per_sweep": ms,
             "bytes_per_state": 8 * (2 + ns) + 8 * (4 + 2 * ns) + 1,
             "max_rel_T_roundtrip": err, "status_nonzero": bad,
-            "inputs": "T log-uniform 300-15000 K, rho log-uniform 1e-4-1 kg/m^3, Y Dirichlet(1)"}
+            "species": ns,
+            "inputs": "T log-uniform 300-15000 K, rho log-uniform 1e-4-1 kg/m^3, Y Dirichlet(1)"
+                      + (" over the heavy species, neutral" if any(c < 0 for c in q) else "")}
 
 
 def serving_bench(A, I, nreq, seed, precision):
@@ -467,9 +492,10 @@ def ours_arm(args, rank, world, local_rank):
     # ---------------- model variants on the same workload (FP64, same steps) ----------------
     def variant(cfg_v):
         gas_v = A.gas_model_load(cfg_v)
-        Uv = torch.empty(n, dtype=torch.float64, device=dev)
+        n_v = A.state_size(gas_v, cfg_v)
+        Uv = torch.empty(n_v, dtype=torch.float64, device=dev)
         dQv = torch.empty_like(Uv)
-        stv = A.state_init(gas_v, cfg_v, Uv, dQv, I.state_noise(n, cfg["seed"]))
+        stv = A.state_init(gas_v, cfg_v, Uv, dQv, I.state_noise(n_v, cfg["seed"]))
         for _ in range(args.warmup):
             for k in range(STAGES):
                 A.rk_stage(stv, k, dt)
@@ -495,6 +521,13 @@ def ours_arm(args, rank, world, local_rank):
         smd.update(cost_vs_algebraic=s_ms / max_ms,
                    note="Stefan-Maxwell system (Eq. 17) solved at every face instead of the "
                         "algebraic model (Eq. 18); same case, FP64")
+    air11 = None
+    if not args.no_air11:
+        air11, a_ms = variant(I.with_species(cfg))
+        air11.update(cost_vs_air5=a_ms / max_ms,
+                     note="eleven-species air (N2, O2, NO, N, O, N2+, O2+, NO+, N+, O+, e-; 49 "
+                          "reactions; ambipolar ions, zero-current electrons) on the same case "
+                          "from the same neutral initial state, FP64")
     lte = None
     if not args.no_lte:
         lte, l_ms = variant(dict(cfg, kind="lte"))
@@ -515,6 +548,11 @@ def ours_arm(args, rank, world, local_rank):
         sweep = thermo_sweep(A, gas, dev, int(args.thermo_states), 1000 + rank)
         sweep["mixed"] = thermo_sweep(A, gas, dev, int(args.thermo_states), 1000 + rank,
                                       precision=A.MIXED)
+        if not args.no_air11:
+            gas11 = A.gas_model_load(I.with_species(cfg))
+            sweep["air11"] = thermo_sweep(A, gas11, dev, int(args.thermo_states), 2000 + rank)
+            sweep["air11"]["mixed"] = thermo_sweep(A, gas11, dev, int(args.thermo_states),
+                                                   2000 + rank, precision=A.MIXED)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -534,7 +572,7 @@ def ours_arm(args, rank, world, local_rank):
                               "frac": value / world * RHS_FP64_FLOP_PER_POINT / 1e6 / FP64_PEAK_TFLOPS},
                 "wall_s_timed": t_wall, "status_flags": status, "mixed": mixed,
                 "serving": serving, "serving_fp64": serving_fp64, "stefan_maxwell": smd,
-                "lte": lte, "thermo_sweep": sweep,
+                "lte": lte, "air11": air11, "thermo_sweep": sweep,
                 "kernels": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1]}}
         print(json.dumps(line), flush=True)
     if world > 1:
