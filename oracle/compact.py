@@ -167,3 +167,63 @@ def ifc(f, axis):
 
 def dfc(f, axis):
     return apply(f, axis, 'D', 'fc')
+
+
+# ---------------------------------------------------------------------------------------------
+# Periodic lines (the spanwise direction of three-dimensional cases)
+# ---------------------------------------------------------------------------------------------
+# A periodic line of n cells has centres at k + 1/2 and faces at i (i = 0..n-1; face n is face 0).
+# Every row is an interior row of the sixth-order schemes above, with indices taken modulo n; A is
+# then circulant and the oracle solves it densely.
+
+@lru_cache(maxsize=None)
+def periodic_matrices(kind, direction, n):
+    """Dense (A, B), both (n, n), of the periodic operator; kind 'I' or 'D', direction 'cf'
+    (centres -> faces) or 'fc' (faces -> centres)."""
+    coef = INTERP6 if kind == 'I' else DERIV6
+    a, b, alpha = float(coef['a']), float(coef['b']), float(coef['alpha'])
+    A = np.zeros((n, n))
+    B = np.zeros((n, n))
+    for r in range(n):
+        A[r, r] = 1.0
+        A[r, (r - 1) % n] += alpha
+        A[r, (r + 1) % n] += alpha
+        # inputs at offsets -3/2, -1/2, +1/2, +3/2 from output r
+        if direction == 'cf':          # face r; centre k sits at k + 1/2
+            km3, km1, kp1, kp3 = r - 2, r - 1, r, r + 1
+        else:                          # centre r + 1/2; face i sits at i
+            km3, km1, kp1, kp3 = r - 1, r, r + 1, r + 2
+        if kind == 'I':
+            w = {km3: b / 2, km1: a / 2, kp1: a / 2, kp3: b / 2}
+        else:
+            w = {km3: -b / 3, km1: -a, kp1: a, kp3: b / 3}
+        for k, v in w.items():
+            B[r, k % n] += v
+    return A, B
+
+
+def apply_periodic(f, axis, kind, direction):
+    """Apply the periodic operator along ``axis`` (index-space result, spacing 1)."""
+    f = np.asarray(f, dtype=np.float64)
+    fm = np.moveaxis(f, axis, 0)
+    n = fm.shape[0]
+    A, B = periodic_matrices(kind, direction, n)
+    x = fm.reshape(n, -1)
+    y = np.linalg.solve(A, B @ x)
+    return np.moveaxis(y.reshape(fm.shape), 0, axis)
+
+
+def icf_p(f, axis):
+    return apply_periodic(f, axis, 'I', 'cf')
+
+
+def ifc_p(f, axis):
+    return apply_periodic(f, axis, 'I', 'fc')
+
+
+def dcf_p(f, axis):
+    return apply_periodic(f, axis, 'D', 'cf')
+
+
+def dfc_p(f, axis):
+    return apply_periodic(f, axis, 'D', 'fc')

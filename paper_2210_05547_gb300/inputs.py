@@ -22,6 +22,11 @@ Workloads (shapes follow the paper's cases; there is no dataset):
   for a table with ions and electrons, Dirichlet(1) over the heavy species and the electrons that
   make each state neutral.
 * ``with_species`` -- any case on the eleven-species table (ions and electrons start at zero).
+* ``jet_case`` -- sonic jet from a circular orifice into a Mach 8 crossflow on a spanwise-periodic
+  domain (the jet case of Sec. 4 in three dimensions): 512 x 256 x 128 cells over x 38.5-71,
+  y 0-10 (cubic clustering, kappa_y = 0.15), z 0-10 (periodic, 10 jet diameters), T_inf = 600 K,
+  p_inf = 49800 Pa, Re_D = 25291 (Re_inf on a_inf = Re_D / Ma); orifice centre x = 52.5, spanwise
+  centre, radius and momentum ratio J in [1, 3] drawn from the seed; jet sonic at T_inf.
 """
 from __future__ import annotations
 
@@ -60,6 +65,23 @@ def sbli_case(nx=2048, ny=256, seed=0, kind="cneq"):
         artificial_diffusivity=1, C_mu=0.002, C_beta=1.75, C_kappa=0.01, C_D=0.01,
         noise_amp=1.0e-4, dt=2.0e-3, filter_sigma=0.05, diffusion_model="ramshaw", table="air5",
     )
+
+
+def jet_case(nx=512, ny=256, nz=128, seed=0, kind="cneq"):
+    """Sonic jet in a hypersonic crossflow, spanwise periodic, artificial diffusivity on."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0x3e7]))
+    c = bl_case(nx, ny, seed, kind)
+    c.update(
+        name=f"jet_{nx}x{ny}x{nz}", nz=nz, x0=38.5, x1=71.0, y0=0.0, y1=10.0, z0=0.0, z1=10.0,
+        y_stretch="cubic", y_param=0.15, T_inf=600.0, p_inf=49800.0, mach=8.0,
+        reynolds=25291.0 / 8.0, T_wall=1500.0, delta_coef=20.0,
+        sponge_in=1.0, sponge_out=2.0, sponge_top_cells=max(2, (20 * ny) // 500),
+        artificial_diffusivity=1, C_D=0.01, dt=5.0e-4, filter_sigma=0.0,
+        jet=1, jet_x=52.5, jet_z=5.0 + float(rng.uniform(-1.0, 1.0)),
+        jet_radius=0.5 * float(rng.uniform(0.9, 1.1)), jet_edge=0.1,
+        jet_J=float(rng.uniform(1.0, 3.0)), jet_T_ratio=1.0,
+    )
+    return c
 
 
 def with_species(cfg, table="air11"):
