@@ -27,8 +27,10 @@
  *   centres  (ny rows x nx columns, x fastest): rho, rho_s for s = 1..ns-1, rho*E
  *   x-faces  (ny rows x (nx+1) columns):       rho*u
  *   y-faces  ((ny+1) rows x nx columns):       rho*v
- * concatenated in that order, FP64, nondimensional per Eq. (7). Total length from
- * hyp_state_size(). The right-hand side has the same layout.
+ * concatenated in that order, FP64, nondimensional per Eq. (7). Three-dimensional grids stack nz
+ * such planes per field (z slowest) and append rho*w on the z-faces (nz x ny x nx; face k lies
+ * between centres k-1 and k of the periodic direction). Total length from hyp_state_size(). The
+ * right-hand side has the same layout.
  */
 #ifndef HYP_H
 #define HYP_H
@@ -99,12 +101,18 @@ typedef struct {
 
 /* Structured grid: nx x ny cells; x uniform on [x0, x1]; y on [y0, y1] with
  * y_stretch 0 = uniform, 1 = tanh wall clustering y = y0 + (y1-y0)(1 - tanh(q(1-s))/tanh q),
- * 2 = the cubic map of Eq. (27) with kappa_y = q; s = j/ny at grid (tau) nodes. */
+ * 2 = the cubic map of Eq. (27) with kappa_y = q; s = j/ny at grid (tau) nodes.
+ * nz > 1: a three-dimensional grid with nz uniform, periodic cells on [z0, z1) (nz <= 1: the
+ * two-dimensional grid). Three-dimensional grids take the cneq, frozen or cpg gas, the algebraic
+ * diffusion and no state filter, and run hyp_rhs / hyp_rk_stage (the two-register RK3) only; the
+ * state adds rho w on the z-faces (see the state layout above) and the case may carry a jet. */
 typedef struct {
     int32_t nx, ny;
     double x0, x1, y0, y1;
     int32_t y_stretch;
     double y_param;
+    int32_t nz;
+    double z0, z1;
 } hyp_grid_desc;
 
 /* Case: boundary conditions (Sec. 3.2, Fig. 2), sponge (Eq. 26), shock capturing (Sec. 3.3),
@@ -129,6 +137,14 @@ typedef struct {
                                       this damping of the grid-to-grid mode (see hyp_rk_stage) */
     int32_t diffusion_model;       /* HYP_GAS_CNEQ: 0 the algebraic model of Eq. 18, 1 the
                                       Stefan-Maxwell system of Eq. 17 solved at every face */
+    /* Three-dimensional grids: a sonic jet through a circular orifice in the wall (the jet in
+     * hypersonic crossflow of Sec. 4). Inside the orifice the wall face holds the Dirichlet mass
+     * flux of a sonic jet at T_j = jet_T_ratio T_inf and p_j = jet_J Ma^2 p_inf (so that jet_J is
+     * the momentum ratio rho_j v_j^2 / (rho_inf U_inf^2)), blended to the wall by
+     * 1/2 (1 - tanh((r - jet_radius) / (jet_edge jet_radius))), r the distance to (jet_x, jet_z)
+     * on the periodic domain; the wall temperature of the heat flux blends to T_j the same way. */
+    int32_t jet;
+    double jet_x, jet_z, jet_radius, jet_edge, jet_J, jet_T_ratio;
 } hyp_case;
 
 /* Load a gas table (plain-text SPECIES / LEVEL / REACTION lines, see data/air5.dat) and build

@@ -21,7 +21,10 @@ those of the two-dimensional oracle (oracle/flow.py) with the third direction ad
   holds the Dirichlet mass flux rho_j v_j of a sonic jet at T_j = T_jet_ratio T_inf with
   p_j = J Ma_inf^2 p_inf (so that J = rho_j v_j^2 / (rho_inf U_inf^2)), blended to the no-slip
   wall by a tanh of width jet_edge r_j; the wall temperature of the heat flux blends from T_wall
-  to T_j the same way; u = w = 0 and no diffusion through the wall.
+  to T_j the same way; u = w = 0 and no diffusion through the wall. The reference and initial
+  states carry the jet's plume, so that the first cells above the orifice hold its density and
+  momentum: the two-dimensional profile's T, p, u, v are blended towards (T_j, p_j, 0, v_j) with
+  F = f(r) exp(-((y - y0) / (jet_height r_j))^2), and the wall faces hold rho v of that blend.
 
 Every step follows the two-dimensional sequence of oracle.flow.rhs; with a z-uniform state and no
 jet each z-plane gives exactly that right-hand side (pinned in tests/test_oracle_flow3d.py).
@@ -92,11 +95,23 @@ def jet_blend(cfg, x, z):
 
 def jet_state(cfg, sc):
     """Nondimensional mass flux rho_j v_j and the jet temperature (K) of the sonic jet."""
+    T_j, p_j, v_j = jet_primitives(cfg, sc)
+    rho_j = p_j / (sc.R * T_j) / sc.rho
+    return rho_j * v_j, T_j
+
+
+def jet_primitives(cfg, sc):
+    """T_j (K), p_j (Pa) and the nondimensional v_j of the sonic jet."""
     T_j = cfg["jet_T_ratio"] * sc.T
     p_j = cfg["jet_J"] * sc.mach ** 2 * sc.p
-    rho_j = p_j / (sc.R * T_j) / sc.rho
     v_j = math.sqrt(sc.gamma * sc.R * T_j) / sc.a
-    return rho_j * v_j, T_j
+    return T_j, p_j, v_j
+
+
+def plume(cfg, x, y, z):
+    """Blend factor of the jet's plume at (x, y, z)."""
+    h = cfg.get("jet_height", 2.0) * cfg["jet_radius"]
+    return jet_blend(cfg, x, z) * np.exp(-((y - cfg["y0"]) / h) ** 2)
 
 
 def make_case(cfg, tab, noise=None) -> Case3D:
@@ -113,30 +128,38 @@ def make_case(cfg, tab, noise=None) -> Case3D:
     zf = cfg["z0"] + dz * np.arange(nz)
     zc = zf + 0.5 * dz
     ref = {}
+    jet_on = bool(cfg.get("jet", 0))
+    if jet_on:
+        T_j, p_j, v_j = jet_primitives(cfg, sc)
 
-    def plane(xs, ys):
-        Xn, Yn = np.meshgrid(xs, ys)
-        T, p, u, v, Y = F._primitive_profile(cfg, sc, tab, kind, Xn, Yn)
-        rho, rhoY, rhoE = F._conserved_from_primitive(tab, kind, sc, T, p, u, v, Y)
+    def nodes(xs, ys):
+        """Conserved rho, rho_s, rho E and the velocities at (z, y, x) nodes with the plume."""
+        Zn, Yn, Xn = np.meshgrid(zc, ys, xs, indexing="ij")
+        T, p, u, v, Y = F._primitive_profile(cfg, sc, tab, kind, Xn[0], Yn[0])
+        T, p, u, v = (np.broadcast_to(a, Zn.shape) for a in (T, p, u, v))
+        Y = np.broadcast_to(Y[:, None], (tab.ns,) + Zn.shape)
+        if jet_on:
+            Fp = plume(cfg, Xn, Yn, Zn)
+            T = T + (T_j - T) * Fp
+            p = p + (p_j - p) * Fp
+            u = u * (1.0 - Fp)
+            v = v + (v_j - v) * Fp
+        rho, rhoY, rhoE = F._conserved_from_primitive(tab, kind, sc, np.array(T), np.array(p),
+                                                      np.array(u), np.array(v), np.array(Y))
         return rho, rhoY, rhoE, u, v
 
-    rho, rhoY, rhoE, _, _ = plane(g.xc, g.yc)
-    ref["rho"] = np.broadcast_to(rho, (nz, ny, nx))
+    rho, rhoY, rhoE, _, _ = nodes(g.xc, g.yc)
+    ref["rho"] = rho
     for s in range(1, ns):
-        ref[f"rs{s}"] = np.broadcast_to(rhoY[s], (nz, ny, nx))
-    ref["rhoE"] = np.broadcast_to(rhoE, (nz, ny, nx))
-    rho_u, _, _, u, _ = plane(g.xf, g.yc)
-    ref["rhou"] = np.broadcast_to(rho_u * u, (nz, ny, nx + 1))
-    rho_v, _, _, _, v = plane(g.xc, g.yf)
-    rhov = np.array(np.broadcast_to(rho_v * v, (nz, ny + 1, nx)))
+        ref[f"rs{s}"] = rhoY[s]
+    ref["rhoE"] = rhoE
+    rho_u, _, _, u, _ = nodes(g.xf, g.yc)
+    ref["rhou"] = rho_u * u
+    rho_v, _, _, _, v = nodes(g.xc, g.yf)
+    ref["rhov"] = rho_v * v
     Xw, Zw = np.meshgrid(g.xc, zc)                     # wall faces: (nz, nx)
-    if cfg.get("jet", 0):
-        jet = jet_blend(cfg, Xw, Zw)
-        mflux, T_j = jet_state(cfg, sc)
-    else:
-        jet, mflux, T_j = np.zeros((nz, nx)), 0.0, cfg["T_wall"]
-    rhov[:, 0, :] = mflux * jet
-    ref["rhov"] = rhov
+    jet = jet_blend(cfg, Xw, Zw) if jet_on else np.zeros((nz, nx))
+    T_jet = T_j if jet_on else cfg["T_wall"]
     ref["rhow"] = np.zeros((nz, ny, nx))
     U_ref = pack(ns, nx, ny, nz, ref)
     Xc, Yc = np.meshgrid(g.xc, g.yc)
@@ -156,7 +179,7 @@ def make_case(cfg, tab, noise=None) -> Case3D:
         f["rhou"][:, :, nx] = r["rhou"][:, :, nx]
         f["rhov"][:, 0, :] = r["rhov"][:, 0, :]
         f["rhov"][:, ny, :] = r["rhov"][:, ny, :]
-    Tw = cfg["T_wall"] + (T_j - cfg["T_wall"]) * jet
+    Tw = cfg["T_wall"] + (T_jet - cfg["T_wall"]) * jet
     return Case3D(cfg=cfg, tab=tab, kind=kind, sc=sc, grid=g, nz=nz, zeta=1.0 / dz, zc=zc, zf=zf,
                   U_ref=U_ref, sigma=sigma, U0=U0, jet=jet, T_wall_face=Tw)
 

@@ -39,7 +39,8 @@ class Freestream(ctypes.Structure):
 class GridDesc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("x0", ctypes.c_double),
                 ("x1", ctypes.c_double), ("y0", ctypes.c_double), ("y1", ctypes.c_double),
-                ("y_stretch", ctypes.c_int32), ("y_param", ctypes.c_double)]
+                ("y_stretch", ctypes.c_int32), ("y_param", ctypes.c_double),
+                ("nz", ctypes.c_int32), ("z0", ctypes.c_double), ("z1", ctypes.c_double)]
 
 
 class CaseDesc(ctypes.Structure):
@@ -52,7 +53,10 @@ class CaseDesc(ctypes.Structure):
                 ("C_mu", ctypes.c_double), ("C_beta", ctypes.c_double),
                 ("C_kappa", ctypes.c_double), ("C_D", ctypes.c_double),
                 ("noise_amp", ctypes.c_double), ("noise", ctypes.POINTER(ctypes.c_double)),
-                ("filter_sigma", ctypes.c_double), ("diffusion_model", ctypes.c_int32)]
+                ("filter_sigma", ctypes.c_double), ("diffusion_model", ctypes.c_int32),
+                ("jet", ctypes.c_int32), ("jet_x", ctypes.c_double), ("jet_z", ctypes.c_double),
+                ("jet_radius", ctypes.c_double), ("jet_edge", ctypes.c_double),
+                ("jet_J", ctypes.c_double), ("jet_T_ratio", ctypes.c_double)]
 
 
 class Request(ctypes.Structure):
@@ -192,7 +196,8 @@ def freestream_struct(cfg):
 
 def grid_struct(cfg):
     return GridDesc(cfg["nx"], cfg["ny"], cfg["x0"], cfg["x1"], cfg["y0"], cfg["y1"],
-                    STRETCH[cfg["y_stretch"]], cfg["y_param"])
+                    STRETCH[cfg["y_stretch"]], cfg["y_param"], int(cfg.get("nz", 1)),
+                    float(cfg.get("z0", 0.0)), float(cfg.get("z1", 1.0)))
 
 
 def case_struct(cfg, noise=None):
@@ -208,6 +213,10 @@ def case_struct(cfg, noise=None):
     c.noise_amp = cfg["noise_amp"]
     c.filter_sigma = cfg.get("filter_sigma", 0.0)
     c.diffusion_model = DIFFUSION_MODELS[cfg.get("diffusion_model", "ramshaw")]
+    c.jet = int(cfg.get("jet", 0))
+    if c.jet:
+        c.jet_x, c.jet_z, c.jet_radius = cfg["jet_x"], cfg["jet_z"], cfg["jet_radius"]
+        c.jet_edge, c.jet_J, c.jet_T_ratio = cfg["jet_edge"], cfg["jet_J"], cfg["jet_T_ratio"]
     if noise is not None:
         arr = np.ascontiguousarray(noise, dtype=np.float64)
         c.noise = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
@@ -391,8 +400,9 @@ def state_len(cfg, ns=None):
     """Length of the state vector of a case (layout of include/hyp.h)."""
     from .inputs import TABLE_SPECIES
     ns = ns or TABLE_SPECIES[cfg.get("table", "air5")]
-    nx, ny = cfg["nx"], cfg["ny"]
-    return (ns + 1) * nx * ny + (nx + 1) * ny + nx * (ny + 1)
+    nx, ny, nz = cfg["nx"], cfg["ny"], int(cfg.get("nz", 1))
+    n = (ns + 1) * nx * ny + (nx + 1) * ny + nx * (ny + 1)
+    return n * nz + nx * ny * nz if nz > 1 else n
 
 
 class Server:

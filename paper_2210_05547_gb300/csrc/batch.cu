@@ -420,6 +420,7 @@ extern "C" int hyp_batch_create(int precision, hyp_batch** out) {
 extern "C" int hyp_batch_add(hyp_batch* b, hyp_state* st, double dt) {
     if (!b || !st) return fail(HYP_ERR_ARG, "null argument");
     if (!(dt >= 0.0)) return fail(HYP_ERR_ARG, "time step must be >= 0");
+    if (st->grid->g3) return fail(HYP_ERR_ARG, "the batch takes two-dimensional grids");
     for (const auto& m : b->members)
         if (m.st == st) return fail(HYP_ERR_ARG, "state is already in the batch");
     const GasDev& g = st->grid->gas;

@@ -126,6 +126,7 @@ using hyp::PH_COUNT;
 using hyp::Scratch;
 
 struct hyp_grid {
+    void* g3;                    // three-dimensional grids: their own data (rhs.cu), else null
     Dims d;
     hyp_case cas;
     GasDev gas;

@@ -565,6 +565,8 @@ struct PlanBuilder {
     }
 };
 
+#include "rhs3d.cuh"
+
 }  // namespace
 
 // ---------------------------------------------------------------------------------------------
@@ -575,6 +577,8 @@ static int check_desc(const hyp_grid_desc* d) {
     if (!d) return fail(HYP_ERR_ARG, "null grid descriptor");
     if (d->nx < 8 || d->ny < 8) return fail(HYP_ERR_ARG, "grid needs at least 8 cells per direction");
     if ((long long)d->nx * d->ny > (1LL << 28)) return fail(HYP_ERR_ARG, "grid too large");
+    if (d->nz > 1 && (d->nz < 4 || (long long)(d->nx + 1) * (d->ny + 1) * d->nz > (1LL << 31)))
+        return fail(HYP_ERR_ARG, "three-dimensional grids need 4 to 2^31 / ((nx+1)(ny+1)) z-cells");
     if (!(d->x1 > d->x0) || !(d->y1 > d->y0)) return fail(HYP_ERR_ARG, "empty domain");
     if (d->y_stretch < 0 || d->y_stretch > 2) return fail(HYP_ERR_ARG, "unknown y stretching");
     return HYP_OK;
@@ -586,11 +590,18 @@ extern "C" int hyp_state_size(const hyp_gas* gas, const hyp_grid_desc* desc, int
     if (rc) return rc;
     const long long nc = (long long)desc->nx * desc->ny;
     *n = (NSP + 1) * nc + (long long)(desc->nx + 1) * desc->ny + (long long)desc->nx * (desc->ny + 1);
+    if (desc->nz > 1) *n = *n * desc->nz + nc * desc->nz;        // planes, then rho w
     return HYP_OK;
 }
 
 static void free_grid(hyp_grid* G) {
     if (!G) return;
+    if (G->g3) {
+        free_grid3((Grid3*)G->g3);
+        cudaFree(G->status);
+        delete G;
+        return;
+    }
     cudaFree(G->pool);
     cudaFree(G->mask);
     cudaFree(G->status);
@@ -632,6 +643,26 @@ extern "C" int hyp_state_init(const hyp_gas* gas, const hyp_grid_desc* desc, con
     G->cas.noise = nullptr;
     G->gas = g;
     G->stream = s;
+    if (desc->nz > 1) {
+        cudaError_t e = cudaMalloc(&G->status, sizeof(unsigned));
+        if (e != cudaSuccess) {
+            delete G;
+            return cuda_fail(e, "cudaMalloc(status)");
+        }
+        const int r3 = init3(gas, desc, cas, U, dQ, s, G);
+        if (r3) {
+            if (G->g3) free_grid3((Grid3*)G->g3);
+            cudaFree(G->status);
+            delete G;
+            return r3;
+        }
+        hyp_state* st = new hyp_state();
+        st->grid = G;
+        st->U = U;
+        st->dQ = dQ;
+        *out = st;
+        return HYP_OK;
+    }
     const Dims& d = G->d;
     const int nx = d.nx, ny = d.ny;
     const long long nc = d.size(NC), nxf = d.size(NXF), nyf = d.size(NYF), ncn = d.size(NCN);
@@ -1126,6 +1157,9 @@ extern "C" int hyp_rhs(const hyp_gas* gas, const hyp_grid* grid, const double* U
     if (precision != HYP_FP64 && precision != HYP_MIXED) return fail(HYP_ERR_ARG, "unknown precision");
     if (U == dUdt) return fail(HYP_ERR_ARG, "U and dUdt must not alias");
     hyp_grid* G = const_cast<hyp_grid*>(grid);
+    if (G->g3)
+        return run_rhs3(gas, G, U, dUdt, 0, 0.0, 0.0, 0.0, nullptr, nullptr, precision,
+                        (cudaStream_t)stream);
     return run_rhs(gas, G, U, dUdt, 0, 0.0, 0.0, 0.0, nullptr, nullptr, precision,
                    (cudaStream_t)stream);
 }
@@ -1163,6 +1197,11 @@ extern "C" int hyp_rk_stage_scheme(hyp_state* st, int scheme, int stage, double 
     // the gas handle is not stored in the state: the grid keeps a copy of the device tables
     hyp_gas tmp;
     tmp.dev = G->gas;
+    if (G->g3) {
+        if (scheme != HYP_RK3_2N) return fail(HYP_ERR_ARG, "three-dimensional grids step the two-register RK3");
+        return run_rhs3(&tmp, G, st->U, nullptr, 1, RK_A[stage], RK_B[stage], dt, st->U, st->dQ,
+                        precision, (cudaStream_t)stream);
+    }
     int mode = 1;
     double A = RK_A[stage < 3 ? stage : 0], B = RK_B[stage < 3 ? stage : 0];
     if (scheme == HYP_RK3_TVD) {
@@ -1199,6 +1238,7 @@ extern "C" int hyp_wall_fluxes(const hyp_gas* gas, const hyp_grid* grid, const d
     if (!gas || !grid || !U || !q_w || !tau_w) return fail(HYP_ERR_ARG, "null argument");
     if (precision != HYP_FP64 && precision != HYP_MIXED) return fail(HYP_ERR_ARG, "unknown precision");
     hyp_grid* G = const_cast<hyp_grid*>(grid);
+    if (G->g3) return fail(HYP_ERR_ARG, "hyp_wall_fluxes takes two-dimensional grids");
     const GridView v = G->view();
     if (!v.wall) return fail(HYP_ERR_ARG, "the case has no wall");
     cudaStream_t s = (cudaStream_t)stream;
@@ -1238,6 +1278,7 @@ extern "C" const char* hyp_profile_name(int id) {
 extern "C" int hyp_grid_profile(const hyp_grid* grid, int enable) {
     if (!grid) return fail(HYP_ERR_ARG, "null grid");
     hyp_grid* G = const_cast<hyp_grid*>(grid);
+    if (G->g3) return fail(HYP_ERR_ARG, "the event profile covers two-dimensional grids");
     if (!G->prof) G->prof = new EventProfile();
     EventProfile* P = G->prof;
     if (enable) {
@@ -1315,6 +1356,7 @@ extern "C" int hyp_rhs_noalloc(const hyp_gas* gas, const hyp_grid* grid, const d
     if (!gas || !grid || !U || !dUdt) return fail(HYP_ERR_ARG, "null argument");
     if (U == dUdt) return fail(HYP_ERR_ARG, "U and dUdt must not alias");
     hyp_grid* G = const_cast<hyp_grid*>(grid);
+    if (G->g3) return fail(HYP_ERR_ARG, "hyp_rhs_noalloc takes two-dimensional grids");
     cudaStream_t s = (cudaStream_t)stream;
     int njobs = 0;
     for (int ph = 0; ph < PH_COUNT; ++ph) njobs = std::max(njobs, G->ph_start[ph] + G->ph_count[ph]);

@@ -1,0 +1,1054 @@
+// Three-dimensional grids (hyp_grid_desc.nz > 1): the right-hand side of rhs.cu with a uniform,
+// periodic third direction z and an optional jet from a circular orifice in the wall (the jet in
+// hypersonic crossflow of Sec. 4, here with a spanwise-periodic domain). Included by rhs.cu
+// inside its file-local namespace, so it shares the reference profile, grid map and operator
+// construction of the two-dimensional path.
+//
+// Layout (x fastest): centres (nz, ny, nx) hold rho, rho_s (s >= 1), rho E; rho u on x-faces
+// (nz, ny, nx+1); rho v on y-faces (nz, ny+1, nx); rho w on z-faces (nz, ny, nx), face k between
+// centres k-1 and k. Shear stresses and cross momentum fluxes sit on edges: xy-edges
+// (nz, ny+1, nx+1), xz-edges (the x-face array shape, at z-faces), yz-edges (the y-face shape).
+//
+// Every step follows the two-dimensional sequence, extended by the z terms: velocity gradients
+// at centres and on the three edge families, the three-dimensional strain and vorticity in the
+// artificial-diffusivity sensors (fourth differences and Gaussian filter periodic in z), stresses
+// at centres and edges, species and energy fluxes on the three face families, divergences in
+// three directions. Lines along x and y use the compact operators of the two-dimensional path
+// (one thread per line, Thomas factors of the operator); lines along z are periodic: every row
+// is interior, so the forward and backward recurrences run with the operator's constant
+// factors around the ring, started W = 48 rows early from zero (the dropped history is scaled by
+// at most 3^-48 < 1e-22; the result is the periodic solution to rounding).
+//
+// Jet (reading; the paper gives a sonic jet of prescribed temperature ratio and momentum ratio
+// J): inside the orifice the wall face holds the Dirichlet mass flux of a sonic jet at
+// T_j = jet_T_ratio T_inf and p_j = J Ma^2 p_inf, blended to the no-slip wall by
+// 1/2 (1 - tanh((r - r_j) / (jet_edge r_j))) (r: distance to the jet centre, the spanwise
+// separation taken on the periodic domain); the wall temperature of the heat flux blends from
+// T_wall to T_j the same way; u = w = 0 and no diffusion through the wall.
+
+enum Shape3 : int { C3 = 0, XF3 = 1, YF3 = 2, XY3 = 3 };
+
+struct Sh3 {
+    int nx, ny, nz;
+    __host__ __device__ int pitch(int t) const { return (t == C3 || t == YF3) ? nx : nx + 1; }
+    __host__ __device__ int rows(int t) const { return (t == C3 || t == XF3) ? ny : ny + 1; }
+    __host__ __device__ long long plane(int t) const { return (long long)pitch(t) * rows(t); }
+    __host__ __device__ long long size(int t) const { return plane(t) * nz; }
+};
+
+// One batched line operation over a 3-D array.
+struct Line3 {
+    const LineOp* op;          // x or y operator (device); unused along z
+    int axis, tin, tout;       // 0 x, 1 y, 2 z; array shapes of input and output
+    const double* in;
+    double* out;
+    const double* metric;      // x, y: per output point along the line (nullable)
+    double scale;              // z lines: includes the metric zeta
+    double wall;               // y lines with a wall operator: wall value, or per line:
+    const double* wall_arr;    //   wall value of line (k, i) at k * nx + i
+    int kind, dir;             // z lines: 0 interpolation / 1 derivative; 0 c->f / 1 f->c
+    double wa, wb, lm, cp;     // z lines: the operator's constant factors
+};
+
+constexpr int W3 = 48;   // warm-up rows of the periodic recurrences
+
+__device__ __forceinline__ double row3(int kind, double p0, double p1, double p2, double p3,
+                                       double wa, double wb, double lm, double d) {
+    if (kind == 0) return fma(-lm, d, fma(wa, p1 + p2, wb * (p0 + p3)));
+    return fma(-lm, d, fma(wa, p2 - p1, wb * (p3 - p0)));
+}
+
+// Lines along x or y: one thread per line, forward recurrence into the output, back substitution
+// in place.
+__global__ void __launch_bounds__(128) k_line3(Line3 L, Sh3 sh) {
+    const LineOp& op = *L.op;
+    const long long nlines = L.axis == 0 ? (long long)sh.rows(L.tin) * sh.nz
+                                         : (long long)sh.pitch(L.tin) * sh.nz;
+    for (long long line = blockIdx.x * (long long)blockDim.x + threadIdx.x; line < nlines;
+         line += (long long)gridDim.x * blockDim.x) {
+        long long bi, bo, ei, eo;
+        if (L.axis == 0) {
+            bi = line * sh.pitch(L.tin);
+            bo = line * sh.pitch(L.tout);
+            ei = eo = 1;
+        } else {
+            const long long k = line / sh.pitch(L.tin), i = line - k * sh.pitch(L.tin);
+            bi = k * sh.plane(L.tin) + i;
+            bo = k * sh.plane(L.tout) + i;
+            ei = sh.pitch(L.tin);
+            eo = sh.pitch(L.tout);
+        }
+        const double* __restrict__ in = L.in + bi;
+        double* __restrict__ out = L.out + bo;
+        const double wallv = L.wall_arr ? L.wall_arr[line] : L.wall;
+        const int m = op.m;
+        double d = 0.0;
+        for (int r = 0; r < m; ++r) {
+            if (r < op.first_interior || r > op.last_interior) {
+                int c = 0;
+                while (op.crow[c] != r) ++c;
+                double v = op.gw[c] * wallv;
+                for (int q = 0; q < op.cnum[c]; ++q) v += op.cw[c][q] * in[(op.cstart[c] + q) * ei];
+                d = v;
+            } else {
+                const int s0 = op.dir == 0 ? r - 2 : r - 1;
+                d = row3(op.kind, in[s0 * ei], in[(s0 + 1) * ei], in[(s0 + 2) * ei],
+                         in[(s0 + 3) * ei], op.wa[r], op.wb[r], op.lm[r], d);
+            }
+            out[r * eo] = d;
+        }
+        double y = 0.0;
+        for (int r = m - 1; r >= 0; --r) {
+            y = out[r * eo] - (r < m - 1 ? op.cprime[r] * y : 0.0);
+            const double mt = L.metric ? L.metric[r] : 1.0;
+            out[r * eo] = L.scale * (mt * y);
+        }
+    }
+}
+
+// Periodic lines along z: one thread per line.
+__global__ void __launch_bounds__(128) k_line3z(Line3 L, Sh3 sh) {
+    const long long plane = sh.plane(L.tin);
+    const int n = sh.nz;
+    for (long long line = blockIdx.x * (long long)blockDim.x + threadIdx.x; line < plane;
+         line += (long long)gridDim.x * blockDim.x) {
+        const double* __restrict__ in = L.in + line;
+        double* __restrict__ out = L.out + line;
+        auto at = [&](int r) { return in[(long long)(((r % n) + n) % n) * plane]; };
+        double d = 0.0;
+        for (int t = -W3; t < n; ++t) {
+            const int s0 = L.dir == 0 ? t - 2 : t - 1;
+            d = row3(L.kind, at(s0), at(s0 + 1), at(s0 + 2), at(s0 + 3), L.wa, L.wb, L.lm, d);
+            if (t >= 0) out[(long long)t * plane] = d;
+        }
+        double y = out[(long long)((n - 1 + W3) % n) * plane];
+        for (int t = n - 2 + W3; t >= n; --t) y = out[(long long)(t % n) * plane] - L.cp * y;
+        for (int t = n - 1; t >= 0; --t) {
+            y = out[(long long)t * plane] - L.cp * y;
+            out[(long long)t * plane] = L.scale * y;
+        }
+    }
+}
+
+struct Grid3 {
+    Sh3 sh;
+    double zeta;
+    long long nc, nxf, nyf, nxy, nstate;
+    long long off[NSP + 4];    // rho, rho_s (1..NSP-1), rho E, rho u, rho v, rho w
+    double* pool;
+    // centres (and z-faces, same shape)
+    double *ru_c, *rv_c, *rw_c, *T, *p, *H, *u_c, *v_c, *w_c, *e, *a, *mu_e, *K, *beta, *Tcache;
+    double *Y[NSP], *X[NSP], *h[NSP], *W[NSP], *Wd[NSP], *G[NSP];
+    double *dudx, *dvdy, *dwdz, *tau_xx, *tau_yy, *tau_zz, *Gxx, *Gyy, *Gzz, *mux_c, *mvy_c, *mwz_c;
+    double *S, *div, *fsw, *dudy_c, *dvdx_c, *dudz_c, *dwdx_c, *dvdz_c, *dwdy_c, *tc[4];
+    double *raw[AD_FIELDS], *filt[AD_FIELDS];
+    double *rho_zf, *w_zf, *mwz_f;
+    double *Yz[NSP], *Gz[NSP], *hz[NSP], *dXdz[NSP], *Fsz[NSP];
+    double *Hz, *Kz, *dTdz, *tzz_z, *u_z, *v_z, *txz_z, *tyz_z, *FEz;
+    // x-faces and xz-edges
+    double *rho_xf, *u_xf, *mux_f, *mu_xf, *Yx[NSP], *Gx[NSP], *hx[NSP], *dXdx[NSP], *Fsx[NSP];
+    double *Hx, *Kx, *dTdx, *txx_x, *v_x, *w_x, *txy_x, *txz_x, *FEx;
+    double *dudz_xz, *dwdx_xz, *u_xz, *w_xz, *rho_xz, *mu_xz, *tau_xz, *Gxz, *tx[2];
+    // y-faces and yz-edges
+    double *rho_yf, *v_yf, *mvy_f, *mu_yf, *Yy[NSP], *Gy[NSP], *hy[NSP], *dXdy[NSP], *Fsy[NSP];
+    double *Hy, *Ky, *dTdy, *tyy_y, *u_y, *w_y, *txy_y, *tyz_y, *FEy;
+    double *dvdz_yz, *dwdy_yz, *v_yz, *w_yz, *rho_yz, *mu_yz, *tau_yz, *Gyz;
+    // xy-edges
+    double *dudy_xy, *dvdx_xy, *u_xy, *v_xy, *rho_xy, *mu_xy, *tau_xy, *Gxy;
+    // state-sized
+    double *DX, *DY, *DZ, *SRC, *R;
+    double *Uref, *sigma;
+    uint8_t* mask;
+    double *xi_c, *xi_f, *eta_c, *eta_f, *Tw;
+    LineOp* ops;
+    double* opdata;
+    Line3 zop[2][2];           // periodic z operators [kind][dir] (constants only)
+    std::vector<Line3> p1, p3, ad1, ad2, mu, face, faceb, divs;
+};
+
+struct View3 {
+    Sh3 sh;
+    long long off[NSP + 4];
+    int wall, ad;
+    double C_mu, C_beta, C_kappa, C_D, zeta;
+    const double *xi_c, *eta_c;
+    unsigned* status;
+};
+
+// ---- pointwise kernels ----
+#define RANGE3(n) for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < (n); \
+                       q += (long long)gridDim.x * blockDim.x)
+
+__global__ void k_fv3(Grid3 g, View3 v, const double* __restrict__ U) {
+    const long long a = g.nxf, b = a + g.nyf, c = b + g.nc;
+    RANGE3(c) {
+        if (q < a) {
+            const double m = U[v.off[NSP + 1] + q], u = m / g.rho_xf[q];
+            g.u_xf[q] = u;
+            g.mux_f[q] = m * u;
+        } else if (q < b) {
+            const long long i = q - a;
+            const double m = U[v.off[NSP + 2] + i], vv = m / g.rho_yf[i];
+            g.v_yf[i] = vv;
+            g.mvy_f[i] = m * vv;
+        } else {
+            const long long i = q - b;
+            const double m = U[v.off[NSP + 3] + i], w = m / g.rho_zf[i];
+            g.w_zf[i] = w;
+            g.mwz_f[i] = m * w;
+        }
+    }
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(128) k_closure3(GasDev gd, Scales sc, Grid3 g, View3 v,
+                                                  const double* __restrict__ U) {
+    const bool cneq = sc.kind == HYP_GAS_CNEQ;
+    RANGE3(g.nc) {
+        const long long idx = q;
+        const double rho = U[v.off[0] + idx];
+        const double irho = 1.0 / rho;
+        double Y[NSP];
+        double rest = rho;
+#pragma unroll
+        for (int sp = 1; sp < NSP; ++sp) {
+            const double r = U[v.off[sp] + idx];
+            Y[sp] = r * irho;
+            rest -= r;
+        }
+        Y[0] = rest * irho;
+        const double rhoE = U[v.off[NSP] + idx];
+        const double u = g.ru_c[idx] * irho, vv = g.rv_c[idx] * irho, w = g.rw_c[idx] * irho;
+        const double e = rhoE * irho - 0.5 * (u * u + vv * vv + w * w);
+        double T, p, mu, k, a;
+        double h[NSP], wd[NSP], X[NSP], W[NSP], Wd[NSP];
+        if (sc.kind == HYP_GAS_CPG) {
+            T = sc.gamma_inf * e;
+            p = rho * (sc.gamma_inf - 1.0) / sc.gamma_inf * T;
+            const double Td = T * sc.T_ref;
+            mu = SUTH_C1 * Td * sqrt(Td) / (Td + SUTH_TS) / sc.mu_inf;
+            k = mu;
+            a = sqrt(sc.gamma_inf * p / rho);
+#pragma unroll
+            for (int sp = 0; sp < NSP; ++sp) h[sp] = wd[sp] = X[sp] = W[sp] = Wd[sp] = 0.0;
+        } else {
+            ClosureOut o;
+            closure_si_p<MIXED>(gd, rho * sc.rho_inf, e * sc.a_inf * sc.a_inf, Y, g.Tcache[idx],
+                                cneq, cneq, o);
+            if (o.status) atomicOr(v.status, o.status);
+            g.Tcache[idx] = o.T;
+            T = o.T / sc.T_ref;
+            p = o.p / (sc.rho_inf * sc.a_inf * sc.a_inf);
+            mu = o.mu / sc.mu_inf;
+            k = o.k / sc.k_inf;
+            a = o.a / sc.a_inf;
+            double ym = 0.0;
+#pragma unroll
+            for (int sp = 0; sp < NSP; ++sp) ym += Y[sp] * gd.invM[sp];
+            const double wscale = sc.L_ref / (sc.rho_inf * sc.a_inf);
+            const double inva2 = 1.0 / (sc.a_inf * sc.a_inf);
+#pragma unroll
+            for (int sp = 0; sp < NSP; ++sp) {
+                h[sp] = o.h[sp] * inva2;
+                wd[sp] = o.wdot[sp] * wscale;
+                X[sp] = o.X[sp];
+                W[sp] = cneq && (!HAS_CHARGE || gd.heavy[sp]) ? rho * gd.M[sp] * ym : 0.0;
+                Wd[sp] = W[sp] * (o.D[sp] * sc.rho_inf / sc.mu_inf) / sc.Re;
+            }
+        }
+        g.T[idx] = T;
+        g.p[idx] = p;
+        g.H[idx] = (rhoE + p) * irho;
+        g.u_c[idx] = u;
+        g.v_c[idx] = vv;
+        g.w_c[idx] = w;
+        g.e[idx] = e;
+        g.a[idx] = a;
+        g.mu_e[idx] = mu / sc.Re;
+        g.K[idx] = k / (sc.Re * sc.Pr);
+#pragma unroll
+        for (int sp = 0; sp < NSP; ++sp) {
+            g.Y[sp][idx] = Y[sp];
+            g.X[sp][idx] = X[sp];
+            g.h[sp][idx] = h[sp];
+            g.W[sp][idx] = W[sp];
+            g.Wd[sp][idx] = Wd[sp];
+            g.G[sp][idx] = Wd[sp];
+        }
+        g.beta[idx] = 0.0;
+#pragma unroll
+        for (int sp = 1; sp < NSP; ++sp) g.SRC[v.off[sp] + idx] = wd[sp];
+    }
+}
+
+__global__ void k_adprep3(Grid3 g) {
+    RANGE3(g.nc) {
+        const double ux = g.dudx[q], vy = g.dvdy[q], wz = g.dwdz[q];
+        const double uy = g.dudy_c[q], vx = g.dvdx_c[q], uz = g.dudz_c[q], wx = g.dwdx_c[q];
+        const double vz = g.dvdz_c[q], wy = g.dwdy_c[q];
+        const double sxy = uy + vx, sxz = uz + wx, syz = vz + wy;
+        g.S[q] = sqrt(ux * ux + vy * vy + wz * wz + 0.5 * sxy * sxy + 0.5 * sxz * sxz + 0.5 * syz * syz);
+        const double dv = ux + vy + wz;
+        const double o1 = vx - uy, o2 = uz - wx, o3 = wy - vz;
+        const double om2 = o1 * o1 + o2 * o2 + o3 * o3;
+        g.div[q] = dv;
+        g.fsw[q] = dv < 0.0 ? dv * dv / (dv * dv + om2 + DUCROS_EPS) : 0.0;
+    }
+}
+
+__device__ __forceinline__ double d4_3(const double* f, const Sh3& s, int k, int j, int i, int axis) {
+    const long long nx = s.nx, pl = (long long)s.nx * s.ny;
+    if (axis == 0) {
+        const int c = min(max(i, 2), s.nx - 3);
+        const double* r = f + k * pl + j * nx + c;
+        return r[-2] - 4.0 * r[-1] + 6.0 * r[0] - 4.0 * r[1] + r[2];
+    }
+    if (axis == 1) {
+        const int c = min(max(j, 2), s.ny - 3);
+        const double* r = f + k * pl + c * nx + i;
+        return r[-2 * nx] - 4.0 * r[-nx] + 6.0 * r[0] - 4.0 * r[nx] + r[2 * nx];
+    }
+    const double* b = f + j * nx + i;
+    auto at = [&](int kk) { return b[(long long)(((kk % s.nz) + s.nz) % s.nz) * pl]; };
+    return at(k + 2) - 4.0 * at(k + 1) + 6.0 * at(k) - 4.0 * at(k - 1) + at(k - 2);
+}
+
+__global__ void k_adraw3(Grid3 g, View3 v, const double* __restrict__ U, int cneq) {
+    const Sh3 s = g.sh;
+    const double dz = 1.0 / v.zeta;
+    RANGE3(g.nc) {
+        const int i = (int)(q % s.nx);
+        const long long t = q / s.nx;
+        const int j = (int)(t % s.ny), k = (int)(t / s.ny);
+        const double dx = 1.0 / v.xi_c[i], dy = 1.0 / v.eta_c[j];
+        const double rho = U[v.off[0] + q];
+        auto sens = [&](const double* f, int l) {
+            const double fx = d4_3(f, s, k, j, i, 0), fy = d4_3(f, s, k, j, i, 1),
+                         fz = d4_3(f, s, k, j, i, 2);
+            return l == 2 ? fx * dx * dx + fy * dy * dy + fz * dz * dz : fx * dx + fy * dy + fz * dz;
+        };
+        g.raw[0][q] = v.C_mu * rho * fabs(sens(g.S, 2));
+        g.raw[1][q] = v.C_beta * rho * g.fsw[q] * fabs(sens(g.div, 2));
+        g.raw[2][q] = v.C_kappa * rho * g.a[q] / g.T[q] * fabs(sens(g.e, 1));
+#pragma unroll
+        for (int sp = 0; sp < NSP; ++sp) g.raw[3 + sp][q] = cneq ? v.C_D * g.a[q] * fabs(sens(g.Y[sp], 1)) : 0.0;
+    }
+}
+
+// Gaussian filter of the raw diffusivities along one axis (x, y clamped; z periodic):
+// pass 0 raw -> filt (x), 1 filt -> raw (y), 2 raw -> filt (z)
+__global__ void k_gauss3(Grid3 g, int axis) {
+    const Sh3 s = g.sh;
+    const long long n = g.nc, pl = (long long)s.nx * s.ny;
+    RANGE3((long long)AD_FIELDS * n) {
+        const int f = (int)(q / n);
+        const long long idx = q - f * n;
+        const double* __restrict__ in = axis == 1 ? g.filt[f] : g.raw[f];
+        double* __restrict__ out = axis == 1 ? g.raw[f] : g.filt[f];
+        const int i = (int)(idx % s.nx);
+        const long long t = idx / s.nx;
+        const int j = (int)(t % s.ny), k = (int)(t / s.ny);
+        double acc = c_gauss[0] * in[idx];
+        if (axis == 0) {
+            const double* r = in + idx - i;
+#pragma unroll
+            for (int d = 1; d <= 4; ++d) acc += c_gauss[d] * (r[max(i - d, 0)] + r[min(i + d, s.nx - 1)]);
+        } else if (axis == 1) {
+            const double* b = in + k * pl + i;
+#pragma unroll
+            for (int d = 1; d <= 4; ++d)
+                acc += c_gauss[d] * (b[(long long)max(j - d, 0) * s.nx] + b[(long long)min(j + d, s.ny - 1) * s.nx]);
+        } else {
+            const double* b = in + (long long)j * s.nx + i;
+#pragma unroll
+            for (int d = 1; d <= 4; ++d)
+                acc += c_gauss[d] * (b[(long long)(((k - d) % s.nz + s.nz) % s.nz) * pl] +
+                                     b[(long long)((k + d) % s.nz) * pl]);
+        }
+        out[idx] = acc;
+    }
+}
+
+__global__ void k_adcombine3(Grid3 g) {
+    RANGE3(g.nc) {
+        g.mu_e[q] += g.filt[0][q];
+        g.beta[q] = g.filt[1][q];
+        g.K[q] += g.filt[2][q];
+#pragma unroll
+        for (int sp = 0; sp < NSP; ++sp) g.G[sp][q] = g.Wd[sp][q] + g.W[sp][q] * g.filt[3 + sp][q];
+    }
+}
+
+__global__ void k_stress3(Grid3 g) {
+    const long long a = g.nc, b = a + g.nxy, c = b + g.nxf, d = c + g.nyf;
+    RANGE3(d) {
+        if (q < a) {
+            const double ux = g.dudx[q], vy = g.dvdy[q], wz = g.dwdz[q];
+            const double dv = ux + vy + wz, mu = g.mu_e[q], be = g.beta[q];
+            const double txx = mu * (2.0 * ux - 2.0 / 3.0 * dv) + be * dv;
+            const double tyy = mu * (2.0 * vy - 2.0 / 3.0 * dv) + be * dv;
+            const double tzz = mu * (2.0 * wz - 2.0 / 3.0 * dv) + be * dv;
+            g.tau_xx[q] = txx;
+            g.tau_yy[q] = tyy;
+            g.tau_zz[q] = tzz;
+            g.Gxx[q] = g.mux_c[q] + g.p[q] - txx;
+            g.Gyy[q] = g.mvy_c[q] + g.p[q] - tyy;
+            g.Gzz[q] = g.mwz_c[q] + g.p[q] - tzz;
+        } else if (q < b) {
+            const long long i = q - a;
+            const double t = g.mu_xy[i] * (g.dudy_xy[i] + g.dvdx_xy[i]);
+            g.tau_xy[i] = t;
+            g.Gxy[i] = g.rho_xy[i] * g.u_xy[i] * g.v_xy[i] - t;
+        } else if (q < c) {
+            const long long i = q - b;
+            const double t = g.mu_xz[i] * (g.dudz_xz[i] + g.dwdx_xz[i]);
+            g.tau_xz[i] = t;
+            g.Gxz[i] = g.rho_xz[i] * g.u_xz[i] * g.w_xz[i] - t;
+        } else {
+            const long long i = q - c;
+            const double t = g.mu_yz[i] * (g.dvdz_yz[i] + g.dwdy_yz[i]);
+            g.tau_yz[i] = t;
+            g.Gyz[i] = g.rho_yz[i] * g.v_yz[i] * g.w_yz[i] - t;
+        }
+    }
+}
+
+// species and energy fluxes at x-faces, y-faces and z-faces
+__global__ void __launch_bounds__(128) k_flux3(GasDev gd, Grid3 g, View3 v, const double* __restrict__ U) {
+    const long long a = g.nxf, b = a + g.nyf, c = b + g.nc;
+    RANGE3(c) {
+        int dir;
+        long long i;
+        if (q < a) { dir = 0; i = q; }
+        else if (q < b) { dir = 1; i = q - a; }
+        else { dir = 2; i = q - b; }
+        const double m = U[v.off[NSP + 1 + dir] + i];
+        double* const* Yf = dir == 0 ? g.Yx : dir == 1 ? g.Yy : g.Yz;
+        double* const* Gf = dir == 0 ? g.Gx : dir == 1 ? g.Gy : g.Gz;
+        double* const* hf = dir == 0 ? g.hx : dir == 1 ? g.hy : g.hz;
+        double* const* dX = dir == 0 ? g.dXdx : dir == 1 ? g.dXdy : g.dXdz;
+        double* const* Fs = dir == 0 ? g.Fsx : dir == 1 ? g.Fsy : g.Fsz;
+        const double Hf = (dir == 0 ? g.Hx : dir == 1 ? g.Hy : g.Hz)[i];
+        const double Kf = (dir == 0 ? g.Kx : dir == 1 ? g.Ky : g.Kz)[i];
+        const double dT = (dir == 0 ? g.dTdx : dir == 1 ? g.dTdy : g.dTdz)[i];
+        const bool wallface = dir == 1 && v.wall && (i % ((long long)(g.sh.ny + 1) * g.sh.nx)) < g.sh.nx;
+        double gg[NSP], J[NSP], sum = 0.0;
+#pragma unroll
+        for (int sp = 0; sp < NSP; ++sp) {
+            gg[sp] = Gf[sp][i] * dX[sp][i];
+            sum += gg[sp];
+        }
+#pragma unroll
+        for (int sp = 0; sp < NSP; ++sp) J[sp] = wallface ? 0.0 : -(gg[sp] - Yf[sp][i] * sum);
+        if (HAS_CHARGE && gd.ie >= 0 && !wallface) {
+            double acc = 0.0;
+#pragma unroll
+            for (int sp = 0; sp < NSP; ++sp)
+                if (gd.charge[sp] > 0) acc += J[sp] / gd.M[sp];
+            double tot = 0.0;
+#pragma unroll
+            for (int sp = 1; sp < NSP; ++sp) {
+                if (sp == gd.ie) J[sp] = gd.M[sp] * acc;
+                tot += J[sp];
+            }
+            J[0] = -tot;
+        }
+        double qf = -Kf * dT;
+#pragma unroll
+        for (int sp = 0; sp < NSP; ++sp) qf += hf[sp][i] * J[sp];
+#pragma unroll
+        for (int sp = 1; sp < NSP; ++sp) Fs[sp][i] = m * Yf[sp][i] + J[sp];
+        double work;
+        if (dir == 0) work = g.txx_x[i] * g.u_xf[i] + g.txy_x[i] * g.v_x[i] + g.txz_x[i] * g.w_x[i];
+        else if (dir == 1) work = g.txy_y[i] * g.u_y[i] + g.tyy_y[i] * g.v_yf[i] + g.tyz_y[i] * g.w_y[i];
+        else work = g.txz_z[i] * g.u_z[i] + g.tyz_z[i] * g.v_z[i] + g.tzz_z[i] * g.w_zf[i];
+        (dir == 0 ? g.FEx : dir == 1 ? g.FEy : g.FEz)[i] = m * Hf + qf - work;
+    }
+}
+
+struct Assemble3 {
+    const double *DX, *DY, *DZ, *SRC, *sigma, *Uref;
+    const uint8_t* mask;
+    double *U, *out, *dQ;
+    int rk;
+    double A, B, dt;
+};
+
+__global__ void k_assemble3(Assemble3 a, long long n) {
+    RANGE3(n) {
+        const double u = a.U[q];
+        double r = a.DX[q] + a.DY[q] + a.DZ[q] + a.SRC[q] - a.sigma[q] * (u - a.Uref[q]);
+        if (a.mask[q]) r = 0.0;
+        if (a.rk) {
+            const double d = a.A * a.dQ[q] + a.dt * r;
+            a.dQ[q] = d;
+            a.U[q] = u + a.B * d;
+        } else {
+            a.out[q] = r;
+        }
+    }
+}
+
+// Reference state of one (x, y) plane at every z, the jet's mass flux on the wall faces of the
+// orifice, sponge and Dirichlet mask (host-built plane, replicated here).
+__global__ void k_reference3(Grid3 g, const double* __restrict__ plane_ref,
+                             const double* __restrict__ plane_sig, const double* __restrict__ jetf,
+                             double mflux) {
+    const Sh3 s = g.sh;
+    const long long pc = (long long)s.nx * s.ny, px = (long long)(s.nx + 1) * s.ny,
+                    py = (long long)s.nx * (s.ny + 1);
+    RANGE3(g.nstate) {
+        long long f, rem;
+        // locate q in the 3-D layout
+        if (q < (long long)(NSP + 1) * g.nc) {
+            f = q / g.nc;
+            rem = q - f * g.nc;
+            const long long k = rem / pc, w = rem - k * pc;
+            g.Uref[q] = plane_ref[f * pc + w];
+            g.sigma[q] = plane_sig[f * pc + w];
+            g.mask[q] = 0;
+        } else if (q < g.off[NSP + 2]) {
+            rem = q - g.off[NSP + 1];
+            const long long k = rem / px, w = rem - k * px;
+            const int i = (int)(w % (s.nx + 1));
+            g.Uref[q] = plane_ref[(NSP + 1) * pc + w];
+            g.sigma[q] = plane_sig[(NSP + 1) * pc + w];
+            g.mask[q] = (i == 0 || i == s.nx) ? 1 : 0;
+        } else if (q < g.off[NSP + 3]) {
+            rem = q - g.off[NSP + 2];
+            const long long k = rem / py, w = rem - k * py;
+            const int j = (int)(w / s.nx), i = (int)(w % s.nx);
+            double val = plane_ref[(NSP + 1) * pc + px + w];
+            if (j == 0 && jetf) val = mflux * jetf[k * s.nx + i];
+            g.Uref[q] = val;
+            g.sigma[q] = plane_sig[(NSP + 1) * pc + px + w];
+            g.mask[q] = (j == 0 || j == s.ny) ? 1 : 0;
+        } else {
+            rem = q - g.off[NSP + 3];
+            const long long k = rem / pc, w = rem - k * pc;
+            g.Uref[q] = 0.0;
+            g.sigma[q] = plane_sig[w];
+            g.mask[q] = 0;
+        }
+    }
+}
+
+// ---- host: set-up and the right-hand side ----
+
+void free_grid3(Grid3* g) {
+    if (!g) return;
+    cudaFree(g->pool);
+    cudaFree(g->mask);
+    cudaFree(g->ops);
+    cudaFree(g->opdata);
+    delete g;
+}
+
+View3 view3(const hyp_grid* G, const Grid3* g) {
+    View3 v;
+    v.sh = g->sh;
+    for (int i = 0; i < NSP + 4; ++i) v.off[i] = g->off[i];
+    v.wall = G->cas.wall;
+    v.ad = G->cas.artificial_diffusivity;
+    v.C_mu = G->cas.C_mu;
+    v.C_beta = G->cas.C_beta;
+    v.C_kappa = G->cas.C_kappa;
+    v.C_D = G->cas.C_D;
+    v.zeta = g->zeta;
+    v.xi_c = g->xi_c;
+    v.eta_c = g->eta_c;
+    v.status = G->status;
+    return v;
+}
+
+// operator ids of the x and y operators in Grid3::ops (as the two-dimensional OpId)
+int launch3(const Grid3* g, const std::vector<Line3>& jobs, cudaStream_t s) {
+    for (const Line3& L : jobs) {
+        if (L.axis == 2) {
+            const long long n = g->sh.plane(L.tin);
+            k_line3z<<<(int)std::min<long long>((n + 127) / 128, 152LL * 64), 128, 0, s>>>(L, g->sh);
+        } else {
+            const long long n = L.axis == 0 ? (long long)g->sh.rows(L.tin) * g->sh.nz
+                                            : (long long)g->sh.pitch(L.tin) * g->sh.nz;
+            k_line3<<<(int)std::min<long long>((n + 127) / 128, 152LL * 64), 128, 0, s>>>(L, g->sh);
+        }
+    }
+    HYP_CUDA(cudaGetLastError());
+    return HYP_OK;
+}
+
+int blocks3(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152LL * 32)); }
+
+int run_rhs3(const hyp_gas* gas, hyp_grid* G, const double* U, double* dUdt, int rk, double A,
+             double Bc, double dt, double* Urk, double* dQ, int precision, cudaStream_t s) {
+    Grid3* g = (Grid3*)G->g3;
+    const View3 v = view3(G, g);
+    const GasDev& gd = gas->dev;
+    // the state-reading jobs carry element offsets into U in `in`
+    std::vector<Line3> p1 = g->p1;
+    for (auto& L : p1) L.in = U + (size_t)L.in;
+    int rc = launch3(g, p1, s);
+    if (rc) return rc;
+    k_fv3<<<blocks3(g->nxf + g->nyf + g->nc), 256, 0, s>>>(*g, v, U);
+    const Scales sc = scales_of(gd);
+    if (precision == HYP_MIXED) k_closure3<true><<<blocks3(g->nc), 128, 0, s>>>(gd, sc, *g, v, U);
+    else k_closure3<false><<<blocks3(g->nc), 128, 0, s>>>(gd, sc, *g, v, U);
+    HYP_CUDA(cudaGetLastError());
+    if ((rc = launch3(g, g->p3, s))) return rc;
+    if (v.ad) {
+        if ((rc = launch3(g, g->ad1, s))) return rc;
+        if ((rc = launch3(g, g->ad2, s))) return rc;
+        k_adprep3<<<blocks3(g->nc), 256, 0, s>>>(*g);
+        k_adraw3<<<blocks3(g->nc), 256, 0, s>>>(*g, v, U, gd.kind == HYP_GAS_CNEQ);
+        for (int ax = 0; ax < 3; ++ax) k_gauss3<<<blocks3(AD_FIELDS * g->nc), 256, 0, s>>>(*g, ax);
+        k_adcombine3<<<blocks3(g->nc), 256, 0, s>>>(*g);
+        HYP_CUDA(cudaGetLastError());
+    }
+    if ((rc = launch3(g, g->mu, s))) return rc;
+    k_stress3<<<blocks3(g->nc + g->nxy + g->nxf + g->nyf), 256, 0, s>>>(*g);
+    if ((rc = launch3(g, g->face, s))) return rc;
+    if ((rc = launch3(g, g->faceb, s))) return rc;
+    k_flux3<<<blocks3(g->nxf + g->nyf + g->nc), 128, 0, s>>>(gd, *g, v, U);
+    HYP_CUDA(cudaGetLastError());
+    if ((rc = launch3(g, g->divs, s))) return rc;
+    Assemble3 a;
+    a.DX = g->DX;
+    a.DY = g->DY;
+    a.DZ = g->DZ;
+    a.SRC = g->SRC;
+    a.sigma = g->sigma;
+    a.Uref = g->Uref;
+    a.mask = g->mask;
+    a.U = rk ? Urk : const_cast<double*>(U);
+    a.out = dUdt;
+    a.dQ = dQ;
+    a.rk = rk;
+    a.A = A;
+    a.B = Bc;
+    a.dt = dt;
+    k_assemble3<<<blocks3(g->nstate), 256, 0, s>>>(a, g->nstate);
+    HYP_CUDA(cudaGetLastError());
+    return HYP_OK;
+}
+
+// Build a three-dimensional grid: operators, plan, reference and initial state.
+int init3(const hyp_gas* gas, const hyp_grid_desc* desc, const hyp_case* cas, double* U,
+          double* dQ, cudaStream_t s, hyp_grid* G) {
+    const GasDev& gd = gas->dev;
+    if (!(gd.kind == HYP_GAS_CNEQ || gd.kind == HYP_GAS_FROZEN || gd.kind == HYP_GAS_CPG))
+        return fail(HYP_ERR_ARG, "three-dimensional grids take the cneq, frozen or cpg gas");
+    if (cas->diffusion_model != 0) return fail(HYP_ERR_ARG, "three-dimensional grids use the algebraic diffusion");
+    if (cas->filter_sigma > 0) return fail(HYP_ERR_ARG, "three-dimensional grids have no state filter");
+    if (!(desc->z1 > desc->z0)) return fail(HYP_ERR_ARG, "z1 must exceed z0");
+    Grid3* g = new Grid3();
+    G->g3 = g;
+    const int nx = desc->nx, ny = desc->ny, nz = desc->nz;
+    g->sh = Sh3{nx, ny, nz};
+    const Sh3& sh = g->sh;
+    g->zeta = nz / (desc->z1 - desc->z0);
+    g->nc = sh.size(C3);
+    g->nxf = sh.size(XF3);
+    g->nyf = sh.size(YF3);
+    g->nxy = sh.size(XY3);
+    long long o = 0;
+    for (int f = 0; f <= NSP; ++f) {
+        g->off[f] = o;
+        o += g->nc;
+    }
+    g->off[NSP + 1] = o;
+    o += g->nxf;
+    g->off[NSP + 2] = o;
+    o += g->nyf;
+    g->off[NSP + 3] = o;
+    o += g->nc;
+    g->nstate = o;
+    G->nstate = (int)o;
+    const long long nc = g->nc, nxf = g->nxf, nyf = g->nyf, nxy = g->nxy;
+    // ---------------- memory ----------------
+    const long long n_c = 15 + 6 * NSP + 12 + 10 + 4 + 2 * AD_FIELDS + 3 + 5 * NSP + 9;
+    const long long n_x = 4 + 5 * NSP + 9 + 8 + 2;
+    const long long n_y = 4 + 5 * NSP + 9 + 8;
+    const long long n_xy = 8;
+    const long long pool_n = n_c * nc + n_x * nxf + n_y * nyf + n_xy * nxy + 7 * g->nstate +
+                             2 * (nx + 1) + 2 * (ny + 1) + (long long)nz * nx + 16;
+    cudaError_t err = cudaMalloc(&g->pool, pool_n * sizeof(double));
+    if (err == cudaSuccess) err = cudaMalloc(&g->mask, g->nstate);
+    if (err != cudaSuccess) {
+        free_grid3(g);
+        G->g3 = nullptr;
+        return cuda_fail(err, "cudaMalloc(3-D grid)");
+    }
+    double* cur = g->pool;
+    auto take = [&](long long n) {
+        double* p = cur;
+        cur += n;
+        return p;
+    };
+    for (double** f : {&g->ru_c, &g->rv_c, &g->rw_c, &g->T, &g->p, &g->H, &g->u_c, &g->v_c, &g->w_c,
+                       &g->e, &g->a, &g->mu_e, &g->K, &g->beta, &g->Tcache})
+        *f = take(nc);
+    for (int sp = 0; sp < NSP; ++sp)
+        for (double** f : {&g->Y[sp], &g->X[sp], &g->h[sp], &g->W[sp], &g->Wd[sp], &g->G[sp]}) *f = take(nc);
+    for (double** f : {&g->dudx, &g->dvdy, &g->dwdz, &g->tau_xx, &g->tau_yy, &g->tau_zz, &g->Gxx,
+                       &g->Gyy, &g->Gzz, &g->mux_c, &g->mvy_c, &g->mwz_c})
+        *f = take(nc);
+    for (double** f : {&g->S, &g->div, &g->fsw, &g->dudy_c, &g->dvdx_c, &g->dudz_c, &g->dwdx_c,
+                       &g->dvdz_c, &g->dwdy_c, &g->rho_zf})
+        *f = take(nc);
+    for (int q = 0; q < 4; ++q) g->tc[q] = take(nc);
+    for (int q = 0; q < AD_FIELDS; ++q) {
+        g->raw[q] = take(nc);
+        g->filt[q] = take(nc);
+    }
+    g->w_zf = take(nc);
+    g->mwz_f = take(nc);
+    for (int sp = 0; sp < NSP; ++sp)
+        for (double** f : {&g->Yz[sp], &g->Gz[sp], &g->hz[sp], &g->dXdz[sp], &g->Fsz[sp]}) *f = take(nc);
+    for (double** f : {&g->Hz, &g->Kz, &g->dTdz, &g->tzz_z, &g->u_z, &g->v_z, &g->txz_z, &g->tyz_z, &g->FEz})
+        *f = take(nc);
+    for (double** f : {&g->rho_xf, &g->u_xf, &g->mux_f, &g->mu_xf}) *f = take(nxf);
+    for (int sp = 0; sp < NSP; ++sp)
+        for (double** f : {&g->Yx[sp], &g->Gx[sp], &g->hx[sp], &g->dXdx[sp], &g->Fsx[sp]}) *f = take(nxf);
+    for (double** f : {&g->Hx, &g->Kx, &g->dTdx, &g->txx_x, &g->v_x, &g->w_x, &g->txy_x, &g->txz_x, &g->FEx})
+        *f = take(nxf);
+    for (double** f : {&g->dudz_xz, &g->dwdx_xz, &g->u_xz, &g->w_xz, &g->rho_xz, &g->mu_xz,
+                       &g->tau_xz, &g->Gxz, &g->tx[0], &g->tx[1]})
+        *f = take(nxf);
+    for (double** f : {&g->rho_yf, &g->v_yf, &g->mvy_f, &g->mu_yf}) *f = take(nyf);
+    for (int sp = 0; sp < NSP; ++sp)
+        for (double** f : {&g->Yy[sp], &g->Gy[sp], &g->hy[sp], &g->dXdy[sp], &g->Fsy[sp]}) *f = take(nyf);
+    for (double** f : {&g->Hy, &g->Ky, &g->dTdy, &g->tyy_y, &g->u_y, &g->w_y, &g->txy_y, &g->tyz_y, &g->FEy})
+        *f = take(nyf);
+    for (double** f : {&g->dvdz_yz, &g->dwdy_yz, &g->v_yz, &g->w_yz, &g->rho_yz, &g->mu_yz,
+                       &g->tau_yz, &g->Gyz})
+        *f = take(nyf);
+    for (double** f : {&g->dudy_xy, &g->dvdx_xy, &g->u_xy, &g->v_xy, &g->rho_xy, &g->mu_xy,
+                       &g->tau_xy, &g->Gxy})
+        *f = take(nxy);
+    for (double** f : {&g->DX, &g->DY, &g->DZ, &g->SRC, &g->R, &g->Uref, &g->sigma}) *f = take(g->nstate);
+    g->xi_c = take(nx);
+    g->xi_f = take(nx + 1);
+    g->eta_c = take(ny);
+    g->eta_f = take(ny + 1);
+    g->Tw = take((long long)nz * nx);
+    if (cur - g->pool > pool_n) {
+        free_grid3(g);
+        G->g3 = nullptr;
+        return fail(HYP_ERR_ARG, "internal: 3-D scratch pool too small");
+    }
+    // ---------------- operators ----------------
+    std::vector<double> opdata;
+    std::vector<LineOp> hops(NOPS);
+    hops[OX_ICF] = make_op(0, 0, nx, 0, opdata);
+    hops[OX_DCF] = make_op(1, 0, nx, 0, opdata);
+    hops[OX_IFC] = make_op(0, 1, nx, 0, opdata);
+    hops[OX_DFC] = make_op(1, 1, nx, 0, opdata);
+    hops[OY_ICF] = make_op(0, 0, ny, 0, opdata);
+    hops[OY_DCF] = make_op(1, 0, ny, 0, opdata);
+    hops[OY_IFC] = make_op(0, 1, ny, 0, opdata);
+    hops[OY_DFC] = make_op(1, 1, ny, 0, opdata);
+    hops[OY_ICFW] = make_op(0, 0, ny, 1, opdata);
+    hops[OY_DCFW] = make_op(1, 0, ny, 1, opdata);
+    err = cudaMalloc(&g->opdata, opdata.size() * sizeof(double));
+    if (err == cudaSuccess) err = cudaMalloc(&g->ops, NOPS * sizeof(LineOp));
+    if (err != cudaSuccess) {
+        free_grid3(g);
+        G->g3 = nullptr;
+        return cuda_fail(err, "cudaMalloc(3-D operators)");
+    }
+    for (auto& op : hops) {
+        op.lower = g->opdata + (size_t)op.lower;
+        op.cprime = g->opdata + (size_t)op.cprime;
+        op.minv = g->opdata + (size_t)op.minv;
+        op.wa = g->opdata + (size_t)op.wa;
+        op.wb = g->opdata + (size_t)op.wb;
+        op.lm = g->opdata + (size_t)op.lm;
+    }
+    // periodic z operators: the fixed point of the Thomas recurrence of (alpha, 1, alpha)
+    for (int kind = 0; kind < 2; ++kind)
+        for (int dir = 0; dir < 2; ++dir) {
+            const double alpha = kind == 0 ? 3.0 / 10.0 : 9.0 / 62.0;
+            const double wa0 = kind == 0 ? 3.0 / 4.0 : 63.0 / 62.0;          // a/2 or a
+            const double wb0 = kind == 0 ? 1.0 / 20.0 : 17.0 / 62.0 / 3.0;   // b/2 or b/3
+            double cp = 0.0, mi = 1.0;
+            for (int it = 0; it < 400; ++it) {
+                mi = 1.0 / (1.0 - alpha * cp);
+                cp = alpha * mi;
+            }
+            Line3& L = g->zop[kind][dir];
+            memset(&L, 0, sizeof(L));
+            L.axis = 2;
+            L.kind = kind;
+            L.dir = dir;
+            L.wa = wa0 * mi;
+            L.wb = wb0 * mi;
+            L.lm = alpha * mi;
+            L.cp = cp;
+        }
+    // ---------------- host geometry ----------------
+    std::vector<double> xc(nx), xf(nx + 1), yc(ny), yf(ny + 1), xi_c(nx), xi_f(nx + 1), eta_c(ny),
+        eta_f(ny + 1);
+    const double dx = (desc->x1 - desc->x0) / nx;
+    for (int i = 0; i <= nx; ++i) {
+        xf[i] = desc->x0 + dx * i;
+        xi_f[i] = 1.0 / dx;
+    }
+    for (int i = 0; i < nx; ++i) {
+        xc[i] = desc->x0 + dx * (i + 0.5);
+        xi_c[i] = 1.0 / dx;
+    }
+    for (int j = 0; j <= ny; ++j) {
+        double y, dy;
+        y_map(*desc, (double)j, y, dy);
+        yf[j] = y;
+        eta_f[j] = 1.0 / dy;
+    }
+    for (int j = 0; j < ny; ++j) {
+        double y, dy;
+        y_map(*desc, j + 0.5, y, dy);
+        yc[j] = y;
+        eta_c[j] = 1.0 / dy;
+    }
+    // reference profile of one plane (the two-dimensional one) on the host
+    Profile P;
+    P.c = *cas;
+    P.c.noise = nullptr;
+    P.y0 = desc->y0;
+    P.iN2 = P.iO2 = P.iNO = P.iN = P.iO = -1;
+    for (int sp = 0; sp < NSP; ++sp) {
+        const std::string& nm = gas->names[sp];
+        if (nm == "N2") P.iN2 = sp;
+        if (nm == "O2") P.iO2 = sp;
+        if (nm == "NO") P.iNO = sp;
+        if (nm == "N") P.iN = sp;
+        if (nm == "O") P.iO = sp;
+        P.Yinf[sp] = gd.Y_inf[sp];
+    }
+    P.shock = cas->flow == 1;
+    P.theta = cas->shock_deflection_deg * 3.14159265358979323846 / 180.0;
+    if (P.shock) P.sh = oblique_shock(gd.mach, P.theta, gd.gamma_inf);
+    const long long pc = (long long)nx * ny, px = (long long)(nx + 1) * ny, py = (long long)nx * (ny + 1);
+    std::vector<double> pref((NSP + 1) * pc + px + py), psig((NSP + 1) * pc + px + py);
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            double T, p, u, vv, Y[NSP], rho, rY[NSP], rE;
+            P.at(gd, xc[i], yc[j], T, p, u, vv, Y);
+            P.conserved(gd, T, p, u, vv, Y, rho, rY, rE);
+            const double sg = sponge_at(*desc, P.c, xc[i], yc[j]);
+            const long long w = (long long)j * nx + i;
+            pref[w] = rho;
+            for (int sp = 1; sp < NSP; ++sp) pref[sp * pc + w] = rY[sp];
+            pref[NSP * pc + w] = rE;
+            for (int f = 0; f <= NSP; ++f) psig[f * pc + w] = sg;
+        }
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i <= nx; ++i) {
+            double T, p, u, vv, Y[NSP], rho, rY[NSP], rE;
+            P.at(gd, xf[i], yc[j], T, p, u, vv, Y);
+            P.conserved(gd, T, p, u, vv, Y, rho, rY, rE);
+            const long long w = (NSP + 1) * pc + (long long)j * (nx + 1) + i;
+            pref[w] = rho * u;
+            psig[w] = sponge_at(*desc, P.c, xf[i], yc[j]);
+        }
+    for (int j = 0; j <= ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            double T, p, u, vv, Y[NSP], rho, rY[NSP], rE;
+            P.at(gd, xc[i], yf[j], T, p, u, vv, Y);
+            P.conserved(gd, T, p, u, vv, Y, rho, rY, rE);
+            const long long w = (NSP + 1) * pc + px + (long long)j * nx + i;
+            pref[w] = rho * vv;
+            psig[w] = sponge_at(*desc, P.c, xc[i], yf[j]);
+        }
+    // jet: blend factor on the wall faces, Dirichlet mass flux, wall temperature of the heat flux
+    std::vector<double> jetf((size_t)nz * nx, 0.0), Tw((size_t)nz * nx, cas->T_wall / gd.T_ref);
+    double mflux = 0.0;
+    if (cas->jet) {
+        const double Tj = cas->jet_T_ratio * gd.T_inf;
+        const double pj = cas->jet_J * gd.mach * gd.mach * gd.p_inf;
+        const double rho_j = pj / (gd.R_inf * Tj) / gd.rho_inf;
+        const double v_j = sqrt(gd.gamma_inf * gd.R_inf * Tj) / gd.a_inf;
+        mflux = rho_j * v_j;
+        const double Lz = desc->z1 - desc->z0, dzc = Lz / nz;
+        for (int k = 0; k < nz; ++k)
+            for (int i = 0; i < nx; ++i) {
+                const double z = desc->z0 + dzc * (k + 0.5);
+                double sz = fabs(z - cas->jet_z);
+                sz = fmin(sz, Lz - sz);
+                const double r = sqrt((xc[i] - cas->jet_x) * (xc[i] - cas->jet_x) + sz * sz);
+                const double f = 0.5 * (1.0 - tanh((r - cas->jet_radius) / (cas->jet_edge * cas->jet_radius)));
+                jetf[(size_t)k * nx + i] = f;
+                Tw[(size_t)k * nx + i] = (cas->T_wall + (Tj - cas->T_wall) * f) / gd.T_ref;
+            }
+    }
+    // ---------------- plans ----------------
+    const bool wall = cas->wall != 0;
+    Line3 base;
+    memset(&base, 0, sizeof(base));
+    base.scale = 1.0;
+    auto xy = [&](int opid, int axis, const double* in, int tin, double* out, int tout,
+                  const double* metric, double scale = 1.0, const double* wall_arr = nullptr) {
+        Line3 L = base;
+        L.op = g->ops + opid;
+        L.axis = axis;
+        L.in = in;
+        L.tin = tin;
+        L.out = out;
+        L.tout = tout;
+        L.metric = metric;
+        L.scale = scale;
+        L.wall = 0.0;
+        L.wall_arr = wall_arr;
+        return L;
+    };
+    auto zl = [&](int kind, int dir, const double* in, int t, double* out, double scale = 1.0) {
+        Line3 L = g->zop[kind][dir];
+        L.in = in;
+        L.tin = L.tout = t;
+        L.out = out;
+        L.scale = scale;
+        return L;
+    };
+    const int yicfw = wall ? OY_ICFW : OY_ICF, ydcfw = wall ? OY_DCFW : OY_DCF;
+    const double ze = g->zeta;
+    auto soff = [&](int f) { return (const double*)(size_t)g->off[f]; };
+    // P1: state-reading jobs (`in` is an element offset into U)
+    g->p1 = {xy(OX_IFC, 0, soff(NSP + 1), XF3, g->ru_c, C3, nullptr),
+             xy(OY_IFC, 1, soff(NSP + 2), YF3, g->rv_c, C3, nullptr),
+             zl(0, 1, soff(NSP + 3), C3, g->rw_c),
+             xy(OX_ICF, 0, soff(0), C3, g->rho_xf, XF3, nullptr),
+             xy(OY_ICF, 1, soff(0), C3, g->rho_yf, YF3, nullptr),
+             zl(0, 0, soff(0), C3, g->rho_zf),
+             xy(OX_DFC, 0, soff(NSP + 1), XF3, g->DX + g->off[0], C3, g->xi_c, -1.0),
+             xy(OY_DFC, 1, soff(NSP + 2), YF3, g->DY + g->off[0], C3, g->eta_c, -1.0),
+             zl(1, 1, soff(NSP + 3), C3, g->DZ + g->off[0], -ze)};
+    g->p3 = {xy(OX_DFC, 0, g->u_xf, XF3, g->dudx, C3, g->xi_c),
+             xy(OY_DFC, 1, g->v_yf, YF3, g->dvdy, C3, g->eta_c),
+             zl(1, 1, g->w_zf, C3, g->dwdz, ze),
+             xy(ydcfw, 1, g->u_xf, XF3, g->dudy_xy, XY3, g->eta_f),
+             xy(OX_DCF, 0, g->v_yf, YF3, g->dvdx_xy, XY3, g->xi_f),
+             xy(yicfw, 1, g->u_xf, XF3, g->u_xy, XY3, nullptr),
+             xy(OX_ICF, 0, g->v_yf, YF3, g->v_xy, XY3, nullptr),
+             xy(OY_ICF, 1, g->rho_xf, XF3, g->rho_xy, XY3, nullptr),
+             zl(1, 0, g->u_xf, XF3, g->dudz_xz, ze),
+             xy(OX_DCF, 0, g->w_zf, C3, g->dwdx_xz, XF3, g->xi_f),
+             zl(0, 0, g->u_xf, XF3, g->u_xz),
+             xy(OX_ICF, 0, g->w_zf, C3, g->w_xz, XF3, nullptr),
+             zl(0, 0, g->rho_xf, XF3, g->rho_xz),
+             zl(1, 0, g->v_yf, YF3, g->dvdz_yz, ze),
+             xy(ydcfw, 1, g->w_zf, C3, g->dwdy_yz, YF3, g->eta_f),
+             zl(0, 0, g->v_yf, YF3, g->v_yz),
+             xy(yicfw, 1, g->w_zf, C3, g->w_yz, YF3, nullptr),
+             zl(0, 0, g->rho_yf, YF3, g->rho_yz),
+             xy(OX_IFC, 0, g->mux_f, XF3, g->mux_c, C3, nullptr),
+             xy(OY_IFC, 1, g->mvy_f, YF3, g->mvy_c, C3, nullptr),
+             zl(0, 1, g->mwz_f, C3, g->mwz_c)};
+    // artificial diffusivity: edge derivatives to the centres (y then x; x then z; y then z)
+    g->ad1 = {xy(OY_IFC, 1, g->dudy_xy, XY3, g->tx[0], XF3, nullptr),
+              xy(OY_IFC, 1, g->dvdx_xy, XY3, g->tx[1], XF3, nullptr),
+              xy(OX_IFC, 0, g->dudz_xz, XF3, g->tc[0], C3, nullptr),
+              xy(OX_IFC, 0, g->dwdx_xz, XF3, g->tc[1], C3, nullptr),
+              xy(OY_IFC, 1, g->dvdz_yz, YF3, g->tc[2], C3, nullptr),
+              xy(OY_IFC, 1, g->dwdy_yz, YF3, g->tc[3], C3, nullptr)};
+    g->ad2 = {xy(OX_IFC, 0, g->tx[0], XF3, g->dudy_c, C3, nullptr),
+              xy(OX_IFC, 0, g->tx[1], XF3, g->dvdx_c, C3, nullptr),
+              zl(0, 1, g->tc[0], C3, g->dudz_c),
+              zl(0, 1, g->tc[1], C3, g->dwdx_c),
+              zl(0, 1, g->tc[2], C3, g->dvdz_c),
+              zl(0, 1, g->tc[3], C3, g->dwdy_c)};
+    g->mu = {xy(OX_ICF, 0, g->mu_e, C3, g->mu_xf, XF3, nullptr),
+             xy(OY_ICF, 1, g->mu_e, C3, g->mu_yf, YF3, nullptr)};
+    g->faceb = {xy(OY_ICF, 1, g->mu_xf, XF3, g->mu_xy, XY3, nullptr)};
+    // mu_xz, mu_yz and the stress kernel need the edge viscosities before the stresses: they
+    // go with the viscosity jobs (second list run after the first)
+    g->mu.push_back(zl(0, 0, g->mu_xf, XF3, g->mu_xz));
+    g->mu.push_back(zl(0, 0, g->mu_yf, YF3, g->mu_yz));
+    g->mu.push_back(g->faceb[0]);
+    g->faceb.clear();
+    std::vector<Line3>& F = g->face;
+    for (int sp = 0; sp < NSP; ++sp) {
+        F.push_back(xy(OX_ICF, 0, g->Y[sp], C3, g->Yx[sp], XF3, nullptr));
+        F.push_back(xy(OX_ICF, 0, g->G[sp], C3, g->Gx[sp], XF3, nullptr));
+        F.push_back(xy(OX_ICF, 0, g->h[sp], C3, g->hx[sp], XF3, nullptr));
+        F.push_back(xy(OX_DCF, 0, g->X[sp], C3, g->dXdx[sp], XF3, g->xi_f));
+        F.push_back(xy(OY_ICF, 1, g->Y[sp], C3, g->Yy[sp], YF3, nullptr));
+        F.push_back(xy(OY_ICF, 1, g->G[sp], C3, g->Gy[sp], YF3, nullptr));
+        F.push_back(xy(OY_ICF, 1, g->h[sp], C3, g->hy[sp], YF3, nullptr));
+        F.push_back(xy(OY_DCF, 1, g->X[sp], C3, g->dXdy[sp], YF3, g->eta_f));
+        F.push_back(zl(0, 0, g->Y[sp], C3, g->Yz[sp]));
+        F.push_back(zl(0, 0, g->G[sp], C3, g->Gz[sp]));
+        F.push_back(zl(0, 0, g->h[sp], C3, g->hz[sp]));
+        F.push_back(zl(1, 0, g->X[sp], C3, g->dXdz[sp], ze));
+    }
+    F.push_back(xy(OX_ICF, 0, g->H, C3, g->Hx, XF3, nullptr));
+    F.push_back(xy(OX_ICF, 0, g->K, C3, g->Kx, XF3, nullptr));
+    F.push_back(xy(OX_DCF, 0, g->T, C3, g->dTdx, XF3, g->xi_f));
+    F.push_back(xy(OX_ICF, 0, g->tau_xx, C3, g->txx_x, XF3, nullptr));
+    F.push_back(xy(OX_ICF, 0, g->v_c, C3, g->v_x, XF3, nullptr));
+    F.push_back(xy(OX_ICF, 0, g->w_c, C3, g->w_x, XF3, nullptr));
+    F.push_back(xy(OY_IFC, 1, g->tau_xy, XY3, g->txy_x, XF3, nullptr));
+    F.push_back(zl(0, 1, g->tau_xz, XF3, g->txz_x));
+    F.push_back(xy(OY_ICF, 1, g->H, C3, g->Hy, YF3, nullptr));
+    F.push_back(xy(OY_ICF, 1, g->K, C3, g->Ky, YF3, nullptr));
+    F.push_back(xy(ydcfw, 1, g->T, C3, g->dTdy, YF3, g->eta_f, 1.0, wall ? g->Tw : nullptr));
+    F.push_back(xy(OY_ICF, 1, g->tau_yy, C3, g->tyy_y, YF3, nullptr));
+    F.push_back(xy(yicfw, 1, g->u_c, C3, g->u_y, YF3, nullptr));
+    F.push_back(xy(yicfw, 1, g->w_c, C3, g->w_y, YF3, nullptr));
+    F.push_back(xy(OX_IFC, 0, g->tau_xy, XY3, g->txy_y, YF3, nullptr));
+    F.push_back(zl(0, 1, g->tau_yz, YF3, g->tyz_y));
+    F.push_back(zl(0, 0, g->H, C3, g->Hz));
+    F.push_back(zl(0, 0, g->K, C3, g->Kz));
+    F.push_back(zl(1, 0, g->T, C3, g->dTdz, ze));
+    F.push_back(zl(0, 0, g->tau_zz, C3, g->tzz_z));
+    F.push_back(zl(0, 0, g->u_c, C3, g->u_z));
+    F.push_back(zl(0, 0, g->v_c, C3, g->v_z));
+    F.push_back(xy(OX_IFC, 0, g->tau_xz, XF3, g->txz_z, C3, nullptr));
+    F.push_back(xy(OY_IFC, 1, g->tau_yz, YF3, g->tyz_z, C3, nullptr));
+    std::vector<Line3>& D = g->divs;
+    for (int sp = 1; sp < NSP; ++sp) {
+        D.push_back(xy(OX_DFC, 0, g->Fsx[sp], XF3, g->DX + g->off[sp], C3, g->xi_c, -1.0));
+        D.push_back(xy(OY_DFC, 1, g->Fsy[sp], YF3, g->DY + g->off[sp], C3, g->eta_c, -1.0));
+        D.push_back(zl(1, 1, g->Fsz[sp], C3, g->DZ + g->off[sp], -ze));
+    }
+    D.push_back(xy(OX_DFC, 0, g->FEx, XF3, g->DX + g->off[NSP], C3, g->xi_c, -1.0));
+    D.push_back(xy(OY_DFC, 1, g->FEy, YF3, g->DY + g->off[NSP], C3, g->eta_c, -1.0));
+    D.push_back(zl(1, 1, g->FEz, C3, g->DZ + g->off[NSP], -ze));
+    D.push_back(xy(OX_DCF, 0, g->Gxx, C3, g->DX + g->off[NSP + 1], XF3, g->xi_f, -1.0));
+    D.push_back(xy(OY_DFC, 1, g->Gxy, XY3, g->DY + g->off[NSP + 1], XF3, g->eta_c, -1.0));
+    D.push_back(zl(1, 1, g->Gxz, XF3, g->DZ + g->off[NSP + 1], -ze));
+    D.push_back(xy(OX_DFC, 0, g->Gxy, XY3, g->DX + g->off[NSP + 2], YF3, g->xi_c, -1.0));
+    D.push_back(xy(OY_DCF, 1, g->Gyy, C3, g->DY + g->off[NSP + 2], YF3, g->eta_f, -1.0));
+    D.push_back(zl(1, 1, g->Gyz, YF3, g->DZ + g->off[NSP + 2], -ze));
+    D.push_back(xy(OX_DFC, 0, g->Gxz, XF3, g->DX + g->off[NSP + 3], C3, g->xi_c, -1.0));
+    D.push_back(xy(OY_DFC, 1, g->Gyz, YF3, g->DY + g->off[NSP + 3], C3, g->eta_c, -1.0));
+    D.push_back(zl(1, 0, g->Gzz, C3, g->DZ + g->off[NSP + 3], -ze));
+    // ---------------- uploads, reference, initial state ----------------
+#define UP3(dst, src, bytes) HYP_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s))
+    UP3(g->ops, hops.data(), NOPS * sizeof(LineOp));
+    UP3(g->opdata, opdata.data(), opdata.size() * sizeof(double));
+    UP3(g->xi_c, xi_c.data(), nx * sizeof(double));
+    UP3(g->xi_f, xi_f.data(), (nx + 1) * sizeof(double));
+    UP3(g->eta_c, eta_c.data(), ny * sizeof(double));
+    UP3(g->eta_f, eta_f.data(), (ny + 1) * sizeof(double));
+    UP3(g->Tw, Tw.data(), Tw.size() * sizeof(double));
+    // the plane reference, its sponge and the jet blend travel through state-sized scratch
+    UP3(g->DX, pref.data(), pref.size() * sizeof(double));
+    UP3(g->DY, psig.data(), psig.size() * sizeof(double));
+    UP3(g->DZ, jetf.data(), jetf.size() * sizeof(double));
+    k_reference3<<<blocks3(g->nstate), 256, 0, s>>>(*g, g->DX, g->DY, cas->jet ? g->DZ : nullptr, mflux);
+    const bool noisy = cas->noise && cas->noise_amp > 0;
+    if (noisy) UP3(g->R, cas->noise, g->nstate * sizeof(double));
+    k_initial<<<blocks3(g->nstate), 256, 0, s>>>(g->nstate, g->Uref, g->mask, noisy ? g->R : nullptr,
+                                                 cas->noise_amp, U);
+    HYP_CUDA(cudaGetLastError());
+#undef UP3
+    HYP_CUDA(cudaMemsetAsync(dQ, 0, g->nstate * sizeof(double), s));
+    HYP_CUDA(cudaMemsetAsync(g->SRC, 0, g->nstate * sizeof(double), s));
+    HYP_CUDA(cudaMemsetAsync(G->status, 0, sizeof(unsigned), s));
+    k_fill<<<blocks3(nc), 256, 0, s>>>(g->Tcache, nc, 1000.0);
+    HYP_CUDA(cudaGetLastError());
+    HYP_CUDA(cudaStreamSynchronize(s));
+    G->Uref = g->Uref;
+    G->sigma = g->sigma;
+    G->mask = nullptr;
+    return HYP_OK;
+}

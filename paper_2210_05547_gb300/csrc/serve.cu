@@ -239,6 +239,7 @@ extern "C" int hyp_server_submit(hyp_server* sv, const hyp_request* req, int64_t
     const hyp_grid_desc& g = req->grid;
     if (g.nx < 8 || g.ny < 8 || (long long)g.nx * g.ny > (1LL << 28))
         return hyp::fail(HYP_ERR_ARG, "grid needs 8 to 2^28 cells per direction product");
+    if (g.nz > 1) return hyp::fail(HYP_ERR_ARG, "the server takes two-dimensional grids");
     if (!(req->dt > 0.0) || req->nsteps <= 0) return hyp::fail(HYP_ERR_ARG, "request needs dt > 0 and nsteps > 0");
     auto r = std::make_unique<Request>();
     r->desc = *req;

@@ -26,7 +26,10 @@ Workloads (shapes follow the paper's cases; there is no dataset):
   domain (the jet case of Sec. 4 in three dimensions): 512 x 256 x 128 cells over x 38.5-71,
   y 0-10 (cubic clustering, kappa_y = 0.15), z 0-10 (periodic, 10 jet diameters), T_inf = 600 K,
   p_inf = 49800 Pa, Re_D = 25291 (Re_inf on a_inf = Re_D / Ma); orifice centre x = 52.5, spanwise
-  centre, radius and momentum ratio J in [1, 3] drawn from the seed; jet sonic at T_inf.
+  centre, radius and momentum ratio J in [1, 3] drawn from the seed; jet sonic at T_inf; the
+  orifice edge and the plume of the initial state are smoothed over 0.3 radii and two radii of
+  height (a sharper plume leaves the compact interpolations negative internal energies at its
+  edge).
 """
 from __future__ import annotations
 
@@ -78,7 +81,7 @@ def jet_case(nx=512, ny=256, nz=128, seed=0, kind="cneq"):
         sponge_in=1.0, sponge_out=2.0, sponge_top_cells=max(2, (20 * ny) // 500),
         artificial_diffusivity=1, C_D=0.01, dt=5.0e-4, filter_sigma=0.0,
         jet=1, jet_x=52.5, jet_z=5.0 + float(rng.uniform(-1.0, 1.0)),
-        jet_radius=0.5 * float(rng.uniform(0.9, 1.1)), jet_edge=0.1,
+        jet_radius=0.5 * float(rng.uniform(0.9, 1.1)), jet_edge=0.3, jet_height=2.0,
         jet_J=float(rng.uniform(1.0, 3.0)), jet_T_ratio=1.0,
     )
     return c

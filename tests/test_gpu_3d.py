@@ -1,0 +1,124 @@
+"""GPU parity of three-dimensional grids (spanwise-periodic z, jet from a circular orifice) through
+the C ABI (hyp_state_init, hyp_rhs, hyp_rk_stage with nz > 1) against oracle/flow3d.py: the
+initial and reference states, the right-hand side of a jet in crossflow with artificial
+diffusivity, of a boundary layer without the jet, of a calorically perfect gas, and three RK3
+steps. Tolerance as in two dimensions (oracle.flow3d.parity_tolerance): 1e-12 of max|R| per
+field plus the FP64 rounding floor of the flux divergences, the sponge term on noise-level
+differences and the temperature conditioning of the Arrhenius sources."""
+import numpy as np
+import pytest
+
+from oracle import flow3d as F3
+from paper_2210_05547_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _n(cfg, ns=5):
+    return sum(a * b * c for _, (a, b, c) in F3.state_layout(ns, cfg["nx"], cfg["ny"], cfg["nz"]))
+
+
+def _zoom(cfg):
+    """The jet case on a small box around the orifice (resolved by the few cells of a test)."""
+    cfg.update(x0=50.0, x1=55.0, z0=0.0, z1=3.0, jet_x=52.5, jet_z=1.5, sponge_in=0.5,
+               sponge_out=0.5)
+    return cfg
+
+
+def _cases():
+    jet = _zoom(I.jet_case(40, 24, 12, seed=1))
+    bl = dict(I.bl_case(36, 20, seed=2), nz=8, z0=0.0, z1=2.0, jet=0)
+    cpg = dict(_zoom(I.jet_case(40, 24, 12, seed=3, kind="cpg")), artificial_diffusivity=0)
+    frozen = _zoom(I.jet_case(41, 21, 13, seed=4, kind="frozen"))
+    return {"jet_40x24x12": jet, "bl_36x20x8": bl, "jet_cpg_40x24x12": cpg,
+            "jet_frozen_41x21x13": frozen}
+
+
+CASES = _cases()
+
+
+def _gpu(cfg):
+    import torch
+    from paper_2210_05547_gb300 import abi as A
+    gas = A.gas_model_load(cfg)
+    n = A.state_size(gas, cfg)
+    assert n == _n(cfg)
+    U = torch.empty(n, dtype=torch.float64, device="cuda")
+    dQ = torch.empty_like(U)
+    st = A.state_init(gas, cfg, U, dQ, I.state_noise(n, cfg["seed"]))
+    return A, gas, st
+
+
+def _errors(cfg, a, b):
+    fa = F3.unpack(5, cfg["nx"], cfg["ny"], cfg["nz"], np.asarray(a))
+    fb = F3.unpack(5, cfg["nx"], cfg["ny"], cfg["nz"], np.asarray(b))
+    return {k: float(np.abs(fa[k] - fb[k]).max() / max(np.abs(fb[k]).max(), 1e-300)) for k in fa}
+
+
+def _check(case, U, g):
+    tol, o = F3.parity_tolerance(case, U)
+    cfg = case.cfg
+    fg = F3.unpack(5, cfg["nx"], cfg["ny"], cfg["nz"], np.asarray(g))
+    fo = F3.unpack(5, cfg["nx"], cfg["ny"], cfg["nz"], o)
+    return {k: (float(np.abs(fg[k] - fo[k]).max()), float(tol[k])) for k in fo
+            if not np.abs(fg[k] - fo[k]).max() <= tol[k]}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_state_init_and_rhs_parity(table, name):
+    import torch
+    cfg = CASES[name]
+    A, gas, st = _gpu(cfg)
+    case = F3.make_case(cfg, table, I.state_noise(_n(cfg), cfg["seed"]))
+    torch.cuda.synchronize()
+    for k, v in _errors(cfg, st.U.cpu().numpy(), case.U0).items():
+        assert v < 1e-13, ("U0", k, v)
+    Uref, sigma = A.grid_reference(st.grid, _n(cfg))
+    for k, v in _errors(cfg, Uref, case.U_ref).items():
+        assert v < 1e-13, ("Uref", k, v)
+    R = torch.empty_like(st.U)
+    A.rhs(gas, st.grid, st.U, R)
+    torch.cuda.synchronize()
+    bad = _check(case, case.U0, R.cpu().numpy())
+    assert not bad, bad
+    assert A.grid_status(st.grid) == 0
+
+
+def test_rk3_steps_follow_the_oracle(table):
+    import torch
+    cfg = CASES["jet_40x24x12"]
+    A, gas, st = _gpu(cfg)
+    case = F3.make_case(cfg, table, I.state_noise(_n(cfg), cfg["seed"]))
+    U = case.U0.copy()
+    dQ = np.zeros_like(U)
+    names = [name for name, _ in F3.state_layout(5, cfg["nx"], cfg["ny"], cfg["nz"])]
+    carried = {name: 0.0 for name in names}
+    for step in range(3):
+        for k in range(3):
+            tol, _ = F3.parity_tolerance(case, U)
+            for name in carried:
+                carried[name] = 2.2 * carried[name] + cfg["dt"] * tol[name]
+            U, dQ, _ = F3.rk_stage(case, U, dQ, k, cfg["dt"])
+            A.rk_stage(st, k, cfg["dt"])
+    torch.cuda.synchronize()
+    fg = F3.unpack(5, cfg["nx"], cfg["ny"], cfg["nz"], st.U.cpu().numpy())
+    fo = F3.unpack(5, cfg["nx"], cfg["ny"], cfg["nz"], U)
+    for name in fo:
+        err = np.abs(fg[name] - fo[name]).max()
+        assert err <= 1e-13 * np.abs(fo[name]).max() + carried[name], (name, err, carried[name])
+    assert A.grid_status(st.grid) == 0
+
+
+def test_three_dimensional_grids_are_rejected_where_unsupported(table):
+    import torch
+    from paper_2210_05547_gb300 import abi as A
+    cfg = CASES["bl_36x20x8"]
+    _, gas, st = _gpu(cfg)
+    with pytest.raises(A.HypError, match="two-dimensional"):
+        A.Batch().add(st, 1e-4)
+    q = torch.empty(cfg["nx"], dtype=torch.float64, device="cuda")
+    tw = torch.empty(cfg["nx"] + 1, dtype=torch.float64, device="cuda")
+    with pytest.raises(A.HypError, match="two-dimensional"):
+        A.wall_fluxes(gas, st.grid, st.U, q, tw)
+    with pytest.raises(A.HypError, match="two-register RK3"):
+        A.rk_stage_scheme(st, "tvd3", 0, 1e-4)
