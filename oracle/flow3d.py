@@ -24,7 +24,7 @@ those of the two-dimensional oracle (oracle/flow.py) with the third direction ad
   to T_j the same way; u = w = 0 and no diffusion through the wall. The reference and initial
   states carry the jet's plume, so that the first cells above the orifice hold its density and
   momentum: the two-dimensional profile's T, p, u, v are blended towards (T_j, p_j, 0, v_j) with
-  F = f(r) exp(-((y - y0) / (jet_height r_j))^2), and the wall faces hold rho v of that blend.
+  F = f(r) exp(-((y - y0) / (2 r_j))^2), and the wall faces hold rho v of that blend.
 
 Every step follows the two-dimensional sequence of oracle.flow.rhs; with a z-uniform state and no
 jet each z-plane gives exactly that right-hand side (pinned in tests/test_oracle_flow3d.py).
@@ -108,9 +108,12 @@ def jet_primitives(cfg, sc):
     return T_j, p_j, v_j
 
 
+JET_PLUME_HEIGHT = 2.0       # plume height of the initial state, in orifice radii
+
+
 def plume(cfg, x, y, z):
     """Blend factor of the jet's plume at (x, y, z)."""
-    h = cfg.get("jet_height", 2.0) * cfg["jet_radius"]
+    h = JET_PLUME_HEIGHT * cfg["jet_radius"]
     return jet_blend(cfg, x, z) * np.exp(-((y - cfg["y0"]) / h) ** 2)
 
 

@@ -163,7 +163,11 @@ struct Grid3 {
     LineOp* ops;
     double* opdata;
     Line3 zop[2][2];           // periodic z operators [kind][dir] (constants only)
-    std::vector<Line3> p1, p3, ad1, ad2, mu, face, faceb, divs;
+    struct Plan3* plan;        // host: the line jobs of each phase
+};
+
+struct Plan3 {
+    std::vector<Line3> p1, p3, ad1, ad2, mu, face, divs;
 };
 
 struct View3 {
@@ -489,47 +493,86 @@ __global__ void k_assemble3(Assemble3 a, long long n) {
     }
 }
 
-// Reference state of one (x, y) plane at every z, the jet's mass flux on the wall faces of the
-// orifice, sponge and Dirichlet mask (host-built plane, replicated here).
-__global__ void k_reference3(Grid3 g, const double* __restrict__ plane_ref,
-                             const double* __restrict__ plane_sig, const double* __restrict__ jetf,
-                             double mflux) {
+// Jet of a three-dimensional case: orifice centre, radius, edge and the plume height of the
+// initial state (two radii), and the sonic jet's T (K), p (Pa) and nondimensional v.
+struct Jet3 {
+    int on;
+    double x, z, r, edge, height, Lz, T, p, v;
+    __host__ __device__ double blend(double xx, double zz) const {
+        double sz = fabs(zz - z);
+        sz = fmin(sz, Lz - sz);
+        const double rr = sqrt((xx - x) * (xx - x) + sz * sz);
+        return 0.5 * (1.0 - tanh((rr - r) / (edge * r)));
+    }
+};
+
+// Reference state Q_ref, sponge strength and Dirichlet mask at every entry of the 3-D state: the
+// two-dimensional profile at (x, y), blended towards the jet inside its plume
+// F = blend(x, z) exp(-((y - y0) / (height r))^2) (T, p -> T_j, p_j; u -> 0; v -> v_j).
+__global__ void k_reference3(GasDev gd, Profile P, hyp_grid_desc d, Jet3 jet, Grid3 g) {
     const Sh3 s = g.sh;
-    const long long pc = (long long)s.nx * s.ny, px = (long long)(s.nx + 1) * s.ny,
-                    py = (long long)s.nx * (s.ny + 1);
+    const double dx = (d.x1 - d.x0) / s.nx, dz = (d.z1 - d.z0) / s.nz;
     RANGE3(g.nstate) {
-        long long f, rem;
-        // locate q in the 3-D layout
+        int field, node, i, j, k;
+        long long rem;
         if (q < (long long)(NSP + 1) * g.nc) {
-            f = q / g.nc;
-            rem = q - f * g.nc;
-            const long long k = rem / pc, w = rem - k * pc;
-            g.Uref[q] = plane_ref[f * pc + w];
-            g.sigma[q] = plane_sig[f * pc + w];
-            g.mask[q] = 0;
+            field = (int)(q / g.nc);
+            rem = q - field * g.nc;
+            node = 0;
         } else if (q < g.off[NSP + 2]) {
+            field = NSP + 1;
             rem = q - g.off[NSP + 1];
-            const long long k = rem / px, w = rem - k * px;
-            const int i = (int)(w % (s.nx + 1));
-            g.Uref[q] = plane_ref[(NSP + 1) * pc + w];
-            g.sigma[q] = plane_sig[(NSP + 1) * pc + w];
-            g.mask[q] = (i == 0 || i == s.nx) ? 1 : 0;
+            node = 1;
         } else if (q < g.off[NSP + 3]) {
+            field = NSP + 2;
             rem = q - g.off[NSP + 2];
-            const long long k = rem / py, w = rem - k * py;
-            const int j = (int)(w / s.nx), i = (int)(w % s.nx);
-            double val = plane_ref[(NSP + 1) * pc + px + w];
-            if (j == 0 && jetf) val = mflux * jetf[k * s.nx + i];
-            g.Uref[q] = val;
-            g.sigma[q] = plane_sig[(NSP + 1) * pc + px + w];
-            g.mask[q] = (j == 0 || j == s.ny) ? 1 : 0;
+            node = 2;
         } else {
+            field = NSP + 3;
             rem = q - g.off[NSP + 3];
-            const long long k = rem / pc, w = rem - k * pc;
-            g.Uref[q] = 0.0;
-            g.sigma[q] = plane_sig[w];
-            g.mask[q] = 0;
+            node = 0;
         }
+        const int pitch = node == 1 ? s.nx + 1 : s.nx, rows = node == 2 ? s.ny + 1 : s.ny;
+        k = (int)(rem / ((long long)pitch * rows));
+        const long long w = rem - (long long)k * pitch * rows;
+        j = (int)(w / pitch);
+        i = (int)(w - (long long)j * pitch);
+        const double x = d.x0 + dx * (node == 1 ? (double)i : i + 0.5);
+        double y, dyde;
+        y_map(d, node == 2 ? (double)j : j + 0.5, y, dyde);
+        const double z = d.z0 + dz * (k + 0.5);
+        const double sg = sponge_at(d, P.c, x, y);
+        g.sigma[q] = sg;
+        if (field == NSP + 3) {
+            g.Uref[q] = 0.0;
+            g.mask[q] = 0;
+            continue;
+        }
+        double T, p, u, v, Y[NSP], rho, rY[NSP], rE;
+        P.at(gd, x, y, T, p, u, v, Y);
+        if (jet.on) {
+            const double yh = (y - d.y0) / (jet.height * jet.r);
+            const double F = jet.blend(x, z) * exp(-yh * yh);
+            T = T + (jet.T - T) * F;
+            p = p + (jet.p - p) * F;
+            u = u * (1.0 - F);
+            v = v + (jet.v - v) * F;
+        }
+        P.conserved(gd, T, p, u, v, Y, rho, rY, rE);
+        double val;
+        uint8_t m = 0;
+        if (field == 0) val = rho;
+        else if (field < NSP) val = rY[field];
+        else if (field == NSP) val = rE;
+        else if (field == NSP + 1) {
+            val = rho * u;
+            m = (i == 0 || i == s.nx) ? 1 : 0;
+        } else {
+            val = rho * v;
+            m = (j == 0 || j == s.ny) ? 1 : 0;
+        }
+        g.Uref[q] = val;
+        g.mask[q] = m;
     }
 }
 
@@ -537,6 +580,7 @@ __global__ void k_reference3(Grid3 g, const double* __restrict__ plane_ref,
 
 void free_grid3(Grid3* g) {
     if (!g) return;
+    delete g->plan;
     cudaFree(g->pool);
     cudaFree(g->mask);
     cudaFree(g->ops);
@@ -585,7 +629,8 @@ int run_rhs3(const hyp_gas* gas, hyp_grid* G, const double* U, double* dUdt, int
     const View3 v = view3(G, g);
     const GasDev& gd = gas->dev;
     // the state-reading jobs carry element offsets into U in `in`
-    std::vector<Line3> p1 = g->p1;
+    const Plan3& pl = *g->plan;
+    std::vector<Line3> p1 = pl.p1;
     for (auto& L : p1) L.in = U + (size_t)L.in;
     int rc = launch3(g, p1, s);
     if (rc) return rc;
@@ -594,23 +639,22 @@ int run_rhs3(const hyp_gas* gas, hyp_grid* G, const double* U, double* dUdt, int
     if (precision == HYP_MIXED) k_closure3<true><<<blocks3(g->nc), 128, 0, s>>>(gd, sc, *g, v, U);
     else k_closure3<false><<<blocks3(g->nc), 128, 0, s>>>(gd, sc, *g, v, U);
     HYP_CUDA(cudaGetLastError());
-    if ((rc = launch3(g, g->p3, s))) return rc;
+    if ((rc = launch3(g, pl.p3, s))) return rc;
     if (v.ad) {
-        if ((rc = launch3(g, g->ad1, s))) return rc;
-        if ((rc = launch3(g, g->ad2, s))) return rc;
+        if ((rc = launch3(g, pl.ad1, s))) return rc;
+        if ((rc = launch3(g, pl.ad2, s))) return rc;
         k_adprep3<<<blocks3(g->nc), 256, 0, s>>>(*g);
         k_adraw3<<<blocks3(g->nc), 256, 0, s>>>(*g, v, U, gd.kind == HYP_GAS_CNEQ);
         for (int ax = 0; ax < 3; ++ax) k_gauss3<<<blocks3(AD_FIELDS * g->nc), 256, 0, s>>>(*g, ax);
         k_adcombine3<<<blocks3(g->nc), 256, 0, s>>>(*g);
         HYP_CUDA(cudaGetLastError());
     }
-    if ((rc = launch3(g, g->mu, s))) return rc;
+    if ((rc = launch3(g, pl.mu, s))) return rc;
     k_stress3<<<blocks3(g->nc + g->nxy + g->nxf + g->nyf), 256, 0, s>>>(*g);
-    if ((rc = launch3(g, g->face, s))) return rc;
-    if ((rc = launch3(g, g->faceb, s))) return rc;
+    if ((rc = launch3(g, pl.face, s))) return rc;
     k_flux3<<<blocks3(g->nxf + g->nyf + g->nc), 128, 0, s>>>(gd, *g, v, U);
     HYP_CUDA(cudaGetLastError());
-    if ((rc = launch3(g, g->divs, s))) return rc;
+    if ((rc = launch3(g, pl.divs, s))) return rc;
     Assemble3 a;
     a.DX = g->DX;
     a.DY = g->DY;
@@ -642,6 +686,8 @@ int init3(const hyp_gas* gas, const hyp_grid_desc* desc, const hyp_case* cas, do
     if (!(desc->z1 > desc->z0)) return fail(HYP_ERR_ARG, "z1 must exceed z0");
     Grid3* g = new Grid3();
     G->g3 = g;
+    g->plan = new Plan3();
+    Plan3& pl = *g->plan;
     const int nx = desc->nx, ny = desc->ny, nz = desc->nz;
     g->sh = Sh3{nx, ny, nz};
     const Sh3& sh = g->sh;
@@ -809,7 +855,7 @@ int init3(const hyp_gas* gas, const hyp_grid_desc* desc, const hyp_case* cas, do
         yc[j] = y;
         eta_c[j] = 1.0 / dy;
     }
-    // reference profile of one plane (the two-dimensional one) on the host
+    // reference profile (the two-dimensional one, evaluated on the device at every node)
     Profile P;
     P.c = *cas;
     P.c.noise = nullptr;
@@ -827,57 +873,28 @@ int init3(const hyp_gas* gas, const hyp_grid_desc* desc, const hyp_case* cas, do
     P.shock = cas->flow == 1;
     P.theta = cas->shock_deflection_deg * 3.14159265358979323846 / 180.0;
     if (P.shock) P.sh = oblique_shock(gd.mach, P.theta, gd.gamma_inf);
-    const long long pc = (long long)nx * ny, px = (long long)(nx + 1) * ny, py = (long long)nx * (ny + 1);
-    std::vector<double> pref((NSP + 1) * pc + px + py), psig((NSP + 1) * pc + px + py);
-    for (int j = 0; j < ny; ++j)
-        for (int i = 0; i < nx; ++i) {
-            double T, p, u, vv, Y[NSP], rho, rY[NSP], rE;
-            P.at(gd, xc[i], yc[j], T, p, u, vv, Y);
-            P.conserved(gd, T, p, u, vv, Y, rho, rY, rE);
-            const double sg = sponge_at(*desc, P.c, xc[i], yc[j]);
-            const long long w = (long long)j * nx + i;
-            pref[w] = rho;
-            for (int sp = 1; sp < NSP; ++sp) pref[sp * pc + w] = rY[sp];
-            pref[NSP * pc + w] = rE;
-            for (int f = 0; f <= NSP; ++f) psig[f * pc + w] = sg;
-        }
-    for (int j = 0; j < ny; ++j)
-        for (int i = 0; i <= nx; ++i) {
-            double T, p, u, vv, Y[NSP], rho, rY[NSP], rE;
-            P.at(gd, xf[i], yc[j], T, p, u, vv, Y);
-            P.conserved(gd, T, p, u, vv, Y, rho, rY, rE);
-            const long long w = (NSP + 1) * pc + (long long)j * (nx + 1) + i;
-            pref[w] = rho * u;
-            psig[w] = sponge_at(*desc, P.c, xf[i], yc[j]);
-        }
-    for (int j = 0; j <= ny; ++j)
-        for (int i = 0; i < nx; ++i) {
-            double T, p, u, vv, Y[NSP], rho, rY[NSP], rE;
-            P.at(gd, xc[i], yf[j], T, p, u, vv, Y);
-            P.conserved(gd, T, p, u, vv, Y, rho, rY, rE);
-            const long long w = (NSP + 1) * pc + px + (long long)j * nx + i;
-            pref[w] = rho * vv;
-            psig[w] = sponge_at(*desc, P.c, xc[i], yf[j]);
-        }
-    // jet: blend factor on the wall faces, Dirichlet mass flux, wall temperature of the heat flux
-    std::vector<double> jetf((size_t)nz * nx, 0.0), Tw((size_t)nz * nx, cas->T_wall / gd.T_ref);
-    double mflux = 0.0;
+    // jet: the sonic jet's state, the wall temperature of the heat flux on the wall faces
+    Jet3 jet;
+    memset(&jet, 0, sizeof(jet));
+    std::vector<double> Tw((size_t)nz * nx, cas->T_wall / gd.T_ref);
     if (cas->jet) {
-        const double Tj = cas->jet_T_ratio * gd.T_inf;
-        const double pj = cas->jet_J * gd.mach * gd.mach * gd.p_inf;
-        const double rho_j = pj / (gd.R_inf * Tj) / gd.rho_inf;
-        const double v_j = sqrt(gd.gamma_inf * gd.R_inf * Tj) / gd.a_inf;
-        mflux = rho_j * v_j;
-        const double Lz = desc->z1 - desc->z0, dzc = Lz / nz;
+        jet.on = 1;
+        jet.x = cas->jet_x;
+        jet.z = cas->jet_z;
+        jet.r = cas->jet_radius;
+        jet.edge = cas->jet_edge;
+        jet.height = 2.0;      // plume height of the initial state, in orifice radii
+        jet.Lz = desc->z1 - desc->z0;
+        jet.T = cas->jet_T_ratio * gd.T_inf;
+        jet.p = cas->jet_J * gd.mach * gd.mach * gd.p_inf;
+        jet.v = sqrt(gd.gamma_inf * gd.R_inf * jet.T) / gd.a_inf;
+        if (!(jet.r > 0 && jet.edge > 0 && jet.T > 0 && jet.p > 0))
+            return fail(HYP_ERR_ARG, "the jet needs a positive radius, edge, J and temperature ratio");
+        const double dzc = (desc->z1 - desc->z0) / nz;
         for (int k = 0; k < nz; ++k)
             for (int i = 0; i < nx; ++i) {
-                const double z = desc->z0 + dzc * (k + 0.5);
-                double sz = fabs(z - cas->jet_z);
-                sz = fmin(sz, Lz - sz);
-                const double r = sqrt((xc[i] - cas->jet_x) * (xc[i] - cas->jet_x) + sz * sz);
-                const double f = 0.5 * (1.0 - tanh((r - cas->jet_radius) / (cas->jet_edge * cas->jet_radius)));
-                jetf[(size_t)k * nx + i] = f;
-                Tw[(size_t)k * nx + i] = (cas->T_wall + (Tj - cas->T_wall) * f) / gd.T_ref;
+                const double f = jet.blend(xc[i], desc->z0 + dzc * (k + 0.5));
+                Tw[(size_t)k * nx + i] = (cas->T_wall + (jet.T - cas->T_wall) * f) / gd.T_ref;
             }
     }
     // ---------------- plans ----------------
@@ -912,7 +929,7 @@ int init3(const hyp_gas* gas, const hyp_grid_desc* desc, const hyp_case* cas, do
     const double ze = g->zeta;
     auto soff = [&](int f) { return (const double*)(size_t)g->off[f]; };
     // P1: state-reading jobs (`in` is an element offset into U)
-    g->p1 = {xy(OX_IFC, 0, soff(NSP + 1), XF3, g->ru_c, C3, nullptr),
+    pl.p1 = {xy(OX_IFC, 0, soff(NSP + 1), XF3, g->ru_c, C3, nullptr),
              xy(OY_IFC, 1, soff(NSP + 2), YF3, g->rv_c, C3, nullptr),
              zl(0, 1, soff(NSP + 3), C3, g->rw_c),
              xy(OX_ICF, 0, soff(0), C3, g->rho_xf, XF3, nullptr),
@@ -921,7 +938,7 @@ int init3(const hyp_gas* gas, const hyp_grid_desc* desc, const hyp_case* cas, do
              xy(OX_DFC, 0, soff(NSP + 1), XF3, g->DX + g->off[0], C3, g->xi_c, -1.0),
              xy(OY_DFC, 1, soff(NSP + 2), YF3, g->DY + g->off[0], C3, g->eta_c, -1.0),
              zl(1, 1, soff(NSP + 3), C3, g->DZ + g->off[0], -ze)};
-    g->p3 = {xy(OX_DFC, 0, g->u_xf, XF3, g->dudx, C3, g->xi_c),
+    pl.p3 = {xy(OX_DFC, 0, g->u_xf, XF3, g->dudx, C3, g->xi_c),
              xy(OY_DFC, 1, g->v_yf, YF3, g->dvdy, C3, g->eta_c),
              zl(1, 1, g->w_zf, C3, g->dwdz, ze),
              xy(ydcfw, 1, g->u_xf, XF3, g->dudy_xy, XY3, g->eta_f),
@@ -943,28 +960,25 @@ int init3(const hyp_gas* gas, const hyp_grid_desc* desc, const hyp_case* cas, do
              xy(OY_IFC, 1, g->mvy_f, YF3, g->mvy_c, C3, nullptr),
              zl(0, 1, g->mwz_f, C3, g->mwz_c)};
     // artificial diffusivity: edge derivatives to the centres (y then x; x then z; y then z)
-    g->ad1 = {xy(OY_IFC, 1, g->dudy_xy, XY3, g->tx[0], XF3, nullptr),
+    pl.ad1 = {xy(OY_IFC, 1, g->dudy_xy, XY3, g->tx[0], XF3, nullptr),
               xy(OY_IFC, 1, g->dvdx_xy, XY3, g->tx[1], XF3, nullptr),
               xy(OX_IFC, 0, g->dudz_xz, XF3, g->tc[0], C3, nullptr),
               xy(OX_IFC, 0, g->dwdx_xz, XF3, g->tc[1], C3, nullptr),
               xy(OY_IFC, 1, g->dvdz_yz, YF3, g->tc[2], C3, nullptr),
               xy(OY_IFC, 1, g->dwdy_yz, YF3, g->tc[3], C3, nullptr)};
-    g->ad2 = {xy(OX_IFC, 0, g->tx[0], XF3, g->dudy_c, C3, nullptr),
+    pl.ad2 = {xy(OX_IFC, 0, g->tx[0], XF3, g->dudy_c, C3, nullptr),
               xy(OX_IFC, 0, g->tx[1], XF3, g->dvdx_c, C3, nullptr),
               zl(0, 1, g->tc[0], C3, g->dudz_c),
               zl(0, 1, g->tc[1], C3, g->dwdx_c),
               zl(0, 1, g->tc[2], C3, g->dvdz_c),
               zl(0, 1, g->tc[3], C3, g->dwdy_c)};
-    g->mu = {xy(OX_ICF, 0, g->mu_e, C3, g->mu_xf, XF3, nullptr),
+    pl.mu = {xy(OX_ICF, 0, g->mu_e, C3, g->mu_xf, XF3, nullptr),
              xy(OY_ICF, 1, g->mu_e, C3, g->mu_yf, YF3, nullptr)};
-    g->faceb = {xy(OY_ICF, 1, g->mu_xf, XF3, g->mu_xy, XY3, nullptr)};
-    // mu_xz, mu_yz and the stress kernel need the edge viscosities before the stresses: they
-    // go with the viscosity jobs (second list run after the first)
-    g->mu.push_back(zl(0, 0, g->mu_xf, XF3, g->mu_xz));
-    g->mu.push_back(zl(0, 0, g->mu_yf, YF3, g->mu_yz));
-    g->mu.push_back(g->faceb[0]);
-    g->faceb.clear();
-    std::vector<Line3>& F = g->face;
+    // edge viscosities from the face ones (the jobs of a list run in order on one stream)
+    pl.mu.push_back(zl(0, 0, g->mu_xf, XF3, g->mu_xz));
+    pl.mu.push_back(zl(0, 0, g->mu_yf, YF3, g->mu_yz));
+    pl.mu.push_back(xy(OY_ICF, 1, g->mu_xf, XF3, g->mu_xy, XY3, nullptr));
+    std::vector<Line3>& F = pl.face;
     for (int sp = 0; sp < NSP; ++sp) {
         F.push_back(xy(OX_ICF, 0, g->Y[sp], C3, g->Yx[sp], XF3, nullptr));
         F.push_back(xy(OX_ICF, 0, g->G[sp], C3, g->Gx[sp], XF3, nullptr));
@@ -1003,7 +1017,7 @@ int init3(const hyp_gas* gas, const hyp_grid_desc* desc, const hyp_case* cas, do
     F.push_back(zl(0, 0, g->v_c, C3, g->v_z));
     F.push_back(xy(OX_IFC, 0, g->tau_xz, XF3, g->txz_z, C3, nullptr));
     F.push_back(xy(OY_IFC, 1, g->tau_yz, YF3, g->tyz_z, C3, nullptr));
-    std::vector<Line3>& D = g->divs;
+    std::vector<Line3>& D = pl.divs;
     for (int sp = 1; sp < NSP; ++sp) {
         D.push_back(xy(OX_DFC, 0, g->Fsx[sp], XF3, g->DX + g->off[sp], C3, g->xi_c, -1.0));
         D.push_back(xy(OY_DFC, 1, g->Fsy[sp], YF3, g->DY + g->off[sp], C3, g->eta_c, -1.0));
@@ -1030,11 +1044,7 @@ int init3(const hyp_gas* gas, const hyp_grid_desc* desc, const hyp_case* cas, do
     UP3(g->eta_c, eta_c.data(), ny * sizeof(double));
     UP3(g->eta_f, eta_f.data(), (ny + 1) * sizeof(double));
     UP3(g->Tw, Tw.data(), Tw.size() * sizeof(double));
-    // the plane reference, its sponge and the jet blend travel through state-sized scratch
-    UP3(g->DX, pref.data(), pref.size() * sizeof(double));
-    UP3(g->DY, psig.data(), psig.size() * sizeof(double));
-    UP3(g->DZ, jetf.data(), jetf.size() * sizeof(double));
-    k_reference3<<<blocks3(g->nstate), 256, 0, s>>>(*g, g->DX, g->DY, cas->jet ? g->DZ : nullptr, mflux);
+    k_reference3<<<blocks3(g->nstate), 128, 0, s>>>(gd, P, *desc, jet, *g);
     const bool noisy = cas->noise && cas->noise_amp > 0;
     if (noisy) UP3(g->R, cas->noise, g->nstate * sizeof(double));
     k_initial<<<blocks3(g->nstate), 256, 0, s>>>(g->nstate, g->Uref, g->mask, noisy ? g->R : nullptr,

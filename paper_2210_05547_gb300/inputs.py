@@ -81,7 +81,7 @@ def jet_case(nx=512, ny=256, nz=128, seed=0, kind="cneq"):
         sponge_in=1.0, sponge_out=2.0, sponge_top_cells=max(2, (20 * ny) // 500),
         artificial_diffusivity=1, C_D=0.01, dt=5.0e-4, filter_sigma=0.0,
         jet=1, jet_x=52.5, jet_z=5.0 + float(rng.uniform(-1.0, 1.0)),
-        jet_radius=0.5 * float(rng.uniform(0.9, 1.1)), jet_edge=0.3, jet_height=2.0,
+        jet_radius=0.5 * float(rng.uniform(0.9, 1.1)), jet_edge=0.3,
         jet_J=float(rng.uniform(1.0, 3.0)), jet_T_ratio=1.0,
     )
     return c
