@@ -399,7 +399,7 @@ def rhs(case: Case3D, U, return_parts=False):
 def parity_tolerance(case: Case3D, U):
     """Per-field absolute tolerance, as oracle.flow.parity_tolerance: 1e-12 max|R_f| + the FP64
     rounding floor of the flux divergence + the sponge term + the temperature conditioning of
-    the Arrhenius sources."""
+    the Arrhenius sources and of the pressure in the momentum and energy fluxes."""
     R, parts = rhs(case, U, return_parts=True)
     g = case.grid
     ns = case.tab.ns
@@ -410,13 +410,33 @@ def parity_tolerance(case: Case3D, U):
     sig_max = max(float(np.max(v)) for v in case.sigma.values())
     for k in tol:
         tol[k] += 16.0 * 2.0 ** -53 * sig_max * np.abs(q[k]).max()
+    T_si = parts["T"] * case.sc.T_ref
+    scale = np.abs(parts["E"]) + np.abs(parts["e"]) + parts["ke"]
+    if case.kind == F.KIND_CPG:
+        dT_rel = 8.0 * 2.0 ** -53 * scale / np.abs(parts["e"])
+    else:
+        dT_rel = 8.0 * 2.0 ** -53 * scale * case.sc.a ** 2 / (parts["th"]["cv"] * T_si)
     if case.kind == F.KIND_CNEQ and case.tab.reactions:
         ta_max = max(r.Ta for r in case.tab.reactions)
-        T_si = parts["T"] * case.sc.T_ref
-        scale = np.abs(parts["E"]) + np.abs(parts["e"]) + parts["ke"]
-        dT_rel = 8.0 * 2.0 ** -53 * scale * case.sc.a ** 2 / (parts["th"]["cv"] * T_si)
         for s in range(1, ns):
             tol[f"rs{s}"] += np.max(np.abs(parts["th"]["wdot"][s]) * ta_max / T_si * dT_rel)
+    # The same temperature conditioning moves the pressure by dp = p dT/T at fixed density; the
+    # momentum fluxes carry p and the energy fluxes p times the velocity, and their derivatives
+    # multiply that by ||D|| <= 6 and the metric (in three dimensions the spanwise derivative of
+    # the pressure, with its uniform metric, has no larger flux term to hide it in).
+    # Each derivative sees the pressure error within a few points of where it is evaluated:
+    # the largest dp within +-3 points along the derivative's direction, times the local metric.
+    from scipy.ndimage import maximum_filter1d
+    dp = np.abs(parts["p"]) * dT_rel
+    spd = np.sqrt(2.0 * parts["ke"])
+    met = (g.xi_c[None, None, :], g.eta_c[None, :, None], case.zeta)
+    near = [maximum_filter1d(dp, 7, axis=a, mode="wrap" if a == 0 else "nearest") * m
+            for a, m in ((2, met[0]), (1, met[1]), (0, met[2]))]
+    near_e = [maximum_filter1d(dp * spd, 7, axis=a, mode="wrap" if a == 0 else "nearest") * m
+              for a, m in ((2, met[0]), (1, met[1]), (0, met[2]))]
+    for name, k in (("rhou", 0), ("rhov", 1), ("rhow", 2)):
+        tol[name] += 16.0 * 6.0 * float(near[k].max())
+    tol["rhoE"] += 16.0 * 6.0 * float(max(a.max() for a in near_e))
     return tol, R
 
 
