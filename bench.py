@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
     ap.add_argument("--no-sm", action="store_true", help="skip the Stefan-Maxwell measurement")
     ap.add_argument("--no-lte", action="store_true", help="skip the LTE measurement")
+    ap.add_argument("--no-3d", action="store_true",
+                    help="skip the three-dimensional jet-in-crossflow measurement")
     ap.add_argument("--no-air11", action="store_true",
                     help="skip the eleven-species measurements")
     ap.add_argument("--serve-requests", type=int, default=48,
@@ -346,6 +348,42 @@ def serving_bench(A, I, nreq, seed, precision):
                         "shock interactions, 20-80 RK3 steps each"}
 
 
+def jet3d_bench(A, I, dev, rank, world, barrier, flush, steps=2, warmup=1):
+    """Sonic jet through a circular orifice into the Mach 8 crossflow, 512 x 256 x 128 cells,
+    spanwise periodic: RK3 steps timed with CUDA events (L2 flushed between steps), FP64 and
+    with binary32 transport."""
+    import torch
+    cfg = I.jet_case(512, 256, 128, seed=7 + rank)
+    gas = A.gas_model_load(cfg)
+    n = A.state_size(gas, cfg)
+    out = {"workload": "jet_512x256x128_cneq5_rk3", "cells": 512 * 256 * 128,
+           "jet_J": cfg["jet_J"], "unit": UNIT}
+    for prec, key in ((A.FP64, "fp64"), (A.MIXED, "mixed")):
+        U = torch.empty(n, dtype=torch.float64, device=dev)
+        dQ = torch.empty_like(U)
+        st = A.state_init(gas, cfg, U, dQ, I.state_noise(n, cfg["seed"]))
+        for _ in range(warmup):
+            for k in range(STAGES):
+                A.rk_stage(st, k, cfg["dt"], precision=prec)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        barrier()
+        for i in range(steps):
+            ev[i][0].record()
+            for k in range(STAGES):
+                A.rk_stage(st, k, cfg["dt"], precision=prec)
+            ev[i][1].record()
+            flush.fill_(float(i))
+        barrier()
+        ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world, dev)
+        out[key] = {"value": job_rate(world, out["cells"], steps, ms), "ms_per_step": ms / steps,
+                    "status_flags": A.grid_status(st.grid),
+                    "finite": bool(torch.isfinite(st.U).all().item())}
+        del st, U, dQ
+        torch.cuda.empty_cache()
+    return out
+
+
 def ours_arm(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -521,6 +559,9 @@ def ours_arm(args, rank, world, local_rank):
         smd.update(cost_vs_algebraic=s_ms / max_ms,
                    note="Stefan-Maxwell system (Eq. 17) solved at every face instead of the "
                         "algebraic model (Eq. 18); same case, FP64")
+    jet3d = None
+    if not args.no_3d:
+        jet3d = jet3d_bench(A, I, dev, rank, world, barrier, flush)
     air11 = None
     if not args.no_air11:
         air11, a_ms = variant(I.with_species(cfg))
@@ -572,7 +613,7 @@ def ours_arm(args, rank, world, local_rank):
                               "frac": value / world * RHS_FP64_FLOP_PER_POINT / 1e6 / FP64_PEAK_TFLOPS},
                 "wall_s_timed": t_wall, "status_flags": status, "mixed": mixed,
                 "serving": serving, "serving_fp64": serving_fp64, "stefan_maxwell": smd,
-                "lte": lte, "air11": air11, "thermo_sweep": sweep,
+                "lte": lte, "air11": air11, "jet3d": jet3d, "thermo_sweep": sweep,
                 "kernels": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1]}}
         print(json.dumps(line), flush=True)
     if world > 1:
