@@ -153,6 +153,11 @@ struct LineJob {
     const double* metric;        // per output element along the line, nullable
     const float* metric_f;       // binary32 copy of metric (HYP_MIXED jobs)
     int f32ok;                   // under HYP_MIXED the constant-factor rows may run in binary32
+    // three-dimensional grids: lines grouped by plane, line L starting at
+    // (L / lpp) * plane stride + (L % lpp) * line stride (lpp = 0: one group)
+    int lpp;
+    long long in_ps, out_ps;
+    const double* wall_arr;      // per-line wall values (line index), replacing wall_value
 };
 
 cudaError_t launch_lines(const LineJob* d_jobs, int njobs, int max_blocks, const double* U,

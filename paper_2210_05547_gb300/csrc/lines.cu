@@ -349,14 +349,14 @@ __device__ __forceinline__ void back_span(int r0, int r1, double& y, const LineO
 template <int KIND, bool F32>
 __device__ __forceinline__ void forward(const LineJob& J, const LineOp& op,
                                         const double* __restrict__ in, double* __restrict__ tmp,
-                                        int s, int e, int W) {
+                                        int s, int e, int W, double wall) {
     const int fs = max(0, s - W);
     const long long ies = J.in_es, oes = J.out_es;
     double d = 0.0;
     Window w{0.0, 0.0, 0.0};
     const double* __restrict__ p = nullptr;
-    fwd_span<KIND, false, F32>(fs, s - 1, d, w, in, p, ies, op, J.wall_value, tmp, oes);
-    fwd_span<KIND, true, F32>(s, e, d, w, in, p, ies, op, J.wall_value, tmp, oes);
+    fwd_span<KIND, false, F32>(fs, s - 1, d, w, in, p, ies, op, wall, tmp, oes);
+    fwd_span<KIND, true, F32>(s, e, d, w, in, p, ies, op, wall, tmp, oes);
 }
 
 template <int OM, bool F32>
@@ -376,10 +376,10 @@ template <bool F32>
 __device__ __forceinline__ void run_line(const LineJob& J, const LineOp& op,
                                          const double* __restrict__ in, double* __restrict__ out,
                                          double* __restrict__ tmp, int s, int e, int m, int W,
-                                         bool active) {
+                                         bool active, double wall) {
     if (active && s <= e) {
-        if (op.kind == 0) forward<0, F32>(J, op, in, tmp, s, e, W);
-        else forward<1, F32>(J, op, in, tmp, s, e, W);
+        if (op.kind == 0) forward<0, F32>(J, op, in, tmp, s, e, W, wall);
+        else forward<1, F32>(J, op, in, tmp, s, e, W, wall);
     }
     __syncthreads();
     if (active && s <= e) {
@@ -412,13 +412,22 @@ __global__ void __launch_bounds__(LINE_BLOCK) k_lines(const LineJob* __restrict_
     const int s = seg * L;
     const int e = min(s + L, m) - 1;
     const int W = op.kind == 0 ? 40 : 26;
-    const double* __restrict__ in =
-        (J.in_state ? U + (size_t)J.in : J.in) + (long long)line * J.in_ls;
-    double* __restrict__ out = J.out + (long long)line * J.out_ls;
-    double* __restrict__ tmp = J.tmp + (long long)line * J.out_ls;
+    long long ioff, ooff;
+    if (J.lpp) {
+        const int k = line / J.lpp, l = line - k * J.lpp;
+        ioff = k * J.in_ps + (long long)l * J.in_ls;
+        ooff = k * J.out_ps + (long long)l * J.out_ls;
+    } else {
+        ioff = (long long)line * J.in_ls;
+        ooff = (long long)line * J.out_ls;
+    }
+    const double* __restrict__ in = (J.in_state ? U + (size_t)J.in : J.in) + ioff;
+    double* __restrict__ out = J.out + ooff;
+    double* __restrict__ tmp = J.tmp + ooff;
+    const double wall = (J.wall_arr && active) ? J.wall_arr[line] : J.wall_value;
     // uniform per block: every thread of a block works on the same job
-    if (mixed && J.f32ok) run_line<true>(J, op, in, out, tmp, s, e, m, W, active);
-    else run_line<false>(J, op, in, out, tmp, s, e, m, W, active);
+    if (mixed && J.f32ok) run_line<true>(J, op, in, out, tmp, s, e, m, W, active, wall);
+    else run_line<false>(J, op, in, out, tmp, s, e, m, W, active, wall);
 }
 
 }  // namespace

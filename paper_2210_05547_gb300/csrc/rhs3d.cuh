@@ -48,6 +48,7 @@ struct Line3 {
     const double* wall_arr;    //   wall value of line (k, i) at k * nx + i
     int kind, dir;             // z lines: 0 interpolation / 1 derivative; 0 c->f / 1 f->c
     double wa, wb, lm, cp;     // z lines: the operator's constant factors
+    int job;                   // x, y lines: index of the segmented line job (Grid3::jobs)
 };
 
 constexpr int W3 = 48;   // warm-up rows of the periodic recurrences
@@ -164,10 +165,13 @@ struct Grid3 {
     double* opdata;
     Line3 zop[2][2];           // periodic z operators [kind][dir] (constants only)
     struct Plan3* plan;        // host: the line jobs of each phase
+    LineJob* jobs;             // device: the x and y lines as segmented line jobs (lines.cu)
+    double* ltmp;              // their forward-sweep storage (jobs run one after another)
 };
 
 struct Plan3 {
     std::vector<Line3> p1, p3, ad1, ad2, mu, face, divs;
+    std::vector<int> blocks;   // per x/y line: blocks of its launch (index Line3::job)
 };
 
 struct View3 {
@@ -581,6 +585,8 @@ __global__ void k_reference3(GasDev gd, Profile P, hyp_grid_desc d, Jet3 jet, Gr
 void free_grid3(Grid3* g) {
     if (!g) return;
     delete g->plan;
+    cudaFree(g->jobs);
+    cudaFree(g->ltmp);
     cudaFree(g->pool);
     cudaFree(g->mask);
     cudaFree(g->ops);
@@ -606,15 +612,14 @@ View3 view3(const hyp_grid* G, const Grid3* g) {
 }
 
 // operator ids of the x and y operators in Grid3::ops (as the two-dimensional OpId)
-int launch3(const Grid3* g, const std::vector<Line3>& jobs, cudaStream_t s) {
+int launch3(const Grid3* g, const std::vector<Line3>& jobs, const double* U, int mixed,
+            cudaStream_t s) {
     for (const Line3& L : jobs) {
         if (L.axis == 2) {
             const long long n = g->sh.plane(L.tin);
             k_line3z<<<(int)std::min<long long>((n + 127) / 128, 152LL * 64), 128, 0, s>>>(L, g->sh);
         } else {
-            const long long n = L.axis == 0 ? (long long)g->sh.rows(L.tin) * g->sh.nz
-                                            : (long long)g->sh.pitch(L.tin) * g->sh.nz;
-            k_line3<<<(int)std::min<long long>((n + 127) / 128, 152LL * 64), 128, 0, s>>>(L, g->sh);
+            HYP_CUDA(launch_lines(g->jobs + L.job, 1, g->plan->blocks[L.job], U, s, mixed));
         }
     }
     HYP_CUDA(cudaGetLastError());
@@ -628,33 +633,35 @@ int run_rhs3(const hyp_gas* gas, hyp_grid* G, const double* U, double* dUdt, int
     Grid3* g = (Grid3*)G->g3;
     const View3 v = view3(G, g);
     const GasDev& gd = gas->dev;
-    // the state-reading jobs carry element offsets into U in `in`
+    // the state-reading jobs carry element offsets into U in `in` (the x and y ones resolve it
+    // in the line kernel)
     const Plan3& pl = *g->plan;
     std::vector<Line3> p1 = pl.p1;
-    for (auto& L : p1) L.in = U + (size_t)L.in;
-    int rc = launch3(g, p1, s);
+    for (auto& L : p1)
+        if (L.axis == 2) L.in = U + (size_t)L.in;
+    int rc = launch3(g, p1, U, 0, s);
     if (rc) return rc;
     k_fv3<<<blocks3(g->nxf + g->nyf + g->nc), 256, 0, s>>>(*g, v, U);
     const Scales sc = scales_of(gd);
     if (precision == HYP_MIXED) k_closure3<true><<<blocks3(g->nc), 128, 0, s>>>(gd, sc, *g, v, U);
     else k_closure3<false><<<blocks3(g->nc), 128, 0, s>>>(gd, sc, *g, v, U);
     HYP_CUDA(cudaGetLastError());
-    if ((rc = launch3(g, pl.p3, s))) return rc;
+    if ((rc = launch3(g, pl.p3, U, 0, s))) return rc;
     if (v.ad) {
-        if ((rc = launch3(g, pl.ad1, s))) return rc;
-        if ((rc = launch3(g, pl.ad2, s))) return rc;
+        if ((rc = launch3(g, pl.ad1, U, 0, s))) return rc;
+        if ((rc = launch3(g, pl.ad2, U, 0, s))) return rc;
         k_adprep3<<<blocks3(g->nc), 256, 0, s>>>(*g);
         k_adraw3<<<blocks3(g->nc), 256, 0, s>>>(*g, v, U, gd.kind == HYP_GAS_CNEQ);
         for (int ax = 0; ax < 3; ++ax) k_gauss3<<<blocks3(AD_FIELDS * g->nc), 256, 0, s>>>(*g, ax);
         k_adcombine3<<<blocks3(g->nc), 256, 0, s>>>(*g);
         HYP_CUDA(cudaGetLastError());
     }
-    if ((rc = launch3(g, pl.mu, s))) return rc;
+    if ((rc = launch3(g, pl.mu, U, 0, s))) return rc;
     k_stress3<<<blocks3(g->nc + g->nxy + g->nxf + g->nyf), 256, 0, s>>>(*g);
-    if ((rc = launch3(g, pl.face, s))) return rc;
+    if ((rc = launch3(g, pl.face, U, 0, s))) return rc;
     k_flux3<<<blocks3(g->nxf + g->nyf + g->nc), 128, 0, s>>>(gd, *g, v, U);
     HYP_CUDA(cudaGetLastError());
-    if ((rc = launch3(g, pl.divs, s))) return rc;
+    if ((rc = launch3(g, pl.divs, U, 0, s))) return rc;
     Assemble3 a;
     a.DX = g->DX;
     a.DY = g->DY;
@@ -1035,6 +1042,58 @@ int init3(const hyp_gas* gas, const hyp_grid_desc* desc, const hyp_case* cas, do
     D.push_back(xy(OX_DFC, 0, g->Gxz, XF3, g->DX + g->off[NSP + 3], C3, g->xi_c, -1.0));
     D.push_back(xy(OY_DFC, 1, g->Gyz, YF3, g->DY + g->off[NSP + 3], C3, g->eta_c, -1.0));
     D.push_back(zl(1, 0, g->Gzz, C3, g->DZ + g->off[NSP + 3], -ze));
+    // x and y lines as segmented line jobs: plane groups for y, segment counts as in two
+    // dimensions, one forward-sweep buffer (the jobs run one after another)
+    {
+        std::vector<LineJob> lj;
+        long long tmp_n = 0;
+        for (auto* list : {&pl.p1, &pl.p3, &pl.ad1, &pl.ad2, &pl.mu, &pl.face, &pl.divs})
+            for (Line3& L : *list) {
+                if (L.axis == 2) continue;
+                const LineOp& op = hops[L.op - g->ops];
+                LineJob j;
+                memset(&j, 0, sizeof(j));
+                j.op = L.op;
+                j.in_state = list == &pl.p1 ? 1 : 0;
+                j.in = L.in;
+                j.out = L.out;
+                j.scale = L.scale;
+                j.metric = L.metric;
+                j.wall_value = L.wall;
+                j.wall_arr = L.wall_arr;
+                if (L.axis == 0) {
+                    j.in_ls = sh.pitch(L.tin);
+                    j.out_ls = sh.pitch(L.tout);
+                    j.in_es = j.out_es = 1;
+                    j.nlines = sh.rows(L.tin) * nz;
+                } else {
+                    j.lpp = sh.pitch(L.tin);
+                    j.in_ls = j.out_ls = 1;
+                    j.in_es = sh.pitch(L.tin);
+                    j.out_es = sh.pitch(L.tout);
+                    j.in_ps = sh.plane(L.tin);
+                    j.out_ps = sh.plane(L.tout);
+                    j.nlines = sh.pitch(L.tin) * nz;
+                }
+                int ns = 1;
+                while (ns < LINE_BLOCK / 2 && (op.m + ns - 1) / ns > 260) ns *= 2;
+                while (ns < LINE_BLOCK / 2 && (long long)j.nlines * ns < 40960 &&
+                       (op.m + 2 * ns - 1) / (2 * ns) >= 32)
+                    ns *= 2;
+                j.nseg = ns;
+                const int lpb = LINE_BLOCK / ns;
+                pl.blocks.push_back((j.nlines + lpb - 1) / lpb);
+                tmp_n = std::max(tmp_n, sh.size(L.tout));
+                L.job = (int)lj.size();
+                lj.push_back(j);
+            }
+        err = cudaMalloc(&g->ltmp, tmp_n * sizeof(double));
+        if (err == cudaSuccess) err = cudaMalloc(&g->jobs, lj.size() * sizeof(LineJob));
+        if (err != cudaSuccess) return cuda_fail(err, "cudaMalloc(3-D line jobs)");
+        for (auto& j : lj) j.tmp = g->ltmp;
+        HYP_CUDA(cudaMemcpyAsync(g->jobs, lj.data(), lj.size() * sizeof(LineJob), cudaMemcpyHostToDevice, s));
+        HYP_CUDA(cudaStreamSynchronize(s));
+    }
     // ---------------- uploads, reference, initial state ----------------
 #define UP3(dst, src, bytes) HYP_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s))
     UP3(g->ops, hops.data(), NOPS * sizeof(LineOp));
