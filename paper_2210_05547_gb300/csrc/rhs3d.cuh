@@ -13,11 +13,12 @@
 // at centres and on the three edge families, the three-dimensional strain and vorticity in the
 // artificial-diffusivity sensors (fourth differences and Gaussian filter periodic in z), stresses
 // at centres and edges, species and energy fluxes on the three face families, divergences in
-// three directions. Lines along x and y use the compact operators of the two-dimensional path
-// (one thread per line, Thomas factors of the operator); lines along z are periodic: every row
-// is interior, so the forward and backward recurrences run with the operator's constant
-// factors around the ring, started W = 48 rows early from zero (the dropped history is scaled by
-// at most 3^-48 < 1e-22; the result is the periodic solution to rounding).
+// three directions. Lines along x and y run through the segmented line kernel of the
+// two-dimensional path (lines.cu; lines along y grouped by z-plane); lines along z are periodic:
+// every row is interior, so the forward and backward recurrences run with the operator's
+// constant factors around the ring, one thread per line, started W rows early from zero (W = 40
+// for the interpolation, factor 1/3, and 26 for the derivative, factor 0.148: the dropped history
+// is below 1e-19 of the values, and the result is the periodic solution to rounding).
 //
 // Jet (reading; the paper gives a sonic jet of prescribed temperature ratio and momentum ratio
 // J): inside the orifice the wall face holds the Dirichlet mass flux of a sonic jet at
@@ -51,7 +52,6 @@ struct Line3 {
     int job;                   // x, y lines: index of the segmented line job (Grid3::jobs)
 };
 
-constexpr int W3 = 48;   // warm-up rows of the periodic recurrences
 
 __device__ __forceinline__ double row3(int kind, double p0, double p1, double p2, double p3,
                                        double wa, double wb, double lm, double d) {
@@ -59,8 +59,8 @@ __device__ __forceinline__ double row3(int kind, double p0, double p1, double p2
     return fma(-lm, d, fma(wa, p2 - p1, wb * (p3 - p0)));
 }
 
-// Lines along x or y: one thread per line, forward recurrence into the output, back substitution
-// in place.
+// Lines along x or y, one thread per line (forward recurrence into the output, back substitution
+// in place): the plain form of the segmented kernel, kept for reference checks.
 __global__ void __launch_bounds__(128) k_line3(Line3 L, Sh3 sh) {
     const LineOp& op = *L.op;
     const long long nlines = L.axis == 0 ? (long long)sh.rows(L.tin) * sh.nz
@@ -116,6 +116,7 @@ __global__ void __launch_bounds__(128) k_line3z(Line3 L, Sh3 sh) {
         const double* __restrict__ in = L.in + line;
         double* __restrict__ out = L.out + line;
         auto at = [&](int r) { return in[(long long)(((r % n) + n) % n) * plane]; };
+        const int W3 = L.kind == 0 ? 40 : 26;     // as the segmented solver: dropped history < 1e-19
         double d = 0.0;
         for (int t = -W3; t < n; ++t) {
             const int s0 = L.dir == 0 ? t - 2 : t - 1;
@@ -140,6 +141,8 @@ struct Grid3 {
     // centres (and z-faces, same shape)
     double *ru_c, *rv_c, *rw_c, *T, *p, *H, *u_c, *v_c, *w_c, *e, *a, *mu_e, *K, *beta, *Tcache;
     double *Y[NSP], *X[NSP], *h[NSP], *W[NSP], *Wd[NSP], *G[NSP];
+    double *esc[NSP], *cvsc[NSP], *cvpc[NSP];   // species e, c_v, dc_v/dT at the cached T
+    int cache_valid;                            // host: the caches hold an evaluation
     double *dudx, *dvdy, *dwdz, *tau_xx, *tau_yy, *tau_zz, *Gxx, *Gyy, *Gzz, *mux_c, *mvy_c, *mwz_c;
     double *S, *div, *fsw, *dudy_c, *dvdx_c, *dudz_c, *dwdx_c, *dvdz_c, *dwdy_c, *tc[4];
     double *raw[AD_FIELDS], *filt[AD_FIELDS];
@@ -177,7 +180,7 @@ struct Plan3 {
 struct View3 {
     Sh3 sh;
     long long off[NSP + 4];
-    int wall, ad;
+    int wall, ad, predict;
     double C_mu, C_beta, C_kappa, C_D, zeta;
     const double *xi_c, *eta_c;
     unsigned* status;
@@ -240,11 +243,31 @@ __global__ void __launch_bounds__(128) k_closure3(GasDev gd, Scales sc, Grid3 g,
 #pragma unroll
             for (int sp = 0; sp < NSP; ++sp) h[sp] = wd[sp] = X[sp] = W[sp] = Wd[sp] = 0.0;
         } else {
+            const double e_si = e * sc.a_inf * sc.a_inf;
+            double T0 = g.Tcache[idx];
+            if (v.predict) {
+                // second-order step from the cached species state with the new composition
+                double ec = 0.0, cvc = 0.0, cvpc = 0.0;
+#pragma unroll
+                for (int sp = 0; sp < NSP; ++sp) {
+                    ec += Y[sp] * g.esc[sp][idx];
+                    cvc += Y[sp] * g.cvsc[sp][idx];
+                    cvpc += Y[sp] * g.cvpc[sp][idx];
+                }
+                const double icv = 1.0 / cvc;
+                const double d1 = (e_si - ec) * icv;
+                T0 += d1 - 0.5 * cvpc * d1 * d1 * icv;
+            }
             ClosureOut o;
-            closure_si_p<MIXED>(gd, rho * sc.rho_inf, e * sc.a_inf * sc.a_inf, Y, g.Tcache[idx],
-                                cneq, cneq, o);
+            closure_si_p<MIXED>(gd, rho * sc.rho_inf, e_si, Y, T0, cneq, cneq, o);
             if (o.status) atomicOr(v.status, o.status);
             g.Tcache[idx] = o.T;
+#pragma unroll
+            for (int sp = 0; sp < NSP; ++sp) {
+                g.esc[sp][idx] = o.es[sp];
+                g.cvsc[sp][idx] = o.cvs[sp];
+                g.cvpc[sp][idx] = o.cvps[sp];
+            }
             T = o.T / sc.T_ref;
             p = o.p / (sc.rho_inf * sc.a_inf * sc.a_inf);
             mu = o.mu / sc.mu_inf;
@@ -600,6 +623,7 @@ View3 view3(const hyp_grid* G, const Grid3* g) {
     for (int i = 0; i < NSP + 4; ++i) v.off[i] = g->off[i];
     v.wall = G->cas.wall;
     v.ad = G->cas.artificial_diffusivity;
+    v.predict = g->cache_valid;
     v.C_mu = G->cas.C_mu;
     v.C_beta = G->cas.C_beta;
     v.C_kappa = G->cas.C_kappa;
@@ -646,6 +670,7 @@ int run_rhs3(const hyp_gas* gas, hyp_grid* G, const double* U, double* dUdt, int
     if (precision == HYP_MIXED) k_closure3<true><<<blocks3(g->nc), 128, 0, s>>>(gd, sc, *g, v, U);
     else k_closure3<false><<<blocks3(g->nc), 128, 0, s>>>(gd, sc, *g, v, U);
     HYP_CUDA(cudaGetLastError());
+    g->cache_valid = 1;
     if ((rc = launch3(g, pl.p3, U, 0, s))) return rc;
     if (v.ad) {
         if ((rc = launch3(g, pl.ad1, U, 0, s))) return rc;
@@ -718,7 +743,7 @@ int init3(const hyp_gas* gas, const hyp_grid_desc* desc, const hyp_case* cas, do
     G->nstate = (int)o;
     const long long nc = g->nc, nxf = g->nxf, nyf = g->nyf, nxy = g->nxy;
     // ---------------- memory ----------------
-    const long long n_c = 15 + 6 * NSP + 12 + 10 + 4 + 2 * AD_FIELDS + 3 + 5 * NSP + 9;
+    const long long n_c = 15 + 9 * NSP + 12 + 10 + 4 + 2 * AD_FIELDS + 3 + 5 * NSP + 9;
     const long long n_x = 4 + 5 * NSP + 9 + 8 + 2;
     const long long n_y = 4 + 5 * NSP + 9 + 8;
     const long long n_xy = 8;
@@ -741,7 +766,9 @@ int init3(const hyp_gas* gas, const hyp_grid_desc* desc, const hyp_case* cas, do
                        &g->e, &g->a, &g->mu_e, &g->K, &g->beta, &g->Tcache})
         *f = take(nc);
     for (int sp = 0; sp < NSP; ++sp)
-        for (double** f : {&g->Y[sp], &g->X[sp], &g->h[sp], &g->W[sp], &g->Wd[sp], &g->G[sp]}) *f = take(nc);
+        for (double** f : {&g->Y[sp], &g->X[sp], &g->h[sp], &g->W[sp], &g->Wd[sp], &g->G[sp],
+                           &g->esc[sp], &g->cvsc[sp], &g->cvpc[sp]})
+            *f = take(nc);
     for (double** f : {&g->dudx, &g->dvdy, &g->dwdz, &g->tau_xx, &g->tau_yy, &g->tau_zz, &g->Gxx,
                        &g->Gyy, &g->Gzz, &g->mux_c, &g->mvy_c, &g->mwz_c})
         *f = take(nc);
