@@ -344,6 +344,10 @@ def serving_bench(A, I, nreq, seed, precision):
             "max_batch": cnt["max_members"],
             "errors": int(sum(1 for s in st if s["error"])),
             "status_nonzero": int(sum(1 for s in st if s["status"])),
+            "status_requests": [{"name": c["name"], "nx": c["nx"], "ny": c["ny"],
+                                 "mach": round(c["mach"], 3), "T_wall": round(c.get("T_wall", 0.0), 1),
+                                 "steps": n, "status": s["status"]}
+                                for (c, n, _), s in zip(reqs, st) if s["status"]],
             "workload": "grids 128x32 to 1024x256, boundary layers Mach 5-20 (wall 300-1500 K) and "
                         "shock interactions, 20-80 RK3 steps each"}
 

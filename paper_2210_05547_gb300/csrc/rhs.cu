@@ -594,11 +594,20 @@ extern "C" int hyp_state_size(const hyp_gas* gas, const hyp_grid_desc* desc, int
     return HYP_OK;
 }
 
+static void free_streams(hyp_grid* G) {
+    if (G->side) cudaStreamDestroy(G->side);
+    for (int k = 0; k < 2; ++k) {
+        if (G->fork[k]) cudaEventDestroy(G->fork[k]);
+        if (G->join[k]) cudaEventDestroy(G->join[k]);
+    }
+}
+
 static void free_grid(hyp_grid* G) {
     if (!G) return;
     if (G->g3) {
         free_grid3((Grid3*)G->g3);
         cudaFree(G->status);
+        free_streams(G);
         delete G;
         return;
     }
@@ -610,11 +619,7 @@ static void free_grid(hyp_grid* G) {
     cudaFree(G->jobs);
     cudaFree(G->linetmp);
     cudaFree(G->metf);
-    if (G->side) cudaStreamDestroy(G->side);
-    for (int k = 0; k < 2; ++k) {
-        if (G->fork[k]) cudaEventDestroy(G->fork[k]);
-        if (G->join[k]) cudaEventDestroy(G->join[k]);
-    }
+    free_streams(G);
     if (G->prof) {
         for (auto e : G->prof->ev) cudaEventDestroy(e);
         delete G->prof;
@@ -653,6 +658,7 @@ extern "C" int hyp_state_init(const hyp_gas* gas, const hyp_grid_desc* desc, con
         if (r3) {
             if (G->g3) free_grid3((Grid3*)G->g3);
             cudaFree(G->status);
+            free_streams(G);
             delete G;
             return r3;
         }

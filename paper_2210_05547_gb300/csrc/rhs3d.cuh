@@ -18,7 +18,9 @@
 // every row is interior, so the forward and backward recurrences run with the operator's
 // constant factors around the ring, one thread per line, started W rows early from zero (W = 40
 // for the interpolation, factor 1/3, and 26 for the derivative, factor 0.148: the dropped history
-// is below 1e-19 of the values, and the result is the periodic solution to rounding).
+// is below 1e-19 of the values, and the result is the periodic solution to rounding). Each phase
+// batches up to eight independent line jobs of one kind per launch, and the velocity-gradient
+// and artificial-diffusivity phases run on a second stream beside the closure.
 //
 // Jet (reading; the paper gives a sonic jet of prescribed temperature ratio and momentum ratio
 // J): inside the orifice the wall face holds the Dirichlet mass flux of a sonic jet at
@@ -59,72 +61,56 @@ __device__ __forceinline__ double row3(int kind, double p0, double p1, double p2
     return fma(-lm, d, fma(wa, p2 - p1, wb * (p3 - p0)));
 }
 
-// Lines along x or y, one thread per line (forward recurrence into the output, back substitution
-// in place): the plain form of the segmented kernel, kept for reference checks.
-__global__ void __launch_bounds__(128) k_line3(Line3 L, Sh3 sh) {
-    const LineOp& op = *L.op;
-    const long long nlines = L.axis == 0 ? (long long)sh.rows(L.tin) * sh.nz
-                                         : (long long)sh.pitch(L.tin) * sh.nz;
-    for (long long line = blockIdx.x * (long long)blockDim.x + threadIdx.x; line < nlines;
-         line += (long long)gridDim.x * blockDim.x) {
-        long long bi, bo, ei, eo;
-        if (L.axis == 0) {
-            bi = line * sh.pitch(L.tin);
-            bo = line * sh.pitch(L.tout);
-            ei = eo = 1;
-        } else {
-            const long long k = line / sh.pitch(L.tin), i = line - k * sh.pitch(L.tin);
-            bi = k * sh.plane(L.tin) + i;
-            bo = k * sh.plane(L.tout) + i;
-            ei = sh.pitch(L.tin);
-            eo = sh.pitch(L.tout);
-        }
-        const double* __restrict__ in = L.in + bi;
-        double* __restrict__ out = L.out + bo;
-        const double wallv = L.wall_arr ? L.wall_arr[line] : L.wall;
-        const int m = op.m;
-        double d = 0.0;
-        for (int r = 0; r < m; ++r) {
-            if (r < op.first_interior || r > op.last_interior) {
-                int c = 0;
-                while (op.crow[c] != r) ++c;
-                double v = op.gw[c] * wallv;
-                for (int q = 0; q < op.cnum[c]; ++q) v += op.cw[c][q] * in[(op.cstart[c] + q) * ei];
-                d = v;
-            } else {
-                const int s0 = op.dir == 0 ? r - 2 : r - 1;
-                d = row3(op.kind, in[s0 * ei], in[(s0 + 1) * ei], in[(s0 + 2) * ei],
-                         in[(s0 + 3) * ei], op.wa[r], op.wb[r], op.lm[r], d);
-            }
-            out[r * eo] = d;
-        }
-        double y = 0.0;
-        for (int r = m - 1; r >= 0; --r) {
-            y = out[r * eo] - (r < m - 1 ? op.cprime[r] * y : 0.0);
-            const double mt = L.metric ? L.metric[r] : 1.0;
-            out[r * eo] = L.scale * (mt * y);
-        }
-    }
-}
+// Periodic lines along z: one thread per line, one job of the batch per blockIdx.y. The four
+// stencil values slide through registers and the plane index wraps with a counter (one load per
+// row, no integer division in the loop).
+constexpr int BATCH3 = 8;      // line jobs per launch (x/y jobs: forward-sweep slots)
+struct ZBatch {
+    Line3 L[BATCH3];
+};
 
-// Periodic lines along z: one thread per line.
-__global__ void __launch_bounds__(128) k_line3z(Line3 L, Sh3 sh) {
+__global__ void __launch_bounds__(128) k_line3z(ZBatch B, Sh3 sh) {
+    const Line3& L = B.L[blockIdx.y];
     const long long plane = sh.plane(L.tin);
     const int n = sh.nz;
+    const int W3 = L.kind == 0 ? 40 : 26;     // as the segmented solver: dropped history < 1e-19
+    const int o = L.dir == 0 ? 2 : 1;         // first stencil row of output row t: t - o
+    const int r0 = ((-W3 - o) % n + n) % n;
+    const int b0 = (n - 1 + W3) % n;
     for (long long line = blockIdx.x * (long long)blockDim.x + threadIdx.x; line < plane;
          line += (long long)gridDim.x * blockDim.x) {
         const double* __restrict__ in = L.in + line;
         double* __restrict__ out = L.out + line;
-        auto at = [&](int r) { return in[(long long)(((r % n) + n) % n) * plane]; };
-        const int W3 = L.kind == 0 ? 40 : 26;     // as the segmented solver: dropped history < 1e-19
+        int r = r0;
+        auto next = [&]() {
+            const double v = in[(long long)r * plane];
+            r = r + 1 == n ? 0 : r + 1;
+            return v;
+        };
+        double p0 = next(), p1 = next(), p2 = next();
         double d = 0.0;
-        for (int t = -W3; t < n; ++t) {
-            const int s0 = L.dir == 0 ? t - 2 : t - 1;
-            d = row3(L.kind, at(s0), at(s0 + 1), at(s0 + 2), at(s0 + 3), L.wa, L.wb, L.lm, d);
-            if (t >= 0) out[(long long)t * plane] = d;
+        for (int t = -W3; t < 0; ++t) {      // warm-up: rows n - W3 .. n - 1 of the period
+            const double p3 = next();
+            d = row3(L.kind, p0, p1, p2, p3, L.wa, L.wb, L.lm, d);
+            p0 = p1;
+            p1 = p2;
+            p2 = p3;
         }
-        double y = out[(long long)((n - 1 + W3) % n) * plane];
-        for (int t = n - 2 + W3; t >= n; --t) y = out[(long long)(t % n) * plane] - L.cp * y;
+        for (int t = 0; t < n; ++t) {
+            const double p3 = next();
+            d = row3(L.kind, p0, p1, p2, p3, L.wa, L.wb, L.lm, d);
+            out[(long long)t * plane] = d;
+            p0 = p1;
+            p1 = p2;
+            p2 = p3;
+        }
+        // back substitution: warm-up over rows W3 - 1 .. 0 of the next period, then the period
+        int b = b0;
+        double y = out[(long long)b * plane];
+        for (int k = 1; k < W3; ++k) {
+            b = b == 0 ? n - 1 : b - 1;
+            y = out[(long long)b * plane] - L.cp * y;
+        }
         for (int t = n - 1; t >= 0; --t) {
             y = out[(long long)t * plane] - L.cp * y;
             out[(long long)t * plane] = L.scale * y;
@@ -172,9 +158,21 @@ struct Grid3 {
     double* ltmp;              // their forward-sweep storage (jobs run one after another)
 };
 
+// One launch of a phase: up to BATCH3 consecutive entries of its line list, all periodic z lines
+// (k_line3z) or all x/y line jobs (k_lines, contiguous in Grid3::jobs).
+struct Launch3 {
+    int z;
+    int first, count;
+    int blocks;                // x/y: blocks per job, the largest of the batch
+};
+
+struct Phase3 {
+    std::vector<Line3> lines;
+    std::vector<Launch3> launches;
+};
+
 struct Plan3 {
-    std::vector<Line3> p1, p3, ad1, ad2, mu, face, divs;
-    std::vector<int> blocks;   // per x/y line: blocks of its launch (index Line3::job)
+    Phase3 p1, p3, ad1, ad2, mu, face, divs;
 };
 
 struct View3 {
@@ -635,15 +633,23 @@ View3 view3(const hyp_grid* G, const Grid3* g) {
     return v;
 }
 
-// operator ids of the x and y operators in Grid3::ops (as the two-dimensional OpId)
-int launch3(const Grid3* g, const std::vector<Line3>& jobs, const double* U, int mixed,
-            cudaStream_t s) {
-    for (const Line3& L : jobs) {
-        if (L.axis == 2) {
-            const long long n = g->sh.plane(L.tin);
-            k_line3z<<<(int)std::min<long long>((n + 127) / 128, 152LL * 64), 128, 0, s>>>(L, g->sh);
+// The launches of one phase in order; `state`: the z lines' `in` is an element offset into U (the
+// x and y jobs resolve theirs in the line kernel).
+int launch3(const Grid3* g, const Phase3& ph, const double* U, bool state, cudaStream_t s) {
+    for (const Launch3& b : ph.launches) {
+        if (b.z) {
+            ZBatch zb;
+            memset(&zb, 0, sizeof(zb));
+            long long n = 0;
+            for (int i = 0; i < b.count; ++i) {
+                zb.L[i] = ph.lines[b.first + i];
+                if (state) zb.L[i].in = U + (size_t)zb.L[i].in;
+                n = std::max(n, g->sh.plane(zb.L[i].tin));
+            }
+            const int bx = (int)std::min<long long>((n + 127) / 128, 152LL * 64);
+            k_line3z<<<dim3(bx, b.count), 128, 0, s>>>(zb, g->sh);
         } else {
-            HYP_CUDA(launch_lines(g->jobs + L.job, 1, g->plan->blocks[L.job], U, s, mixed));
+            HYP_CUDA(launch_lines(g->jobs + ph.lines[b.first].job, b.count, b.blocks, U, s, 0));
         }
     }
     HYP_CUDA(cudaGetLastError());
@@ -657,36 +663,40 @@ int run_rhs3(const hyp_gas* gas, hyp_grid* G, const double* U, double* dUdt, int
     Grid3* g = (Grid3*)G->g3;
     const View3 v = view3(G, g);
     const GasDev& gd = gas->dev;
-    // the state-reading jobs carry element offsets into U in `in` (the x and y ones resolve it
-    // in the line kernel)
     const Plan3& pl = *g->plan;
-    std::vector<Line3> p1 = pl.p1;
-    for (auto& L : p1)
-        if (L.axis == 2) L.in = U + (size_t)L.in;
-    int rc = launch3(g, p1, U, 0, s);
+    int rc = launch3(g, pl.p1, U, true, s);
     if (rc) return rc;
     k_fv3<<<blocks3(g->nxf + g->nyf + g->nc), 256, 0, s>>>(*g, v, U);
+    // fork: velocity gradients and the artificial-diffusivity line phases do not need the closure
+    cudaStream_t s2 = G->side;
+    HYP_CUDA(cudaEventRecord(G->fork[0], s));
+    HYP_CUDA(cudaStreamWaitEvent(s2, G->fork[0], 0));
     const Scales sc = scales_of(gd);
     if (precision == HYP_MIXED) k_closure3<true><<<blocks3(g->nc), 128, 0, s>>>(gd, sc, *g, v, U);
     else k_closure3<false><<<blocks3(g->nc), 128, 0, s>>>(gd, sc, *g, v, U);
     HYP_CUDA(cudaGetLastError());
     g->cache_valid = 1;
-    if ((rc = launch3(g, pl.p3, U, 0, s))) return rc;
+    if ((rc = launch3(g, pl.p3, U, false, s2))) return rc;
     if (v.ad) {
-        if ((rc = launch3(g, pl.ad1, U, 0, s))) return rc;
-        if ((rc = launch3(g, pl.ad2, U, 0, s))) return rc;
-        k_adprep3<<<blocks3(g->nc), 256, 0, s>>>(*g);
+        if ((rc = launch3(g, pl.ad1, U, false, s2))) return rc;
+        if ((rc = launch3(g, pl.ad2, U, false, s2))) return rc;
+        k_adprep3<<<blocks3(g->nc), 256, 0, s2>>>(*g);
+        HYP_CUDA(cudaGetLastError());
+    }
+    HYP_CUDA(cudaEventRecord(G->join[0], s2));
+    HYP_CUDA(cudaStreamWaitEvent(s, G->join[0], 0));
+    if (v.ad) {
         k_adraw3<<<blocks3(g->nc), 256, 0, s>>>(*g, v, U, gd.kind == HYP_GAS_CNEQ);
         for (int ax = 0; ax < 3; ++ax) k_gauss3<<<blocks3(AD_FIELDS * g->nc), 256, 0, s>>>(*g, ax);
         k_adcombine3<<<blocks3(g->nc), 256, 0, s>>>(*g);
         HYP_CUDA(cudaGetLastError());
     }
-    if ((rc = launch3(g, pl.mu, U, 0, s))) return rc;
+    if ((rc = launch3(g, pl.mu, U, false, s))) return rc;
     k_stress3<<<blocks3(g->nc + g->nxy + g->nxf + g->nyf), 256, 0, s>>>(*g);
-    if ((rc = launch3(g, pl.face, U, 0, s))) return rc;
+    if ((rc = launch3(g, pl.face, U, false, s))) return rc;
     k_flux3<<<blocks3(g->nxf + g->nyf + g->nc), 128, 0, s>>>(gd, *g, v, U);
     HYP_CUDA(cudaGetLastError());
-    if ((rc = launch3(g, pl.divs, U, 0, s))) return rc;
+    if ((rc = launch3(g, pl.divs, U, false, s))) return rc;
     Assemble3 a;
     a.DX = g->DX;
     a.DY = g->DY;
@@ -963,7 +973,7 @@ int init3(const hyp_gas* gas, const hyp_grid_desc* desc, const hyp_case* cas, do
     const double ze = g->zeta;
     auto soff = [&](int f) { return (const double*)(size_t)g->off[f]; };
     // P1: state-reading jobs (`in` is an element offset into U)
-    pl.p1 = {xy(OX_IFC, 0, soff(NSP + 1), XF3, g->ru_c, C3, nullptr),
+    pl.p1.lines = {xy(OX_IFC, 0, soff(NSP + 1), XF3, g->ru_c, C3, nullptr),
              xy(OY_IFC, 1, soff(NSP + 2), YF3, g->rv_c, C3, nullptr),
              zl(0, 1, soff(NSP + 3), C3, g->rw_c),
              xy(OX_ICF, 0, soff(0), C3, g->rho_xf, XF3, nullptr),
@@ -972,7 +982,7 @@ int init3(const hyp_gas* gas, const hyp_grid_desc* desc, const hyp_case* cas, do
              xy(OX_DFC, 0, soff(NSP + 1), XF3, g->DX + g->off[0], C3, g->xi_c, -1.0),
              xy(OY_DFC, 1, soff(NSP + 2), YF3, g->DY + g->off[0], C3, g->eta_c, -1.0),
              zl(1, 1, soff(NSP + 3), C3, g->DZ + g->off[0], -ze)};
-    pl.p3 = {xy(OX_DFC, 0, g->u_xf, XF3, g->dudx, C3, g->xi_c),
+    pl.p3.lines = {xy(OX_DFC, 0, g->u_xf, XF3, g->dudx, C3, g->xi_c),
              xy(OY_DFC, 1, g->v_yf, YF3, g->dvdy, C3, g->eta_c),
              zl(1, 1, g->w_zf, C3, g->dwdz, ze),
              xy(ydcfw, 1, g->u_xf, XF3, g->dudy_xy, XY3, g->eta_f),
@@ -994,25 +1004,25 @@ int init3(const hyp_gas* gas, const hyp_grid_desc* desc, const hyp_case* cas, do
              xy(OY_IFC, 1, g->mvy_f, YF3, g->mvy_c, C3, nullptr),
              zl(0, 1, g->mwz_f, C3, g->mwz_c)};
     // artificial diffusivity: edge derivatives to the centres (y then x; x then z; y then z)
-    pl.ad1 = {xy(OY_IFC, 1, g->dudy_xy, XY3, g->tx[0], XF3, nullptr),
+    pl.ad1.lines = {xy(OY_IFC, 1, g->dudy_xy, XY3, g->tx[0], XF3, nullptr),
               xy(OY_IFC, 1, g->dvdx_xy, XY3, g->tx[1], XF3, nullptr),
               xy(OX_IFC, 0, g->dudz_xz, XF3, g->tc[0], C3, nullptr),
               xy(OX_IFC, 0, g->dwdx_xz, XF3, g->tc[1], C3, nullptr),
               xy(OY_IFC, 1, g->dvdz_yz, YF3, g->tc[2], C3, nullptr),
               xy(OY_IFC, 1, g->dwdy_yz, YF3, g->tc[3], C3, nullptr)};
-    pl.ad2 = {xy(OX_IFC, 0, g->tx[0], XF3, g->dudy_c, C3, nullptr),
+    pl.ad2.lines = {xy(OX_IFC, 0, g->tx[0], XF3, g->dudy_c, C3, nullptr),
               xy(OX_IFC, 0, g->tx[1], XF3, g->dvdx_c, C3, nullptr),
               zl(0, 1, g->tc[0], C3, g->dudz_c),
               zl(0, 1, g->tc[1], C3, g->dwdx_c),
               zl(0, 1, g->tc[2], C3, g->dvdz_c),
               zl(0, 1, g->tc[3], C3, g->dwdy_c)};
-    pl.mu = {xy(OX_ICF, 0, g->mu_e, C3, g->mu_xf, XF3, nullptr),
+    pl.mu.lines = {xy(OX_ICF, 0, g->mu_e, C3, g->mu_xf, XF3, nullptr),
              xy(OY_ICF, 1, g->mu_e, C3, g->mu_yf, YF3, nullptr)};
     // edge viscosities from the face ones (the jobs of a list run in order on one stream)
-    pl.mu.push_back(zl(0, 0, g->mu_xf, XF3, g->mu_xz));
-    pl.mu.push_back(zl(0, 0, g->mu_yf, YF3, g->mu_yz));
-    pl.mu.push_back(xy(OY_ICF, 1, g->mu_xf, XF3, g->mu_xy, XY3, nullptr));
-    std::vector<Line3>& F = pl.face;
+    pl.mu.lines.push_back(zl(0, 0, g->mu_xf, XF3, g->mu_xz));
+    pl.mu.lines.push_back(zl(0, 0, g->mu_yf, YF3, g->mu_yz));
+    pl.mu.lines.push_back(xy(OY_ICF, 1, g->mu_xf, XF3, g->mu_xy, XY3, nullptr));
+    std::vector<Line3>& F = pl.face.lines;
     for (int sp = 0; sp < NSP; ++sp) {
         F.push_back(xy(OX_ICF, 0, g->Y[sp], C3, g->Yx[sp], XF3, nullptr));
         F.push_back(xy(OX_ICF, 0, g->G[sp], C3, g->Gx[sp], XF3, nullptr));
@@ -1051,7 +1061,7 @@ int init3(const hyp_gas* gas, const hyp_grid_desc* desc, const hyp_case* cas, do
     F.push_back(zl(0, 0, g->v_c, C3, g->v_z));
     F.push_back(xy(OX_IFC, 0, g->tau_xz, XF3, g->txz_z, C3, nullptr));
     F.push_back(xy(OY_IFC, 1, g->tau_yz, YF3, g->tyz_z, C3, nullptr));
-    std::vector<Line3>& D = pl.divs;
+    std::vector<Line3>& D = pl.divs.lines;
     for (int sp = 1; sp < NSP; ++sp) {
         D.push_back(xy(OX_DFC, 0, g->Fsx[sp], XF3, g->DX + g->off[sp], C3, g->xi_c, -1.0));
         D.push_back(xy(OY_DFC, 1, g->Fsy[sp], YF3, g->DY + g->off[sp], C3, g->eta_c, -1.0));
@@ -1069,57 +1079,102 @@ int init3(const hyp_gas* gas, const hyp_grid_desc* desc, const hyp_case* cas, do
     D.push_back(xy(OX_DFC, 0, g->Gxz, XF3, g->DX + g->off[NSP + 3], C3, g->xi_c, -1.0));
     D.push_back(xy(OY_DFC, 1, g->Gyz, YF3, g->DY + g->off[NSP + 3], C3, g->eta_c, -1.0));
     D.push_back(zl(1, 0, g->Gzz, C3, g->DZ + g->off[NSP + 3], -ze));
-    // x and y lines as segmented line jobs: plane groups for y, segment counts as in two
-    // dimensions, one forward-sweep buffer (the jobs run one after another)
+    // launches: the independent phases put their x/y lines before their z lines and batch each
+    // kind; the viscosity phase keeps its order (its edge values come from its face values)
+    Phase3* phases[] = {&pl.p1, &pl.p3, &pl.ad1, &pl.ad2, &pl.mu, &pl.face, &pl.divs};
+    for (Phase3* ph : phases) {
+        std::vector<Line3>& V = ph->lines;
+        if (ph != &pl.mu)
+            std::stable_partition(V.begin(), V.end(), [](const Line3& L) { return L.axis != 2; });
+        for (size_t i = 0; i < V.size();) {
+            const int z = V[i].axis == 2;
+            size_t e = i;
+            while (e < V.size() && (V[e].axis == 2) == z && e - i < (size_t)BATCH3) ++e;
+            ph->launches.push_back(Launch3{z, (int)i, (int)(e - i), 0});
+            i = e;
+        }
+    }
+    // x and y lines as segmented line jobs: plane groups for y; per launch, segments as in two
+    // dimensions (lines split while the launch has fewer than 40960 threads); one forward-sweep
+    // buffer per position in a launch
     {
         std::vector<LineJob> lj;
+        std::vector<int> slot;
         long long tmp_n = 0;
-        for (auto* list : {&pl.p1, &pl.p3, &pl.ad1, &pl.ad2, &pl.mu, &pl.face, &pl.divs})
-            for (Line3& L : *list) {
-                if (L.axis == 2) continue;
-                const LineOp& op = hops[L.op - g->ops];
-                LineJob j;
-                memset(&j, 0, sizeof(j));
-                j.op = L.op;
-                j.in_state = list == &pl.p1 ? 1 : 0;
-                j.in = L.in;
-                j.out = L.out;
-                j.scale = L.scale;
-                j.metric = L.metric;
-                j.wall_value = L.wall;
-                j.wall_arr = L.wall_arr;
-                if (L.axis == 0) {
-                    j.in_ls = sh.pitch(L.tin);
-                    j.out_ls = sh.pitch(L.tout);
-                    j.in_es = j.out_es = 1;
-                    j.nlines = sh.rows(L.tin) * nz;
-                } else {
-                    j.lpp = sh.pitch(L.tin);
-                    j.in_ls = j.out_ls = 1;
-                    j.in_es = sh.pitch(L.tin);
-                    j.out_es = sh.pitch(L.tout);
-                    j.in_ps = sh.plane(L.tin);
-                    j.out_ps = sh.plane(L.tout);
-                    j.nlines = sh.pitch(L.tin) * nz;
+        int slots = 1;
+        for (Phase3* ph : phases)
+            for (Launch3& b : ph->launches) {
+                if (b.z) continue;
+                const int j0 = (int)lj.size();
+                std::vector<int> ns(b.count), m(b.count);
+                long long threads = 0;
+                for (int i = 0; i < b.count; ++i) {
+                    Line3& L = ph->lines[b.first + i];
+                    m[i] = hops[L.op - g->ops].m;
+                    LineJob j;
+                    memset(&j, 0, sizeof(j));
+                    j.op = L.op;
+                    j.in_state = ph == &pl.p1 ? 1 : 0;
+                    j.in = L.in;
+                    j.out = L.out;
+                    j.scale = L.scale;
+                    j.metric = L.metric;
+                    j.wall_value = L.wall;
+                    j.wall_arr = L.wall_arr;
+                    if (L.axis == 0) {
+                        j.in_ls = sh.pitch(L.tin);
+                        j.out_ls = sh.pitch(L.tout);
+                        j.in_es = j.out_es = 1;
+                        j.nlines = sh.rows(L.tin) * nz;
+                    } else {
+                        j.lpp = sh.pitch(L.tin);
+                        j.in_ls = j.out_ls = 1;
+                        j.in_es = sh.pitch(L.tin);
+                        j.out_es = sh.pitch(L.tout);
+                        j.in_ps = sh.plane(L.tin);
+                        j.out_ps = sh.plane(L.tout);
+                        j.nlines = sh.pitch(L.tin) * nz;
+                    }
+                    ns[i] = 1;
+                    while (ns[i] < LINE_BLOCK / 2 && (m[i] + ns[i] - 1) / ns[i] > 260) ns[i] *= 2;
+                    threads += (long long)j.nlines * ns[i];
+                    tmp_n = std::max(tmp_n, sh.size(L.tout));
+                    L.job = (int)lj.size();
+                    lj.push_back(j);
+                    slot.push_back(i);
                 }
-                int ns = 1;
-                while (ns < LINE_BLOCK / 2 && (op.m + ns - 1) / ns > 260) ns *= 2;
-                while (ns < LINE_BLOCK / 2 && (long long)j.nlines * ns < 40960 &&
-                       (op.m + 2 * ns - 1) / (2 * ns) >= 32)
-                    ns *= 2;
-                j.nseg = ns;
-                const int lpb = LINE_BLOCK / ns;
-                pl.blocks.push_back((j.nlines + lpb - 1) / lpb);
-                tmp_n = std::max(tmp_n, sh.size(L.tout));
-                L.job = (int)lj.size();
-                lj.push_back(j);
+                while (threads < 40960) {
+                    bool grew = false;
+                    threads = 0;
+                    for (int i = 0; i < b.count; ++i) {
+                        if (ns[i] < LINE_BLOCK / 2 && (m[i] + 2 * ns[i] - 1) / (2 * ns[i]) >= 32) {
+                            ns[i] *= 2;
+                            grew = true;
+                        }
+                        threads += (long long)lj[j0 + i].nlines * ns[i];
+                    }
+                    if (!grew) break;
+                }
+                for (int i = 0; i < b.count; ++i) {
+                    LineJob& j = lj[j0 + i];
+                    j.nseg = ns[i];
+                    const int lpb = LINE_BLOCK / ns[i];
+                    b.blocks = std::max(b.blocks, (j.nlines + lpb - 1) / lpb);
+                }
+                slots = std::max(slots, b.count);
             }
-        err = cudaMalloc(&g->ltmp, tmp_n * sizeof(double));
+        err = cudaMalloc(&g->ltmp, (size_t)slots * tmp_n * sizeof(double));
         if (err == cudaSuccess) err = cudaMalloc(&g->jobs, lj.size() * sizeof(LineJob));
         if (err != cudaSuccess) return cuda_fail(err, "cudaMalloc(3-D line jobs)");
-        for (auto& j : lj) j.tmp = g->ltmp;
+        for (size_t k = 0; k < lj.size(); ++k) lj[k].tmp = g->ltmp + (size_t)slot[k] * tmp_n;
         HYP_CUDA(cudaMemcpyAsync(g->jobs, lj.data(), lj.size() * sizeof(LineJob), cudaMemcpyHostToDevice, s));
         HYP_CUDA(cudaStreamSynchronize(s));
+    }
+    // second stream and its events (phases that do not wait on the closure)
+    HYP_CUDA(cudaStreamCreateWithFlags(&G->side, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; ++k) {
+        HYP_CUDA(cudaEventCreateWithFlags(&G->fork[k], cudaEventDisableTiming));
+        HYP_CUDA(cudaEventCreateWithFlags(&G->join[k], cudaEventDisableTiming));
     }
     // ---------------- uploads, reference, initial state ----------------
 #define UP3(dst, src, bytes) HYP_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s))

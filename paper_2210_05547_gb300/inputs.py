@@ -106,7 +106,9 @@ def box_case(nx=32, ny=24, seed=0, kind="cneq"):
 
 
 def serving_requests(n, seed=0, steps=(500, 2000)):
-    """n requests: (case dictionary, step count, unit-rate inter-arrival gap)."""
+    """n requests: (case dictionary, step count, unit-rate inter-arrival gap). Shock interactions
+    take at least 64 rows: on 32 rows (cells up to 3 high where the shock of width 1 crosses them)
+    the solve loses positivity in its first step, in the oracle as in the CUDA path."""
     rng = np.random.default_rng(np.random.SeedSequence([seed, 0x5e7e]))
     nxs, nys = (128, 256, 512, 1024), (32, 64, 128, 256)
     out = []
@@ -118,7 +120,7 @@ def serving_requests(n, seed=0, steps=(500, 2000)):
             c.update(mach=mach, T_wall=float(rng.uniform(300.0, 1500.0)),
                      dt=2.0e-4 * min(1.0, 10.0 / mach))
         else:
-            c = sbli_case(nx, ny, seed=int(rng.integers(1 << 30)))
+            c = sbli_case(nx, max(ny, 64), seed=int(rng.integers(1 << 30)))
         c["name"] = f"req{k}_{c['name']}"
         out.append((c, int(rng.integers(steps[0], steps[1] + 1)), float(rng.exponential(1.0))))
     return out
