@@ -294,28 +294,36 @@ def thermo_sweep(A, gas, dev, n, seed, reps=2, precision=0):
                       + (" over the heavy species, neutral" if any(c < 0 for c in q) else "")}
 
 
-def serving_bench(A, I, nreq, seed, precision):
+def serving_bench(A, I, nreq, seed, precision, air11=0.25):
     """Continuous batching of a stream of independent solves (serving workload): a closed-loop
     burst measures capacity, then nreq requests arrive as a Poisson process at 0.8 x capacity.
-    Reports time-to-solution percentiles and the throughput over the serving window."""
+    A share `air11` of the requests runs on eleven-species air, served by a second server (the
+    eleven-species library) beside the five-species one on the same GPU. Reports time-to-solution
+    percentiles and the throughput over the serving window."""
     import numpy as np
 
     def work(r):
         c, n, _ = r
         return c["nx"] * c["ny"] * 3 * n
 
-    calib = I.serving_requests(12, seed=seed + 1, steps=(20, 80))
-    sv = A.Server(precision=precision, max_members=64)
+    def servers():
+        return {"air5": A.Server(precision=precision, max_members=64),
+                "air11": A.Server(precision=precision, max_members=64, path=A.TABLE_AIR11)}
+
+    calib = I.serving_requests(12, seed=seed + 1, steps=(20, 80), air11=air11)
+    sv = servers()
     t0 = time.perf_counter()
     for c, n, _ in calib:
-        sv.submit(c, n)
-    sv.wait(timeout=900)
+        sv[c["table"]].submit(c, n)
+    for x in sv.values():
+        x.wait(timeout=900)
     cap = sum(work(r) for r in calib) / (time.perf_counter() - t0)      # points*RHS per second
-    sv.close()
-    reqs = I.serving_requests(nreq, seed=seed, steps=(20, 80))
+    for x in sv.values():
+        x.close()
+    reqs = I.serving_requests(nreq, seed=seed, steps=(20, 80), air11=air11)
     mean_work = sum(work(r) for r in reqs) / len(reqs)
     lam = 0.8 * cap / mean_work                                            # requests per second
-    sv = A.Server(precision=precision, max_members=64)
+    sv = servers()
     ids = []
     t_start = time.perf_counter()
     t_next = t_start
@@ -324,11 +332,19 @@ def serving_bench(A, I, nreq, seed, precision):
         delay = t_next - time.perf_counter()
         if delay > 0:
             time.sleep(delay)
-        ids.append(sv.submit(c, n))
-    sv.wait(timeout=1800)
-    st = [sv.stats(i) for i in ids]
-    cnt = sv.counters()
-    sv.close()
+        ids.append((c["table"], sv[c["table"]].submit(c, n)))
+    for x in sv.values():
+        x.wait(timeout=1800)
+    st = [sv[t].stats(i) for t, i in ids]
+    per = {}
+    for t, x in sv.items():
+        cnt = x.counters()
+        mine = [r for r in reqs if r[0]["table"] == t]
+        per[t] = {"requests": len(mine),
+                  "busy_throughput_mpts_rhs_s": sum(work(r) for r in mine) / max(cnt["busy_s"], 1e-30) / 1e6,
+                  "mean_batch": cnt["member_steps"] / max(cnt["batch_steps"], 1),
+                  "max_batch": cnt["max_members"]}
+        x.close()
     tts = np.array([s["t_finish"] - s["t_submit"] for s in st])
     wait = np.array([s["t_admit"] - s["t_submit"] for s in st])
     span = max(s["t_finish"] for s in st) - min(s["t_submit"] for s in st)
@@ -339,17 +355,15 @@ def serving_bench(A, I, nreq, seed, precision):
             "tts_p50_s": float(np.percentile(tts, 50)), "tts_p99_s": float(np.percentile(tts, 99)),
             "queue_wait_p50_s": float(np.percentile(wait, 50)),
             "throughput_mpts_rhs_s": total / span / 1e6,
-            "busy_throughput_mpts_rhs_s": total / max(cnt["busy_s"], 1e-30) / 1e6,
-            "mean_batch": cnt["member_steps"] / max(cnt["batch_steps"], 1),
-            "max_batch": cnt["max_members"],
+            "servers": per,
             "errors": int(sum(1 for s in st if s["error"])),
             "status_nonzero": int(sum(1 for s in st if s["status"])),
             "status_requests": [{"name": c["name"], "nx": c["nx"], "ny": c["ny"],
                                  "mach": round(c["mach"], 3), "T_wall": round(c.get("T_wall", 0.0), 1),
                                  "steps": n, "status": s["status"]}
                                 for (c, n, _), s in zip(reqs, st) if s["status"]],
-            "workload": "grids 128x32 to 1024x256, boundary layers Mach 5-20 (wall 300-1500 K) and "
-                        "shock interactions, 20-80 RK3 steps each"}
+            "workload": f"grids 128x32 to 1024x256, boundary layers Mach 5-20 (wall 300-1500 K) and "
+                        f"shock interactions, 20-80 RK3 steps each, {air11:.0%} on eleven-species air"}
 
 
 def jet3d_bench(A, I, dev, rank, world, barrier, flush, steps=2, warmup=1):

@@ -412,6 +412,7 @@ class Server:
     def __init__(self, precision=FP64, reserve_bytes=4 << 30, max_members=64, kind="cneq",
                  path=TABLE_AIR5):
         self.L = lib(table_species(path))
+        self.path = os.path.abspath(path)
         h = ctypes.c_void_p()
         _check(self.L.hyp_server_create(path.encode(), GAS_KINDS[kind], precision,
                                          int(reserve_bytes), int(max_members), ctypes.byref(h)),
@@ -419,6 +420,8 @@ class Server:
         self.handle = h
 
     def submit(self, cfg, nsteps, dt=None, noise=None, keep_result=False):
+        if os.path.abspath(table_path(cfg)) != self.path:
+            raise ValueError(f"request on {table_path(cfg)}, server on {self.path}")
         r = Request()
         r.fs = freestream_struct(cfg)
         r.grid = grid_struct(cfg)

@@ -16,7 +16,8 @@ Workloads (shapes follow the paper's cases; there is no dataset):
 * ``serving_requests`` -- a stream of independent boundary-layer and shock / boundary-layer
   solves for the serving path: grids from 128 x 32 to 1024 x 256, boundary layers at Mach 5-20
   with wall temperature 300-1500 K, interactions at the Mach and deflection their seed draws,
-  seeded step counts and unit-rate exponential inter-arrival gaps (scaled by the caller).
+  five- or eleven-species air, seeded step counts and unit-rate exponential inter-arrival gaps
+  (scaled by the caller).
 * ``thermo_states`` -- independent thermochemical states: T log-uniform in [300, 15000] K,
   rho log-uniform in [1e-4, 1] kg/m^3, mass fractions Dirichlet(1); ``charged_states`` the same
   for a table with ions and electrons, Dirichlet(1) over the heavy species and the electrons that
@@ -105,11 +106,14 @@ def box_case(nx=32, ny=24, seed=0, kind="cneq"):
     return c
 
 
-def serving_requests(n, seed=0, steps=(500, 2000)):
+def serving_requests(n, seed=0, steps=(500, 2000), air11=0.0):
     """n requests: (case dictionary, step count, unit-rate inter-arrival gap). Shock interactions
     take at least 64 rows: on 32 rows (cells up to 3 high where the shock of width 1 crosses them)
-    the solve loses positivity in its first step, in the oracle as in the CUDA path."""
+    the solve loses positivity in its first step, in the oracle as in the CUDA path. A share
+    `air11` of the requests runs on eleven-species air (drawn from a stream of its own, so the
+    requests themselves do not depend on the share)."""
     rng = np.random.default_rng(np.random.SeedSequence([seed, 0x5e7e]))
+    pick = np.random.default_rng(np.random.SeedSequence([seed, 0x11a1]))
     nxs, nys = (128, 256, 512, 1024), (32, 64, 128, 256)
     out = []
     for k in range(n):
@@ -121,6 +125,8 @@ def serving_requests(n, seed=0, steps=(500, 2000)):
                      dt=2.0e-4 * min(1.0, 10.0 / mach))
         else:
             c = sbli_case(nx, max(ny, 64), seed=int(rng.integers(1 << 30)))
+        if pick.random() < air11:
+            c = with_species(c, "air11")
         c["name"] = f"req{k}_{c['name']}"
         out.append((c, int(rng.integers(steps[0], steps[1] + 1)), float(rng.exponential(1.0))))
     return out

@@ -45,6 +45,27 @@ def test_results_identical_alone_and_in_the_mix(precision):
     sv.close()
 
 
+def test_eleven_species_requests_identical_alone_and_in_the_mix():
+    from paper_2210_05547_gb300 import abi as A
+    reqs = I.serving_requests(4, seed=13, steps=(4, 12), air11=1.0)
+    assert all(c["table"] == "air11" for c, _, _ in reqs)
+    sv = A.Server(precision=0, max_members=8, path=A.TABLE_AIR11)
+    with pytest.raises(ValueError):
+        sv.submit(I.bl_case(128, 32), 2)                # a five-species request
+    ids = []
+    for cfg, nsteps, gap in reqs:
+        noise = I.state_noise(A.state_len(cfg), cfg["seed"])
+        ids.append(sv.submit(cfg, nsteps, noise=noise, keep_result=True))
+        time.sleep(0.02 * gap)
+    sv.wait(timeout=600)
+    for rid, (cfg, nsteps, _) in zip(ids, reqs):
+        st = sv.stats(rid)
+        assert st["done"] == 1 and st["error"] == 0 and st["status"] == 0, st
+        got = sv.result(rid, cfg)
+        assert np.array_equal(got, _alone(cfg, nsteps, 0)), cfg["name"]
+    sv.close()
+
+
 def test_admission_waits_for_memory():
     import torch
     from paper_2210_05547_gb300 import abi as A
