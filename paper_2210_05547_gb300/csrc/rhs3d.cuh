@@ -52,6 +52,7 @@ struct Line3 {
     int kind, dir;             // z lines: 0 interpolation / 1 derivative; 0 c->f / 1 f->c
     double wa, wb, lm, cp;     // z lines: the operator's constant factors
     int job;                   // x, y lines: index of the segmented line job (Grid3::jobs)
+    int f32;                   // feeds only diffusive fluxes: binary32 rows under HYP_MIXED
 };
 
 
@@ -69,52 +70,117 @@ struct ZBatch {
     Line3 L[BATCH3];
 };
 
-__global__ void __launch_bounds__(128) k_line3z(ZBatch B, Sh3 sh) {
+struct ZRing {
+    int n, W3, r0, b0;         // period, warm-up rows, first stencil row, first warm-up back row
+    long long plane;
+    __device__ ZRing(const Line3& L, const Sh3& sh) {
+        plane = sh.plane(L.tin);
+        n = sh.nz;
+        W3 = L.kind == 0 ? 40 : 26;   // as the segmented solver: dropped history < 1e-19
+        const int o = L.dir == 0 ? 2 : 1;          // first stencil row of output row t: t - o
+        r0 = ((-W3 - o) % n + n) % n;
+        b0 = (n - 1 + W3) % n;
+    }
+};
+
+__device__ __forceinline__ void zline64(const Line3& L, const ZRing& z,
+                                        const double* __restrict__ in, double* __restrict__ out) {
+    const long long plane = z.plane;
+    const int n = z.n, W3 = z.W3;
+    int r = z.r0;
+    auto next = [&]() {
+        const double v = in[(long long)r * plane];
+        r = r + 1 == n ? 0 : r + 1;
+        return v;
+    };
+    double p0 = next(), p1 = next(), p2 = next();
+    double d = 0.0;
+    for (int t = -W3; t < 0; ++t) {      // warm-up: rows n - W3 .. n - 1 of the period
+        const double p3 = next();
+        d = row3(L.kind, p0, p1, p2, p3, L.wa, L.wb, L.lm, d);
+        p0 = p1;
+        p1 = p2;
+        p2 = p3;
+    }
+    for (int t = 0; t < n; ++t) {
+        const double p3 = next();
+        d = row3(L.kind, p0, p1, p2, p3, L.wa, L.wb, L.lm, d);
+        out[(long long)t * plane] = d;
+        p0 = p1;
+        p1 = p2;
+        p2 = p3;
+    }
+    // back substitution: warm-up over rows W3 - 1 .. 0 of the next period, then the period
+    int b = z.b0;
+    double y = out[(long long)b * plane];
+    for (int k = 1; k < W3; ++k) {
+        b = b == 0 ? n - 1 : b - 1;
+        y = out[(long long)b * plane] - L.cp * y;
+    }
+    for (int t = n - 1; t >= 0; --t) {
+        y = out[(long long)t * plane] - L.cp * y;
+        out[(long long)t * plane] = L.scale * y;
+    }
+}
+
+__device__ __forceinline__ float* zslot(double* p) { return reinterpret_cast<float*>(p); }
+
+// The same in binary32 (HYP_MIXED, lines feeding only diffusive fluxes): inputs rounded with the
+// integer conversions of fp32.cuh, forward values kept as binary32 in the first half of their
+// output slot, outputs widened back to binary64.
+__device__ __forceinline__ void zline32(const Line3& L, const ZRing& z,
+                                        const double* __restrict__ in, double* __restrict__ out) {
+    const long long plane = z.plane;
+    const int n = z.n, W3 = z.W3;
+    const float wa = f32_of(L.wa), wb = f32_of(L.wb), lm = f32_of(L.lm), cp = f32_of(L.cp),
+                sc = f32_of(L.scale);
+    auto row = [&](float p0, float p1, float p2, float p3, float d) {
+        if (L.kind == 0) return fmaf(-lm, d, fmaf(wa, p1 + p2, wb * (p0 + p3)));
+        return fmaf(-lm, d, fmaf(wa, p2 - p1, wb * (p3 - p0)));
+    };
+    int r = z.r0;
+    auto next = [&]() {
+        const float v = f32_of(in[(long long)r * plane]);
+        r = r + 1 == n ? 0 : r + 1;
+        return v;
+    };
+    float p0 = next(), p1 = next(), p2 = next();
+    float d = 0.0f;
+    for (int t = -W3; t < 0; ++t) {
+        const float p3 = next();
+        d = row(p0, p1, p2, p3, d);
+        p0 = p1;
+        p1 = p2;
+        p2 = p3;
+    }
+    for (int t = 0; t < n; ++t) {
+        const float p3 = next();
+        d = row(p0, p1, p2, p3, d);
+        *zslot(out + (long long)t * plane) = d;
+        p0 = p1;
+        p1 = p2;
+        p2 = p3;
+    }
+    int b = z.b0;
+    float y = *zslot(out + (long long)b * plane);
+    for (int k = 1; k < W3; ++k) {
+        b = b == 0 ? n - 1 : b - 1;
+        y = fmaf(-cp, y, *zslot(out + (long long)b * plane));
+    }
+    for (int t = n - 1; t >= 0; --t) {
+        y = fmaf(-cp, y, *zslot(out + (long long)t * plane));
+        out[(long long)t * plane] = f64_of(sc * y);
+    }
+}
+
+__global__ void __launch_bounds__(128) k_line3z(ZBatch B, Sh3 sh, int mixed) {
     const Line3& L = B.L[blockIdx.y];
-    const long long plane = sh.plane(L.tin);
-    const int n = sh.nz;
-    const int W3 = L.kind == 0 ? 40 : 26;     // as the segmented solver: dropped history < 1e-19
-    const int o = L.dir == 0 ? 2 : 1;         // first stencil row of output row t: t - o
-    const int r0 = ((-W3 - o) % n + n) % n;
-    const int b0 = (n - 1 + W3) % n;
-    for (long long line = blockIdx.x * (long long)blockDim.x + threadIdx.x; line < plane;
+    const ZRing z(L, sh);
+    const bool f32 = mixed && L.f32;      // uniform per block
+    for (long long line = blockIdx.x * (long long)blockDim.x + threadIdx.x; line < z.plane;
          line += (long long)gridDim.x * blockDim.x) {
-        const double* __restrict__ in = L.in + line;
-        double* __restrict__ out = L.out + line;
-        int r = r0;
-        auto next = [&]() {
-            const double v = in[(long long)r * plane];
-            r = r + 1 == n ? 0 : r + 1;
-            return v;
-        };
-        double p0 = next(), p1 = next(), p2 = next();
-        double d = 0.0;
-        for (int t = -W3; t < 0; ++t) {      // warm-up: rows n - W3 .. n - 1 of the period
-            const double p3 = next();
-            d = row3(L.kind, p0, p1, p2, p3, L.wa, L.wb, L.lm, d);
-            p0 = p1;
-            p1 = p2;
-            p2 = p3;
-        }
-        for (int t = 0; t < n; ++t) {
-            const double p3 = next();
-            d = row3(L.kind, p0, p1, p2, p3, L.wa, L.wb, L.lm, d);
-            out[(long long)t * plane] = d;
-            p0 = p1;
-            p1 = p2;
-            p2 = p3;
-        }
-        // back substitution: warm-up over rows W3 - 1 .. 0 of the next period, then the period
-        int b = b0;
-        double y = out[(long long)b * plane];
-        for (int k = 1; k < W3; ++k) {
-            b = b == 0 ? n - 1 : b - 1;
-            y = out[(long long)b * plane] - L.cp * y;
-        }
-        for (int t = n - 1; t >= 0; --t) {
-            y = out[(long long)t * plane] - L.cp * y;
-            out[(long long)t * plane] = L.scale * y;
-        }
+        if (f32) zline32(L, z, L.in + line, L.out + line);
+        else zline64(L, z, L.in + line, L.out + line);
     }
 }
 
@@ -150,6 +216,7 @@ struct Grid3 {
     double *Uref, *sigma;
     uint8_t* mask;
     double *xi_c, *xi_f, *eta_c, *eta_f, *Tw;
+    float* metf;               // binary32 copies of xi_c, xi_f, eta_c, eta_f (HYP_MIXED line jobs)
     LineOp* ops;
     double* opdata;
     Line3 zop[2][2];           // periodic z operators [kind][dir] (constants only)
@@ -608,6 +675,7 @@ void free_grid3(Grid3* g) {
     delete g->plan;
     cudaFree(g->jobs);
     cudaFree(g->ltmp);
+    cudaFree(g->metf);
     cudaFree(g->pool);
     cudaFree(g->mask);
     cudaFree(g->ops);
@@ -635,7 +703,8 @@ View3 view3(const hyp_grid* G, const Grid3* g) {
 
 // The launches of one phase in order; `state`: the z lines' `in` is an element offset into U (the
 // x and y jobs resolve theirs in the line kernel).
-int launch3(const Grid3* g, const Phase3& ph, const double* U, bool state, cudaStream_t s) {
+int launch3(const Grid3* g, const Phase3& ph, const double* U, bool state, int mixed,
+            cudaStream_t s) {
     for (const Launch3& b : ph.launches) {
         if (b.z) {
             ZBatch zb;
@@ -647,9 +716,9 @@ int launch3(const Grid3* g, const Phase3& ph, const double* U, bool state, cudaS
                 n = std::max(n, g->sh.plane(zb.L[i].tin));
             }
             const int bx = (int)std::min<long long>((n + 127) / 128, 152LL * 64);
-            k_line3z<<<dim3(bx, b.count), 128, 0, s>>>(zb, g->sh);
+            k_line3z<<<dim3(bx, b.count), 128, 0, s>>>(zb, g->sh, mixed);
         } else {
-            HYP_CUDA(launch_lines(g->jobs + ph.lines[b.first].job, b.count, b.blocks, U, s, 0));
+            HYP_CUDA(launch_lines(g->jobs + ph.lines[b.first].job, b.count, b.blocks, U, s, mixed));
         }
     }
     HYP_CUDA(cudaGetLastError());
@@ -664,7 +733,8 @@ int run_rhs3(const hyp_gas* gas, hyp_grid* G, const double* U, double* dUdt, int
     const View3 v = view3(G, g);
     const GasDev& gd = gas->dev;
     const Plan3& pl = *g->plan;
-    int rc = launch3(g, pl.p1, U, true, s);
+    const int mx = precision == HYP_MIXED ? 1 : 0;
+    int rc = launch3(g, pl.p1, U, true, mx, s);
     if (rc) return rc;
     k_fv3<<<blocks3(g->nxf + g->nyf + g->nc), 256, 0, s>>>(*g, v, U);
     // fork: velocity gradients and the artificial-diffusivity line phases do not need the closure
@@ -676,10 +746,10 @@ int run_rhs3(const hyp_gas* gas, hyp_grid* G, const double* U, double* dUdt, int
     else k_closure3<false><<<blocks3(g->nc), 128, 0, s>>>(gd, sc, *g, v, U);
     HYP_CUDA(cudaGetLastError());
     g->cache_valid = 1;
-    if ((rc = launch3(g, pl.p3, U, false, s2))) return rc;
+    if ((rc = launch3(g, pl.p3, U, false, mx, s2))) return rc;
     if (v.ad) {
-        if ((rc = launch3(g, pl.ad1, U, false, s2))) return rc;
-        if ((rc = launch3(g, pl.ad2, U, false, s2))) return rc;
+        if ((rc = launch3(g, pl.ad1, U, false, mx, s2))) return rc;
+        if ((rc = launch3(g, pl.ad2, U, false, mx, s2))) return rc;
         k_adprep3<<<blocks3(g->nc), 256, 0, s2>>>(*g);
         HYP_CUDA(cudaGetLastError());
     }
@@ -691,12 +761,12 @@ int run_rhs3(const hyp_gas* gas, hyp_grid* G, const double* U, double* dUdt, int
         k_adcombine3<<<blocks3(g->nc), 256, 0, s>>>(*g);
         HYP_CUDA(cudaGetLastError());
     }
-    if ((rc = launch3(g, pl.mu, U, false, s))) return rc;
+    if ((rc = launch3(g, pl.mu, U, false, mx, s))) return rc;
     k_stress3<<<blocks3(g->nc + g->nxy + g->nxf + g->nyf), 256, 0, s>>>(*g);
-    if ((rc = launch3(g, pl.face, U, false, s))) return rc;
+    if ((rc = launch3(g, pl.face, U, false, mx, s))) return rc;
     k_flux3<<<blocks3(g->nxf + g->nyf + g->nc), 128, 0, s>>>(gd, *g, v, U);
     HYP_CUDA(cudaGetLastError());
-    if ((rc = launch3(g, pl.divs, U, false, s))) return rc;
+    if ((rc = launch3(g, pl.divs, U, false, mx, s))) return rc;
     Assemble3 a;
     a.DX = g->DX;
     a.DY = g->DY;
@@ -1016,51 +1086,58 @@ int init3(const hyp_gas* gas, const hyp_grid_desc* desc, const hyp_case* cas, do
               zl(0, 1, g->tc[1], C3, g->dwdx_c),
               zl(0, 1, g->tc[2], C3, g->dvdz_c),
               zl(0, 1, g->tc[3], C3, g->dwdy_c)};
-    pl.mu.lines = {xy(OX_ICF, 0, g->mu_e, C3, g->mu_xf, XF3, nullptr),
-             xy(OY_ICF, 1, g->mu_e, C3, g->mu_yf, YF3, nullptr)};
+    // under HYP_MIXED the jobs feeding only the diffusive fluxes (viscosities, diffusion and
+    // conduction coefficients, gradients of X_s and T, stresses, the velocities of the viscous
+    // work) run their rows in binary32; those feeding the convective fluxes stay FP64
+    auto f = [](Line3 L) {
+        L.f32 = 1;
+        return L;
+    };
+    pl.mu.lines = {f(xy(OX_ICF, 0, g->mu_e, C3, g->mu_xf, XF3, nullptr)),
+                   f(xy(OY_ICF, 1, g->mu_e, C3, g->mu_yf, YF3, nullptr))};
     // edge viscosities from the face ones (the jobs of a list run in order on one stream)
-    pl.mu.lines.push_back(zl(0, 0, g->mu_xf, XF3, g->mu_xz));
-    pl.mu.lines.push_back(zl(0, 0, g->mu_yf, YF3, g->mu_yz));
-    pl.mu.lines.push_back(xy(OY_ICF, 1, g->mu_xf, XF3, g->mu_xy, XY3, nullptr));
+    pl.mu.lines.push_back(f(zl(0, 0, g->mu_xf, XF3, g->mu_xz)));
+    pl.mu.lines.push_back(f(zl(0, 0, g->mu_yf, YF3, g->mu_yz)));
+    pl.mu.lines.push_back(f(xy(OY_ICF, 1, g->mu_xf, XF3, g->mu_xy, XY3, nullptr)));
     std::vector<Line3>& F = pl.face.lines;
     for (int sp = 0; sp < NSP; ++sp) {
         F.push_back(xy(OX_ICF, 0, g->Y[sp], C3, g->Yx[sp], XF3, nullptr));
-        F.push_back(xy(OX_ICF, 0, g->G[sp], C3, g->Gx[sp], XF3, nullptr));
-        F.push_back(xy(OX_ICF, 0, g->h[sp], C3, g->hx[sp], XF3, nullptr));
-        F.push_back(xy(OX_DCF, 0, g->X[sp], C3, g->dXdx[sp], XF3, g->xi_f));
+        F.push_back(f(xy(OX_ICF, 0, g->G[sp], C3, g->Gx[sp], XF3, nullptr)));
+        F.push_back(f(xy(OX_ICF, 0, g->h[sp], C3, g->hx[sp], XF3, nullptr)));
+        F.push_back(f(xy(OX_DCF, 0, g->X[sp], C3, g->dXdx[sp], XF3, g->xi_f)));
         F.push_back(xy(OY_ICF, 1, g->Y[sp], C3, g->Yy[sp], YF3, nullptr));
-        F.push_back(xy(OY_ICF, 1, g->G[sp], C3, g->Gy[sp], YF3, nullptr));
-        F.push_back(xy(OY_ICF, 1, g->h[sp], C3, g->hy[sp], YF3, nullptr));
-        F.push_back(xy(OY_DCF, 1, g->X[sp], C3, g->dXdy[sp], YF3, g->eta_f));
+        F.push_back(f(xy(OY_ICF, 1, g->G[sp], C3, g->Gy[sp], YF3, nullptr)));
+        F.push_back(f(xy(OY_ICF, 1, g->h[sp], C3, g->hy[sp], YF3, nullptr)));
+        F.push_back(f(xy(OY_DCF, 1, g->X[sp], C3, g->dXdy[sp], YF3, g->eta_f)));
         F.push_back(zl(0, 0, g->Y[sp], C3, g->Yz[sp]));
-        F.push_back(zl(0, 0, g->G[sp], C3, g->Gz[sp]));
-        F.push_back(zl(0, 0, g->h[sp], C3, g->hz[sp]));
-        F.push_back(zl(1, 0, g->X[sp], C3, g->dXdz[sp], ze));
+        F.push_back(f(zl(0, 0, g->G[sp], C3, g->Gz[sp])));
+        F.push_back(f(zl(0, 0, g->h[sp], C3, g->hz[sp])));
+        F.push_back(f(zl(1, 0, g->X[sp], C3, g->dXdz[sp], ze)));
     }
     F.push_back(xy(OX_ICF, 0, g->H, C3, g->Hx, XF3, nullptr));
-    F.push_back(xy(OX_ICF, 0, g->K, C3, g->Kx, XF3, nullptr));
-    F.push_back(xy(OX_DCF, 0, g->T, C3, g->dTdx, XF3, g->xi_f));
-    F.push_back(xy(OX_ICF, 0, g->tau_xx, C3, g->txx_x, XF3, nullptr));
-    F.push_back(xy(OX_ICF, 0, g->v_c, C3, g->v_x, XF3, nullptr));
-    F.push_back(xy(OX_ICF, 0, g->w_c, C3, g->w_x, XF3, nullptr));
-    F.push_back(xy(OY_IFC, 1, g->tau_xy, XY3, g->txy_x, XF3, nullptr));
-    F.push_back(zl(0, 1, g->tau_xz, XF3, g->txz_x));
+    F.push_back(f(xy(OX_ICF, 0, g->K, C3, g->Kx, XF3, nullptr)));
+    F.push_back(f(xy(OX_DCF, 0, g->T, C3, g->dTdx, XF3, g->xi_f)));
+    F.push_back(f(xy(OX_ICF, 0, g->tau_xx, C3, g->txx_x, XF3, nullptr)));
+    F.push_back(f(xy(OX_ICF, 0, g->v_c, C3, g->v_x, XF3, nullptr)));
+    F.push_back(f(xy(OX_ICF, 0, g->w_c, C3, g->w_x, XF3, nullptr)));
+    F.push_back(f(xy(OY_IFC, 1, g->tau_xy, XY3, g->txy_x, XF3, nullptr)));
+    F.push_back(f(zl(0, 1, g->tau_xz, XF3, g->txz_x)));
     F.push_back(xy(OY_ICF, 1, g->H, C3, g->Hy, YF3, nullptr));
-    F.push_back(xy(OY_ICF, 1, g->K, C3, g->Ky, YF3, nullptr));
-    F.push_back(xy(ydcfw, 1, g->T, C3, g->dTdy, YF3, g->eta_f, 1.0, wall ? g->Tw : nullptr));
-    F.push_back(xy(OY_ICF, 1, g->tau_yy, C3, g->tyy_y, YF3, nullptr));
-    F.push_back(xy(yicfw, 1, g->u_c, C3, g->u_y, YF3, nullptr));
-    F.push_back(xy(yicfw, 1, g->w_c, C3, g->w_y, YF3, nullptr));
-    F.push_back(xy(OX_IFC, 0, g->tau_xy, XY3, g->txy_y, YF3, nullptr));
-    F.push_back(zl(0, 1, g->tau_yz, YF3, g->tyz_y));
+    F.push_back(f(xy(OY_ICF, 1, g->K, C3, g->Ky, YF3, nullptr)));
+    F.push_back(f(xy(ydcfw, 1, g->T, C3, g->dTdy, YF3, g->eta_f, 1.0, wall ? g->Tw : nullptr)));
+    F.push_back(f(xy(OY_ICF, 1, g->tau_yy, C3, g->tyy_y, YF3, nullptr)));
+    F.push_back(f(xy(yicfw, 1, g->u_c, C3, g->u_y, YF3, nullptr)));
+    F.push_back(f(xy(yicfw, 1, g->w_c, C3, g->w_y, YF3, nullptr)));
+    F.push_back(f(xy(OX_IFC, 0, g->tau_xy, XY3, g->txy_y, YF3, nullptr)));
+    F.push_back(f(zl(0, 1, g->tau_yz, YF3, g->tyz_y)));
     F.push_back(zl(0, 0, g->H, C3, g->Hz));
-    F.push_back(zl(0, 0, g->K, C3, g->Kz));
-    F.push_back(zl(1, 0, g->T, C3, g->dTdz, ze));
-    F.push_back(zl(0, 0, g->tau_zz, C3, g->tzz_z));
-    F.push_back(zl(0, 0, g->u_c, C3, g->u_z));
-    F.push_back(zl(0, 0, g->v_c, C3, g->v_z));
-    F.push_back(xy(OX_IFC, 0, g->tau_xz, XF3, g->txz_z, C3, nullptr));
-    F.push_back(xy(OY_IFC, 1, g->tau_yz, YF3, g->tyz_z, C3, nullptr));
+    F.push_back(f(zl(0, 0, g->K, C3, g->Kz)));
+    F.push_back(f(zl(1, 0, g->T, C3, g->dTdz, ze)));
+    F.push_back(f(zl(0, 0, g->tau_zz, C3, g->tzz_z)));
+    F.push_back(f(zl(0, 0, g->u_c, C3, g->u_z)));
+    F.push_back(f(zl(0, 0, g->v_c, C3, g->v_z)));
+    F.push_back(f(xy(OX_IFC, 0, g->tau_xz, XF3, g->txz_z, C3, nullptr)));
+    F.push_back(f(xy(OY_IFC, 1, g->tau_yz, YF3, g->tyz_z, C3, nullptr)));
     std::vector<Line3>& D = pl.divs.lines;
     for (int sp = 1; sp < NSP; ++sp) {
         D.push_back(xy(OX_DFC, 0, g->Fsx[sp], XF3, g->DX + g->off[sp], C3, g->xi_c, -1.0));
@@ -1098,6 +1175,11 @@ int init3(const hyp_gas* gas, const hyp_grid_desc* desc, const hyp_case* cas, do
     // dimensions (lines split while the launch has fewer than 40960 threads); one forward-sweep
     // buffer per position in a launch
     {
+        // binary32 copies of the metrics for the jobs that run binary32 rows
+        err = cudaMalloc(&g->metf, (2 * (nx + ny) + 2) * sizeof(float));
+        if (err != cudaSuccess) return cuda_fail(err, "cudaMalloc(3-D binary32 metrics)");
+        const double* met_d[4] = {g->xi_c, g->xi_f, g->eta_c, g->eta_f};
+        const long long met_off[4] = {0, nx, 2LL * nx + 1, 2LL * nx + 1 + ny};
         std::vector<LineJob> lj;
         std::vector<int> slot;
         long long tmp_n = 0;
@@ -1121,6 +1203,9 @@ int init3(const hyp_gas* gas, const hyp_grid_desc* desc, const hyp_case* cas, do
                     j.metric = L.metric;
                     j.wall_value = L.wall;
                     j.wall_arr = L.wall_arr;
+                    j.f32ok = L.f32;
+                    for (int k = 0; k < 4; ++k)
+                        if (L.metric && L.metric == met_d[k]) j.metric_f = g->metf + met_off[k];
                     if (L.axis == 0) {
                         j.in_ls = sh.pitch(L.tin);
                         j.out_ls = sh.pitch(L.tout);
@@ -1184,6 +1269,10 @@ int init3(const hyp_gas* gas, const hyp_grid_desc* desc, const hyp_case* cas, do
     UP3(g->xi_f, xi_f.data(), (nx + 1) * sizeof(double));
     UP3(g->eta_c, eta_c.data(), ny * sizeof(double));
     UP3(g->eta_f, eta_f.data(), (ny + 1) * sizeof(double));
+    std::vector<float> metf_h;
+    for (const auto* v : {&xi_c, &xi_f, &eta_c, &eta_f})
+        for (double x : *v) metf_h.push_back((float)x);
+    UP3(g->metf, metf_h.data(), metf_h.size() * sizeof(float));
     UP3(g->Tw, Tw.data(), Tw.size() * sizeof(double));
     k_reference3<<<blocks3(g->nstate), 128, 0, s>>>(gd, P, *desc, jet, *g);
     const bool noisy = cas->noise && cas->noise_amp > 0;

@@ -2,7 +2,8 @@
 the C ABI (hyp_state_init, hyp_rhs, hyp_rk_stage with nz > 1) against oracle/flow3d.py: the
 initial and reference states, the right-hand side of a jet in crossflow with artificial
 diffusivity, of a boundary layer without the jet, of a calorically perfect gas, and three RK3
-steps. Tolerance as in two dimensions (oracle.flow3d.parity_tolerance): 1e-12 of max|R| per
+steps; the mixed-precision right-hand side. Tolerance as in two dimensions
+(oracle.flow3d.parity_tolerance): 1e-12 of max|R| per
 field plus the FP64 rounding floor of the flux divergences, the sponge term on noise-level
 differences and the temperature conditioning of the Arrhenius sources."""
 import numpy as np
@@ -84,6 +85,31 @@ def test_state_init_and_rhs_parity(table, name):
     torch.cuda.synchronize()
     bad = _check(case, case.U0, R.cpu().numpy())
     assert not bad, bad
+    assert A.grid_status(st.grid) == 0
+
+
+@pytest.mark.parametrize("name", ["jet_40x24x12", "bl_36x20x8"])
+def test_rhs_mixed_within_1e6_of_the_flux_scale(table, name):
+    """HYP_MIXED on three-dimensional grids: binary32 transport, diffusion coefficients and
+    forward-rate exponentials in the closure, binary32 rows in the line jobs that feed only the
+    diffusive fluxes (periodic z lines included); within 1e-6 of the larger of max|R| and the
+    largest flux term entering each field (the spanwise momentum of the layer without the jet is a
+    noise-level balance of much larger terms)."""
+    import torch
+    cfg = CASES[name]
+    A, gas, st = _gpu(cfg)
+    case = F3.make_case(cfg, table, I.state_noise(_n(cfg), cfg["seed"]))
+    U = torch.as_tensor(case.U0).cuda()
+    R = torch.empty_like(U)
+    A.rhs(gas, st.grid, U, R, precision=A.MIXED)
+    torch.cuda.synchronize()
+    o, parts = F3.rhs(case, case.U0, return_parts=True)
+    fg = F3.unpack(5, cfg["nx"], cfg["ny"], cfg["nz"], R.cpu().numpy())
+    fo = F3.unpack(5, cfg["nx"], cfg["ny"], cfg["nz"], o)
+    err = {k: float(np.abs(fg[k] - fo[k]).max() / max(np.abs(fo[k]).max(), parts["gross"][k]))
+           for k in fo}
+    assert max(err.values()) <= 1e-6, err
+    assert max(err.values()) > 1e-12, err          # binary32 arithmetic is in the result
     assert A.grid_status(st.grid) == 0
 
 
