@@ -33,16 +33,16 @@ METRIC = "Mpts*RHS/s FP64"
 UNIT = "Mpts*RHS/s"
 STAGES = 3
 L2_FLUSH_BYTES = 256 << 20
-# FP64 operations per cell-centre point executed by k_closure (DADD + DMUL + 2 DFMA), from the
-# ncu instruction counts recorded in profiles/k_closure_sbli.md.
-CLOSURE_FP64_FLOP_PER_POINT = 3177.0
+# FP64 operations per cell-centre point executed by k_closure (DADD + DMUL + 2 DFMA), from ncu's
+# thread instruction counts of the launches of an RK step after the first (1024 x 256 cells).
+CLOSURE_FP64_FLOP_PER_POINT = 3167.0
 # DRAM bytes (read + write) per k_closure launch at 2048 x 256: 151.4 MB captured at 1024 x 256
-# (one-pass dram__bytes counters, profiles/k_closure_sbli.md) scaled by the point count.
+# (one-pass dram__bytes counters of the same launches) scaled by the point count.
 CLOSURE_DRAM_BYTES = 2 * (50.94e6 + 100.45e6)
 CLOSURE_DRAM_POINTS = 2048 * 256
 # FP64 operations (2 DFMA + DADD + DMUL) per cell centre and right-hand side over every kernel of
-# a step, from the ncu instruction counts in profiles/fp64_flops_sbli_1024x256.md.
-RHS_FP64_FLOP_PER_POINT = 5142.0
+# a step, from ncu's thread instruction counts of every launch of that step.
+RHS_FP64_FLOP_PER_POINT = 5079.0
 # GB300 FP64 peak derived from the unit counts: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
@@ -524,7 +524,7 @@ def ours_arm(args, rank, world, local_rank):
                "unit": UNIT, "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8}
 
     # ---------------- roofline of the dominant kernel ----------------
-    # k_closure has the largest share of the serialised launch list (profiles/launches_*). The
+    # k_closure has the largest share of the serialised ncu launch list of the bench. The
     # event time of a second-stream line phase that runs beside it includes the time it waits for
     # the FP64 pipe the closure holds, so the ranking is not taken from the live totals.
     name = "k_closure" if "k_closure" in prof else max(prof.items(), key=lambda kv: kv[1][0])[0]
