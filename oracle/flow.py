@@ -756,8 +756,9 @@ PARITY_FLOOR = 16.0 * 2.0 ** -53 * 6.0
 # of the Newton residual differ by a few eps (|E| + |e| + |u|^2/2) a_inf^2, which moves T by that
 # over c_v; the tolerance adds max_i |w_s,i| (T_a,max / T_i) (dT/T)_i with that estimate (times 8).
 def parity_tolerance(case: Case, U):
-    """Per-field absolute tolerance: 1e-12 max|R_f| + 8 eps ||D|| max|F_f| max|metric|, plus for
-    species the temperature conditioning of the Arrhenius sources."""
+    """Per-field absolute tolerance: 1e-12 max|R_f| + 8 eps ||D|| max|F_f| max|metric|, plus the
+    sponge term, the temperature conditioning of the Arrhenius sources and of the pressure in the
+    momentum and energy fluxes."""
     R, parts = rhs(case, U, return_parts=True)
     g = case.grid
     f = unpack(case.tab.ns, g.nx, g.ny, R)
@@ -769,13 +770,34 @@ def parity_tolerance(case: Case, U):
     sig_max = max(float(np.max(v)) for v in case.sigma.values())
     for k in tol:
         tol[k] += 16.0 * 2.0 ** -53 * sig_max * np.abs(q[k]).max()
+    T_si = parts["T"] * case.sc.T_ref
+    scale = np.abs(parts["E"]) + np.abs(parts["e"]) + parts["ke"]
+    if case.kind == KIND_CPG:
+        dT_rel = 8.0 * 2.0 ** -53 * scale / np.abs(parts["e"])
+    elif case.kind == KIND_TPG:
+        cv = tpg_cp(case.sc, T_si) - case.sc.R
+        dT_rel = 8.0 * 2.0 ** -53 * scale * case.sc.a ** 2 / (cv * T_si)
+    else:
+        dT_rel = 8.0 * 2.0 ** -53 * scale * case.sc.a ** 2 / (parts["th"]["cv"] * T_si)
     if case.kind == KIND_CNEQ and case.tab.reactions:
         ta_max = max(r.Ta for r in case.tab.reactions)
-        T_si = parts["T"] * case.sc.T_ref
-        scale = np.abs(parts["E"]) + np.abs(parts["e"]) + parts["ke"]
-        dT_rel = 8.0 * 2.0 ** -53 * scale * case.sc.a ** 2 / (parts["th"]["cv"] * T_si)
         for s in range(1, case.tab.ns):
             tol[f"rs{s}"] += np.max(np.abs(parts["th"]["wdot"][s]) * ta_max / T_si * dT_rel)
+    # The same temperature conditioning moves the pressure by dp = p dT/T at fixed density
+    # (Eq. 8 for the perfect gases, p = rho R T of the mixture otherwise); the momentum fluxes
+    # carry p and the energy fluxes p times the velocity, and their derivatives multiply that by
+    # ||D|| <= 6 and the metric (dT/T above already bounds the difference of two evaluations).
+    # Each derivative sees the pressure within a few points of where it is evaluated: the largest
+    # dp within +-3 points along its direction, times the local metric.
+    from scipy.ndimage import maximum_filter1d
+    dp = np.abs(parts["p"]) * dT_rel
+    spd = np.sqrt(2.0 * parts["ke"])
+    mets = ((1, g.xi_c[None, :]), (0, g.eta_c[:, None]))
+    near = [maximum_filter1d(dp, 7, axis=a, mode="nearest") * m for a, m in mets]
+    near_e = [maximum_filter1d(dp * spd, 7, axis=a, mode="nearest") * m for a, m in mets]
+    tol["rhou"] += 6.0 * float(near[0].max())
+    tol["rhov"] += 6.0 * float(near[1].max())
+    tol["rhoE"] += 6.0 * float(max(a.max() for a in near_e))
     if case.kind == KIND_LTE:
         # The reference partial densities of an LTE case are an equilibrium composition,
         # c_s = (p_std / (R T)) exp(a_s . lambda - G_s / (R T)). Two correct evaluations round

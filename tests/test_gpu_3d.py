@@ -139,6 +139,44 @@ def test_rk3_steps_follow_the_oracle(table):
     assert A.grid_status(st.grid) == 0
 
 
+def test_full_size_z_uniform_state_gives_the_2d_rhs(table):
+    """The timed geometry (512 x 256 x 128, the bench's grid and launch configuration) without the
+    jet: a state that does not depend on z gives in every z-plane the right-hand side of the
+    two-dimensional oracle at 512 x 256, every entry within the two-dimensional parity tolerance,
+    and R_w = 0. The property holds at any size (z-derivatives of z-uniform fields vanish, so do
+    the z-fluxes with w = 0); the oracle's own three-dimensional right-hand side is out of reach
+    at 16.8 M cells."""
+    import torch
+    from oracle import flow as F
+    cfg3 = dict(I.jet_case(512, 256, 128, seed=7), jet=0)
+    cfg2 = {k: v for k, v in cfg3.items() if k not in ("nz", "z0", "z1")}
+    nx, ny, nz = cfg3["nx"], cfg3["ny"], cfg3["nz"]
+    n2 = sum(a * b for _, (a, b) in F.state_layout(5, nx, ny))
+    case2 = F.make_case(cfg2, table, I.state_noise(n2, 5))
+    tol, o = F.parity_tolerance(case2, case2.U0)
+    R2 = F.unpack(5, nx, ny, o)
+    f = F.unpack(5, nx, ny, case2.U0)
+    f3 = {k: np.broadcast_to(v, (nz,) + v.shape) for k, v in f.items()}
+    f3["rhow"] = np.zeros((nz, ny, nx))
+    U3 = F3.pack(5, nx, ny, nz, f3)
+    del f3
+    A, gas, st = _gpu(cfg3)
+    U = torch.as_tensor(U3).cuda()
+    del U3
+    R = torch.empty_like(U)
+    A.rhs(gas, st.grid, U, R)
+    torch.cuda.synchronize()
+    assert A.grid_status(st.grid) == 0
+    g = F3.unpack(5, nx, ny, nz, R.cpu().numpy())
+    bad = {}
+    for k, v2 in R2.items():
+        err = float(np.abs(g[k] - v2[None]).max())
+        if not err <= tol[k]:
+            bad[k] = (err, float(tol[k]))
+    assert not bad, bad
+    assert np.abs(g["rhow"]).max() <= 1e-12 * np.abs(R2["rhou"]).max()
+
+
 def test_three_dimensional_grids_are_rejected_where_unsupported(table):
     import torch
     from paper_2210_05547_gb300 import abi as A
