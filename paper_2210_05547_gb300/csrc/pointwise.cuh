@@ -46,9 +46,26 @@ __device__ __forceinline__ void closure_body(const GasDev& g, const Scales& sc, 
         if constexpr (LTE) {
             ClosureOut o;
             double Yeq[NSP], kr;
-            lte_closure<MIXED>(g, rho * sc.rho_inf, e * sc.a_inf * sc.a_inf, s.Tcache[idx], Yeq, kr, o);
+            // the previous evaluation at this point seeds this one: the element potentials start
+            // the first equilibrium solve, and the temperature starts a step (e - e_c) / c_v,eq
+            // off the cached one (kept in the first species-energy cache arrays, which the
+            // equilibrium closure does not otherwise use)
+            const double e_si = e * sc.a_inf * sc.a_inf;
+            double lam[2] = {NAN, NAN}, cv_eq = 0.0;
+            double T0 = s.Tcache[idx];
+            if (v.predict) {
+                lam[0] = s.esc[0][idx];
+                lam[1] = s.esc[1][idx];
+                const double ec = s.esc[2][idx], cvc = s.esc[3][idx];
+                if (cvc > 0.0 && isfinite(ec)) T0 += (e_si - ec) / cvc;
+            }
+            lte_closure<MIXED>(g, rho * sc.rho_inf, e_si, T0, Yeq, kr, o, lam, &cv_eq);
             atomic_status(v.status, o.status);
             s.Tcache[idx] = o.T;
+            s.esc[0][idx] = lam[0];
+            s.esc[1][idx] = lam[1];
+            s.esc[2][idx] = e_si;
+            s.esc[3][idx] = cv_eq;
             T = o.T / sc.T_ref;
             p = o.p / (sc.rho_inf * sc.a_inf * sc.a_inf);
             mu = o.mu / sc.mu_inf;

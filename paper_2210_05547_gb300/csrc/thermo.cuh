@@ -724,10 +724,14 @@ __host__ __device__ inline void lte_at(const GasDev& g, double T, double rho, co
 // a common factor s' (d ln c_s/dT = d ln c_s/dT|_rho + s' a_s . H^-1 b) fixed by
 // sum_s c_s d ln c_s/dT = -c_tot / T; X_s' = X_s (d ln c_s/dT + 1/T). Yout receives the mass
 // fractions, o.X the mole fractions, o.D the averaged diffusion coefficients of the composition,
-// o.k the equilibrium conductivity; o.h and o.wdot are zero.
+// o.k the equilibrium conductivity; o.h and o.wdot are zero. lam (nullable, two values): the
+// element potentials of an earlier evaluation near this state, where the first solve starts when
+// they are finite (otherwise from the bound above); on return the potentials at the result.
+// cv_eq (nullable) receives de/dT along the equilibrium at fixed density at the result.
 template <bool MIXED>
 __host__ __device__ inline void lte_closure(const GasDev& g, double rho, double e, double T0,
-                                            double* Yout, double& k_reactive, ClosureOut& o) {
+                                            double* Yout, double& k_reactive, ClosureOut& o,
+                                            double* lam = nullptr, double* cv_eq = nullptr) {
     o.status = rho > 0.0 ? 0u : HYP_STATUS_NONPHYSICAL;
     const double b[2] = {rho * g.elem_b[0], rho * g.elem_b[1]};
     const double lnb[2] = {log(b[0]), log(b[1])};
@@ -735,6 +739,11 @@ __host__ __device__ inline void lte_closure(const GasDev& g, double rho, double 
     double T = fmin(fmax(T0, T_LO), T_HI);
     double lo = T_LO, hi = T_HI, dx_old = T_HI - T_LO;
     bool warm = false, conv = false;
+    if (lam && isfinite(lam[0]) && isfinite(lam[1])) {
+        q.lam[0] = lam[0];
+        q.lam[1] = lam[1];
+        warm = true;
+    }
     for (int it = 0; it < NEWTON_MAXIT; ++it) {
         lte_at(g, T, rho, b, lnb, warm, q);
         warm = true;
@@ -829,6 +838,11 @@ __host__ __device__ inline void lte_closure(const GasDev& g, double rho, double 
     }
     k_reactive = ctot * kr;
     o.k += k_reactive;
+    if (lam) {
+        lam[0] = q.lam[0];
+        lam[1] = q.lam[1];
+    }
+    if (cv_eq) *cv_eq = q.cv_eq;
 }
 
 }  // namespace hyp
