@@ -38,29 +38,29 @@ def _cases():
 CASES = _cases()
 
 
-def _gpu(cfg):
+def _gpu(cfg, ns=5):
     import torch
     from paper_2210_05547_gb300 import abi as A
     gas = A.gas_model_load(cfg)
     n = A.state_size(gas, cfg)
-    assert n == _n(cfg)
+    assert n == _n(cfg, ns)
     U = torch.empty(n, dtype=torch.float64, device="cuda")
     dQ = torch.empty_like(U)
     st = A.state_init(gas, cfg, U, dQ, I.state_noise(n, cfg["seed"]))
     return A, gas, st
 
 
-def _errors(cfg, a, b):
-    fa = F3.unpack(5, cfg["nx"], cfg["ny"], cfg["nz"], np.asarray(a))
-    fb = F3.unpack(5, cfg["nx"], cfg["ny"], cfg["nz"], np.asarray(b))
+def _errors(cfg, a, b, ns=5):
+    fa = F3.unpack(ns, cfg["nx"], cfg["ny"], cfg["nz"], np.asarray(a))
+    fb = F3.unpack(ns, cfg["nx"], cfg["ny"], cfg["nz"], np.asarray(b))
     return {k: float(np.abs(fa[k] - fb[k]).max() / max(np.abs(fb[k]).max(), 1e-300)) for k in fa}
 
 
 def _check(case, U, g):
     tol, o = F3.parity_tolerance(case, U)
-    cfg = case.cfg
-    fg = F3.unpack(5, cfg["nx"], cfg["ny"], cfg["nz"], np.asarray(g))
-    fo = F3.unpack(5, cfg["nx"], cfg["ny"], cfg["nz"], o)
+    cfg, ns = case.cfg, case.tab.ns
+    fg = F3.unpack(ns, cfg["nx"], cfg["ny"], cfg["nz"], np.asarray(g))
+    fo = F3.unpack(ns, cfg["nx"], cfg["ny"], cfg["nz"], o)
     return {k: (float(np.abs(fg[k] - fo[k]).max()), float(tol[k])) for k in fo
             if not np.abs(fg[k] - fo[k]).max() <= tol[k]}
 
@@ -175,6 +175,41 @@ def test_full_size_z_uniform_state_gives_the_2d_rhs(table):
             bad[k] = (err, float(tol[k]))
     assert not bad, bad
     assert np.abs(g["rhow"]).max() <= 1e-12 * np.abs(R2["rhou"]).max()
+
+
+def test_eleven_species_jet_rhs_parity(table11):
+    """Eleven-species air on the three-dimensional jet (libhyp11.so): the initial state, then the
+    right-hand side with 30% of NO and O inside the layer turned into NO+ and O+ and their
+    electrons, so that ambipolar ion diffusion and the zero-current electron flux act along all
+    three directions."""
+    import torch
+    ns = 11
+    cfg = I.with_species(_zoom(I.jet_case(40, 24, 12, seed=5)))
+    nx, ny, nz = cfg["nx"], cfg["ny"], cfg["nz"]
+    A, gas, st = _gpu(cfg, ns)
+    case = F3.make_case(cfg, table11, I.state_noise(_n(cfg, ns), cfg["seed"]))
+    torch.cuda.synchronize()
+    for k, v in _errors(cfg, st.U.cpu().numpy(), case.U0, ns).items():
+        assert v < 1e-13, ("U0", k, v)
+    f = F3.unpack(ns, nx, ny, nz, case.U0)
+    names = [sp.name for sp in table11.species]
+    M = table11.M()
+    i_no, i_o, i_nop, i_op = (names.index(x) for x in ("NO", "O", "NO+", "O+"))
+    i_e = table11.electron()
+    f[f"rs{i_nop}"] = 0.3 * f[f"rs{i_no}"]
+    f[f"rs{i_op}"] = 0.15 * f[f"rs{i_o}"]
+    f[f"rs{i_no}"] = 0.7 * f[f"rs{i_no}"]
+    f[f"rs{i_o}"] = 0.85 * f[f"rs{i_o}"]
+    f[f"rs{i_e}"] = M[i_e] * (f[f"rs{i_nop}"] / M[i_nop] + f[f"rs{i_op}"] / M[i_op])
+    U = F3.pack(ns, nx, ny, nz, f)
+    Ud = torch.as_tensor(U).cuda()
+    R = torch.empty_like(Ud)
+    A.rhs(gas, st.grid, Ud, R)
+    torch.cuda.synchronize()
+    bad = _check(case, U, R.cpu().numpy())
+    assert not bad, bad
+    assert np.abs(F3.unpack(ns, nx, ny, nz, R.cpu().numpy())[f"rs{i_e}"]).max() > 0.0
+    assert A.grid_status(st.grid) == 0
 
 
 def test_three_dimensional_grids_are_rejected_where_unsupported(table):
