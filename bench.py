@@ -368,28 +368,39 @@ def serving_bench(A, I, nreq, seed, precision, air11=0.25):
 
 def jet3d_bench(A, I, dev, rank, world, barrier, flush, steps=2, warmup=1):
     """Sonic jet through a circular orifice into the Mach 8 crossflow, 512 x 256 x 128 cells,
-    spanwise periodic: RK3 steps timed with CUDA events (L2 flushed between steps), FP64 and
-    with binary32 transport."""
+    spanwise periodic: RK3 steps timed with CUDA events (L2 flushed between steps), FP64, with
+    binary32 transport, and FP64 replayed from one step captured into a CUDA graph."""
     import torch
     cfg = I.jet_case(512, 256, 128, seed=7 + rank)
     gas = A.gas_model_load(cfg)
     n = A.state_size(gas, cfg)
     out = {"workload": "jet_512x256x128_cneq5_rk3", "cells": 512 * 256 * 128,
            "jet_J": cfg["jet_J"], "unit": UNIT}
-    for prec, key in ((A.FP64, "fp64"), (A.MIXED, "mixed")):
+    for prec, key in ((A.FP64, "fp64"), (A.MIXED, "mixed"), (A.FP64, "fp64_graph")):
         U = torch.empty(n, dtype=torch.float64, device=dev)
         dQ = torch.empty_like(U)
         st = A.state_init(gas, cfg, U, dQ, I.state_noise(n, cfg["seed"]))
         for _ in range(warmup):
             for k in range(STAGES):
                 A.rk_stage(st, k, cfg["dt"], precision=prec)
+
+        def step():
+            for k in range(STAGES):
+                A.rk_stage(st, k, cfg["dt"], precision=prec)
+
+        graph = None
+        if key == "fp64_graph":
+            torch.cuda.synchronize()
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph):
+                step()
+            step = graph.replay
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(steps)]
         barrier()
         for i in range(steps):
             ev[i][0].record()
-            for k in range(STAGES):
-                A.rk_stage(st, k, cfg["dt"], precision=prec)
+            step()
             ev[i][1].record()
             flush.fill_(float(i))
         barrier()
@@ -397,7 +408,7 @@ def jet3d_bench(A, I, dev, rank, world, barrier, flush, steps=2, warmup=1):
         out[key] = {"value": job_rate(world, out["cells"], steps, ms), "ms_per_step": ms / steps,
                     "status_flags": A.grid_status(st.grid),
                     "finite": bool(torch.isfinite(st.U).all().item())}
-        del st, U, dQ
+        del step, graph, st, U, dQ
         torch.cuda.empty_cache()
     return out
 
