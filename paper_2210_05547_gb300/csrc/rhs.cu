@@ -640,8 +640,7 @@ extern "C" int hyp_state_init(const hyp_gas* gas, const hyp_grid_desc* desc, con
         return fail(HYP_ERR_ARG, "Stefan-Maxwell diffusion is not defined for charged mixtures");
     cudaStream_t s = (cudaStream_t)stream;
     const GasDev& g = gas->dev;
-    hyp_grid* G = new hyp_grid();
-    memset((void*)G, 0, sizeof(hyp_grid));
+    hyp_grid* G = new hyp_grid();   // value-initialised: every pointer and count starts at zero
     G->d.nx = desc->nx;
     G->d.ny = desc->ny;
     G->cas = *cas;
