@@ -19,8 +19,9 @@
 // constant factors around the ring, one thread per line, started W rows early from zero (W = 40
 // for the interpolation, factor 1/3, and 26 for the derivative, factor 0.148: the dropped history
 // is below 1e-19 of the values, and the result is the periodic solution to rounding). Each phase
-// batches up to eight independent line jobs of one kind per launch, and the velocity-gradient
-// and artificial-diffusivity phases run on a second stream beside the closure.
+// batches up to eight independent line jobs of one kind per launch; the velocity-gradient and
+// artificial-diffusivity phases run on a second stream beside the closure, and the viscosity
+// phase, the stresses and their face values there beside the other face values.
 //
 // Jet (reading; the paper gives a sonic jet of prescribed temperature ratio and momentum ratio
 // J): inside the orifice the wall face holds the Dirichlet mass flux of a sonic jet at
@@ -236,10 +237,13 @@ struct Launch3 {
 struct Phase3 {
     std::vector<Line3> lines;
     std::vector<Launch3> launches;
+    int slot_base = 0;         // first forward-sweep buffer of its x/y jobs
 };
 
+// face: the face values that do not need the stresses; faceb: the stresses' face values, which
+// run with mu on the second stream beside face (so their x/y jobs take other sweep buffers)
 struct Plan3 {
-    Phase3 p1, p3, ad1, ad2, mu, face, divs;
+    Phase3 p1, p3, ad1, ad2, mu, face, faceb, divs;
 };
 
 struct View3 {
@@ -761,9 +765,17 @@ int run_rhs3(const hyp_gas* gas, hyp_grid* G, const double* U, double* dUdt, int
         k_adcombine3<<<blocks3(g->nc), 256, 0, s>>>(*g);
         HYP_CUDA(cudaGetLastError());
     }
-    if ((rc = launch3(g, pl.mu, U, false, mx, s))) return rc;
-    k_stress3<<<blocks3(g->nc + g->nxy + g->nxf + g->nyf), 256, 0, s>>>(*g);
+    // fork: viscosities to faces and edges, the stresses and their face values beside the other
+    // face values
+    HYP_CUDA(cudaEventRecord(G->fork[1], s));
+    HYP_CUDA(cudaStreamWaitEvent(s2, G->fork[1], 0));
+    if ((rc = launch3(g, pl.mu, U, false, mx, s2))) return rc;
+    k_stress3<<<blocks3(g->nc + g->nxy + g->nxf + g->nyf), 256, 0, s2>>>(*g);
+    HYP_CUDA(cudaGetLastError());
+    if ((rc = launch3(g, pl.faceb, U, false, mx, s2))) return rc;
+    HYP_CUDA(cudaEventRecord(G->join[1], s2));
     if ((rc = launch3(g, pl.face, U, false, mx, s))) return rc;
+    HYP_CUDA(cudaStreamWaitEvent(s, G->join[1], 0));
     k_flux3<<<blocks3(g->nxf + g->nyf + g->nc), 128, 0, s>>>(gd, *g, v, U);
     HYP_CUDA(cudaGetLastError());
     if ((rc = launch3(g, pl.divs, U, false, mx, s))) return rc;
@@ -1100,6 +1112,7 @@ int init3(const hyp_gas* gas, const hyp_grid_desc* desc, const hyp_case* cas, do
     pl.mu.lines.push_back(f(zl(0, 0, g->mu_yf, YF3, g->mu_yz)));
     pl.mu.lines.push_back(f(xy(OY_ICF, 1, g->mu_xf, XF3, g->mu_xy, XY3, nullptr)));
     std::vector<Line3>& F = pl.face.lines;
+    std::vector<Line3>& FB = pl.faceb.lines;
     for (int sp = 0; sp < NSP; ++sp) {
         F.push_back(xy(OX_ICF, 0, g->Y[sp], C3, g->Yx[sp], XF3, nullptr));
         F.push_back(f(xy(OX_ICF, 0, g->G[sp], C3, g->Gx[sp], XF3, nullptr)));
@@ -1117,27 +1130,27 @@ int init3(const hyp_gas* gas, const hyp_grid_desc* desc, const hyp_case* cas, do
     F.push_back(xy(OX_ICF, 0, g->H, C3, g->Hx, XF3, nullptr));
     F.push_back(f(xy(OX_ICF, 0, g->K, C3, g->Kx, XF3, nullptr)));
     F.push_back(f(xy(OX_DCF, 0, g->T, C3, g->dTdx, XF3, g->xi_f)));
-    F.push_back(f(xy(OX_ICF, 0, g->tau_xx, C3, g->txx_x, XF3, nullptr)));
+    FB.push_back(f(xy(OX_ICF, 0, g->tau_xx, C3, g->txx_x, XF3, nullptr)));
     F.push_back(f(xy(OX_ICF, 0, g->v_c, C3, g->v_x, XF3, nullptr)));
     F.push_back(f(xy(OX_ICF, 0, g->w_c, C3, g->w_x, XF3, nullptr)));
-    F.push_back(f(xy(OY_IFC, 1, g->tau_xy, XY3, g->txy_x, XF3, nullptr)));
-    F.push_back(f(zl(0, 1, g->tau_xz, XF3, g->txz_x)));
+    FB.push_back(f(xy(OY_IFC, 1, g->tau_xy, XY3, g->txy_x, XF3, nullptr)));
+    FB.push_back(f(zl(0, 1, g->tau_xz, XF3, g->txz_x)));
     F.push_back(xy(OY_ICF, 1, g->H, C3, g->Hy, YF3, nullptr));
     F.push_back(f(xy(OY_ICF, 1, g->K, C3, g->Ky, YF3, nullptr)));
     F.push_back(f(xy(ydcfw, 1, g->T, C3, g->dTdy, YF3, g->eta_f, 1.0, wall ? g->Tw : nullptr)));
-    F.push_back(f(xy(OY_ICF, 1, g->tau_yy, C3, g->tyy_y, YF3, nullptr)));
+    FB.push_back(f(xy(OY_ICF, 1, g->tau_yy, C3, g->tyy_y, YF3, nullptr)));
     F.push_back(f(xy(yicfw, 1, g->u_c, C3, g->u_y, YF3, nullptr)));
     F.push_back(f(xy(yicfw, 1, g->w_c, C3, g->w_y, YF3, nullptr)));
-    F.push_back(f(xy(OX_IFC, 0, g->tau_xy, XY3, g->txy_y, YF3, nullptr)));
-    F.push_back(f(zl(0, 1, g->tau_yz, YF3, g->tyz_y)));
+    FB.push_back(f(xy(OX_IFC, 0, g->tau_xy, XY3, g->txy_y, YF3, nullptr)));
+    FB.push_back(f(zl(0, 1, g->tau_yz, YF3, g->tyz_y)));
     F.push_back(zl(0, 0, g->H, C3, g->Hz));
     F.push_back(f(zl(0, 0, g->K, C3, g->Kz)));
     F.push_back(f(zl(1, 0, g->T, C3, g->dTdz, ze)));
-    F.push_back(f(zl(0, 0, g->tau_zz, C3, g->tzz_z)));
+    FB.push_back(f(zl(0, 0, g->tau_zz, C3, g->tzz_z)));
     F.push_back(f(zl(0, 0, g->u_c, C3, g->u_z)));
     F.push_back(f(zl(0, 0, g->v_c, C3, g->v_z)));
-    F.push_back(f(xy(OX_IFC, 0, g->tau_xz, XF3, g->txz_z, C3, nullptr)));
-    F.push_back(f(xy(OY_IFC, 1, g->tau_yz, YF3, g->tyz_z, C3, nullptr)));
+    FB.push_back(f(xy(OX_IFC, 0, g->tau_xz, XF3, g->txz_z, C3, nullptr)));
+    FB.push_back(f(xy(OY_IFC, 1, g->tau_yz, YF3, g->tyz_z, C3, nullptr)));
     std::vector<Line3>& D = pl.divs.lines;
     for (int sp = 1; sp < NSP; ++sp) {
         D.push_back(xy(OX_DFC, 0, g->Fsx[sp], XF3, g->DX + g->off[sp], C3, g->xi_c, -1.0));
@@ -1158,7 +1171,8 @@ int init3(const hyp_gas* gas, const hyp_grid_desc* desc, const hyp_case* cas, do
     D.push_back(zl(1, 0, g->Gzz, C3, g->DZ + g->off[NSP + 3], -ze));
     // launches: the independent phases put their x/y lines before their z lines and batch each
     // kind; the viscosity phase keeps its order (its edge values come from its face values)
-    Phase3* phases[] = {&pl.p1, &pl.p3, &pl.ad1, &pl.ad2, &pl.mu, &pl.face, &pl.divs};
+    Phase3* phases[] = {&pl.p1, &pl.p3, &pl.ad1, &pl.ad2, &pl.mu, &pl.face, &pl.faceb, &pl.divs};
+    pl.mu.slot_base = pl.faceb.slot_base = BATCH3;
     for (Phase3* ph : phases) {
         std::vector<Line3>& V = ph->lines;
         if (ph != &pl.mu)
@@ -1226,7 +1240,7 @@ int init3(const hyp_gas* gas, const hyp_grid_desc* desc, const hyp_case* cas, do
                     tmp_n = std::max(tmp_n, sh.size(L.tout));
                     L.job = (int)lj.size();
                     lj.push_back(j);
-                    slot.push_back(i);
+                    slot.push_back(ph->slot_base + i);
                 }
                 while (threads < 40960) {
                     bool grew = false;
@@ -1246,7 +1260,7 @@ int init3(const hyp_gas* gas, const hyp_grid_desc* desc, const hyp_case* cas, do
                     const int lpb = LINE_BLOCK / ns[i];
                     b.blocks = std::max(b.blocks, (j.nlines + lpb - 1) / lpb);
                 }
-                slots = std::max(slots, b.count);
+                slots = std::max(slots, ph->slot_base + b.count);
             }
         err = cudaMalloc(&g->ltmp, (size_t)slots * tmp_n * sizeof(double));
         if (err == cudaSuccess) err = cudaMalloc(&g->jobs, lj.size() * sizeof(LineJob));
