@@ -148,8 +148,7 @@ class ClockSampler:
 # CPU baseline: the oracle as it stands, on a bounded sample of the same case
 # ------------------------------------------------------------------------------------------------
 
-def oracle_step_rate(nx, ny, steps=1):
-    """Run `steps` oracle RK3 steps on the SBLI case at nx x ny; return (Mpts*RHS/s, cores, s)."""
+def _oracle_case(nx, ny):
     from oracle import flow as F
     from oracle import gas as G
     from paper_2210_05547_gb300 import inputs as I
@@ -157,18 +156,68 @@ def oracle_step_rate(nx, ny, steps=1):
     cfg = I.sbli_case(nx, ny)
     tab = G.load_table(TABLE_AIR5)
     n = sum(a * b for _, (a, b) in F.state_layout(5, nx, ny))
-    case = F.make_case(cfg, tab, I.state_noise(n, cfg["seed"]))
+    return cfg, F.make_case(cfg, tab, I.state_noise(n, cfg["seed"]))
+
+
+def _oracle_steps(cfg, case, steps):
+    from oracle import flow as F
     U, dQ = case.U0.copy(), case.U0 * 0.0
-    r0 = resource.getrusage(resource.RUSAGE_SELF)
-    t0 = time.perf_counter()
     for _ in range(steps):
         for k in range(STAGES):
             U, dQ, _ = F.rk_stage(case, U, dQ, k, cfg["dt"])
+
+
+def oracle_step_rate(nx, ny, steps=1):
+    """Run `steps` oracle RK3 steps on the SBLI case at nx x ny; return (Mpts*RHS/s, cores, s)."""
+    cfg, case = _oracle_case(nx, ny)
+    r0 = resource.getrusage(resource.RUSAGE_SELF)
+    t0 = time.perf_counter()
+    _oracle_steps(cfg, case, steps)
     wall = time.perf_counter() - t0
     r1 = resource.getrusage(resource.RUSAGE_SELF)
     cpu = (r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime)
     cores = max(1, round(cpu / wall))
     return nx * ny * STAGES * steps / wall / 1e6, cores, wall
+
+
+def _oracle_proc(nx, ny, barrier, out):
+    # one thread per process: numerical libraries must not start their own thread pools
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    cfg, case = _oracle_case(nx, ny)
+    barrier.wait(timeout=120)
+    t0 = time.perf_counter()
+    _oracle_steps(cfg, case, 1)
+    out.put(time.perf_counter() - t0)
+
+
+def oracle_all_cores(nx, ny, deadline_s=300.0):
+    """One oracle RK3 step of the nx x ny sample in each of as many processes as the host has
+    cores (spawned, no GPU), all started together: (Mpts*RHS/s of the whole host, processes,
+    slowest step in s), or None if a process fails or the deadline passes."""
+    import multiprocessing
+    import queue
+    nproc = max(1, min(64, len(os.sched_getaffinity(0))))
+    ctx = multiprocessing.get_context("spawn")
+    barrier, out = ctx.Barrier(nproc), ctx.Queue()
+    procs = [ctx.Process(target=_oracle_proc, args=(nx, ny, barrier, out)) for _ in range(nproc)]
+    for p in procs:
+        p.start()
+    walls, t_end = [], time.monotonic() + deadline_s
+    while len(walls) < nproc and time.monotonic() < t_end:
+        try:
+            walls.append(out.get(timeout=2.0))
+        except queue.Empty:
+            if any(p.exitcode not in (None, 0) for p in procs):
+                break
+    for p in procs:
+        p.join(timeout=10 if len(walls) == nproc else 0.1)
+        if p.is_alive():
+            p.terminate()
+            p.join(timeout=10)
+    if len(walls) < nproc:
+        return None
+    return nproc * nx * ny * STAGES / max(walls) / 1e6, nproc, max(walls)
 
 
 # ------------------------------------------------------------------------------------------------
@@ -629,6 +678,12 @@ def ours_arm(args, rank, world, local_rank):
         r, cores, w = oracle_step_rate(320, 128)
         cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"one oracle RK3 step (3 RHS) of the same case at 320x128 cells, {w:.1f} s"}
+        every = oracle_all_cores(320, 128)
+        if every is not None:
+            ra, na, wa = every
+            cpu["all_cores"] = {"value": ra, "unit": UNIT, "cores": na, "kind": "oracle",
+                                "sample": f"the same step in {na} single-threaded processes at "
+                                          f"once (slowest {wa:.1f} s)"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
