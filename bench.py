@@ -36,6 +36,10 @@ L2_FLUSH_BYTES = 256 << 20
 # FP64 operations per cell-centre point executed by k_closure (DADD + DMUL + 2 DFMA), from ncu's
 # thread instruction counts of the launches of an RK step after the first (1024 x 256 cells).
 CLOSURE_FP64_FLOP_PER_POINT = 3167.0
+# The same counts as FP64 warp-lane instructions (DFMA + DADD + DMUL, 1249.3 + 173.5 + 494.6): a
+# DADD or DMUL takes an FP64 issue slot like a DFMA but counts one flop, so the pipe's occupancy
+# is the instruction rate against 2 instructions per clock per SM.
+CLOSURE_FP64_INSTR_PER_POINT = 1917.4
 # DRAM bytes (read + write) per k_closure launch at 2048 x 256: 151.4 MB captured at 1024 x 256
 # (one-pass dram__bytes counters of the same launches) scaled by the point count.
 CLOSURE_DRAM_BYTES = 2 * (50.94e6 + 100.45e6)
@@ -609,7 +613,10 @@ def ours_arm(args, rank, world, local_rank):
                              if CLOSURE_DRAM_BYTES else None),
                     algorithmic_flop_per_point=CLOSURE_FP64_FLOP_PER_POINT,
                     peak_source="derived: 152 SMs x 2 DFMA/clk x 2.07 GHz (a DFMA probe "
-                                "measured 1.20 TFLOP/s)")
+                                "measured 1.20 TFLOP/s)",
+                    fp64_instr_per_point=CLOSURE_FP64_INSTR_PER_POINT,
+                    fp64_pipe_frac=(CLOSURE_FP64_INSTR_PER_POINT * points / avg_s)
+                                   / (FP64_PEAK_TFLOPS * 1e12 / 2.0))
     else:
         roof.update(bound="alu", achieved=None, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s", frac=None,
                     traffic=None, note="per-point FP64 count not yet measured for this kernel")
