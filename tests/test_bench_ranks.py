@@ -56,3 +56,18 @@ def test_two_gloo_ranks(tmp_path):
     assert r[0]["rate"] == pytest.approx(2 * 1000 * 3 * 4 / 0.015 / 1e6)
     assert r[0]["mach"] != r[1]["mach"]                         # independent replicas
     assert r[1]["ref_rc"] == 0 and r[1]["ref_out"] == ""       # non-zero ranks: no work, no line
+
+
+def test_oracle_baseline_on_every_host_core():
+    """The CPU baseline's all-cores leg: one spawned single-threaded process per host core runs
+    one oracle RK3 step of a small sample; the host rate is the processes' work over the slowest
+    step, so it exceeds the one-core rate and stays below cores x the one-core rate x 1.5."""
+    sys.path.insert(0, ROOT)
+    import bench
+    one, _, _ = bench.oracle_step_rate(48, 24)
+    every = bench.oracle_all_cores(48, 24, deadline_s=240.0)
+    assert every is not None
+    rate, nproc, slowest = every
+    assert nproc == max(1, min(64, len(os.sched_getaffinity(0))))
+    assert slowest > 0.0
+    assert rate > 0.5 * one and rate < 1.5 * nproc * one
