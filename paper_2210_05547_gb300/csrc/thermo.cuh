@@ -292,9 +292,9 @@ __host__ __device__ inline void transport_f64(const GasDev& g, double T, double 
 #pragma unroll
     for (int i = 0; i < NSP; ++i) {
         mu_s[i] = 0.1 * exp((g.blA[i] * lnT + g.blB[i]) * lnT + g.blC[i]);
-        const double sq = sqrt(mu_s[i]);
-        a[i] = sq * g.iMq[i];
-        b[i] = g.Mq[i] / sq;
+        const double rs = rsqrt(mu_s[i]);           // 1 / sqrt(mu_i): one FP64 sequence for both
+        a[i] = mu_s[i] * rs * g.iMq[i];
+        b[i] = g.Mq[i] * rs;
         const double cv_tr = 1.5 * g.Rs[i];
         k_s[i] = mu_s[i] * (2.5 * cv_tr + (s.cv[i] - cv_tr));
     }
