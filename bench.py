@@ -35,18 +35,18 @@ STAGES = 3
 L2_FLUSH_BYTES = 256 << 20
 # FP64 operations per cell-centre point executed by k_closure (DADD + DMUL + 2 DFMA), from ncu's
 # thread instruction counts of the launches of an RK step after the first (1024 x 256 cells).
-CLOSURE_FP64_FLOP_PER_POINT = 3077.0
-# The same counts as FP64 warp-lane instructions (DFMA + DADD + DMUL, 1204.3 + 173.5 + 494.6): a
+CLOSURE_FP64_FLOP_PER_POINT = 3041.0
+# The same counts as FP64 warp-lane instructions (DFMA + DADD + DMUL, 1186.3 + 173.5 + 494.6): a
 # DADD or DMUL takes an FP64 issue slot like a DFMA but counts one flop, so the pipe's occupancy
 # is the instruction rate against 2 instructions per clock per SM.
-CLOSURE_FP64_INSTR_PER_POINT = 1872.4
-# DRAM bytes (read + write) per k_closure launch at 2048 x 256: 151.2 MB captured at 1024 x 256
+CLOSURE_FP64_INSTR_PER_POINT = 1854.4
+# DRAM bytes (read + write) per k_closure launch at 2048 x 256: 150.7 MB captured at 1024 x 256
 # (one-pass dram__bytes counters of the same launches) scaled by the point count.
-CLOSURE_DRAM_BYTES = 2 * (50.63e6 + 100.53e6)
+CLOSURE_DRAM_BYTES = 2 * (50.64e6 + 100.09e6)
 CLOSURE_DRAM_POINTS = 2048 * 256
 # FP64 operations (2 DFMA + DADD + DMUL) per cell centre and right-hand side over every kernel of
 # a step, from ncu's thread instruction counts of every launch of that step.
-RHS_FP64_FLOP_PER_POINT = 4989.0
+RHS_FP64_FLOP_PER_POINT = 4953.0
 # GB300 FP64 peak derived from the unit counts: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 

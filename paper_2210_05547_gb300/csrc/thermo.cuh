@@ -324,7 +324,8 @@ __host__ __device__ inline void transport_f64(const GasDev& g, double T, double 
 #pragma unroll
         for (int i = 0; i < NSP; ++i) den[i] = 0.0;
         const double TmB = exp(-NJA_B * lnT);               // T^-B, shared by every well depth
-        const double c = p / (T * sqrt(T));                  // 1/D_sr = c Omega dinv_sr
+        const double rT = rsqrt(T);
+        const double c = p * (rT * (rT * rT));              // 1/D_sr = c Omega dinv_sr
         for (int q = 0; q < g.neps; ++q) {
             const double ts = T * g.eps_inv[q];
             double om = NJA_A * TmB * g.eps_powB[q];
@@ -370,7 +371,7 @@ __host__ __device__ inline void closure_si_p(const GasDev& g, double rho, double
     o.p = p;
     o.cv = cv;
     o.Rmix = Rmix;
-    o.a = sqrt((cv + Rmix) / cv * p / rho);
+    o.a = sqrt((cv + Rmix) * p / (cv * rho));
 #pragma unroll
     for (int i = 0; i < NSP; ++i) {
         o.h[i] = s.e[i] + g.Rs[i] * T;
@@ -389,7 +390,7 @@ __host__ __device__ inline void closure_si_p(const GasDev& g, double rho, double
 #pragma unroll
     for (int i = 0; i < NSP; ++i) o.wdot[i] = 0.0;
     if (reactions) {
-        const double T15 = T * sqrt(T);
+        const double T15 = T * T * rsqrt(T);
         double r[NSP];
 #pragma unroll
         for (int i = 0; i < NSP; ++i) {
