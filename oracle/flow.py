@@ -557,7 +557,38 @@ def gauss9(f, axis):
 
 
 def filter2(f):
+    """The Gaussian filter along x (axis 1), then along y (axis 0)."""
     return gauss9(gauss9(f, 1), 0)
+
+
+def ducros(div, omega):
+    """Ducros switch H(-div u) (div u)^2 / ((div u)^2 + |omega|^2 + eps)."""
+    return np.where(div < 0.0, div * div / (div * div + omega * omega + DUCROS_EPS), 0.0)
+
+
+def artificial_diffusivity(cfg, rho, a, T, e, Y, dudx, dvdy, dudy_c, dvdx_c, dx, dy):
+    """Artificial shear viscosity, bulk viscosity, conductivity and species diffusivities at the
+    centres (Sec. 3.3, in the form of the localized-artificial-diffusivity papers it cites):
+        mu*  = C_mu    rho           |sum_l d4_l(S) dl^2|~
+        beta* = C_beta rho f_sw      |sum_l d4_l(div u) dl^2|~
+        kappa* = C_kappa rho a / T   |sum_l d4_l(e) dl|~
+        D*_s = C_D a                 |sum_l d4_l(Y_s) dl|~
+    with S = (dudx^2 + dvdy^2 + (dudy + dvdx)^2 / 2)^(1/2), omega = dvdx - dudy, d4_l the fourth
+    index difference along direction l (delta4), dl the local cell size (dx varies along axis 1,
+    dy along axis 0) and ~ the Gaussian filter in x then y (filter2). Arrays are (ny, nx) at the
+    centres; Y is (ns, ny, nx). Returns (mu*, beta*, kappa*, D*)."""
+    S = np.sqrt(dudx * dudx + dvdy * dvdy + 0.5 * (dudy_c + dvdx_c) ** 2)
+    div = dudx + dvdy
+    fsw = ducros(div, dvdx_c - dudy_c)
+    mu_st = filter2(cfg["C_mu"] * rho * np.abs(delta4(S, 1) * dx * dx + delta4(S, 0) * dy * dy))
+    beta_st = filter2(cfg["C_beta"] * rho * fsw
+                      * np.abs(delta4(div, 1) * dx * dx + delta4(div, 0) * dy * dy))
+    kap_st = filter2(cfg["C_kappa"] * rho * a / T
+                     * np.abs(delta4(e, 1) * dx + delta4(e, 0) * dy))
+    D_st = np.stack([filter2(cfg["C_D"] * a
+                             * np.abs(delta4(Y[s], 1) * dx + delta4(Y[s], 0) * dy))
+                     for s in range(Y.shape[0])])
+    return mu_st, beta_st, kap_st, D_st
 
 
 # ---------------------------------------------------------------------------------------------
@@ -610,19 +641,8 @@ def rhs(case: Case, U, return_parts=False):
     if cfg["artificial_diffusivity"]:
         dudy_c = C.ifc(C.ifc(dudy_cn, 0), 1)
         dvdx_c = C.ifc(C.ifc(dvdx_cn, 0), 1)
-        S = np.sqrt(dudx * dudx + dvdy * dvdy + 0.5 * (dudy_c + dvdx_c) ** 2)
-        omega = dvdx_c - dudy_c
-        fsw = np.where(div < 0.0, div * div / (div * div + omega * omega + DUCROS_EPS), 0.0)
-        dx = 1.0 / xi_c
-        dy = 1.0 / eta_c
-        mu_st = filter2(cfg["C_mu"] * rho * np.abs(delta4(S, 1) * dx * dx + delta4(S, 0) * dy * dy))
-        beta_st = filter2(cfg["C_beta"] * rho * fsw
-                          * np.abs(delta4(div, 1) * dx * dx + delta4(div, 0) * dy * dy))
-        kap_st = filter2(cfg["C_kappa"] * rho * th["a"] / T
-                         * np.abs(delta4(e, 1) * dx + delta4(e, 0) * dy))
-        D_st = np.stack([filter2(cfg["C_D"] * th["a"]
-                                 * np.abs(delta4(Y[s], 1) * dx + delta4(Y[s], 0) * dy))
-                         for s in range(ns)])
+        mu_st, beta_st, kap_st, D_st = artificial_diffusivity(
+            cfg, rho, th["a"], T, e, Y, dudx, dvdy, dudy_c, dvdx_c, 1.0 / xi_c, 1.0 / eta_c)
     else:
         mu_st = beta_st = kap_st = np.zeros_like(rho)
         D_st = np.zeros_like(Y)
