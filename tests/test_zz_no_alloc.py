@@ -1,7 +1,9 @@
 """hyp_rhs_noalloc: the right-hand side for callers that may not allocate device memory while they
-run (stream capture, real-time loops, hosts owning all device memory). Its scratch lives in a
-static device array of the library; its result must match hyp_rhs on the same grid and state,
-on two calls in a row. This file is collected last on purpose."""
+run (real-time loops that forbid allocation after start-up, hosts that own all device memory
+through their own allocator). Its scratch lives in a static device array of the library; its
+result must match hyp_rhs on the same grid and state, on two calls in a row, leave the grid's own
+scratch and predictor cache alone, and work up to the array's size limit. This file is collected
+last on purpose."""
 import numpy as np
 import pytest
 
@@ -23,6 +25,7 @@ def test_noalloc_matches_rhs_twice(table, cfg):
     U = torch.as_tensor(case.U0).cuda()
     R_ref = torch.empty_like(U)
     A.rhs(gas, st.grid, U, R_ref)
+    assert A.grid_status(st.grid) == 0
     outs = []
     for _ in range(2):
         R = torch.full_like(U, float("nan"))
@@ -35,6 +38,79 @@ def test_noalloc_matches_rhs_twice(table, cfg):
         for k in ref:
             assert np.abs(got[k] - ref[k]).max() <= tol[k], k
     assert np.array_equal(outs[0], outs[1])       # same inputs, same static scratch reset
+    # status bits go to the grid's word: the noalloc calls set none
+    assert A.grid_status(st.grid) == 0
+
+
+def test_noalloc_leaves_the_grid_scratch_alone(table):
+    """hyp_rhs, hyp_rhs_noalloc, hyp_rhs on one grid: the second hyp_rhs (which starts its Newton
+    iteration from the grid's cached species state) is bitwise the one of hyp_rhs, hyp_rhs on a
+    second grid of the same case, so the noalloc call wrote nothing the grid keeps."""
+    import torch
+    from paper_2210_05547_gb300 import abi as A
+    cfg = I.sbli_case(64, 40, seed=3)
+    case = oracle_case(table, cfg)
+    U = torch.as_tensor(case.U0).cuda()
+    # a second state, so that the cached species state of the first call differs from its own
+    U2 = U * (1.0 + 1e-6)
+    results = []
+    for mix in (True, False):
+        gas, st = gpu_state(cfg)
+        R = torch.empty_like(U)
+        A.rhs(gas, st.grid, U2, R)
+        if mix:
+            Rn = torch.empty_like(U)
+            A.rhs_noalloc(gas, st.grid, U, Rn)
+        A.rhs(gas, st.grid, U, R)
+        torch.cuda.synchronize()
+        results.append(R.cpu().numpy())
+        assert A.grid_status(st.grid) == 0
+    assert np.array_equal(results[0], results[1])
+
+
+def test_noalloc_near_the_size_limit(table):
+    """The largest 64-row grid the static array takes (found by the entry point's own size check,
+    which rejects before launching anything) computes the same right-hand side as hyp_rhs: the
+    line-sweep storage and the launch plan then sit at the very end of the array."""
+    import torch
+    from paper_2210_05547_gb300 import abi as A
+    ny = 64
+
+    def accepted(nx):
+        cfg = I.bl_case(nx, ny)
+        gas, st = gpu_state(cfg)
+        R = torch.empty_like(st.U)
+        try:
+            A.rhs_noalloc(gas, st.grid, st.U, R)
+            torch.cuda.synchronize()
+            return True
+        except A.HypError as e:
+            assert "too large for hyp_rhs_noalloc" in str(e)
+            return False
+
+    lo, hi = 8, 256
+    assert accepted(lo) and not accepted(hi)
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        if accepted(mid):
+            lo = mid
+        else:
+            hi = mid
+    cfg = I.bl_case(lo, ny)
+    gas, st = gpu_state(cfg)
+    case = oracle_case(table, cfg)
+    tol, _ = F.parity_tolerance(case, case.U0)
+    U = torch.as_tensor(case.U0).cuda()
+    R_ref = torch.empty_like(U)
+    R = torch.full_like(U, float("nan"))
+    A.rhs(gas, st.grid, U, R_ref)
+    A.rhs_noalloc(gas, st.grid, U, R)
+    torch.cuda.synchronize()
+    ref = F.unpack(5, cfg["nx"], cfg["ny"], R_ref.cpu().numpy())
+    got = F.unpack(5, cfg["nx"], cfg["ny"], R.cpu().numpy())
+    for k in ref:
+        assert np.abs(got[k] - ref[k]).max() <= tol[k], (lo, k)
+    assert A.grid_status(st.grid) == 0
 
 
 def test_noalloc_rejects_large_grid():
