@@ -34,21 +34,37 @@ UNIT = "Mpts*RHS/s"
 STAGES = 3
 L2_FLUSH_BYTES = 256 << 20
 # FP64 operations per cell-centre point executed by k_closure (DADD + DMUL + 2 DFMA), from ncu's
-# thread instruction counts of the launches of an RK step after the first (1024 x 256 cells).
-CLOSURE_FP64_FLOP_PER_POINT = 3041.0
-# The same counts as FP64 warp-lane instructions (DFMA + DADD + DMUL, 1186.3 + 173.5 + 494.6): a
-# DADD or DMUL takes an FP64 issue slot like a DFMA but counts one flop, so the pipe's occupancy
-# is the instruction rate against 2 instructions per clock per SM.
-CLOSURE_FP64_INSTR_PER_POINT = 1854.4
-# DRAM bytes (read + write) per k_closure launch at 2048 x 256: 150.7 MB captured at 1024 x 256
-# (one-pass dram__bytes counters of the same launches) scaled by the point count.
-CLOSURE_DRAM_BYTES = 2 * (50.64e6 + 100.09e6)
-CLOSURE_DRAM_POINTS = 2048 * 256
+# thread instruction counts of the launches of an RK step after the first (1024 x 256 cells;
+# 702.4 DFMA, 127.0 DADD, 519.5 DMUL per point; profiles/k_closure_sbli.md).
+CLOSURE_FP64_FLOP_PER_POINT = 2051.3
+# The same counts as FP64 warp-lane instructions (DFMA + DADD + DMUL): a DADD or DMUL takes an FP64
+# issue slot like a DFMA but counts one flop, so the pipe's occupancy is the instruction rate
+# against 2 instructions per clock per SM. All instructions on the FP64 pipe (comparisons and
+# conversions included): 1481.5 per point.
+CLOSURE_FP64_INSTR_PER_POINT = 1348.9
+CLOSURE_FP64_PIPE_INSTR_PER_POINT = 1481.5
+# The closure's FP64 operation count when every exponential, logarithm, quotient and square root
+# is CUDA's own (the earlier form of this kernel): 3041 per point. Dividing it by the time of the
+# current kernel gives an effective rate, reported beside the measured-count roofline.
+CLOSURE_LIBM_FLOP_PER_POINT = 3041.0
+# DRAM bytes (read + write) per k_closure launch at 2048 x 256: 578 B per point measured at
+# 1024 x 256 (one-pass dram__bytes counters of the same launches) scaled by the point count.
+CLOSURE_DRAM_BYTES = 578.2 * 1024 * 256
+CLOSURE_DRAM_POINTS = 1024 * 256
 # FP64 operations (2 DFMA + DADD + DMUL) per cell centre and right-hand side over every kernel of
 # a step, from ncu's thread instruction counts of every launch of that step.
 RHS_FP64_FLOP_PER_POINT = 4953.0
 # GB300 FP64 peak derived from the unit counts: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# hyp_thermo_eval (five-species air, FP64, every output): FP64 operations per state, 2 DFMA + DADD
+# + DMUL from ncu's thread instruction counts of one launch over 2e6 states of the sweep's
+# distribution (943.5 DFMA, 233.0 DADD, 597.7 DMUL per state; profiles/k_thermo_eval_sweep.md).
+THERMO_FP64_FLOP_PER_STATE = 2717.7
+THERMO_FP64_INSTR_PER_STATE = 1774.2
+# k_closure3 (the three-dimensional jet's closure, FP64): FP64 operations per cell from ncu's
+# thread instruction counts of the timed launches at 128 x 64 x 32 cells
+# (profiles/k_closure3_jet.md); 0 until measured.
+CLOSURE3_FP64_FLOP_PER_POINT = 0.0
 
 
 def parse():
@@ -68,10 +84,16 @@ def parse():
                     help="skip the three-dimensional jet-in-crossflow measurement")
     ap.add_argument("--no-air11", action="store_true",
                     help="skip the eleven-species measurements")
-    ap.add_argument("--serve-requests", type=int, default=48,
-                    help="requests of the serving measurement (0 skips it)")
+    ap.add_argument("--serve-requests", type=int, default=24,
+                    help="requests of the serving measurement, the first ones of the 500-request "
+                         "serving stream (0 skips it)")
+    ap.add_argument("--serve-fp64", action="store_true",
+                    help="also serve the stream in FP64 through the server")
     ap.add_argument("--thermo-states", type=float, default=1e8,
                     help="states of the pointwise thermochemistry sweep (0 skips it)")
+    ap.add_argument("--jet3d-size", default="512x256x128",
+                    help="cells of the three-dimensional jet measurement, NXxNYxNZ (profiling of "
+                         "small cases)")
     return ap.parse_args()
 
 
@@ -361,7 +383,17 @@ def thermo_sweep(A, gas, dev, n, seed, reps=2, precision=0):
     ms = ev[0].elapsed_time(ev[1]) / reps
     err = float(((T - T0).abs() / T0).max())
     bad = int((status != 0).sum())
+    roof = None
+    if precision == 0 and ns == 5:
+        ach = THERMO_FP64_FLOP_PER_STATE * n / (ms / 1e3) / 1e12
+        roof = {"kernel": "k_thermo_eval", "bound": "alu", "achieved": ach,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                "algorithmic_flop_per_state": THERMO_FP64_FLOP_PER_STATE,
+                "fp64_pipe_frac": THERMO_FP64_INSTR_PER_STATE * n / (ms / 1e3)
+                                  / (FP64_PEAK_TFLOPS * 1e12 / 2.0),
+                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2.07 GHz"}
     return {"value": n / (ms / 1e3) / 1e6, "unit": "Mstates/s", "states": n, "ms_per_sweep": ms,
+            "roofline": roof,
             "bytes_per_state": 8 * (2 + ns) + 8 * (4 + 2 * ns) + 1,
             "max_rel_T_roundtrip": err, "status_nonzero": bad,
             "species": ns,
@@ -369,10 +401,11 @@ def thermo_sweep(A, gas, dev, n, seed, reps=2, precision=0):
                       + (" over the heavy species, neutral" if any(c < 0 for c in q) else "")}
 
 
-def serving_bench(A, I, nreq, seed, precision, air11=0.25, inflight=4):
+def serving_bench(A, I, nreq, seed, precision, air11=0.25, inflight=4, steps=(500, 2000)):
     """Continuous batching of a stream of independent solves (serving workload): a closed loop
-    with `inflight` requests on the GPU measures capacity, then nreq requests arrive as a Poisson
-    process at 0.8 x capacity.
+    with `inflight` requests on the GPU measures capacity (on a short stream of 20-80 steps per
+    request), then the first nreq requests of the serving stream (grids 128x32 to 1024x256, Mach
+    5-20, `steps` RK3 steps each) arrive as a Poisson process at 0.8 x capacity.
     A share `air11` of the requests runs on eleven-species air, served by a second server (the
     eleven-species library) beside the five-species one on the same GPU. Reports time-to-solution
     percentiles and the throughput over the serving window."""
@@ -404,7 +437,7 @@ def serving_bench(A, I, nreq, seed, precision, air11=0.25, inflight=4):
     cap = sum(work(r) for r in calib) / (time.perf_counter() - t0)      # points*RHS per second
     for x in sv.values():
         x.close()
-    reqs = I.serving_requests(nreq, seed=seed, steps=(20, 80), air11=air11)
+    reqs = I.serving_requests(nreq, seed=seed, steps=steps, air11=air11)
     mean_work = sum(work(r) for r in reqs) / len(reqs)
     lam = 0.8 * cap / mean_work                                            # requests per second
     sv = servers()
@@ -446,19 +479,50 @@ def serving_bench(A, I, nreq, seed, precision, air11=0.25, inflight=4):
                                  "mach": round(c["mach"], 3), "T_wall": round(c.get("T_wall", 0.0), 1),
                                  "steps": n, "status": s["status"]}
                                 for (c, n, _), s in zip(reqs, st) if s["status"]],
-            "workload": f"grids 128x32 to 1024x256, boundary layers Mach 5-20 (wall 300-1500 K) and "
-                        f"shock interactions, 20-80 RK3 steps each, {air11:.0%} on eleven-species air"}
+            "workload": f"the first {nreq} requests of the serving stream: grids 128x32 to "
+                        f"1024x256, boundary layers Mach 5-20 (wall 300-1500 K) and shock "
+                        f"interactions, {steps[0]}-{steps[1]} RK3 steps each, {air11:.0%} on "
+                        f"eleven-species air"}
 
 
-def jet3d_bench(A, I, dev, rank, world, barrier, flush, steps=2, warmup=1):
+def serving_plain_fp64(A, I, nreq, seed, air11=0.25, steps=(500, 2000)):
+    """The same requests as serving_bench, stepped one at a time through the plain FP64 path
+    (hyp_state_init, then hyp_rk_stage per stage on the request's own grid), back to back: the
+    throughput the serving path is compared against."""
+    import torch
+    reqs = I.serving_requests(nreq, seed=seed, steps=steps, air11=air11)
+    work = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for c, n, _ in reqs:
+        gas = A.gas_model_load(c)
+        m = A.state_size(gas, c)
+        U = torch.empty(m, dtype=torch.float64, device="cuda")
+        dQ = torch.empty_like(U)
+        st = A.state_init(gas, c, U, dQ, I.state_noise(m, c["seed"]))
+        for _ in range(n):
+            for k in range(STAGES):
+                A.rk_stage(st, k, c["dt"])
+        work += c["nx"] * c["ny"] * STAGES * n
+        del st, U, dQ
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    return {"requests": nreq, "precision": "fp64", "value": work / wall / 1e6,
+            "unit": UNIT, "wall_s": wall,
+            "note": "the serving requests stepped one at a time through hyp_rk_stage (FP64), "
+                    "set-up included, no batching"}
+
+
+def jet3d_bench(A, I, dev, rank, world, barrier, flush, steps=2, warmup=1, size=(512, 256, 128)):
     """Sonic jet through a circular orifice into the Mach 8 crossflow, 512 x 256 x 128 cells,
     spanwise periodic: RK3 steps timed with CUDA events (L2 flushed between steps), FP64, with
     binary32 transport, and FP64 replayed from one step captured into a CUDA graph."""
     import torch
-    cfg = I.jet_case(512, 256, 128, seed=7 + rank)
+    nx, ny, nz = size
+    cfg = I.jet_case(nx, ny, nz, seed=7 + rank)
     gas = A.gas_model_load(cfg)
     n = A.state_size(gas, cfg)
-    out = {"workload": "jet_512x256x128_cneq5_rk3", "cells": 512 * 256 * 128,
+    out = {"workload": f"jet_{nx}x{ny}x{nz}_cneq5_rk3", "cells": nx * ny * nz,
            "jet_J": cfg["jet_J"], "unit": UNIT}
     for prec, key in ((A.FP64, "fp64"), (A.MIXED, "mixed"), (A.FP64, "fp64_graph")):
         U = torch.empty(n, dtype=torch.float64, device=dev)
@@ -473,6 +537,8 @@ def jet3d_bench(A, I, dev, rank, world, barrier, flush, steps=2, warmup=1):
                 A.rk_stage(st, k, cfg["dt"], precision=prec)
 
         graph = None
+        if key == "fp64":
+            A.grid_profile(st.grid, True)
         if key == "fp64_graph":
             torch.cuda.synchronize()
             graph = torch.cuda.CUDAGraph()
@@ -492,6 +558,20 @@ def jet3d_bench(A, I, dev, rank, world, barrier, flush, steps=2, warmup=1):
         out[key] = {"value": job_rate(world, out["cells"], steps, ms), "ms_per_step": ms / steps,
                     "status_flags": A.grid_status(st.grid),
                     "finite": bool(torch.isfinite(st.U).all().item())}
+        if key == "fp64":
+            A.grid_profile(st.grid, False)
+            cms, ccount = A.grid_profile_read(st.grid).get("k_closure", (0.0, 0))
+            if ccount:
+                avg_s = cms / ccount / 1e3
+                roof = {"kernel": "k_closure3", "launches": ccount, "avg_launch_ms": avg_s * 1e3,
+                        "share_of_step": cms / max(sum(a.elapsed_time(b) for a, b in ev), 1e-30),
+                        "bound": "alu", "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                        "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2.07 GHz"}
+                if CLOSURE3_FP64_FLOP_PER_POINT > 0:
+                    ach = CLOSURE3_FP64_FLOP_PER_POINT * out["cells"] / avg_s / 1e12
+                    roof.update(achieved=ach, frac=ach / FP64_PEAK_TFLOPS,
+                                algorithmic_flop_per_point=CLOSURE3_FP64_FLOP_PER_POINT)
+                out["roofline"] = roof
         del step, graph, st, U, dQ
         torch.cuda.empty_cache()
     return out
@@ -637,8 +717,13 @@ def ours_arm(args, rank, world, local_rank):
                     peak_source="derived: 152 SMs x 2 DFMA/clk x 2.07 GHz (a DFMA probe "
                                 "measured 1.20 TFLOP/s)",
                     fp64_instr_per_point=CLOSURE_FP64_INSTR_PER_POINT,
-                    fp64_pipe_frac=(CLOSURE_FP64_INSTR_PER_POINT * points / avg_s)
-                                   / (FP64_PEAK_TFLOPS * 1e12 / 2.0))
+                    fp64_pipe_frac=(CLOSURE_FP64_PIPE_INSTR_PER_POINT * points / avg_s)
+                                   / (FP64_PEAK_TFLOPS * 1e12 / 2.0),
+                    effective_frac=CLOSURE_LIBM_FLOP_PER_POINT * points / avg_s / 1e12
+                                   / FP64_PEAK_TFLOPS,
+                    effective_note="the FP64 operation count of the same closure with CUDA's "
+                                   "exp, division and reciprocal (3041 per point) over this "
+                                   "kernel's time")
     else:
         roof.update(bound="alu", achieved=None, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s", frac=None,
                     traffic=None, note="per-point FP64 count not yet measured for this kernel")
@@ -677,7 +762,8 @@ def ours_arm(args, rank, world, local_rank):
                         "algebraic model (Eq. 18); same case, FP64")
     jet3d = None
     if not args.no_3d:
-        jet3d = jet3d_bench(A, I, dev, rank, world, barrier, flush)
+        jet3d = jet3d_bench(A, I, dev, rank, world, barrier, flush,
+                            size=tuple(int(v) for v in args.jet3d_size.split("x")))
     air11 = None
     if not args.no_air11:
         air11, a_ms = variant(I.with_species(cfg))
@@ -693,10 +779,14 @@ def ours_arm(args, rank, world, local_rank):
                         "and equilibrium conductivity per point, no species equations; same "
                         "case, FP64")
 
-    serving = serving_fp64 = None
+    serving = serving_fp64 = serving_plain = None
     if args.serve_requests > 0:
         serving = serving_bench(A, I, args.serve_requests, 100 + rank, A.MIXED)
-        serving_fp64 = serving_bench(A, I, args.serve_requests, 100 + rank, A.FP64)
+        serving_plain = serving_plain_fp64(A, I, args.serve_requests, 100 + rank)
+        serving["vs_plain_fp64_one_at_a_time"] = (serving["throughput_mpts_rhs_s"]
+                                                  / serving_plain["value"])
+        if args.serve_fp64:
+            serving_fp64 = serving_bench(A, I, args.serve_requests, 100 + rank, A.FP64)
 
     sweep = None
     if args.thermo_states > 0:
@@ -738,9 +828,14 @@ def ours_arm(args, rank, world, local_rank):
                               "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s (per GPU)",
                               "frac": value / world * RHS_FP64_FLOP_PER_POINT / 1e6 / FP64_PEAK_TFLOPS},
                 "wall_s_timed": t_wall, "status_flags": status, "mixed": mixed,
-                "serving": serving, "serving_fp64": serving_fp64, "stefan_maxwell": smd,
+                "serving": serving, "serving_fp64": serving_fp64,
+                "serving_plain_fp64": serving_plain, "stefan_maxwell": smd,
                 "lte": lte, "air11": air11, "jet3d": jet3d, "thermo_sweep": sweep,
-                "kernels": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1]}}
+                "kernels": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1]},
+                "kernels_note": "live CUDA-event time of each kernel summed over the timed steps; "
+                                "the phases on the second stream overlap the closure, so the sum "
+                                "exceeds the step time and is not a serial breakdown (the "
+                                "serialised shares are in the ncu launch list)"}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -332,6 +332,14 @@ void hyp_server_free(hyp_server* sv);
  * (binary64): DEVICE outputs, each nullable. */
 int hyp_round_f32(int64_t n, const double* x, float* y, double* back, void* stream);
 
+/* The binary64 exponential, quotient and reciprocal the FP64 closure uses (diagnostics; no
+ * counterpart in the paper): exp by Tang's table-driven method and a / b, 1 / b from a binary32
+ * reciprocal refined in binary64, each within 2 ulp; arguments outside their fast ranges (|a| >=
+ * 512 for exp, |b| outside [2^-120, 2^120] for the quotients) go through CUDA's exp and division.
+ * fn 0: out[i] = exp(a[i]); fn 1: out[i] = a[i] / b[i]; fn 2: out[i] = 1 / b[i]. a, b (the one a
+ * function does not read may be null), out: DEVICE arrays of n doubles. */
+int hyp_fp64_fast(int fn, int64_t n, const double* a, const double* b, double* out, void* stream);
+
 /* Pointwise closure of Sec. 2.2 in SI units for n independent states (the work the paper hands
  * to its real-gas library, Sec. 3.4). Inputs (DEVICE): rho[n] kg/m^3, e[n] J/kg internal energy
  * including formation enthalpy (298.15 K reference), Y[ns*n] mass fractions species-major
@@ -362,21 +370,24 @@ int hyp_lte_eval(const hyp_gas* gas, int64_t n, const double* rho, const double*
                  double* p, double* Y, double* mu, double* k, double* k_reactive,
                  uint8_t* status, int precision, void* stream);
 
-/* hyp_rhs without any device allocation of its own scratch (the paper has no counterpart; this
- * is an interface for callers that may not allocate device memory while they run: work enqueued
- * during CUDA stream capture, real-time loops that forbid allocation after start-up, hosts that
- * own all device memory through their own allocator). It computes the same right-hand side as
- * hyp_rhs for the same gas, grid and U, within rounding (the Newton inversion starts from 1000 K
- * instead of the grid's previous temperatures). Arguments as for hyp_rhs, always FP64.
+/* hyp_rhs without any device allocation of its own scratch (the paper has no counterpart). It is
+ * for callers that may not allocate device memory while they run: real-time solver loops that
+ * forbid allocation after start-up, and hosts (simulation frameworks, language runtimes, plug-in
+ * hosts) that own all device memory through their own allocator and do not let a library call
+ * cudaMalloc behind their back. It computes the same right-hand side as hyp_rhs for the same gas,
+ * grid and U, within rounding (the Newton inversion starts from 1000 K instead of the grid's
+ * previous temperatures). Arguments as for hyp_rhs, always FP64; two-dimensional grids only.
  * - Scratch: every per-call scratch field, the line-sweep storage and the launch plan live in one
  *   file-scope device array of 12 MiB (1,572,864 doubles) that every GPU loading the library holds
  *   until exit. Grids needing more (a few thousand cells, e.g. up to 64 x 64) are rejected with
- *   HYP_ERR_ARG and the required size in hyp_last_error(). The grid's own scratch is not touched;
- *   its read-only data (metrics, reference state, sponge, operators) are used.
+ *   HYP_ERR_ARG and the required size in hyp_last_error(). The grid's own scratch and predictor
+ *   cache are not touched, so hyp_rhs and hyp_rhs_noalloc may be mixed on one grid; its read-only
+ *   data (metrics, reference state, sponge, operators) are used. Per-point status bits (Newton,
+ *   energy range, rho <= 0) are OR-ed into the grid's status word, read with hyp_grid_status.
  * - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- *   that device current; make that first call before any stream capture.
- * - Each call reads the grid's launch plan back to the host and synchronises `stream` once, then
- *   enqueues asynchronously. It calls no cudaMalloc, cudaFree or other allocating routine.
+ *   that device current.
+ * - Each call only enqueues work on `stream` (the launch plan is copied and relocated by a kernel):
+ *   no host synchronisation, and no cudaMalloc, cudaFree or other allocating routine.
  * - All calls on a device share the array: it keeps the last call's contents (the parts that must
  *   start at zero are cleared on every call), and calls that overlap on the GPU race. */
 int hyp_rhs_noalloc(const hyp_gas* gas, const hyp_grid* grid, const double* U, double* dUdt,
@@ -384,7 +395,8 @@ int hyp_rhs_noalloc(const hyp_gas* gas, const hyp_grid* grid, const double* U, d
 
 /* Event profile of the launches that hyp_rhs / hyp_rk_stage make on a grid (diagnostics; no
  * counterpart in the paper). hyp_grid_profile(grid, 1) clears the totals and starts recording a
- * pair of CUDA events around every launch on the caller's stream; (grid, 0) stops. Reading
+ * pair of CUDA events around every launch (on a three-dimensional grid: around the closure's
+ * launches only) on the caller's stream; (grid, 0) stops. Reading
  * synchronises on the recorded events and returns, for the first n kernel ids, the summed
  * device time in ms and the launch count (HOST arrays, nullable). Kernel ids run from 0 to
  * hyp_profile_count() - 1; hyp_profile_name(id) is a static string. */

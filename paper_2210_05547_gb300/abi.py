@@ -97,6 +97,7 @@ EXPORTS = {
     "hyp_rhs_noalloc": (_I, [_P, _P, _P, _P, _P]),
     "hyp_wall_fluxes": (_I, [_P, _P, _P, _P, _P, _I, _P]),
     "hyp_round_f32": (_I, [_I64, _P, _P, _P, _P]),
+    "hyp_fp64_fast": (_I, [_I, _I64, _P, _P, _P, _P]),
     "hyp_batch_create": (_I, [_I, ctypes.POINTER(_P)]),
     "hyp_batch_add": (_I, [_P, _P, _D]),
     "hyp_batch_remove": (_I, [_P, _P]),
@@ -349,6 +350,15 @@ def round_f32(x, y=None, back=None, stream=None):
                                _dptr(y, n, torch.float32) if y is not None else None,
                                _dptr(back, n, torch.float64) if back is not None else None,
                                _stream(stream)))
+
+
+def fp64_fast(fn, out, a=None, b=None, stream=None):
+    """hyp_fp64_fast: fn 0 exp(a), 1 a / b, 2 1 / b as the FP64 closure computes them, device."""
+    import torch
+    n = out.numel()
+    _check(lib().hyp_fp64_fast(fn, n, _dptr(a, n, torch.float64) if a is not None else None,
+                               _dptr(b, n, torch.float64) if b is not None else None,
+                               _dptr(out, n, torch.float64), _stream(stream)))
 
 
 class Batch:

@@ -133,6 +133,7 @@ struct LineOp {
     int rc;
     double wac, wbc, lmc, cpc;
     float wac_f, wbc_f, lmc_f, cpc_f;   // the same in binary32 (HYP_MIXED jobs)
+    float wac_l, wbc_l, lmc_l, cpc_l;   // their remainders: (x_f, x_l) is x as a double word
     int ncl;                     // closure rows (<= 4)
     int crow[4], cstart[4], cnum[4];
     double cw[4][5];

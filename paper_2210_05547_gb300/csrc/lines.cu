@@ -23,11 +23,17 @@
 // the rows of that constant stretch are software-pipelined: the loads for row r + 8 are issued
 // while row r is computed.
 //
-// Jobs marked f32ok run that constant stretch in binary32 under HYP_MIXED (the interpolations and
-// derivatives that feed only the diffusive fluxes): inputs are rounded with integer instructions,
-// the recurrences run on the FP32 pipe, the forward values of those rows are kept as binary32 in
-// the first half of their 8-byte storage slot, and outputs are widened back to binary64. Closure
-// rows and the first interior rows stay FP64.
+// Under HYP_MIXED that constant stretch leaves the FP64 pipe. Jobs marked f32ok (the
+// interpolations and derivatives that feed only the diffusive fluxes) run it in plain binary32:
+// inputs are rounded with integer instructions, the recurrences run on the FP32 pipe, the forward
+// values of those rows are kept as binary32 in the first half of their 8-byte storage slot, and
+// outputs are widened back to binary64. Every other job (those feeding the convective fluxes,
+// the pressure and the divergences) runs it in double-word arithmetic (dword.cuh): each binary64
+// input is split into a pair of binary32 numbers, the recurrences carry their rounding errors in
+// the low word (error-free sums and FMA products, about 48 significand bits), the forward values
+// are kept as a binary32 pair in the 8-byte slot, and each output is the binary64 sum of its
+// pair. Closure rows and the first interior rows stay FP64.
+#include "dword.cuh"
 #include "fp32.cuh"
 #include "internal.h"
 
@@ -177,8 +183,64 @@ __device__ __forceinline__ void fwd_rows_const32(int r, int r1, double& d, Windo
     p += (long long)n * ies;
 }
 
+template <int KIND>
+__device__ __forceinline__ dword interior_row_dw(dword d, dword p0, dword p1, dword p2, dword p3,
+                                                 dword wa, dword wb, dword lm) {
+    const dword s1 = KIND == 0 ? dw_add(p1, p2) : dw_sub(p2, p1);
+    const dword s2 = KIND == 0 ? dw_add(p0, p3) : dw_sub(p3, p0);
+    return dw_sub(dw_add(dw_mul(wa, s1), dw_mul(wb, s2)), dw_mul(lm, d));
+}
+
+// The constant-factor rows r..r1 in double-word arithmetic (jobs not marked f32ok under
+// HYP_MIXED). The window keeps each input both as binary64 (handed back to the FP64 rows that
+// follow) and as a double word.
+template <int KIND, bool STORE>
+__device__ __forceinline__ void fwd_rows_constdw(int r, int r1, double& d, Window& w,
+                                                 const double* __restrict__& p, long long ies,
+                                                 const LineOp& op, double* __restrict__ tmp,
+                                                 long long oes) {
+    const int n = r1 - r + 1;
+    if (n <= 0) return;
+    const dword wa{op.wac_f, op.wac_l}, wb{op.wbc_f, op.wbc_l}, lm{op.lmc_f, op.lmc_l};
+    const double* __restrict__ pp = p;
+    dword dd = dw_of(d), p0 = dw_of(w.p0), p1 = dw_of(w.p1), p2 = dw_of(w.p2);
+    double q[PF];
+#pragma unroll
+    for (int k = 0; k < PF; ++k) q[k] = k < n ? pp[(long long)k * ies] : 0.0;
+    for (; r + PF - 1 <= r1; r += PF) {
+#pragma unroll
+        for (int k = 0; k < PF; ++k) {
+            const double x3 = q[k];
+            const dword p3 = dw_of(x3);
+            q[k] = r + PF + k <= r1 ? pp[(long long)(PF + k) * ies] : 0.0;
+            dd = interior_row_dw<KIND>(dd, p0, p1, p2, p3, wa, wb, lm);
+            if (STORE) dw_store(tmp + (long long)(r + k) * oes, dd);
+            p0 = p1;
+            p1 = p2;
+            p2 = p3;
+            shift(w, x3);
+        }
+        pp += PF * ies;
+    }
+#pragma unroll
+    for (int k = 0; k < PF - 1; ++k) {
+        if (r + k <= r1) {
+            const double x3 = q[k];
+            const dword p3 = dw_of(x3);
+            dd = interior_row_dw<KIND>(dd, p0, p1, p2, p3, wa, wb, lm);
+            if (STORE) dw_store(tmp + (long long)(r + k) * oes, dd);
+            p0 = p1;
+            p1 = p2;
+            p2 = p3;
+            shift(w, x3);
+        }
+    }
+    d = dw_to_f64(dd);
+    p += (long long)n * ies;
+}
+
 // Forward sweep over rows r..r1 of one kind of region (closure / per-row / constant interior).
-template <int KIND, bool STORE, bool F32>
+template <int KIND, bool STORE, int MODE>
 __device__ __forceinline__ void fwd_span(int r, int r1, double& d, Window& w,
                                          const double* __restrict__ in,
                                          const double* __restrict__& p, long long ies,
@@ -209,7 +271,8 @@ __device__ __forceinline__ void fwd_span(int r, int r1, double& d, Window& w,
         }
         const int rcn = min(r1, li);
         if (r <= rcn) {
-            if (F32) fwd_rows_const32<KIND, STORE>(r, rcn, d, w, p, ies, op, tmp, oes);
+            if (MODE == 1) fwd_rows_const32<KIND, STORE>(r, rcn, d, w, p, ies, op, tmp, oes);
+            else if (MODE == 2) fwd_rows_constdw<KIND, STORE>(r, rcn, d, w, p, ies, op, tmp, oes);
             else fwd_rows_const<KIND, STORE>(r, rcn, d, w, p, ies, op, tmp, oes);
             r = rcn + 1;
         }
@@ -326,8 +389,48 @@ __device__ __forceinline__ void back_rows_const32(int r0, int r1, double& y,
     y = f64_of(yf);
 }
 
+// The constant-factor rows r0 >= r >= r1 in double-word arithmetic, reading the double-word
+// forward values; each output is the binary64 sum of its pair (times the metric in binary64).
+template <int OM>
+__device__ __forceinline__ void back_rows_constdw(int r0, int r1, double& y,
+                                                  const double* __restrict__ tmp, long long oes,
+                                                  dword cc, const double* __restrict__ met,
+                                                  double* __restrict__ out) {
+    const int n = r0 - r1 + 1;
+    if (n <= 0) return;
+    dword yd = dw_of(y);
+    dword q[PF];
+    double mq[PF];
+#pragma unroll
+    for (int k = 0; k < PF; ++k) {
+        q[k] = k < n ? dw_load(tmp + (long long)(r0 - k) * oes) : dword{0.0f, 0.0f};
+        mq[k] = (OM >= 3 && k < n) ? met[r0 - k] : 0.0;
+    }
+    int r = r0;
+    for (; r - PF + 1 >= r1; r -= PF) {
+#pragma unroll
+        for (int k = 0; k < PF; ++k) {
+            const dword t = q[k];
+            const double m = mq[k];
+            const int rn = r - PF - k;
+            q[k] = rn >= r1 ? dw_load(tmp + (long long)rn * oes) : dword{0.0f, 0.0f};
+            if (OM >= 3) mq[k] = rn >= r1 ? met[rn] : 0.0;
+            yd = dw_sub(t, dw_mul(cc, yd));
+            if (OM != 0) put<OM>(out, oes, r - k, dw_to_f64(yd), m);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < PF - 1; ++k) {
+        if (r - k >= r1) {
+            yd = dw_sub(q[k], dw_mul(cc, yd));
+            if (OM != 0) put<OM>(out, oes, r - k, dw_to_f64(yd), mq[k]);
+        }
+    }
+    y = dw_to_f64(yd);
+}
+
 // Back substitution over rows r0 >= r >= r1, split at the constant-factor stretch.
-template <int OM, bool F32>
+template <int OM, int MODE>
 __device__ __forceinline__ void back_span(int r0, int r1, double& y, const LineOp& op,
                                           const double* __restrict__ tmp, long long oes,
                                           const double* __restrict__ met,
@@ -339,14 +442,16 @@ __device__ __forceinline__ void back_span(int r0, int r1, double& y, const LineO
     if (r0 >= a) back_rows_var<OM>(r0, a, y, tmp, oes, op.cprime, met, out);
     const int c0 = min(r0, li), c1 = max(r1, rc);
     if (c0 >= c1) {
-        if (F32) back_rows_const32<OM>(c0, c1, y, tmp, oes, op.cpc_f, met_f, out);
+        if (MODE == 1) back_rows_const32<OM>(c0, c1, y, tmp, oes, op.cpc_f, met_f, out);
+        else if (MODE == 2)
+            back_rows_constdw<OM>(c0, c1, y, tmp, oes, dword{op.cpc_f, op.cpc_l}, met, out);
         else back_rows_const<OM>(c0, c1, y, tmp, oes, op.cpc, met, out);
     }
     const int v0 = min(r0, rc - 1);
     if (v0 >= r1) back_rows_var<OM>(v0, r1, y, tmp, oes, op.cprime, met, out);
 }
 
-template <int KIND, bool F32>
+template <int KIND, int MODE>
 __device__ __forceinline__ void forward(const LineJob& J, const LineOp& op,
                                         const double* __restrict__ in, double* __restrict__ tmp,
                                         int s, int e, int W, double wall) {
@@ -355,31 +460,34 @@ __device__ __forceinline__ void forward(const LineJob& J, const LineOp& op,
     double d = 0.0;
     Window w{0.0, 0.0, 0.0};
     const double* __restrict__ p = nullptr;
-    fwd_span<KIND, false, F32>(fs, s - 1, d, w, in, p, ies, op, wall, tmp, oes);
-    fwd_span<KIND, true, F32>(s, e, d, w, in, p, ies, op, wall, tmp, oes);
+    fwd_span<KIND, false, MODE>(fs, s - 1, d, w, in, p, ies, op, wall, tmp, oes);
+    fwd_span<KIND, true, MODE>(s, e, d, w, in, p, ies, op, wall, tmp, oes);
 }
 
-template <int OM, bool F32>
+template <int OM, int MODE>
 __device__ __forceinline__ void backward(const LineOp& op, const double* __restrict__ tmp,
                                          long long oes, const double* __restrict__ met,
                                          const float* __restrict__ met_f,
                                          double* __restrict__ out, int s, int e, int be) {
     // the last row is a closure row (FP64 storage) or, for lines without one, an interior row
-    const bool last32 = F32 && be >= op.rc && be <= op.last_interior;
-    double y = last32 ? f64_of(*slot32(tmp + (long long)be * oes)) : tmp[(long long)be * oes];
+    const bool last_c = MODE != 0 && be >= op.rc && be <= op.last_interior;
+    double y;
+    if (last_c && MODE == 1) y = f64_of(*slot32(tmp + (long long)be * oes));
+    else if (last_c) y = dw_to_f64(dw_load(tmp + (long long)be * oes));
+    else y = tmp[(long long)be * oes];
     if (be <= e) put<OM>(out, oes, be, y, OM >= 3 ? met[be] : 0.0);
-    back_span<0, F32>(be - 1, e + 1, y, op, tmp, oes, met, met_f, out);   // warm-up rows
-    back_span<OM, F32>(min(be - 1, e), s, y, op, tmp, oes, met, met_f, out);
+    back_span<0, MODE>(be - 1, e + 1, y, op, tmp, oes, met, met_f, out);   // warm-up rows
+    back_span<OM, MODE>(min(be - 1, e), s, y, op, tmp, oes, met, met_f, out);
 }
 
-template <bool F32>
+template <int MODE>
 __device__ __forceinline__ void run_line(const LineJob& J, const LineOp& op,
                                          const double* __restrict__ in, double* __restrict__ out,
                                          double* __restrict__ tmp, int s, int e, int m, int W,
                                          bool active, double wall) {
     if (active && s <= e) {
-        if (op.kind == 0) forward<0, F32>(J, op, in, tmp, s, e, W, wall);
-        else forward<1, F32>(J, op, in, tmp, s, e, W, wall);
+        if (op.kind == 0) forward<0, MODE>(J, op, in, tmp, s, e, W, wall);
+        else forward<1, MODE>(J, op, in, tmp, s, e, W, wall);
     }
     __syncthreads();
     if (active && s <= e) {
@@ -389,11 +497,11 @@ __device__ __forceinline__ void run_line(const LineJob& J, const LineOp& op,
         const bool neg = J.scale < 0.0;
         const long long oes = J.out_es;
         if (met) {
-            if (neg) backward<4, F32>(op, tmp, oes, met, met_f, out, s, e, be);
-            else backward<3, F32>(op, tmp, oes, met, met_f, out, s, e, be);
+            if (neg) backward<4, MODE>(op, tmp, oes, met, met_f, out, s, e, be);
+            else backward<3, MODE>(op, tmp, oes, met, met_f, out, s, e, be);
         } else {
-            if (neg) backward<2, F32>(op, tmp, oes, met, met_f, out, s, e, be);
-            else backward<1, F32>(op, tmp, oes, met, met_f, out, s, e, be);
+            if (neg) backward<2, MODE>(op, tmp, oes, met, met_f, out, s, e, be);
+            else backward<1, MODE>(op, tmp, oes, met, met_f, out, s, e, be);
         }
     }
 }
@@ -426,8 +534,9 @@ __global__ void __launch_bounds__(LINE_BLOCK) k_lines(const LineJob* __restrict_
     double* __restrict__ tmp = J.tmp + ooff;
     const double wall = (J.wall_arr && active) ? J.wall_arr[line] : J.wall_value;
     // uniform per block: every thread of a block works on the same job
-    if (mixed && J.f32ok) run_line<true>(J, op, in, out, tmp, s, e, m, W, active, wall);
-    else run_line<false>(J, op, in, out, tmp, s, e, m, W, active, wall);
+    if (mixed && J.f32ok) run_line<1>(J, op, in, out, tmp, s, e, m, W, active, wall);
+    else if (mixed) run_line<2>(J, op, in, out, tmp, s, e, m, W, active, wall);
+    else run_line<0>(J, op, in, out, tmp, s, e, m, W, active, wall);
 }
 
 }  // namespace

@@ -24,10 +24,18 @@ __device__ __forceinline__ void closure_body(const GasDev& g, const Scales& sc, 
     const bool cpg = sc.kind == HYP_GAS_CPG;
     const bool tpg = sc.kind == HYP_GAS_TPG;
     const bool cneq = sc.kind == HYP_GAS_CNEQ;
+    // reciprocals of the freestream scales, once per thread: the loop multiplies by them, with
+    // __dmul_rn so that no product is fused into a later addition (the single-grid and batched
+    // kernels inline this body into different code and must round identically)
+    const double iT_ref = 1.0 / sc.T_ref, imu_inf = 1.0 / sc.mu_inf, ik_inf = 1.0 / sc.k_inf;
+    const double ia_inf = 1.0 / sc.a_inf, iRe = 1.0 / sc.Re, iRePr = 1.0 / (sc.Re * sc.Pr);
+    const double ip_ref = ia_inf * ia_inf / sc.rho_inf, ia2 = ia_inf * ia_inf;
+    const double d_nd = sc.rho_inf * imu_inf * iRe;     // D (SI) -> rho_inf D / (mu_inf Re)
+    const double wscale = sc.L_ref * ia_inf / sc.rho_inf;   // w (SI) -> nondimensional
     for (long long li = lo + threadIdx.x; li < hi; li += stride) {
         const int idx = (int)li;
         const double rho = U[v.off[0] + idx];
-        const double irho = 1.0 / rho;
+        const double irho = cl_rcp(rho);
         double Y[NSP];
         double rest = rho;
 #pragma unroll
@@ -66,11 +74,11 @@ __device__ __forceinline__ void closure_body(const GasDev& g, const Scales& sc, 
             s.esc[1][idx] = lam[1];
             s.esc[2][idx] = e_si;
             s.esc[3][idx] = cv_eq;
-            T = o.T / sc.T_ref;
-            p = o.p / (sc.rho_inf * sc.a_inf * sc.a_inf);
-            mu = o.mu / sc.mu_inf;
-            k = o.k / sc.k_inf;
-            a = o.a / sc.a_inf;
+            T = __dmul_rn(o.T, iT_ref);
+            p = __dmul_rn(o.p, ip_ref);
+            mu = __dmul_rn(o.mu, imu_inf);
+            k = __dmul_rn(o.k, ik_inf);
+            a = __dmul_rn(o.a, ia_inf);
 #pragma unroll
             for (int sp = 0; sp < NSP; ++sp) {
                 h[sp] = wd[sp] = W[sp] = Wd[sp] = 0.0;
@@ -114,7 +122,7 @@ __device__ __forceinline__ void closure_body(const GasDev& g, const Scales& sc, 
                     cvc += Y[sp] * s.cvsc[sp][idx];
                     cvpc += Y[sp] * s.cvpc[sp][idx];
                 }
-                const double icv = 1.0 / cvc;
+                const double icv = cl_rcp(cvc);
                 const double d1 = (e_si - ec) * icv;
                 T0 += d1 - 0.5 * cvpc * d1 * d1 * icv;
             }
@@ -128,24 +136,22 @@ __device__ __forceinline__ void closure_body(const GasDev& g, const Scales& sc, 
                 s.cvsc[sp][idx] = o.cvs[sp];
                 s.cvpc[sp][idx] = o.cvps[sp];
             }
-            T = o.T / sc.T_ref;
-            p = o.p / (sc.rho_inf * sc.a_inf * sc.a_inf);
-            mu = o.mu / sc.mu_inf;
-            k = o.k / sc.k_inf;
-            a = o.a / sc.a_inf;
+            T = __dmul_rn(o.T, iT_ref);
+            p = __dmul_rn(o.p, ip_ref);
+            mu = __dmul_rn(o.mu, imu_inf);
+            k = __dmul_rn(o.k, ik_inf);
+            a = __dmul_rn(o.a, ia_inf);
             double ym = 0.0;
 #pragma unroll
             for (int sp = 0; sp < NSP; ++sp) ym += Y[sp] * g.invM[sp];
-            const double wscale = sc.L_ref / (sc.rho_inf * sc.a_inf);
-            const double inva2 = 1.0 / (sc.a_inf * sc.a_inf);
 #pragma unroll
             for (int sp = 0; sp < NSP; ++sp) {
-                h[sp] = o.h[sp] * inva2;
-                wd[sp] = o.wdot[sp] * wscale;
+                h[sp] = __dmul_rn(o.h[sp], ia2);
+                wd[sp] = __dmul_rn(o.wdot[sp], wscale);
                 X[sp] = o.X[sp];
                 // the electron's diffusive flux follows the ions (flux_point): no coefficient
                 W[sp] = cneq && (!HAS_CHARGE || g.heavy[sp]) ? rho * g.M[sp] * ym : 0.0;
-                Wd[sp] = cneq ? W[sp] * (o.D[sp] * sc.rho_inf / sc.mu_inf) / sc.Re : 0.0;
+                Wd[sp] = cneq ? __dmul_rn(W[sp], __dmul_rn(o.D[sp], d_nd)) : 0.0;
             }
         }
         s.T[idx] = T;
@@ -155,8 +161,8 @@ __device__ __forceinline__ void closure_body(const GasDev& g, const Scales& sc, 
         s.v_c[idx] = vv;
         s.e[idx] = e;
         s.a[idx] = a;
-        s.mu_e[idx] = mu / sc.Re;
-        s.K[idx] = k / (sc.Re * sc.Pr);
+        s.mu_e[idx] = __dmul_rn(mu, iRe);
+        s.K[idx] = __dmul_rn(k, iRePr);
         if (!v.ad) s.beta[idx] = 0.0;
 #pragma unroll
         for (int sp = 0; sp < NSP; ++sp) {
@@ -182,13 +188,13 @@ __device__ __forceinline__ void face_vel_body(const GridView& v, const double* _
         const int i = (int)li;
         if (i < nxf) {
             const double m = U[v.off[NSP + 1] + i];
-            const double u = m / s.rho_xf[i];
+            const double u = cl_div(m, s.rho_xf[i]);
             s.u_xf[i] = u;
             s.mux_f[i] = m * u;
         } else {
             const int j = i - nxf;
             const double m = U[v.off[NSP + 2] + j];
-            const double vv = m / s.rho_yf[j];
+            const double vv = cl_div(m, s.rho_yf[j]);
             s.v_yf[j] = vv;
             s.mvy_f[j] = m * vv;
         }
@@ -206,7 +212,7 @@ __device__ __forceinline__ void ad_prep_body(const Scratch& s, long long lo, lon
         const double dv = ux + vy;
         const double om = vx - uy;
         s.div[i] = dv;
-        s.fsw[i] = dv < 0.0 ? dv * dv / (dv * dv + om * om + DUCROS_EPS) : 0.0;
+        s.fsw[i] = dv < 0.0 ? cl_div(dv * dv, dv * dv + om * om + DUCROS_EPS) : 0.0;
     }
 }
 
@@ -228,13 +234,13 @@ __device__ __forceinline__ void ad_raw_body(bool cneq, const GridView& v,
     for (long long li = lo + threadIdx.x; li < hi; li += stride) {
         const int idx = (int)li;
         const int j = idx / v.nx, i = idx - j * v.nx;
-        const double dx = 1.0 / v.xi_c[i], dy = 1.0 / v.eta_c[j];
+        const double dx = cl_rcp(v.xi_c[i]), dy = cl_rcp(v.eta_c[j]);
         const double rho = U[v.off[0] + idx];
         s.raw[0][idx] = v.C_mu * rho *
                         fabs(d4x(s.S, j, i, v.nx) * dx * dx + d4y(s.S, j, i, v.nx, v.ny) * dy * dy);
         s.raw[1][idx] = v.C_beta * rho * s.fsw[idx] *
                         fabs(d4x(s.div, j, i, v.nx) * dx * dx + d4y(s.div, j, i, v.nx, v.ny) * dy * dy);
-        s.raw[2][idx] = v.C_kappa * rho * s.a[idx] / s.T[idx] *
+        s.raw[2][idx] = v.C_kappa * rho * cl_div(s.a[idx], s.T[idx]) *
                         fabs(d4x(s.e, j, i, v.nx) * dx + d4y(s.e, j, i, v.nx, v.ny) * dy);
 #pragma unroll
         for (int sp = 0; sp < NSP; ++sp)

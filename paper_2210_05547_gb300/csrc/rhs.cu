@@ -368,6 +368,10 @@ LineOp make_op(int kind, int dir, int n, int wall, std::vector<double>& data) {
         op.wbc_f = (float)op.wbc;
         op.lmc_f = (float)op.lmc;
         op.cpc_f = (float)op.cpc;
+        op.wac_l = (float)(op.wac - (double)op.wac_f);
+        op.wbc_l = (float)(op.wbc - (double)op.wbc_f);
+        op.lmc_l = (float)(op.lmc - (double)op.lmc_f);
+        op.cpc_l = (float)(op.cpc - (double)op.cpc_f);
     }
     // store offsets into data (fixed up to device pointers later)
     const size_t base = data.size();
@@ -391,7 +395,7 @@ enum OpId { OX_ICF, OX_DCF, OX_IFC, OX_DFC, OY_ICF, OY_DCF, OY_IFC, OY_DFC, OY_I
 #define GRID_RANGE(n) (long long)blockIdx.x * blockDim.x, (long long)(n), (long long)gridDim.x * blockDim.x
 
 template <bool MIXED, bool LTE>
-__global__ void __launch_bounds__(128) k_closure(GasDev g, Scales sc, GridView v,
+__global__ void __launch_bounds__(128, 3) k_closure(GasDev g, Scales sc, GridView v,
                                                  const double* __restrict__ U, Scratch s) {
     closure_body<MIXED, LTE>(g, sc, v, U, s, GRID_RANGE((long long)v.nx * v.ny));
 }
@@ -565,6 +569,29 @@ struct PlanBuilder {
     }
 };
 
+// Event profile (hyp_grid_profile): a pair of CUDA events around a launch on stream s.
+static int prof_begin(hyp_grid* G, int kid, cudaStream_t s) {
+    EventProfile* P = G->prof;
+    if (!P || !P->on) return -1;
+    if (P->used + 2 > P->ev.size()) {
+        for (int k = 0; k < 256; ++k) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return -1;
+            P->ev.push_back(e);
+        }
+        P->id.resize(P->ev.size() / 2);
+    }
+    const size_t slot = P->used;
+    P->used += 2;
+    P->id[slot / 2] = kid;
+    cudaEventRecord(P->ev[slot], s);
+    return (int)slot;
+}
+
+static void prof_end(hyp_grid* G, int slot, cudaStream_t s) {
+    if (slot >= 0) cudaEventRecord(G->prof->ev[slot + 1], s);
+}
+
 #include "rhs3d.cuh"
 
 }  // namespace
@@ -734,6 +761,9 @@ extern "C" int hyp_state_init(const hyp_gas* gas, const hyp_grid_desc* desc, con
     const long long pool_n = n_c_fields * nc + n_xf_fields * nxf + n_yf_fields * nyf +
                              n_cn_fields * ncn + 6 * ns_ + (2 * nx + 1) + (2 * ny + 1) + 4;
     cudaError_t err = cudaMalloc(&G->pool, pool_n * sizeof(double));
+    // cleared once: entries a kernel reads before any kernel writes them (fields of held boundary
+    // rows, for instance) then read as zero on every grid, whatever the allocation held before
+    if (err == cudaSuccess) err = cudaMemsetAsync(G->pool, 0, pool_n * sizeof(double), s);
     if (err != cudaSuccess) {
         free_grid(G);
         return cuda_fail(err, "cudaMalloc(grid pool)");
@@ -1045,28 +1075,6 @@ extern "C" int hyp_grid_status(const hyp_grid* G, uint32_t* flags, int clear) {
     return HYP_OK;
 }
 
-static int prof_begin(hyp_grid* G, int kid, cudaStream_t s) {
-    EventProfile* P = G->prof;
-    if (!P || !P->on) return -1;
-    if (P->used + 2 > P->ev.size()) {
-        for (int k = 0; k < 256; ++k) {
-            cudaEvent_t e;
-            if (cudaEventCreate(&e) != cudaSuccess) return -1;
-            P->ev.push_back(e);
-        }
-        P->id.resize(P->ev.size() / 2);
-    }
-    const size_t slot = P->used;
-    P->used += 2;
-    P->id[slot / 2] = kid;
-    cudaEventRecord(P->ev[slot], s);
-    return (int)slot;
-}
-
-static void prof_end(hyp_grid* G, int slot, cudaStream_t s) {
-    if (slot >= 0) cudaEventRecord(G->prof->ev[slot + 1], s);
-}
-
 #define TIMED_ON(st, kid, ...)                        \
     do {                                              \
         const int _slot = prof_begin(G, kid, st);     \
@@ -1274,6 +1282,30 @@ extern "C" int hyp_round_f32(int64_t n, const double* x, float* y, double* back,
     return HYP_OK;
 }
 
+// The binary64 exponential, quotient and reciprocal of the closure (fp64_fast.cuh), one per
+// element: fn 0 out = exp(a), 1 out = a / b, 2 out = 1 / b.
+__global__ void k_fp64_fast(int fn, int64_t n, const double* __restrict__ a,
+                            const double* __restrict__ b, double* __restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (fn == 0) out[i] = tang_exp(a[i]);
+        else if (fn == 1) out[i] = fast_div(a[i], b[i]);
+        else out[i] = fast_rcp(b[i]);
+    }
+}
+
+extern "C" int hyp_fp64_fast(int fn, int64_t n, const double* a, const double* b, double* out,
+                             void* stream) {
+    if (fn < 0 || fn > 2 || n < 0) return fail(HYP_ERR_ARG, "unknown function or negative n");
+    if (n > 0 && (!out || (fn <= 1 && !a) || (fn >= 1 && !b)))
+        return fail(HYP_ERR_ARG, "null argument");
+    if (n == 0) return HYP_OK;
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 16);
+    k_fp64_fast<<<(int)blocks, 256, 0, (cudaStream_t)stream>>>(fn, n, a, b, out);
+    HYP_CUDA(cudaGetLastError());
+    return HYP_OK;
+}
+
 extern "C" int hyp_profile_count(void) { return KID_COUNT; }
 
 extern "C" const char* hyp_profile_name(int id) {
@@ -1283,7 +1315,6 @@ extern "C" const char* hyp_profile_name(int id) {
 extern "C" int hyp_grid_profile(const hyp_grid* grid, int enable) {
     if (!grid) return fail(HYP_ERR_ARG, "null grid");
     hyp_grid* G = const_cast<hyp_grid*>(grid);
-    if (G->g3) return fail(HYP_ERR_ARG, "the event profile covers two-dimensional grids");
     if (!G->prof) G->prof = new EventProfile();
     EventProfile* P = G->prof;
     if (enable) {
@@ -1322,13 +1353,14 @@ extern "C" int hyp_grid_profile_read(const hyp_grid* grid, int n, double* ms, in
 // ---------------------------------------------------------------------------------------------
 // hyp_rhs_noalloc: the right-hand side with all per-call scratch in one static device array.
 //
-// Some callers may not allocate device memory once they are running: code that enqueues work
-// while a CUDA stream is being captured into a graph (an allocation there breaks or invalidates
-// the capture), real-time solver loops that forbid allocation after start-up, and hosts that own
-// all device memory through their own allocator. hyp_rhs never allocates either, but it keeps
-// its scratch inside the grid handle; this variant instead takes every scratch field, the line
-// sweep storage and its launch plan from the file-scope array below, so a grid's scratch is not
-// touched. The grid's read-only data (metrics, reference state, sponge, operators) are used as is.
+// Some callers may not allocate device memory once they are running: real-time solver loops that
+// forbid allocation after start-up, and hosts (simulation frameworks, language runtimes, plug-in
+// hosts) that own all device memory through their own allocator and do not let a library call
+// cudaMalloc behind their back. hyp_rhs never allocates either, but it keeps its scratch inside
+// the grid handle, which the grid allocated when it was built; this variant instead takes every
+// scratch field, the line-sweep storage and its launch plan from the file-scope array below, so a
+// grid's scratch is not touched. The grid's read-only data (metrics, reference state, sponge,
+// operators) are used as is, and the per-point status bits go to the grid's status word.
 // ---------------------------------------------------------------------------------------------
 
 #define HYP_NOALLOC_DOUBLES (3LL << 19)   // 1,572,864 doubles = 12 MiB per GPU
@@ -1338,6 +1370,25 @@ extern "C" int hyp_grid_profile_read(const hyp_grid* grid, int n, double* ms, in
 static __device__ __align__(256) double g_noalloc_scratch[HYP_NOALLOC_DOUBLES];
 static double* g_noalloc_base[HYP_NOALLOC_MAX_DEVICES];
 static std::mutex g_noalloc_mutex;
+
+// Copy of a launch plan whose field pointers into the grid's scratch pool or line-sweep storage
+// are moved to the same offsets in the static array (one thread per job).
+__global__ void k_relocate_jobs(const LineJob* __restrict__ src, LineJob* __restrict__ dst, int n,
+                                const double* pool, long long pool_n, const double* linetmp,
+                                long long linetmp_n, double* base, double* tmp_base) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    auto relocate = [&](const double* p) -> double* {
+        if (p >= pool && p < pool + pool_n) return base + (p - pool);
+        if (p >= linetmp && p < linetmp + linetmp_n) return tmp_base + (p - linetmp);
+        return const_cast<double*>(p);
+    };
+    LineJob j = src[k];
+    if (!j.in_state) j.in = relocate(j.in);
+    j.out = relocate(j.out);
+    j.tmp = relocate(j.tmp);
+    dst[k] = j;
+}
 
 // Device address of the static array on the current device, looked up once per device. The
 // array's name in host code is only a host-side stand-in, so the address must come from
@@ -1382,21 +1433,17 @@ extern "C" int hyp_rhs_noalloc(const hyp_gas* gas, const hyp_grid* grid, const d
         if (p >= G->linetmp && p < G->linetmp + G->linetmp_n) return tmp_base + (p - G->linetmp);
         return const_cast<double*>(p);
     };
-    // the grid's launch plan, with its scratch pointers moved into the static array
-    LineJob jobs[HYP_NOALLOC_MAX_JOBS];
-    HYP_CUDA(cudaMemcpyAsync(jobs, G->jobs, njobs * sizeof(LineJob), cudaMemcpyDeviceToHost, s));
-    HYP_CUDA(cudaStreamSynchronize(s));
-    for (int k = 0; k < njobs; ++k) {
-        if (!jobs[k].in_state) jobs[k].in = relocate(jobs[k].in);
-        jobs[k].out = relocate(jobs[k].out);
-        jobs[k].tmp = relocate(jobs[k].tmp);
-    }
-    HYP_CUDA(cudaMemcpyAsync(djobs, jobs, njobs * sizeof(LineJob), cudaMemcpyHostToDevice, s));
+    // the grid's launch plan, copied on the device with its scratch pointers moved into the
+    // static array (no host buffer, no synchronisation)
+    k_relocate_jobs<<<blocks_for(njobs, 64), 64, 0, s>>>(G->jobs, djobs, njobs, G->pool, scratch_n,
+                                                         G->linetmp, G->linetmp_n, base, tmp_base);
+    HYP_CUDA(cudaGetLastError());
     Scratch S = G->s;
     double** fields = reinterpret_cast<double**>(&S);
     for (size_t k = 0; k < sizeof(Scratch) / sizeof(double*); ++k) fields[k] = relocate(fields[k]);
-    // state carried between calls is reset: species sources start at zero, Newton starts at 1000 K
-    HYP_CUDA(cudaMemsetAsync(S.SRC, 0, G->nstate * sizeof(double), s));
+    // every call starts from cleared scratch, as a newly built grid does (the array keeps the last
+    // call's contents, possibly of another grid); the Newton iteration starts at 1000 K
+    HYP_CUDA(cudaMemsetAsync(base, 0, (scratch_n + G->linetmp_n) * sizeof(double), s));
     const long long nc = G->d.size(NC);
     k_fill<<<blocks_for(nc, 256), 256, 0, s>>>(S.Tcache, nc, 1000.0);
     HYP_CUDA(cudaGetLastError());

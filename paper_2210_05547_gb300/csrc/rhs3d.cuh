@@ -746,8 +746,10 @@ int run_rhs3(const hyp_gas* gas, hyp_grid* G, const double* U, double* dUdt, int
     HYP_CUDA(cudaEventRecord(G->fork[0], s));
     HYP_CUDA(cudaStreamWaitEvent(s2, G->fork[0], 0));
     const Scales sc = scales_of(gd);
+    const int slot = prof_begin(G, KID_CLOSURE, s);     // the event profile's one 3-D entry
     if (precision == HYP_MIXED) k_closure3<true><<<blocks3(g->nc), 128, 0, s>>>(gd, sc, *g, v, U);
     else k_closure3<false><<<blocks3(g->nc), 128, 0, s>>>(gd, sc, *g, v, U);
+    prof_end(G, slot, s);
     HYP_CUDA(cudaGetLastError());
     g->cache_valid = 1;
     if ((rc = launch3(g, pl.p3, U, false, mx, s2))) return rc;

@@ -14,6 +14,7 @@
 #include "internal.h"
 #ifdef __CUDACC__
 #include "fp32.cuh"
+#include "fp64_fast.cuh"
 #endif
 
 namespace hyp {
@@ -34,6 +35,39 @@ constexpr double OMEGA_CUT = 40.0;     // skip collision-integral exponentials b
 constexpr double NJA_A = 1.06036, NJA_B = 0.15610, NJA_C = 0.19300, NJA_D = 0.47635;
 constexpr double NJA_E = 1.03587, NJA_F = 1.52996, NJA_G = 1.76474, NJA_H = 3.89411;
 
+// Binary64 exponential, quotient and reciprocal of the closure: on the device the forms of
+// fp64_fast.cuh (Tang's table-driven exp, Newton-refined binary32 reciprocals; within 2 ulp, on
+// about half the FP64-pipe instructions of CUDA's), on the host the C library.
+__host__ __device__ inline double cl_exp(double x) {
+#ifdef __CUDA_ARCH__
+    return tang_exp(x);
+#else
+    return exp(x);
+#endif
+}
+
+__host__ __device__ inline double cl_div(double a, double b) {
+#ifdef __CUDA_ARCH__
+    return fast_div(a, b);
+#else
+    return a / b;
+#endif
+}
+
+__host__ __device__ inline double cl_rcp(double b) {
+#ifdef __CUDA_ARCH__
+    return fast_rcp(b);
+#else
+    return 1.0 / b;
+#endif
+}
+
+// 1 / (e^x - 1) for x > 0: from the exponential where e^x - 1 loses at most a bit (x >= 1),
+// from expm1 below.
+__host__ __device__ inline double cl_inv_expm1(double x) {
+    return x >= 1.0 ? cl_rcp(cl_exp(x) - 1.0) : 1.0 / expm1(x);
+}
+
 // Species modal sums at temperature T: energies (J/kg), heat capacities and their temperature
 // derivative, and the electronic partition function / vibrational factor used by the equilibrium
 // constants, with what a first-order shift in T needs.
@@ -48,7 +82,7 @@ struct SpeciesState {
 };
 
 __host__ __device__ inline void species_state(const GasDev& g, double T, SpeciesState& s) {
-    const double invT = 1.0 / T;
+    const double invT = cl_rcp(T);
     const double invT2 = invT * invT;
 #pragma unroll
     for (int i = 0; i < NSP; ++i) {
@@ -57,14 +91,14 @@ __host__ __device__ inline void species_state(const GasDev& g, double T, Species
             const double th = g.lev_th[i][l];
             const double x = th * invT;
             if (x > LEVEL_CUT) break;
-            const double w = th == 0.0 ? g.lev_g[i][l] : g.lev_g[i][l] * exp(-x);
+            const double w = th == 0.0 ? g.lev_g[i][l] : g.lev_g[i][l] * cl_exp(-x);
             const double wt = w * th;
             q += w;
             m1 += wt;
             m2 += wt * th;
             m3 += wt * th * th;
         }
-        const double iq = 1.0 / q;
+        const double iq = cl_rcp(q);
         m1 *= iq;
         m2 *= iq;
         m3 *= iq;
@@ -76,7 +110,7 @@ __host__ __device__ inline void species_state(const GasDev& g, double T, Species
         double r = 0.0, xv = 0.0;
         if (g.linear[i]) {
             xv = g.theta_v[i] * invT;
-            r = 1.0 / expm1(xv);
+            r = cl_inv_expm1(xv);
             const double b = (1.0 + r) * r;                  // e^x / (e^x - 1)^2
             eo += T + g.theta_v[i] * r;
             cvo += 1.0 + xv * xv * b;
@@ -96,7 +130,7 @@ __host__ __device__ inline void species_state(const GasDev& g, double T, Species
 // First-order shift of a species state from T to T + dT (used after a Newton step of at most
 // 1e-8 T, where the neglected second-order terms are below 1e-16 relative).
 __host__ __device__ inline void species_shift(const GasDev& g, double T, double dT, SpeciesState& s) {
-    const double invT = 1.0 / T;
+    const double invT = cl_rcp(T);
 #pragma unroll
     for (int i = 0; i < NSP; ++i) {
         s.e[i] += s.cv[i] * dT;
@@ -138,7 +172,7 @@ __host__ __device__ inline double temperature_guess(const GasDev& g, double e, c
         const int mid = (lo + hi) / 2;
         if (emix(mid) <= e) lo = mid; else hi = mid;
     }
-    const double Ta = exp(g.etab_lnT0 + lo * g.etab_dlnT), Tb = exp(g.etab_lnT0 + hi * g.etab_dlnT);
+    const double Ta = cl_exp(g.etab_lnT0 + lo * g.etab_dlnT), Tb = cl_exp(g.etab_lnT0 + hi * g.etab_dlnT);
     const double ea = emix(lo), eb = emix(hi);
     double ca = 0.0, cb = 0.0;
 #pragma unroll
@@ -147,7 +181,7 @@ __host__ __device__ inline double temperature_guess(const GasDev& g, double e, c
         cb += Y[i] * g.etab_cv[i][hi];
     }
     const double h = Tb - Ta;
-    double t = (e - ea) / (eb - ea);                 // linear start
+    double t = cl_div(e - ea, eb - ea);              // linear start
     for (int it = 0; it < 3; ++it) {
         const double t2 = t * t, t3 = t2 * t;
         const double h00 = 2 * t3 - 3 * t2 + 1, h10 = t3 - 2 * t2 + t;
@@ -155,7 +189,7 @@ __host__ __device__ inline double temperature_guess(const GasDev& g, double e, c
         const double f = h00 * ea + h10 * h * ca + h01 * eb + h11 * h * cb - e;
         const double df = (6 * t2 - 6 * t) * ea + (3 * t2 - 4 * t + 1) * h * ca +
                           (-6 * t2 + 6 * t) * eb + (3 * t2 - 2 * t) * h * cb;
-        if (df > 0.0) t -= f / df;
+        if (df > 0.0) t -= cl_div(f, df);
         t = fmin(fmax(t, 0.0), 1.0);
     }
     return Ta + t * h;
@@ -176,7 +210,7 @@ __host__ __device__ inline double temperature_from_energy(const GasDev& g, doubl
             cv += Y[i] * s.cv[i];
         }
         if (f > 0.0) hi = T; else lo = T;
-        double Tn = T - f / cv;
+        double Tn = T - cl_div(f, cv);
         if (fabs(Tn - T) <= NEWTON_RTOL * T) {
             species_shift(g, T, Tn - T, s);
             return Tn;
@@ -291,7 +325,7 @@ __host__ __device__ inline void transport_f64(const GasDev& g, double T, double 
     double mu_s[NSP], a[NSP], b[NSP], k_s[NSP];
 #pragma unroll
     for (int i = 0; i < NSP; ++i) {
-        mu_s[i] = 0.1 * exp((g.blA[i] * lnT + g.blB[i]) * lnT + g.blC[i]);
+        mu_s[i] = 0.1 * cl_exp((g.blA[i] * lnT + g.blB[i]) * lnT + g.blC[i]);
         const double rs = rsqrt(mu_s[i]);           // 1 / sqrt(mu_i): one FP64 sequence for both
         a[i] = mu_s[i] * rs * g.iMq[i];
         b[i] = g.Mq[i] * rs;
@@ -309,7 +343,7 @@ __host__ __device__ inline void transport_f64(const GasDev& g, double T, double 
             const double t = 1.0 + a[i] * b[r];
             phi += o.X[r] * t * t * g.wilke_d[i][r];
         }
-        const double w = o.X[i] / phi;
+        const double w = cl_div(o.X[i], phi);
         mu += w * mu_s[i];
         kk += w * k_s[i];
     }
@@ -323,15 +357,15 @@ __host__ __device__ inline void transport_f64(const GasDev& g, double T, double 
         double den[NSP];
 #pragma unroll
         for (int i = 0; i < NSP; ++i) den[i] = 0.0;
-        const double TmB = exp(-NJA_B * lnT);               // T^-B, shared by every well depth
+        const double TmB = cl_exp(-NJA_B * lnT);            // T^-B, shared by every well depth
         const double rT = rsqrt(T);
         const double c = p * (rT * (rT * rT));              // 1/D_sr = c Omega dinv_sr
         for (int q = 0; q < g.neps; ++q) {
             const double ts = T * g.eps_inv[q];
             double om = NJA_A * TmB * g.eps_powB[q];
-            if (NJA_D * ts < OMEGA_CUT) om += NJA_C * exp(-NJA_D * ts);
-            if (NJA_F * ts < OMEGA_CUT) om += NJA_E * exp(-NJA_F * ts);
-            if (NJA_H * ts < OMEGA_CUT) om += NJA_G * exp(-NJA_H * ts);
+            if (NJA_D * ts < OMEGA_CUT) om += NJA_C * cl_exp(-NJA_D * ts);
+            if (NJA_F * ts < OMEGA_CUT) om += NJA_E * cl_exp(-NJA_F * ts);
+            if (NJA_H * ts < OMEGA_CUT) om += NJA_G * cl_exp(-NJA_H * ts);
             const double com = c * om;
             for (int pr = g.pstart[q]; pr < g.pstart[q + 1]; ++pr) {
                 const int i = g.pair_i[pr], r = g.pair_r[pr];
@@ -342,7 +376,7 @@ __host__ __device__ inline void transport_f64(const GasDev& g, double T, double 
         }
 #pragma unroll
         for (int i = 0; i < NSP; ++i) {
-            o.D[i] = den[i] != 0.0 ? (1.0 - o.X[i]) / den[i] : 0.0;
+            o.D[i] = den[i] != 0.0 ? cl_div(1.0 - o.X[i], den[i]) : 0.0;
             if (HAS_CHARGE) o.D[i] *= g.dfac[i];   // ambipolar ions, no electron coefficient
         }
     }
@@ -366,12 +400,12 @@ __host__ __device__ inline void closure_si_p(const GasDev& g, double rho, double
     }
     const double Rmix = R_U * ym;
     const double p = rho * Rmix * T;
-    const double iym = 1.0 / ym;
+    const double iym = cl_rcp(ym);
     o.T = T;
     o.p = p;
     o.cv = cv;
     o.Rmix = Rmix;
-    o.a = sqrt((cv + Rmix) * p / (cv * rho));
+    o.a = sqrt(cl_div((cv + Rmix) * p, cv * rho));
 #pragma unroll
     for (int i = 0; i < NSP; ++i) {
         o.h[i] = s.e[i] + g.Rs[i] * T;
@@ -381,7 +415,7 @@ __host__ __device__ inline void closure_si_p(const GasDev& g, double rho, double
         o.cvps[i] = s.cvp[i];
     }
     const double lnT = log(T);
-    const double invT = 1.0 / T;
+    const double invT = cl_rcp(T);
 
     // ---- kinetics (Eqs. 14, 15) ----
     // K_c = exp(-sum_s nu_s G_s/(R T)) (p_std/(R T))^dnu with G_s/(R T) = E0_s/(R T) - ln q_s, so
@@ -425,8 +459,8 @@ __host__ __device__ inline void closure_si_p(const GasDev& g, double rho, double
             if (MIXED) Ef = f64_of(expf(f32_of(base - g.g_Ta[k] * invT)));
             else
 #endif
-                Ef = exp(base - g.g_Ta[k] * invT);
-            const double Eb = exp(base - (g.g_Ta[k] - g.g_theta_d[k]) * invT) * den / num;
+                Ef = cl_exp(base - g.g_Ta[k] * invT);
+            const double Eb = cl_exp(base - (g.g_Ta[k] - g.g_theta_d[k]) * invT) * cl_div(den, num);
             const double Rg = w * (Ef * fwd - Eb * bwd);
 #pragma unroll
             for (int i = 0; i < NSP; ++i) molar[i] += g.g_nud[k][i] * Rg;
@@ -519,14 +553,14 @@ __device__ inline void stefan_maxwell_face(const GasDev& g, double Tsi, double p
         b[r] = r == 0 ? 0.0 : rho * ym * dX[r];
     }
     const double lnT = log(Tsi);
-    const double TmB = exp(-NJA_B * lnT);
+    const double TmB = cl_exp(-NJA_B * lnT);
     const double cc = psi / (Tsi * sqrt(Tsi)) * dscale;
     for (int q = 0; q < g.neps; ++q) {
         const double ts = Tsi * g.eps_inv[q];
         double om = NJA_A * TmB * g.eps_powB[q];
-        if (NJA_D * ts < OMEGA_CUT) om += NJA_C * exp(-NJA_D * ts);
-        if (NJA_F * ts < OMEGA_CUT) om += NJA_E * exp(-NJA_F * ts);
-        if (NJA_H * ts < OMEGA_CUT) om += NJA_G * exp(-NJA_H * ts);
+        if (NJA_D * ts < OMEGA_CUT) om += NJA_C * cl_exp(-NJA_D * ts);
+        if (NJA_F * ts < OMEGA_CUT) om += NJA_E * cl_exp(-NJA_F * ts);
+        if (NJA_H * ts < OMEGA_CUT) om += NJA_G * cl_exp(-NJA_H * ts);
         for (int pr = g.pstart[q]; pr < g.pstart[q + 1]; ++pr) {
             const int i = g.pair_i[pr], r = g.pair_r[pr];
             const double w = cc * om * g.pair_dinv[pr];          // nondimensional 1 / D_ir
@@ -634,7 +668,7 @@ __host__ __device__ inline bool lte_solve(const GasDev& g, const double* gam, co
 #pragma unroll
         for (int i = 0; i < NSP; ++i) {
             const double a0 = g.atoms[i][0], a1 = g.atoms[i][1];
-            const double ci = exp(a0 * lam[0] + a1 * lam[1] - gam[i]);
+            const double ci = cl_exp(a0 * lam[0] + a1 * lam[1] - gam[i]);
             S0 += a0 * ci;
             S1 += a1 * ci;
             J00 += a0 * a0 * ci;
@@ -654,12 +688,12 @@ __host__ __device__ inline bool lte_solve(const GasDev& g, const double* gam, co
         if (fmax(fabs(d0), fabs(d1)) <= EQ_TOL) {
 #pragma unroll
             for (int i = 0; i < NSP; ++i)
-                c[i] = exp(g.atoms[i][0] * lam[0] + g.atoms[i][1] * lam[1] - gam[i]);
+                c[i] = cl_exp(g.atoms[i][0] * lam[0] + g.atoms[i][1] * lam[1] - gam[i]);
             return true;
         }
     }
 #pragma unroll
-    for (int i = 0; i < NSP; ++i) c[i] = exp(g.atoms[i][0] * lam[0] + g.atoms[i][1] * lam[1] - gam[i]);
+    for (int i = 0; i < NSP; ++i) c[i] = cl_exp(g.atoms[i][0] * lam[0] + g.atoms[i][1] * lam[1] - gam[i]);
     return false;
 }
 
