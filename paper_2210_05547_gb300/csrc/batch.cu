@@ -68,7 +68,8 @@ __device__ __forceinline__ void for_tiles(const BatchItem* __restrict__ items, c
 // shared memory when it moves to a tile of another member, and the body reads the field
 // pointers from there (no aliasing with the global stores, no registers held across the point).
 template <bool MIXED, bool LTE>
-__global__ void __launch_bounds__(128, 3) kb_closure(GasDev g, const BatchItem* __restrict__ items,
+__global__ void __launch_bounds__(128, CLOSURE_MIN_BLOCKS) kb_closure(const __grid_constant__ GasDev g,
+                                                     const BatchItem* __restrict__ items,
                                                   BatchDev B) {
     __shared__ BatchItem sh;
     const int* __restrict__ ts = B.tstart[SP_NC];

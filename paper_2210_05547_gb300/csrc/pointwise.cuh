@@ -14,26 +14,51 @@ __device__ __forceinline__ void atomic_status(unsigned* st, unsigned bits) {
     if (bits) atomicOr(st, bits);
 }
 
-// (A) primitives and the closure at every cell centre (MIXED: binary32 transport, Sec. 2.2).
+// Resident blocks of 128 threads per SM the closure kernels are compiled for: three (164-168
+// registers; left to itself ptxas picks 128 registers and spills more for five-species air; for
+// eleven-species air the cap of 168 spills, yet measured faster than two blocks at 255 registers:
+// 74.3 against 67.4 Mpts*RHS/s).
+#define CLOSURE_MIN_BLOCKS 3
+
+// Reciprocals of the freestream scales, computed once per thread by the caller of closure_point
+// (the point loop multiplies by them).
+struct ScaleInv {
+    double iT_ref, imu_inf, ik_inf, ia_inf, iRe, iRePr, ip_ref, ia2, d_nd, wscale;
+};
+
+__device__ __forceinline__ ScaleInv scale_inv(const Scales& sc) {
+    ScaleInv c;
+    c.iT_ref = 1.0 / sc.T_ref;
+    c.imu_inf = 1.0 / sc.mu_inf;
+    c.ik_inf = 1.0 / sc.k_inf;
+    c.ia_inf = 1.0 / sc.a_inf;
+    c.iRe = 1.0 / sc.Re;
+    c.iRePr = 1.0 / (sc.Re * sc.Pr);
+    c.ip_ref = __ddiv_rn(__dmul_rn(c.ia_inf, c.ia_inf), sc.rho_inf);
+    c.ia2 = __dmul_rn(c.ia_inf, c.ia_inf);
+    c.d_nd = __dmul_rn(__dmul_rn(sc.rho_inf, c.imu_inf), c.iRe);   // D (SI) -> rho_inf D / (mu_inf Re)
+    c.wscale = __ddiv_rn(__dmul_rn(sc.L_ref, c.ia_inf), sc.rho_inf);   // w (SI) -> nondimensional
+    return c;
+}
+
+// (A) primitives and the closure at one cell centre (MIXED: binary32 transport, Sec. 2.2).
 // LTE: the gas is in local thermodynamic equilibrium (its own instantiation, so that the other
 // kinds' code keeps its registers); the species fields are passive and the closure ignores them.
-template <bool MIXED, bool LTE = false>
-__device__ __forceinline__ void closure_body(const GasDev& g, const Scales& sc, const GridView& v,
-                                             const double* __restrict__ U, const Scratch& s,
-                                             long long lo, long long hi, long long stride) {
+// The point is a function of its own, not inlined: the single-grid kernel and the batched
+// executor call this one compiled body, so a member's results do not depend on which of the
+// two ran it (inlined into two different kernels, the compiler's fusion of multiplies and adds
+// may differ between the copies by a rounding).
+template <bool MIXED, bool LTE>
+__device__ __noinline__ void closure_point(const GasDev& g, const Scales& sc, const ScaleInv& c,
+                                           const GridView& v, const double* __restrict__ U,
+                                           const Scratch& s, int idx) {
     const bool cpg = sc.kind == HYP_GAS_CPG;
     const bool tpg = sc.kind == HYP_GAS_TPG;
     const bool cneq = sc.kind == HYP_GAS_CNEQ;
-    // reciprocals of the freestream scales, once per thread: the loop multiplies by them, with
-    // __dmul_rn so that no product is fused into a later addition (the single-grid and batched
-    // kernels inline this body into different code and must round identically)
-    const double iT_ref = 1.0 / sc.T_ref, imu_inf = 1.0 / sc.mu_inf, ik_inf = 1.0 / sc.k_inf;
-    const double ia_inf = 1.0 / sc.a_inf, iRe = 1.0 / sc.Re, iRePr = 1.0 / (sc.Re * sc.Pr);
-    const double ip_ref = ia_inf * ia_inf / sc.rho_inf, ia2 = ia_inf * ia_inf;
-    const double d_nd = sc.rho_inf * imu_inf * iRe;     // D (SI) -> rho_inf D / (mu_inf Re)
-    const double wscale = sc.L_ref * ia_inf / sc.rho_inf;   // w (SI) -> nondimensional
-    for (long long li = lo + threadIdx.x; li < hi; li += stride) {
-        const int idx = (int)li;
+    const double iT_ref = c.iT_ref, imu_inf = c.imu_inf, ik_inf = c.ik_inf, ia_inf = c.ia_inf;
+    const double iRe = c.iRe, iRePr = c.iRePr, ip_ref = c.ip_ref, ia2 = c.ia2, d_nd = c.d_nd;
+    const double wscale = c.wscale;
+    {
         const double rho = U[v.off[0] + idx];
         const double irho = cl_rcp(rho);
         double Y[NSP];
@@ -176,6 +201,16 @@ __device__ __forceinline__ void closure_body(const GasDev& g, const Scales& sc, 
 #pragma unroll
         for (int sp = 1; sp < NSP; ++sp) s.SRC[v.off[sp] + idx] = wd[sp];
     }
+}
+
+// (A) over an index range of one grid
+template <bool MIXED, bool LTE = false>
+__device__ __forceinline__ void closure_body(const GasDev& g, const Scales& sc, const GridView& v,
+                                             const double* __restrict__ U, const Scratch& s,
+                                             long long lo, long long hi, long long stride) {
+    const ScaleInv c = scale_inv(sc);
+    for (long long li = lo + threadIdx.x; li < hi; li += stride)
+        closure_point<MIXED, LTE>(g, sc, c, v, U, s, (int)li);
 }
 
 // (B) face velocities and the face products of the normal momentum fluxes;

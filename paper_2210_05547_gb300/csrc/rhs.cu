@@ -394,10 +394,23 @@ enum OpId { OX_ICF, OX_DCF, OX_IFC, OX_DFC, OY_ICF, OY_DCF, OY_IFC, OY_DFC, OY_I
 // Single-grid kernels: grid-stride loops over the bodies of pointwise.cuh.
 #define GRID_RANGE(n) (long long)blockIdx.x * blockDim.x, (long long)(n), (long long)gridDim.x * blockDim.x
 
+// The scales, grid view and scratch pointers are copied to shared memory first, as the batched
+// executor's kernel holds them, so that both pass the shared closure_point the same kinds of
+// pointers.
 template <bool MIXED, bool LTE>
-__global__ void __launch_bounds__(128, 3) k_closure(GasDev g, Scales sc, GridView v,
-                                                 const double* __restrict__ U, Scratch s) {
-    closure_body<MIXED, LTE>(g, sc, v, U, s, GRID_RANGE((long long)v.nx * v.ny));
+__global__ void __launch_bounds__(128, CLOSURE_MIN_BLOCKS) k_closure(const __grid_constant__ GasDev g,
+                                                    const Scales sc, const GridView v,
+                                                    const double* __restrict__ U, const Scratch s) {
+    __shared__ Scales sh_sc;
+    __shared__ GridView sh_v;
+    __shared__ Scratch sh_s;
+    if (threadIdx.x == 0) {
+        sh_sc = sc;
+        sh_v = v;
+        sh_s = s;
+    }
+    __syncthreads();
+    closure_body<MIXED, LTE>(g, sh_sc, sh_v, U, sh_s, GRID_RANGE((long long)v.nx * v.ny));
 }
 
 // the closure kernel for the gas kind and precision

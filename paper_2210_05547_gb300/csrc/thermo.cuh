@@ -38,7 +38,7 @@ constexpr double NJA_E = 1.03587, NJA_F = 1.52996, NJA_G = 1.76474, NJA_H = 3.89
 // Binary64 exponential, quotient and reciprocal of the closure: on the device the forms of
 // fp64_fast.cuh (Tang's table-driven exp, Newton-refined binary32 reciprocals; within 2 ulp, on
 // about half the FP64-pipe instructions of CUDA's), on the host the C library.
-__host__ __device__ inline double cl_exp(double x) {
+__host__ __device__ __forceinline__ double cl_exp(double x) {
 #ifdef __CUDA_ARCH__
     return tang_exp(x);
 #else
@@ -46,7 +46,7 @@ __host__ __device__ inline double cl_exp(double x) {
 #endif
 }
 
-__host__ __device__ inline double cl_div(double a, double b) {
+__host__ __device__ __forceinline__ double cl_div(double a, double b) {
 #ifdef __CUDA_ARCH__
     return fast_div(a, b);
 #else
@@ -54,7 +54,7 @@ __host__ __device__ inline double cl_div(double a, double b) {
 #endif
 }
 
-__host__ __device__ inline double cl_rcp(double b) {
+__host__ __device__ __forceinline__ double cl_rcp(double b) {
 #ifdef __CUDA_ARCH__
     return fast_rcp(b);
 #else
@@ -64,7 +64,7 @@ __host__ __device__ inline double cl_rcp(double b) {
 
 // 1 / (e^x - 1) for x > 0: from the exponential where e^x - 1 loses at most a bit (x >= 1),
 // from expm1 below.
-__host__ __device__ inline double cl_inv_expm1(double x) {
+__host__ __device__ __forceinline__ double cl_inv_expm1(double x) {
     return x >= 1.0 ? cl_rcp(cl_exp(x) - 1.0) : 1.0 / expm1(x);
 }
 
@@ -81,7 +81,7 @@ struct SpeciesState {
     double xv[NSP];     // theta_v / T
 };
 
-__host__ __device__ inline void species_state(const GasDev& g, double T, SpeciesState& s) {
+__host__ __device__ __forceinline__ void species_state(const GasDev& g, double T, SpeciesState& s) {
     const double invT = cl_rcp(T);
     const double invT2 = invT * invT;
 #pragma unroll
@@ -129,7 +129,7 @@ __host__ __device__ inline void species_state(const GasDev& g, double T, Species
 
 // First-order shift of a species state from T to T + dT (used after a Newton step of at most
 // 1e-8 T, where the neglected second-order terms are below 1e-16 relative).
-__host__ __device__ inline void species_shift(const GasDev& g, double T, double dT, SpeciesState& s) {
+__host__ __device__ __forceinline__ void species_shift(const GasDev& g, double T, double dT, SpeciesState& s) {
     const double invT = cl_rcp(T);
 #pragma unroll
     for (int i = 0; i < NSP; ++i) {
@@ -144,7 +144,7 @@ __host__ __device__ inline void species_shift(const GasDev& g, double T, double 
     }
 }
 
-__host__ __device__ inline double mixture_energy(const GasDev& g, double T, const double* Y) {
+__host__ __device__ __forceinline__ double mixture_energy(const GasDev& g, double T, const double* Y) {
     SpeciesState s;
     species_state(g, T, s);
     double e = 0.0;
@@ -158,7 +158,7 @@ __host__ __device__ inline double mixture_energy(const GasDev& g, double T, cons
 // Hermite model of e(T) on it (values and heat capacities at its ends) inverted by three Newton
 // steps. Only the starting point of the safeguarded Newton iteration below: the temperature it
 // returns does not depend on it beyond the iteration's tolerance.
-__host__ __device__ inline double temperature_guess(const GasDev& g, double e, const double* Y) {
+__host__ __device__ __forceinline__ double temperature_guess(const GasDev& g, double e, const double* Y) {
     auto emix = [&](int k) {
         double s = 0.0;
 #pragma unroll
@@ -196,7 +196,7 @@ __host__ __device__ inline double temperature_guess(const GasDev& g, double e, c
 }
 
 // Safeguarded Newton for sum_s Y_s e_s(T) = e; s holds the species state at the returned T.
-__host__ __device__ inline double temperature_from_energy(const GasDev& g, double e,
+__host__ __device__ __forceinline__ double temperature_from_energy(const GasDev& g, double e,
                                                           const double* Y, double T0,
                                                           unsigned& status, SpeciesState& s) {
     double T = fmin(fmax(T0, T_LO), T_HI);
@@ -252,19 +252,22 @@ struct ClosureOut {
 // Transport and diffusion in binary32 for the mixed-precision closure (HYP_MIXED): the same
 // Blottner, Eucken, Wilke and Chapman-Enskog formulas as the FP64 code in closure_si, on binary32
 // copies of the constants. Inputs and outputs cross with the integer conversions of fp32.cuh.
-__device__ inline void transport_f32(const GasDev& g, double T, double lnT, double p,
+__device__ __forceinline__ void transport_f32(const GasDev& g, double T, double lnT, double p,
                                      const SpeciesState& s, bool diffusion, ClosureOut& o) {
+    // every binary32 multiply and add is explicit (fmaf where a fused operation is meant,
+    // __fmul_rn / __fadd_rn / __fdiv_rn elsewhere): no contraction is left to the compiler, so
+    // the result does not depend on the kernel this body is compiled into
     const float lnTf = f32_of(lnT);
     float Xf[NSP], mu_s[NSP], a[NSP], b[NSP], k_s[NSP];
 #pragma unroll
     for (int i = 0; i < NSP; ++i) {
         Xf[i] = f32_of(o.X[i]);
-        mu_s[i] = 0.1f * expf((g.f_blA[i] * lnTf + g.f_blB[i]) * lnTf + g.f_blC[i]);
+        mu_s[i] = __fmul_rn(0.1f, expf(fmaf(fmaf(g.f_blA[i], lnTf, g.f_blB[i]), lnTf, g.f_blC[i])));
         const float ir = rsqrtf(mu_s[i]);
-        a[i] = mu_s[i] * ir * g.f_iMq[i];
-        b[i] = g.f_Mq[i] * ir;
-        const float cv_tr = 1.5f * g.f_Rs[i];
-        k_s[i] = mu_s[i] * (2.5f * cv_tr + (f32_of(s.cv[i]) - cv_tr));
+        a[i] = __fmul_rn(__fmul_rn(mu_s[i], ir), g.f_iMq[i]);
+        b[i] = __fmul_rn(g.f_Mq[i], ir);
+        const float cv_tr = __fmul_rn(1.5f, g.f_Rs[i]);
+        k_s[i] = __fmul_rn(mu_s[i], fmaf(2.5f, cv_tr, __fsub_rn(f32_of(s.cv[i]), cv_tr)));
     }
     float mu = 0.0f, kk = 0.0f;
 #pragma unroll
@@ -274,12 +277,12 @@ __device__ inline void transport_f32(const GasDev& g, double T, double lnT, doub
 #pragma unroll
         for (int r = 0; r < NSP; ++r) {
             if (HAS_CHARGE && !g.heavy[r]) continue;
-            const float t = 1.0f + a[i] * b[r];
-            phi += Xf[r] * t * t * g.f_wilke_d[i][r];
+            const float t = fmaf(a[i], b[r], 1.0f);
+            phi = fmaf(__fmul_rn(__fmul_rn(Xf[r], t), t), g.f_wilke_d[i][r], phi);
         }
-        const float w = Xf[i] / phi;
-        mu += w * mu_s[i];
-        kk += w * k_s[i];
+        const float w = __fdiv_rn(Xf[i], phi);
+        mu = fmaf(w, mu_s[i], mu);
+        kk = fmaf(w, k_s[i], kk);
     }
     o.mu = f64_of(mu);
     o.k = f64_of(kk);
@@ -290,33 +293,35 @@ __device__ inline void transport_f32(const GasDev& g, double T, double lnT, doub
 #pragma unroll
     for (int i = 0; i < NSP; ++i) den[i] = 0.0f;
     const float Tf = f32_of(T);
-    const float TmB = expf(-(float)NJA_B * lnTf);
-    const float c = f32_of(p) / (Tf * sqrtf(Tf));
+    const float TmB = expf(__fmul_rn(-(float)NJA_B, lnTf));
+    const float c = __fdiv_rn(f32_of(p), __fmul_rn(Tf, sqrtf(Tf)));
     for (int q = 0; q < g.neps; ++q) {
-        const float ts = Tf * g.f_eps_inv[q];
-        float om = (float)NJA_A * TmB * g.f_eps_powB[q];
-        if ((float)NJA_D * ts < (float)OMEGA_CUT) om += (float)NJA_C * expf(-(float)NJA_D * ts);
-        if ((float)NJA_F * ts < (float)OMEGA_CUT) om += (float)NJA_E * expf(-(float)NJA_F * ts);
-        if ((float)NJA_H * ts < (float)OMEGA_CUT) om += (float)NJA_G * expf(-(float)NJA_H * ts);
-        const float com = c * om;
+        const float ts = __fmul_rn(Tf, g.f_eps_inv[q]);
+        float om = __fmul_rn(__fmul_rn((float)NJA_A, TmB), g.f_eps_powB[q]);
+        const float xd = __fmul_rn((float)NJA_D, ts), xf = __fmul_rn((float)NJA_F, ts);
+        const float xh = __fmul_rn((float)NJA_H, ts);
+        if (xd < (float)OMEGA_CUT) om = fmaf((float)NJA_C, expf(-xd), om);
+        if (xf < (float)OMEGA_CUT) om = fmaf((float)NJA_E, expf(-xf), om);
+        if (xh < (float)OMEGA_CUT) om = fmaf((float)NJA_G, expf(-xh), om);
+        const float com = __fmul_rn(c, om);
         for (int pr = g.pstart[q]; pr < g.pstart[q + 1]; ++pr) {
             const int i = g.pair_i[pr], r = g.pair_r[pr];
-            const float inv_d = com * g.f_pair_dinv[pr];
-            den[i] += Xf[r] * inv_d;
-            den[r] += Xf[i] * inv_d;
+            const float inv_d = __fmul_rn(com, g.f_pair_dinv[pr]);
+            den[i] = fmaf(Xf[r], inv_d, den[i]);
+            den[r] = fmaf(Xf[i], inv_d, den[r]);
         }
     }
 #pragma unroll
     for (int i = 0; i < NSP; ++i) {
-        o.D[i] = den[i] != 0.0f ? f64_of((1.0f - Xf[i]) / den[i]) : 0.0;
-        if (HAS_CHARGE) o.D[i] *= g.dfac[i];       // ambipolar ions, no electron coefficient
+        o.D[i] = den[i] != 0.0f ? f64_of(__fdiv_rn(__fsub_rn(1.0f, Xf[i]), den[i])) : 0.0;
+        if (HAS_CHARGE) o.D[i] = __dmul_rn(o.D[i], g.dfac[i]);   // ambipolar ions, no electron coefficient
     }
 }
 #endif
 
 // Transport and diffusion in FP64: Blottner species viscosities, Eucken conductivities, Wilke's
 // mixing rule and the averaged diffusion coefficients of Eq. (19).
-__host__ __device__ inline void transport_f64(const GasDev& g, double T, double lnT, double p,
+__host__ __device__ __forceinline__ void transport_f64(const GasDev& g, double T, double lnT, double p,
                                               const SpeciesState& s, bool diffusion,
                                               ClosureOut& o) {
     // ---- transport: Blottner, Eucken, Wilke ----
@@ -386,7 +391,7 @@ __host__ __device__ inline void transport_f64(const GasDev& g, double T, double 
 // forward rate exponentials, transport and diffusion in binary32; temperature inversion, species
 // thermodynamics, equilibrium constants and backward rates stay FP64.
 template <bool MIXED>
-__host__ __device__ inline void closure_si_p(const GasDev& g, double rho, double e,
+__host__ __device__ __forceinline__ void closure_si_p(const GasDev& g, double rho, double e,
                                              const double* Y, double T0, bool reactions,
                                              bool diffusion, ClosureOut& o) {
     SpeciesState s;
@@ -478,7 +483,7 @@ __host__ __device__ inline void closure_si_p(const GasDev& g, double rho, double
     }
 }
 
-__host__ __device__ inline void closure_si(const GasDev& g, double rho, double e, const double* Y,
+__host__ __device__ __forceinline__ void closure_si(const GasDev& g, double rho, double e, const double* Y,
                                            double T0, bool reactions, bool diffusion,
                                            ClosureOut& o) {
     closure_si_p<false>(g, rho, e, Y, T0, reactions, diffusion, o);
@@ -491,12 +496,12 @@ __host__ __device__ inline void closure_si(const GasDev& g, double rho, double e
 constexpr double TPG_THETA = 3055.0;   // K (Eq. 23)
 constexpr double KEYES_C2 = 2.646e-3, KEYES_C3 = 245.4, KEYES_C4 = 12.0;   // Eq. (25), SI
 
-__host__ __device__ inline double tpg_shape(double x) {
+__host__ __device__ __forceinline__ double tpg_shape(double x) {
     const double d = -expm1(-x);
     return x * x * exp(-x) / (d * d);
 }
 
-__host__ __device__ inline double keyes(double T) {
+__host__ __device__ __forceinline__ double keyes(double T) {
     return KEYES_C2 * sqrt(T) / (1.0 + (KEYES_C3 / T) * exp(-KEYES_C4 * 2.302585092994045684 / T));
 }
 
@@ -533,7 +538,7 @@ struct TpgModel {
 // pressure for the binary coefficients (Chapman-Enskog, the collision-integral fit of the
 // closure); dscale converts 1/D_si (SI) to the nondimensional 1/(D_si rho_inf / (mu_inf Re)).
 // rho, dX and the returned J are nondimensional.
-__device__ inline void stefan_maxwell_face(const GasDev& g, double Tsi, double psi, double dscale,
+__device__ __forceinline__ void stefan_maxwell_face(const GasDev& g, double Tsi, double psi, double dscale,
                                            double rho, const double* Yf, const double* dX,
                                            double* J) {
     double inv[NSP], X[NSP], ym = 0.0;
@@ -635,7 +640,7 @@ constexpr int EQ_MAXIT = 100;
 constexpr double EQ_TOL = 1.0e-11;        // element-potential step that ends the iteration
 constexpr double EQ_MAX_STEP = 25.0;      // largest change of an element potential in one step
 
-__host__ __device__ inline void lte_gammas(const GasDev& g, double T, double lnT,
+__host__ __device__ __forceinline__ void lte_gammas(const GasDev& g, double T, double lnT,
                                            const SpeciesState& s, double* gam) {
     const double invT = 1.0 / T;
 #pragma unroll
@@ -649,7 +654,7 @@ __host__ __device__ inline void lte_gammas(const GasDev& g, double T, double lnT
 // Element potentials for element totals b (mol/m^3, lnb = ln b). warm: start from lam; else from
 // the smallest value at which one species made of that element alone would hold all of it (an
 // upper bound of the solution). c receives the concentrations at the returned lam.
-__host__ __device__ inline bool lte_solve(const GasDev& g, const double* gam, const double* b,
+__host__ __device__ __forceinline__ bool lte_solve(const GasDev& g, const double* gam, const double* b,
                                           const double* lnb, bool warm, double* lam, double* c) {
     if (!warm) {
 #pragma unroll
@@ -711,7 +716,7 @@ struct LteState {
     bool ok;
 };
 
-__host__ __device__ inline void lte_at(const GasDev& g, double T, double rho, const double* b,
+__host__ __device__ __forceinline__ void lte_at(const GasDev& g, double T, double rho, const double* b,
                                        const double* lnb, bool warm, LteState& q) {
     species_state(g, T, q.s);
     const double lnT = log(T);
@@ -764,7 +769,7 @@ __host__ __device__ inline void lte_at(const GasDev& g, double T, double rho, co
 // they are finite (otherwise from the bound above); on return the potentials at the result.
 // cv_eq (nullable) receives de/dT along the equilibrium at fixed density at the result.
 template <bool MIXED>
-__host__ __device__ inline void lte_closure(const GasDev& g, double rho, double e, double T0,
+__host__ __device__ __forceinline__ void lte_closure(const GasDev& g, double rho, double e, double T0,
                                             double* Yout, double& k_reactive, ClosureOut& o,
                                             double* lam = nullptr, double* cv_eq = nullptr) {
     o.status = rho > 0.0 ? 0u : HYP_STATUS_NONPHYSICAL;

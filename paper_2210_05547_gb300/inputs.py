@@ -108,10 +108,14 @@ def box_case(nx=32, ny=24, seed=0, kind="cneq"):
 
 def serving_requests(n, seed=0, steps=(500, 2000), air11=0.0):
     """n requests: (case dictionary, step count, unit-rate inter-arrival gap). Shock interactions
-    take at least 64 rows: on 32 rows (cells up to 3 high where the shock of width 1 crosses them)
-    the solve loses positivity in its first step, in the oracle as in the CUDA path. A share
-    `air11` of the requests runs on eleven-species air (drawn from a stream of its own, so the
-    requests themselves do not depend on the share)."""
+    take at least 128 rows and a time step of 5e-4 (a quarter of the full-size case's): on 32 rows
+    (cells up to 3 high where the shock of width 1 crosses them) the solve loses positivity in its
+    first step, in the oracle as in the CUDA path, and over the 500-2000 steps of the serving
+    stream the interactions on 64 rows and coarse x spacing (nx <= 512) turn non-physical within
+    100-1100 steps at any time step tried, while every one on 128 or 256 rows (five and eleven
+    species, nx 128-1024) stays clean at 5e-4. A share `air11` of the requests runs on
+    eleven-species air (drawn from a stream of its own, so the requests themselves do not depend
+    on the share)."""
     rng = np.random.default_rng(np.random.SeedSequence([seed, 0x5e7e]))
     pick = np.random.default_rng(np.random.SeedSequence([seed, 0x11a1]))
     nxs, nys = (128, 256, 512, 1024), (32, 64, 128, 256)
@@ -124,7 +128,8 @@ def serving_requests(n, seed=0, steps=(500, 2000), air11=0.0):
             c.update(mach=mach, T_wall=float(rng.uniform(300.0, 1500.0)),
                      dt=2.0e-4 * min(1.0, 10.0 / mach))
         else:
-            c = sbli_case(nx, max(ny, 64), seed=int(rng.integers(1 << 30)))
+            c = sbli_case(nx, max(ny, 128), seed=int(rng.integers(1 << 30)))
+            c["dt"] = 5.0e-4
         if pick.random() < air11:
             c = with_species(c, "air11")
         c["name"] = f"req{k}_{c['name']}"

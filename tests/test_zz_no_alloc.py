@@ -14,7 +14,9 @@ from paper_2210_05547_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("cfg", [I.bl_case(48, 32), I.sbli_case(64, 40, seed=1)],
+# (the 64 x 40 shock case of seed 1 is not used here: at that resolution a dozen cells of its
+# initial state have internal energies below e(50 K), which the oracle and the library both flag)
+@pytest.mark.parametrize("cfg", [I.bl_case(48, 32), I.sbli_case(64, 40, seed=3)],
                          ids=["bl_48x32", "sbli_64x40"])
 def test_noalloc_matches_rhs_twice(table, cfg):
     import torch
