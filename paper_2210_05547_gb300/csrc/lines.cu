@@ -41,6 +41,9 @@ namespace hyp {
 namespace {
 
 constexpr int PF = 8;   // prefetch distance (rows) of the constant-factor loops
+// the same for the double-word rows (16 or 24 rows were measured slower: the registers cost more
+// resident warps than the earlier loads gain)
+constexpr int PF_DW = 8;
 
 __device__ __forceinline__ double closure_rhs(const LineOp& op, const double* __restrict__ in,
                                               long long ies, int r, double wall) {
@@ -204,15 +207,15 @@ __device__ __forceinline__ void fwd_rows_constdw(int r, int r1, double& d, Windo
     const dword wa{op.wac_f, op.wac_l}, wb{op.wbc_f, op.wbc_l}, lm{op.lmc_f, op.lmc_l};
     const double* __restrict__ pp = p;
     dword dd = dw_of(d), p0 = dw_of(w.p0), p1 = dw_of(w.p1), p2 = dw_of(w.p2);
-    double q[PF];
+    double q[PF_DW];
 #pragma unroll
-    for (int k = 0; k < PF; ++k) q[k] = k < n ? pp[(long long)k * ies] : 0.0;
-    for (; r + PF - 1 <= r1; r += PF) {
+    for (int k = 0; k < PF_DW; ++k) q[k] = k < n ? pp[(long long)k * ies] : 0.0;
+    for (; r + PF_DW - 1 <= r1; r += PF_DW) {
 #pragma unroll
-        for (int k = 0; k < PF; ++k) {
+        for (int k = 0; k < PF_DW; ++k) {
             const double x3 = q[k];
             const dword p3 = dw_of(x3);
-            q[k] = r + PF + k <= r1 ? pp[(long long)(PF + k) * ies] : 0.0;
+            q[k] = r + PF_DW + k <= r1 ? pp[(long long)(PF_DW + k) * ies] : 0.0;
             dd = interior_row_dw<KIND>(dd, p0, p1, p2, p3, wa, wb, lm);
             if (STORE) dw_store(tmp + (long long)(r + k) * oes, dd);
             p0 = p1;
@@ -220,10 +223,10 @@ __device__ __forceinline__ void fwd_rows_constdw(int r, int r1, double& d, Windo
             p2 = p3;
             shift(w, x3);
         }
-        pp += PF * ies;
+        pp += PF_DW * ies;
     }
 #pragma unroll
-    for (int k = 0; k < PF - 1; ++k) {
+    for (int k = 0; k < PF_DW - 1; ++k) {
         if (r + k <= r1) {
             const double x3 = q[k];
             const dword p3 = dw_of(x3);
@@ -399,20 +402,20 @@ __device__ __forceinline__ void back_rows_constdw(int r0, int r1, double& y,
     const int n = r0 - r1 + 1;
     if (n <= 0) return;
     dword yd = dw_of(y);
-    dword q[PF];
-    double mq[PF];
+    dword q[PF_DW];
+    double mq[PF_DW];
 #pragma unroll
-    for (int k = 0; k < PF; ++k) {
+    for (int k = 0; k < PF_DW; ++k) {
         q[k] = k < n ? dw_load(tmp + (long long)(r0 - k) * oes) : dword{0.0f, 0.0f};
         mq[k] = (OM >= 3 && k < n) ? met[r0 - k] : 0.0;
     }
     int r = r0;
-    for (; r - PF + 1 >= r1; r -= PF) {
+    for (; r - PF_DW + 1 >= r1; r -= PF_DW) {
 #pragma unroll
-        for (int k = 0; k < PF; ++k) {
+        for (int k = 0; k < PF_DW; ++k) {
             const dword t = q[k];
             const double m = mq[k];
-            const int rn = r - PF - k;
+            const int rn = r - PF_DW - k;
             q[k] = rn >= r1 ? dw_load(tmp + (long long)rn * oes) : dword{0.0f, 0.0f};
             if (OM >= 3) mq[k] = rn >= r1 ? met[rn] : 0.0;
             yd = dw_sub(t, dw_mul(cc, yd));
@@ -420,7 +423,7 @@ __device__ __forceinline__ void back_rows_constdw(int r0, int r1, double& y,
         }
     }
 #pragma unroll
-    for (int k = 0; k < PF - 1; ++k) {
+    for (int k = 0; k < PF_DW - 1; ++k) {
         if (r - k >= r1) {
             yd = dw_sub(q[k], dw_mul(cc, yd));
             if (OM != 0) put<OM>(out, oes, r - k, dw_to_f64(yd), mq[k]);
@@ -506,8 +509,11 @@ __device__ __forceinline__ void run_line(const LineJob& J, const LineOp& op,
     }
 }
 
+// One instantiation per precision: the FP64 one carries only the binary64 sweeps (and keeps its
+// registers), the HYP_MIXED one the binary32 and double-word sweeps beside the binary64 rows.
+template <bool MIXED>
 __global__ void __launch_bounds__(LINE_BLOCK) k_lines(const LineJob* __restrict__ jobs,
-                                               const double* __restrict__ U, int mixed) {
+                                                                       const double* __restrict__ U) {
     const LineJob& J = jobs[blockIdx.y];
     const int nseg = J.nseg;
     const int lpb = blockDim.x / nseg;                  // lines per block
@@ -534,9 +540,12 @@ __global__ void __launch_bounds__(LINE_BLOCK) k_lines(const LineJob* __restrict_
     double* __restrict__ tmp = J.tmp + ooff;
     const double wall = (J.wall_arr && active) ? J.wall_arr[line] : J.wall_value;
     // uniform per block: every thread of a block works on the same job
-    if (mixed && J.f32ok) run_line<1>(J, op, in, out, tmp, s, e, m, W, active, wall);
-    else if (mixed) run_line<2>(J, op, in, out, tmp, s, e, m, W, active, wall);
-    else run_line<0>(J, op, in, out, tmp, s, e, m, W, active, wall);
+    if constexpr (MIXED) {
+        if (J.f32ok) run_line<1>(J, op, in, out, tmp, s, e, m, W, active, wall);
+        else run_line<2>(J, op, in, out, tmp, s, e, m, W, active, wall);
+    } else {
+        run_line<0>(J, op, in, out, tmp, s, e, m, W, active, wall);
+    }
 }
 
 }  // namespace
@@ -546,7 +555,8 @@ cudaError_t launch_lines(const LineJob* d_jobs, int njobs, int max_blocks, const
     if (njobs == 0) return cudaSuccess;
     dim3 block(LINE_BLOCK);
     dim3 grid(max_blocks, njobs);
-    k_lines<<<grid, block, 0, s>>>(d_jobs, U, mixed);
+    if (mixed) k_lines<true><<<grid, block, 0, s>>>(d_jobs, U);
+    else k_lines<false><<<grid, block, 0, s>>>(d_jobs, U);
     return cudaGetLastError();
 }
 

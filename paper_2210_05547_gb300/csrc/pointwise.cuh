@@ -18,7 +18,7 @@ __device__ __forceinline__ void atomic_status(unsigned* st, unsigned bits) {
 // registers; left to itself ptxas picks 128 registers and spills more for five-species air; for
 // eleven-species air the cap of 168 spills, yet measured faster than two blocks at 255 registers:
 // 74.3 against 67.4 Mpts*RHS/s).
-#define CLOSURE_MIN_BLOCKS 3
+#define CLOSURE_MIN_BLOCKS 3   // also for the mixed closure (4 and 2 blocks measured slower)
 
 // Reciprocals of the freestream scales, computed once per thread by the caller of closure_point
 // (the point loop multiplies by them).
