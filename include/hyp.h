@@ -63,11 +63,14 @@ enum hyp_gas_kind {
 
 /* HYP_FP64: every step in binary64. HYP_MIXED: in binary32 the transport and diffusion
  * coefficients (Blottner, Eucken, Wilke, Chapman-Enskog; Sec. 2.2.1, Eq. 19), the forward-rate
- * exponentials (Eq. 13) and the interior rows of the compact interpolations and derivatives that
- * feed only the diffusive fluxes (Sec. 3.1); in binary64 the temperature inversion, species
- * thermodynamics, equilibrium constants and backward rates, the operators feeding the convective
- * fluxes, pressure and the artificial-diffusivity sensors, every divergence, the fluxes themselves
- * and the stage update. */
+ * exponentials (Eq. 13), the species heat capacities and the weakly populated electronic levels
+ * (theta / T >= 9) of the species thermodynamics (Sec. 2.2.1), and the interior rows of the compact
+ * interpolations and derivatives that feed only the diffusive fluxes (Sec. 3.1); in double-word
+ * binary32 (each value a pair of binary32 words) the interior rows of the other compact operators;
+ * in binary64 the Newton iteration for the temperature, the vibrational factors and populated
+ * electronic levels that set the species energies, equilibrium constants and backward rates,
+ * every closure row of the operators, every divergence, the fluxes themselves and the stage
+ * update. */
 enum hyp_precision { HYP_FP64 = 0, HYP_MIXED = 1 };
 
 enum hyp_error {

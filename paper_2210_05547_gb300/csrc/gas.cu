@@ -384,6 +384,11 @@ extern "C" int hyp_gas_model_load(const char* path, int kind, const hyp_freestre
         d.f_Mq[i] = (float)d.Mq[i];
         d.f_iMq[i] = (float)d.iMq[i];
         d.f_Rs[i] = (float)d.Rs[i];
+        d.f_theta_v[i] = (float)d.theta_v[i];
+        for (int l = 0; l < MAXLEV; ++l) {
+            d.f_lev_g[i][l] = (float)d.lev_g[i][l];
+            d.f_lev_th[i][l] = (float)d.lev_th[i][l];
+        }
         for (int j = 0; j < NSP; ++j) d.f_wilke_d[i][j] = (float)d.wilke_d[i][j];
     }
     for (int q = 0; q < NSP * (NSP - 1) / 2; ++q) d.f_pair_dinv[q] = (float)d.pair_dinv[q];

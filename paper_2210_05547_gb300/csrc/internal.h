@@ -62,8 +62,10 @@ struct GasDev {
     double pair_dinv[NSP * (NSP - 1) / 2];   // pi sigma^2 / ((3/16) sqrt(2 pi k^3 / m_sr))
     double eps_inv[MAXEPS];      // 1 / sqrt(eps_s eps_r)
     double eps_powB[MAXEPS];     // sqrt(eps_s eps_r)^B of the collision-integral fit
-    // binary32 copies of the transport constants for the mixed-precision closure (HYP_MIXED)
+    // binary32 copies of the transport and modal constants for the mixed-precision closure
+    // (HYP_MIXED)
     float f_blA[NSP], f_blB[NSP], f_blC[NSP], f_Mq[NSP], f_iMq[NSP], f_Rs[NSP];
+    float f_theta_v[NSP], f_lev_g[NSP][MAXLEV], f_lev_th[NSP][MAXLEV];
     float f_wilke_d[NSP][NSP];
     float f_pair_dinv[NSP * (NSP - 1) / 2];
     float f_eps_inv[MAXEPS], f_eps_powB[MAXEPS];

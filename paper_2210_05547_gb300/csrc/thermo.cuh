@@ -27,6 +27,7 @@ constexpr int NEWTON_MAXIT = 60;
 // Stop after a Newton step of at most 1e-8 T: the error left after that step is of order
 // (dT/T)^2 ~ 1e-16 relative.
 constexpr double NEWTON_RTOL = 1.0e-8;
+constexpr double NEWTON_RTOL_MIXED = 1.0e-6;   // binary32 modal sums (temperature_from_energy)
 constexpr double SUTH_C1 = 1.458e-6;   // Eq. (24)
 constexpr double SUTH_TS = 110.4;      // Eq. (24)
 constexpr double LEVEL_CUT = 45.0;     // skip electronic levels with theta / T above this
@@ -144,6 +145,93 @@ __host__ __device__ __forceinline__ void species_shift(const GasDev& g, double T
     }
 }
 
+#ifdef __CUDACC__
+// The species modal sums of species_state for the mixed-precision closure (HYP_MIXED), split by
+// what each term contributes to the energy. In binary64: the vibrational factor
+// r = 1 / (e^x - 1) (theta_v r reaches ~T at high temperature) and the Boltzmann factors of the
+// populated electronic levels (theta / T < LEVEL_HOT_F64: the fine-structure levels of O and NO
+// at any temperature, the excited levels once they hold more than ~1e-4 of the population), with
+// the partition function q_el and the mean level energy m1 summed over them in binary64. In
+// binary32: the weakly populated levels (their energy share is below 2.5 e^-9 9 ~ 3e-3 of T, so
+// their binary32 rounding moves e_s by < 1e-9 R_s T), the second and third level moments and the
+// heat capacities with their temperature derivative. A fully binary32 electronic sum was measured
+// to move the inverted temperature by up to 5e-8 relative, which the exponents T_a / T ~ 50 of
+// the dissociation rates carry into the species source terms at ~1e-6 of their scale. The energy
+// is assembled in binary64 from its formation, translational-rotational (exact multiples of T),
+// vibrational and electronic parts. Every binary32 multiply and add is explicit, as in
+// transport_f32.
+constexpr float LEVEL_HOT_F64 = 9.0f;
+
+__device__ __forceinline__ void species_state_f32(const GasDev& g, double T, SpeciesState& s) {
+    const double invT = cl_rcp(T);
+    const float iT = f32_of(invT);
+    const float iT2 = __fmul_rn(iT, iT);
+#pragma unroll
+    for (int i = 0; i < NSP; ++i) {
+        double qd = 0.0, s1d = 0.0;                     // binary64 sums: populated levels
+        float qc = 0.0f, s1c = 0.0f, s2 = 0.0f, s3 = 0.0f;
+        for (int l = 0; l < g.nlev[i]; ++l) {
+            const float th = g.f_lev_th[i][l];
+            const float x = __fmul_rn(th, iT);
+            if (x > (float)LEVEL_CUT) break;
+            float w;
+            if (x < LEVEL_HOT_F64) {
+                const double wd = th == 0.0f ? g.lev_g[i][l]
+                                             : g.lev_g[i][l] * cl_exp(-(g.lev_th[i][l] * invT));
+                qd += wd;
+                s1d = fma(wd, g.lev_th[i][l], s1d);
+                w = f32_of(wd);
+            } else {
+                w = __fmul_rn(g.f_lev_g[i][l], expf(-x));
+                qc = __fadd_rn(qc, w);
+                s1c = fmaf(w, th, s1c);
+            }
+            const float wt2 = __fmul_rn(__fmul_rn(w, th), th);
+            s2 = __fadd_rn(s2, wt2);
+            s3 = fmaf(wt2, th, s3);
+        }
+        qd += f64_of(qc);
+        // with no populated excited level (N2, and N and O2 below a few thousand K) the mean level
+        // energy is the weak levels' alone, below 3e-3 T: binary32 suffices
+        const double m1d = s1d == 0.0 ? f64_of(__fdiv_rn(s1c, f32_of(qd)))
+                                      : cl_div(s1d + f64_of(s1c), qd);
+        const float iq = __frcp_rn(f32_of(qd));
+        const float m1 = f32_of(m1d);
+        const float m2 = __fmul_rn(s2, iq);
+        const float m3 = __fmul_rn(s3, iq);
+        const float var = fmaf(-m1, m1, m2);
+        double ev = m1d;                                 // electronic + vibrational energy, K
+        float cvo = fmaf(var, iT2, 1.5f);
+        float cvpo = __fmul_rn(__fmul_rn(fmaf(-2.0f * m1, var, fmaf(-m1, m2, m3)), iT2), iT2);
+        cvpo = fmaf(__fmul_rn(-2.0f * var, iT2), iT, cvpo);
+        if (g.linear[i]) {
+            const double xd = g.theta_v[i] * invT;
+            const double rd = cl_inv_expm1(xd);
+            ev = fma(g.theta_v[i], rd, ev);
+            const float xv = f32_of(xd);
+            const float r = f32_of(rd);
+            const float b = __fmul_rn(__fadd_rn(1.0f, r), r);
+            const float xb = __fmul_rn(__fmul_rn(xv, xv), b);
+            cvo = __fadd_rn(cvo, __fadd_rn(1.0f, xb));
+            // d/dT [x^2 e^x / (e^x - 1)^2] = -(x / T) x b (2 - x - 2 x r)
+            const float t = __fsub_rn(__fsub_rn(2.0f, xv), __fmul_rn(2.0f * xv, r));
+            cvpo = fmaf(-__fmul_rn(xb, iT), t, cvpo);
+            s.iem1[i] = rd;
+            s.xv[i] = xd;
+        } else {
+            s.iem1[i] = 0.0;
+            s.xv[i] = 0.0;
+        }
+        const double ctr = g.linear[i] ? 2.5 : 1.5;     // translation (+ rotation), per R_s
+        s.e[i] = fma(g.Rs[i], fma(ctr, T, ev), g.e0[i]);
+        s.cv[i] = f64_of(__fmul_rn(g.f_Rs[i], cvo));
+        s.cvp[i] = f64_of(__fmul_rn(g.f_Rs[i], cvpo));
+        s.qel[i] = qd;
+        s.m1[i] = m1d;
+    }
+}
+#endif
+
 __host__ __device__ __forceinline__ double mixture_energy(const GasDev& g, double T, const double* Y) {
     SpeciesState s;
     species_state(g, T, s);
@@ -196,13 +284,22 @@ __host__ __device__ __forceinline__ double temperature_guess(const GasDev& g, do
 }
 
 // Safeguarded Newton for sum_s Y_s e_s(T) = e; s holds the species state at the returned T.
+// MIXED (device only): the electronic modal sums in binary32 (species_state_f32). Their rounding
+// moves sum_s Y_s e_s(T) by up to ~1e-8 c_v T, so successive Newton steps need not fall below
+// 1e-8 T; the iteration stops at 1e-6 T instead, where the step's own error, (dT/T)^2 relative,
+// and that of the first-order shift are ~1e-12, far below the binary32 part.
+template <bool MIXED = false>
 __host__ __device__ __forceinline__ double temperature_from_energy(const GasDev& g, double e,
                                                           const double* Y, double T0,
                                                           unsigned& status, SpeciesState& s) {
     double T = fmin(fmax(T0, T_LO), T_HI);
     double lo = T_LO, hi = T_HI;
     for (int it = 0; it < NEWTON_MAXIT; ++it) {
-        species_state(g, T, s);
+#ifdef __CUDA_ARCH__
+        if constexpr (MIXED) species_state_f32(g, T, s);
+        else
+#endif
+            species_state(g, T, s);
         double f = -e, cv = 0.0;
 #pragma unroll
         for (int i = 0; i < NSP; ++i) {
@@ -211,7 +308,7 @@ __host__ __device__ __forceinline__ double temperature_from_energy(const GasDev&
         }
         if (f > 0.0) hi = T; else lo = T;
         double Tn = T - cl_div(f, cv);
-        if (fabs(Tn - T) <= NEWTON_RTOL * T) {
+        if (fabs(Tn - T) <= (MIXED ? NEWTON_RTOL_MIXED : NEWTON_RTOL) * T) {
             species_shift(g, T, Tn - T, s);
             return Tn;
         }
@@ -388,15 +485,16 @@ __host__ __device__ __forceinline__ void transport_f64(const GasDev& g, double T
 }
 
 // Full closure (SI). reactions: evaluate w_s; diffusion: evaluate D_s. MIXED (device only): the
-// forward rate exponentials, transport and diffusion in binary32; temperature inversion, species
-// thermodynamics, equilibrium constants and backward rates stay FP64.
+// species modal sums (electronic and vibrational parts of e_s, c_v,s, the partition-function
+// factors), the forward rate exponentials, transport and diffusion in binary32; the Newton
+// iteration for T, the assembly of e_s, the equilibrium constants and backward rates stay FP64.
 template <bool MIXED>
 __host__ __device__ __forceinline__ void closure_si_p(const GasDev& g, double rho, double e,
                                              const double* Y, double T0, bool reactions,
                                              bool diffusion, ClosureOut& o) {
     SpeciesState s;
     o.status = rho > 0.0 ? 0u : HYP_STATUS_NONPHYSICAL;
-    const double T = temperature_from_energy(g, e, Y, T0, o.status, s);
+    const double T = temperature_from_energy<MIXED>(g, e, Y, T0, o.status, s);
     double ym = 0.0, cv = 0.0;
 #pragma unroll
     for (int i = 0; i < NSP; ++i) {
