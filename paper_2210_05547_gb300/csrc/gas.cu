@@ -348,6 +348,15 @@ extern "C" int hyp_gas_model_load(const char* path, int kind, const hyp_freestre
                                      "element alone");
         }
     }
+    {
+        SpeciesState lo, hi;
+        species_state(d, T_LO, lo);
+        species_state(d, T_HI, hi);
+        for (int i = 0; i < NSP; ++i) {
+            d.e_lo[i] = lo.e[i];
+            d.e_hi[i] = hi.e[i];
+        }
+    }
     SpeciesState s;
     species_state(d, fs->T_inf, s);
     double cv = 0.0;

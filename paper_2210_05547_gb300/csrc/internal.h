@@ -74,6 +74,7 @@ struct GasDev {
     // earlier temperature is known
     double etab_lnT0, etab_dlnT;
     double etab_e[NSP][ETAB_N], etab_cv[NSP][ETAB_N];
+    double e_lo[NSP], e_hi[NSP];   // species energies at the ends of the inversion's range
     // kinetics (Eqs. 13-15): elementary reactions with explicit colliders, sorted by group
     int gstart[MAXG + 1];        // reactions of group k: [gstart[k], gstart[k+1])
     double C[MAXR];              // SI pre-exponential factor

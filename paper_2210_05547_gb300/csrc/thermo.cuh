@@ -152,14 +152,14 @@ __host__ __device__ __forceinline__ void species_shift(const GasDev& g, double T
 // populated electronic levels (theta / T < LEVEL_HOT_F64: the fine-structure levels of O and NO
 // at any temperature, the excited levels once they hold more than ~1e-4 of the population), with
 // the partition function q_el and the mean level energy m1 summed over them in binary64. In
-// binary32: the weakly populated levels (their energy share is below 2.5 e^-9 9 ~ 3e-3 of T, so
-// their binary32 rounding moves e_s by < 1e-9 R_s T), the second and third level moments and the
-// heat capacities with their temperature derivative. A fully binary32 electronic sum was measured
-// to move the inverted temperature by up to 5e-8 relative, which the exponents T_a / T ~ 50 of
-// the dissociation rates carry into the species source terms at ~1e-6 of their scale. The energy
-// is assembled in binary64 from its formation, translational-rotational (exact multiples of T),
-// vibrational and electronic parts. Every binary32 multiply and add is explicit, as in
-// transport_f32.
+// binary32: the weakly populated levels (a level's energy share is at most (g_l / g_0) 9 e^-9 <=
+// 6.7e-3 of T, so its binary32 rounding, ~1e-6 relative with that of theta / T, moves e_s by
+// < 1e-8 R_s T), the second and third level moments and the heat capacities with their
+// temperature derivative. A fully binary32 electronic sum was measured to move the inverted
+// temperature by up to 5e-8 relative, which the exponents T_a / T ~ 50 of the dissociation rates
+// carry into the species source terms at ~1e-6 of their scale. The energy is assembled in
+// binary64 from its formation, translational-rotational (exact multiples of T), vibrational and
+// electronic parts. Every binary32 multiply and add is explicit, as in transport_f32.
 constexpr float LEVEL_HOT_F64 = 9.0f;
 
 __device__ __forceinline__ void species_state_f32(const GasDev& g, double T, SpeciesState& s) {
@@ -316,8 +316,15 @@ __host__ __device__ __forceinline__ double temperature_from_energy(const GasDev&
         T = Tn;
     }
     {
-        const double elo = mixture_energy(g, T_LO, Y);
-        const double ehi = mixture_energy(g, T_HI, Y);
+        // the energy lies outside the temperature range (T clamped to its end) or the iteration
+        // failed; the mixture energies at the ends come from the species energies there, which
+        // the gas model holds (full species evaluations inlined here would only add code)
+        double elo = 0.0, ehi = 0.0;
+#pragma unroll
+        for (int i = 0; i < NSP; ++i) {
+            elo += Y[i] * g.e_lo[i];
+            ehi += Y[i] * g.e_hi[i];
+        }
         if (e <= elo) {
             T = T_LO;
             status |= HYP_STATUS_T_CLAMPED;
@@ -374,6 +381,10 @@ __device__ __forceinline__ void transport_f32(const GasDev& g, double T, double 
 #pragma unroll
         for (int r = 0; r < NSP; ++r) {
             if (HAS_CHARGE && !g.heavy[r]) continue;
+            if (r == i) {
+                phi = __fadd_rn(phi, Xf[i]);    // (1 + a_i b_i)^2 d_ii = 1
+                continue;
+            }
             const float t = fmaf(a[i], b[r], 1.0f);
             phi = fmaf(__fmul_rn(__fmul_rn(Xf[r], t), t), g.f_wilke_d[i][r], phi);
         }
@@ -442,6 +453,10 @@ __host__ __device__ __forceinline__ void transport_f64(const GasDev& g, double T
 #pragma unroll
         for (int r = 0; r < NSP; ++r) {
             if (HAS_CHARGE && !g.heavy[r]) continue;
+            if (r == i) {
+                phi += o.X[i];          // (1 + a_i b_i)^2 d_ii = 2^2 / sqrt(16) = 1
+                continue;
+            }
             const double t = 1.0 + a[i] * b[r];
             phi += o.X[r] * t * t * g.wilke_d[i][r];
         }
@@ -566,7 +581,8 @@ __host__ __device__ __forceinline__ void closure_si_p(const GasDev& g, double rh
             const double Eb = cl_exp(base - (g.g_Ta[k] - g.g_theta_d[k]) * invT) * cl_div(den, num);
             const double Rg = w * (Ef * fwd - Eb * bwd);
 #pragma unroll
-            for (int i = 0; i < NSP; ++i) molar[i] += g.g_nud[k][i] * Rg;
+            for (int i = 0; i < NSP; ++i)
+                if (g.g_nu[k][i] != 0) molar[i] += g.g_nud[k][i] * Rg;   // the group's species only
         }
 #pragma unroll
         for (int i = 0; i < NSP; ++i) o.wdot[i] = g.M[i] * molar[i];

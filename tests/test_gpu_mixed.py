@@ -11,12 +11,15 @@ bound held here:
 
 * conversion (hyp_round_f32): equal to the hardware round-to-nearest-even for every result in the
   normal binary32 range, widening back exact;
-* thermo_eval: T and p within 3e-9 relative. Each electronic level with theta / T >= 9 (binary32)
-  holds at most g_l / g_0 x e^-x <= 2.5 * 9 e^-9 = 2.8e-3 of R_s T; its binary32 value (expf within
-  2 ulp, a product and two sums) errs by at most ~5 * 2^-24 = 3e-7 relative, and at most two such
-  levels per species hold more than 1e-4 of that share, so e_s moves by <= 1.7e-9 R_s T and T by
-  <= 1.7e-9 T max_s R_s / c_v,s <= 1.2e-9 T (the binary32 c_v enters only through the last Newton
-  step, below 1e-6 T: 1e-13). mu, k, D within 4e-6 relative per state. The binary32 result
+* thermo_eval: T and p within 3e-9 relative. An electronic level evaluated in binary32
+  (x = theta / T >= 9) holds at most (g_l / g_0) x e^-x <= 6 * 9 e^-9 = 6.7e-3 of R_s T
+  (g_l / g_0 <= 6 in both gas tables; the next weak level of a species holds far less). Its
+  binary32 Boltzmann factor errs by about (1.5 x + 3) 2^-24 relative: the rounding of 1/T and of
+  theta / T scaled by x, expf within 2 ulp, a product; 1e-6 at x = 9. So e_s moves by <= ~7e-9
+  R_s T, and T by that over c_v,s >= 2.5 R_s for the molecule with the ratio 6 (2.5 and 1.5 R_s
+  for the atoms at their ratio 2.5): <= ~2e-9 T. The binary32 c_v enters only through the last
+  Newton step, below 1e-6 T: 1e-13. Measured: 1.3e-9 over 2e5 states, 300-15000 K. mu, k, D
+  within 4e-6 relative per state. The binary32 result
   of exp(x) carries the rounding of its argument, |x| 2^-24, and the Blottner exponent reaches
   |x| ~ 25 (1.5e-6); the binary32 sums of Wilke's rule and Eq. (19) add a few 2^-24;
 * thermo_eval wdot: within 1e-5 of max|wdot_s| per species (forward-rate exponent up to ~40 at
