@@ -64,7 +64,8 @@ enum hyp_gas_kind {
 /* HYP_FP64: every step in binary64. HYP_MIXED: in binary32 the transport and diffusion
  * coefficients (Blottner, Eucken, Wilke, Chapman-Enskog; Sec. 2.2.1, Eq. 19), the forward-rate
  * exponentials (Eq. 13), the species heat capacities and the weakly populated electronic levels
- * (theta / T >= 9) of the species thermodynamics (Sec. 2.2.1), and the interior rows of the compact
+ * (theta / T >= 9) of the species thermodynamics (Sec. 2.2.1; in the right-hand side, whose
+ * neighbouring cells share a choice per level, not in hyp_thermo_eval), and the interior rows of the compact
  * interpolations and derivatives that feed only the diffusive fluxes (Sec. 3.1); in double-word
  * binary32 (each value a pair of binary32 words) the interior rows of the other compact operators;
  * in binary64 the Newton iteration for the temperature, the vibrational factors and populated
@@ -188,6 +189,14 @@ int hyp_grid_reference(const hyp_grid* grid, double* U_ref_host, double* sigma_h
 /* Read and optionally clear the OR of the per-point status bits raised since the last clear.
  * Synchronises the grid's stream. */
 int hyp_grid_status(const hyp_grid* grid, uint32_t* flags, int clear);
+
+/* Temperature (K) at every cell centre from the grid's last hyp_rhs or hyp_rk_stage: the T the
+ * closure inverted from the internal energy (Sec. 2.2). hyp_rhs_noalloc keeps its closure in its
+ * own scratch and does not change it. T: DEVICE, caller-owned, n_T doubles, n_T = nx*ny
+ * (nx*ny*nz for a three-dimensional grid), x fastest. Enqueued on `stream` (order it after the
+ * evaluation it reads). HYP_ERR_ARG if n_T is not the cell count or no closure has run on the
+ * grid yet. */
+int hyp_grid_temperature(const hyp_grid* grid, int64_t n_T, double* T, void* stream);
 
 void hyp_state_free(hyp_state* st);
 

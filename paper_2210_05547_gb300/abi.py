@@ -87,6 +87,7 @@ EXPORTS = {
     "hyp_state_grid": (_P, [_P]),
     "hyp_grid_reference": (_I, [_P, _P, _P]),
     "hyp_grid_status": (_I, [_P, ctypes.POINTER(ctypes.c_uint32), _I]),
+    "hyp_grid_temperature": (_I, [_P, ctypes.c_int64, _P, _P]),
     "hyp_state_free": (None, [_P]),
     "hyp_rhs": (_I, [_P, _P, _P, _P, _I, _P]),
     "hyp_rk_stage": (_I, [_P, _I, _D, _I, _P]),
@@ -487,6 +488,15 @@ def grid_status(grid, clear=False):
     flags = ctypes.c_uint32()
     _check(L.hyp_grid_status(grid, ctypes.byref(flags), int(clear)), L)
     return flags.value
+
+
+def grid_temperature(grid, T, stream=None):
+    """hyp_grid_temperature: the cell-centre temperatures (K) of the grid's last closure into the
+    device tensor T (nx*ny or nx*ny*nz doubles)."""
+    import torch
+    L = _grid_lib(grid)
+    _check(L.hyp_grid_temperature(grid, T.numel(), _dptr(T, None, torch.float64),
+                                  _stream(stream)), L)
 
 
 def thermo_eval(gas, rho, e, Y, T=None, p=None, wdot=None, mu=None, k=None, D=None,

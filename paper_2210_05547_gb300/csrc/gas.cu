@@ -393,11 +393,6 @@ extern "C" int hyp_gas_model_load(const char* path, int kind, const hyp_freestre
         d.f_Mq[i] = (float)d.Mq[i];
         d.f_iMq[i] = (float)d.iMq[i];
         d.f_Rs[i] = (float)d.Rs[i];
-        d.f_theta_v[i] = (float)d.theta_v[i];
-        for (int l = 0; l < MAXLEV; ++l) {
-            d.f_lev_g[i][l] = (float)d.lev_g[i][l];
-            d.f_lev_th[i][l] = (float)d.lev_th[i][l];
-        }
         for (int j = 0; j < NSP; ++j) d.f_wilke_d[i][j] = (float)d.wilke_d[i][j];
     }
     for (int q = 0; q < NSP * (NSP - 1) / 2; ++q) d.f_pair_dinv[q] = (float)d.pair_dinv[q];
@@ -459,7 +454,8 @@ __global__ void __launch_bounds__(128) k_thermo_eval(
 #pragma unroll
         for (int s = 0; s < NSP; ++s) y[s] = Y[s * n + i];
         ClosureOut o;
-        closure_si_p<MIXED>(g, rho[i], e[i], y, temperature_guess(g, e[i], y), reactions && wdot,
+        // binary64 modal sums in both precisions: independent states (closure_si_p, MODES32)
+        closure_si_p<MIXED, false>(g, rho[i], e[i], y, temperature_guess(g, e[i], y), reactions && wdot,
                             diffusion && D, o);
         if (T) T[i] = o.T;
         if (p) p[i] = o.p;

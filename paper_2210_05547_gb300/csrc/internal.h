@@ -62,10 +62,8 @@ struct GasDev {
     double pair_dinv[NSP * (NSP - 1) / 2];   // pi sigma^2 / ((3/16) sqrt(2 pi k^3 / m_sr))
     double eps_inv[MAXEPS];      // 1 / sqrt(eps_s eps_r)
     double eps_powB[MAXEPS];     // sqrt(eps_s eps_r)^B of the collision-integral fit
-    // binary32 copies of the transport and modal constants for the mixed-precision closure
-    // (HYP_MIXED)
+    // binary32 copies of the transport constants for the mixed-precision closure (HYP_MIXED)
     float f_blA[NSP], f_blB[NSP], f_blC[NSP], f_Mq[NSP], f_iMq[NSP], f_Rs[NSP];
-    float f_theta_v[NSP], f_lev_g[NSP][MAXLEV], f_lev_th[NSP][MAXLEV];
     float f_wilke_d[NSP][NSP];
     float f_pair_dinv[NSP * (NSP - 1) / 2];
     float f_eps_inv[MAXEPS], f_eps_powB[MAXEPS];
@@ -74,7 +72,6 @@ struct GasDev {
     // earlier temperature is known
     double etab_lnT0, etab_dlnT;
     double etab_e[NSP][ETAB_N], etab_cv[NSP][ETAB_N];
-    double e_lo[NSP], e_hi[NSP];   // species energies at the ends of the inversion's range
     // kinetics (Eqs. 13-15): elementary reactions with explicit colliders, sorted by group
     int gstart[MAXG + 1];        // reactions of group k: [gstart[k], gstart[k+1])
     double C[MAXR];              // SI pre-exponential factor
@@ -105,6 +102,7 @@ struct GasDev {
     double lnA_tr[NSP];          // ln A_tr
     double ln_isr[NSP];          // ln(1 / (sigma theta_r)) for linear molecules
     double theta0[NSP];          // E0_s / R_u (K): ground-state energy incl. formation
+    double e_lo[NSP], e_hi[NSP]; // species energies at the ends of the inversion's range
 };
 
 }  // namespace hyp

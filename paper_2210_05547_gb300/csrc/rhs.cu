@@ -1190,6 +1190,19 @@ extern "C" int hyp_rhs(const hyp_gas* gas, const hyp_grid* grid, const double* U
                    (cudaStream_t)stream);
 }
 
+extern "C" int hyp_grid_temperature(const hyp_grid* grid, int64_t n_T, double* T, void* stream) {
+    if (!grid || !T) return fail(HYP_ERR_ARG, "null argument");
+    const Grid3* g3 = static_cast<const Grid3*>(grid->g3);
+    const int valid = g3 ? g3->cache_valid : grid->cache_valid;
+    if (!valid) return fail(HYP_ERR_ARG, "no closure has been evaluated on this grid");
+    const double* src = g3 ? g3->Tcache : grid->s.Tcache;
+    const long long n = g3 ? g3->nc : (long long)grid->d.nx * grid->d.ny;
+    if (n_T != n) return fail(HYP_ERR_ARG, "T must hold one double per cell centre");
+    HYP_CUDA(cudaMemcpyAsync(T, src, sizeof(double) * n, cudaMemcpyDeviceToDevice,
+                             (cudaStream_t)stream));
+    return HYP_OK;
+}
+
 // The state filter after the last RK stage: x pass into the scratch state vector, y pass back.
 static int launch_filter(hyp_grid* G, double* U, cudaStream_t s) {
     const double sigma = G->cas.filter_sigma;

@@ -171,7 +171,7 @@ __device__ __forceinline__ void species_state_f32(const GasDev& g, double T, Spe
         double qd = 0.0, s1d = 0.0;                     // binary64 sums: populated levels
         float qc = 0.0f, s1c = 0.0f, s2 = 0.0f, s3 = 0.0f;
         for (int l = 0; l < g.nlev[i]; ++l) {
-            const float th = g.f_lev_th[i][l];
+            const float th = f32_of(g.lev_th[i][l]);
             const float x = __fmul_rn(th, iT);
             if (x > (float)LEVEL_CUT) break;
             float w;
@@ -182,7 +182,7 @@ __device__ __forceinline__ void species_state_f32(const GasDev& g, double T, Spe
                 s1d = fma(wd, g.lev_th[i][l], s1d);
                 w = f32_of(wd);
             } else {
-                w = __fmul_rn(g.f_lev_g[i][l], expf(-x));
+                w = __fmul_rn(f32_of(g.lev_g[i][l]), expf(-x));
                 qc = __fadd_rn(qc, w);
                 s1c = fmaf(w, th, s1c);
             }
@@ -503,13 +503,17 @@ __host__ __device__ __forceinline__ void transport_f64(const GasDev& g, double T
 // species modal sums (electronic and vibrational parts of e_s, c_v,s, the partition-function
 // factors), the forward rate exponentials, transport and diffusion in binary32; the Newton
 // iteration for T, the assembly of e_s, the equilibrium constants and backward rates stay FP64.
-template <bool MIXED>
+// MODES32 (with MIXED): the split modal sums of species_state_f32. Its binary64-or-binary32
+// choice per electronic level follows T, so it stays uniform across a warp where neighbouring
+// cells have similar temperatures (the right-hand side); the sweep of independent states
+// (hyp_thermo_eval), whose temperatures differ from lane to lane, keeps the binary64 sums.
+template <bool MIXED, bool MODES32 = MIXED>
 __host__ __device__ __forceinline__ void closure_si_p(const GasDev& g, double rho, double e,
                                              const double* Y, double T0, bool reactions,
                                              bool diffusion, ClosureOut& o) {
     SpeciesState s;
     o.status = rho > 0.0 ? 0u : HYP_STATUS_NONPHYSICAL;
-    const double T = temperature_from_energy<MIXED>(g, e, Y, T0, o.status, s);
+    const double T = temperature_from_energy<MIXED && MODES32>(g, e, Y, T0, o.status, s);
     double ym = 0.0, cv = 0.0;
 #pragma unroll
     for (int i = 0; i < NSP; ++i) {

@@ -66,8 +66,7 @@ def test_thermo_eval_mixed(A, gas, table11):
     e = G.mixture_energy(table11, T, Y)
     g = _run(A, gas, rho, e, Y, precision=1)
     o = G.thermo_eval(table11, rho, e, Y)
-    # binary32 weakly populated electronic levels: T within 3e-9 (the bound of test_gpu_mixed.py)
-    assert np.max(np.abs(g["T"] - o["T"]) / o["T"]) < 3e-9
+    assert np.max(np.abs(g["T"] - o["T"]) / o["T"]) < 1e-13
     err = {k: float(np.max(np.abs(g[k] - o[k]) / np.abs(o[k]))) for k in ("mu", "k")}
     assert max(err.values()) < 4e-6 and max(err.values()) > 1e-9, err
 
