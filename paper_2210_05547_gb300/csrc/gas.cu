@@ -402,14 +402,16 @@ extern "C" int hyp_gas_model_load(const char* path, int kind, const hyp_freestre
     }
     d.etab_lnT0 = log(T_LO);
     d.etab_dlnT = (log(T_HI) - log(T_LO)) / (ETAB_N - 1);
+    g->etab_host.assign(2 * NSP * ETAB_N, 0.0);
     for (int k = 0; k < ETAB_N; ++k) {
         SpeciesState st;
         species_state(d, exp(d.etab_lnT0 + k * d.etab_dlnT), st);
         for (int i = 0; i < NSP; ++i) {
-            d.etab_e[i][k] = st.e[i];
-            d.etab_cv[i][k] = st.cv[i];
+            g->etab_host[i * ETAB_N + k] = st.e[i];
+            g->etab_host[(NSP + i) * ETAB_N + k] = st.cv[i];
         }
     }
+    d.etab = nullptr;
     d.Re = fs->reynolds;
     d.Pr = d.mu_inf * d.cp_inf / d.k_inf;
     d.T_ref = (d.gamma_inf - 1.0) * fs->T_inf;
@@ -430,7 +432,10 @@ extern "C" int hyp_gas_scales(const hyp_gas* gas, int* n_species, double* sc) {
     return HYP_OK;
 }
 
-extern "C" void hyp_gas_free(hyp_gas* gas) { delete gas; }
+extern "C" void hyp_gas_free(hyp_gas* gas) {
+    if (gas && gas->etab_dev) cudaFree(gas->etab_dev);
+    delete gas;
+}
 
 extern "C" const char* hyp_last_error(void) { return g_last_error.c_str(); }
 
@@ -505,6 +510,25 @@ __global__ void k_thermo_energy(GasDev g, int64_t n, const double* __restrict__ 
     }
 }
 
+// The device copy of the starting-temperature table (GasDev::etab), made by the first evaluation
+// that needs it: loading a gas model stays a host-only step.
+int gas_etab(const hyp_gas* cgas) {
+    hyp_gas* gas = const_cast<hyp_gas*>(cgas);
+    std::lock_guard<std::mutex> lock(gas->etab_mu);
+    if (gas->etab_dev) return HYP_OK;
+    const size_t bytes = sizeof(double) * gas->etab_host.size();
+    double* p = nullptr;
+    HYP_CUDA(cudaMalloc(&p, bytes));
+    const cudaError_t err = cudaMemcpy(p, gas->etab_host.data(), bytes, cudaMemcpyHostToDevice);
+    if (err != cudaSuccess) {
+        cudaFree(p);
+        HYP_CUDA(err);
+    }
+    gas->etab_dev = p;
+    gas->dev.etab = p;
+    return HYP_OK;
+}
+
 int grid_for(int64_t n, int block) {
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
@@ -527,6 +551,7 @@ extern "C" int hyp_thermo_eval(const hyp_gas* gas, int64_t n, const double* rho,
         return fail(HYP_ERR_ARG, "an LTE gas has no independent composition: use hyp_lte_eval");
     if (n == 0) return HYP_OK;
     if (!rho || !e || !Y) return fail(HYP_ERR_ARG, "null input");
+    if (const int rc = gas_etab(gas)) return rc;
     const int block = 128;
     if (precision == HYP_MIXED)
         k_thermo_eval<true><<<grid_for(n, block), block, 0, (cudaStream_t)stream>>>(
@@ -557,6 +582,7 @@ extern "C" int hyp_lte_eval(const hyp_gas* gas, int64_t n, const double* rho, co
     if (precision != HYP_FP64 && precision != HYP_MIXED) return fail(HYP_ERR_ARG, "unknown precision");
     if (n == 0) return HYP_OK;
     if (!rho || !e) return fail(HYP_ERR_ARG, "null input");
+    if (const int rc = gas_etab(gas)) return rc;
     const int block = 128;
     if (precision == HYP_MIXED)
         k_lte_eval<true><<<grid_for(n, block), block, 0, (cudaStream_t)stream>>>(

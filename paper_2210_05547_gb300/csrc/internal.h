@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -69,9 +70,11 @@ struct GasDev {
     float f_eps_inv[MAXEPS], f_eps_powB[MAXEPS];
     // species energies e_s and heat capacities c_v,s (J/kg, J/(kg K)) at ETAB_N temperatures
     // spaced evenly in ln T from 50 K to 1e5 K: a starting temperature for the inversion when no
-    // earlier temperature is known
+    // earlier temperature is known. A device array [e | c_v][species][ETAB_N] in global memory
+    // (the bisection reads it at a different temperature in every lane, which the constant cache
+    // would serialise); null until an evaluation that needs it (hyp_thermo_eval, hyp_lte_eval).
     double etab_lnT0, etab_dlnT;
-    double etab_e[NSP][ETAB_N], etab_cv[NSP][ETAB_N];
+    const double* etab;
     // kinetics (Eqs. 13-15): elementary reactions with explicit colliders, sorted by group
     int gstart[MAXG + 1];        // reactions of group k: [gstart[k], gstart[k+1])
     double C[MAXR];              // SI pre-exponential factor
@@ -110,6 +113,9 @@ struct GasDev {
 struct hyp_gas {
     hyp::GasDev dev;
     std::vector<std::string> names;
+    std::vector<double> etab_host;   // the table behind GasDev::etab
+    double* etab_dev = nullptr;      // its device copy, made on first use (gas.cu)
+    std::mutex etab_mu;
 };
 
 namespace hyp {

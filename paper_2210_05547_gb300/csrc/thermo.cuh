@@ -247,10 +247,11 @@ __host__ __device__ __forceinline__ double mixture_energy(const GasDev& g, doubl
 // steps. Only the starting point of the safeguarded Newton iteration below: the temperature it
 // returns does not depend on it beyond the iteration's tolerance.
 __host__ __device__ __forceinline__ double temperature_guess(const GasDev& g, double e, const double* Y) {
+    const double* et = g.etab;       // device only: [e | c_v][species][ETAB_N]
     auto emix = [&](int k) {
         double s = 0.0;
 #pragma unroll
-        for (int i = 0; i < NSP; ++i) s += Y[i] * g.etab_e[i][k];
+        for (int i = 0; i < NSP; ++i) s += Y[i] * et[i * ETAB_N + k];
         return s;
     };
     int lo = 0, hi = ETAB_N - 1;
@@ -265,8 +266,8 @@ __host__ __device__ __forceinline__ double temperature_guess(const GasDev& g, do
     double ca = 0.0, cb = 0.0;
 #pragma unroll
     for (int i = 0; i < NSP; ++i) {
-        ca += Y[i] * g.etab_cv[i][lo];
-        cb += Y[i] * g.etab_cv[i][hi];
+        ca += Y[i] * et[(NSP + i) * ETAB_N + lo];
+        cb += Y[i] * et[(NSP + i) * ETAB_N + hi];
     }
     const double h = Tb - Ta;
     double t = cl_div(e - ea, eb - ea);              // linear start
