@@ -344,11 +344,12 @@ void hyp_server_free(hyp_server* sv);
  * (binary64): DEVICE outputs, each nullable. */
 int hyp_round_f32(int64_t n, const double* x, float* y, double* back, void* stream);
 
-/* The binary64 exponential, quotient and reciprocal the FP64 closure uses (diagnostics; no
- * counterpart in the paper): exp by Tang's table-driven method and a / b, 1 / b from a binary32
- * reciprocal refined in binary64, each within 2 ulp; arguments outside their fast ranges (|a| >=
- * 512 for exp, |b| outside [2^-120, 2^120] for the quotients) go through CUDA's exp and division.
- * fn 0: out[i] = exp(a[i]); fn 1: out[i] = a[i] / b[i]; fn 2: out[i] = 1 / b[i]. a, b (the one a
+/* The binary64 exponential, quotient, reciprocal and logarithm the FP64 closure uses
+ * (diagnostics; no counterpart in the paper): exp and log by Tang's table-driven methods, a / b
+ * and 1 / b from a binary32 reciprocal refined in binary64, each within 2 ulp; arguments outside
+ * their fast ranges (|a| >= 512 for exp, |b| outside [2^-120, 2^120] for the quotients, a outside
+ * [2, 2^1000) for log) go through CUDA's exp, division and log. fn 0: out[i] = exp(a[i]); fn 1:
+ * out[i] = a[i] / b[i]; fn 2: out[i] = 1 / b[i]; fn 3: out[i] = log(a[i]). a, b (the one a
  * function does not read may be null), out: DEVICE arrays of n doubles. */
 int hyp_fp64_fast(int fn, int64_t n, const double* a, const double* b, double* out, void* stream);
 

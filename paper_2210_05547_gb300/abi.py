@@ -354,7 +354,8 @@ def round_f32(x, y=None, back=None, stream=None):
 
 
 def fp64_fast(fn, out, a=None, b=None, stream=None):
-    """hyp_fp64_fast: fn 0 exp(a), 1 a / b, 2 1 / b as the FP64 closure computes them, device."""
+    """hyp_fp64_fast: fn 0 exp(a), 1 a / b, 2 1 / b, 3 log(a) as the FP64 closure computes them,
+    device."""
     import torch
     n = out.numel()
     _check(lib().hyp_fp64_fast(fn, n, _dptr(a, n, torch.float64) if a is not None else None,

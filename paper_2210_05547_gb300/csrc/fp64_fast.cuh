@@ -1,4 +1,4 @@
-// Binary64 exponentials and quotients on fewer FP64-pipe instructions.
+// Binary64 exponentials, logarithms and quotients on fewer FP64-pipe instructions.
 //
 // GB300 retires two FP64 FMAs per clock per SM against 128 binary32 FMAs and 64 integer
 // operations, so in the FP64 closure one FP64 instruction costs as much pipe time as dozens of
@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include "exp_table.h"
+#include "log_table.h"
 #include "fp32.cuh"
 
 namespace hyp {
@@ -81,6 +82,33 @@ __device__ __forceinline__ double fast_div(double a, double b) {
     const double y1 = fma(y0, fma(-b, y0, 1.0), y0);
     const double q = __dmul_rn(a, y1);
     return fma(fma(-b, q, a), y1, q);
+}
+
+// log(x) for x >= 2 by Tang's table-driven method (ACM TOMS 16(4), 1990) in its reciprocal form:
+// x = 2^m y with y in [1, 2) and j the top 7 fraction bits of y (integer instructions),
+// r = y inv_j - 1 in one FMA (inv_j the binary64 nearest to 1 / c_j, c_j = 1 + (j + 1/2) / 128;
+// |r| < 2^-8, rounding error below 2^-61), log1p(r) = r - r^2/2 + r^3/3 - r^4/4 + r^5/5 - r^6/6
+// (Taylor; the first omitted term below 2e-18), and
+// log x = (m LN2_HI + T_j,hi) + (m LN2_LO + T_j,lo + log1p(r)) with T_j = -log(inv_j) from the
+// table. No cancellation for x >= 2 (log x >= ln2): within 1 ulp. 11 FP64 instructions. Below
+// 2 (where log x may be near zero), at or above 2^1000, and NaN: CUDA's log.
+__device__ __forceinline__ double table_log(double x) {
+    const int hx = __double2hiint(x);
+    const int ex = (hx >> 20) & 0x7ff;
+    if (hx < 0x40000000 || ex >= 1023 + 1000) return log(x);
+    const int j = (hx >> 13) & (LOG_TABLE_N - 1);
+    const double y = __hiloint2double((hx & 0x000fffff) | 0x3ff00000, __double2loint(x));
+    const double* t = LOG_TABLE[j];
+    const double r = fma(y, t[0], -1.0);
+    double c = fma(r, -1.0 / 6.0, 0.2);
+    c = fma(r, c, -0.25);
+    c = fma(r, c, 1.0 / 3.0);
+    c = fma(r, c, -0.5);
+    const double p = fma(__dmul_rn(r, r), c, r);
+    const double md = f64_of_int(ex - 1023);
+    const double hi = fma(md, LOG_LN2_HI, t[1]);
+    const double lo = fma(md, LOG_LN2_LO, t[2]) + p;
+    return hi + lo;
 }
 
 }  // namespace hyp

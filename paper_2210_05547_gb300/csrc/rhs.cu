@@ -1316,14 +1316,15 @@ __global__ void k_fp64_fast(int fn, int64_t n, const double* __restrict__ a,
          i += (int64_t)gridDim.x * blockDim.x) {
         if (fn == 0) out[i] = tang_exp(a[i]);
         else if (fn == 1) out[i] = fast_div(a[i], b[i]);
-        else out[i] = fast_rcp(b[i]);
+        else if (fn == 2) out[i] = fast_rcp(b[i]);
+        else out[i] = table_log(a[i]);
     }
 }
 
 extern "C" int hyp_fp64_fast(int fn, int64_t n, const double* a, const double* b, double* out,
                              void* stream) {
-    if (fn < 0 || fn > 2 || n < 0) return fail(HYP_ERR_ARG, "unknown function or negative n");
-    if (n > 0 && (!out || (fn <= 1 && !a) || (fn >= 1 && !b)))
+    if (fn < 0 || fn > 3 || n < 0) return fail(HYP_ERR_ARG, "unknown function or negative n");
+    if (n > 0 && (!out || ((fn <= 1 || fn == 3) && !a) || ((fn == 1 || fn == 2) && !b)))
         return fail(HYP_ERR_ARG, "null argument");
     if (n == 0) return HYP_OK;
     const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 16);

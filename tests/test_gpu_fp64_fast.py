@@ -1,7 +1,7 @@
-"""The binary64 exponential, quotient and reciprocal of the FP64 closure (hyp_fp64_fast): within
-2 ulp of the exact result over the closure's argument ranges (the exact result from numpy's long
-double arithmetic, at least 64 significand bits), and equal to CUDA's own functions where the
-arguments leave the fast ranges."""
+"""The binary64 exponential, quotient, reciprocal and logarithm of the FP64 closure
+(hyp_fp64_fast): within 2 ulp of the exact result over the closure's argument ranges (the exact
+result from numpy's long double arithmetic, at least 64 significand bits), and equal to CUDA's own
+functions where the arguments leave the fast ranges."""
 import numpy as np
 import pytest
 
@@ -72,3 +72,24 @@ def test_quotient_outside_the_fast_range_is_cudas():
     got_r = _run(2, b=b)
     want_r = (1.0 / torch.as_tensor(b).cuda()).cpu().numpy()
     assert np.array_equal(got_r, want_r, equal_nan=True)
+
+
+def test_log_within_two_ulp():
+    rng = np.random.default_rng(9)
+    x = np.concatenate([
+        np.exp(rng.uniform(np.log(2.0), 690.0, 300_000)),   # the whole fast range
+        rng.uniform(50.0, 1.0e5, 300_000),                  # temperatures of the closure
+        rng.uniform(2.0, 4.0, 100_000),                     # the first binade
+        np.array([2.0, 2.0 + 2.0 ** -51, 4.0 - 2.0 ** -50, 1024.0, 1000.0, 2.0 ** 999]),
+    ])
+    got = _run(3, a=x)
+    err = _ulp_error(got, np.log(x.astype(np.longdouble)))
+    assert err.max() <= 2.0, (err.max(), x[np.argmax(err)])
+
+
+def test_log_outside_the_fast_range_is_cudas():
+    import torch
+    x = np.array([1.999, 1.0, 0.5, 1e-300, 0.0, -1.0, 2.0 ** 1000, 1e308, np.inf, np.nan])
+    got = _run(3, a=x)
+    want = torch.log(torch.as_tensor(x).cuda()).cpu().numpy()
+    assert np.array_equal(got, want, equal_nan=True)
