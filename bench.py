@@ -35,37 +35,38 @@ STAGES = 3
 L2_FLUSH_BYTES = 256 << 20
 # FP64 operations per cell-centre point executed by k_closure (DADD + DMUL + 2 DFMA), from ncu's
 # thread instruction counts of a launch of an RK step after the first (1024 x 256 cells;
-# 712.8 DFMA, 125.8 DADD, 529.3 DMUL per point; profiles/k_closure_sbli.md).
-CLOSURE_FP64_FLOP_PER_POINT = 2080.7
+# 680.8 DFMA, 124.8 DADD, 513.3 DMUL per point; profiles/k_closure_sbli.md).
+CLOSURE_FP64_FLOP_PER_POINT = 1999.7
 # The same counts as FP64 warp-lane instructions (DFMA + DADD + DMUL): a DADD or DMUL takes an FP64
 # issue slot like a DFMA but counts one flop, so the pipe's occupancy is the instruction rate
 # against 2 instructions per clock per SM. All instructions on the FP64 pipe (comparisons and
-# conversions included): 1500.5 per point.
-CLOSURE_FP64_INSTR_PER_POINT = 1367.9
-CLOSURE_FP64_PIPE_INSTR_PER_POINT = 1500.5
+# conversions included): 1460.5 per point.
+CLOSURE_FP64_INSTR_PER_POINT = 1318.9
+CLOSURE_FP64_PIPE_INSTR_PER_POINT = 1460.5
 # The closure's FP64 operation count when every exponential, logarithm, quotient and square root
 # is CUDA's own (the earlier form of this kernel): 3041 per point. Dividing it by the time of the
 # current kernel gives an effective rate, reported beside the measured-count roofline.
 CLOSURE_LIBM_FLOP_PER_POINT = 3041.0
-# DRAM bytes (read + write) per k_closure launch at 2048 x 256: 704 B per point measured at
-# 1024 x 256 (one-pass dram__bytes counters of the same launch) scaled by the point count.
-CLOSURE_DRAM_BYTES = 703.8 * 1024 * 256
+# DRAM bytes (read + write) per k_closure launch at 2048 x 256: 696 B per point measured at
+# 1024 x 256 (dram__bytes counters of the same launch) scaled by the point count.
+CLOSURE_DRAM_BYTES = 695.7 * 1024 * 256
 CLOSURE_DRAM_POINTS = 1024 * 256
 # FP64 operations (2 DFMA + DADD + DMUL) per cell centre and right-hand side over every kernel of
 # a step, from ncu's thread instruction counts of every launch of one step at 1024 x 256:
-# closure 2080.7, line operators 1104.9, pointwise kernels 781.3 (profiles/fp64_flops_sbli_1024x256.md).
-RHS_FP64_FLOP_PER_POINT = 3966.9
+# closure 1999.7, line operators 1104.9, pointwise kernels 781.3 (profiles/fp64_flops_sbli_1024x256.md;
+# the closure re-counted after its last change, the other kernels unchanged since their count).
+RHS_FP64_FLOP_PER_POINT = 3885.9
 # GB300 FP64 peak derived from the unit counts: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # hyp_thermo_eval (five-species air, FP64, every output): FP64 operations per state, 2 DFMA + DADD
 # + DMUL from ncu's thread instruction counts of one launch over 2e6 states of the sweep's
-# distribution (943.5 DFMA, 233.0 DADD, 597.7 DMUL per state; profiles/k_thermo_eval_sweep.md).
-THERMO_FP64_FLOP_PER_STATE = 2717.7
-THERMO_FP64_INSTR_PER_STATE = 1774.2
+# distribution (919.5 DFMA, 232.0 DADD, 585.6 DMUL per state; profiles/k_thermo_eval_sweep.md).
+THERMO_FP64_FLOP_PER_STATE = 2656.6
+THERMO_FP64_INSTR_PER_STATE = 1737.1
 # k_closure3 (the three-dimensional jet's closure, FP64): FP64 operations per cell from ncu's
 # thread instruction counts of the first launch after a warm-up step at 256 x 128 x 64 cells
-# (818.1 DFMA, 112.7 DADD, 523.8 DMUL per cell; profiles/k_closure3_jet.md).
-CLOSURE3_FP64_FLOP_PER_POINT = 2272.6
+# (794.1 DFMA, 111.7 DADD, 511.5 DMUL per cell; profiles/k_closure3_jet.md).
+CLOSURE3_FP64_FLOP_PER_POINT = 2211.3
 
 
 def parse():
