@@ -77,6 +77,25 @@ __device__ __forceinline__ dword dw_of(double x) {
     return {h, __uint_as_float((__float_as_uint(r) & 0x807fffffu) | ((unsigned)er << 23))};
 }
 
+// One step x <- r - c x of a first-order linear recurrence (|c| < 1) with the high and low words
+// on two separate dependency chains. The high word takes one product and one sum:
+//   c.h x.h = ph + pl exactly (FMA), r.h - ph = sh + sl exactly (two-sum).
+// The low word gathers the rounding errors, the low parts and the cross terms:
+//   x'.l = (sl - pl) + (r.l - c.l x.h) - c.h x.l.
+// The low word's own chain is one FMA, and the rest of its terms come off the high word's chain.
+// The pair is left unnormalised: it still represents r - c x to a few 2^-48 of the recurrence's
+// scale, and |c| < 1 keeps the low word small. A sequence of steps is thus bound by one product
+// and one sum per step, not by a normalised double-word multiply and subtract.
+__device__ __forceinline__ dword dw_step(dword x, dword r, dword c) {
+    const float ph = __fmul_rn(c.h, x.h);
+    const float pl = fmaf(c.h, x.h, -ph);
+    const float sh = __fsub_rn(r.h, ph);
+    const float bb = __fsub_rn(sh, r.h);
+    const float sl = __fadd_rn(__fsub_rn(r.h, __fsub_rn(sh, bb)), __fsub_rn(-ph, bb));
+    const float t = __fadd_rn(__fsub_rn(sl, pl), fmaf(-c.l, x.h, r.l));
+    return dword{sh, fmaf(-c.h, x.l, t)};
+}
+
 __device__ __forceinline__ double dw_to_f64(dword a) { return f64_of(a.h) + f64_of(a.l); }
 
 // the 8-byte forward-sweep slot holding a double word

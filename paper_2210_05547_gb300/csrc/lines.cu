@@ -27,12 +27,14 @@
 // interpolations and derivatives that feed only the diffusive fluxes) run it in plain binary32:
 // inputs are rounded with integer instructions, the recurrences run on the FP32 pipe, the forward
 // values of those rows are kept as binary32 in the first half of their 8-byte storage slot, and
-// outputs are widened back to binary64. Every other job (those feeding the convective fluxes,
-// the pressure and the divergences) runs it in double-word arithmetic (dword.cuh): each binary64
-// input is split into a pair of binary32 numbers, the recurrences carry their rounding errors in
-// the low word (error-free sums and FMA products, about 48 significand bits), the forward values
-// are kept as a binary32 pair in the 8-byte slot, and each output is the binary64 sum of its
-// pair. Closure rows and the first interior rows stay FP64.
+// outputs are widened back to binary64. The other derivatives (those feeding the convective
+// fluxes, the pressure and the divergences) form the adjacent differences of their inputs in
+// binary64 and run the recurrence in binary32 on those derivative-sized values (fwd_rows_cdiff).
+// The other interpolations run it in double-word arithmetic (dword.cuh): each binary64 input is
+// split into a pair of binary32 numbers, and the recurrences carry their rounding errors in the
+// low word (error-free sums and FMA products, about 48 significand bits). The forward values are
+// kept as a binary32 pair in the 8-byte slot, and each output is the binary64 sum of its pair.
+// Closure rows and the first interior rows stay FP64.
 #include "dword.cuh"
 #include "fp32.cuh"
 #include "internal.h"
@@ -186,12 +188,14 @@ __device__ __forceinline__ void fwd_rows_const32(int r, int r1, double& d, Windo
     p += (long long)n * ies;
 }
 
+// The row's right-hand side is formed off the recurrence's dependency chain; the recurrence step
+// itself is dw_step (one binary32 product and sum on the chain of the high word).
 template <int KIND>
 __device__ __forceinline__ dword interior_row_dw(dword d, dword p0, dword p1, dword p2, dword p3,
                                                  dword wa, dword wb, dword lm) {
     const dword s1 = KIND == 0 ? dw_add(p1, p2) : dw_sub(p2, p1);
     const dword s2 = KIND == 0 ? dw_add(p0, p3) : dw_sub(p3, p0);
-    return dw_sub(dw_add(dw_mul(wa, s1), dw_mul(wb, s2)), dw_mul(lm, d));
+    return dw_step(d, dw_add(dw_mul(wa, s1), dw_mul(wb, s2)), lm);
 }
 
 // The constant-factor rows r..r1 in double-word arithmetic (jobs not marked f32ok under
@@ -242,6 +246,60 @@ __device__ __forceinline__ void fwd_rows_constdw(int r, int r1, double& d, Windo
     p += (long long)n * ies;
 }
 
+// The constant-factor rows r..r1 of a derivative (KIND 1) under HYP_MIXED, jobs not marked
+// f32ok. The row's right-hand side wa (p2 - p1) + wb (p3 - p0) is built from the adjacent
+// differences of the inputs: each difference is formed in binary64 and rounded to binary32. A
+// difference of neighbours within a factor of two is exact in binary64, else within an ulp of
+// itself. p3 - p0 is the sum of three adjacent differences. The recurrence then runs in binary32
+// on derivative-sized values. Their rounding is relative to the derivative, not to the field it
+// differentiates: the cancellation that made binary32 inputs miss the error bound happens in
+// the binary64 differences.
+template <bool STORE>
+__device__ __forceinline__ void fwd_rows_cdiff(int r, int r1, double& d, Window& w,
+                                               const double* __restrict__& p, long long ies,
+                                               const LineOp& op, double* __restrict__ tmp,
+                                               long long oes) {
+    const int n = r1 - r + 1;
+    if (n <= 0) return;
+    const float wa = op.wac_f, wb = op.wbc_f, lm = op.lmc_f;
+    const double* __restrict__ pp = p;
+    float df = f32_of(d);
+    float e1 = f32_of(w.p1 - w.p0), e2 = f32_of(w.p2 - w.p1);
+    double q[PF];
+#pragma unroll
+    for (int k = 0; k < PF; ++k) q[k] = k < n ? pp[(long long)k * ies] : 0.0;
+    for (; r + PF - 1 <= r1; r += PF) {
+#pragma unroll
+        for (int k = 0; k < PF; ++k) {
+            const double x3 = q[k];
+            q[k] = r + PF + k <= r1 ? pp[(long long)(PF + k) * ies] : 0.0;
+            const float e3 = f32_of(x3 - w.p2);
+            const float rhs = fmaf(wa, e2, __fmul_rn(wb, __fadd_rn(__fadd_rn(e1, e2), e3)));
+            df = fmaf(-lm, df, rhs);
+            if (STORE) *slot32(tmp + (long long)(r + k) * oes) = df;
+            e1 = e2;
+            e2 = e3;
+            shift(w, x3);
+        }
+        pp += PF * ies;
+    }
+#pragma unroll
+    for (int k = 0; k < PF - 1; ++k) {
+        if (r + k <= r1) {
+            const double x3 = q[k];
+            const float e3 = f32_of(x3 - w.p2);
+            const float rhs = fmaf(wa, e2, __fmul_rn(wb, __fadd_rn(__fadd_rn(e1, e2), e3)));
+            df = fmaf(-lm, df, rhs);
+            if (STORE) *slot32(tmp + (long long)(r + k) * oes) = df;
+            e1 = e2;
+            e2 = e3;
+            shift(w, x3);
+        }
+    }
+    d = f64_of(df);
+    p += (long long)n * ies;
+}
+
 // Forward sweep over rows r..r1 of one kind of region (closure / per-row / constant interior).
 template <int KIND, bool STORE, int MODE>
 __device__ __forceinline__ void fwd_span(int r, int r1, double& d, Window& w,
@@ -274,8 +332,9 @@ __device__ __forceinline__ void fwd_span(int r, int r1, double& d, Window& w,
         }
         const int rcn = min(r1, li);
         if (r <= rcn) {
-            if (MODE == 1) fwd_rows_const32<KIND, STORE>(r, rcn, d, w, p, ies, op, tmp, oes);
-            else if (MODE == 2) fwd_rows_constdw<KIND, STORE>(r, rcn, d, w, p, ies, op, tmp, oes);
+            if constexpr (MODE == 1) fwd_rows_const32<KIND, STORE>(r, rcn, d, w, p, ies, op, tmp, oes);
+            else if constexpr (MODE == 2) fwd_rows_constdw<KIND, STORE>(r, rcn, d, w, p, ies, op, tmp, oes);
+            else if constexpr (MODE == 3) fwd_rows_cdiff<STORE>(r, rcn, d, w, p, ies, op, tmp, oes);
             else fwd_rows_const<KIND, STORE>(r, rcn, d, w, p, ies, op, tmp, oes);
             r = rcn + 1;
         }
@@ -418,14 +477,14 @@ __device__ __forceinline__ void back_rows_constdw(int r0, int r1, double& y,
             const int rn = r - PF_DW - k;
             q[k] = rn >= r1 ? dw_load(tmp + (long long)rn * oes) : dword{0.0f, 0.0f};
             if (OM >= 3) mq[k] = rn >= r1 ? met[rn] : 0.0;
-            yd = dw_sub(t, dw_mul(cc, yd));
+            yd = dw_step(yd, t, cc);
             if (OM != 0) put<OM>(out, oes, r - k, dw_to_f64(yd), m);
         }
     }
 #pragma unroll
     for (int k = 0; k < PF_DW - 1; ++k) {
         if (r - k >= r1) {
-            yd = dw_sub(q[k], dw_mul(cc, yd));
+            yd = dw_step(yd, q[k], cc);
             if (OM != 0) put<OM>(out, oes, r - k, dw_to_f64(yd), mq[k]);
         }
     }
@@ -445,7 +504,7 @@ __device__ __forceinline__ void back_span(int r0, int r1, double& y, const LineO
     if (r0 >= a) back_rows_var<OM>(r0, a, y, tmp, oes, op.cprime, met, out);
     const int c0 = min(r0, li), c1 = max(r1, rc);
     if (c0 >= c1) {
-        if (MODE == 1) back_rows_const32<OM>(c0, c1, y, tmp, oes, op.cpc_f, met_f, out);
+        if (MODE == 1 || MODE == 3) back_rows_const32<OM>(c0, c1, y, tmp, oes, op.cpc_f, met_f, out);
         else if (MODE == 2)
             back_rows_constdw<OM>(c0, c1, y, tmp, oes, dword{op.cpc_f, op.cpc_l}, met, out);
         else back_rows_const<OM>(c0, c1, y, tmp, oes, op.cpc, met, out);
@@ -475,7 +534,7 @@ __device__ __forceinline__ void backward(const LineOp& op, const double* __restr
     // the last row is a closure row (FP64 storage) or, for lines without one, an interior row
     const bool last_c = MODE != 0 && be >= op.rc && be <= op.last_interior;
     double y;
-    if (last_c && MODE == 1) y = f64_of(*slot32(tmp + (long long)be * oes));
+    if (last_c && (MODE == 1 || MODE == 3)) y = f64_of(*slot32(tmp + (long long)be * oes));
     else if (last_c) y = dw_to_f64(dw_load(tmp + (long long)be * oes));
     else y = tmp[(long long)be * oes];
     if (be <= e) put<OM>(out, oes, be, y, OM >= 3 ? met[be] : 0.0);
@@ -489,7 +548,8 @@ __device__ __forceinline__ void run_line(const LineJob& J, const LineOp& op,
                                          double* __restrict__ tmp, int s, int e, int m, int W,
                                          bool active, double wall) {
     if (active && s <= e) {
-        if (op.kind == 0) forward<0, MODE>(J, op, in, tmp, s, e, W, wall);
+        if constexpr (MODE == 3) forward<1, MODE>(J, op, in, tmp, s, e, W, wall);   // derivatives only
+        else if (op.kind == 0) forward<0, MODE>(J, op, in, tmp, s, e, W, wall);
         else forward<1, MODE>(J, op, in, tmp, s, e, W, wall);
     }
     __syncthreads();
@@ -542,6 +602,7 @@ __global__ void __launch_bounds__(LINE_BLOCK) k_lines(const LineJob* __restrict_
     // uniform per block: every thread of a block works on the same job
     if constexpr (MIXED) {
         if (J.f32ok) run_line<1>(J, op, in, out, tmp, s, e, m, W, active, wall);
+        else if (op.kind == 1) run_line<3>(J, op, in, out, tmp, s, e, m, W, active, wall);
         else run_line<2>(J, op, in, out, tmp, s, e, m, W, active, wall);
     } else {
         run_line<0>(J, op, in, out, tmp, s, e, m, W, active, wall);
