@@ -65,7 +65,8 @@ enum hyp_gas_kind {
  * coefficients (Blottner, Eucken, Wilke, Chapman-Enskog; Sec. 2.2.1, Eq. 19), the forward-rate
  * exponentials (Eq. 13), the species heat capacities and the weakly populated electronic levels
  * (theta / T >= 9) of the species thermodynamics (Sec. 2.2.1; in the right-hand side, whose
- * neighbouring cells share a choice per level, not in hyp_thermo_eval), and the interior rows of the compact
+ * neighbouring cells share a choice per level, not in hyp_thermo_eval), the Gaussian filter of
+ * the artificial diffusivities (Sec. 3.3), and the interior rows of the compact
  * interpolations and derivatives that feed only the diffusive fluxes (Sec. 3.1); in double-word
  * binary32 (each value a pair of binary32 words) the interior rows of the other compact operators;
  * in binary64 the Newton iteration for the temperature, the vibrational factors and populated

@@ -109,9 +109,10 @@ __global__ void kb_ad_raw(const BatchItem* __restrict__ items, BatchDev B) {
     });
 }
 
+template <bool MIXED>
 __global__ void kb_gauss(const BatchItem* __restrict__ items, BatchDev B, int dir) {
     for_tiles(items, B, SP_GAUSS, [&](const BatchItem& it, long long lo, long long hi) {
-        if (it.v.ad) gauss_body(it.v, it.s, dir, lo, hi, blockDim.x);
+        if (it.v.ad) gauss_body<MIXED>(it.v, it.s, dir, lo, hi, blockDim.x);
     });
 }
 
@@ -355,8 +356,13 @@ int launch_step(hyp_batch* b, cudaStream_t s) {
         HYP_CUDA(cudaEventRecord(b->join[0], s2));
         HYP_CUDA(cudaStreamWaitEvent(s, b->join[0], 0));
         kb_ad_raw<<<grid_for_tiles(b, SP_NC, pw), 256, 0, s>>>(b->d_items, B);
-        kb_gauss<<<grid_for_tiles(b, SP_GAUSS, pw), 256, 0, s>>>(b->d_items, B, 0);
-        kb_gauss<<<grid_for_tiles(b, SP_GAUSS, pw), 256, 0, s>>>(b->d_items, B, 1);
+        if (mixed) {
+            kb_gauss<true><<<grid_for_tiles(b, SP_GAUSS, pw), 256, 0, s>>>(b->d_items, B, 0);
+            kb_gauss<true><<<grid_for_tiles(b, SP_GAUSS, pw), 256, 0, s>>>(b->d_items, B, 1);
+        } else {
+            kb_gauss<false><<<grid_for_tiles(b, SP_GAUSS, pw), 256, 0, s>>>(b->d_items, B, 0);
+            kb_gauss<false><<<grid_for_tiles(b, SP_GAUSS, pw), 256, 0, s>>>(b->d_items, B, 1);
+        }
         kb_ad_combine<<<grid_for_tiles(b, SP_NC, pw), 256, 0, s>>>(b->d_items, B);
         kb_stress_c<<<grid_for_tiles(b, SP_NC, pw), 256, 0, s>>>(b->d_items, B);
         HYP_CUDA(cudaGetLastError());

@@ -46,4 +46,19 @@ __device__ __forceinline__ double f64_of(float x) {
     return __hiloint2double((int)hi, (int)(u << 29));
 }
 
+// binary64 -> binary32 by truncating the significand (relative error below 2^-23, towards zero),
+// magnitudes below binary32's normal range flushed to a signed zero, finite magnitudes above it
+// to infinity. Half the integer instructions of f32_of, for smoothing sums of nonnegative fields
+// where that error is immaterial (the mixed path's Gaussian filter of the artificial
+// diffusivities); NaN becomes infinity.
+__device__ __forceinline__ float f32_trunc(double x) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(u >> 32);
+    const int ex = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+    const unsigned sign = hi & 0x80000000u;
+    if (ex <= 0) return __uint_as_float(sign);
+    if (ex >= 255) return __uint_as_float(sign | 0x7f800000u);
+    return __uint_as_float(sign | ((unsigned)ex << 23) | ((hi & 0xfffffu) << 3) | ((unsigned)u >> 29));
+}
+
 }  // namespace hyp

@@ -18,6 +18,10 @@ inline constexpr double RK_B[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};
 // nine-point truncated Gaussian filter weights (centre, +-1, +-2, +-3, +-4)
 static __constant__ double c_gauss[5] = {3565.0 / 10368.0, 3091.0 / 12960.0, 1997.0 / 25920.0,
                                   149.0 / 12960.0, 107.0 / 103680.0};
+// the same weights rounded to binary32 (the mixed path's filter)
+static __constant__ float c_gauss_f[5] = {(float)(3565.0 / 10368.0), (float)(3091.0 / 12960.0),
+                                          (float)(1997.0 / 25920.0), (float)(149.0 / 12960.0),
+                                          (float)(107.0 / 103680.0)};
 
 enum Node { NC = 0, NXF = 1, NYF = 2, NCN = 3 };
 

@@ -288,6 +288,11 @@ __device__ __forceinline__ void ad_raw_body(bool cneq, const GridView& v,
 
 // Gaussian filter of the eight raw diffusivities along x (dir 0) or y (dir 1); indices clamp.
 // Index range: field f * nc + point.
+// MIXED: the filter in binary32 (truncated inputs, binary32 weights and sums, the result widened
+// exactly). The filtered fields are the artificial diffusivities, nonnegative and entering only the
+// diffusive fluxes, where the few 2^-24 of relative error are immaterial; in binary64 this
+// kernel is bound by the FP64 pipe (nine operations a point on eight fields).
+template <bool MIXED>
 __device__ __forceinline__ void gauss_body(const GridView& v, const Scratch& s, int dir,
                                            long long lo, long long hi, long long stride) {
     const long long n = (long long)v.nx * v.ny;
@@ -297,19 +302,38 @@ __device__ __forceinline__ void gauss_body(const GridView& v, const Scratch& s, 
         const double* __restrict__ in = dir == 0 ? s.raw[f] : s.filt[f];
         double* __restrict__ out = dir == 0 ? s.filt[f] : s.raw[f];
         const int j = idx / v.nx, i = idx - j * v.nx;
-        double acc = c_gauss[0] * in[idx];
-        if (dir == 0) {
-            const double* r = in + (long long)j * v.nx;
+        if constexpr (MIXED) {
+            float acc = __fmul_rn(c_gauss_f[0], f32_trunc(in[idx]));
+            if (dir == 0) {
+                const double* r = in + (long long)j * v.nx;
 #pragma unroll
-            for (int d = 1; d <= 4; ++d)
-                acc += c_gauss[d] * (r[max(i - d, 0)] + r[min(i + d, v.nx - 1)]);
+                for (int d = 1; d <= 4; ++d)
+                    acc = fmaf(c_gauss_f[d], __fadd_rn(f32_trunc(r[max(i - d, 0)]),
+                                                       f32_trunc(r[min(i + d, v.nx - 1)])), acc);
+            } else {
+#pragma unroll
+                for (int d = 1; d <= 4; ++d)
+                    acc = fmaf(c_gauss_f[d],
+                               __fadd_rn(f32_trunc(in[(long long)max(j - d, 0) * v.nx + i]),
+                                         f32_trunc(in[(long long)min(j + d, v.ny - 1) * v.nx + i])),
+                               acc);
+            }
+            out[idx] = f64_of(acc);
         } else {
+            double acc = c_gauss[0] * in[idx];
+            if (dir == 0) {
+                const double* r = in + (long long)j * v.nx;
 #pragma unroll
-            for (int d = 1; d <= 4; ++d)
-                acc += c_gauss[d] * (in[(long long)max(j - d, 0) * v.nx + i] +
-                                     in[(long long)min(j + d, v.ny - 1) * v.nx + i]);
+                for (int d = 1; d <= 4; ++d)
+                    acc += c_gauss[d] * (r[max(i - d, 0)] + r[min(i + d, v.nx - 1)]);
+            } else {
+#pragma unroll
+                for (int d = 1; d <= 4; ++d)
+                    acc += c_gauss[d] * (in[(long long)max(j - d, 0) * v.nx + i] +
+                                         in[(long long)min(j + d, v.ny - 1) * v.nx + i]);
+            }
+            out[idx] = acc;
         }
-        out[idx] = acc;
     }
 }
 

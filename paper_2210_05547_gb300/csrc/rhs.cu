@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "grid.h"
@@ -437,8 +438,9 @@ __global__ void k_ad_raw(int cneq, GridView v, const double* __restrict__ U, Scr
     ad_raw_body(cneq != 0, v, U, s, GRID_RANGE((long long)v.nx * v.ny));
 }
 
+template <bool MIXED>
 __global__ void k_gauss(GridView v, Scratch s, int dir) {
-    gauss_body(v, s, dir, GRID_RANGE((long long)AD_FIELDS * v.nx * v.ny));
+    gauss_body<MIXED>(v, s, dir, GRID_RANGE((long long)AD_FIELDS * v.nx * v.ny));
 }
 
 __global__ void k_ad_combine(GridView v, Scratch s) {
@@ -1138,8 +1140,13 @@ static int run_rhs(const hyp_gas* gas, hyp_grid* G, const double* U, double* dUd
     if (v.ad) {
         TIMED(KID_AD_RAW, (k_ad_raw<<<blocks_for(nc, 256), 256, 0, s>>>(g.kind == HYP_GAS_CNEQ, v, U, S)));
         const int gg = blocks_for(AD_FIELDS * nc, 256);
-        TIMED(KID_AD_GAUSS, (k_gauss<<<gg, 256, 0, s>>>(v, S, 0)));
-        TIMED(KID_AD_GAUSS, (k_gauss<<<gg, 256, 0, s>>>(v, S, 1)));
+        if (mixed) {
+            TIMED(KID_AD_GAUSS, (k_gauss<true><<<gg, 256, 0, s>>>(v, S, 0)));
+            TIMED(KID_AD_GAUSS, (k_gauss<true><<<gg, 256, 0, s>>>(v, S, 1)));
+        } else {
+            TIMED(KID_AD_GAUSS, (k_gauss<false><<<gg, 256, 0, s>>>(v, S, 0)));
+            TIMED(KID_AD_GAUSS, (k_gauss<false><<<gg, 256, 0, s>>>(v, S, 1)));
+        }
         TIMED(KID_AD_COMBINE, (k_ad_combine<<<blocks_for(nc, 256), 256, 0, s>>>(v, S)));
         HYP_CUDA(cudaGetLastError());
     }
@@ -1493,8 +1500,8 @@ extern "C" int hyp_rhs_noalloc(const hyp_gas* gas, const hyp_grid* grid, const d
         k_ad_prep<<<blocks_for(nc, 256), 256, 0, s>>>(v, S);
         k_ad_raw<<<blocks_for(nc, 256), 256, 0, s>>>(g.kind == HYP_GAS_CNEQ, v, U, S);
         const int gg = blocks_for(AD_FIELDS * nc, 256);
-        k_gauss<<<gg, 256, 0, s>>>(v, S, 0);
-        k_gauss<<<gg, 256, 0, s>>>(v, S, 1);
+        k_gauss<false><<<gg, 256, 0, s>>>(v, S, 0);
+        k_gauss<false><<<gg, 256, 0, s>>>(v, S, 1);
         k_ad_combine<<<blocks_for(nc, 256), 256, 0, s>>>(v, S);
         HYP_CUDA(cudaGetLastError());
     }

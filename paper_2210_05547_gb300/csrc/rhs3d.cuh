@@ -436,8 +436,20 @@ __global__ void k_adraw3(Grid3 g, View3 v, const double* __restrict__ U, int cne
 }
 
 // Gaussian filter of the raw diffusivities along one axis (x, y clamped; z periodic):
-// pass 0 raw -> filt (x), 1 filt -> raw (y), 2 raw -> filt (z)
+// pass 0 raw -> filt (x), 1 filt -> raw (y), 2 raw -> filt (z). MIXED: in binary32 as gauss_body
+// (pointwise.cuh) does for two-dimensional grids.
+template <typename R, bool MIXED>
+__device__ __forceinline__ R gauss3_load(const double* p) {
+    if constexpr (MIXED) return f32_trunc(*p);
+    else return *p;
+}
+
+__device__ __forceinline__ float gauss3_fma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double gauss3_fma(double a, double b, double c) { return fma(a, b, c); }
+
+template <bool MIXED>
 __global__ void k_gauss3(Grid3 g, int axis) {
+    using R = typename std::conditional<MIXED, float, double>::type;
     const Sh3 s = g.sh;
     const long long n = g.nc, pl = (long long)s.nx * s.ny;
     RANGE3((long long)AD_FIELDS * n) {
@@ -448,24 +460,33 @@ __global__ void k_gauss3(Grid3 g, int axis) {
         const int i = (int)(idx % s.nx);
         const long long t = idx / s.nx;
         const int j = (int)(t % s.ny), k = (int)(t / s.ny);
-        double acc = c_gauss[0] * in[idx];
+        const R* w;
+        if constexpr (MIXED) w = c_gauss_f;
+        else w = c_gauss;
+        R acc = w[0] * gauss3_load<R, MIXED>(in + idx);
         if (axis == 0) {
             const double* r = in + idx - i;
 #pragma unroll
-            for (int d = 1; d <= 4; ++d) acc += c_gauss[d] * (r[max(i - d, 0)] + r[min(i + d, s.nx - 1)]);
+            for (int d = 1; d <= 4; ++d)
+                acc = gauss3_fma(w[d], gauss3_load<R, MIXED>(r + max(i - d, 0)) +
+                                    gauss3_load<R, MIXED>(r + min(i + d, s.nx - 1)), acc);
         } else if (axis == 1) {
             const double* b = in + k * pl + i;
 #pragma unroll
             for (int d = 1; d <= 4; ++d)
-                acc += c_gauss[d] * (b[(long long)max(j - d, 0) * s.nx] + b[(long long)min(j + d, s.ny - 1) * s.nx]);
+                acc = gauss3_fma(w[d], gauss3_load<R, MIXED>(b + (long long)max(j - d, 0) * s.nx) +
+                                    gauss3_load<R, MIXED>(b + (long long)min(j + d, s.ny - 1) * s.nx),
+                          acc);
         } else {
             const double* b = in + (long long)j * s.nx + i;
 #pragma unroll
             for (int d = 1; d <= 4; ++d)
-                acc += c_gauss[d] * (b[(long long)(((k - d) % s.nz + s.nz) % s.nz) * pl] +
-                                     b[(long long)((k + d) % s.nz) * pl]);
+                acc = gauss3_fma(w[d], gauss3_load<R, MIXED>(b + (long long)(((k - d) % s.nz + s.nz) % s.nz) * pl) +
+                                    gauss3_load<R, MIXED>(b + (long long)((k + d) % s.nz) * pl),
+                          acc);
         }
-        out[idx] = acc;
+        if constexpr (MIXED) out[idx] = f64_of(acc);
+        else out[idx] = acc;
     }
 }
 
@@ -763,7 +784,10 @@ int run_rhs3(const hyp_gas* gas, hyp_grid* G, const double* U, double* dUdt, int
     HYP_CUDA(cudaStreamWaitEvent(s, G->join[0], 0));
     if (v.ad) {
         k_adraw3<<<blocks3(g->nc), 256, 0, s>>>(*g, v, U, gd.kind == HYP_GAS_CNEQ);
-        for (int ax = 0; ax < 3; ++ax) k_gauss3<<<blocks3(AD_FIELDS * g->nc), 256, 0, s>>>(*g, ax);
+        for (int ax = 0; ax < 3; ++ax) {
+            if (mx) k_gauss3<true><<<blocks3(AD_FIELDS * g->nc), 256, 0, s>>>(*g, ax);
+            else k_gauss3<false><<<blocks3(AD_FIELDS * g->nc), 256, 0, s>>>(*g, ax);
+        }
         k_adcombine3<<<blocks3(g->nc), 256, 0, s>>>(*g);
         HYP_CUDA(cudaGetLastError());
     }
