@@ -5,10 +5,10 @@ Chapman-Enskog; Sec. 2.2.1, Eq. 19), the forward-rate exponentials (Eq. 13), the
 capacities and the weakly populated electronic levels of the species thermodynamics (Sec. 2.2.1),
 the Gaussian filter of the artificial diffusivities (Sec. 3.3) and the interior rows of the
 compact operators that feed only the diffusive fluxes in binary32, the other derivatives'
-recurrences in binary32 on binary64 differences,
-the other interpolations in double-word binary32, and the rest (Newton iteration for T, the
-vibrational factors and populated electronic levels that set e_s, equilibrium constants, backward
-rates, divergences, fluxes, stage update) in binary64. The stated error of each output and the
+recurrences in binary32 on binary64 differences, the other interpolations in double-word
+binary32, and the rest (Newton iteration for T, the vibrational factors and populated electronic
+levels that set e_s, equilibrium constants, backward rates, divergences, fluxes, stage update) in
+binary64. The stated error of each output and the
 bound held here:
 
 * conversion (hyp_round_f32): equal to the hardware round-to-nearest-even for every result in the
