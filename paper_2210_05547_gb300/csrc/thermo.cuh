@@ -294,6 +294,30 @@ __host__ __device__ __forceinline__ double temperature_guess(const GasDev& g, do
     return Ta + t * h;
 }
 
+#ifdef __CUDACC__
+// The first-order shift of species_shift for the mixed-precision closure. The step is below
+// 1e-6 T (NEWTON_RTOL_MIXED), so the corrections of the partition function and vibrational
+// factor are at most 45 x 1e-6 of the value. They are formed in binary32, whose rounding stays
+// below 1e-11 of the value, and added in binary64. The energies and heat capacities take their
+// binary64 FMA. theta_v / T is not carried on, since nothing reads it after the shift.
+__device__ __forceinline__ void species_shift_f32(const GasDev& g, double T, double dT,
+                                                  SpeciesState& s) {
+    const float iT = __frcp_rn(f32_of(T));
+    const float dTf = f32_of(dT);
+    const float idT = __fmul_rn(iT, dTf);
+#pragma unroll
+    for (int i = 0; i < NSP; ++i) {
+        s.e[i] = fma(s.cv[i], dT, s.e[i]);
+        s.cv[i] = fma(s.cvp[i], dT, s.cv[i]);
+        s.qel[i] += f64_of(__fmul_rn(__fmul_rn(f32_of(s.qel[i]), f32_of(s.m1[i])), __fmul_rn(iT, idT)));
+        if (g.linear[i]) {
+            const float r = f32_of(s.iem1[i]);
+            s.iem1[i] += f64_of(__fmul_rn(__fmul_rn(f32_of(s.xv[i]), idT), __fmul_rn(__fadd_rn(1.0f, r), r)));
+        }
+    }
+}
+#endif
+
 // Safeguarded Newton for sum_s Y_s e_s(T) = e; s holds the species state at the returned T.
 // MIXED (device only): the electronic modal sums in binary32 (species_state_f32). Their rounding
 // moves sum_s Y_s e_s(T) by up to ~1e-8 c_v T, so successive Newton steps need not fall below
@@ -320,7 +344,11 @@ __host__ __device__ __forceinline__ double temperature_from_energy(const GasDev&
         if (f > 0.0) hi = T; else lo = T;
         double Tn = T - cl_div(f, cv);
         if (fabs(Tn - T) <= (MIXED ? NEWTON_RTOL_MIXED : NEWTON_RTOL) * T) {
-            species_shift(g, T, Tn - T, s);
+#ifdef __CUDA_ARCH__
+            if constexpr (MIXED) species_shift_f32(g, T, Tn - T, s);
+            else
+#endif
+                species_shift(g, T, Tn - T, s);
             return Tn;
         }
         if (!(Tn > lo && Tn < hi)) Tn = 0.5 * (lo + hi);
