@@ -255,7 +255,8 @@ int rebuild(hyp_batch* b, cudaStream_t s) {
         it.n[SP_NC] = nc;
         it.n[SP_FACES] = G->d.size(hyp::NXF) + G->d.size(hyp::NYF);
         it.n[SP_NCN] = G->d.size(hyp::NCN);
-        it.n[SP_GAUSS] = (long long)AD_FIELDS * nc;
+        // the binary32 filter's threads take every field of a point (gauss_body)
+        it.n[SP_GAUSS] = b->precision == HYP_MIXED ? nc : (long long)AD_FIELDS * nc;
         it.n[SP_STATE] = G->nstate;
         it.n[SP_FILTER] = G->cas.filter_sigma > 0.0 ? G->nstate : 0;
     }

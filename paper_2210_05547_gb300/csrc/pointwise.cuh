@@ -287,39 +287,54 @@ __device__ __forceinline__ void ad_raw_body(bool cneq, const GridView& v,
 }
 
 // Gaussian filter of the eight raw diffusivities along x (dir 0) or y (dir 1); indices clamp.
-// Index range: field f * nc + point.
-// MIXED: the filter in binary32 (truncated inputs, binary32 weights and sums, the result widened
-// exactly). The filtered fields are the artificial diffusivities, nonnegative and entering only the
-// diffusive fluxes, where the few 2^-24 of relative error are immaterial; in binary64 this
-// kernel is bound by the FP64 pipe (nine operations a point on eight fields).
+// FP64: index range field f * nc + point, one field value per thread (the filter is bound by the
+// FP64 pipe, nine operations a point; the threads' independent loads hide the latency).
+// MIXED: in binary32 (truncated inputs, binary32 weights and sums, the result widened exactly)
+// over the points, each thread filtering every field at its point, so the point's indices and
+// clamped neighbours are computed once for the eight fields (integer work bounds the binary32
+// form). The filtered fields are the artificial diffusivities, nonnegative and entering only the
+// diffusive fluxes, where the few 2^-24 of relative error are immaterial.
 template <bool MIXED>
 __device__ __forceinline__ void gauss_body(const GridView& v, const Scratch& s, int dir,
                                            long long lo, long long hi, long long stride) {
-    const long long n = (long long)v.nx * v.ny;
-    for (long long li = lo + threadIdx.x; li < hi; li += stride) {
-        const int f = (int)(li / n);
-        const int idx = (int)(li - f * n);
-        const double* __restrict__ in = dir == 0 ? s.raw[f] : s.filt[f];
-        double* __restrict__ out = dir == 0 ? s.filt[f] : s.raw[f];
-        const int j = idx / v.nx, i = idx - j * v.nx;
-        if constexpr (MIXED) {
-            float acc = __fmul_rn(c_gauss_f[0], f32_trunc(in[idx]));
+    if constexpr (MIXED) {
+        for (long long li = lo + threadIdx.x; li < hi; li += stride) {
+            const int idx = (int)li;
+            const int j = idx / v.nx, i = idx - j * v.nx;
+            int nb[8];                                   // neighbours -4..-1, +1..+4, clamped
             if (dir == 0) {
-                const double* r = in + (long long)j * v.nx;
 #pragma unroll
-                for (int d = 1; d <= 4; ++d)
-                    acc = fmaf(c_gauss_f[d], __fadd_rn(f32_trunc(r[max(i - d, 0)]),
-                                                       f32_trunc(r[min(i + d, v.nx - 1)])), acc);
+                for (int d = 1; d <= 4; ++d) {
+                    nb[d - 1] = j * v.nx + max(i - d, 0);
+                    nb[3 + d] = j * v.nx + min(i + d, v.nx - 1);
+                }
             } else {
 #pragma unroll
-                for (int d = 1; d <= 4; ++d)
-                    acc = fmaf(c_gauss_f[d],
-                               __fadd_rn(f32_trunc(in[(long long)max(j - d, 0) * v.nx + i]),
-                                         f32_trunc(in[(long long)min(j + d, v.ny - 1) * v.nx + i])),
-                               acc);
+                for (int d = 1; d <= 4; ++d) {
+                    nb[d - 1] = max(j - d, 0) * v.nx + i;
+                    nb[3 + d] = min(j + d, v.ny - 1) * v.nx + i;
+                }
             }
-            out[idx] = f64_of(acc);
-        } else {
+#pragma unroll 2
+            for (int f = 0; f < AD_FIELDS; ++f) {
+                const double* __restrict__ in = dir == 0 ? s.raw[f] : s.filt[f];
+                double* __restrict__ out = dir == 0 ? s.filt[f] : s.raw[f];
+                float acc = __fmul_rn(c_gauss_f[0], f32_trunc(in[idx]));
+#pragma unroll
+                for (int d = 1; d <= 4; ++d)
+                    acc = fmaf(c_gauss_f[d], __fadd_rn(f32_trunc(in[nb[d - 1]]), f32_trunc(in[nb[3 + d]])),
+                               acc);
+                out[idx] = f64_of(acc);
+            }
+        }
+    } else {
+        const long long n = (long long)v.nx * v.ny;
+        for (long long li = lo + threadIdx.x; li < hi; li += stride) {
+            const int f = (int)(li / n);
+            const int idx = (int)(li - f * n);
+            const double* __restrict__ in = dir == 0 ? s.raw[f] : s.filt[f];
+            double* __restrict__ out = dir == 0 ? s.filt[f] : s.raw[f];
+            const int j = idx / v.nx, i = idx - j * v.nx;
             double acc = c_gauss[0] * in[idx];
             if (dir == 0) {
                 const double* r = in + (long long)j * v.nx;

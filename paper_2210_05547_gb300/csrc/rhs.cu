@@ -440,7 +440,7 @@ __global__ void k_ad_raw(int cneq, GridView v, const double* __restrict__ U, Scr
 
 template <bool MIXED>
 __global__ void k_gauss(GridView v, Scratch s, int dir) {
-    gauss_body<MIXED>(v, s, dir, GRID_RANGE((long long)AD_FIELDS * v.nx * v.ny));
+    gauss_body<MIXED>(v, s, dir, GRID_RANGE((MIXED ? 1LL : (long long)AD_FIELDS) * v.nx * v.ny));
 }
 
 __global__ void k_ad_combine(GridView v, Scratch s) {
@@ -1139,7 +1139,7 @@ static int run_rhs(const hyp_gas* gas, hyp_grid* G, const double* U, double* dUd
     HYP_CUDA(cudaStreamWaitEvent(s, G->join[0], 0));
     if (v.ad) {
         TIMED(KID_AD_RAW, (k_ad_raw<<<blocks_for(nc, 256), 256, 0, s>>>(g.kind == HYP_GAS_CNEQ, v, U, S)));
-        const int gg = blocks_for(AD_FIELDS * nc, 256);
+        const int gg = blocks_for(mixed ? nc : AD_FIELDS * nc, 256);
         if (mixed) {
             TIMED(KID_AD_GAUSS, (k_gauss<true><<<gg, 256, 0, s>>>(v, S, 0)));
             TIMED(KID_AD_GAUSS, (k_gauss<true><<<gg, 256, 0, s>>>(v, S, 1)));

@@ -452,41 +452,42 @@ __global__ void k_gauss3(Grid3 g, int axis) {
     using R = typename std::conditional<MIXED, float, double>::type;
     const Sh3 s = g.sh;
     const long long n = g.nc, pl = (long long)s.nx * s.ny;
-    RANGE3((long long)AD_FIELDS * n) {
-        const int f = (int)(q / n);
-        const long long idx = q - f * n;
-        const double* __restrict__ in = axis == 1 ? g.filt[f] : g.raw[f];
-        double* __restrict__ out = axis == 1 ? g.raw[f] : g.filt[f];
+    const R* w;
+    if constexpr (MIXED) w = c_gauss_f;
+    else w = c_gauss;
+    // FP64: one field value per thread (field-major index range, as gauss_body); binary32: every
+    // field of a point per thread
+    RANGE3(MIXED ? n : (long long)AD_FIELDS * n) {
+        const int f0 = MIXED ? 0 : (int)(q / n);
+        const long long idx = q - (long long)f0 * n;
         const int i = (int)(idx % s.nx);
         const long long t = idx / s.nx;
         const int j = (int)(t % s.ny), k = (int)(t / s.ny);
-        const R* w;
-        if constexpr (MIXED) w = c_gauss_f;
-        else w = c_gauss;
-        R acc = w[0] * gauss3_load<R, MIXED>(in + idx);
-        if (axis == 0) {
-            const double* r = in + idx - i;
+        long long nb[8];                                 // neighbours -4..-1, +1..+4 (indices)
 #pragma unroll
-            for (int d = 1; d <= 4; ++d)
-                acc = gauss3_fma(w[d], gauss3_load<R, MIXED>(r + max(i - d, 0)) +
-                                    gauss3_load<R, MIXED>(r + min(i + d, s.nx - 1)), acc);
-        } else if (axis == 1) {
-            const double* b = in + k * pl + i;
-#pragma unroll
-            for (int d = 1; d <= 4; ++d)
-                acc = gauss3_fma(w[d], gauss3_load<R, MIXED>(b + (long long)max(j - d, 0) * s.nx) +
-                                    gauss3_load<R, MIXED>(b + (long long)min(j + d, s.ny - 1) * s.nx),
-                          acc);
-        } else {
-            const double* b = in + (long long)j * s.nx + i;
-#pragma unroll
-            for (int d = 1; d <= 4; ++d)
-                acc = gauss3_fma(w[d], gauss3_load<R, MIXED>(b + (long long)(((k - d) % s.nz + s.nz) % s.nz) * pl) +
-                                    gauss3_load<R, MIXED>(b + (long long)((k + d) % s.nz) * pl),
-                          acc);
+        for (int d = 1; d <= 4; ++d) {
+            if (axis == 0) {
+                nb[d - 1] = idx - i + max(i - d, 0);
+                nb[3 + d] = idx - i + min(i + d, s.nx - 1);
+            } else if (axis == 1) {
+                nb[d - 1] = idx + (long long)(max(j - d, 0) - j) * s.nx;
+                nb[3 + d] = idx + (long long)(min(j + d, s.ny - 1) - j) * s.nx;
+            } else {
+                nb[d - 1] = idx + (long long)(((k - d) % s.nz + s.nz) % s.nz - k) * pl;
+                nb[3 + d] = idx + (long long)((k + d) % s.nz - k) * pl;
+            }
         }
-        if constexpr (MIXED) out[idx] = f64_of(acc);
-        else out[idx] = acc;
+        for (int f = f0; f < (MIXED ? AD_FIELDS : f0 + 1); ++f) {
+            const double* __restrict__ in = axis == 1 ? g.filt[f] : g.raw[f];
+            double* __restrict__ out = axis == 1 ? g.raw[f] : g.filt[f];
+            R acc = w[0] * gauss3_load<R, MIXED>(in + idx);
+#pragma unroll
+            for (int d = 1; d <= 4; ++d)
+                acc = gauss3_fma(w[d], gauss3_load<R, MIXED>(in + nb[d - 1]) +
+                                           gauss3_load<R, MIXED>(in + nb[3 + d]), acc);
+            if constexpr (MIXED) out[idx] = f64_of(acc);
+            else out[idx] = acc;
+        }
     }
 }
 
@@ -785,7 +786,7 @@ int run_rhs3(const hyp_gas* gas, hyp_grid* G, const double* U, double* dUdt, int
     if (v.ad) {
         k_adraw3<<<blocks3(g->nc), 256, 0, s>>>(*g, v, U, gd.kind == HYP_GAS_CNEQ);
         for (int ax = 0; ax < 3; ++ax) {
-            if (mx) k_gauss3<true><<<blocks3(AD_FIELDS * g->nc), 256, 0, s>>>(*g, ax);
+            if (mx) k_gauss3<true><<<blocks3(g->nc), 256, 0, s>>>(*g, ax);
             else k_gauss3<false><<<blocks3(AD_FIELDS * g->nc), 256, 0, s>>>(*g, ax);
         }
         k_adcombine3<<<blocks3(g->nc), 256, 0, s>>>(*g);
