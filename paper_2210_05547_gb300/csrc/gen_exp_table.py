@@ -34,27 +34,39 @@ def f32(x: D) -> float:
     return struct.unpack("<f", struct.pack("<f", float(x)))[0]
 
 
-def main() -> None:
+def tables():
+    """(table, C_HI, C_LO, INV_C): 2^(j/256) for j = 0..255 as binary64, the Cody-Waite split of
+    ln2/256 and 256/ln2 as a binary32 value (held in a Python float)."""
     table = [float((D(j) / L * LN2).exp()) for j in range(L)]
     c = LN2 / L
     c_hi = trunc_bits(float(c), 33)
     c_lo = float(c - D(c_hi))
     inv = f32(D(L) / LN2)
+    return table, c_hi, c_lo, inv
+
+
+def render() -> str:
+    table, c_hi, c_lo, inv = tables()
+    out = ["// Generated by gen_exp_table.py: constants of the table-driven exponential\n",
+           "// (Tang 1989) in fp64_fast.cuh. Do not edit.\n#pragma once\n\n",
+           "namespace hyp {\n\n",
+           f"constexpr int EXP_TABLE_N = {L};\n",
+           f"constexpr double EXP_C_HI = {c_hi.hex()};   // ln2/256, 33 bits\n",
+           f"constexpr double EXP_C_LO = {c_lo.hex()};   // ln2/256 - EXP_C_HI\n",
+           f"constexpr float EXP_INV_C = {inv.hex()}f;   // 256/ln2 in binary32\n",
+           "// 2^(j/256), j = 0..255, each the binary64 nearest to the exact value\n",
+           "__device__ const double EXP_TABLE[EXP_TABLE_N] = {\n"]
+    for j in range(0, L, 3):
+        row = ", ".join(t.hex() for t in table[j:j + 3])
+        out.append(f"    {row},\n")
+    out.append("};\n\n}  // namespace hyp\n")
+    return "".join(out)
+
+
+def main() -> None:
     out = os.path.join(os.path.dirname(os.path.abspath(__file__)), "exp_table.h")
     with open(out, "w") as fh:
-        fh.write("// Generated by gen_exp_table.py: constants of the table-driven exponential\n")
-        fh.write("// (Tang 1989) in fp64_fast.cuh. Do not edit.\n#pragma once\n\n")
-        fh.write("namespace hyp {\n\n")
-        fh.write(f"constexpr int EXP_TABLE_N = {L};\n")
-        fh.write(f"constexpr double EXP_C_HI = {c_hi.hex()};   // ln2/256, 33 bits\n")
-        fh.write(f"constexpr double EXP_C_LO = {c_lo.hex()};   // ln2/256 - EXP_C_HI\n")
-        fh.write(f"constexpr float EXP_INV_C = {inv.hex()}f;   // 256/ln2 in binary32\n")
-        fh.write("// 2^(j/256), j = 0..255, each the binary64 nearest to the exact value\n")
-        fh.write("__device__ const double EXP_TABLE[EXP_TABLE_N] = {\n")
-        for j in range(0, L, 3):
-            row = ", ".join(t.hex() for t in table[j:j + 3])
-            fh.write(f"    {row},\n")
-        fh.write("};\n\n}  // namespace hyp\n")
+        fh.write(render())
     print(out)
 
 

@@ -35,33 +35,41 @@ def trunc_bits(x: float, bits: int) -> float:
     return struct.unpack("<d", struct.pack("<Q", u))[0]
 
 
-def main() -> None:
-    inv, t_hi, t_lo = [], [], []
+def tables():
+    """(rows, LN2_HI, LN2_LO): rows[j] = (inv_j, -log(inv_j) head, remainder) as binary64."""
+    rows = []
     for j in range(N):
         c = 1 + (D(j) + D("0.5")) / N
         v = float(1 / c)                       # Decimal -> binary64 rounds to nearest
         t = -D(v).ln()
         h = float(t)
-        inv.append(v)
-        t_hi.append(h)
-        t_lo.append(float(t - D(h)))
+        rows.append((v, h, float(t - D(h))))
     ln2 = D(2).ln()
     ln2_hi = trunc_bits(float(ln2), 42)
-    ln2_lo = float(ln2 - D(ln2_hi))
+    return rows, ln2_hi, float(ln2 - D(ln2_hi))
+
+
+def render() -> str:
+    rows, ln2_hi, ln2_lo = tables()
+    out = ["// Generated by gen_log_table.py: constants of the table-driven logarithm\n",
+           "// (Tang 1990, reciprocal form) in fp64_fast.cuh. Do not edit.\n#pragma once\n\n",
+           "namespace hyp {\n\n",
+           f"constexpr int LOG_TABLE_N = {N};\n",
+           f"constexpr double LOG_LN2_HI = {ln2_hi.hex()};   // ln2, 42 bits\n",
+           f"constexpr double LOG_LN2_LO = {ln2_lo.hex()};   // ln2 - LOG_LN2_HI\n",
+           "// per j: the binary64 nearest to 1 / (1 + (j + 1/2) / 128), then -log of that value\n",
+           "// as a head and the binary64 nearest to the remainder\n",
+           "__device__ const double LOG_TABLE[LOG_TABLE_N][3] = {\n"]
+    for v, h, lo in rows:
+        out.append(f"    {{{v.hex()}, {h.hex()}, {lo.hex()}}},\n")
+    out.append("};\n\n}  // namespace hyp\n")
+    return "".join(out)
+
+
+def main() -> None:
     out = os.path.join(os.path.dirname(os.path.abspath(__file__)), "log_table.h")
     with open(out, "w") as fh:
-        fh.write("// Generated by gen_log_table.py: constants of the table-driven logarithm\n")
-        fh.write("// (Tang 1990, reciprocal form) in fp64_fast.cuh. Do not edit.\n#pragma once\n\n")
-        fh.write("namespace hyp {\n\n")
-        fh.write(f"constexpr int LOG_TABLE_N = {N};\n")
-        fh.write(f"constexpr double LOG_LN2_HI = {ln2_hi.hex()};   // ln2, 42 bits\n")
-        fh.write(f"constexpr double LOG_LN2_LO = {ln2_lo.hex()};   // ln2 - LOG_LN2_HI\n")
-        fh.write("// per j: the binary64 nearest to 1 / (1 + (j + 1/2) / 128), then -log of that value\n")
-        fh.write("// as a head and the binary64 nearest to the remainder\n")
-        fh.write("__device__ const double LOG_TABLE[LOG_TABLE_N][3] = {\n")
-        for j in range(N):
-            fh.write(f"    {{{inv[j].hex()}, {t_hi[j].hex()}, {t_lo[j].hex()}}},\n")
-        fh.write("};\n\n}  // namespace hyp\n")
+        fh.write(render())
 
 
 if __name__ == "__main__":
