@@ -331,9 +331,12 @@ int launch_step(hyp_batch* b, cudaStream_t s) {
     const int mixed = b->precision == HYP_MIXED ? 1 : 0;
     const int pw = b->pw_blocks;
     cudaStream_t s2 = b->side;
+    // the sensors' cross-derivative interpolations (PH_AD1, PH_AD2) run in binary64 in both
+    // precisions, as in run_rhs
     auto lines = [&](int ph, cudaStream_t st) {
+        const int mx = (ph == PH_AD1 || ph == PH_AD2) ? 0 : mixed;
         return launch_lines(b->d_jobs + b->ph_start[ph], b->ph_count[ph], b->ph_blocks[ph],
-                            nullptr, st, mixed);
+                            nullptr, st, mx);
     };
     for (int stage = 0; stage < 3; ++stage) {
         HYP_CUDA(lines(PH_P1, s));

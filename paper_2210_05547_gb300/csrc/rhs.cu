@@ -1129,9 +1129,12 @@ static int run_rhs(const hyp_gas* gas, hyp_grid* G, const double* U, double* dUd
                                                       G->ph_blocks[PH_P3], U, s2, mx));
     HYP_CUDA(e1);
     if (v.ad) {
-        TIMED_ON(s2, KID_LINES_AD, e1 = launch_lines(G->jobs + G->ph_start[PH_AD1], 2, G->ph_blocks[PH_AD1], U, s2, mx));
+        // the two small interpolation phases of the sensors' cross derivatives run in binary64 in
+        // both precisions: with two jobs their lines cannot fill the GPU, and at that occupancy the
+        // binary64 recurrence (one FMA per row on its chain) beats the double-word one
+        TIMED_ON(s2, KID_LINES_AD, e1 = launch_lines(G->jobs + G->ph_start[PH_AD1], 2, G->ph_blocks[PH_AD1], U, s2, 0));
         HYP_CUDA(e1);
-        TIMED_ON(s2, KID_LINES_AD, e1 = launch_lines(G->jobs + G->ph_start[PH_AD2], 2, G->ph_blocks[PH_AD2], U, s2, mx));
+        TIMED_ON(s2, KID_LINES_AD, e1 = launch_lines(G->jobs + G->ph_start[PH_AD2], 2, G->ph_blocks[PH_AD2], U, s2, 0));
         HYP_CUDA(e1);
         TIMED_ON(s2, KID_AD_PREP, (k_ad_prep<<<blocks_for(nc, 256), 256, 0, s2>>>(v, S)));
     }
